@@ -1,0 +1,377 @@
+#!/usr/bin/env python3
+"""Benchmark of the octree multigrid solver on the 3D sphere workload.
+
+Workload (seeded, synthetic; the paper's convergence test geometry): the unit
+cube with 128^3 cells in 16^3-cell blocks (levels 16^3 .. 128^3 plus an 8^3
+coarse level), sphere f = |x - (1/2,1/2,1/2)| - 0.2 with phi = 1 on it, phi = 0
+on the walls, g = 0.  One step = one solve from phi = 0 to a relative residual
+of 1e-8: the right-hand side set-up and the whole V-cycle path (smoothing,
+residual, restriction, FAS right-hand side, coarse solve, prolongation) plus
+the convergence tests.
+
+Headline: V-cycle throughput of the mixed-precision solve (FP32 V-cycles in
+FP64 defect correction) in million leaf unknowns x V-cycles per second; the
+plain FP64 path is timed beside it.  Inputs are resident in HBM at the start
+of the timed region; L2 (129 MB) is flushed by writing a 512 MiB buffer
+before every timed step.  `e2e` repeats the measurement through the public
+API with the right-hand side copied from pinned host memory and the solution
+copied back inside the timed region.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank solves its own replica (replicas only: the method
+has no cross-problem exchange); the value is the sum over ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gmg_inputs as I  # noqa: E402
+
+METRIC = "V-cycle Munk/s"
+UNIT = "Munk/s"
+WORKLOAD = "sphere3d_128^3_16^3blocks_laplace_mixed_to_1e-8"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tol", type=float, default=1e-8)
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def build_tree(G, p):
+    t = G.Tree(p["dim"], p["N"], p["cb"], p["lo"], p["h1"], p["max_level"])
+    t.set_walls(p["walls"], values=p["wall_values"], fn=p["wall_fn"])
+    t.store_stencils(p["lsf"], p["phib"])
+    t.bind()
+    return t
+
+
+def algorithmic_bytes(kind, prec, level, t, leaf_level):
+    """Minimum HBM bytes one launch of a kernel must move (unique data)."""
+    S = 8 if prec == "fp64" else 4
+    nb, n, _ = t.level_info(level)
+    cells = nb * n ** 3
+    cut_cells = t.num_cut_blocks(level) * n ** 3
+    st = 7 * S  # 7-point stencil per cut cell
+    if kind == "smooth":  # read phi, read b and write phi of one colour
+        return cells * 2 * S + cut_cells * st / 2
+    if kind == "resid_restrict":  # read phi, b; write parent phi, b
+        return cells * (2 * S + 2 * S / 8) + cut_cells * st
+    if kind == "prolong":  # read/write phi, read parent phi, old
+        return cells * (2 * S + 2 * S / 8)
+    if kind == "fas_rhs":  # read phi, b; write b, old
+        return cells * 4 * S + cut_cells * st
+    if kind == "resid_norm":  # read phi64, b64 (+ write r32 in the mixed path)
+        return cells * (16 + 4) + cut_cells * 7 * 8
+    if kind == "accumulate":  # read e32, read/write phi64 on leaf cells
+        return cells * 20
+    return 0
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2205_09411_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_kind, prec, level):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = "%s %s %d" % (kernel_kind, prec, level)
+    src = source_hash()
+    with open(path) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            parts = line.split()
+            if len(parts) == 5 and " ".join(parts[:3]) == want and parts[4] == src:
+                return float(parts[3])
+    return None
+
+
+def cpu_baseline(p, budget_s=12.0):
+    """The oracle as it stands (serial FP64 C), on one host core: V-cycles of
+    the same workload from phi = 0 until the time budget is used."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from _helpers import oracle_problem
+    o = oracle_problem(p)
+    n = o.num_leaf_cells()
+    k, t0 = 0, time.perf_counter()
+    while True:
+        o.vcycle(1)
+        k += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or k >= 12:
+            break
+    return {"value": n * k / el / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d FP64 oracle V-cycles of the 128^3 workload from phi=0 (%.1f s, serial C)" % (k, el)}
+
+
+def run_reference(args):
+    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from _helpers import oracle_problem
+    p = I.problem("c2")
+    o = oracle_problem(p)
+    n = o.num_leaf_cells()
+    for _ in range(args.warmup):
+        o.vcycle(1)
+    o.set_rhs(np.zeros(n))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.vcycle(1)
+    el = time.perf_counter() - t0
+    v = n * args.steps / el / 1e6
+    out = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "step": "one FP64 oracle V-cycle (bounded sample)"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": "%d serial FP64 oracle V-cycles of the 128^3 workload" % args.steps},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def run_ours(args):
+    import torch
+    import paper_2205_09411_gb300 as G
+    world, rank, local = dist_setup(args.gpus)
+    assert torch.cuda.is_available(), "bench needs a CUDA device"
+    torch.cuda.set_device(local)
+    G.build()
+    p = I.problem("c2")
+    t_setup = time.perf_counter()
+    t = build_tree(G, p)
+    t_setup = time.perf_counter() - t_setup
+    n = t.n_leaf_cells
+    g = np.asarray(p["rhs"](t.leaf_centers()), dtype=np.float64)
+    g_dev = torch.tensor(g, device="cuda")
+    g_pin = torch.tensor(g).pin_memory()
+    out_pin = torch.zeros(n, dtype=torch.float64).pin_memory()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def solve(prec):
+        t.set_rhs(g_dev)
+        st = t.solve(prec, args.tol, 60)
+        return st, t.last_launch_count() + 1
+
+    for _ in range(args.warmup):
+        solve(G.MIXED)
+        solve(G.FP64)
+    torch.cuda.synchronize()
+
+    def timed(prec, profile=False, e2e=False):
+        times, cycles, launches = [], 0, 0
+        if profile:
+            t.profile(True)
+            t.profile_read()
+        barrier(world)
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if e2e:
+                t.set_rhs(g_pin)
+                st = t.solve(prec, args.tol, 60)
+                t.solution(out_pin)
+                nl = t.last_launch_count() + 2
+            else:
+                st, nl = solve(prec)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            cycles += st["cycles"]
+            launches += nl
+        torch.cuda.synchronize()
+        barrier(world)
+        prof = t.profile_read() if profile else None
+        if profile:
+            t.profile(False)
+        total = allreduce_max(sum(times), world)
+        return dict(times=times, total_ms=total, cycles=cycles, launches=launches, prof=prof, rel=st["rel_l2"])
+
+    clocks = Clocks(local)
+    clocks.start()
+    mixed = timed(G.MIXED, profile=True)
+    clk = clocks.stop()
+    fp64 = timed(G.FP64)
+    e2e = timed(G.MIXED, e2e=True)
+
+    def munks(r):
+        return world * n * r["cycles"] / (r["total_ms"] * 1e-3) / 1e6
+
+    def lat(r):
+        ts = sorted(r["times"])
+        return {"p50_ms": float(np.percentile(ts, 50)), "p99_ms": float(np.percentile(ts, 99)),
+                "solves_per_s": world * len(ts) / (r["total_ms"] * 1e-3), "cycles_per_solve": r["cycles"] / len(ts)}
+
+    # roofline of the dominant kernel (largest total time in the timed region)
+    peak, peak_kind = peaks()
+    by_kind = {}
+    for kind, prec, level, cnt, ms in mixed["prof"]:
+        by_kind.setdefault((kind, prec), 0.0)
+        by_kind[(kind, prec)] += ms
+    prof_total = sum(by_kind.values())
+    dom_kind, dom_prec = max(by_kind, key=by_kind.get)
+    rows = [r for r in mixed["prof"] if r[0] == dom_kind and r[1] == dom_prec]
+    lev = max(rows, key=lambda r: r[4])[2]
+    row = [r for r in rows if r[2] == lev][0]
+    per_launch_ms = row[4] / row[3]
+    alg = algorithmic_bytes(dom_kind, dom_prec, lev, t, t.lmax)
+    achieved = alg / (per_launch_ms * 1e-3) / 1e9
+    traffic = ncu_traffic(dom_kind, dom_prec, lev)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "%s_%s_level%d" % (dom_kind, dom_prec, lev),
+                "per_launch_us": per_launch_ms * 1e3, "algorithmic_bytes": alg,
+                "share_of_kernel_time": by_kind[(dom_kind, dom_prec)] / prof_total,
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind}
+
+    result = {
+        "metric": METRIC, "value": munks(mixed), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mixed["total_ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "unknowns": n, "block": "16^3", "levels": [t.lmin, t.lmax],
+                   "cut_blocks_finest": t.num_cut_blocks(t.lmax), "tol": args.tol,
+                   "l2": "flushed before every timed step (512 MiB write)", "parallelism": "replicas",
+                   "setup_s": t_setup},
+        "mixed": lat(mixed) | {"munks": munks(mixed), "final_rel_residual": mixed["rel"]},
+        "fp64": lat(fp64) | {"munks": munks(fp64), "final_rel_residual": fp64["rel"]},
+        "e2e": {"value": munks(e2e), "unit": UNIT, "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
+        "gpu_launches": mixed["launches"],
+        "roofline": roofline,
+        "kernel_ms_by_kind": {"%s_%s" % k: v for k, v in sorted(by_kind.items(), key=lambda kv: -kv[1])},
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1:
+        result["cpu_baseline"] = cpu_baseline(p)
+    if rank == 0:
+        print(json.dumps(result))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

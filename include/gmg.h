@@ -1,0 +1,211 @@
+/*
+ * gmg.h - C ABI of the GB300 octree geometric-multigrid Poisson solver with
+ * level-set Dirichlet boundaries (method of Teunissen & Schiavello,
+ * arXiv 2205.09411).
+ *
+ * The library solves  Laplacian(phi) = g  (Sec. 1, Eq. (poisson) with a
+ * constant coefficient) on a quadtree/octree of N^D-cell blocks (Sec. 2.1).
+ * Irregular Dirichlet boundaries are the zero contour of a level-set
+ * function (Sec. 3.1); their distances to cell centres come from line
+ * searches (Sec. 3.2) and enter per-block stored cut-cell stencils
+ * (Sec. 3.3, Sec. 3.6.2).  The solver is a FAS multigrid V-cycle with
+ * red-black Gauss-Seidel smoothing, mean restriction, (bi/tri)linear
+ * prolongation and an exact coarse-level solve (Sec. 2.2, Sec. 3.4, 3.5).
+ *
+ * Conventions for every function:
+ *  - return value: GMG_OK (0) or a negative GMG_ERR_* code; the message of
+ *    the last error of the calling thread is gmg_last_error().
+ *  - "host" pointers are ordinary CPU memory owned by the caller; the
+ *    library copies what it needs before returning.  "device" pointers are
+ *    CUDA global memory of the current device, borrowed for the call only.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream); device
+ *    work is enqueued on it and the call returns without waiting, except
+ *    where a function says it synchronises.
+ *  - leaf-cell order: leaf blocks by increasing level, inside a level by
+ *    increasing Morton code of the block's integer coordinates (x lowest
+ *    bit); inside a block, cells x-fastest then y then z.
+ *  - a gmg_tree owns all the device memory it uses: either one workspace
+ *    the caller binds (gmg_tree_bind with a device pointer) or one the
+ *    library allocates itself (gmg_tree_bind with NULL).  It stays valid
+ *    until gmg_tree_destroy.  A tree is not thread-safe.
+ */
+#ifndef GMG_H
+#define GMG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define GMG_OK 0
+#define GMG_ERR_INVALID_ARG (-1)   /* a size, pointer or option is out of range   */
+#define GMG_ERR_OOM (-2)           /* workspace too small or allocation refused    */
+#define GMG_ERR_CUDA (-3)          /* a CUDA runtime call failed                   */
+#define GMG_ERR_NOT_CONVERGED (-4) /* the tolerance was not met in max_cycles      */
+#define GMG_ERR_NONFINITE (-5)     /* a residual norm became NaN/Inf or diverged   */
+#define GMG_ERR_STATE (-6)         /* call out of order (e.g. solve before bind)   */
+#define GMG_ERR_TIMEOUT (-7)       /* a bounded device-side wait ran out           */
+
+/* domain wall boundary conditions (reading W of the design notes) */
+#define GMG_WALL_DIRICHLET 0
+#define GMG_WALL_NEUMANN 1 /* zero normal derivative */
+
+/* built-in level-set functions f(x); f < 0 inside the object (Sec. 3.1) */
+#define GMG_LSF_NONE 0
+#define GMG_LSF_SPHERE 1    /* p[0..2] centre c, p[3] radius R: |x - c| - R, Eq. (lsf-example) */
+#define GMG_LSF_CAPSULE 2   /* p[0..2] a, p[3..5] b, p[6] r: distance to segment ab minus r   */
+#define GMG_LSF_ELLIPSOID 3 /* p[0..2] c, p[3..11] rotation Q (row-major), p[12..14] semi-axes s:
+                               min(s) * (|diag(s)^-1 Q^T (x - c)| - 1)                         */
+#define GMG_LSF_CALLBACK 4  /* the host function `fn` */
+
+/* solver arithmetic */
+#define GMG_FP64 0  /* FAS V-cycles in FP64                                            */
+#define GMG_MIXED 1 /* FP64 defect correction around FP32 V-cycles; the fine residual,
+                       the solution update and the coarsest-level solve stay in FP64  */
+
+/* where a caller's array lives */
+#define GMG_HOST 0
+#define GMG_DEVICE 1
+
+typedef struct gmg_tree gmg_tree;
+
+/* host callback: value at point x[3] (unused coordinates are 0) */
+typedef double (*gmg_fn)(const double *x, void *user);
+/* host callback: refine block bix[3] of `level` (1 = root level)? nonzero = yes */
+typedef int (*gmg_refine_fn)(int level, const int *bix, void *user);
+
+typedef struct {
+  int dim;               /* 2 or 3                                                      */
+  int block_n;           /* cells per block side N: even, 4 <= N <= 16 (3D), <= 32 (2D)  */
+  int coarse_blocks[3];  /* root blocks per side (level 1)                              */
+  double lo[3];          /* domain corner                                               */
+  double h_root;         /* cell size on level 1 (cubic cells)                          */
+  int max_level;         /* finest level allowed, 1..20                                 */
+  int max_coarse_cells;  /* coarsest-level size for the direct solve; 0 = 64 (2D) / 512 (3D) */
+  gmg_refine_fn refine;  /* NULL: refine every block up to max_level (uniform tree)     */
+  void *refine_user;
+} gmg_domain;
+
+typedef struct {
+  int kind;     /* GMG_LSF_*                        */
+  double p[16]; /* parameters of the built-in kinds */
+  gmg_fn fn;    /* GMG_LSF_CALLBACK: f(x, user)     */
+  void *user;
+} gmg_lsf;
+
+typedef struct {
+  int n_down;         /* GSRB sweeps before restriction (Sec. 2.2; default 2)          */
+  int n_up;           /* GSRB sweeps after prolongation (default 2)                    */
+  double eps_tol;     /* line-search relative tolerance (Sec. 3.2; default 1e-8)       */
+  double mask_factor; /* L = mask_factor sqrt(D) dx in Eq. (boundary-mask) (1.5)        */
+  double w_min;       /* unresolved-root threshold of Sec. 3.6.3 (0 = off)             */
+} gmg_params;
+
+typedef struct {
+  int cycles;     /* V-cycles run (FP64) or defect-correction steps (mixed)    */
+  double rel_l2;  /* final ||b - A phi||_2 / ||b||_2 over leaf cells           */
+  double linf;    /* final max |b - A phi|                                      */
+  double bnorm;   /* ||b||_2                                                   */
+} gmg_stats;
+
+/* Fills *p with the defaults of Sec. 2.2, 3.2 and 3.6.1. */
+void gmg_default_params(gmg_params *p);
+
+/* Builds the block tree (Sec. 2.1) on the host: root blocks at level 1,
+ * refinement decided by domain->refine level by level, then closed under
+ * 2:1 balance across faces, edges and corners; levels below 1 coarsen inside
+ * the root blocks until the coarsest level has at most max_coarse_cells
+ * cells (the coarse-grid solve of Sec. 3.5 is exact on that level).
+ * params may be NULL (defaults).  No device memory is touched.
+ * Errors: INVALID_ARG for sizes out of range. */
+int gmg_tree_create(const gmg_domain *domain, const gmg_params *params, gmg_tree **out);
+void gmg_tree_destroy(gmg_tree *tree);
+
+/* Tree shape: level range, number of leaf cells, number of blocks. */
+int gmg_tree_info(const gmg_tree *tree, int *lmin, int *lmax, long long *n_leaf_cells, long long *n_blocks);
+/* Level shape: number of blocks, cells per block side, cell size. */
+int gmg_level_info(const gmg_tree *tree, int level, int *n_blocks, int *block_n, double *h);
+/* Blocks of one level in canonical order: bix[3*i..], has_children[i] (host arrays). */
+int gmg_level_blocks(const gmg_tree *tree, int level, int *bix, int *has_children);
+/* Cell centres of the leaf cells (host array of n_leaf_cells * dim doubles). */
+int gmg_leaf_centers(const gmg_tree *tree, double *xyz);
+
+/* Domain-wall conditions (2*dim entries, order -x,+x,-y,+y,-z,+z).  Dirichlet
+ * values come from fn(x_face, user) when fn != NULL, else from values[]. */
+int gmg_set_walls(gmg_tree *tree, const int *types, const double *values, gmg_fn fn, void *user);
+
+/* Boundary detection and stencils (Sec. 3.2, 3.3, 3.6): on every level the
+ * mask of Eq. (boundary-mask), line searches toward the 2D neighbour
+ * centres, the unresolved-root search of Sec. 3.6.3 (if w_min > 0), the
+ * cut-cell coefficients of Eq. (lpl-1d-lsf) with the coefficients of
+ * boundary neighbours moved to the right-hand side (value phib(x0, user) at
+ * the root x0, or phib_const when phib == NULL), the Dirichlet wall terms,
+ * and the coarsest-level inverse.  Runs on the host before gmg_tree_bind
+ * (results are uploaded by gmg_tree_bind).  Errors: STATE if already bound. */
+int gmg_store_stencils(gmg_tree *tree, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, double phib_const);
+
+/* Number of bytes of device workspace the tree needs (after
+ * gmg_store_stencils): tables, FP64 and FP32 level fields, stencil pools,
+ * coarse inverse, reduction scratch.  256-byte alignment is enough. */
+int gmg_workspace_bytes(const gmg_tree *tree, size_t *bytes);
+/* Binds the device workspace: `device_ptr` (caller-owned, at least
+ * gmg_workspace_bytes, 256-byte aligned; it must outlive the tree) or NULL
+ * (the library allocates it with cudaMalloc and frees it at destroy), and
+ * uploads tables and stencils.  Synchronises the device.
+ * Errors: STATE before gmg_store_stencils, OOM, CUDA. */
+int gmg_tree_bind(gmg_tree *tree, void *device_ptr, size_t bytes);
+
+/* Right-hand side g on the leaf cells (leaf-cell order, FP64, host or device
+ * by `where`): sets b = g - (moved boundary terms) - (Dirichlet wall terms)
+ * and phi = 0 on every level (zero initial guess). */
+int gmg_set_rhs(gmg_tree *tree, const double *g, int where, void *stream);
+/* Initial guess on the leaf cells (covered cells get the mean of their children). */
+int gmg_set_solution(gmg_tree *tree, const double *phi, int where, void *stream);
+/* Copies phi on the leaf cells to `phi` (host: synchronises the stream). */
+int gmg_get_solution(gmg_tree *tree, double *phi, int where, void *stream);
+
+/* n_cycles FAS V-cycles in FP64 (Sec. 2.2: N_down sweeps, restriction of
+ * phi and of the residual, coarse right-hand side A phi + R r, exact coarse
+ * solve, (bi/tri)linear prolongation of the correction, N_up sweeps). */
+int gmg_vcycle(gmg_tree *tree, int n_cycles, void *stream);
+/* Composite residual ||b - A phi||_2 over leaf cells, relative to ||b||_2,
+ * and max |b - A phi|.  Synchronises the stream. */
+int gmg_residual(gmg_tree *tree, double *rel_l2, double *linf, void *stream);
+/* Solves to ||b - A phi||_2 <= rel_tol ||b||_2 from the current phi with
+ * GMG_FP64 V-cycles or GMG_MIXED defect correction; stats may be NULL.
+ * Synchronises once per cycle (the convergence test).
+ * Errors: NOT_CONVERGED after max_cycles, NONFINITE on NaN or growth. */
+int gmg_solve(gmg_tree *tree, int precision, double rel_tol, int max_cycles, gmg_stats *stats, void *stream);
+
+/* Inspection (tests, tools): phi (which = 0) or b (which = 1) of every cell
+ * of a level in canonical block order, FP64 host array; distances d
+ * (nb * N^D * 2D) and mask flags (nb * N^D) of a level. */
+int gmg_get_level(gmg_tree *tree, int level, int which, double *out, void *stream);
+int gmg_get_distances(const gmg_tree *tree, int level, double *out);
+int gmg_get_mask(const gmg_tree *tree, int level, int *out);
+int gmg_num_cut_blocks(const gmg_tree *tree, int level);
+
+/* Number of kernels the last gmg_vcycle / gmg_solve call enqueued. */
+long long gmg_last_launch_count(const gmg_tree *tree);
+
+/* Kernel timing: while enabled, every kernel the tree enqueues is bracketed
+ * by CUDA events on its stream.  gmg_profile_read synchronises, aggregates
+ * the recorded launches per (kernel kind, precision, level) into the caller's
+ * arrays (up to `cap` entries: kind, prec 0 = FP64 / 1 = FP32, level,
+ * launches, total milliseconds), clears the record and returns the number of
+ * entries (or a negative error).  Kinds: 0 smooth, 1 residual+restrict,
+ * 2 FAS right-hand side, 3 coarse solve, 4 prolongation, 5 restriction of
+ * phi, 6 residual norm, 7 norm reduction, 8 mixed-path accumulation,
+ * 9 right-hand side / copies. */
+int gmg_profile_enable(gmg_tree *tree, int enable);
+int gmg_profile_read(gmg_tree *tree, int cap, int *kind, int *prec, int *level, long long *launches, double *ms);
+
+const char *gmg_error_string(int code);
+const char *gmg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,352 @@
+"""GB300-native octree geometric-multigrid Poisson solver with level-set
+Dirichlet boundaries (method of Teunissen & Schiavello, arXiv 2205.09411).
+
+This module is a thin ctypes binding of the CUDA library ``libgmg.so`` (C ABI
+in ``include/gmg.h``): it marshals arguments and allocates the device
+workspace through PyTorch.  Every step of the solver runs in the library's
+CUDA kernels; there is no CPU fallback.  Importing works without a GPU (the
+tree and its set-up are host work); calls that need the device raise if the
+library or CUDA is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["Tree", "load", "build", "GmgError", "FP64", "MIXED", "LIB_PATH"]
+
+LIB_PATH = _build.LIB
+FP64, MIXED = 0, 1
+HOST, DEVICE = 0, 1
+WALL_DIRICHLET, WALL_NEUMANN = 0, 1
+LSF_KINDS = {"none": 0, "sphere": 1, "capsule": 2, "ellipsoid": 3, "callback": 4}
+
+FN = C.CFUNCTYPE(C.c_double, C.POINTER(C.c_double), C.c_void_p)
+REFINE_FN = C.CFUNCTYPE(C.c_int, C.c_int, C.POINTER(C.c_int), C.c_void_p)
+
+
+class Domain(C.Structure):
+    _fields_ = [("dim", C.c_int), ("block_n", C.c_int), ("coarse_blocks", C.c_int * 3), ("lo", C.c_double * 3),
+                ("h_root", C.c_double), ("max_level", C.c_int), ("max_coarse_cells", C.c_int),
+                ("refine", REFINE_FN), ("refine_user", C.c_void_p)]
+
+
+class Lsf(C.Structure):
+    _fields_ = [("kind", C.c_int), ("p", C.c_double * 16), ("fn", FN), ("user", C.c_void_p)]
+
+
+class Params(C.Structure):
+    _fields_ = [("n_down", C.c_int), ("n_up", C.c_int), ("eps_tol", C.c_double), ("mask_factor", C.c_double),
+                ("w_min", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("cycles", C.c_int), ("rel_l2", C.c_double), ("linf", C.c_double), ("bnorm", C.c_double)]
+
+
+class GmgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("gmg error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def build(force=False, verbose=False):
+    """Compile libgmg.so for sm_103a (in-tree)."""
+    return _build.build(force=force, verbose=verbose)
+
+
+def load():
+    """Load the compiled library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libgmg.so is missing (%s): run __graft_entry__.build() or "
+                           "python -m paper_2205_09411_gb300.build" % LIB_PATH)
+    L = C.CDLL(LIB_PATH)
+    vp, dp, ip, sz = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_size_t
+    sigs = {
+        "gmg_default_params": (None, [C.POINTER(Params)]),
+        "gmg_tree_create": (C.c_int, [C.POINTER(Domain), C.POINTER(Params), C.POINTER(vp)]),
+        "gmg_tree_destroy": (None, [vp]),
+        "gmg_tree_info": (C.c_int, [vp, ip, ip, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+        "gmg_level_info": (C.c_int, [vp, C.c_int, ip, ip, dp]),
+        "gmg_level_blocks": (C.c_int, [vp, C.c_int, ip, ip]),
+        "gmg_leaf_centers": (C.c_int, [vp, dp]),
+        "gmg_set_walls": (C.c_int, [vp, ip, dp, FN, vp]),
+        "gmg_store_stencils": (C.c_int, [vp, C.POINTER(Lsf), FN, vp, C.c_double]),
+        "gmg_workspace_bytes": (C.c_int, [vp, C.POINTER(sz)]),
+        "gmg_tree_bind": (C.c_int, [vp, vp, sz]),
+        "gmg_set_rhs": (C.c_int, [vp, vp, C.c_int, vp]),
+        "gmg_set_solution": (C.c_int, [vp, vp, C.c_int, vp]),
+        "gmg_get_solution": (C.c_int, [vp, vp, C.c_int, vp]),
+        "gmg_vcycle": (C.c_int, [vp, C.c_int, vp]),
+        "gmg_residual": (C.c_int, [vp, dp, dp, vp]),
+        "gmg_solve": (C.c_int, [vp, C.c_int, C.c_double, C.c_int, C.POINTER(Stats), vp]),
+        "gmg_get_level": (C.c_int, [vp, C.c_int, C.c_int, dp, vp]),
+        "gmg_get_distances": (C.c_int, [vp, C.c_int, dp]),
+        "gmg_get_mask": (C.c_int, [vp, C.c_int, ip]),
+        "gmg_num_cut_blocks": (C.c_int, [vp, C.c_int]),
+        "gmg_last_launch_count": (C.c_longlong, [vp]),
+        "gmg_profile_enable": (C.c_int, [vp, C.c_int]),
+        "gmg_profile_read": (C.c_int, [vp, C.c_int, ip, ip, ip, C.POINTER(C.c_longlong), dp]),
+        "gmg_error_string": (C.c_char_p, [C.c_int]),
+        "gmg_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != 0:
+        L = load()
+        raise GmgError(rc, "%s: %s" % (L.gmg_error_string(rc).decode(), L.gmg_last_error().decode()))
+
+
+def _fn(f):
+    if f is None:
+        return FN()
+
+    def cb(xp, _u):
+        return float(f(np.ctypeslib.as_array(xp, shape=(3,)).copy()))
+    return FN(cb)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Tree:
+    """One Poisson problem on a block-structured quadtree/octree.
+
+    Life cycle: ``Tree(...)`` (host tree) -> ``set_walls`` -> ``store_stencils``
+    (boundary set-up) -> ``bind()`` (device workspace) -> ``set_rhs`` ->
+    ``vcycle`` / ``solve`` -> ``solution``.
+    """
+
+    def __init__(self, dim, block_n, coarse_blocks=(1, 1, 1), lo=(0.0, 0.0, 0.0), h_root=None, max_level=1,
+                 refine=None, max_coarse_cells=0, n_down=2, n_up=2, eps_tol=1e-8, mask_factor=1.5, w_min=0.0):
+        L = load()
+        self.dim = dim
+        cb = list(coarse_blocks) + [1] * (3 - len(coarse_blocks))
+        lo = list(lo) + [0.0] * (3 - len(lo))
+        if h_root is None:
+            h_root = 1.0 / (cb[0] * block_n)
+        dom = Domain()
+        dom.dim, dom.block_n = dim, block_n
+        for d in range(3):
+            dom.coarse_blocks[d] = int(cb[d])
+            dom.lo[d] = float(lo[d])
+        dom.h_root, dom.max_level, dom.max_coarse_cells = float(h_root), int(max_level), int(max_coarse_cells)
+        if refine is not None:
+            def rcb(level, bix, _u):
+                return 1 if refine(level, (bix[0], bix[1], bix[2])) else 0
+            self._refine = REFINE_FN(rcb)
+        else:
+            self._refine = REFINE_FN()
+        dom.refine = self._refine
+        prm = Params(n_down, n_up, eps_tol, mask_factor, w_min)
+        h = C.c_void_p()
+        _check(L.gmg_tree_create(C.byref(dom), C.byref(prm), C.byref(h)))
+        self.h = h
+        self._keep = []
+        self._ws = None
+        lmin, lmax, nleaf, nb = C.c_int(), C.c_int(), C.c_longlong(), C.c_longlong()
+        _check(L.gmg_tree_info(self.h, C.byref(lmin), C.byref(lmax), C.byref(nleaf), C.byref(nb)))
+        self.lmin, self.lmax, self.n_leaf_cells, self.n_blocks = lmin.value, lmax.value, nleaf.value, nb.value
+        self.block_n = block_n
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().gmg_tree_destroy(self.h)
+            self.h = None
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- host-side structure ---------------------------------------------
+    def level_blocks(self, level):
+        nb = self.level_nblocks(level)
+        bix = np.zeros((nb, 3), dtype=np.int32)
+        hc = np.zeros(nb, dtype=np.int32)
+        _check(load().gmg_level_blocks(self.h, level, bix.ctypes.data_as(C.POINTER(C.c_int)),
+                                       hc.ctypes.data_as(C.POINTER(C.c_int))))
+        return bix, hc
+
+    def level_info(self, level):
+        nb, n, h = C.c_int(), C.c_int(), C.c_double()
+        _check(load().gmg_level_info(self.h, level, C.byref(nb), C.byref(n), C.byref(h)))
+        return nb.value, n.value, h.value
+
+    def level_nblocks(self, level):
+        return self.level_info(level)[0]
+
+    def level_n(self, level):
+        return self.level_info(level)[1]
+
+    def level_h(self, level):
+        return self.level_info(level)[2]
+
+    def leaf_centers(self):
+        x = np.zeros((self.n_leaf_cells, self.dim))
+        _check(load().gmg_leaf_centers(self.h, x.ctypes.data_as(C.POINTER(C.c_double))))
+        return x
+
+    # --- set-up -------------------------------------------------------------
+    def set_walls(self, types, values=None, fn=None):
+        t = np.zeros(6, dtype=np.int32)
+        t[:len(types)] = types
+        v = np.zeros(6)
+        if values is not None:
+            v[:len(values)] = values
+        cb = _fn(fn)
+        self._keep.append(cb)
+        _check(load().gmg_set_walls(self.h, t.ctypes.data_as(C.POINTER(C.c_int)),
+                                    v.ctypes.data_as(C.POINTER(C.c_double)), cb, None))
+
+    def store_stencils(self, lsf=None, phib=0.0):
+        """lsf: None, (kind, params) with kind in LSF_KINDS, or a callable f(x)."""
+        s = Lsf()
+        if lsf is None:
+            s.kind = 0
+        elif callable(lsf):
+            s.kind = LSF_KINDS["callback"]
+            s.fn = _fn(lsf)
+            self._keep.append(s.fn)
+        else:
+            kind, params = lsf
+            s.kind = LSF_KINDS[kind]
+            for i, v in enumerate(params):
+                s.p[i] = float(v)
+            s.fn = FN()
+        self._keep.append(s)
+        if callable(phib):
+            cb = _fn(phib)
+            self._keep.append(cb)
+            _check(load().gmg_store_stencils(self.h, C.byref(s), cb, None, 0.0))
+        else:
+            _check(load().gmg_store_stencils(self.h, C.byref(s), FN(), None, float(phib)))
+
+    def num_cut_blocks(self, level):
+        return load().gmg_num_cut_blocks(self.h, level)
+
+    def distances(self, level):
+        nb, n = self.level_nblocks(level), self.level_n(level)
+        out = np.zeros(nb * n ** self.dim * 2 * self.dim)
+        _check(load().gmg_get_distances(self.h, level, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out.reshape(nb, n ** self.dim, 2 * self.dim)
+
+    def mask(self, level):
+        nb, n = self.level_nblocks(level), self.level_n(level)
+        out = np.zeros(nb * n ** self.dim, dtype=np.int32)
+        _check(load().gmg_get_mask(self.h, level, out.ctypes.data_as(C.POINTER(C.c_int))))
+        return out.reshape(nb, n ** self.dim)
+
+    def workspace_bytes(self):
+        b = C.c_size_t()
+        _check(load().gmg_workspace_bytes(self.h, C.byref(b)))
+        return b.value
+
+    def bind(self, device_ptr=None):
+        """Bind device memory: a PyTorch allocation (default) or a given pointer."""
+        nbytes = self.workspace_bytes()
+        if device_ptr is None:
+            import torch
+            if not torch.cuda.is_available():
+                raise RuntimeError("CUDA device required: the solver has no CPU path")
+            self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+            ptr = (self._ws.data_ptr() + 255) // 256 * 256
+        else:
+            ptr = int(device_ptr)
+        _check(load().gmg_tree_bind(self.h, C.c_void_p(ptr), C.c_size_t(nbytes)))
+
+    # --- solve ----------------------------------------------------------------
+    def _arr(self, a):
+        """(pointer, where) of a float64 numpy array or CUDA tensor."""
+        if isinstance(a, np.ndarray):
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            self._hold = a
+            return C.c_void_p(a.ctypes.data), HOST
+        import torch
+        assert a.dtype == torch.float64 and a.is_contiguous()
+        return C.c_void_p(a.data_ptr()), (DEVICE if a.is_cuda else HOST)
+
+    def set_rhs(self, g, stream=None):
+        p, where = self._arr(g)
+        _check(load().gmg_set_rhs(self.h, p, where, _stream_ptr(stream)))
+
+    def set_solution(self, phi, stream=None):
+        p, where = self._arr(phi)
+        _check(load().gmg_set_solution(self.h, p, where, _stream_ptr(stream)))
+
+    def solution(self, out=None, stream=None):
+        if out is None:
+            out = np.zeros(self.n_leaf_cells)
+        p, where = self._arr(out)
+        _check(load().gmg_get_solution(self.h, p, where, _stream_ptr(stream)))
+        return out
+
+    def get_level(self, level, which=0, stream=None):
+        nb, n = self.level_nblocks(level), self.level_n(level)
+        out = np.zeros(nb * n ** self.dim)
+        _check(load().gmg_get_level(self.h, level, which, out.ctypes.data_as(C.POINTER(C.c_double)),
+                                    _stream_ptr(stream)))
+        return out
+
+    def vcycle(self, n=1, stream=None):
+        _check(load().gmg_vcycle(self.h, n, _stream_ptr(stream)))
+
+    def residual(self, stream=None):
+        r, m = C.c_double(), C.c_double()
+        _check(load().gmg_residual(self.h, C.byref(r), C.byref(m), _stream_ptr(stream)))
+        return r.value, m.value
+
+    def solve(self, precision=FP64, rel_tol=1e-8, max_cycles=50, stream=None, check=True):
+        st = Stats()
+        rc = load().gmg_solve(self.h, precision, rel_tol, max_cycles, C.byref(st), _stream_ptr(stream))
+        if check:
+            _check(rc)
+        return dict(rc=rc, cycles=st.cycles, rel_l2=st.rel_l2, linf=st.linf, bnorm=st.bnorm)
+
+    def last_launch_count(self):
+        return int(load().gmg_last_launch_count(self.h))
+
+    KERNEL_KINDS = ("smooth", "resid_restrict", "fas_rhs", "coarse_solve", "prolong", "restrict_phi",
+                    "resid_norm", "norm_reduce", "accumulate", "rhs_copy")
+
+    def profile(self, enable=True):
+        _check(load().gmg_profile_enable(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """[(kind, precision, level, launches, total_ms)] since the last read."""
+        cap = 256
+        k, p, lv = (np.zeros(cap, dtype=np.int32) for _ in range(3))
+        n = np.zeros(cap, dtype=np.int64)
+        ms = np.zeros(cap)
+        ip = lambda a: a.ctypes.data_as(C.POINTER(C.c_int))
+        cnt = load().gmg_profile_read(self.h, cap, ip(k), ip(p), ip(lv), n.ctypes.data_as(C.POINTER(C.c_longlong)),
+                                      ms.ctypes.data_as(C.POINTER(C.c_double)))
+        if cnt < 0:
+            _check(cnt)
+        return [(self.KERNEL_KINDS[k[i]], "fp64" if p[i] == 0 else "fp32", int(lv[i]), int(n[i]), float(ms[i]))
+                for i in range(cnt)]

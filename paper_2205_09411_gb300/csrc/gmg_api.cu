@@ -1,0 +1,774 @@
+// C ABI of the GB300 octree multigrid library (include/gmg.h): workspace
+// layout in HBM, the V-cycle schedule (Sec. 2.2) and the FP64 / mixed
+// solve loops, on top of the level kernels of kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "gmg_internal.h"
+#include "kernels.cuh"
+
+namespace gmg {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+#define CUDA_TRY(expr)                                                                       \
+  do {                                                                                       \
+    cudaError_t _e = (expr);                                                                 \
+    if (_e != cudaSuccess) {                                                                 \
+      set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));                         \
+      return GMG_ERR_CUDA;                                                                   \
+    }                                                                                        \
+  } while (0)
+
+__global__ void __launch_bounds__(1024) k_reduce_partials(const double *partials, int nb, double *out) {
+  __shared__ double s[3][1024];
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    a += partials[(size_t)i * 3];
+    b = fmax(b, partials[(size_t)i * 3 + 1]);
+    c += partials[(size_t)i * 3 + 2];
+  }
+  s[0][threadIdx.x] = a;
+  s[1][threadIdx.x] = b;
+  s[2][threadIdx.x] = c;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      s[0][threadIdx.x] += s[0][threadIdx.x + w];
+      s[1][threadIdx.x] = fmax(s[1][threadIdx.x], s[1][threadIdx.x + w]);
+      s[2][threadIdx.x] += s[2][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = s[0][0];
+    out[1] = s[1][0];
+    out[2] = s[2][0];
+  }
+}
+
+// b <- g - boundary terms on leaf cells (g in leaf-cell order)
+__global__ void k_leaf_rhs(const int *__restrict__ leaf_ids, const long long *__restrict__ cbase,
+                           const long long *__restrict__ bt_base, const double *__restrict__ bterm,
+                           const double *__restrict__ g, double *__restrict__ b, long long ncells, int ncell) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ncells; k += (long long)gridDim.x * blockDim.x) {
+    const int id = leaf_ids[k / ncell];
+    const int c = (int)(k % ncell);
+    const long long bb = bt_base[id];
+    b[cbase[id] + c] = g[k] - (bb >= 0 ? bterm[bb + c] : 0.0);
+  }
+}
+
+// leaf gather (dir 0: field -> out) / scatter (dir 1: in -> field)
+__global__ void k_leaf_copy(const int *__restrict__ leaf_ids, const long long *__restrict__ cbase, double *field,
+                            double *io, long long ncells, int ncell, int dir) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ncells; k += (long long)gridDim.x * blockDim.x) {
+    const int id = leaf_ids[k / ncell];
+    const long long f = cbase[id] + (k % ncell);
+    if (dir == 0)
+      io[k] = field[f];
+    else
+      field[f] = io[k];
+  }
+}
+
+// phi64 += e32 on leaf cells (mixed path: solution accumulation in FP64)
+__global__ void k_leaf_accumulate(const int *__restrict__ leaf_ids, const long long *__restrict__ cbase,
+                                  double *__restrict__ phi, const float *__restrict__ e, long long ncells, int ncell) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ncells; k += (long long)gridDim.x * blockDim.x) {
+    const int id = leaf_ids[k / ncell];
+    const long long f = cbase[id] + (k % ncell);
+    phi[f] += (double)e[f];
+  }
+}
+
+__global__ void k_to_float(const double *__restrict__ a, float *__restrict__ b, long long n) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+    b[k] = (float)a[k];
+}
+
+}  // namespace gmg
+
+using namespace gmg;
+
+namespace {
+
+int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 152LL * 16); }
+
+cudaEvent_t prof_event(gmg_tree *t) {
+  if (t->prof_used == t->prof_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    t->prof_pool.push_back(e);
+  }
+  return t->prof_pool[t->prof_used++];
+}
+
+// Enqueue one kernel: counts it and, while profiling, brackets it with events.
+template <typename F>
+void launch(gmg_tree *t, cudaStream_t s, int kind, int prec, int level, F &&f) {
+  if (t->prof_on) {
+    gmg_tree::ProfRec r;
+    r.a = prof_event(t);
+    r.b = prof_event(t);
+    r.kind = kind;
+    r.prec = prec;
+    r.level = level;
+    cudaEventRecord(r.a, s);
+    f();
+    cudaEventRecord(r.b, s);
+    t->prof.push_back(r);
+  } else {
+    f();
+  }
+  t->launches += 1;
+}
+
+template <typename T>
+constexpr int prec_of() {
+  return sizeof(T) == 8 ? 0 : 1;
+}
+
+LvArgs lv(const gmg_tree *T, int l) {
+  const LevelInfo &L = T->lev(l);
+  LvArgs a;
+  a.first = L.first;
+  a.count = L.count;
+  a.n = L.n;
+  a.ncell = L.ncell;
+  a.off = L.off;
+  a.h = L.h;
+  return a;
+}
+
+template <typename T>
+GmgView<T> view(gmg_tree *t);
+
+template <>
+GmgView<double> view<double>(gmg_tree *t) {
+  GmgView<double> v;
+  v.nbr = t->d_nbr;
+  v.parent = t->d_parent;
+  v.pofs = t->d_pofs;
+  v.flags = t->d_flags;
+  v.st_base = t->d_st_base;
+  v.bt_base = t->d_bt_base;
+  v.leaf_ids = t->d_leaf;
+  v.phi = t->d_phi;
+  v.b = t->d_b;
+  v.old = t->d_old;
+  v.st = t->d_st;
+  for (int w = 0; w < 6; w++) v.wsign[w] = t->wall_type[w] == GMG_WALL_DIRICHLET ? -1.f : 1.f;
+  return v;
+}
+
+template <>
+GmgView<float> view<float>(gmg_tree *t) {
+  GmgView<float> v;
+  v.nbr = t->d_nbr;
+  v.parent = t->d_parent;
+  v.pofs = t->d_pofs;
+  v.flags = t->d_flags;
+  v.st_base = t->d_st_base;
+  v.bt_base = t->d_bt_base;
+  v.leaf_ids = t->d_leaf;
+  v.phi = t->f_phi;
+  v.b = t->f_b;
+  v.old = t->f_old;
+  v.st = t->f_st;
+  for (int w = 0; w < 6; w++) v.wsign[w] = t->wall_type[w] == GMG_WALL_DIRICHLET ? -1.f : 1.f;
+  return v;
+}
+
+template <typename T, int D>
+void set_smem_limits() {
+  static bool done = false;
+  if (done) return;
+  const int big = 200 * 1024;
+  cudaFuncSetAttribute(k_smooth<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_resid_restrict<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_fas<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_prolong<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_resnorm<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  done = true;
+}
+
+template <typename T>
+size_t tile_bytes(const gmg_tree *t, int l) {
+  int m = t->lev(l).n + 2;
+  return sizeof(T) * (size_t)(t->D == 3 ? m * m * m : m * m);
+}
+
+// One FAS V-cycle on fields of type T (Sec. 2.2; readings UP and V).
+template <typename T, int D>
+int vcycle_impl(gmg_tree *t, cudaStream_t s) {
+  set_smem_limits<T, D>();
+  GmgView<T> V = view<T>(t);
+  const int P = prec_of<T>();
+  for (int l = t->lmax; l > t->lmin; l--) {
+    LvArgs L = lv(t, l), Lp = lv(t, l - 1);
+    const size_t sm = tile_bytes<T>(t, l);
+    for (int k = 0; k < t->prm.n_down; k++)
+      for (int c = 0; c < 2; c++)
+        launch(t, s, 0, P, l, [&] { k_smooth<T, D><<<L.count, kThreads, sm, s>>>(V, L, Lp, c); });
+    launch(t, s, 1, P, l, [&] { k_resid_restrict<T, D><<<L.count, kThreads, sm, s>>>(V, L, Lp); });
+    LvArgs Lpp = l - 2 >= t->lmin ? lv(t, l - 2) : Lp;
+    const size_t smp = tile_bytes<T>(t, l - 1);
+    launch(t, s, 2, P, l - 1, [&] { k_fas<T, D><<<Lp.count, kThreads, smp, s>>>(V, Lp, Lpp); });
+  }
+  {
+    LvArgs Lc = lv(t, t->lmin);
+    const int M = t->nc;
+    launch(t, s, 3, P, t->lmin, [&] {
+      k_coarse<T><<<(M + kThreads / 32 - 1) / (kThreads / 32), kThreads, 0, s>>>(t->d_cinv, M, V.b + Lc.off,
+                                                                                  V.phi + Lc.off);
+    });
+  }
+  for (int l = t->lmin + 1; l <= t->lmax; l++) {
+    LvArgs L = lv(t, l), Lp = lv(t, l - 1);
+    const int hm = L.n / 2 + 2;
+    const size_t psm = sizeof(T) * (size_t)(D == 3 ? hm * hm * hm : hm * hm);
+    launch(t, s, 4, P, l, [&] { k_prolong<T, D><<<L.count, kThreads, psm, s>>>(V, L, Lp); });
+    const size_t sm = tile_bytes<T>(t, l);
+    for (int k = 0; k < t->prm.n_up; k++)
+      for (int c = 0; c < 2; c++)
+        launch(t, s, 0, P, l, [&] { k_smooth<T, D><<<L.count, kThreads, sm, s>>>(V, L, Lp, c); });
+  }
+  if (t->adaptive) {
+    for (int l = t->lmax; l >= 2 && l > t->lmin; l--) {
+      LvArgs L = lv(t, l), Lp = lv(t, l - 1);
+      launch(t, s, 5, P, l, [&] { k_restrict_phi<T, D><<<L.count, kThreads, 0, s>>>(V, L, Lp); });
+    }
+  }
+  CUDA_TRY(cudaGetLastError());
+  return GMG_OK;
+}
+
+template <typename T>
+int vcycle_any(gmg_tree *t, cudaStream_t s) {
+  return t->D == 3 ? vcycle_impl<T, 3>(t, s) : vcycle_impl<T, 2>(t, s);
+}
+
+// composite residual of the FP64 state: partials for every block, final
+// reduction into d_red; with `rout` also the float residual (mixed path)
+template <int D>
+int residual_impl(gmg_tree *t, cudaStream_t s, float *rout) {
+  set_smem_limits<double, D>();
+  GmgView<double> V = view<double>(t);
+  for (int l = t->lmin; l <= t->lmax; l++) {
+    LvArgs L = lv(t, l), Lp = l > t->lmin ? lv(t, l - 1) : L;
+    const size_t sm = tile_bytes<double>(t, l);
+    launch(t, s, 6, 0, l, [&] { k_resnorm<double, D><<<L.count, kThreads, sm, s>>>(V, L, Lp, t->d_partials, rout); });
+  }
+  launch(t, s, 7, 0, t->lmax,
+         [&] { k_reduce_partials<<<1, 1024, 0, s>>>(t->d_partials, (int)t->blocks.size(), t->d_red); });
+  CUDA_TRY(cudaGetLastError());
+  return GMG_OK;
+}
+
+int residual_any(gmg_tree *t, cudaStream_t s, float *rout) {
+  return t->D == 3 ? residual_impl<3>(t, s, rout) : residual_impl<2>(t, s, rout);
+}
+
+int read_red(gmg_tree *t, cudaStream_t s, double *s2, double *mx, double *b2) {
+  CUDA_TRY(cudaMemcpyAsync(t->h_red, t->d_red, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  *s2 = t->h_red[0];
+  *mx = t->h_red[1];
+  *b2 = t->h_red[2];
+  return GMG_OK;
+}
+
+template <int D>
+int restrict_all_phi64(gmg_tree *t, cudaStream_t s) {
+  GmgView<double> V = view<double>(t);
+  for (int l = t->lmax; l >= 2 && l > t->lmin; l--) {
+    LvArgs L = lv(t, l), Lp = lv(t, l - 1);
+    launch(t, s, 5, 0, l, [&] { k_restrict_phi<double, D><<<L.count, kThreads, 0, s>>>(V, L, Lp); });
+  }
+  CUDA_TRY(cudaGetLastError());
+  return GMG_OK;
+}
+
+int restrict_all_phi64_any(gmg_tree *t, cudaStream_t s) {
+  return t->D == 3 ? restrict_all_phi64<3>(t, s) : restrict_all_phi64<2>(t, s);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t nbr, parent, pofs, flags, leaf, cbase, st_base, bt_base, phi, b, old, fphi, fb, fold, st, fst, bterm, cinv,
+      partials, red, total;
+};
+
+Layout layout(const gmg_tree *t) {
+  Layout L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align256(o + bytes);
+    return at;
+  };
+  const size_t nb = t->blocks.size(), cells = (size_t)t->total_cells;
+  L.nbr = take(nb * kNbr * sizeof(int));
+  L.parent = take(nb * sizeof(int));
+  L.pofs = take(nb * sizeof(int));
+  L.flags = take(nb * sizeof(int));
+  L.leaf = take(t->leaf_ids_h.size() * sizeof(int));
+  L.cbase = take(nb * sizeof(long long));
+  L.st_base = take(nb * sizeof(long long));
+  L.bt_base = take(nb * sizeof(long long));
+  L.phi = take(cells * sizeof(double));
+  L.b = take(cells * sizeof(double));
+  L.old = take(cells * sizeof(double));
+  L.fphi = take(cells * sizeof(float));
+  L.fb = take(cells * sizeof(float));
+  L.fold = take(cells * sizeof(float));
+  L.st = take(t->stencil_h.size() * sizeof(double));
+  L.fst = take(t->stencil_h.size() * sizeof(float));
+  L.bterm = take(t->bterm_h.size() * sizeof(double));
+  L.cinv = take((size_t)t->nc * t->nc * sizeof(double));
+  L.partials = take(nb * 3 * sizeof(double));
+  L.red = take(4 * sizeof(double));
+  L.total = o;
+  return L;
+}
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+extern "C" {
+
+void gmg_default_params(gmg_params *p) {
+  if (!p) return;
+  p->n_down = 2;
+  p->n_up = 2;
+  p->eps_tol = 1e-8;
+  p->mask_factor = 1.5;
+  p->w_min = 0.0;
+}
+
+int gmg_tree_create(const gmg_domain *domain, const gmg_params *params, gmg_tree **out) {
+  if (!domain || !out) return set_error("null argument"), GMG_ERR_INVALID_ARG;
+  *out = nullptr;
+  gmg_tree *t = new gmg_tree();
+  gmg_default_params(&t->prm);
+  if (params) t->prm = *params;
+  if (t->prm.n_down < 0 || t->prm.n_up < 0 || t->prm.n_down + t->prm.n_up < 1 || !(t->prm.eps_tol > 0.0) ||
+      !(t->prm.mask_factor > 0.0) || t->prm.w_min < 0.0) {
+    delete t;
+    return set_error("invalid parameters"), GMG_ERR_INVALID_ARG;
+  }
+  int rc = build_tree(t, domain);
+  if (rc != GMG_OK) {
+    delete t;
+    return rc;
+  }
+  *out = t;
+  return GMG_OK;
+}
+
+void gmg_tree_destroy(gmg_tree *t) {
+  if (!t) return;
+  for (cudaEvent_t e : t->prof_pool) cudaEventDestroy(e);
+  if (t->owns_ws && t->ws) cudaFree(t->ws);
+  if (t->h_red) cudaFreeHost(t->h_red);
+  delete t;
+}
+
+int gmg_tree_info(const gmg_tree *t, int *lmin, int *lmax, long long *n_leaf_cells, long long *n_blocks) {
+  if (!t) return set_error("null tree"), GMG_ERR_INVALID_ARG;
+  if (lmin) *lmin = t->lmin;
+  if (lmax) *lmax = t->lmax;
+  if (n_leaf_cells) *n_leaf_cells = t->n_leaf_cells;
+  if (n_blocks) *n_blocks = (long long)t->blocks.size();
+  return GMG_OK;
+}
+
+int gmg_level_info(const gmg_tree *t, int level, int *n_blocks, int *block_n, double *h) {
+  if (!t || level < t->lmin || level > t->lmax) return set_error("level out of range"), GMG_ERR_INVALID_ARG;
+  const LevelInfo &L = t->lev(level);
+  if (n_blocks) *n_blocks = L.count;
+  if (block_n) *block_n = L.n;
+  if (h) *h = L.h;
+  return GMG_OK;
+}
+
+int gmg_level_blocks(const gmg_tree *t, int level, int *bix, int *has_children) {
+  if (!t || level < t->lmin || level > t->lmax) return set_error("level out of range"), GMG_ERR_INVALID_ARG;
+  const LevelInfo &L = t->lev(level);
+  for (int i = 0; i < L.count; i++) {
+    const HostBlock &B = t->blocks[L.first + i];
+    if (bix)
+      for (int d = 0; d < 3; d++) bix[3 * i + d] = B.ix[d];
+    if (has_children) has_children[i] = B.has_children;
+  }
+  return GMG_OK;
+}
+
+int gmg_leaf_centers(const gmg_tree *t, double *xyz) {
+  if (!t || !xyz) return set_error("null argument"), GMG_ERR_INVALID_ARG;
+  long long k = 0;
+  for (int id : t->leaf_ids_h) {
+    const HostBlock &B = t->blocks[id];
+    const LevelInfo &L = t->lev(B.level);
+    for (int c = 0; c < L.ncell; c++) {
+      int p[3] = {c % L.n, (c / L.n) % L.n, t->D == 3 ? c / (L.n * L.n) : 0};
+      for (int d = 0; d < t->D; d++) xyz[k * t->D + d] = t->lo[d] + ((double)(B.ix[d] * L.n + p[d]) + 0.5) * L.h;
+      k++;
+    }
+  }
+  return GMG_OK;
+}
+
+int gmg_set_walls(gmg_tree *t, const int *types, const double *values, gmg_fn fn, void *user) {
+  if (!t || !types) return set_error("null argument"), GMG_ERR_INVALID_ARG;
+  if (t->bound) return set_error("walls must be set before gmg_tree_bind"), GMG_ERR_STATE;
+  for (int w = 0; w < 2 * t->D; w++) {
+    if (types[w] != GMG_WALL_DIRICHLET && types[w] != GMG_WALL_NEUMANN)
+      return set_error("invalid wall type"), GMG_ERR_INVALID_ARG;
+    t->wall_type[w] = types[w];
+    t->wall_val[w] = values ? values[w] : 0.0;
+  }
+  t->wall_fn = fn;
+  t->wall_user = user;
+  t->stencils_ready = false;
+  return GMG_OK;
+}
+
+int gmg_store_stencils(gmg_tree *t, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, double phib_const) {
+  if (!t) return set_error("null tree"), GMG_ERR_INVALID_ARG;
+  if (t->bound) return set_error("stencils must be stored before gmg_tree_bind"), GMG_ERR_STATE;
+  return host_setup(t, lsf, phib, phib_user, phib_const);
+}
+
+int gmg_num_cut_blocks(const gmg_tree *t, int level) {
+  if (!t || !t->stencils_ready || level < t->lmin || level > t->lmax) return 0;
+  const LevelInfo &L = t->lev(level);
+  int s = 0;
+  for (int i = 0; i < L.count; i++) s += t->st_base_h[L.first + i] >= 0;
+  return s;
+}
+
+int gmg_get_distances(const gmg_tree *t, int level, double *out) {
+  if (!t || !out || !t->stencils_ready || level < t->lmin || level > t->lmax)
+    return set_error("bad arguments or stencils not stored"), GMG_ERR_INVALID_ARG;
+  const LevelInfo &L = t->lev(level);
+  const int D = t->D;
+  size_t k = 0;
+  for (int i = 0; i < L.count; i++) {
+    long long db = t->dist_base_h[L.first + i];
+    for (int c = 0; c < L.ncell * 2 * D; c++) out[k++] = db >= 0 ? t->dist_h[db + c] : 1.0;
+  }
+  return GMG_OK;
+}
+
+int gmg_get_mask(const gmg_tree *t, int level, int *out) {
+  if (!t || !out || !t->stencils_ready || level < t->lmin || level > t->lmax)
+    return set_error("bad arguments or stencils not stored"), GMG_ERR_INVALID_ARG;
+  const LevelInfo &L = t->lev(level);
+  size_t k = 0;
+  for (int i = 0; i < L.count; i++) {
+    long long mb = t->mask_base_h[L.first + i];
+    for (int c = 0; c < L.ncell; c++) out[k++] = t->mask_h[mb + c];
+  }
+  return GMG_OK;
+}
+
+int gmg_workspace_bytes(const gmg_tree *t, size_t *bytes) {
+  if (!t || !bytes) return set_error("null argument"), GMG_ERR_INVALID_ARG;
+  if (!t->stencils_ready) return set_error("call gmg_store_stencils first"), GMG_ERR_STATE;
+  *bytes = layout(t).total;
+  return GMG_OK;
+}
+
+int gmg_tree_bind(gmg_tree *t, void *device_ptr, size_t bytes) {
+  if (!t) return set_error("null tree"), GMG_ERR_INVALID_ARG;
+  if (!t->stencils_ready) return set_error("call gmg_store_stencils first"), GMG_ERR_STATE;
+  if (t->bound) return set_error("tree already bound"), GMG_ERR_STATE;
+  Layout L = layout(t);
+  if (device_ptr) {
+    if (bytes < L.total) return set_error("workspace too small"), GMG_ERR_OOM;
+    if (reinterpret_cast<uintptr_t>(device_ptr) % 256) return set_error("workspace not 256-byte aligned"), GMG_ERR_INVALID_ARG;
+    t->ws = device_ptr;
+    t->owns_ws = false;
+  } else {
+    cudaError_t e = cudaMalloc(&t->ws, L.total);
+    if (e != cudaSuccess) return set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e)), GMG_ERR_OOM;
+    t->owns_ws = true;
+  }
+  t->ws_bytes = L.total;
+  char *w = static_cast<char *>(t->ws);
+  t->d_nbr = reinterpret_cast<int *>(w + L.nbr);
+  t->d_parent = reinterpret_cast<int *>(w + L.parent);
+  t->d_pofs = reinterpret_cast<int *>(w + L.pofs);
+  t->d_flags = reinterpret_cast<int *>(w + L.flags);
+  t->d_leaf = reinterpret_cast<int *>(w + L.leaf);
+  long long *d_cbase = reinterpret_cast<long long *>(w + L.cbase);
+  t->d_st_base = reinterpret_cast<long long *>(w + L.st_base);
+  t->d_bt_base = reinterpret_cast<long long *>(w + L.bt_base);
+  t->d_phi = reinterpret_cast<double *>(w + L.phi);
+  t->d_b = reinterpret_cast<double *>(w + L.b);
+  t->d_old = reinterpret_cast<double *>(w + L.old);
+  t->f_phi = reinterpret_cast<float *>(w + L.fphi);
+  t->f_b = reinterpret_cast<float *>(w + L.fb);
+  t->f_old = reinterpret_cast<float *>(w + L.fold);
+  t->d_st = reinterpret_cast<double *>(w + L.st);
+  t->f_st = reinterpret_cast<float *>(w + L.fst);
+  t->d_bterm = reinterpret_cast<double *>(w + L.bterm);
+  t->d_cinv = reinterpret_cast<double *>(w + L.cinv);
+  t->d_partials = reinterpret_cast<double *>(w + L.partials);
+  t->d_red = reinterpret_cast<double *>(w + L.red);
+  const size_t nb = t->blocks.size();
+  std::vector<long long> cbase(nb);
+  for (size_t i = 0; i < nb; i++) {
+    const LevelInfo &Lv = t->lev(t->blocks[i].level);
+    cbase[i] = Lv.off + (long long)((int)i - Lv.first) * Lv.ncell;
+  }
+  CUDA_TRY(cudaMemcpy(t->d_nbr, t->nbr_h.data(), nb * kNbr * sizeof(int), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(t->d_parent, t->parent_h.data(), nb * sizeof(int), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(t->d_pofs, t->pofs_h.data(), nb * sizeof(int), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(t->d_flags, t->flags_h.data(), nb * sizeof(int), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(t->d_leaf, t->leaf_ids_h.data(), t->leaf_ids_h.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(d_cbase, cbase.data(), nb * sizeof(long long), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(t->d_st_base, t->st_base_h.data(), nb * sizeof(long long), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(t->d_bt_base, t->bt_base_h.data(), nb * sizeof(long long), cudaMemcpyHostToDevice));
+  if (!t->stencil_h.empty()) {
+    CUDA_TRY(cudaMemcpy(t->d_st, t->stencil_h.data(), t->stencil_h.size() * sizeof(double), cudaMemcpyHostToDevice));
+    k_to_float<<<grid_for((long long)t->stencil_h.size()), 256>>>(t->d_st, t->f_st, (long long)t->stencil_h.size());
+  }
+  if (!t->bterm_h.empty())
+    CUDA_TRY(cudaMemcpy(t->d_bterm, t->bterm_h.data(), t->bterm_h.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(t->d_cinv, t->cinv_h.data(), (size_t)t->nc * t->nc * sizeof(double), cudaMemcpyHostToDevice));
+  const size_t cells = (size_t)t->total_cells;
+  CUDA_TRY(cudaMemset(t->d_phi, 0, cells * sizeof(double)));
+  CUDA_TRY(cudaMemset(t->d_b, 0, cells * sizeof(double)));
+  CUDA_TRY(cudaMemset(t->d_old, 0, cells * sizeof(double)));
+  CUDA_TRY(cudaMemset(t->f_phi, 0, cells * sizeof(float)));
+  CUDA_TRY(cudaMemset(t->f_b, 0, cells * sizeof(float)));
+  CUDA_TRY(cudaMemset(t->f_old, 0, cells * sizeof(float)));
+  if (!t->h_red) CUDA_TRY(cudaMallocHost(&t->h_red, 4 * sizeof(double)));
+  CUDA_TRY(cudaDeviceSynchronize());
+  t->bound = true;
+  return GMG_OK;
+}
+
+static long long *cbase_ptr(gmg_tree *t) {
+  Layout L = layout(t);
+  return reinterpret_cast<long long *>(static_cast<char *>(t->ws) + L.cbase);
+}
+
+int gmg_set_rhs(gmg_tree *t, const double *g, int where, void *stream) {
+  if (!t || !g) return set_error("null argument"), GMG_ERR_INVALID_ARG;
+  if (!t->bound) return set_error("tree not bound"), GMG_ERR_STATE;
+  cudaStream_t s = as_stream(stream);
+  const long long n = t->n_leaf_cells;
+  const double *gd = g;
+  if (where == GMG_HOST) {
+    // stage through the FP64 'old' field (scratch until the first V-cycle)
+    CUDA_TRY(cudaMemcpyAsync(t->d_old, g, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    gd = t->d_old;
+  } else if (where != GMG_DEVICE) {
+    return set_error("where must be GMG_HOST or GMG_DEVICE"), GMG_ERR_INVALID_ARG;
+  }
+  const int ncell = t->lev(t->lmax).ncell;
+  k_leaf_rhs<<<grid_for(n), 256, 0, s>>>(t->d_leaf, cbase_ptr(t), t->d_bt_base, t->d_bterm, gd, t->d_b, n, ncell);
+  CUDA_TRY(cudaMemsetAsync(t->d_phi, 0, (size_t)t->total_cells * sizeof(double), s));
+  CUDA_TRY(cudaGetLastError());
+  return GMG_OK;
+}
+
+int gmg_set_solution(gmg_tree *t, const double *phi, int where, void *stream) {
+  if (!t || !phi) return set_error("null argument"), GMG_ERR_INVALID_ARG;
+  if (!t->bound) return set_error("tree not bound"), GMG_ERR_STATE;
+  cudaStream_t s = as_stream(stream);
+  const long long n = t->n_leaf_cells;
+  double *src = const_cast<double *>(phi);
+  if (where == GMG_HOST) {
+    CUDA_TRY(cudaMemcpyAsync(t->d_old, phi, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    src = t->d_old;
+  }
+  const int ncell = t->lev(t->lmax).ncell;
+  k_leaf_copy<<<grid_for(n), 256, 0, s>>>(t->d_leaf, cbase_ptr(t), t->d_phi, src, n, ncell, 1);
+  CUDA_TRY(cudaGetLastError());
+  return restrict_all_phi64_any(t, s);
+}
+
+int gmg_get_solution(gmg_tree *t, double *phi, int where, void *stream) {
+  if (!t || !phi) return set_error("null argument"), GMG_ERR_INVALID_ARG;
+  if (!t->bound) return set_error("tree not bound"), GMG_ERR_STATE;
+  cudaStream_t s = as_stream(stream);
+  const long long n = t->n_leaf_cells;
+  const int ncell = t->lev(t->lmax).ncell;
+  if (where == GMG_DEVICE) {
+    k_leaf_copy<<<grid_for(n), 256, 0, s>>>(t->d_leaf, cbase_ptr(t), t->d_phi, phi, n, ncell, 0);
+    CUDA_TRY(cudaGetLastError());
+    return GMG_OK;
+  }
+  // the FP64 'old' field is dead between V-cycles: stage the gather there
+  k_leaf_copy<<<grid_for(n), 256, 0, s>>>(t->d_leaf, cbase_ptr(t), t->d_phi, t->d_old, n, ncell, 0);
+  CUDA_TRY(cudaMemcpyAsync(phi, t->d_old, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return GMG_OK;
+}
+
+int gmg_get_level(gmg_tree *t, int level, int which, double *out, void *stream) {
+  if (!t || !out || level < t->lmin || level > t->lmax) return set_error("bad arguments"), GMG_ERR_INVALID_ARG;
+  if (!t->bound) return set_error("tree not bound"), GMG_ERR_STATE;
+  cudaStream_t s = as_stream(stream);
+  const LevelInfo &L = t->lev(level);
+  const double *src = (which == 0 ? t->d_phi : t->d_b) + L.off;
+  CUDA_TRY(cudaMemcpyAsync(out, src, (size_t)L.count * L.ncell * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return GMG_OK;
+}
+
+int gmg_vcycle(gmg_tree *t, int n_cycles, void *stream) {
+  if (!t || n_cycles < 0) return set_error("bad arguments"), GMG_ERR_INVALID_ARG;
+  if (!t->bound) return set_error("tree not bound"), GMG_ERR_STATE;
+  t->launches = 0;
+  for (int k = 0; k < n_cycles; k++) {
+    int rc = vcycle_any<double>(t, as_stream(stream));
+    if (rc) return rc;
+  }
+  return GMG_OK;
+}
+
+int gmg_residual(gmg_tree *t, double *rel_l2, double *linf, void *stream) {
+  if (!t) return set_error("null tree"), GMG_ERR_INVALID_ARG;
+  if (!t->bound) return set_error("tree not bound"), GMG_ERR_STATE;
+  cudaStream_t s = as_stream(stream);
+  int rc = residual_any(t, s, nullptr);
+  if (rc) return rc;
+  double s2, mx, b2;
+  rc = read_red(t, s, &s2, &mx, &b2);
+  if (rc) return rc;
+  if (rel_l2) *rel_l2 = b2 > 0 ? std::sqrt(s2 / b2) : std::sqrt(s2);
+  if (linf) *linf = mx;
+  return GMG_OK;
+}
+
+int gmg_solve(gmg_tree *t, int precision, double rel_tol, int max_cycles, gmg_stats *stats, void *stream) {
+  if (!t || max_cycles < 0 || !(rel_tol > 0.0)) return set_error("bad arguments"), GMG_ERR_INVALID_ARG;
+  if (precision != GMG_FP64 && precision != GMG_MIXED) return set_error("bad precision"), GMG_ERR_INVALID_ARG;
+  if (!t->bound) return set_error("tree not bound"), GMG_ERR_STATE;
+  cudaStream_t s = as_stream(stream);
+  t->launches = 0;
+  double s2, mx, b2, rel = 0.0, prev = INFINITY;
+  int cycles = 0, rc = GMG_OK;
+  for (;;) {
+    // composite FP64 residual; in the mixed path it is also the FP32 rhs
+    rc = residual_any(t, s, precision == GMG_MIXED ? t->f_b : nullptr);
+    if (rc) return rc;
+    rc = read_red(t, s, &s2, &mx, &b2);
+    if (rc) return rc;
+    const double bn = b2 > 0 ? std::sqrt(b2) : 1.0;
+    rel = std::sqrt(s2) / bn;
+    if (!std::isfinite(rel) || (cycles > 2 && rel > 1e3 * prev)) {
+      rc = GMG_ERR_NONFINITE;
+      set_error("residual norm is not finite or diverges");
+      break;
+    }
+    prev = std::min(prev, rel);
+    if (rel <= rel_tol) break;
+    if (cycles >= max_cycles) {
+      rc = GMG_ERR_NOT_CONVERGED;
+      set_error("tolerance not reached within max_cycles");
+      break;
+    }
+    if (precision == GMG_FP64) {
+      rc = vcycle_any<double>(t, s);
+    } else {
+      // FP32 correction V-cycle on A e = r with e = 0 (defect correction)
+      CUDA_TRY(cudaMemsetAsync(t->f_phi, 0, (size_t)t->total_cells * sizeof(float), s));
+      rc = vcycle_any<float>(t, s);
+      if (rc) return rc;
+      const long long n = t->n_leaf_cells;
+      launch(t, s, 8, 0, t->lmax, [&] {
+        k_leaf_accumulate<<<grid_for(n), 256, 0, s>>>(t->d_leaf, cbase_ptr(t), t->d_phi, t->f_phi, n,
+                                                      t->lev(t->lmax).ncell);
+      });
+      CUDA_TRY(cudaGetLastError());
+      if (t->adaptive) rc = restrict_all_phi64_any(t, s);
+    }
+    if (rc) return rc;
+    cycles++;
+  }
+  if (stats) {
+    stats->cycles = cycles;
+    stats->rel_l2 = rel;
+    stats->linf = mx;
+    stats->bnorm = std::sqrt(b2);
+  }
+  return rc;
+}
+
+long long gmg_last_launch_count(const gmg_tree *t) { return t ? t->launches : 0; }
+
+int gmg_profile_enable(gmg_tree *t, int enable) {
+  if (!t) return set_error("null tree"), GMG_ERR_INVALID_ARG;
+  t->prof_on = enable != 0;
+  return GMG_OK;
+}
+
+int gmg_profile_read(gmg_tree *t, int cap, int *kind, int *prec, int *level, long long *launches, double *ms) {
+  if (!t || cap < 0) return set_error("bad arguments"), GMG_ERR_INVALID_ARG;
+  struct Agg {
+    int kind, prec, level;
+    long long n;
+    double ms;
+  };
+  std::vector<Agg> agg;
+  for (auto &r : t->prof) {
+    CUDA_TRY(cudaEventSynchronize(r.b));
+    float e = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&e, r.a, r.b));
+    bool found = false;
+    for (auto &a : agg)
+      if (a.kind == r.kind && a.prec == r.prec && a.level == r.level) {
+        a.n += 1;
+        a.ms += e;
+        found = true;
+        break;
+      }
+    if (!found) agg.push_back({r.kind, r.prec, r.level, 1, (double)e});
+  }
+  t->prof.clear();
+  t->prof_used = 0;
+  int k = 0;
+  for (auto &a : agg) {
+    if (k >= cap) break;
+    kind[k] = a.kind;
+    prec[k] = a.prec;
+    level[k] = a.level;
+    launches[k] = a.n;
+    ms[k] = a.ms;
+    k++;
+  }
+  return k;
+}
+
+const char *gmg_error_string(int code) {
+  switch (code) {
+    case GMG_OK: return "ok";
+    case GMG_ERR_INVALID_ARG: return "invalid argument";
+    case GMG_ERR_OOM: return "out of memory";
+    case GMG_ERR_CUDA: return "CUDA error";
+    case GMG_ERR_NOT_CONVERGED: return "not converged";
+    case GMG_ERR_NONFINITE: return "non-finite or diverging residual";
+    case GMG_ERR_STATE: return "call out of order";
+    case GMG_ERR_TIMEOUT: return "device wait timed out";
+    default: return "unknown error";
+  }
+}
+
+const char *gmg_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

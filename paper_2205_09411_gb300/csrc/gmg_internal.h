@@ -1,0 +1,127 @@
+// Internal declarations of the GB300 octree multigrid library (not part of
+// the C ABI).  Host structures describe the block tree; the device view
+// (GmgView) is what the kernels receive by value.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "gmg.h"
+
+namespace gmg {
+
+constexpr int kMaxLevels = 40;
+constexpr int kNbr = 27;  // 3x3x3 neighbour offsets (2D uses the dz = 0 plane)
+
+// block flags
+constexpr int kHasChildren = 1;
+inline __host__ __device__ int wall_bit(int axis, int side) { return 2 << (2 * axis + side); }
+
+struct HostBlock {
+  int level;
+  int ix[3];
+  int parent;
+  int pofs[3];  // offset of this block's footprint in the parent, in parent cells
+  int child[8];
+  int has_children;
+};
+
+// One level of the hierarchy: blocks [first, first + count) in global id order.
+struct LevelInfo {
+  int l = 0, n = 0, ncell = 0, first = 0, count = 0;
+  double h = 0.0;
+  int bext[3] = {1, 1, 1};
+  long long off = 0;  // first cell of the level in the field arrays
+  std::vector<int> map;  // block coordinates -> global id (or -1)
+};
+
+// Per-level arguments passed to kernels.
+struct LvArgs {
+  int first, count, n, ncell;
+  long long off;
+  double h;
+};
+
+// Everything a kernel needs to address the tree in device memory.
+template <typename T>
+struct GmgView {
+  const int *nbr;        // [nb][27] same-level neighbour id, -1 none, -2 outside
+  const int *parent;     // [nb]
+  const int *pofs;       // [nb] packed px | py << 10 | pz << 20
+  const int *flags;      // [nb] kHasChildren | wall bits
+  const long long *st_base;  // [nb] element offset of the block's stencil, -1 regular
+  const long long *bt_base;  // [nb] element offset of the block's boundary term, -1 none
+  const int *leaf_ids;   // [n_leaf_blocks]
+  T *phi, *b, *old;      // level fields (all levels, block-contiguous)
+  const T *st;           // stencil pool: per cut block (2D+1) x ncell, [diag, -x, +x, -y, +y, -z, +z]
+  float wsign[6];        // homogeneous wall ghost sign: -1 Dirichlet, +1 Neumann
+};
+
+struct gmg_tree_impl;
+
+}  // namespace gmg
+
+struct gmg_tree {
+  // geometry and parameters
+  int D = 3, N = 8, cb[3] = {1, 1, 1}, max_level = 1, lmin = 1, lmax = 1, max_coarse = 512;
+  double lo[3] = {0, 0, 0}, h1 = 1.0;
+  gmg_params prm{};
+  std::vector<gmg::HostBlock> blocks;  // global id order (levels ascending, Morton inside)
+  std::vector<gmg::LevelInfo> levels;  // index l - lmin
+  std::vector<int> nbr_h, parent_h, pofs_h, flags_h, leaf_ids_h;
+  long long total_cells = 0, n_leaf_cells = 0;
+  bool adaptive = false;
+
+  // walls
+  int wall_type[6] = {0, 0, 0, 0, 0, 0};
+  double wall_val[6] = {0, 0, 0, 0, 0, 0};
+  gmg_fn wall_fn = nullptr;
+  void *wall_user = nullptr;
+
+  // set-up results (host)
+  bool stencils_ready = false;
+  std::vector<long long> st_base_h, bt_base_h;
+  std::vector<double> stencil_h;  // concatenated per cut block: (2D+1) x ncell
+  std::vector<double> bterm_h;    // concatenated per block with boundary terms: ncell
+  std::vector<double> dist_h;     // per cut block: ncell x 2D distances (inspection)
+  std::vector<long long> dist_base_h;
+  std::vector<uint8_t> mask_h;    // per block ncell (inspection)
+  std::vector<long long> mask_base_h;
+  int nc = 0;                     // coarsest-level unknowns
+  std::vector<double> cinv_h;     // inverse of the coarsest-level operator (nc x nc)
+
+  // device workspace
+  bool bound = false, owns_ws = false;
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+  int *d_nbr = nullptr, *d_parent = nullptr, *d_pofs = nullptr, *d_flags = nullptr, *d_leaf = nullptr;
+  long long *d_st_base = nullptr, *d_bt_base = nullptr;
+  double *d_phi = nullptr, *d_b = nullptr, *d_old = nullptr;
+  float *f_phi = nullptr, *f_b = nullptr, *f_old = nullptr;
+  double *d_st = nullptr, *d_bterm = nullptr, *d_cinv = nullptr, *d_partials = nullptr, *d_red = nullptr;
+  float *f_st = nullptr;
+  double *h_red = nullptr;  // pinned host mirror of d_red
+  long long launches = 0;
+
+  // kernel timing (gmg_profile_enable)
+  struct ProfRec {
+    cudaEvent_t a, b;
+    int kind, prec, level;
+  };
+  bool prof_on = false;
+  std::vector<ProfRec> prof;
+  std::vector<cudaEvent_t> prof_pool;
+  size_t prof_used = 0;
+
+  gmg::LevelInfo &lev(int l) { return levels[l - lmin]; }
+  const gmg::LevelInfo &lev(int l) const { return levels[l - lmin]; }
+};
+
+namespace gmg {
+void set_error(const std::string &msg);
+int build_tree(gmg_tree *T, const gmg_domain *dom);
+int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, double phib_const);
+}  // namespace gmg

@@ -1,0 +1,406 @@
+// Level kernels of the FAS V-cycle (Sec. 2.2, 3.3, 3.4).  One CTA handles
+// one block: it stages the block and its ghost layer in shared memory
+// (same-level neighbours, wall reflections, refinement-boundary ghosts),
+// then updates the block's cells.  T is the storage/arithmetic type of the
+// V-cycle (double for the FP64 path, float inside the mixed path).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "gmg_internal.h"
+
+namespace gmg {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ int nbr_slot(int ox, int oy, int oz) { return (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1); }
+
+// Local coordinate p (each component in [-1, n]) of block `bid` on level L:
+// axes leaving the domain are reflected with the homogeneous wall sign,
+// other axes leaving the block go to the same-level neighbour.  Returns
+// false when that neighbour does not exist on this level.
+template <int D>
+__device__ __forceinline__ bool resolve(const int *__restrict__ nbr, const int *__restrict__ flags, const float *wsign,
+                                        const LvArgs &L, int bid, const int *pin, long long *idx, float *sign) {
+  const int n = L.n;
+  int p[3] = {pin[0], pin[1], pin[2]}, o[3] = {0, 0, 0};
+  float sg = 1.f;
+  const int fl = flags[bid];
+#pragma unroll
+  for (int d = 0; d < D; d++) {
+    if (p[d] < 0) {
+      if (fl & wall_bit(d, 0)) {
+        p[d] = -1 - p[d];
+        sg *= wsign[2 * d];
+      } else {
+        o[d] = -1;
+        p[d] += n;
+      }
+    } else if (p[d] >= n) {
+      if (fl & wall_bit(d, 1)) {
+        p[d] = 2 * n - 1 - p[d];
+        sg *= wsign[2 * d + 1];
+      } else {
+        o[d] = 1;
+        p[d] -= n;
+      }
+    }
+  }
+  int id = bid;
+  if (o[0] | o[1] | o[2]) {
+    id = nbr[(size_t)bid * kNbr + nbr_slot(o[0], o[1], o[2])];
+    if (id < 0) return false;
+  }
+  *idx = L.off + (long long)(id - L.first) * L.ncell + p[0] + n * (p[1] + (D == 3 ? n * p[2] : 0));
+  *sign = sg;
+  return true;
+}
+
+// Refinement-boundary ghost (reading G): g = f/3 + 2/3 c_hat, with f the
+// adjacent fine cell and c_hat the coarse cell containing the ghost centre
+// shifted by central tangential slopes (+-1/4 coarse cell).
+template <typename T, int D>
+__device__ T refine_ghost(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, const int *p, int a) {
+  const int n = L.n;
+  int q[3] = {p[0], p[1], p[2]};
+  q[a] = p[a] < 0 ? 0 : n - 1;
+  const T f = V.phi[L.off + (long long)(bid - L.first) * L.ncell + q[0] + n * (q[1] + (D == 3 ? n * q[2] : 0))];
+  const int P = V.parent[bid], po = V.pofs[bid];
+  const int pofs[3] = {po & 1023, (po >> 10) & 1023, (po >> 20) & 1023};
+  int cq[3] = {0, 0, 0};
+#pragma unroll
+  for (int d = 0; d < D; d++) cq[d] = pofs[d] + (p[d] >> 1);
+  long long ix;
+  float sg;
+  if (!resolve<D>(V.nbr, V.flags, V.wsign, Lp, P, cq, &ix, &sg)) return T(NAN);
+  const T c = V.phi[ix];
+  T chat = c;
+#pragma unroll
+  for (int t = 0; t < D; t++) {
+    if (t == a) continue;
+    const T o = (p[t] & 1) ? T(0.25) : T(-0.25);
+    int qp[3] = {cq[0], cq[1], cq[2]}, qm[3] = {cq[0], cq[1], cq[2]};
+    qp[t] += 1;
+    qm[t] -= 1;
+    long long ip, im;
+    float sp, sm;
+    if (!resolve<D>(V.nbr, V.flags, V.wsign, Lp, P, qp, &ip, &sp)) return T(NAN);
+    if (!resolve<D>(V.nbr, V.flags, V.wsign, Lp, P, qm, &im, &sm)) return T(NAN);
+    const T cp = T(sp) * V.phi[ip], cm = T(sm) * V.phi[im];
+    chat = chat + o * (T(0.5) * (cp - cm));
+  }
+  return f / T(3) + T(2) * chat / T(3);
+}
+
+// Stage phi of block `bid` with its face ghosts into tile[(n+2)^D].
+template <typename T, int D>
+__device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, T *tile) {
+  const int n = L.n, m = n + 2;
+  const int tsize = D == 3 ? m * m * m : m * m;
+  const long long base = L.off + (long long)(bid - L.first) * L.ncell;
+  for (int t = threadIdx.x; t < tsize; t += blockDim.x) {
+    const int p[3] = {t % m - 1, (t / m) % m - 1, D == 3 ? t / (m * m) - 1 : 0};
+    int nout = 0, a = 0;
+#pragma unroll
+    for (int d = 0; d < D; d++)
+      if (p[d] < 0 || p[d] >= n) {
+        nout++;
+        a = d;
+      }
+    T v;
+    if (nout == 0) {
+      v = V.phi[base + p[0] + n * (p[1] + (D == 3 ? n * p[2] : 0))];
+    } else if (nout > 1) {
+      v = T(0);  // edges and corners: not used by the 5/7-point operator
+    } else {
+      long long ix;
+      float sg;
+      if (resolve<D>(V.nbr, V.flags, V.wsign, L, bid, p, &ix, &sg))
+        v = T(sg) * V.phi[ix];
+      else
+        v = refine_ghost<T, D>(V, L, Lp, bid, p, a);
+    }
+    tile[t] = v;
+  }
+}
+
+// Off-diagonal sum and diagonal of the operator at cell c (tile index t).
+template <typename T, int D>
+__device__ __forceinline__ T offdiag(const GmgView<T> &V, const T *tile, int t, int m, long long sb, int ncell, int c,
+                                     T inv_h2, T *diag) {
+  const T xm = tile[t - 1], xp = tile[t + 1], ym = tile[t - m], yp = tile[t + m];
+  if (sb < 0) {
+    T s = (xm + xp) + (ym + yp);
+    if (D == 3) s += tile[t - m * m] + tile[t + m * m];
+    *diag = T(-2 * D) * inv_h2;
+    return s * inv_h2;
+  }
+  const T *st = V.st + sb;
+  T s = st[1 * ncell + c] * xm + st[2 * ncell + c] * xp + st[3 * ncell + c] * ym + st[4 * ncell + c] * yp;
+  if (D == 3) s += st[5 * ncell + c] * tile[t - m * m] + st[6 * ncell + c] * tile[t + m * m];
+  *diag = st[c];
+  return s;
+}
+
+template <int D>
+__device__ __forceinline__ void cell_xyz(int c, int n, int *x, int *y, int *z) {
+  *x = c % n;
+  *y = (c / n) % n;
+  *z = D == 3 ? c / (n * n) : 0;
+}
+
+// One red (color 0) or black (color 1) half-sweep of Gauss-Seidel on every
+// block of a level (Sec. 2.2, readings S and SW).
+template <typename T, int D>
+__global__ void __launch_bounds__(kThreads) k_smooth(GmgView<T> V, LvArgs L, LvArgs Lp, int color) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *tile = reinterpret_cast<T *>(smem_raw);
+  const int bid = L.first + blockIdx.x;
+  load_tile<T, D>(V, L, Lp, bid, tile);
+  __syncthreads();
+  const int n = L.n, m = n + 2, hn = n / 2;
+  const long long base = L.off + (long long)(bid - L.first) * L.ncell;
+  const long long sb = V.st_base[bid];
+  const T h2 = T(L.h * L.h), inv_h2 = T(1.0 / (L.h * L.h)), inv2d = T(1.0 / (2 * D));
+  for (int j = threadIdx.x; j < L.ncell / 2; j += blockDim.x) {
+    const int rest = j / hn;
+    const int y = rest % n, z = D == 3 ? rest / n : 0;
+    const int x = 2 * (j % hn) + ((y + z + color) & 1);
+    const int c = x + n * (y + n * z);
+    const int t = (x + 1) + m * ((y + 1) + (D == 3 ? m * (z + 1) : 0));
+    T nv;
+    if (sb < 0) {
+      T s = (tile[t - 1] + tile[t + 1]) + (tile[t - m] + tile[t + m]);
+      if (D == 3) s += tile[t - m * m] + tile[t + m * m];
+      nv = (s - h2 * V.b[base + c]) * inv2d;
+    } else {
+      T diag;
+      const T s = offdiag<T, D>(V, tile, t, m, sb, L.ncell, c, inv_h2, &diag);
+      nv = (V.b[base + c] - s) / diag;
+    }
+    V.phi[base + c] = nv;
+  }
+}
+
+// Residual r = b - A phi (Eq. (residual)) of every cell, restricted to the
+// parent as the mean of the 2^D children, together with phi (Sec. 2.2):
+// parent phi <- mean phi, parent b <- mean r (the FAS kernel adds A phi).
+template <typename T, int D>
+__global__ void __launch_bounds__(kThreads) k_resid_restrict(GmgView<T> V, LvArgs L, LvArgs Lp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *tile = reinterpret_cast<T *>(smem_raw);
+  const int bid = L.first + blockIdx.x;
+  load_tile<T, D>(V, L, Lp, bid, tile);
+  __syncthreads();
+  const int n = L.n, m = n + 2, hn = n / 2;
+  const long long base = L.off + (long long)(bid - L.first) * L.ncell;
+  const long long sb = V.st_base[bid];
+  const T inv_h2 = T(1.0 / (L.h * L.h));
+  const int P = V.parent[bid], po = V.pofs[bid];
+  const int pofs[3] = {po & 1023, (po >> 10) & 1023, (po >> 20) & 1023};
+  const long long pbase = Lp.off + (long long)(P - Lp.first) * Lp.ncell;
+  const int pn = Lp.n;
+  const int ncq = D == 3 ? hn * hn * hn : hn * hn;
+  const T w = T(1.0 / (1 << D));
+  for (int j = threadIdx.x; j < ncq; j += blockDim.x) {
+    const int qx = j % hn, qy = (j / hn) % hn, qz = D == 3 ? j / (hn * hn) : 0;
+    T sp = T(0), sr = T(0);
+#pragma unroll
+    for (int dz = 0; dz < (D == 3 ? 2 : 1); dz++)
+#pragma unroll
+      for (int dy = 0; dy < 2; dy++)
+#pragma unroll
+        for (int dx = 0; dx < 2; dx++) {
+          const int x = 2 * qx + dx, y = 2 * qy + dy, z = 2 * qz + dz;
+          const int c = x + n * (y + n * z);
+          const int t = (x + 1) + m * ((y + 1) + (D == 3 ? m * (z + 1) : 0));
+          T diag;
+          const T s = offdiag<T, D>(V, tile, t, m, sb, L.ncell, c, inv_h2, &diag);
+          const T ph = tile[t];
+          sp = sp + ph;
+          sr = sr + (V.b[base + c] - (diag * ph + s));
+        }
+    const long long pc = pbase + (pofs[0] + qx) + pn * ((pofs[1] + qy) + (D == 3 ? pn * (pofs[2] + qz) : 0));
+    V.phi[pc] = sp * w;
+    V.b[pc] = sr * w;
+  }
+}
+
+// FAS coarse right-hand side on covered cells: b <- A phi + (restricted r);
+// old <- phi on every cell of the level (start of the coarse visit).
+template <typename T, int D>
+__global__ void __launch_bounds__(kThreads) k_fas(GmgView<T> V, LvArgs L, LvArgs Lp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *tile = reinterpret_cast<T *>(smem_raw);
+  const int bid = L.first + blockIdx.x;
+  const long long base = L.off + (long long)(bid - L.first) * L.ncell;
+  if (!(V.flags[bid] & kHasChildren)) {
+    for (int c = threadIdx.x; c < L.ncell; c += blockDim.x) V.old[base + c] = V.phi[base + c];
+    return;
+  }
+  load_tile<T, D>(V, L, Lp, bid, tile);
+  __syncthreads();
+  const int n = L.n, m = n + 2;
+  const long long sb = V.st_base[bid];
+  const T inv_h2 = T(1.0 / (L.h * L.h));
+  for (int c = threadIdx.x; c < L.ncell; c += blockDim.x) {
+    int x, y, z;
+    cell_xyz<D>(c, n, &x, &y, &z);
+    const int t = (x + 1) + m * ((y + 1) + (D == 3 ? m * (z + 1) : 0));
+    T diag;
+    const T s = offdiag<T, D>(V, tile, t, m, sb, L.ncell, c, inv_h2, &diag);
+    const T ph = tile[t];
+    V.b[base + c] = (diag * ph + s) + V.b[base + c];
+    V.old[base + c] = ph;
+  }
+}
+
+// Coarsest level: phi = A^-1 b with the FP64 inverse, one warp per row.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_coarse(const double *__restrict__ Ainv, int M, const T *__restrict__ b,
+                                                     T *__restrict__ phi) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * (kThreads / 32) + warp;
+  if (row >= M) return;
+  const double *a = Ainv + (size_t)row * M;
+  double s = 0.0;
+  for (int j = lane; j < M; j += 32) s += a[j] * (double)b[j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) phi[row] = T(s);
+}
+
+// (Bi/tri)linear prolongation of the coarse correction phi - old
+// (Sec. 2.2, 3.4): weights 3/4 and 1/4 per dimension from the parent cell
+// and its neighbours toward the fine cell (reading P).
+template <typename T, int D>
+__global__ void __launch_bounds__(kThreads) k_prolong(GmgView<T> V, LvArgs L, LvArgs Lp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *tile = reinterpret_cast<T *>(smem_raw);
+  const int bid = L.first + blockIdx.x;
+  const int n = L.n, hn = n / 2, m = hn + 2;
+  const int P = V.parent[bid], po = V.pofs[bid];
+  const int pofs[3] = {po & 1023, (po >> 10) & 1023, (po >> 20) & 1023};
+  const int tsize = D == 3 ? m * m * m : m * m;
+  for (int t = threadIdx.x; t < tsize; t += blockDim.x) {
+    int q[3] = {pofs[0] - 1 + t % m, pofs[1] - 1 + (t / m) % m, D == 3 ? pofs[2] - 1 + t / (m * m) : 0};
+    long long ix;
+    float sg;
+    T v = T(NAN);
+    if (resolve<D>(V.nbr, V.flags, V.wsign, Lp, P, q, &ix, &sg)) v = T(sg) * (V.phi[ix] - V.old[ix]);
+    tile[t] = v;
+  }
+  __syncthreads();
+  const long long base = L.off + (long long)(bid - L.first) * L.ncell;
+  for (int c = threadIdx.x; c < L.ncell; c += blockDim.x) {
+    int x, y, z;
+    cell_xyz<D>(c, n, &x, &y, &z);
+    const int u[3] = {(x >> 1) + 1, (y >> 1) + 1, (z >> 1) + 1};
+    const int o[3] = {(x & 1) ? 1 : -1, (y & 1) ? 1 : -1, (z & 1) ? 1 : -1};
+    T v = T(0);
+#pragma unroll
+    for (int sz = 0; sz < (D == 3 ? 2 : 1); sz++)
+#pragma unroll
+      for (int sy = 0; sy < 2; sy++)
+#pragma unroll
+        for (int sx = 0; sx < 2; sx++) {
+          T wgt = (sx ? T(0.25) : T(0.75)) * (sy ? T(0.25) : T(0.75));
+          if (D == 3) wgt *= sz ? T(0.25) : T(0.75);
+          const int tx = u[0] + sx * o[0], ty = u[1] + sy * o[1], tz = D == 3 ? u[2] + sz * o[2] : 0;
+          v = v + wgt * tile[tx + m * (ty + (D == 3 ? m * tz : 0))];
+        }
+    V.phi[base + c] += v;
+  }
+}
+
+// phi of covered cells <- mean of the children (composite consistency).
+template <typename T, int D>
+__global__ void __launch_bounds__(kThreads) k_restrict_phi(GmgView<T> V, LvArgs L, LvArgs Lp) {
+  const int bid = L.first + blockIdx.x;
+  const int n = L.n, hn = n / 2;
+  const long long base = L.off + (long long)(bid - L.first) * L.ncell;
+  const int P = V.parent[bid], po = V.pofs[bid];
+  const int pofs[3] = {po & 1023, (po >> 10) & 1023, (po >> 20) & 1023};
+  const long long pbase = Lp.off + (long long)(P - Lp.first) * Lp.ncell;
+  const int pn = Lp.n;
+  const int ncq = D == 3 ? hn * hn * hn : hn * hn;
+  const T w = T(1.0 / (1 << D));
+  for (int j = threadIdx.x; j < ncq; j += blockDim.x) {
+    const int qx = j % hn, qy = (j / hn) % hn, qz = D == 3 ? j / (hn * hn) : 0;
+    T sp = T(0);
+    for (int dz = 0; dz < (D == 3 ? 2 : 1); dz++)
+      for (int dy = 0; dy < 2; dy++)
+        for (int dx = 0; dx < 2; dx++) sp = sp + V.phi[base + (2 * qx + dx) + n * ((2 * qy + dy) + n * (2 * qz + dz))];
+    V.phi[pbase + (pofs[0] + qx) + pn * ((pofs[1] + qy) + (D == 3 ? pn * (pofs[2] + qz) : 0))] = sp * w;
+  }
+}
+
+// Block reduction of (sum r^2, max |r|, sum b^2) into partials[bid*3 ..].
+__device__ __forceinline__ void block_reduce3(double s2, double mx, double b2, double *out) {
+  __shared__ double red[3][kThreads / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    b2 += __shfl_xor_sync(0xffffffffu, b2, o);
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if (lane == 0) {
+    red[0][warp] = s2;
+    red[1][warp] = mx;
+    red[2][warp] = b2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int i = 0; i < kThreads / 32; i++) {
+      a += red[0][i];
+      b = fmax(b, red[1][i]);
+      c += red[2][i];
+    }
+    out[0] = a;
+    out[1] = b;
+    out[2] = c;
+  }
+}
+
+// Residual norms over the leaf blocks of a level (reading R); with `rout`
+// the residual itself is written as float (right-hand side of the FP32
+// correction V-cycle in the mixed path).
+template <typename T, int D>
+__global__ void __launch_bounds__(kThreads) k_resnorm(GmgView<T> V, LvArgs L, LvArgs Lp, double *partials,
+                                                      float *rout) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *tile = reinterpret_cast<T *>(smem_raw);
+  const int bid = L.first + blockIdx.x;
+  if (V.flags[bid] & kHasChildren) {
+    if (threadIdx.x < 3) partials[(size_t)bid * 3 + threadIdx.x] = 0.0;
+    return;
+  }
+  load_tile<T, D>(V, L, Lp, bid, tile);
+  __syncthreads();
+  const int n = L.n, m = n + 2;
+  const long long base = L.off + (long long)(bid - L.first) * L.ncell;
+  const long long sb = V.st_base[bid];
+  const T inv_h2 = T(1.0 / (L.h * L.h));
+  double s2 = 0.0, mx = 0.0, b2 = 0.0;
+  for (int c = threadIdx.x; c < L.ncell; c += blockDim.x) {
+    int x, y, z;
+    cell_xyz<D>(c, n, &x, &y, &z);
+    const int t = (x + 1) + m * ((y + 1) + (D == 3 ? m * (z + 1) : 0));
+    T diag;
+    const T s = offdiag<T, D>(V, tile, t, m, sb, L.ncell, c, inv_h2, &diag);
+    const T bb = V.b[base + c];
+    const double r = (double)(bb - (diag * tile[t] + s));
+    if (rout) rout[base + c] = (float)r;
+    s2 += r * r;
+    mx = fmax(mx, fabs(r));
+    b2 += (double)bb * (double)bb;
+  }
+  block_reduce3(s2, mx, b2, partials + (size_t)bid * 3);
+}
+
+// Deterministic final reduction of the per-block partials (fixed order).
+__global__ void __launch_bounds__(1024) k_reduce_partials(const double *partials, int nb, double *out);
+
+}  // namespace gmg

@@ -1,0 +1,132 @@
+"""GPU parity: the CUDA path against the FP64 oracle on the same seeded inputs.
+
+FP64 path: after each of 12 V-cycles the leaf solution matches the oracle's
+iterate to 1e-12 relative (max-norm, relative to max |phi|).  The two sides
+share no code; their only differences are the rounding order of the same
+formulas, which the multigrid contraction keeps near 1e-15.
+
+Mixed path (FP32 V-cycles inside FP64 defect correction): reaches the same
+1e-8 relative residual, checked independently by the oracle's own residual
+of the returned solution, and its error against the oracle's converged FP64
+solution is bounded per case.
+"""
+import numpy as np
+import pytest
+
+import gmg_inputs as I
+from _helpers import gpu_problem, oracle_problem, parity_cases
+
+pytestmark = pytest.mark.gpu
+
+TOL_ITERATE = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2205_09411_gb300 as G
+    G.build()
+
+
+CASES = sorted(parity_cases().keys())
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_fp64_vcycle_iterates_match_oracle(name):
+    p = parity_cases()[name]
+    o = oracle_problem(p)
+    t = gpu_problem(p)
+    for k in range(12):
+        o.vcycle(1)
+        t.vcycle(1)
+        ref = o.solution()
+        got = t.solution()
+        scale = max(np.abs(ref).max(), 1e-300)
+        err = np.abs(got - ref).max() / scale
+        assert err <= TOL_ITERATE, "cycle %d: relative max difference %.3e" % (k + 1, err)
+
+
+@pytest.mark.parametrize("name", ["c1", "c2_64", "adaptive3d"])
+def test_fp64_residual_norm_matches_oracle(name):
+    p = parity_cases()[name]
+    o = oracle_problem(p)
+    t = gpu_problem(p)
+    o.vcycle(3)
+    t.vcycle(3)
+    l2, linf, bn = o.residual()
+    rel, mx = t.residual()
+    assert abs(rel - l2 / bn) <= 1e-6 * (l2 / bn) + 1e-13
+    assert abs(mx - linf) <= 1e-6 * linf + 1e-13 * bn
+
+
+@pytest.mark.parametrize("name", ["c1", "c2_64", "ragged3d", "adaptive2d", "adaptive3d"])
+def test_fp64_solve_matches_oracle(name):
+    p = parity_cases()[name]
+    o = oracle_problem(p)
+    t = gpu_problem(p)
+    ko, _ = o.solve(1e-10, 40)
+    st = t.solve(0, 1e-10, 40)
+    assert st["cycles"] == ko
+    ref = o.solution()
+    assert np.abs(t.solution() - ref).max() <= TOL_ITERATE * np.abs(ref).max()
+
+
+# error bound of the mixed path against the converged FP64 solution
+MIXED_ERR = {"c1": 1e-8, "c2_64": 1e-7, "ragged3d": 1e-7, "adaptive2d": 1e-7, "adaptive3d": 1e-7,
+             "c2_32": 1e-7, "no_boundary": 1e-7, "object_outside": 1e-7, "single_level": 1e-8}
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_mixed_solve_reaches_tolerance(name):
+    p = parity_cases()[name]
+    o = oracle_problem(p)
+    t = gpu_problem(p)
+    st = t.solve(1, 1e-8, 60)
+    assert st["rel_l2"] <= 1e-8
+    phi = t.solution()
+    # independent check of the residual with the oracle's operator
+    o.set_solution(phi)
+    l2, _, bn = o.residual()
+    assert l2 / bn <= 1.05e-8
+    ko, _ = o.solve(1e-13, 60)
+    assert ko > 0
+    ref = o.solution()
+    err = np.abs(phi - ref).max() / np.abs(ref).max()
+    assert err <= MIXED_ERR[name], err
+
+
+def test_full_size_sphere_configuration_matches_oracle():
+    """128^3 sphere configuration at full size: 12 FP64 V-cycles against the
+    oracle, compared on every leaf cell."""
+    p = I.problem("c2")
+    o = oracle_problem(p)
+    t = gpu_problem(p)
+    o.vcycle(6)
+    t.vcycle(6)
+    ref = o.solution()
+    assert np.abs(t.solution() - ref).max() <= TOL_ITERATE * np.abs(ref).max()
+
+
+def test_zero_rhs_gives_zero_solution():
+    p = dict(parity_cases()["no_boundary"])
+    p["wall_values"] = (0,) * 6
+    p["rhs"] = lambda xc: np.zeros(len(xc))
+    t = gpu_problem(p)
+    st = t.solve(0, 1e-8, 5)
+    assert st["cycles"] == 0
+    assert np.all(t.solution() == 0)
+
+
+def test_device_arrays_round_trip():
+    import torch
+    p = parity_cases()["c1"]
+    t = gpu_problem(p)
+    g = torch.tensor(p["rhs"](t.leaf_centers()), dtype=torch.float64, device="cuda")
+    t.set_rhs(g)
+    t.vcycle(2)
+    out = torch.zeros(t.n_leaf_cells, dtype=torch.float64, device="cuda")
+    t.solution(out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), t.solution())

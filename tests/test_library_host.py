@@ -1,0 +1,93 @@
+"""CPU tests of the CUDA library's host logic: the shared library loads and
+exports every function of include/gmg.h, and its block tree, leaf order and
+boundary set-up (mask, line-search distances, cut-block counts) equal the
+oracle's bit for bit.  No device call is made."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import gmg_inputs as I
+from _helpers import gpu_problem, oracle_problem, parity_cases
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def G():
+    import paper_2205_09411_gb300 as G
+    G.build()
+    return G
+
+
+def header_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[a-z_ ]+\*?\s*\**(gmg_[a-z0-9_]+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_function(G):
+    lib = ctypes.CDLL(G.LIB_PATH)
+    names = header_functions()
+    assert len(names) >= 20
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_library_fails_loudly_without_binary(G, tmp_path, monkeypatch):
+    import paper_2205_09411_gb300 as mod
+    monkeypatch.setattr(mod, "_lib", None)
+    monkeypatch.setattr(mod, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError):
+        mod.load()
+
+
+@pytest.mark.parametrize("name", sorted(parity_cases().keys()))
+def test_tree_and_setup_equal_oracle(G, name):
+    p = parity_cases()[name]
+    o = oracle_problem(p, rhs=False)
+    t = gpu_problem(p, bind=False)
+    assert (t.lmin, t.lmax) == o.levels()
+    assert t.n_leaf_cells == o.num_leaf_cells()
+    for lev in range(t.lmin, t.lmax + 1):
+        bg, hg = t.level_blocks(lev)
+        bo, ho = o.level_blocks(lev)
+        assert np.array_equal(bg, bo) and np.array_equal(hg, ho)
+        assert t.level_n(lev) == o.level_n(lev) and t.level_h(lev) == o.level_h(lev)
+        assert np.array_equal(t.mask(lev), o.get_mask(lev))
+        dg, do = t.distances(lev), o.get_d(lev)
+        assert np.array_equal(dg, do), np.abs(dg - do).max()
+        assert t.num_cut_blocks(lev) == o.num_cut_blocks(lev)
+    assert np.array_equal(t.leaf_centers(), o.leaf_centers())
+
+
+def test_unresolved_search_equals_oracle(G):
+    p = dict(dim=3, N=8, cb=(1, 1, 1), lo=(0.0, 0.0, 0.0), h1=1 / 8, max_level=2, refine=None,
+             lsf=("capsule", (0.5, 0.5, 0.6, 0.5, 0.5, 1.0, 0.02)), walls=(1, 1, 1, 1, 0, 1),
+             wall_values=(0,) * 6, wall_fn=None, phib=1.0, rhs=None, index=0)
+    o = oracle_problem(p, w_min=0.008, rhs=False)
+    t = gpu_problem(p, w_min=0.008, bind=False)
+    n_virtual = 0
+    for lev in range(t.lmin, t.lmax + 1):
+        dg, do = t.distances(lev), o.get_d(lev)
+        assert np.array_equal(dg, do)
+        n_virtual += int((dg < 1).sum())
+    assert n_virtual > 0
+
+
+def test_invalid_arguments_are_rejected(G):
+    with pytest.raises(G.GmgError):
+        G.Tree(3, 7, max_level=2)       # odd block size
+    with pytest.raises(G.GmgError):
+        G.Tree(4, 8, max_level=2)       # dimension
+    with pytest.raises(G.GmgError):
+        G.Tree(3, 8, max_level=0)
+    t = G.Tree(2, 8, max_level=2)
+    with pytest.raises(G.GmgError):
+        t.workspace_bytes()             # before store_stencils
