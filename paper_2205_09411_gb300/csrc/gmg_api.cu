@@ -186,16 +186,51 @@ GmgView<float> view<float>(gmg_tree *t) {
   return v;
 }
 
+template <int V>
+using IC = std::integral_constant<int, V>;
+
+// Calls f(IC<NT>) with NT the compile-time block side for n (0 = runtime).
+template <int D, typename F>
+void with_nt(int n, F &&f) {
+  if (D == 3) {
+    switch (n) {
+      case 4: f(IC<4>{}); return;
+      case 8: f(IC<8>{}); return;
+      case 16: f(IC<16>{}); return;
+      default: f(IC<0>{}); return;
+    }
+  } else {
+    switch (n) {
+      case 8: f(IC<8>{}); return;
+      case 16: f(IC<16>{}); return;
+      case 32: f(IC<32>{}); return;
+      default: f(IC<0>{}); return;
+    }
+  }
+}
+
+template <typename T, int D, int NT>
+void set_smem_limits_nt() {
+  const int big = 200 * 1024;
+  cudaFuncSetAttribute(k_smooth<T, D, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_resid_restrict<T, D, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_fas<T, D, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_prolong<T, D, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_resnorm<T, D, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+}
+
 template <typename T, int D>
 void set_smem_limits() {
+  for (int n : {4, 8, 16, 32, 2}) with_nt<D>(n, [&](auto nt) { set_smem_limits_nt<T, D, decltype(nt)::value>(); });
+}
+
+void set_all_smem_limits() {
   static bool done = false;
   if (done) return;
-  const int big = 200 * 1024;
-  cudaFuncSetAttribute(k_smooth<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  cudaFuncSetAttribute(k_resid_restrict<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  cudaFuncSetAttribute(k_fas<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  cudaFuncSetAttribute(k_prolong<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  cudaFuncSetAttribute(k_resnorm<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  set_smem_limits<double, 2>();
+  set_smem_limits<double, 3>();
+  set_smem_limits<float, 2>();
+  set_smem_limits<float, 3>();
   done = true;
 }
 
@@ -208,19 +243,24 @@ size_t tile_bytes(const gmg_tree *t, int l) {
 // One FAS V-cycle on fields of type T (Sec. 2.2; readings UP and V).
 template <typename T, int D>
 int vcycle_impl(gmg_tree *t, cudaStream_t s) {
-  set_smem_limits<T, D>();
   GmgView<T> V = view<T>(t);
   const int P = prec_of<T>();
   for (int l = t->lmax; l > t->lmin; l--) {
     LvArgs L = lv(t, l), Lp = lv(t, l - 1);
     const size_t sm = tile_bytes<T>(t, l);
-    for (int k = 0; k < t->prm.n_down; k++)
-      for (int c = 0; c < 2; c++)
-        launch(t, s, 0, P, l, [&] { k_smooth<T, D><<<L.count, kThreads, sm, s>>>(V, L, Lp, c); });
-    launch(t, s, 1, P, l, [&] { k_resid_restrict<T, D><<<L.count, kThreads, sm, s>>>(V, L, Lp); });
+    with_nt<D>(L.n, [&](auto nt) {
+      constexpr int NT = decltype(nt)::value;
+      for (int k = 0; k < t->prm.n_down; k++)
+        for (int c = 0; c < 2; c++)
+          launch(t, s, 0, P, l, [&] { k_smooth<T, D, NT><<<L.count, kThreads, sm, s>>>(V, L, Lp, c); });
+      launch(t, s, 1, P, l, [&] { k_resid_restrict<T, D, NT><<<L.count, kThreads, sm, s>>>(V, L, Lp); });
+    });
     LvArgs Lpp = l - 2 >= t->lmin ? lv(t, l - 2) : Lp;
     const size_t smp = tile_bytes<T>(t, l - 1);
-    launch(t, s, 2, P, l - 1, [&] { k_fas<T, D><<<Lp.count, kThreads, smp, s>>>(V, Lp, Lpp); });
+    with_nt<D>(Lp.n, [&](auto nt) {
+      constexpr int NT = decltype(nt)::value;
+      launch(t, s, 2, P, l - 1, [&] { k_fas<T, D, NT><<<Lp.count, kThreads, smp, s>>>(V, Lp, Lpp); });
+    });
   }
   {
     LvArgs Lc = lv(t, t->lmin);
@@ -234,16 +274,22 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s) {
     LvArgs L = lv(t, l), Lp = lv(t, l - 1);
     const int hm = L.n / 2 + 2;
     const size_t psm = sizeof(T) * (size_t)(D == 3 ? hm * hm * hm : hm * hm);
-    launch(t, s, 4, P, l, [&] { k_prolong<T, D><<<L.count, kThreads, psm, s>>>(V, L, Lp); });
     const size_t sm = tile_bytes<T>(t, l);
-    for (int k = 0; k < t->prm.n_up; k++)
-      for (int c = 0; c < 2; c++)
-        launch(t, s, 0, P, l, [&] { k_smooth<T, D><<<L.count, kThreads, sm, s>>>(V, L, Lp, c); });
+    with_nt<D>(L.n, [&](auto nt) {
+      constexpr int NT = decltype(nt)::value;
+      launch(t, s, 4, P, l, [&] { k_prolong<T, D, NT><<<L.count, kThreads, psm, s>>>(V, L, Lp); });
+      for (int k = 0; k < t->prm.n_up; k++)
+        for (int c = 0; c < 2; c++)
+          launch(t, s, 0, P, l, [&] { k_smooth<T, D, NT><<<L.count, kThreads, sm, s>>>(V, L, Lp, c); });
+    });
   }
   if (t->adaptive) {
     for (int l = t->lmax; l >= 2 && l > t->lmin; l--) {
       LvArgs L = lv(t, l), Lp = lv(t, l - 1);
-      launch(t, s, 5, P, l, [&] { k_restrict_phi<T, D><<<L.count, kThreads, 0, s>>>(V, L, Lp); });
+      with_nt<D>(L.n, [&](auto nt) {
+        constexpr int NT = decltype(nt)::value;
+        launch(t, s, 5, P, l, [&] { k_restrict_phi<T, D, NT><<<L.count, kThreads, 0, s>>>(V, L, Lp); });
+      });
     }
   }
   CUDA_TRY(cudaGetLastError());
@@ -255,20 +301,26 @@ int vcycle_any(gmg_tree *t, cudaStream_t s) {
   return t->D == 3 ? vcycle_impl<T, 3>(t, s) : vcycle_impl<T, 2>(t, s);
 }
 
-// composite residual of the FP64 state: partials for every block, final
-// reduction into d_red; with `rout` also the float residual (mixed path)
+// Composite residual of the FP64 state over the leaf blocks: per-block
+// partials, deterministic final reduction into d_red and a copy to the
+// pinned host mirror; with `rout` also the float residual (mixed path).
 template <int D>
 int residual_impl(gmg_tree *t, cudaStream_t s, float *rout) {
-  set_smem_limits<double, D>();
   GmgView<double> V = view<double>(t);
   for (int l = t->lmin; l <= t->lmax; l++) {
     LvArgs L = lv(t, l), Lp = l > t->lmin ? lv(t, l - 1) : L;
+    if (!t->level_has_leaves[l - t->lmin]) continue;
     const size_t sm = tile_bytes<double>(t, l);
-    launch(t, s, 6, 0, l, [&] { k_resnorm<double, D><<<L.count, kThreads, sm, s>>>(V, L, Lp, t->d_partials, rout); });
+    with_nt<D>(L.n, [&](auto nt) {
+      constexpr int NT = decltype(nt)::value;
+      launch(t, s, 6, 0, l,
+             [&] { k_resnorm<double, D, NT><<<L.count, kThreads, sm, s>>>(V, L, Lp, t->d_partials, rout); });
+    });
   }
   launch(t, s, 7, 0, t->lmax,
          [&] { k_reduce_partials<<<1, 1024, 0, s>>>(t->d_partials, (int)t->blocks.size(), t->d_red); });
   CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(t->h_red, t->d_red, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
   return GMG_OK;
 }
 
@@ -276,21 +328,15 @@ int residual_any(gmg_tree *t, cudaStream_t s, float *rout) {
   return t->D == 3 ? residual_impl<3>(t, s, rout) : residual_impl<2>(t, s, rout);
 }
 
-int read_red(gmg_tree *t, cudaStream_t s, double *s2, double *mx, double *b2) {
-  CUDA_TRY(cudaMemcpyAsync(t->h_red, t->d_red, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaStreamSynchronize(s));
-  *s2 = t->h_red[0];
-  *mx = t->h_red[1];
-  *b2 = t->h_red[2];
-  return GMG_OK;
-}
-
 template <int D>
 int restrict_all_phi64(gmg_tree *t, cudaStream_t s) {
   GmgView<double> V = view<double>(t);
   for (int l = t->lmax; l >= 2 && l > t->lmin; l--) {
     LvArgs L = lv(t, l), Lp = lv(t, l - 1);
-    launch(t, s, 5, 0, l, [&] { k_restrict_phi<double, D><<<L.count, kThreads, 0, s>>>(V, L, Lp); });
+    with_nt<D>(L.n, [&](auto nt) {
+      constexpr int NT = decltype(nt)::value;
+      launch(t, s, 5, 0, l, [&] { k_restrict_phi<double, D, NT><<<L.count, kThreads, 0, s>>>(V, L, Lp); });
+    });
   }
   CUDA_TRY(cudaGetLastError());
   return GMG_OK;
@@ -298,6 +344,59 @@ int restrict_all_phi64(gmg_tree *t, cudaStream_t s) {
 
 int restrict_all_phi64_any(gmg_tree *t, cudaStream_t s) {
   return t->D == 3 ? restrict_all_phi64<3>(t, s) : restrict_all_phi64<2>(t, s);
+}
+
+// one defect-correction step of the mixed path: e = 0, FP32 V-cycle on
+// A e = r, phi += e in FP64 (and covered cells restricted)
+int mixed_step(gmg_tree *t, cudaStream_t s) {
+  CUDA_TRY(cudaMemsetAsync(t->f_phi, 0, (size_t)t->total_cells * sizeof(float), s));
+  int rc = vcycle_any<float>(t, s);
+  if (rc) return rc;
+  const long long n = t->n_leaf_cells;
+  launch(t, s, 8, 0, t->lmax, [&] {
+    k_leaf_accumulate<<<grid_for(n), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, t->f_phi, n,
+                                                  t->lev(t->lmax).ncell);
+  });
+  CUDA_TRY(cudaGetLastError());
+  if (t->adaptive) return restrict_all_phi64_any(t, s);
+  return GMG_OK;
+}
+
+// Runs `enqueue` through a CUDA graph captured on first use (slot), or
+// directly while kernel timing is on.
+template <typename F>
+int run_graph(gmg_tree *t, int slot, cudaStream_t s, F &&enqueue) {
+  if (t->prof_on || !t->use_graphs) return enqueue(s);
+  gmg_tree::GraphSlot &g = t->graphs[slot];
+  if (!g.exec) {
+    if (!t->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&t->cap_stream, cudaStreamNonBlocking));
+    const long long before = t->launches;
+    CUDA_TRY(cudaStreamBeginCapture(t->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue(t->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(t->cap_stream, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    CUDA_TRY(e);
+    const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CUDA_TRY(ei);
+    g.kernels = t->launches - before;
+    t->launches = before;
+  }
+  CUDA_TRY(cudaGraphLaunch(g.exec, s));
+  t->launches += g.kernels;
+  return GMG_OK;
+}
+
+int read_red(gmg_tree *t, cudaStream_t s, double *s2, double *mx, double *b2) {
+  CUDA_TRY(cudaStreamSynchronize(s));
+  *s2 = t->h_red[0];
+  *mx = t->h_red[1];
+  *b2 = t->h_red[2];
+  return GMG_OK;
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -377,6 +476,9 @@ int gmg_tree_create(const gmg_domain *domain, const gmg_params *params, gmg_tree
 
 void gmg_tree_destroy(gmg_tree *t) {
   if (!t) return;
+  for (auto &g : t->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (t->cap_stream) cudaStreamDestroy(t->cap_stream);
   for (cudaEvent_t e : t->prof_pool) cudaEventDestroy(e);
   if (t->owns_ws && t->ws) cudaFree(t->ws);
   if (t->h_red) cudaFreeHost(t->h_red);
@@ -511,7 +613,8 @@ int gmg_tree_bind(gmg_tree *t, void *device_ptr, size_t bytes) {
   t->d_pofs = reinterpret_cast<int *>(w + L.pofs);
   t->d_flags = reinterpret_cast<int *>(w + L.flags);
   t->d_leaf = reinterpret_cast<int *>(w + L.leaf);
-  long long *d_cbase = reinterpret_cast<long long *>(w + L.cbase);
+  t->d_cbase = reinterpret_cast<long long *>(w + L.cbase);
+  long long *d_cbase = t->d_cbase;
   t->d_st_base = reinterpret_cast<long long *>(w + L.st_base);
   t->d_bt_base = reinterpret_cast<long long *>(w + L.bt_base);
   t->d_phi = reinterpret_cast<double *>(w + L.phi);
@@ -554,16 +657,17 @@ int gmg_tree_bind(gmg_tree *t, void *device_ptr, size_t bytes) {
   CUDA_TRY(cudaMemset(t->f_phi, 0, cells * sizeof(float)));
   CUDA_TRY(cudaMemset(t->f_b, 0, cells * sizeof(float)));
   CUDA_TRY(cudaMemset(t->f_old, 0, cells * sizeof(float)));
+  // blocks on levels without leaves never write their residual partials
+  CUDA_TRY(cudaMemset(t->d_partials, 0, nb * 3 * sizeof(double)));
   if (!t->h_red) CUDA_TRY(cudaMallocHost(&t->h_red, 4 * sizeof(double)));
+  t->level_has_leaves.assign(t->levels.size(), 0);
+  for (int id : t->leaf_ids_h) t->level_has_leaves[t->blocks[id].level - t->lmin] = 1;
+  set_all_smem_limits();
   CUDA_TRY(cudaDeviceSynchronize());
   t->bound = true;
   return GMG_OK;
 }
 
-static long long *cbase_ptr(gmg_tree *t) {
-  Layout L = layout(t);
-  return reinterpret_cast<long long *>(static_cast<char *>(t->ws) + L.cbase);
-}
 
 int gmg_set_rhs(gmg_tree *t, const double *g, int where, void *stream) {
   if (!t || !g) return set_error("null argument"), GMG_ERR_INVALID_ARG;
@@ -579,7 +683,7 @@ int gmg_set_rhs(gmg_tree *t, const double *g, int where, void *stream) {
     return set_error("where must be GMG_HOST or GMG_DEVICE"), GMG_ERR_INVALID_ARG;
   }
   const int ncell = t->lev(t->lmax).ncell;
-  k_leaf_rhs<<<grid_for(n), 256, 0, s>>>(t->d_leaf, cbase_ptr(t), t->d_bt_base, t->d_bterm, gd, t->d_b, n, ncell);
+  k_leaf_rhs<<<grid_for(n), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_bt_base, t->d_bterm, gd, t->d_b, n, ncell);
   CUDA_TRY(cudaMemsetAsync(t->d_phi, 0, (size_t)t->total_cells * sizeof(double), s));
   CUDA_TRY(cudaGetLastError());
   return GMG_OK;
@@ -596,7 +700,7 @@ int gmg_set_solution(gmg_tree *t, const double *phi, int where, void *stream) {
     src = t->d_old;
   }
   const int ncell = t->lev(t->lmax).ncell;
-  k_leaf_copy<<<grid_for(n), 256, 0, s>>>(t->d_leaf, cbase_ptr(t), t->d_phi, src, n, ncell, 1);
+  k_leaf_copy<<<grid_for(n), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, src, n, ncell, 1);
   CUDA_TRY(cudaGetLastError());
   return restrict_all_phi64_any(t, s);
 }
@@ -608,12 +712,12 @@ int gmg_get_solution(gmg_tree *t, double *phi, int where, void *stream) {
   const long long n = t->n_leaf_cells;
   const int ncell = t->lev(t->lmax).ncell;
   if (where == GMG_DEVICE) {
-    k_leaf_copy<<<grid_for(n), 256, 0, s>>>(t->d_leaf, cbase_ptr(t), t->d_phi, phi, n, ncell, 0);
+    k_leaf_copy<<<grid_for(n), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, phi, n, ncell, 0);
     CUDA_TRY(cudaGetLastError());
     return GMG_OK;
   }
   // the FP64 'old' field is dead between V-cycles: stage the gather there
-  k_leaf_copy<<<grid_for(n), 256, 0, s>>>(t->d_leaf, cbase_ptr(t), t->d_phi, t->d_old, n, ncell, 0);
+  k_leaf_copy<<<grid_for(n), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, t->d_old, n, ncell, 0);
   CUDA_TRY(cudaMemcpyAsync(phi, t->d_old, n * sizeof(double), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   return GMG_OK;
@@ -634,8 +738,9 @@ int gmg_vcycle(gmg_tree *t, int n_cycles, void *stream) {
   if (!t || n_cycles < 0) return set_error("bad arguments"), GMG_ERR_INVALID_ARG;
   if (!t->bound) return set_error("tree not bound"), GMG_ERR_STATE;
   t->launches = 0;
+  cudaStream_t s = as_stream(stream);
   for (int k = 0; k < n_cycles; k++) {
-    int rc = vcycle_any<double>(t, as_stream(stream));
+    int rc = run_graph(t, gmg_tree::kGraphVcycle64, s, [&](cudaStream_t cs) { return vcycle_any<double>(t, cs); });
     if (rc) return rc;
   }
   return GMG_OK;
@@ -645,7 +750,8 @@ int gmg_residual(gmg_tree *t, double *rel_l2, double *linf, void *stream) {
   if (!t) return set_error("null tree"), GMG_ERR_INVALID_ARG;
   if (!t->bound) return set_error("tree not bound"), GMG_ERR_STATE;
   cudaStream_t s = as_stream(stream);
-  int rc = residual_any(t, s, nullptr);
+  t->launches = 0;
+  int rc = run_graph(t, gmg_tree::kGraphResid64, s, [&](cudaStream_t cs) { return residual_any(t, cs, nullptr); });
   if (rc) return rc;
   double s2, mx, b2;
   rc = read_red(t, s, &s2, &mx, &b2);
@@ -663,10 +769,13 @@ int gmg_solve(gmg_tree *t, int precision, double rel_tol, int max_cycles, gmg_st
   t->launches = 0;
   double s2, mx, b2, rel = 0.0, prev = INFINITY;
   int cycles = 0, rc = GMG_OK;
+  const bool mixed = precision == GMG_MIXED;
+  float *rout = mixed ? t->f_b : nullptr;
+  // first residual; then each iteration = one cycle + the residual after it
+  rc = run_graph(t, mixed ? gmg_tree::kGraphResidMixed : gmg_tree::kGraphResid64, s,
+                 [&](cudaStream_t cs) { return residual_any(t, cs, rout); });
+  if (rc) return rc;
   for (;;) {
-    // composite FP64 residual; in the mixed path it is also the FP32 rhs
-    rc = residual_any(t, s, precision == GMG_MIXED ? t->f_b : nullptr);
-    if (rc) return rc;
     rc = read_red(t, s, &s2, &mx, &b2);
     if (rc) return rc;
     const double bn = b2 > 0 ? std::sqrt(b2) : 1.0;
@@ -683,21 +792,10 @@ int gmg_solve(gmg_tree *t, int precision, double rel_tol, int max_cycles, gmg_st
       set_error("tolerance not reached within max_cycles");
       break;
     }
-    if (precision == GMG_FP64) {
-      rc = vcycle_any<double>(t, s);
-    } else {
-      // FP32 correction V-cycle on A e = r with e = 0 (defect correction)
-      CUDA_TRY(cudaMemsetAsync(t->f_phi, 0, (size_t)t->total_cells * sizeof(float), s));
-      rc = vcycle_any<float>(t, s);
-      if (rc) return rc;
-      const long long n = t->n_leaf_cells;
-      launch(t, s, 8, 0, t->lmax, [&] {
-        k_leaf_accumulate<<<grid_for(n), 256, 0, s>>>(t->d_leaf, cbase_ptr(t), t->d_phi, t->f_phi, n,
-                                                      t->lev(t->lmax).ncell);
-      });
-      CUDA_TRY(cudaGetLastError());
-      if (t->adaptive) rc = restrict_all_phi64_any(t, s);
-    }
+    rc = run_graph(t, mixed ? gmg_tree::kGraphCycleMixed : gmg_tree::kGraphCycle64, s, [&](cudaStream_t cs) {
+      int r = mixed ? mixed_step(t, cs) : vcycle_any<double>(t, cs);
+      return r ? r : residual_any(t, cs, rout);
+    });
     if (rc) return rc;
     cycles++;
   }

@@ -98,13 +98,25 @@ struct gmg_tree {
   void *ws = nullptr;
   size_t ws_bytes = 0;
   int *d_nbr = nullptr, *d_parent = nullptr, *d_pofs = nullptr, *d_flags = nullptr, *d_leaf = nullptr;
-  long long *d_st_base = nullptr, *d_bt_base = nullptr;
+  long long *d_st_base = nullptr, *d_bt_base = nullptr, *d_cbase = nullptr;
   double *d_phi = nullptr, *d_b = nullptr, *d_old = nullptr;
   float *f_phi = nullptr, *f_b = nullptr, *f_old = nullptr;
   double *d_st = nullptr, *d_bterm = nullptr, *d_cinv = nullptr, *d_partials = nullptr, *d_red = nullptr;
   float *f_st = nullptr;
   double *h_red = nullptr;  // pinned host mirror of d_red
   long long launches = 0;
+
+  std::vector<char> level_has_leaves;  // index l - lmin
+
+  // CUDA graphs of the solve phases (captured on first use)
+  struct GraphSlot {
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;
+  };
+  enum { kGraphResid64 = 0, kGraphResidMixed, kGraphCycle64, kGraphCycleMixed, kGraphVcycle64, kGraphSlots };
+  GraphSlot graphs[kGraphSlots];
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;
 
   // kernel timing (gmg_profile_enable)
   struct ProfRec {

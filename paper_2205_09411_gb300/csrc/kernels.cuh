@@ -13,6 +13,9 @@ namespace gmg {
 
 constexpr int kThreads = 256;
 
+// cells of a block of side n (compile-time when n is)
+#define NCELL (D == 3 ? n * n * n : n * n)
+
 __device__ __forceinline__ int nbr_slot(int ox, int oy, int oz) { return (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1); }
 
 // Local coordinate p (each component in [-1, n]) of block `bid` on level L:
@@ -92,35 +95,151 @@ __device__ T refine_ghost(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
   return f / T(3) + T(2) * chat / T(3);
 }
 
-// Stage phi of block `bid` with its face ghosts into tile[(n+2)^D].
-template <typename T, int D>
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+};
+
+// Source of one ghost-face value: a cell of a same-level neighbour (or of
+// the block itself, reflected at a wall) and its sign; false when the
+// neighbour is missing (refinement boundary, reading G).
+template <int D>
+__device__ __forceinline__ bool face_source(const int *s_nb, int fl, const float *wsign, const LvArgs &L, int n,
+                                            int bid, const int *p, int a, int side, long long *idx, float *sg) {
+  const int ncell = D == 3 ? n * n * n : n * n;
+  int q[3] = {p[0], p[1], p[2]};
+  int id = s_nb[2 * a + side];
+  *sg = 1.f;
+  if (fl & wall_bit(a, side)) {
+    q[a] = side ? n - 1 : 0;
+    *sg = wsign[2 * a + side];
+    id = bid;
+  } else {
+    if (id < 0) return false;
+    q[a] = side ? 0 : n - 1;
+  }
+  *idx = L.off + (long long)(id - L.first) * ncell + q[0] + n * (q[1] + (D == 3 ? n * q[2] : 0));
+  return true;
+}
+
+// Stage phi of block `bid` with its face ghosts into tile[(n+2)^D].  The
+// face neighbours' ids and the block flags are read once per CTA; every
+// thread then issues all its global loads (16-byte vectors for the block's
+// cells, scalars for the 2D ghost faces) before the shared-memory stores.
+// NT is the block side when known at compile time (0: runtime L.n).
+template <typename T, int D, int NT>
 __device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, T *tile) {
-  const int n = L.n, m = n + 2;
-  const int tsize = D == 3 ? m * m * m : m * m;
-  const long long base = L.off + (long long)(bid - L.first) * L.ncell;
-  for (int t = threadIdx.x; t < tsize; t += blockDim.x) {
-    const int p[3] = {t % m - 1, (t / m) % m - 1, D == 3 ? t / (m * m) - 1 : 0};
-    int nout = 0, a = 0;
+  __shared__ int s_nb[6];
+  __shared__ int s_fl;
+  const int n = NT ? NT : L.n, m = n + 2;
+  const int ncell = D == 3 ? n * n * n : n * n;
+  if (threadIdx.x < 2 * D) {
+    const int a = threadIdx.x >> 1, side = threadIdx.x & 1;
+    const int o[3] = {a == 0 ? 2 * side - 1 : 0, a == 1 ? 2 * side - 1 : 0, a == 2 ? 2 * side - 1 : 0};
+    s_nb[threadIdx.x] = V.nbr[(size_t)bid * kNbr + nbr_slot(o[0], o[1], o[2])];
+  }
+  if (threadIdx.x == 0) s_fl = V.flags[bid];
+  const long long base = L.off + (long long)(bid - L.first) * ncell;
+  constexpr int VEC = 16 / sizeof(T);
+  using VT = typename Vec16<T>::type;
+  const VT *__restrict__ src = reinterpret_cast<const VT *>(V.phi + base);
+  const int nvec = ncell / VEC;
+  const int nf = D == 3 ? n * n : n;
+  if (NT) {
+    constexpr int NC = NT ? (D == 3 ? NT * NT * NT : NT * NT) : 1;
+    constexpr int NF = NT ? (D == 3 ? NT * NT : NT) : 1;
+    constexpr int IV = NC / VEC >= 1 ? (NC / VEC + kThreads - 1) / kThreads : 1;
+    constexpr int IF = (2 * D * NF + kThreads - 1) / kThreads;
+    VT rv[IV];
 #pragma unroll
-    for (int d = 0; d < D; d++)
-      if (p[d] < 0 || p[d] >= n) {
-        nout++;
-        a = d;
+    for (int k = 0; k < IV; k++) {
+      const int i = threadIdx.x + k * kThreads;
+      if (i < nvec) rv[k] = src[i];
+    }
+    __syncthreads();
+    const int fl = s_fl;
+    T rf[IF];
+    int tf[IF];
+#pragma unroll
+    for (int k = 0; k < IF; k++) {
+      const int i = threadIdx.x + k * kThreads;
+      tf[k] = -1;
+      if (i < 2 * D * nf) {
+        const int f = i / nf, j = i - f * nf;
+        const int a = f >> 1, side = f & 1;
+        int p[3] = {0, 0, 0};
+        if (D == 3) {
+          p[a == 0 ? 1 : 0] = j % n;
+          p[a == 2 ? 1 : 2] = j / n;
+        } else {
+          p[1 - a] = j;
+        }
+        long long ix;
+        float sg;
+        if (face_source<D>(s_nb, fl, V.wsign, L, n, bid, p, a, side, &ix, &sg)) {
+          rf[k] = T(sg) * V.phi[ix];
+        } else {
+          p[a] = side ? n : -1;
+          rf[k] = refine_ghost<T, D>(V, L, Lp, bid, p, a);
+        }
+        p[a] = side ? n : -1;
+        tf[k] = (p[0] + 1) + m * ((p[1] + 1) + (D == 3 ? m * (p[2] + 1) : 0));
       }
-    T v;
-    if (nout == 0) {
-      v = V.phi[base + p[0] + n * (p[1] + (D == 3 ? n * p[2] : 0))];
-    } else if (nout > 1) {
-      v = T(0);  // edges and corners: not used by the 5/7-point operator
-    } else {
+    }
+#pragma unroll
+    for (int k = 0; k < IV; k++) {
+      const int i = threadIdx.x + k * kThreads;
+      if (i < nvec) {
+        const int c = i * VEC;
+        const int x = c % n, y = (c / n) % n, z = D == 3 ? c / (n * n) : 0;
+        T *dst = tile + (x + 1) + m * ((y + 1) + (D == 3 ? m * (z + 1) : 0));
+        const T *e = reinterpret_cast<const T *>(&rv[k]);
+#pragma unroll
+        for (int q = 0; q < VEC; q++) dst[q] = e[q];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < IF; k++)
+      if (tf[k] >= 0) tile[tf[k]] = rf[k];
+  } else {
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+      const VT v = src[i];
+      const int c = i * VEC;
+      const int x = c % n, y = (c / n) % n, z = D == 3 ? c / (n * n) : 0;
+      T *dst = tile + (x + 1) + m * ((y + 1) + (D == 3 ? m * (z + 1) : 0));
+      const T *e = reinterpret_cast<const T *>(&v);
+      for (int q = 0; q < VEC; q++) dst[q] = e[q];
+    }
+    __syncthreads();
+    const int fl = s_fl;
+    for (int i = threadIdx.x; i < 2 * D * nf; i += blockDim.x) {
+      const int f = i / nf, j = i - f * nf;
+      const int a = f >> 1, side = f & 1;
+      int p[3] = {0, 0, 0};
+      if (D == 3) {
+        p[a == 0 ? 1 : 0] = j % n;
+        p[a == 2 ? 1 : 2] = j / n;
+      } else {
+        p[1 - a] = j;
+      }
       long long ix;
       float sg;
-      if (resolve<D>(V.nbr, V.flags, V.wsign, L, bid, p, &ix, &sg))
+      T v;
+      if (face_source<D>(s_nb, fl, V.wsign, L, n, bid, p, a, side, &ix, &sg)) {
         v = T(sg) * V.phi[ix];
-      else
+      } else {
+        p[a] = side ? n : -1;
         v = refine_ghost<T, D>(V, L, Lp, bid, p, a);
+      }
+      p[a] = side ? n : -1;
+      tile[(p[0] + 1) + m * ((p[1] + 1) + (D == 3 ? m * (p[2] + 1) : 0))] = v;
     }
-    tile[t] = v;
   }
 }
 
@@ -142,6 +261,21 @@ __device__ __forceinline__ T offdiag(const GmgView<T> &V, const T *tile, int t, 
   return s;
 }
 
+// r = b - A phi at cell c; the regular 5/7-point form costs 2D - 1 adds and
+// two fused multiply-adds (FP64 throughput is the bound on this path).
+template <typename T, int D>
+__device__ __forceinline__ T residual_at(const GmgView<T> &V, const T *tile, int t, int m, long long sb, int ncell,
+                                         int c, T inv_h2, T b) {
+  if (sb < 0) {
+    T s = (tile[t - 1] + tile[t + 1]) + (tile[t - m] + tile[t + m]);
+    if (D == 3) s += tile[t - m * m] + tile[t + m * m];
+    return b - inv_h2 * (s - T(2 * D) * tile[t]);
+  }
+  T diag;
+  const T s = offdiag<T, D>(V, tile, t, m, sb, ncell, c, inv_h2, &diag);
+  return b - (diag * tile[t] + s);
+}
+
 template <int D>
 __device__ __forceinline__ void cell_xyz(int c, int n, int *x, int *y, int *z) {
   *x = c % n;
@@ -151,49 +285,79 @@ __device__ __forceinline__ void cell_xyz(int c, int n, int *x, int *y, int *z) {
 
 // One red (color 0) or black (color 1) half-sweep of Gauss-Seidel on every
 // block of a level (Sec. 2.2, readings S and SW).
-template <typename T, int D>
+template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kThreads) k_smooth(GmgView<T> V, LvArgs L, LvArgs Lp, int color) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *tile = reinterpret_cast<T *>(smem_raw);
   const int bid = L.first + blockIdx.x;
-  load_tile<T, D>(V, L, Lp, bid, tile);
-  __syncthreads();
-  const int n = L.n, m = n + 2, hn = n / 2;
-  const long long base = L.off + (long long)(bid - L.first) * L.ncell;
-  const long long sb = V.st_base[bid];
+  const int n = NT ? NT : L.n, m = n + 2, hn = n / 2;
+  const long long base = L.off + (long long)(bid - L.first) * NCELL;
   const T h2 = T(L.h * L.h), inv_h2 = T(1.0 / (L.h * L.h)), inv2d = T(1.0 / (2 * D));
-  for (int j = threadIdx.x; j < L.ncell / 2; j += blockDim.x) {
-    const int rest = j / hn;
-    const int y = rest % n, z = D == 3 ? rest / n : 0;
-    const int x = 2 * (j % hn) + ((y + z + color) & 1);
-    const int c = x + n * (y + n * z);
-    const int t = (x + 1) + m * ((y + 1) + (D == 3 ? m * (z + 1) : 0));
-    T nv;
-    if (sb < 0) {
-      T s = (tile[t - 1] + tile[t + 1]) + (tile[t - m] + tile[t + m]);
-      if (D == 3) s += tile[t - m * m] + tile[t + m * m];
-      nv = (s - h2 * V.b[base + c]) * inv2d;
-    } else {
-      T diag;
-      const T s = offdiag<T, D>(V, tile, t, m, sb, L.ncell, c, inv_h2, &diag);
-      nv = (V.b[base + c] - s) / diag;
+  // cells of this colour handled by the thread; their b is loaded before
+  // the tile so that both loads are in flight together
+  constexpr int IC = NT ? ((D == 3 ? NT * NT * NT : NT * NT) / 2 + kThreads - 1) / kThreads : 1;
+  const int nhalf = NCELL / 2;
+  const long long sb = V.st_base[bid];
+  // With a compile-time side every thread runs exactly one batch (IC cells
+  // per thread cover the colour) and issues its b loads before the tile is
+  // staged; with a runtime side the tile is staged first and the cells loop.
+  // Either way every thread reaches the barrier exactly once.
+  if (!NT) {
+    load_tile<T, D, NT>(V, L, Lp, bid, tile);
+    __syncthreads();
+  }
+  const int j_end = NT ? (int)blockDim.x : nhalf;
+  for (int j0 = threadIdx.x; j0 < j_end; j0 += IC * blockDim.x) {
+    T bv[IC];
+    int cc[IC], tt[IC];
+#pragma unroll
+    for (int k = 0; k < IC; k++) {
+      const int j = j0 + k * blockDim.x;
+      cc[k] = -1;
+      if (j < nhalf) {
+        const int rest = j / hn;
+        const int y = rest % n, z = D == 3 ? rest / n : 0;
+        const int x = 2 * (j % hn) + ((y + z + color) & 1);
+        cc[k] = x + n * (y + n * z);
+        tt[k] = (x + 1) + m * ((y + 1) + (D == 3 ? m * (z + 1) : 0));
+        bv[k] = V.b[base + cc[k]];
+      }
     }
-    V.phi[base + c] = nv;
+    if (NT) {
+      load_tile<T, D, NT>(V, L, Lp, bid, tile);
+      __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < IC; k++) {
+      if (cc[k] < 0) continue;
+      const int t = tt[k], c = cc[k];
+      T nv;
+      if (sb < 0) {
+        T s = (tile[t - 1] + tile[t + 1]) + (tile[t - m] + tile[t + m]);
+        if (D == 3) s += tile[t - m * m] + tile[t + m * m];
+        nv = (s - h2 * bv[k]) * inv2d;
+      } else {
+        T diag;
+        const T s = offdiag<T, D>(V, tile, t, m, sb, NCELL, c, inv_h2, &diag);
+        nv = (bv[k] - s) / diag;
+      }
+      V.phi[base + c] = nv;
+    }
   }
 }
 
 // Residual r = b - A phi (Eq. (residual)) of every cell, restricted to the
 // parent as the mean of the 2^D children, together with phi (Sec. 2.2):
 // parent phi <- mean phi, parent b <- mean r (the FAS kernel adds A phi).
-template <typename T, int D>
+template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kThreads) k_resid_restrict(GmgView<T> V, LvArgs L, LvArgs Lp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *tile = reinterpret_cast<T *>(smem_raw);
   const int bid = L.first + blockIdx.x;
-  load_tile<T, D>(V, L, Lp, bid, tile);
+  load_tile<T, D, NT>(V, L, Lp, bid, tile);
   __syncthreads();
-  const int n = L.n, m = n + 2, hn = n / 2;
-  const long long base = L.off + (long long)(bid - L.first) * L.ncell;
+  const int n = NT ? NT : L.n, m = n + 2, hn = n / 2;
+  const long long base = L.off + (long long)(bid - L.first) * NCELL;
   const long long sb = V.st_base[bid];
   const T inv_h2 = T(1.0 / (L.h * L.h));
   const int P = V.parent[bid], po = V.pofs[bid];
@@ -214,11 +378,8 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(GmgView<T> V, LvArg
           const int x = 2 * qx + dx, y = 2 * qy + dy, z = 2 * qz + dz;
           const int c = x + n * (y + n * z);
           const int t = (x + 1) + m * ((y + 1) + (D == 3 ? m * (z + 1) : 0));
-          T diag;
-          const T s = offdiag<T, D>(V, tile, t, m, sb, L.ncell, c, inv_h2, &diag);
-          const T ph = tile[t];
-          sp = sp + ph;
-          sr = sr + (V.b[base + c] - (diag * ph + s));
+          sp = sp + tile[t];
+          sr = sr + residual_at<T, D>(V, tile, t, m, sb, NCELL, c, inv_h2, V.b[base + c]);
         }
     const long long pc = pbase + (pofs[0] + qx) + pn * ((pofs[1] + qy) + (D == 3 ? pn * (pofs[2] + qz) : 0));
     V.phi[pc] = sp * w;
@@ -228,27 +389,27 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(GmgView<T> V, LvArg
 
 // FAS coarse right-hand side on covered cells: b <- A phi + (restricted r);
 // old <- phi on every cell of the level (start of the coarse visit).
-template <typename T, int D>
+template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kThreads) k_fas(GmgView<T> V, LvArgs L, LvArgs Lp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *tile = reinterpret_cast<T *>(smem_raw);
   const int bid = L.first + blockIdx.x;
-  const long long base = L.off + (long long)(bid - L.first) * L.ncell;
+  const int n = NT ? NT : L.n, m = n + 2;
+  const long long base = L.off + (long long)(bid - L.first) * NCELL;
   if (!(V.flags[bid] & kHasChildren)) {
-    for (int c = threadIdx.x; c < L.ncell; c += blockDim.x) V.old[base + c] = V.phi[base + c];
+    for (int c = threadIdx.x; c < NCELL; c += blockDim.x) V.old[base + c] = V.phi[base + c];
     return;
   }
-  load_tile<T, D>(V, L, Lp, bid, tile);
+  load_tile<T, D, NT>(V, L, Lp, bid, tile);
   __syncthreads();
-  const int n = L.n, m = n + 2;
   const long long sb = V.st_base[bid];
   const T inv_h2 = T(1.0 / (L.h * L.h));
-  for (int c = threadIdx.x; c < L.ncell; c += blockDim.x) {
+  for (int c = threadIdx.x; c < NCELL; c += blockDim.x) {
     int x, y, z;
     cell_xyz<D>(c, n, &x, &y, &z);
     const int t = (x + 1) + m * ((y + 1) + (D == 3 ? m * (z + 1) : 0));
     T diag;
-    const T s = offdiag<T, D>(V, tile, t, m, sb, L.ncell, c, inv_h2, &diag);
+    const T s = offdiag<T, D>(V, tile, t, m, sb, NCELL, c, inv_h2, &diag);
     const T ph = tile[t];
     V.b[base + c] = (diag * ph + s) + V.b[base + c];
     V.old[base + c] = ph;
@@ -273,12 +434,12 @@ __global__ void __launch_bounds__(kThreads) k_coarse(const double *__restrict__ 
 // (Bi/tri)linear prolongation of the coarse correction phi - old
 // (Sec. 2.2, 3.4): weights 3/4 and 1/4 per dimension from the parent cell
 // and its neighbours toward the fine cell (reading P).
-template <typename T, int D>
+template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kThreads) k_prolong(GmgView<T> V, LvArgs L, LvArgs Lp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *tile = reinterpret_cast<T *>(smem_raw);
   const int bid = L.first + blockIdx.x;
-  const int n = L.n, hn = n / 2, m = hn + 2;
+  const int n = NT ? NT : L.n, hn = n / 2, m = hn + 2;
   const int P = V.parent[bid], po = V.pofs[bid];
   const int pofs[3] = {po & 1023, (po >> 10) & 1023, (po >> 20) & 1023};
   const int tsize = D == 3 ? m * m * m : m * m;
@@ -291,8 +452,8 @@ __global__ void __launch_bounds__(kThreads) k_prolong(GmgView<T> V, LvArgs L, Lv
     tile[t] = v;
   }
   __syncthreads();
-  const long long base = L.off + (long long)(bid - L.first) * L.ncell;
-  for (int c = threadIdx.x; c < L.ncell; c += blockDim.x) {
+  const long long base = L.off + (long long)(bid - L.first) * NCELL;
+  for (int c = threadIdx.x; c < NCELL; c += blockDim.x) {
     int x, y, z;
     cell_xyz<D>(c, n, &x, &y, &z);
     const int u[3] = {(x >> 1) + 1, (y >> 1) + 1, (z >> 1) + 1};
@@ -314,11 +475,11 @@ __global__ void __launch_bounds__(kThreads) k_prolong(GmgView<T> V, LvArgs L, Lv
 }
 
 // phi of covered cells <- mean of the children (composite consistency).
-template <typename T, int D>
+template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kThreads) k_restrict_phi(GmgView<T> V, LvArgs L, LvArgs Lp) {
   const int bid = L.first + blockIdx.x;
-  const int n = L.n, hn = n / 2;
-  const long long base = L.off + (long long)(bid - L.first) * L.ncell;
+  const int n = NT ? NT : L.n, hn = n / 2;
+  const long long base = L.off + (long long)(bid - L.first) * NCELL;
   const int P = V.parent[bid], po = V.pofs[bid];
   const int pofs[3] = {po & 1023, (po >> 10) & 1023, (po >> 20) & 1023};
   const long long pbase = Lp.off + (long long)(P - Lp.first) * Lp.ncell;
@@ -367,7 +528,7 @@ __device__ __forceinline__ void block_reduce3(double s2, double mx, double b2, d
 // Residual norms over the leaf blocks of a level (reading R); with `rout`
 // the residual itself is written as float (right-hand side of the FP32
 // correction V-cycle in the mixed path).
-template <typename T, int D>
+template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kThreads) k_resnorm(GmgView<T> V, LvArgs L, LvArgs Lp, double *partials,
                                                       float *rout) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -377,26 +538,28 @@ __global__ void __launch_bounds__(kThreads) k_resnorm(GmgView<T> V, LvArgs L, Lv
     if (threadIdx.x < 3) partials[(size_t)bid * 3 + threadIdx.x] = 0.0;
     return;
   }
-  load_tile<T, D>(V, L, Lp, bid, tile);
+  load_tile<T, D, NT>(V, L, Lp, bid, tile);
   __syncthreads();
-  const int n = L.n, m = n + 2;
-  const long long base = L.off + (long long)(bid - L.first) * L.ncell;
+  const int n = NT ? NT : L.n, m = n + 2;
+  const long long base = L.off + (long long)(bid - L.first) * NCELL;
   const long long sb = V.st_base[bid];
   const T inv_h2 = T(1.0 / (L.h * L.h));
-  double s2 = 0.0, mx = 0.0, b2 = 0.0;
-  for (int c = threadIdx.x; c < L.ncell; c += blockDim.x) {
+  // the norms only steer the stopping test: squares and maxima of the
+  // rounded residual are accumulated in FP32 per thread, then in FP64
+  float s2f = 0.f, mxf = 0.f, b2f = 0.f;
+  for (int c = threadIdx.x; c < NCELL; c += blockDim.x) {
     int x, y, z;
     cell_xyz<D>(c, n, &x, &y, &z);
     const int t = (x + 1) + m * ((y + 1) + (D == 3 ? m * (z + 1) : 0));
-    T diag;
-    const T s = offdiag<T, D>(V, tile, t, m, sb, L.ncell, c, inv_h2, &diag);
     const T bb = V.b[base + c];
-    const double r = (double)(bb - (diag * tile[t] + s));
-    if (rout) rout[base + c] = (float)r;
-    s2 += r * r;
-    mx = fmax(mx, fabs(r));
-    b2 += (double)bb * (double)bb;
+    const float r = (float)residual_at<T, D>(V, tile, t, m, sb, NCELL, c, inv_h2, bb);
+    if (rout) rout[base + c] = r;
+    s2f = fmaf(r, r, s2f);
+    mxf = fmaxf(mxf, fabsf(r));
+    const float bf = (float)bb;
+    b2f = fmaf(bf, bf, b2f);
   }
+  const double s2 = s2f, mx = mxf, b2 = b2f;
   block_reduce3(s2, mx, b2, partials + (size_t)bid * 3);
 }
 
