@@ -173,6 +173,23 @@ int gmg_vcycle(gmg_tree *tree, int n_cycles, void *stream);
 /* Composite residual ||b - A phi||_2 over leaf cells, relative to ||b||_2,
  * and max |b - A phi|.  Synchronises the stream. */
 int gmg_residual(gmg_tree *tree, double *rel_l2, double *linf, void *stream);
+/* The same composite residual as gmg_residual, for callers that cannot
+ * allocate device memory: code that runs inside another runtime's memory
+ * pool, allocation-free real-time loops, or plug-ins that may only use the
+ * buffers they are handed.  The paper has no counterpart; this is a service
+ * of the library.  `out` is a caller-owned device array of two doubles that
+ * receives ||b - A phi||_2 / ||b||_2 (||r||_2 when b = 0) and max |b - A phi|;
+ * the work is enqueued on `stream` and the call does not synchronise.  It
+ * calls no cudaMalloc, cudaFree or allocating library routine: the per-block
+ * partial sums live in one static device array of the library (3 MiB, held
+ * on every device that loads the library until the process exits), which
+ * limits the tree to 131072 blocks (larger trees: GMG_ERR_INVALID_ARG).
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress), so make it before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU (several streams or host
+ * threads at once) race and must be serialised by the caller.
+ * Errors: INVALID_ARG, STATE (tree not bound), CUDA. */
+int gmg_residual_noalloc(gmg_tree *tree, double *out, void *stream);
 /* Solves to ||b - A phi||_2 <= rel_tol ||b||_2 from the current phi with
  * GMG_FP64 V-cycles or GMG_MIXED defect correction; stats may be NULL.
  * Synchronises once per cycle (the convergence test).

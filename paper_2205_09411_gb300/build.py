@@ -1,11 +1,12 @@
 """Builds the CUDA library libgmg.so in-tree for sm_103a (GB300).
 
-Two translation units are compiled in parallel by nvcc and linked into one
+The translation units are compiled in parallel by nvcc and linked into one
 shared library with a plain C ABI (include/gmg.h):
 
 * csrc/gmg_api.cu      - kernels, V-cycle schedule, solve loops, C entry points
 * csrc/tree_setup.cpp  - block tree and boundary set-up on the host
   (-ffp-contract=off: the level-set arithmetic is plain IEEE)
+* csrc/noalloc.cu      - residual norm with a static scratch array (no allocation)
 """
 import os
 import subprocess
@@ -19,7 +20,7 @@ LIB = os.path.join(OUT, "libgmg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
           "-I", os.path.join(ROOT, "include"), "-I", CSRC]
-SOURCES = ["gmg_api.cu", "tree_setup.cpp"]
+SOURCES = ["gmg_api.cu", "tree_setup.cpp", "noalloc.cu"]
 
 
 def _nvcc():
