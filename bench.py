@@ -306,10 +306,14 @@ def run_ours(args):
 
     clocks = Clocks(local)
     clocks.start()
-    mixed = timed(G.MIXED, profile=True)
+    mixed = timed(G.MIXED)
     clk = clocks.stop()
     fp64 = timed(G.FP64)
     e2e = timed(G.MIXED, e2e=True)
+    # kernel durations: the same steps again with CUDA events around every
+    # kernel (each phase is queued behind a short delay kernel, so the events
+    # time the kernels and not the host)
+    mixed["prof"] = timed(G.MIXED, profile=True)["prof"]
 
     def munks(r):
         return world * n * r["cycles"] / (r["total_ms"] * 1e-3) / 1e6
@@ -354,6 +358,8 @@ def run_ours(args):
         "gpu_launches": mixed["launches"],
         "roofline": roofline,
         "kernel_ms_by_kind": {"%s_%s" % k: v for k, v in sorted(by_kind.items(), key=lambda kv: -kv[1])},
+        "kernel_us_per_launch": {"%s_%s_l%d" % (k, p_, lv): round(ms * 1e3 / cnt, 2)
+                                 for k, p_, lv, cnt, ms in mixed["prof"]},
         "clocks": clk,
     }
     if rank == 0 and world == 1:

@@ -49,6 +49,7 @@ struct LvArgs {
 template <typename T>
 struct GmgView {
   const int *nbr;        // [nb][27] same-level neighbour id, -1 none, -2 outside
+  const int *pnb;        // [nb][27] the parent's same-level neighbours (nbr of the parent)
   const int *parent;     // [nb]
   const int *pofs;       // [nb] packed px | py << 10 | pz << 20
   const int *flags;      // [nb] kHasChildren | wall bits
@@ -97,7 +98,7 @@ struct gmg_tree {
   bool bound = false, owns_ws = false;
   void *ws = nullptr;
   size_t ws_bytes = 0;
-  int *d_nbr = nullptr, *d_parent = nullptr, *d_pofs = nullptr, *d_flags = nullptr, *d_leaf = nullptr;
+  int *d_nbr = nullptr, *d_pnb = nullptr, *d_parent = nullptr, *d_pofs = nullptr, *d_flags = nullptr, *d_leaf = nullptr;
   long long *d_st_base = nullptr, *d_bt_base = nullptr, *d_cbase = nullptr;
   double *d_phi = nullptr, *d_b = nullptr, *d_old = nullptr;
   float *f_phi = nullptr, *f_b = nullptr, *f_old = nullptr;

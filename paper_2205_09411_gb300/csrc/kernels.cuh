@@ -59,6 +59,43 @@ __device__ __forceinline__ bool resolve(const int *__restrict__ nbr, const int *
   return true;
 }
 
+// resolve() with the block's 27 same-level neighbours already in shared
+// memory (-2 marks a neighbour position outside the domain).
+template <int D>
+__device__ __forceinline__ bool resolve_s(const int *s_nb, int bid, const LvArgs &L, const float *wsign,
+                                          const int *pin, long long *idx, float *sign) {
+  const int n = L.n;
+  int p[3] = {pin[0], pin[1], pin[2]}, o[3] = {0, 0, 0};
+  float sg = 1.f;
+#pragma unroll
+  for (int d = 0; d < D; d++) {
+    const int lo = nbr_slot(d == 0 ? -1 : 0, d == 1 ? -1 : 0, d == 2 ? -1 : 0);
+    const int hi = nbr_slot(d == 0 ? 1 : 0, d == 1 ? 1 : 0, d == 2 ? 1 : 0);
+    if (p[d] < 0) {
+      if (s_nb[lo] == -2) {
+        p[d] = -1 - p[d];
+        sg *= wsign[2 * d];
+      } else {
+        o[d] = -1;
+        p[d] += n;
+      }
+    } else if (p[d] >= n) {
+      if (s_nb[hi] == -2) {
+        p[d] = 2 * n - 1 - p[d];
+        sg *= wsign[2 * d + 1];
+      } else {
+        o[d] = 1;
+        p[d] -= n;
+      }
+    }
+  }
+  const int id = (o[0] | o[1] | o[2]) ? s_nb[nbr_slot(o[0], o[1], o[2])] : bid;
+  if (id < 0) return false;
+  *idx = L.off + (long long)(id - L.first) * L.ncell + p[0] + n * (p[1] + (D == 3 ? n * p[2] : 0));
+  *sign = sg;
+  return true;
+}
+
 // Refinement-boundary ghost (reading G): g = f/3 + 2/3 c_hat, with f the
 // adjacent fine cell and c_hat the coarse cell containing the ghost centre
 // shifted by central tangential slopes (+-1/4 coarse cell).
@@ -128,13 +165,16 @@ __device__ __forceinline__ bool face_source(const int *s_nb, int fl, const float
   return true;
 }
 
-// Stage phi of block `bid` with its face ghosts into tile[(n+2)^D].  The
-// face neighbours' ids and the block flags are read once per CTA; every
-// thread then issues all its global loads (16-byte vectors for the block's
-// cells, scalars for the 2D ghost faces) before the shared-memory stores.
-// NT is the block side when known at compile time (0: runtime L.n).
+// Stage phi of block `bid` with its face ghosts into tile[(n+2)^D] and, if
+// sbv != nullptr, the block's b into the dense array sbv[n^D].  The face
+// neighbours' ids and the block flags are read once per CTA; every thread
+// issues all its global loads (16-byte vectors for the block's cells,
+// scalars for the 2D ghost faces) before any shared-memory store, so that
+// the whole stage costs two dependent memory round trips.  Ends with a
+// barrier.  NT is the block side when known at compile time (0: runtime).
 template <typename T, int D, int NT>
-__device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, T *tile) {
+__device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, T *tile,
+                          T *sbv = nullptr) {
   __shared__ int s_nb[6];
   __shared__ int s_fl;
   const int n = NT ? NT : L.n, m = n + 2;
@@ -149,6 +189,7 @@ __device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
   constexpr int VEC = 16 / sizeof(T);
   using VT = typename Vec16<T>::type;
   const VT *__restrict__ src = reinterpret_cast<const VT *>(V.phi + base);
+  const VT *__restrict__ srcb = reinterpret_cast<const VT *>(V.b + base);
   const int nvec = ncell / VEC;
   const int nf = D == 3 ? n * n : n;
   if (NT) {
@@ -156,11 +197,14 @@ __device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
     constexpr int NF = NT ? (D == 3 ? NT * NT : NT) : 1;
     constexpr int IV = NC / VEC >= 1 ? (NC / VEC + kThreads - 1) / kThreads : 1;
     constexpr int IF = (2 * D * NF + kThreads - 1) / kThreads;
-    VT rv[IV];
+    VT rv[IV], rb[IV];
 #pragma unroll
     for (int k = 0; k < IV; k++) {
       const int i = threadIdx.x + k * kThreads;
-      if (i < nvec) rv[k] = src[i];
+      if (i < nvec) {
+        rv[k] = src[i];
+        if (sbv) rb[k] = srcb[i];
+      }
     }
     __syncthreads();
     const int fl = s_fl;
@@ -202,6 +246,7 @@ __device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
         const T *e = reinterpret_cast<const T *>(&rv[k]);
 #pragma unroll
         for (int q = 0; q < VEC; q++) dst[q] = e[q];
+        if (sbv) reinterpret_cast<VT *>(sbv)[i] = rb[k];
       }
     }
 #pragma unroll
@@ -215,6 +260,7 @@ __device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
       T *dst = tile + (x + 1) + m * ((y + 1) + (D == 3 ? m * (z + 1) : 0));
       const T *e = reinterpret_cast<const T *>(&v);
       for (int q = 0; q < VEC; q++) dst[q] = e[q];
+      if (sbv) reinterpret_cast<VT *>(sbv)[i] = srcb[i];
     }
     __syncthreads();
     const int fl = s_fl;
@@ -241,39 +287,14 @@ __device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
       tile[(p[0] + 1) + m * ((p[1] + 1) + (D == 3 ? m * (p[2] + 1) : 0))] = v;
     }
   }
+  __syncthreads();
 }
 
-// Off-diagonal sum and diagonal of the operator at cell c (tile index t).
-template <typename T, int D>
-__device__ __forceinline__ T offdiag(const GmgView<T> &V, const T *tile, int t, int m, long long sb, int ncell, int c,
-                                     T inv_h2, T *diag) {
-  const T xm = tile[t - 1], xp = tile[t + 1], ym = tile[t - m], yp = tile[t + m];
-  if (sb < 0) {
-    T s = (xm + xp) + (ym + yp);
-    if (D == 3) s += tile[t - m * m] + tile[t + m * m];
-    *diag = T(-2 * D) * inv_h2;
-    return s * inv_h2;
-  }
-  const T *st = V.st + sb;
-  T s = st[1 * ncell + c] * xm + st[2 * ncell + c] * xp + st[3 * ncell + c] * ym + st[4 * ncell + c] * yp;
-  if (D == 3) s += st[5 * ncell + c] * tile[t - m * m] + st[6 * ncell + c] * tile[t + m * m];
-  *diag = st[c];
-  return s;
-}
-
-// r = b - A phi at cell c; the regular 5/7-point form costs 2D - 1 adds and
-// two fused multiply-adds (FP64 throughput is the bound on this path).
-template <typename T, int D>
-__device__ __forceinline__ T residual_at(const GmgView<T> &V, const T *tile, int t, int m, long long sb, int ncell,
-                                         int c, T inv_h2, T b) {
-  if (sb < 0) {
-    T s = (tile[t - 1] + tile[t + 1]) + (tile[t - m] + tile[t + m]);
-    if (D == 3) s += tile[t - m * m] + tile[t + m * m];
-    return b - inv_h2 * (s - T(2 * D) * tile[t]);
-  }
-  T diag;
-  const T s = offdiag<T, D>(V, tile, t, m, sb, ncell, c, inv_h2, &diag);
-  return b - (diag * tile[t] + s);
+// Shared memory of the level kernels: the ghosted tile and the dense b.
+template <typename T>
+__host__ __device__ inline size_t level_smem_bytes(int D, int n) {
+  const int m = n + 2;
+  return sizeof(T) * (size_t)((D == 3 ? m * m * m : m * m) + (D == 3 ? n * n * n : n * n));
 }
 
 template <int D>
@@ -283,66 +304,67 @@ __device__ __forceinline__ void cell_xyz(int c, int n, int *x, int *y, int *z) {
   *z = D == 3 ? c / (n * n) : 0;
 }
 
+// Stencil coefficients of a cut block are read from global memory, all
+// seven of a cell in one batch.
+template <typename T, int D>
+__device__ __forceinline__ T offdiag_st(const T *__restrict__ st, const T *tile, int t, int m, int ncell, int c,
+                                        T *diag) {
+  T cf[2 * D + 1];
+#pragma unroll
+  for (int k = 0; k < 2 * D + 1; k++) cf[k] = st[k * ncell + c];
+  T s = cf[1] * tile[t - 1] + cf[2] * tile[t + 1] + cf[3] * tile[t - m] + cf[4] * tile[t + m];
+  if (D == 3) s += cf[5] * tile[t - m * m] + cf[6] * tile[t + m * m];
+  *diag = cf[0];
+  return s;
+}
+
+// r = b - A phi at cell c (tile index t); the regular 5/7-point form costs
+// 2D - 1 adds and two fused multiply-adds (FP64 throughput bounds that path).
+template <typename T, int D>
+__device__ __forceinline__ T resid_cell(const T *__restrict__ st, long long sb, const T *tile, int t, int m, int ncell,
+                                        int c, T inv_h2, T b) {
+  if (sb < 0) {
+    T s = (tile[t - 1] + tile[t + 1]) + (tile[t - m] + tile[t + m]);
+    if (D == 3) s += tile[t - m * m] + tile[t + m * m];
+    return b - inv_h2 * (s - T(2 * D) * tile[t]);
+  }
+  T diag;
+  const T s = offdiag_st<T, D>(st + sb, tile, t, m, ncell, c, &diag);
+  return b - (diag * tile[t] + s);
+}
+
 // One red (color 0) or black (color 1) half-sweep of Gauss-Seidel on every
-// block of a level (Sec. 2.2, readings S and SW).
+// block of a level (Sec. 2.2, readings S and SW):
+// phi_i <- (b_i - sum_j c_ij phi_j) / c_ii on the cells of one colour.
 template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kThreads) k_smooth(GmgView<T> V, LvArgs L, LvArgs Lp, int color) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *tile = reinterpret_cast<T *>(smem_raw);
   const int bid = L.first + blockIdx.x;
   const int n = NT ? NT : L.n, m = n + 2, hn = n / 2;
+  T *tile = reinterpret_cast<T *>(smem_raw);
+  T *sbv = tile + (D == 3 ? m * m * m : m * m);
   const long long base = L.off + (long long)(bid - L.first) * NCELL;
-  const T h2 = T(L.h * L.h), inv_h2 = T(1.0 / (L.h * L.h)), inv2d = T(1.0 / (2 * D));
-  // cells of this colour handled by the thread; their b is loaded before
-  // the tile so that both loads are in flight together
-  constexpr int IC = NT ? ((D == 3 ? NT * NT * NT : NT * NT) / 2 + kThreads - 1) / kThreads : 1;
-  const int nhalf = NCELL / 2;
   const long long sb = V.st_base[bid];
-  // With a compile-time side every thread runs exactly one batch (IC cells
-  // per thread cover the colour) and issues its b loads before the tile is
-  // staged; with a runtime side the tile is staged first and the cells loop.
-  // Either way every thread reaches the barrier exactly once.
-  if (!NT) {
-    load_tile<T, D, NT>(V, L, Lp, bid, tile);
-    __syncthreads();
-  }
-  const int j_end = NT ? (int)blockDim.x : nhalf;
-  for (int j0 = threadIdx.x; j0 < j_end; j0 += IC * blockDim.x) {
-    T bv[IC];
-    int cc[IC], tt[IC];
-#pragma unroll
-    for (int k = 0; k < IC; k++) {
-      const int j = j0 + k * blockDim.x;
-      cc[k] = -1;
-      if (j < nhalf) {
-        const int rest = j / hn;
-        const int y = rest % n, z = D == 3 ? rest / n : 0;
-        const int x = 2 * (j % hn) + ((y + z + color) & 1);
-        cc[k] = x + n * (y + n * z);
-        tt[k] = (x + 1) + m * ((y + 1) + (D == 3 ? m * (z + 1) : 0));
-        bv[k] = V.b[base + cc[k]];
-      }
+  load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv);
+  const T h2 = T(L.h * L.h), inv2d = T(1.0 / (2 * D));
+  const int nhalf = NCELL / 2;
+  for (int j = threadIdx.x; j < nhalf; j += blockDim.x) {
+    const int rest = j / hn;
+    const int y = rest % n, z = D == 3 ? rest / n : 0;
+    const int x = 2 * (j % hn) + ((y + z + color) & 1);
+    const int c = x + n * (y + n * z);
+    const int t = (x + 1) + m * ((y + 1) + (D == 3 ? m * (z + 1) : 0));
+    T nv;
+    if (sb < 0) {
+      T s = (tile[t - 1] + tile[t + 1]) + (tile[t - m] + tile[t + m]);
+      if (D == 3) s += tile[t - m * m] + tile[t + m * m];
+      nv = (s - h2 * sbv[c]) * inv2d;
+    } else {
+      T diag;
+      const T s = offdiag_st<T, D>(V.st + sb, tile, t, m, NCELL, c, &diag);
+      nv = (sbv[c] - s) / diag;
     }
-    if (NT) {
-      load_tile<T, D, NT>(V, L, Lp, bid, tile);
-      __syncthreads();
-    }
-#pragma unroll
-    for (int k = 0; k < IC; k++) {
-      if (cc[k] < 0) continue;
-      const int t = tt[k], c = cc[k];
-      T nv;
-      if (sb < 0) {
-        T s = (tile[t - 1] + tile[t + 1]) + (tile[t - m] + tile[t + m]);
-        if (D == 3) s += tile[t - m * m] + tile[t + m * m];
-        nv = (s - h2 * bv[k]) * inv2d;
-      } else {
-        T diag;
-        const T s = offdiag<T, D>(V, tile, t, m, sb, NCELL, c, inv_h2, &diag);
-        nv = (bv[k] - s) / diag;
-      }
-      V.phi[base + c] = nv;
-    }
+    V.phi[base + c] = nv;
   }
 }
 
@@ -352,15 +374,14 @@ __global__ void __launch_bounds__(kThreads) k_smooth(GmgView<T> V, LvArgs L, LvA
 template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kThreads) k_resid_restrict(GmgView<T> V, LvArgs L, LvArgs Lp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *tile = reinterpret_cast<T *>(smem_raw);
   const int bid = L.first + blockIdx.x;
-  load_tile<T, D, NT>(V, L, Lp, bid, tile);
-  __syncthreads();
   const int n = NT ? NT : L.n, m = n + 2, hn = n / 2;
-  const long long base = L.off + (long long)(bid - L.first) * NCELL;
+  T *tile = reinterpret_cast<T *>(smem_raw);
+  T *sbv = tile + (D == 3 ? m * m * m : m * m);
   const long long sb = V.st_base[bid];
-  const T inv_h2 = T(1.0 / (L.h * L.h));
   const int P = V.parent[bid], po = V.pofs[bid];
+  load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv);
+  const T inv_h2 = T(1.0 / (L.h * L.h));
   const int pofs[3] = {po & 1023, (po >> 10) & 1023, (po >> 20) & 1023};
   const long long pbase = Lp.off + (long long)(P - Lp.first) * Lp.ncell;
   const int pn = Lp.n;
@@ -379,7 +400,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(GmgView<T> V, LvArg
           const int c = x + n * (y + n * z);
           const int t = (x + 1) + m * ((y + 1) + (D == 3 ? m * (z + 1) : 0));
           sp = sp + tile[t];
-          sr = sr + residual_at<T, D>(V, tile, t, m, sb, NCELL, c, inv_h2, V.b[base + c]);
+          sr = sr + resid_cell<T, D>(V.st, sb, tile, t, m, NCELL, c, inv_h2, sbv[c]);
         }
     const long long pc = pbase + (pofs[0] + qx) + pn * ((pofs[1] + qy) + (D == 3 ? pn * (pofs[2] + qz) : 0));
     V.phi[pc] = sp * w;
@@ -392,26 +413,39 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(GmgView<T> V, LvArg
 template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kThreads) k_fas(GmgView<T> V, LvArgs L, LvArgs Lp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *tile = reinterpret_cast<T *>(smem_raw);
   const int bid = L.first + blockIdx.x;
   const int n = NT ? NT : L.n, m = n + 2;
   const long long base = L.off + (long long)(bid - L.first) * NCELL;
   if (!(V.flags[bid] & kHasChildren)) {
-    for (int c = threadIdx.x; c < NCELL; c += blockDim.x) V.old[base + c] = V.phi[base + c];
+    constexpr int VEC = 16 / sizeof(T);
+    using VT = typename Vec16<T>::type;
+    const VT *src = reinterpret_cast<const VT *>(V.phi + base);
+    VT *dst = reinterpret_cast<VT *>(V.old + base);
+    for (int i = threadIdx.x; i < NCELL / VEC; i += blockDim.x) dst[i] = src[i];
     return;
   }
-  load_tile<T, D, NT>(V, L, Lp, bid, tile);
-  __syncthreads();
+  T *tile = reinterpret_cast<T *>(smem_raw);
+  T *sbv = tile + (D == 3 ? m * m * m : m * m);
   const long long sb = V.st_base[bid];
+  load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv);
   const T inv_h2 = T(1.0 / (L.h * L.h));
   for (int c = threadIdx.x; c < NCELL; c += blockDim.x) {
     int x, y, z;
     cell_xyz<D>(c, n, &x, &y, &z);
     const int t = (x + 1) + m * ((y + 1) + (D == 3 ? m * (z + 1) : 0));
-    T diag;
-    const T s = offdiag<T, D>(V, tile, t, m, sb, NCELL, c, inv_h2, &diag);
+    // A phi + rr = b_rr - (b_rr - A phi), written out directly
     const T ph = tile[t];
-    V.b[base + c] = (diag * ph + s) + V.b[base + c];
+    T ap;
+    if (sb < 0) {
+      T s = (tile[t - 1] + tile[t + 1]) + (tile[t - m] + tile[t + m]);
+      if (D == 3) s += tile[t - m * m] + tile[t + m * m];
+      ap = inv_h2 * (s - T(2 * D) * ph);
+    } else {
+      T diag;
+      const T s = offdiag_st<T, D>(V.st + sb, tile, t, m, NCELL, c, &diag);
+      ap = diag * ph + s;
+    }
+    V.b[base + c] = ap + sbv[c];
     V.old[base + c] = ph;
   }
 }
@@ -437,10 +471,28 @@ __global__ void __launch_bounds__(kThreads) k_coarse(const double *__restrict__ 
 template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kThreads) k_prolong(GmgView<T> V, LvArgs L, LvArgs Lp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_nb[kNbr];
   T *tile = reinterpret_cast<T *>(smem_raw);
   const int bid = L.first + blockIdx.x;
   const int n = NT ? NT : L.n, hn = n / 2, m = hn + 2;
+  // the parent's 27 same-level neighbours (precomputed per block), -2 outside
+  if (threadIdx.x < kNbr) s_nb[threadIdx.x] = V.pnb[(size_t)bid * kNbr + threadIdx.x];
   const int P = V.parent[bid], po = V.pofs[bid];
+  // the block's own phi, loaded while the coarse correction is staged
+  constexpr int VEC = 16 / sizeof(T);
+  using VT = typename Vec16<T>::type;
+  const long long base = L.off + (long long)(bid - L.first) * NCELL;
+  VT *__restrict__ fine = reinterpret_cast<VT *>(V.phi + base);
+  constexpr int IV = NT ? ((D == 3 ? NT * NT * NT : NT * NT) / VEC + kThreads - 1) / kThreads : 1;
+  VT rv[IV];
+  if (NT) {
+#pragma unroll
+    for (int k = 0; k < IV; k++) {
+      const int i = threadIdx.x + k * kThreads;
+      if (i < NCELL / VEC) rv[k] = fine[i];
+    }
+  }
+  __syncthreads();
   const int pofs[3] = {po & 1023, (po >> 10) & 1023, (po >> 20) & 1023};
   const int tsize = D == 3 ? m * m * m : m * m;
   for (int t = threadIdx.x; t < tsize; t += blockDim.x) {
@@ -448,14 +500,13 @@ __global__ void __launch_bounds__(kThreads) k_prolong(GmgView<T> V, LvArgs L, Lv
     long long ix;
     float sg;
     T v = T(NAN);
-    if (resolve<D>(V.nbr, V.flags, V.wsign, Lp, P, q, &ix, &sg)) v = T(sg) * (V.phi[ix] - V.old[ix]);
+    if (resolve_s<D>(s_nb, P, Lp, V.wsign, q, &ix, &sg)) v = T(sg) * (V.phi[ix] - V.old[ix]);
     tile[t] = v;
   }
   __syncthreads();
-  const long long base = L.off + (long long)(bid - L.first) * NCELL;
-  for (int c = threadIdx.x; c < NCELL; c += blockDim.x) {
-    int x, y, z;
-    cell_xyz<D>(c, n, &x, &y, &z);
+  // fine cell (x,y,z): parent cell u = (x/2,...) + 1 in tile coordinates,
+  // the interpolation partner on the side of the fine cell's centre
+  auto interp = [&](int x, int y, int z) {
     const int u[3] = {(x >> 1) + 1, (y >> 1) + 1, (z >> 1) + 1};
     const int o[3] = {(x & 1) ? 1 : -1, (y & 1) ? 1 : -1, (z & 1) ? 1 : -1};
     T v = T(0);
@@ -470,7 +521,28 @@ __global__ void __launch_bounds__(kThreads) k_prolong(GmgView<T> V, LvArgs L, Lv
           const int tx = u[0] + sx * o[0], ty = u[1] + sy * o[1], tz = D == 3 ? u[2] + sz * o[2] : 0;
           v = v + wgt * tile[tx + m * (ty + (D == 3 ? m * tz : 0))];
         }
-    V.phi[base + c] += v;
+    return v;
+  };
+  if (NT) {
+#pragma unroll
+    for (int k = 0; k < IV; k++) {
+      const int i = threadIdx.x + k * kThreads;
+      if (i < NCELL / VEC) {
+        T *e = reinterpret_cast<T *>(&rv[k]);
+        const int c = i * VEC;
+        int x, y, z;
+        cell_xyz<D>(c, n, &x, &y, &z);
+#pragma unroll
+        for (int q = 0; q < VEC; q++) e[q] += interp(x + q, y, z);
+        fine[i] = rv[k];
+      }
+    }
+  } else {
+    for (int c = threadIdx.x; c < NCELL; c += blockDim.x) {
+      int x, y, z;
+      cell_xyz<D>(c, n, &x, &y, &z);
+      V.phi[base + c] += interp(x, y, z);
+    }
   }
 }
 
@@ -532,17 +604,17 @@ template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kThreads) k_resnorm(GmgView<T> V, LvArgs L, LvArgs Lp, double *partials,
                                                       float *rout) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *tile = reinterpret_cast<T *>(smem_raw);
   const int bid = L.first + blockIdx.x;
   if (V.flags[bid] & kHasChildren) {
     if (threadIdx.x < 3) partials[(size_t)bid * 3 + threadIdx.x] = 0.0;
     return;
   }
-  load_tile<T, D, NT>(V, L, Lp, bid, tile);
-  __syncthreads();
   const int n = NT ? NT : L.n, m = n + 2;
+  T *tile = reinterpret_cast<T *>(smem_raw);
+  T *sbv = tile + (D == 3 ? m * m * m : m * m);
   const long long base = L.off + (long long)(bid - L.first) * NCELL;
   const long long sb = V.st_base[bid];
+  load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv);
   const T inv_h2 = T(1.0 / (L.h * L.h));
   // the norms only steer the stopping test: squares and maxima of the
   // rounded residual are accumulated in FP32 per thread, then in FP64
@@ -551,16 +623,15 @@ __global__ void __launch_bounds__(kThreads) k_resnorm(GmgView<T> V, LvArgs L, Lv
     int x, y, z;
     cell_xyz<D>(c, n, &x, &y, &z);
     const int t = (x + 1) + m * ((y + 1) + (D == 3 ? m * (z + 1) : 0));
-    const T bb = V.b[base + c];
-    const float r = (float)residual_at<T, D>(V, tile, t, m, sb, NCELL, c, inv_h2, bb);
+    const T bb = sbv[c];
+    const float r = (float)resid_cell<T, D>(V.st, sb, tile, t, m, NCELL, c, inv_h2, bb);
     if (rout) rout[base + c] = r;
     s2f = fmaf(r, r, s2f);
     mxf = fmaxf(mxf, fabsf(r));
     const float bf = (float)bb;
     b2f = fmaf(bf, bf, b2f);
   }
-  const double s2 = s2f, mx = mxf, b2 = b2f;
-  block_reduce3(s2, mx, b2, partials + (size_t)bid * 3);
+  block_reduce3((double)s2f, (double)mxf, (double)b2f, partials + (size_t)bid * 3);
 }
 
 // Deterministic final reduction of the per-block partials (fixed order).

@@ -77,6 +77,7 @@ template <int D, int NT>
 void launch_resnorm(gmg_tree *t, int l, double *partials, cudaStream_t s) {
   gmg::GmgView<double> V;
   V.nbr = t->d_nbr;
+  V.pnb = t->d_pnb;
   V.parent = t->d_parent;
   V.pofs = t->d_pofs;
   V.flags = t->d_flags;
@@ -95,9 +96,10 @@ void launch_resnorm(gmg_tree *t, int l, double *partials, cudaStream_t s) {
     const gmg::LevelInfo &Pi = t->lev(l - 1);
     Lp = gmg::LvArgs{Pi.first, Pi.count, Pi.n, Pi.ncell, Pi.off, Pi.h};
   }
-  const int m = Li.n + 2;
-  const size_t sm = sizeof(double) * (size_t)(D == 3 ? m * m * m : m * m);
+  const size_t sm = gmg::level_smem_bytes<double>(D, Li.n);
   cudaFuncSetAttribute(gmg::k_resnorm<double, D, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(gmg::k_resnorm<double, D, NT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       (int)cudaSharedmemCarveoutMaxShared);
   gmg::k_resnorm<double, D, NT><<<L.count, gmg::kThreads, sm, s>>>(V, L, Lp, partials, nullptr);
 }
 
@@ -138,6 +140,8 @@ extern "C" int gmg_residual_noalloc(gmg_tree *t, double *out, void *stream) {
     else
       launch_resnorm_any<2>(t, l, scratch, s);
   }
+  cudaFuncSetAttribute(k_reduce_noalloc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       (int)cudaSharedmemCarveoutMaxShared);
   k_reduce_noalloc<<<1, 1024, 0, s>>>((int)nb, out);
   e = cudaGetLastError();
   if (e != cudaSuccess) return gmg::set_error(std::string("kernel launch: ") + cudaGetErrorString(e)), GMG_ERR_CUDA;
