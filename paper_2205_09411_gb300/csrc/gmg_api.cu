@@ -172,7 +172,8 @@ GmgView<double> view<double>(gmg_tree *t) {
   v.b = t->d_b;
   v.old = t->d_old;
   v.st = t->d_st;
-  for (int w = 0; w < 6; w++) v.wsign[w] = t->wall_type[w] == GMG_WALL_DIRICHLET ? -1.f : 1.f;
+  v.wneu = 0;
+  for (int w = 0; w < 6; w++) v.wneu |= (t->wall_type[w] == GMG_WALL_NEUMANN ? 1 : 0) << w;
   return v;
 }
 
@@ -191,7 +192,8 @@ GmgView<float> view<float>(gmg_tree *t) {
   v.b = t->f_b;
   v.old = t->f_old;
   v.st = t->f_st;
-  for (int w = 0; w < 6; w++) v.wsign[w] = t->wall_type[w] == GMG_WALL_DIRICHLET ? -1.f : 1.f;
+  v.wneu = 0;
+  for (int w = 0; w < 6; w++) v.wneu |= (t->wall_type[w] == GMG_WALL_NEUMANN ? 1 : 0) << w;
   return v;
 }
 
@@ -201,7 +203,7 @@ using IC = std::integral_constant<int, V>;
 // Calls f(IC<NT>) with NT the compile-time block side for n (0 = runtime).
 template <int D, typename F>
 void with_nt(int n, F &&f) {
-  if (D == 3) {
+  if constexpr (D == 3) {
     switch (n) {
       case 4: f(IC<4>{}); return;
       case 8: f(IC<8>{}); return;

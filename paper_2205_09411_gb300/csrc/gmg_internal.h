@@ -58,7 +58,7 @@ struct GmgView {
   const int *leaf_ids;   // [n_leaf_blocks]
   T *phi, *b, *old;      // level fields (all levels, block-contiguous)
   const T *st;           // stencil pool: per cut block (2D+1) x ncell, [diag, -x, +x, -y, +y, -z, +z]
-  float wsign[6];        // homogeneous wall ghost sign: -1 Dirichlet, +1 Neumann
+  int wneu;              // bit w set: wall w is Neumann (ghost +phi), else Dirichlet (-phi)
 };
 
 struct gmg_tree_impl;

@@ -23,7 +23,7 @@ __device__ __forceinline__ int nbr_slot(int ox, int oy, int oz) { return (oz + 1
 // other axes leaving the block go to the same-level neighbour.  Returns
 // false when that neighbour does not exist on this level.
 template <int D>
-__device__ __forceinline__ bool resolve(const int *__restrict__ nbr, const int *__restrict__ flags, const float *wsign,
+__device__ __forceinline__ bool resolve(const int *__restrict__ nbr, const int *__restrict__ flags, int wneu,
                                         const LvArgs &L, int bid, const int *pin, long long *idx, float *sign) {
   const int n = L.n;
   int p[3] = {pin[0], pin[1], pin[2]}, o[3] = {0, 0, 0};
@@ -34,7 +34,7 @@ __device__ __forceinline__ bool resolve(const int *__restrict__ nbr, const int *
     if (p[d] < 0) {
       if (fl & wall_bit(d, 0)) {
         p[d] = -1 - p[d];
-        sg *= wsign[2 * d];
+        sg *= ((wneu >> (2 * d)) & 1) ? 1.f : -1.f;
       } else {
         o[d] = -1;
         p[d] += n;
@@ -42,7 +42,7 @@ __device__ __forceinline__ bool resolve(const int *__restrict__ nbr, const int *
     } else if (p[d] >= n) {
       if (fl & wall_bit(d, 1)) {
         p[d] = 2 * n - 1 - p[d];
-        sg *= wsign[2 * d + 1];
+        sg *= ((wneu >> (2 * d + 1)) & 1) ? 1.f : -1.f;
       } else {
         o[d] = 1;
         p[d] -= n;
@@ -62,7 +62,7 @@ __device__ __forceinline__ bool resolve(const int *__restrict__ nbr, const int *
 // resolve() with the block's 27 same-level neighbours already in shared
 // memory (-2 marks a neighbour position outside the domain).
 template <int D>
-__device__ __forceinline__ bool resolve_s(const int *s_nb, int bid, const LvArgs &L, const float *wsign,
+__device__ __forceinline__ bool resolve_s(const int *s_nb, int bid, const LvArgs &L, int wneu,
                                           const int *pin, long long *idx, float *sign) {
   const int n = L.n;
   int p[3] = {pin[0], pin[1], pin[2]}, o[3] = {0, 0, 0};
@@ -74,7 +74,7 @@ __device__ __forceinline__ bool resolve_s(const int *s_nb, int bid, const LvArgs
     if (p[d] < 0) {
       if (s_nb[lo] == -2) {
         p[d] = -1 - p[d];
-        sg *= wsign[2 * d];
+        sg *= ((wneu >> (2 * d)) & 1) ? 1.f : -1.f;
       } else {
         o[d] = -1;
         p[d] += n;
@@ -82,7 +82,7 @@ __device__ __forceinline__ bool resolve_s(const int *s_nb, int bid, const LvArgs
     } else if (p[d] >= n) {
       if (s_nb[hi] == -2) {
         p[d] = 2 * n - 1 - p[d];
-        sg *= wsign[2 * d + 1];
+        sg *= ((wneu >> (2 * d + 1)) & 1) ? 1.f : -1.f;
       } else {
         o[d] = 1;
         p[d] -= n;
@@ -100,7 +100,8 @@ __device__ __forceinline__ bool resolve_s(const int *s_nb, int bid, const LvArgs
 // adjacent fine cell and c_hat the coarse cell containing the ghost centre
 // shifted by central tangential slopes (+-1/4 coarse cell).
 template <typename T, int D>
-__device__ T refine_ghost(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, const int *p, int a) {
+__device__ __noinline__ T refine_ghost(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, const int *p,
+                                       int a) {
   const int n = L.n;
   int q[3] = {p[0], p[1], p[2]};
   q[a] = p[a] < 0 ? 0 : n - 1;
@@ -112,7 +113,7 @@ __device__ T refine_ghost(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
   for (int d = 0; d < D; d++) cq[d] = pofs[d] + (p[d] >> 1);
   long long ix;
   float sg;
-  if (!resolve<D>(V.nbr, V.flags, V.wsign, Lp, P, cq, &ix, &sg)) return T(NAN);
+  if (!resolve<D>(V.nbr, V.flags, V.wneu, Lp, P, cq, &ix, &sg)) return T(NAN);
   const T c = V.phi[ix];
   T chat = c;
 #pragma unroll
@@ -124,8 +125,8 @@ __device__ T refine_ghost(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
     qm[t] -= 1;
     long long ip, im;
     float sp, sm;
-    if (!resolve<D>(V.nbr, V.flags, V.wsign, Lp, P, qp, &ip, &sp)) return T(NAN);
-    if (!resolve<D>(V.nbr, V.flags, V.wsign, Lp, P, qm, &im, &sm)) return T(NAN);
+    if (!resolve<D>(V.nbr, V.flags, V.wneu, Lp, P, qp, &ip, &sp)) return T(NAN);
+    if (!resolve<D>(V.nbr, V.flags, V.wneu, Lp, P, qm, &im, &sm)) return T(NAN);
     const T cp = T(sp) * V.phi[ip], cm = T(sm) * V.phi[im];
     chat = chat + o * (T(0.5) * (cp - cm));
   }
@@ -143,41 +144,63 @@ struct Vec16<double> {
   using type = double2;
 };
 
-// Source of one ghost-face value: a cell of a same-level neighbour (or of
-// the block itself, reflected at a wall) and its sign; false when the
-// neighbour is missing (refinement boundary, reading G).
-template <int D>
-__device__ __forceinline__ bool face_source(const int *s_nb, int fl, const float *wsign, const LvArgs &L, int n,
-                                            int bid, const int *p, int a, int side, long long *idx, float *sg) {
-  const int ncell = D == 3 ? n * n * n : n * n;
-  int q[3] = {p[0], p[1], p[2]};
-  int id = s_nb[2 * a + side];
-  *sg = 1.f;
-  if (fl & wall_bit(a, side)) {
-    q[a] = side ? n - 1 : 0;
-    *sg = wsign[2 * a + side];
-    id = bid;
-  } else {
-    if (id < 0) return false;
-    q[a] = side ? 0 : n - 1;
-  }
-  *idx = L.off + (long long)(id - L.first) * ncell + q[0] + n * (q[1] + (D == 3 ? n * q[2] : 0));
-  return true;
+// Asynchronous global -> shared copies (cp.async): they take no registers,
+// so a CTA can keep all of its block's loads in flight at once.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *smem, const T *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
-// Stage phi of block `bid` with its face ghosts into tile[(n+2)^D] and, if
-// sbv != nullptr, the block's b into the dense array sbv[n^D].  The face
-// neighbours' ids and the block flags are read once per CTA; every thread
-// issues all its global loads (16-byte vectors for the block's cells,
-// scalars for the 2D ghost faces) before any shared-memory store, so that
-// the whole stage costs two dependent memory round trips.  Ends with a
-// barrier.  NT is the block side when known at compile time (0: runtime).
+// Tile of one block in shared memory: its cells plus one ghost layer.  Rows
+// along x are [.. ghost x=-1 | x = 0..n-1 | ghost x=n ..] with the first cell
+// at X0 = 16 / sizeof(T), so every row of cells starts on a 16-byte boundary
+// (16-byte cp.async); rows are R = n + 2 X0 long, y and z carry one ghost.
+template <typename T, int D>
+struct TileGeo {
+  int n, X0, R, sy, sz, size;
+  __host__ __device__ explicit TileGeo(int n_)
+      : n(n_),
+        X0(16 / (int)sizeof(T)),
+        R(n_ + 2 * (16 / (int)sizeof(T))),
+        sy(n_ + 2 * (16 / (int)sizeof(T))),
+        sz((n_ + 2 * (16 / (int)sizeof(T))) * (n_ + 2)),
+        size(D == 3 ? (n_ + 2 * (16 / (int)sizeof(T))) * (n_ + 2) * (n_ + 2)
+                    : (n_ + 2 * (16 / (int)sizeof(T))) * (n_ + 2)) {}
+  __host__ __device__ int idx(int x, int y, int z) const { return (x + X0) + sy * (y + 1) + (D == 3 ? sz * (z + 1) : 0); }
+};
+
+// Shared memory of the level kernels: the tile and the block's dense b.
+template <typename T>
+__host__ __device__ inline size_t level_smem_bytes(int D, int n) {
+  const int tile = D == 3 ? TileGeo<T, 3>(n).size : TileGeo<T, 2>(n).size;
+  return sizeof(T) * (size_t)(tile + (D == 3 ? n * n * n : n * n));
+}
+
+// Stage phi of block `bid` with its face ghosts into the tile and, if
+// sbv != nullptr, the block's b into the dense array sbv[n^D].  The cells and
+// b are copied with 16-byte cp.async while the face neighbours' ids are read;
+// the neighbours' faces follow as element cp.async; wall ghosts (reflection
+// of the adjacent cell, homogeneous sign) and refinement-boundary ghosts
+// (reading G) are filled once the copies have landed.  Ends with a barrier.
 template <typename T, int D, int NT>
 __device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, T *tile,
                           T *sbv = nullptr) {
   __shared__ int s_nb[6];
   __shared__ int s_fl;
-  const int n = NT ? NT : L.n, m = n + 2;
+  const int n = NT ? NT : L.n;
+  const TileGeo<T, D> G(n);
   const int ncell = D == 3 ? n * n * n : n * n;
   if (threadIdx.x < 2 * D) {
     const int a = threadIdx.x >> 1, side = threadIdx.x & 1;
@@ -187,114 +210,90 @@ __device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
   if (threadIdx.x == 0) s_fl = V.flags[bid];
   const long long base = L.off + (long long)(bid - L.first) * ncell;
   constexpr int VEC = 16 / sizeof(T);
-  using VT = typename Vec16<T>::type;
-  const VT *__restrict__ src = reinterpret_cast<const VT *>(V.phi + base);
-  const VT *__restrict__ srcb = reinterpret_cast<const VT *>(V.b + base);
-  const int nvec = ncell / VEC;
-  const int nf = D == 3 ? n * n : n;
-  if (NT) {
-    constexpr int NC = NT ? (D == 3 ? NT * NT * NT : NT * NT) : 1;
-    constexpr int NF = NT ? (D == 3 ? NT * NT : NT) : 1;
-    constexpr int IV = NC / VEC >= 1 ? (NC / VEC + kThreads - 1) / kThreads : 1;
-    constexpr int IF = (2 * D * NF + kThreads - 1) / kThreads;
-    VT rv[IV], rb[IV];
-#pragma unroll
-    for (int k = 0; k < IV; k++) {
-      const int i = threadIdx.x + k * kThreads;
-      if (i < nvec) {
-        rv[k] = src[i];
-        if (sbv) rb[k] = srcb[i];
-      }
-    }
-    __syncthreads();
-    const int fl = s_fl;
-    T rf[IF];
-    int tf[IF];
-#pragma unroll
-    for (int k = 0; k < IF; k++) {
-      const int i = threadIdx.x + k * kThreads;
-      tf[k] = -1;
-      if (i < 2 * D * nf) {
-        const int f = i / nf, j = i - f * nf;
-        const int a = f >> 1, side = f & 1;
-        int p[3] = {0, 0, 0};
-        if (D == 3) {
-          p[a == 0 ? 1 : 0] = j % n;
-          p[a == 2 ? 1 : 2] = j / n;
-        } else {
-          p[1 - a] = j;
-        }
-        long long ix;
-        float sg;
-        if (face_source<D>(s_nb, fl, V.wsign, L, n, bid, p, a, side, &ix, &sg)) {
-          rf[k] = T(sg) * V.phi[ix];
-        } else {
-          p[a] = side ? n : -1;
-          rf[k] = refine_ghost<T, D>(V, L, Lp, bid, p, a);
-        }
-        p[a] = side ? n : -1;
-        tf[k] = (p[0] + 1) + m * ((p[1] + 1) + (D == 3 ? m * (p[2] + 1) : 0));
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < IV; k++) {
-      const int i = threadIdx.x + k * kThreads;
-      if (i < nvec) {
-        const int c = i * VEC;
-        const int x = c % n, y = (c / n) % n, z = D == 3 ? c / (n * n) : 0;
-        T *dst = tile + (x + 1) + m * ((y + 1) + (D == 3 ? m * (z + 1) : 0));
-        const T *e = reinterpret_cast<const T *>(&rv[k]);
-#pragma unroll
-        for (int q = 0; q < VEC; q++) dst[q] = e[q];
-        if (sbv) reinterpret_cast<VT *>(sbv)[i] = rb[k];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < IF; k++)
-      if (tf[k] >= 0) tile[tf[k]] = rf[k];
-  } else {
-    for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
-      const VT v = src[i];
+  if (n % VEC == 0) {  // 16-byte chunks never cross a row of the tile
+    for (int i = threadIdx.x; i < ncell / VEC; i += blockDim.x) {
       const int c = i * VEC;
       const int x = c % n, y = (c / n) % n, z = D == 3 ? c / (n * n) : 0;
-      T *dst = tile + (x + 1) + m * ((y + 1) + (D == 3 ? m * (z + 1) : 0));
-      const T *e = reinterpret_cast<const T *>(&v);
-      for (int q = 0; q < VEC; q++) dst[q] = e[q];
-      if (sbv) reinterpret_cast<VT *>(sbv)[i] = srcb[i];
+      cp_async16(tile + G.idx(x, y, z), V.phi + base + c);
+      if (sbv) cp_async16(sbv + c, V.b + base + c);
     }
-    __syncthreads();
-    const int fl = s_fl;
-    for (int i = threadIdx.x; i < 2 * D * nf; i += blockDim.x) {
-      const int f = i / nf, j = i - f * nf;
-      const int a = f >> 1, side = f & 1;
-      int p[3] = {0, 0, 0};
-      if (D == 3) {
-        p[a == 0 ? 1 : 0] = j % n;
-        p[a == 2 ? 1 : 2] = j / n;
-      } else {
-        p[1 - a] = j;
-      }
-      long long ix;
-      float sg;
-      T v;
-      if (face_source<D>(s_nb, fl, V.wsign, L, n, bid, p, a, side, &ix, &sg)) {
-        v = T(sg) * V.phi[ix];
-      } else {
-        p[a] = side ? n : -1;
-        v = refine_ghost<T, D>(V, L, Lp, bid, p, a);
-      }
-      p[a] = side ? n : -1;
-      tile[(p[0] + 1) + m * ((p[1] + 1) + (D == 3 ? m * (p[2] + 1) : 0))] = v;
+  } else {  // blocks narrower than one vector (coarse sub-levels)
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+      const int x = c % n, y = (c / n) % n, z = D == 3 ? c / (n * n) : 0;
+      cp_async_elem(tile + G.idx(x, y, z), V.phi + base + c);
+      if (sbv) cp_async_elem(sbv + c, V.b + base + c);
     }
+  }
+  __syncthreads();
+  const int fl = s_fl;
+  const int nf = D == 3 ? n * n : n;
+  // face i: axis a, side; ghost cell (gx,gy,gz); source cell in the
+  // neighbour (sx,sy_,sz_) or, at a wall, the reflected cell of this block
+  for (int i = threadIdx.x; i < 2 * D * nf; i += blockDim.x) {
+    const int f = i / nf, j = i - f * nf;
+    const int a = f >> 1, side = f & 1;
+    const int id = s_nb[f];
+    if ((fl & wall_bit(a, side)) || id < 0) continue;
+    const int u = j % n, v = D == 3 ? j / n : 0;
+    const int gn = side ? n : -1, sn = side ? 0 : n - 1;
+    const int gx = a == 0 ? gn : u, gy = a == 1 ? gn : (a == 0 ? u : v), gz = a == 2 ? gn : v;
+    const int qx = a == 0 ? sn : u, qy = a == 1 ? sn : (a == 0 ? u : v), qz = a == 2 ? sn : v;
+    cp_async_elem(tile + G.idx(gx, gy, gz),
+                  V.phi + L.off + (long long)(id - L.first) * ncell + qx + n * (qy + (D == 3 ? n * qz : 0)));
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * D * nf; i += blockDim.x) {
+    const int f = i / nf, j = i - f * nf;
+    const int a = f >> 1, side = f & 1;
+    const bool wall = (fl & wall_bit(a, side)) != 0;
+    if (!wall && s_nb[f] >= 0) continue;
+    const int u = j % n, v = D == 3 ? j / n : 0;
+    const int gn = side ? n : -1, mn = side ? n - 1 : 0;
+    const int gx = a == 0 ? gn : u, gy = a == 1 ? gn : (a == 0 ? u : v), gz = a == 2 ? gn : v;
+    T val;
+    if (wall) {
+      const int mx = a == 0 ? mn : u, my = a == 1 ? mn : (a == 0 ? u : v), mz = a == 2 ? mn : v;
+      val = (((V.wneu >> f) & 1) ? T(1) : T(-1)) * tile[G.idx(mx, my, mz)];
+    } else {
+      const int g[3] = {gx, gy, gz};
+      val = refine_ghost<T, D>(V, L, Lp, bid, g, a);
+    }
+    tile[G.idx(gx, gy, gz)] = val;
   }
   __syncthreads();
 }
 
-// Shared memory of the level kernels: the ghosted tile and the dense b.
-template <typename T>
-__host__ __device__ inline size_t level_smem_bytes(int D, int n) {
-  const int m = n + 2;
-  return sizeof(T) * (size_t)((D == 3 ? m * m * m : m * m) + (D == 3 ? n * n * n : n * n));
+template <typename T, int D>
+__device__ __forceinline__ T nb_sum(const T *tile, int t, int sy, int sz) {
+  T s = (tile[t - 1] + tile[t + 1]) + (tile[t - sy] + tile[t + sy]);
+  if (D == 3) s += tile[t - sz] + tile[t + sz];
+  return s;
+}
+
+// Off-diagonal sum and diagonal from a cut block's stored stencil (read
+// from global memory, the 2D + 1 coefficients of a cell in one batch).
+template <typename T, int D>
+__device__ __forceinline__ T offdiag_st(const T *__restrict__ st, const T *tile, int t, int sy, int sz, int ncell,
+                                        int c, T *diag) {
+  T cf[2 * D + 1];
+#pragma unroll
+  for (int k = 0; k < 2 * D + 1; k++) cf[k] = st[k * ncell + c];
+  T s = cf[1] * tile[t - 1] + cf[2] * tile[t + 1] + cf[3] * tile[t - sy] + cf[4] * tile[t + sy];
+  if (D == 3) s += cf[5] * tile[t - sz] + cf[6] * tile[t + sz];
+  *diag = cf[0];
+  return s;
+}
+
+// r = b - A phi at cell c (tile index t); the regular 5/7-point form costs
+// 2D - 1 adds and two fused multiply-adds (FP64 throughput bounds that path).
+template <typename T, int D>
+__device__ __forceinline__ T resid_cell(const T *__restrict__ st, long long sb, const T *tile, int t, int sy, int sz,
+                                        int ncell, int c, T inv_h2, T b) {
+  if (sb < 0) return b - inv_h2 * (nb_sum<T, D>(tile, t, sy, sz) - T(2 * D) * tile[t]);
+  T diag;
+  const T s = offdiag_st<T, D>(st + sb, tile, t, sy, sz, ncell, c, &diag);
+  return b - (diag * tile[t] + s);
 }
 
 template <int D>
@@ -304,35 +303,6 @@ __device__ __forceinline__ void cell_xyz(int c, int n, int *x, int *y, int *z) {
   *z = D == 3 ? c / (n * n) : 0;
 }
 
-// Stencil coefficients of a cut block are read from global memory, all
-// seven of a cell in one batch.
-template <typename T, int D>
-__device__ __forceinline__ T offdiag_st(const T *__restrict__ st, const T *tile, int t, int m, int ncell, int c,
-                                        T *diag) {
-  T cf[2 * D + 1];
-#pragma unroll
-  for (int k = 0; k < 2 * D + 1; k++) cf[k] = st[k * ncell + c];
-  T s = cf[1] * tile[t - 1] + cf[2] * tile[t + 1] + cf[3] * tile[t - m] + cf[4] * tile[t + m];
-  if (D == 3) s += cf[5] * tile[t - m * m] + cf[6] * tile[t + m * m];
-  *diag = cf[0];
-  return s;
-}
-
-// r = b - A phi at cell c (tile index t); the regular 5/7-point form costs
-// 2D - 1 adds and two fused multiply-adds (FP64 throughput bounds that path).
-template <typename T, int D>
-__device__ __forceinline__ T resid_cell(const T *__restrict__ st, long long sb, const T *tile, int t, int m, int ncell,
-                                        int c, T inv_h2, T b) {
-  if (sb < 0) {
-    T s = (tile[t - 1] + tile[t + 1]) + (tile[t - m] + tile[t + m]);
-    if (D == 3) s += tile[t - m * m] + tile[t + m * m];
-    return b - inv_h2 * (s - T(2 * D) * tile[t]);
-  }
-  T diag;
-  const T s = offdiag_st<T, D>(st + sb, tile, t, m, ncell, c, &diag);
-  return b - (diag * tile[t] + s);
-}
-
 // One red (color 0) or black (color 1) half-sweep of Gauss-Seidel on every
 // block of a level (Sec. 2.2, readings S and SW):
 // phi_i <- (b_i - sum_j c_ij phi_j) / c_ii on the cells of one colour.
@@ -340,9 +310,10 @@ template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kThreads) k_smooth(GmgView<T> V, LvArgs L, LvArgs Lp, int color) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int bid = L.first + blockIdx.x;
-  const int n = NT ? NT : L.n, m = n + 2, hn = n / 2;
+  const int n = NT ? NT : L.n, hn = n / 2;
+  const TileGeo<T, D> G(n);
   T *tile = reinterpret_cast<T *>(smem_raw);
-  T *sbv = tile + (D == 3 ? m * m * m : m * m);
+  T *sbv = tile + G.size;
   const long long base = L.off + (long long)(bid - L.first) * NCELL;
   const long long sb = V.st_base[bid];
   load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv);
@@ -353,15 +324,13 @@ __global__ void __launch_bounds__(kThreads) k_smooth(GmgView<T> V, LvArgs L, LvA
     const int y = rest % n, z = D == 3 ? rest / n : 0;
     const int x = 2 * (j % hn) + ((y + z + color) & 1);
     const int c = x + n * (y + n * z);
-    const int t = (x + 1) + m * ((y + 1) + (D == 3 ? m * (z + 1) : 0));
+    const int t = G.idx(x, y, z);
     T nv;
     if (sb < 0) {
-      T s = (tile[t - 1] + tile[t + 1]) + (tile[t - m] + tile[t + m]);
-      if (D == 3) s += tile[t - m * m] + tile[t + m * m];
-      nv = (s - h2 * sbv[c]) * inv2d;
+      nv = (nb_sum<T, D>(tile, t, G.sy, G.sz) - h2 * sbv[c]) * inv2d;
     } else {
       T diag;
-      const T s = offdiag_st<T, D>(V.st + sb, tile, t, m, NCELL, c, &diag);
+      const T s = offdiag_st<T, D>(V.st + sb, tile, t, G.sy, G.sz, NCELL, c, &diag);
       nv = (sbv[c] - s) / diag;
     }
     V.phi[base + c] = nv;
@@ -375,9 +344,10 @@ template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kThreads) k_resid_restrict(GmgView<T> V, LvArgs L, LvArgs Lp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int bid = L.first + blockIdx.x;
-  const int n = NT ? NT : L.n, m = n + 2, hn = n / 2;
+  const int n = NT ? NT : L.n, hn = n / 2;
+  const TileGeo<T, D> G(n);
   T *tile = reinterpret_cast<T *>(smem_raw);
-  T *sbv = tile + (D == 3 ? m * m * m : m * m);
+  T *sbv = tile + G.size;
   const long long sb = V.st_base[bid];
   const int P = V.parent[bid], po = V.pofs[bid];
   load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv);
@@ -398,9 +368,9 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(GmgView<T> V, LvArg
         for (int dx = 0; dx < 2; dx++) {
           const int x = 2 * qx + dx, y = 2 * qy + dy, z = 2 * qz + dz;
           const int c = x + n * (y + n * z);
-          const int t = (x + 1) + m * ((y + 1) + (D == 3 ? m * (z + 1) : 0));
+          const int t = G.idx(x, y, z);
           sp = sp + tile[t];
-          sr = sr + resid_cell<T, D>(V.st, sb, tile, t, m, NCELL, c, inv_h2, sbv[c]);
+          sr = sr + resid_cell<T, D>(V.st, sb, tile, t, G.sy, G.sz, NCELL, c, inv_h2, sbv[c]);
         }
     const long long pc = pbase + (pofs[0] + qx) + pn * ((pofs[1] + qy) + (D == 3 ? pn * (pofs[2] + qz) : 0));
     V.phi[pc] = sp * w;
@@ -414,7 +384,8 @@ template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kThreads) k_fas(GmgView<T> V, LvArgs L, LvArgs Lp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int bid = L.first + blockIdx.x;
-  const int n = NT ? NT : L.n, m = n + 2;
+  const int n = NT ? NT : L.n;
+  const TileGeo<T, D> G(n);
   const long long base = L.off + (long long)(bid - L.first) * NCELL;
   if (!(V.flags[bid] & kHasChildren)) {
     constexpr int VEC = 16 / sizeof(T);
@@ -425,24 +396,21 @@ __global__ void __launch_bounds__(kThreads) k_fas(GmgView<T> V, LvArgs L, LvArgs
     return;
   }
   T *tile = reinterpret_cast<T *>(smem_raw);
-  T *sbv = tile + (D == 3 ? m * m * m : m * m);
+  T *sbv = tile + G.size;
   const long long sb = V.st_base[bid];
   load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv);
   const T inv_h2 = T(1.0 / (L.h * L.h));
   for (int c = threadIdx.x; c < NCELL; c += blockDim.x) {
     int x, y, z;
     cell_xyz<D>(c, n, &x, &y, &z);
-    const int t = (x + 1) + m * ((y + 1) + (D == 3 ? m * (z + 1) : 0));
-    // A phi + rr = b_rr - (b_rr - A phi), written out directly
+    const int t = G.idx(x, y, z);
     const T ph = tile[t];
     T ap;
     if (sb < 0) {
-      T s = (tile[t - 1] + tile[t + 1]) + (tile[t - m] + tile[t + m]);
-      if (D == 3) s += tile[t - m * m] + tile[t + m * m];
-      ap = inv_h2 * (s - T(2 * D) * ph);
+      ap = inv_h2 * (nb_sum<T, D>(tile, t, G.sy, G.sz) - T(2 * D) * ph);
     } else {
       T diag;
-      const T s = offdiag_st<T, D>(V.st + sb, tile, t, m, NCELL, c, &diag);
+      const T s = offdiag_st<T, D>(V.st + sb, tile, t, G.sy, G.sz, NCELL, c, &diag);
       ap = diag * ph + s;
     }
     V.b[base + c] = ap + sbv[c];
@@ -500,7 +468,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong(GmgView<T> V, LvArgs L, Lv
     long long ix;
     float sg;
     T v = T(NAN);
-    if (resolve_s<D>(s_nb, P, Lp, V.wsign, q, &ix, &sg)) v = T(sg) * (V.phi[ix] - V.old[ix]);
+    if (resolve_s<D>(s_nb, P, Lp, V.wneu, q, &ix, &sg)) v = T(sg) * (V.phi[ix] - V.old[ix]);
     tile[t] = v;
   }
   __syncthreads();
@@ -609,9 +577,10 @@ __global__ void __launch_bounds__(kThreads) k_resnorm(GmgView<T> V, LvArgs L, Lv
     if (threadIdx.x < 3) partials[(size_t)bid * 3 + threadIdx.x] = 0.0;
     return;
   }
-  const int n = NT ? NT : L.n, m = n + 2;
+  const int n = NT ? NT : L.n;
+  const TileGeo<T, D> G(n);
   T *tile = reinterpret_cast<T *>(smem_raw);
-  T *sbv = tile + (D == 3 ? m * m * m : m * m);
+  T *sbv = tile + G.size;
   const long long base = L.off + (long long)(bid - L.first) * NCELL;
   const long long sb = V.st_base[bid];
   load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv);
@@ -622,9 +591,8 @@ __global__ void __launch_bounds__(kThreads) k_resnorm(GmgView<T> V, LvArgs L, Lv
   for (int c = threadIdx.x; c < NCELL; c += blockDim.x) {
     int x, y, z;
     cell_xyz<D>(c, n, &x, &y, &z);
-    const int t = (x + 1) + m * ((y + 1) + (D == 3 ? m * (z + 1) : 0));
     const T bb = sbv[c];
-    const float r = (float)resid_cell<T, D>(V.st, sb, tile, t, m, NCELL, c, inv_h2, bb);
+    const float r = (float)resid_cell<T, D>(V.st, sb, tile, G.idx(x, y, z), G.sy, G.sz, NCELL, c, inv_h2, bb);
     if (rout) rout[base + c] = r;
     s2f = fmaf(r, r, s2f);
     mxf = fmaxf(mxf, fabsf(r));

@@ -88,7 +88,8 @@ void launch_resnorm(gmg_tree *t, int l, double *partials, cudaStream_t s) {
   V.b = t->d_b;
   V.old = t->d_old;
   V.st = t->d_st;
-  for (int w = 0; w < 6; w++) V.wsign[w] = t->wall_type[w] == GMG_WALL_DIRICHLET ? -1.f : 1.f;
+  V.wneu = 0;
+  for (int w = 0; w < 6; w++) V.wneu |= (t->wall_type[w] == GMG_WALL_NEUMANN ? 1 : 0) << w;
   const gmg::LevelInfo &Li = t->lev(l);
   gmg::LvArgs L{Li.first, Li.count, Li.n, Li.ncell, Li.off, Li.h};
   gmg::LvArgs Lp = L;
