@@ -219,6 +219,23 @@ long long gmg_last_launch_count(const gmg_tree *tree);
 int gmg_profile_enable(gmg_tree *tree, int enable);
 int gmg_profile_read(gmg_tree *tree, int cap, int *kind, int *prec, int *level, long long *launches, double *ms);
 
+/* Execution options (defaults in brackets): GMG_OPT_GRAPHS [1] replays the
+ * solve phases as captured CUDA graphs; GMG_OPT_COARSE_COOP [1] runs the
+ * levels with at most 160 blocks and the coarse solve in one cooperative
+ * launch with grid barriers; GMG_OPT_SPIN_LIMIT [2^24] bounds the polls of
+ * such a barrier (about 100 ns each) before it records GMG_ERR_TIMEOUT.
+ * Results are identical with every setting. */
+#define GMG_OPT_GRAPHS 1
+#define GMG_OPT_COARSE_COOP 2
+#define GMG_OPT_SPIN_LIMIT 3
+int gmg_set_option(gmg_tree *tree, int option, long long value);
+
+/* Failure-detection self test: launches a cooperative kernel whose grid
+ * barrier waits for one CTA more than exist, so its bounded wait must run
+ * out.  Synchronises the stream; returns GMG_ERR_TIMEOUT when the wait ended
+ * as designed (the context stays usable), GMG_OK if it did not. */
+int gmg_selftest_barrier_timeout(gmg_tree *tree, long long spin_limit, void *stream);
+
 const char *gmg_error_string(int code);
 const char *gmg_last_error(void);
 

@@ -97,6 +97,8 @@ def load():
         "gmg_last_launch_count": (C.c_longlong, [vp]),
         "gmg_profile_enable": (C.c_int, [vp, C.c_int]),
         "gmg_profile_read": (C.c_int, [vp, C.c_int, ip, ip, ip, C.POINTER(C.c_longlong), dp]),
+        "gmg_set_option": (C.c_int, [vp, C.c_int, C.c_longlong]),
+        "gmg_selftest_barrier_timeout": (C.c_int, [vp, C.c_longlong, vp]),
         "gmg_error_string": (C.c_char_p, [C.c_int]),
         "gmg_last_error": (C.c_char_p, []),
     }
@@ -327,6 +329,14 @@ class Tree:
         if check:
             _check(rc)
         return dict(rc=rc, cycles=st.cycles, rel_l2=st.rel_l2, linf=st.linf, bnorm=st.bnorm)
+
+    OPTIONS = {"graphs": 1, "coarse_coop": 2, "spin_limit": 3}
+
+    def set_option(self, name, value):
+        _check(load().gmg_set_option(self.h, self.OPTIONS[name], int(value)))
+
+    def selftest_barrier_timeout(self, spin_limit=1 << 16, stream=None):
+        return load().gmg_selftest_barrier_timeout(self.h, int(spin_limit), _stream_ptr(stream))
 
     def last_launch_count(self):
         return int(load().gmg_last_launch_count(self.h))

@@ -10,6 +10,7 @@
 #include <string>
 
 #include "gmg_internal.h"
+#include "coarse_cycle.cuh"
 #include "kernels.cuh"
 
 namespace gmg {
@@ -26,7 +27,8 @@ void set_error(const std::string &msg) { g_last_error = msg; }
     }                                                                                        \
   } while (0)
 
-__global__ void __launch_bounds__(1024) k_reduce_partials(const double *partials, int nb, double *out) {
+__global__ void __launch_bounds__(1024) k_reduce_partials(const double *partials, int nb, double *out,
+                                                          const GridBar *bar) {
   __shared__ double s[3][1024];
   double a = 0.0, b = 0.0, c = 0.0;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
@@ -50,6 +52,7 @@ __global__ void __launch_bounds__(1024) k_reduce_partials(const double *partials
     out[0] = s[0][0];
     out[1] = s[1][0];
     out[2] = s[2][0];
+    out[3] = bar ? (double)bar->err : 0.0;  // a timed-out barrier of the coarse cycle
   }
 }
 
@@ -267,11 +270,66 @@ size_t tile_bytes(const gmg_tree *t, int l) {
 }
 
 // One FAS V-cycle on fields of type T (Sec. 2.2; readings UP and V).
+// Levels lmin .. ls in one cooperative launch (coarse_cycle.cuh).
+template <typename T, int D>
+int coop_cycle(gmg_tree *t, cudaStream_t s, int ls) {
+  GmgView<T> V = view<T>(t);
+  LevelSet LS{};
+  LS.lmin = t->lmin;
+  for (int l = t->lmin; l <= t->lmax; l++) LS.lv[l - t->lmin] = lv(t, l);
+  CycleArgs A{t->lmin, ls, t->prm.n_down, t->prm.n_up, t->nc, t->d_cinv, t->d_bar, t->spin_limit};
+  size_t sm = 0;
+  int maxb = 1;
+  for (int l = t->lmin; l <= ls; l++) {
+    const int hm = t->lev(l).n / 2 + 2;
+    sm = std::max(sm, tile_bytes<T>(t, l));
+    sm = std::max(sm, sizeof(T) * (size_t)(D == 3 ? hm * hm * hm : hm * hm));
+    maxb = std::max(maxb, t->lev(l).count);
+  }
+  int rc = GMG_OK;
+  with_nt<D>(t->N, [&](auto nt) {
+    constexpr int NT = decltype(nt)::value;
+    auto kern = k_cycle_coop<T, D, NT>;
+    int per_sm = 0;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, sm);
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int G = std::max(1, std::min(maxb, per_sm * sms));
+    if (per_sm < 1) {
+      set_error("the coarse-cycle kernel cannot be made resident");
+      rc = GMG_ERR_CUDA;
+      return;
+    }
+    cudaMemsetAsync(&t->d_bar->count, 0, sizeof(unsigned int), s);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    launch(t, s, 3, prec_of<T>(), t->lmin, [&] { cudaLaunchKernelEx(&cfg, kern, V, LS, A); });
+  });
+  if (rc) return rc;
+  CUDA_TRY(cudaGetLastError());
+  return GMG_OK;
+}
+
+// One FAS V-cycle on fields of type T (Sec. 2.2; readings UP and V): the
+// fine levels with one launch per phase, the levels up to coop_split in
+// one cooperative launch.
 template <typename T, int D>
 int vcycle_impl(gmg_tree *t, cudaStream_t s) {
   GmgView<T> V = view<T>(t);
   const int P = prec_of<T>();
-  for (int l = t->lmax; l > t->lmin; l--) {
+  const int ls = t->use_coop ? t->coop_split : t->lmin;
+  for (int l = t->lmax; l > ls; l--) {
     LvArgs L = lv(t, l), Lp = lv(t, l - 1);
     const size_t sm = tile_bytes<T>(t, l);
     with_nt<D>(L.n, [&](auto nt) {
@@ -288,7 +346,10 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s) {
       launch(t, s, 2, P, l - 1, [&] { k_fas<T, D, NT><<<Lp.count, kThreads, smp, s>>>(V, Lp, Lpp); });
     });
   }
-  {
+  if (t->use_coop) {
+    int rc = coop_cycle<T, D>(t, s, ls);
+    if (rc) return rc;
+  } else {
     LvArgs Lc = lv(t, t->lmin);
     const int M = t->nc;
     launch(t, s, 3, P, t->lmin, [&] {
@@ -296,7 +357,7 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s) {
                                                                                   V.phi + Lc.off);
     });
   }
-  for (int l = t->lmin + 1; l <= t->lmax; l++) {
+  for (int l = ls + 1; l <= t->lmax; l++) {
     LvArgs L = lv(t, l), Lp = lv(t, l - 1);
     const int hm = L.n / 2 + 2;
     const size_t psm = sizeof(T) * (size_t)(D == 3 ? hm * hm * hm : hm * hm);
@@ -344,9 +405,9 @@ int residual_impl(gmg_tree *t, cudaStream_t s, float *rout) {
     });
   }
   launch(t, s, 7, 0, t->lmax,
-         [&] { k_reduce_partials<<<1, 1024, 0, s>>>(t->d_partials, (int)t->blocks.size(), t->d_red); });
+         [&] { k_reduce_partials<<<1, 1024, 0, s>>>(t->d_partials, (int)t->blocks.size(), t->d_red, t->d_bar); });
   CUDA_TRY(cudaGetLastError());
-  CUDA_TRY(cudaMemcpyAsync(t->h_red, t->d_red, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(t->h_red, t->d_red, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
   return GMG_OK;
 }
 
@@ -426,6 +487,11 @@ int read_red(gmg_tree *t, cudaStream_t s, double *s2, double *mx, double *b2) {
   *s2 = t->h_red[0];
   *mx = t->h_red[1];
   *b2 = t->h_red[2];
+  if (t->h_red[3] != 0.0) {  // a grid barrier timed out: report once, then clear
+    CUDA_TRY(cudaMemset(t->d_bar, 0, sizeof(GridBar)));
+    set_error("a grid barrier of the coarse-level cycle timed out");
+    return GMG_ERR_TIMEOUT;
+  }
   return GMG_OK;
 }
 
@@ -433,7 +499,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t nbr, pnb, parent, pofs, flags, leaf, cbase, st_base, bt_base, phi, b, old, fphi, fb, fold, st, fst, bterm, cinv,
-      partials, red, total;
+      partials, red, bar, total;
 };
 
 Layout layout(const gmg_tree *t) {
@@ -466,6 +532,7 @@ Layout layout(const gmg_tree *t) {
   L.cinv = take((size_t)t->nc * t->nc * sizeof(double));
   L.partials = take(nb * 3 * sizeof(double));
   L.red = take(4 * sizeof(double));
+  L.bar = take(sizeof(GridBar));
   L.total = o;
   return L;
 }
@@ -661,6 +728,7 @@ int gmg_tree_bind(gmg_tree *t, void *device_ptr, size_t bytes) {
   t->d_cinv = reinterpret_cast<double *>(w + L.cinv);
   t->d_partials = reinterpret_cast<double *>(w + L.partials);
   t->d_red = reinterpret_cast<double *>(w + L.red);
+  t->d_bar = reinterpret_cast<GridBar *>(w + L.bar);
   const size_t nb = t->blocks.size();
   std::vector<long long> cbase(nb);
   for (size_t i = 0; i < nb; i++) {
@@ -700,6 +768,12 @@ int gmg_tree_bind(gmg_tree *t, void *device_ptr, size_t bytes) {
   CUDA_TRY(cudaMemset(t->f_old, 0, cells * sizeof(float)));
   // blocks on levels without leaves never write their residual partials
   CUDA_TRY(cudaMemset(t->d_partials, 0, nb * 3 * sizeof(double)));
+  CUDA_TRY(cudaMemset(t->d_red, 0, 4 * sizeof(double)));
+  CUDA_TRY(cudaMemset(t->d_bar, 0, sizeof(GridBar)));
+  // levels up to coop_split run inside one cooperative kernel (few blocks each)
+  t->coop_split = t->lmin;
+  for (int l = t->lmin; l <= t->lmax; l++)
+    if (t->lev(l).count <= kCoopMaxBlocks) t->coop_split = l;
   if (!t->h_red) CUDA_TRY(cudaMallocHost(&t->h_red, 4 * sizeof(double)));
   t->level_has_leaves.assign(t->levels.size(), 0);
   for (int id : t->leaf_ids_h) t->level_has_leaves[t->blocks[id].level - t->lmin] = 1;
@@ -850,6 +924,48 @@ int gmg_solve(gmg_tree *t, int precision, double rel_tol, int max_cycles, gmg_st
 }
 
 long long gmg_last_launch_count(const gmg_tree *t) { return t ? t->launches : 0; }
+
+int gmg_set_option(gmg_tree *t, int option, long long value) {
+  if (!t) return set_error("null tree"), GMG_ERR_INVALID_ARG;
+  switch (option) {
+    case GMG_OPT_GRAPHS: t->use_graphs = value != 0; break;
+    case GMG_OPT_COARSE_COOP: t->use_coop = value != 0; break;
+    case GMG_OPT_SPIN_LIMIT:
+      if (value < 1) return set_error("spin limit must be positive"), GMG_ERR_INVALID_ARG;
+      t->spin_limit = value;
+      break;
+    default: return set_error("unknown option"), GMG_ERR_INVALID_ARG;
+  }
+  for (auto &g : t->graphs)
+    if (g.exec) {
+      cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+    }
+  return GMG_OK;
+}
+
+int gmg_selftest_barrier_timeout(gmg_tree *t, long long spin_limit, void *stream) {
+  if (!t || spin_limit < 1) return set_error("bad arguments"), GMG_ERR_INVALID_ARG;
+  if (!t->bound) return set_error("tree not bound"), GMG_ERR_STATE;
+  cudaStream_t s = as_stream(stream);
+  CUDA_TRY(cudaMemsetAsync(t->d_bar, 0, sizeof(GridBar), s));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(4);
+  cfg.blockDim = dim3(32);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  CUDA_TRY(cudaLaunchKernelEx(&cfg, k_barrier_selftest, t->d_bar, spin_limit));
+  GridBar h{};
+  CUDA_TRY(cudaMemcpyAsync(&h, t->d_bar, sizeof(GridBar), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  CUDA_TRY(cudaMemsetAsync(t->d_bar, 0, sizeof(GridBar), s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return h.err;
+}
 
 int gmg_profile_enable(gmg_tree *t, int enable) {
   if (!t) return set_error("null tree"), GMG_ERR_INVALID_ARG;

@@ -14,6 +14,8 @@
 namespace gmg {
 
 constexpr int kMaxLevels = 40;
+constexpr int kCoopMaxBlocks = 160;  // levels with at most this many blocks join the cooperative coarse cycle
+struct GridBar;
 constexpr int kNbr = 27;  // 3x3x3 neighbour offsets (2D uses the dz = 0 plane)
 
 // block flags
@@ -117,6 +119,10 @@ struct gmg_tree {
   enum { kGraphResid64 = 0, kGraphResidMixed, kGraphCycle64, kGraphCycleMixed, kGraphVcycle64, kGraphSlots };
   GraphSlot graphs[kGraphSlots];
   bool use_graphs = true;
+  bool use_coop = true;       // coarse levels in one cooperative launch
+  int coop_split = 0;         // highest level run inside that launch
+  long long spin_limit = 1LL << 24;
+  gmg::GridBar *d_bar = nullptr;
   cudaStream_t cap_stream = nullptr;
 
   // kernel timing (gmg_profile_enable)

@@ -307,9 +307,7 @@ __device__ __forceinline__ void cell_xyz(int c, int n, int *x, int *y, int *z) {
 // block of a level (Sec. 2.2, readings S and SW):
 // phi_i <- (b_i - sum_j c_ij phi_j) / c_ii on the cells of one colour.
 template <typename T, int D, int NT>
-__global__ void __launch_bounds__(kThreads) k_smooth(GmgView<T> V, LvArgs L, LvArgs Lp, int color) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int bid = L.first + blockIdx.x;
+__device__ void smooth_block(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, int color, unsigned char *smem_raw) {
   const int n = NT ? NT : L.n, hn = n / 2;
   const TileGeo<T, D> G(n);
   T *tile = reinterpret_cast<T *>(smem_raw);
@@ -337,13 +335,17 @@ __global__ void __launch_bounds__(kThreads) k_smooth(GmgView<T> V, LvArgs L, LvA
   }
 }
 
+template <typename T, int D, int NT>
+__global__ void __launch_bounds__(kThreads) k_smooth(GmgView<T> V, LvArgs L, LvArgs Lp, int color) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  smooth_block<T, D, NT>(V, L, Lp, L.first + blockIdx.x, color, smem_raw);
+}
+
 // Residual r = b - A phi (Eq. (residual)) of every cell, restricted to the
 // parent as the mean of the 2^D children, together with phi (Sec. 2.2):
 // parent phi <- mean phi, parent b <- mean r (the FAS kernel adds A phi).
 template <typename T, int D, int NT>
-__global__ void __launch_bounds__(kThreads) k_resid_restrict(GmgView<T> V, LvArgs L, LvArgs Lp) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int bid = L.first + blockIdx.x;
+__device__ void resid_restrict_block(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, unsigned char *smem_raw) {
   const int n = NT ? NT : L.n, hn = n / 2;
   const TileGeo<T, D> G(n);
   T *tile = reinterpret_cast<T *>(smem_raw);
@@ -378,12 +380,16 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(GmgView<T> V, LvArg
   }
 }
 
+template <typename T, int D, int NT>
+__global__ void __launch_bounds__(kThreads) k_resid_restrict(GmgView<T> V, LvArgs L, LvArgs Lp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  resid_restrict_block<T, D, NT>(V, L, Lp, L.first + blockIdx.x, smem_raw);
+}
+
 // FAS coarse right-hand side on covered cells: b <- A phi + (restricted r);
 // old <- phi on every cell of the level (start of the coarse visit).
 template <typename T, int D, int NT>
-__global__ void __launch_bounds__(kThreads) k_fas(GmgView<T> V, LvArgs L, LvArgs Lp) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int bid = L.first + blockIdx.x;
+__device__ void fas_block(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, unsigned char *smem_raw) {
   const int n = NT ? NT : L.n;
   const TileGeo<T, D> G(n);
   const long long base = L.off + (long long)(bid - L.first) * NCELL;
@@ -418,6 +424,12 @@ __global__ void __launch_bounds__(kThreads) k_fas(GmgView<T> V, LvArgs L, LvArgs
   }
 }
 
+template <typename T, int D, int NT>
+__global__ void __launch_bounds__(kThreads) k_fas(GmgView<T> V, LvArgs L, LvArgs Lp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  fas_block<T, D, NT>(V, L, Lp, L.first + blockIdx.x, smem_raw);
+}
+
 // Coarsest level: phi = A^-1 b with the FP64 inverse, one warp per row.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_coarse(const double *__restrict__ Ainv, int M, const T *__restrict__ b,
@@ -437,11 +449,9 @@ __global__ void __launch_bounds__(kThreads) k_coarse(const double *__restrict__ 
 // (Sec. 2.2, 3.4): weights 3/4 and 1/4 per dimension from the parent cell
 // and its neighbours toward the fine cell (reading P).
 template <typename T, int D, int NT>
-__global__ void __launch_bounds__(kThreads) k_prolong(GmgView<T> V, LvArgs L, LvArgs Lp) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ void prolong_block(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, unsigned char *smem_raw) {
   __shared__ int s_nb[kNbr];
   T *tile = reinterpret_cast<T *>(smem_raw);
-  const int bid = L.first + blockIdx.x;
   const int n = NT ? NT : L.n, hn = n / 2, m = hn + 2;
   // the parent's 27 same-level neighbours (precomputed per block), -2 outside
   if (threadIdx.x < kNbr) s_nb[threadIdx.x] = V.pnb[(size_t)bid * kNbr + threadIdx.x];
@@ -512,6 +522,12 @@ __global__ void __launch_bounds__(kThreads) k_prolong(GmgView<T> V, LvArgs L, Lv
       V.phi[base + c] += interp(x, y, z);
     }
   }
+}
+
+template <typename T, int D, int NT>
+__global__ void __launch_bounds__(kThreads) k_prolong(GmgView<T> V, LvArgs L, LvArgs Lp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  prolong_block<T, D, NT>(V, L, Lp, L.first + blockIdx.x, smem_raw);
 }
 
 // phi of covered cells <- mean of the children (composite consistency).
@@ -603,6 +619,7 @@ __global__ void __launch_bounds__(kThreads) k_resnorm(GmgView<T> V, LvArgs L, Lv
 }
 
 // Deterministic final reduction of the per-block partials (fixed order).
-__global__ void __launch_bounds__(1024) k_reduce_partials(const double *partials, int nb, double *out);
+__global__ void __launch_bounds__(1024) k_reduce_partials(const double *partials, int nb, double *out,
+                                                          const GridBar *bar);
 
 }  // namespace gmg

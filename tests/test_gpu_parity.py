@@ -133,3 +133,37 @@ def test_device_arrays_round_trip():
     t.solution(out)
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy(), t.solution())
+
+
+@pytest.mark.parametrize("name", ["c2_64", "adaptive3d", "ragged3d", "c1"])
+@pytest.mark.parametrize("graphs,coop", [(0, 0), (1, 0), (0, 1)])
+def test_execution_paths_give_the_oracle_iterates(name, graphs, coop):
+    """The same V-cycle scheduled differently (captured graph or direct
+    launches; coarse levels in one cooperative launch or one launch per
+    phase) gives the oracle's iterates."""
+    p = parity_cases()[name]
+    o = oracle_problem(p)
+    t = gpu_problem(p)
+    t.set_option("graphs", graphs)
+    t.set_option("coarse_coop", coop)
+    for k in range(4):
+        o.vcycle(1)
+        t.vcycle(1)
+    ref = o.solution()
+    assert np.abs(t.solution() - ref).max() <= TOL_ITERATE * np.abs(ref).max()
+    st = t.solve(1, 1e-8, 60)
+    assert st["rel_l2"] <= 1e-8
+
+
+def test_bounded_barrier_wait_reports_timeout_and_context_survives():
+    """Failure detection without a fault: a grid barrier that can never
+    complete ends its bounded wait with GMG_ERR_TIMEOUT; the device stays
+    usable and the next solve is correct."""
+    p = parity_cases()["c2_32"]
+    t = gpu_problem(p)
+    assert t.selftest_barrier_timeout(1 << 16) == -7
+    o = oracle_problem(p)
+    o.vcycle(3)
+    t.vcycle(3)
+    ref = o.solution()
+    assert np.abs(t.solution() - ref).max() <= TOL_ITERATE * np.abs(ref).max()
