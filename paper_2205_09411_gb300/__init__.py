@@ -330,7 +330,7 @@ class Tree:
             _check(rc)
         return dict(rc=rc, cycles=st.cycles, rel_l2=st.rel_l2, linf=st.linf, bnorm=st.bnorm)
 
-    OPTIONS = {"graphs": 1, "coarse_coop": 2, "spin_limit": 3}
+    OPTIONS = {"graphs": 1, "coarse_coop": 2, "spin_limit": 3, "fused_sweeps": 4}
 
     def set_option(self, name, value):
         _check(load().gmg_set_option(self.h, self.OPTIONS[name], int(value)))

@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kThreads) k_cycle_coop(GmgView<T> V, LevelSet 
       for (int j = lane; j < A.nc; j += 32) s += a[j] * (double)V.b[Lc.off + j];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) V.phi[Lc.off + row] = T(s);
+      if (lane == 0) V.phi[Lc.poff + row] = T(s);
     }
   }
   if (!grid_sync(A.bar, G, A.spin_limit)) return;

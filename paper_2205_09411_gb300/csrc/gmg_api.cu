@@ -8,9 +8,11 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 
 #include "gmg_internal.h"
 #include "coarse_cycle.cuh"
+#include "fused_sweeps.cuh"
 #include "kernels.cuh"
 
 namespace gmg {
@@ -154,6 +156,7 @@ LvArgs lv(const gmg_tree *T, int l) {
   a.ncell = L.ncell;
   a.off = L.off;
   a.h = L.h;
+  a.poff = L.off;
   return a;
 }
 
@@ -246,9 +249,21 @@ void set_smem_limits() {
   for (int n : {4, 8, 16, 32, 2}) with_nt<D>(n, [&](auto nt) { set_smem_limits_nt<T, D, decltype(nt)::value>(); });
 }
 
+template <int D, int NT>
+void fused_attrs() {
+  if constexpr (NT != 0) {
+    kernel_attrs(k_smooth_tb<float, D, NT, 2>, true);
+    kernel_attrs(k_smooth_tb<float, D, NT, 4>, true);
+  }
+}
+
 void set_all_smem_limits() {
   static bool done = false;
   if (done) return;
+  for (int n : {8, 16, 32}) {
+    with_nt<2>(n, [&](auto nt) { fused_attrs<2, decltype(nt)::value>(); });
+    with_nt<3>(n, [&](auto nt) { fused_attrs<3, decltype(nt)::value>(); });
+  }
   set_smem_limits<double, 2>();
   set_smem_limits<double, 3>();
   set_smem_limits<float, 2>();
@@ -321,6 +336,38 @@ int coop_cycle(gmg_tree *t, cudaStream_t s, int ls) {
   return GMG_OK;
 }
 
+// Fused sweeps (fused_sweeps.cuh) run on FP32 levels whose blocks have all
+// their neighbours on the level, for 1 or 2 red/black steps per leg.
+template <typename T>
+bool fused_level(const gmg_tree *t, int l) {
+  if (!std::is_same<T, float>::value || !t->use_fused) return false;
+  const int n = t->lev(l).n;
+  const bool n_ok = t->D == 3 ? (n == 8 || n == 16) : (n == 8 || n == 16 || n == 32);
+  const bool k_ok = (t->prm.n_down == 1 || t->prm.n_down == 2) && (t->prm.n_up == 1 || t->prm.n_up == 2);
+  return n_ok && k_ok && t->level_complete[l - t->lmin];
+}
+
+template <typename T, int D>
+void launch_fused(gmg_tree *t, cudaStream_t s, int l, int sweeps, long long in_poff, long long out_poff) {
+  GmgView<T> V = view<T>(t);
+  LvArgs L = lv(t, l);
+  L.poff = in_poff;
+  auto go = [&](auto nt, auto kk) {
+    constexpr int NT = decltype(nt)::value, K = decltype(kk)::value;
+    if constexpr (NT != 0) {
+      const size_t sm = FusedGeo<T, D, NT, K>::smem_bytes();
+      launch(t, s, 0, prec_of<T>(), l,
+             [&] { k_smooth_tb<T, D, NT, K><<<L.count, kThreads, sm, s>>>(V, L, out_poff); });
+    }
+  };
+  with_nt<D>(L.n, [&](auto nt) {
+    if (sweeps == 1)
+      go(nt, IC<2>{});
+    else
+      go(nt, IC<4>{});
+  });
+}
+
 // One FAS V-cycle on fields of type T (Sec. 2.2; readings UP and V): the
 // fine levels with one launch per phase, the levels up to coop_split in
 // one cooperative launch.
@@ -329,14 +376,21 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s) {
   GmgView<T> V = view<T>(t);
   const int P = prec_of<T>();
   const int ls = t->use_coop ? t->coop_split : t->lmin;
+  const long long other = t->total_cells;  // offset of the second FP32 phi buffer
   for (int l = t->lmax; l > ls; l--) {
     LvArgs L = lv(t, l), Lp = lv(t, l - 1);
     const size_t sm = tile_bytes<T>(t, l);
+    const bool fused = fused_level<T>(t, l);
+    if (fused) {  // N_down steps in one pass into the second buffer
+      launch_fused<T, D>(t, s, l, t->prm.n_down, L.off, L.off + other);
+      L.poff = L.off + other;
+    }
     with_nt<D>(L.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
-      for (int k = 0; k < t->prm.n_down; k++)
-        for (int c = 0; c < 2; c++)
-          launch(t, s, 0, P, l, [&] { k_smooth<T, D, NT><<<L.count, kThreads, sm, s>>>(V, L, Lp, c); });
+      if (!fused)
+        for (int k = 0; k < t->prm.n_down; k++)
+          for (int c = 0; c < 2; c++)
+            launch(t, s, 0, P, l, [&] { k_smooth<T, D, NT><<<L.count, kThreads, sm, s>>>(V, L, Lp, c); });
       launch(t, s, 1, P, l, [&] { k_resid_restrict<T, D, NT><<<L.count, kThreads, sm, s>>>(V, L, Lp); });
     });
     LvArgs Lpp = l - 2 >= t->lmin ? lv(t, l - 2) : Lp;
@@ -354,7 +408,7 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s) {
     const int M = t->nc;
     launch(t, s, 3, P, t->lmin, [&] {
       k_coarse<T><<<(M + kThreads / 32 - 1) / (kThreads / 32), kThreads, 0, s>>>(t->d_cinv, M, V.b + Lc.off,
-                                                                                  V.phi + Lc.off);
+                                                                                  V.phi + Lc.poff);
     });
   }
   for (int l = ls + 1; l <= t->lmax; l++) {
@@ -362,13 +416,17 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s) {
     const int hm = L.n / 2 + 2;
     const size_t psm = sizeof(T) * (size_t)(D == 3 ? hm * hm * hm : hm * hm);
     const size_t sm = tile_bytes<T>(t, l);
+    const bool fused = fused_level<T>(t, l);
+    if (fused) L.poff = L.off + other;  // the down leg left phi in the second buffer
     with_nt<D>(L.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
       launch(t, s, 4, P, l, [&] { k_prolong<T, D, NT><<<L.count, kThreads, psm, s>>>(V, L, Lp); });
-      for (int k = 0; k < t->prm.n_up; k++)
-        for (int c = 0; c < 2; c++)
-          launch(t, s, 0, P, l, [&] { k_smooth<T, D, NT><<<L.count, kThreads, sm, s>>>(V, L, Lp, c); });
+      if (!fused)
+        for (int k = 0; k < t->prm.n_up; k++)
+          for (int c = 0; c < 2; c++)
+            launch(t, s, 0, P, l, [&] { k_smooth<T, D, NT><<<L.count, kThreads, sm, s>>>(V, L, Lp, c); });
     });
+    if (fused) launch_fused<T, D>(t, s, l, t->prm.n_up, L.off + other, L.off);  // back to the first buffer
   }
   if (t->adaptive) {
     for (int l = t->lmax; l >= 2 && l > t->lmin; l--) {
@@ -523,7 +581,7 @@ Layout layout(const gmg_tree *t) {
   L.phi = take(cells * sizeof(double));
   L.b = take(cells * sizeof(double));
   L.old = take(cells * sizeof(double));
-  L.fphi = take(cells * sizeof(float));
+  L.fphi = take(2 * cells * sizeof(float));  // two buffers: fused sweeps write the other one
   L.fb = take(cells * sizeof(float));
   L.fold = take(cells * sizeof(float));
   L.st = take(t->stencil_h.size() * sizeof(double));
@@ -775,6 +833,10 @@ int gmg_tree_bind(gmg_tree *t, void *device_ptr, size_t bytes) {
   for (int l = t->lmin; l <= t->lmax; l++)
     if (t->lev(l).count <= kCoopMaxBlocks) t->coop_split = l;
   if (!t->h_red) CUDA_TRY(cudaMallocHost(&t->h_red, 4 * sizeof(double)));
+  t->level_complete.assign(t->levels.size(), 1);
+  for (size_t i = 0; i < nb; i++)
+    for (int k = 0; k < kNbr; k++)
+      if (t->nbr_h[i * kNbr + k] == -1) t->level_complete[t->blocks[i].level - t->lmin] = 0;
   t->level_has_leaves.assign(t->levels.size(), 0);
   for (int id : t->leaf_ids_h) t->level_has_leaves[t->blocks[id].level - t->lmin] = 1;
   set_all_smem_limits();
@@ -930,6 +992,7 @@ int gmg_set_option(gmg_tree *t, int option, long long value) {
   switch (option) {
     case GMG_OPT_GRAPHS: t->use_graphs = value != 0; break;
     case GMG_OPT_COARSE_COOP: t->use_coop = value != 0; break;
+    case GMG_OPT_FUSED_SWEEPS: t->use_fused = value != 0; break;
     case GMG_OPT_SPIN_LIMIT:
       if (value < 1) return set_error("spin limit must be positive"), GMG_ERR_INVALID_ARG;
       t->spin_limit = value;

@@ -43,8 +43,9 @@ struct LevelInfo {
 // Per-level arguments passed to kernels.
 struct LvArgs {
   int first, count, n, ncell;
-  long long off;
+  long long off;   // first cell of the level in the b / old / stencil-indexed fields
   double h;
+  long long poff;  // first cell of the level in phi (off, or off + total cells in the second buffer)
 };
 
 // Everything a kernel needs to address the tree in device memory.
@@ -120,6 +121,8 @@ struct gmg_tree {
   GraphSlot graphs[kGraphSlots];
   bool use_graphs = true;
   bool use_coop = true;       // coarse levels in one cooperative launch
+  bool use_fused = true;      // temporally blocked FP32 sweeps on uniform levels
+  std::vector<char> level_complete;  // every block has all 26 neighbours on its level (or walls)
   int coop_split = 0;         // highest level run inside that launch
   long long spin_limit = 1LL << 24;
   gmg::GridBar *d_bar = nullptr;

@@ -105,7 +105,8 @@ __device__ __noinline__ T refine_ghost(const GmgView<T> &V, const LvArgs &L, con
   const int n = L.n;
   int q[3] = {p[0], p[1], p[2]};
   q[a] = p[a] < 0 ? 0 : n - 1;
-  const T f = V.phi[L.off + (long long)(bid - L.first) * L.ncell + q[0] + n * (q[1] + (D == 3 ? n * q[2] : 0))];
+  const T f = V.phi[L.poff + (long long)(bid - L.first) * L.ncell + q[0] + n * (q[1] + (D == 3 ? n * q[2] : 0))];
+  const long long dp = Lp.poff - Lp.off;  // phi of the coarse level may live in the second buffer
   const int P = V.parent[bid], po = V.pofs[bid];
   const int pofs[3] = {po & 1023, (po >> 10) & 1023, (po >> 20) & 1023};
   int cq[3] = {0, 0, 0};
@@ -114,7 +115,7 @@ __device__ __noinline__ T refine_ghost(const GmgView<T> &V, const LvArgs &L, con
   long long ix;
   float sg;
   if (!resolve<D>(V.nbr, V.flags, V.wneu, Lp, P, cq, &ix, &sg)) return T(NAN);
-  const T c = V.phi[ix];
+  const T c = V.phi[ix + dp];
   T chat = c;
 #pragma unroll
   for (int t = 0; t < D; t++) {
@@ -127,7 +128,7 @@ __device__ __noinline__ T refine_ghost(const GmgView<T> &V, const LvArgs &L, con
     float sp, sm;
     if (!resolve<D>(V.nbr, V.flags, V.wneu, Lp, P, qp, &ip, &sp)) return T(NAN);
     if (!resolve<D>(V.nbr, V.flags, V.wneu, Lp, P, qm, &im, &sm)) return T(NAN);
-    const T cp = T(sp) * V.phi[ip], cm = T(sm) * V.phi[im];
+    const T cp = T(sp) * V.phi[ip + dp], cm = T(sm) * V.phi[im + dp];
     chat = chat + o * (T(0.5) * (cp - cm));
   }
   return f / T(3) + T(2) * chat / T(3);
@@ -208,19 +209,20 @@ __device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
     s_nb[threadIdx.x] = V.nbr[(size_t)bid * kNbr + nbr_slot(o[0], o[1], o[2])];
   }
   if (threadIdx.x == 0) s_fl = V.flags[bid];
-  const long long base = L.off + (long long)(bid - L.first) * ncell;
+  const long long base = L.off + (long long)(bid - L.first) * ncell;   // b
+  const long long pbase = L.poff + (long long)(bid - L.first) * ncell; // phi
   constexpr int VEC = 16 / sizeof(T);
   if (n % VEC == 0) {  // 16-byte chunks never cross a row of the tile
     for (int i = threadIdx.x; i < ncell / VEC; i += blockDim.x) {
       const int c = i * VEC;
       const int x = c % n, y = (c / n) % n, z = D == 3 ? c / (n * n) : 0;
-      cp_async16(tile + G.idx(x, y, z), V.phi + base + c);
+      cp_async16(tile + G.idx(x, y, z), V.phi + pbase + c);
       if (sbv) cp_async16(sbv + c, V.b + base + c);
     }
   } else {  // blocks narrower than one vector (coarse sub-levels)
     for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
       const int x = c % n, y = (c / n) % n, z = D == 3 ? c / (n * n) : 0;
-      cp_async_elem(tile + G.idx(x, y, z), V.phi + base + c);
+      cp_async_elem(tile + G.idx(x, y, z), V.phi + pbase + c);
       if (sbv) cp_async_elem(sbv + c, V.b + base + c);
     }
   }
@@ -239,7 +241,7 @@ __device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
     const int gx = a == 0 ? gn : u, gy = a == 1 ? gn : (a == 0 ? u : v), gz = a == 2 ? gn : v;
     const int qx = a == 0 ? sn : u, qy = a == 1 ? sn : (a == 0 ? u : v), qz = a == 2 ? sn : v;
     cp_async_elem(tile + G.idx(gx, gy, gz),
-                  V.phi + L.off + (long long)(id - L.first) * ncell + qx + n * (qy + (D == 3 ? n * qz : 0)));
+                  V.phi + L.poff + (long long)(id - L.first) * ncell + qx + n * (qy + (D == 3 ? n * qz : 0)));
   }
   cp_async_wait_all();
   __syncthreads();
@@ -312,7 +314,7 @@ __device__ void smooth_block(const GmgView<T> &V, const LvArgs &L, const LvArgs 
   const TileGeo<T, D> G(n);
   T *tile = reinterpret_cast<T *>(smem_raw);
   T *sbv = tile + G.size;
-  const long long base = L.off + (long long)(bid - L.first) * NCELL;
+  const long long pbase = L.poff + (long long)(bid - L.first) * NCELL;
   const long long sb = V.st_base[bid];
   load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv);
   const T h2 = T(L.h * L.h), inv2d = T(1.0 / (2 * D));
@@ -331,7 +333,7 @@ __device__ void smooth_block(const GmgView<T> &V, const LvArgs &L, const LvArgs 
       const T s = offdiag_st<T, D>(V.st + sb, tile, t, G.sy, G.sz, NCELL, c, &diag);
       nv = (sbv[c] - s) / diag;
     }
-    V.phi[base + c] = nv;
+    V.phi[pbase + c] = nv;
   }
 }
 
@@ -356,6 +358,7 @@ __device__ void resid_restrict_block(const GmgView<T> &V, const LvArgs &L, const
   const T inv_h2 = T(1.0 / (L.h * L.h));
   const int pofs[3] = {po & 1023, (po >> 10) & 1023, (po >> 20) & 1023};
   const long long pbase = Lp.off + (long long)(P - Lp.first) * Lp.ncell;
+  const long long pdelta = Lp.poff - Lp.off;
   const int pn = Lp.n;
   const int ncq = D == 3 ? hn * hn * hn : hn * hn;
   const T w = T(1.0 / (1 << D));
@@ -375,7 +378,7 @@ __device__ void resid_restrict_block(const GmgView<T> &V, const LvArgs &L, const
           sr = sr + resid_cell<T, D>(V.st, sb, tile, t, G.sy, G.sz, NCELL, c, inv_h2, sbv[c]);
         }
     const long long pc = pbase + (pofs[0] + qx) + pn * ((pofs[1] + qy) + (D == 3 ? pn * (pofs[2] + qz) : 0));
-    V.phi[pc] = sp * w;
+    V.phi[pc + pdelta] = sp * w;
     V.b[pc] = sr * w;
   }
 }
@@ -396,7 +399,7 @@ __device__ void fas_block(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
   if (!(V.flags[bid] & kHasChildren)) {
     constexpr int VEC = 16 / sizeof(T);
     using VT = typename Vec16<T>::type;
-    const VT *src = reinterpret_cast<const VT *>(V.phi + base);
+    const VT *src = reinterpret_cast<const VT *>(V.phi + (L.poff - L.off) + base);
     VT *dst = reinterpret_cast<VT *>(V.old + base);
     for (int i = threadIdx.x; i < NCELL / VEC; i += blockDim.x) dst[i] = src[i];
     return;
@@ -459,7 +462,7 @@ __device__ void prolong_block(const GmgView<T> &V, const LvArgs &L, const LvArgs
   // the block's own phi, loaded while the coarse correction is staged
   constexpr int VEC = 16 / sizeof(T);
   using VT = typename Vec16<T>::type;
-  const long long base = L.off + (long long)(bid - L.first) * NCELL;
+  const long long base = L.poff + (long long)(bid - L.first) * NCELL;
   VT *__restrict__ fine = reinterpret_cast<VT *>(V.phi + base);
   constexpr int IV = NT ? ((D == 3 ? NT * NT * NT : NT * NT) / VEC + kThreads - 1) / kThreads : 1;
   VT rv[IV];
@@ -478,7 +481,7 @@ __device__ void prolong_block(const GmgView<T> &V, const LvArgs &L, const LvArgs
     long long ix;
     float sg;
     T v = T(NAN);
-    if (resolve_s<D>(s_nb, P, Lp, V.wneu, q, &ix, &sg)) v = T(sg) * (V.phi[ix] - V.old[ix]);
+    if (resolve_s<D>(s_nb, P, Lp, V.wneu, q, &ix, &sg)) v = T(sg) * (V.phi[ix + (Lp.poff - Lp.off)] - V.old[ix]);
     tile[t] = v;
   }
   __syncthreads();
@@ -535,10 +538,10 @@ template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kThreads) k_restrict_phi(GmgView<T> V, LvArgs L, LvArgs Lp) {
   const int bid = L.first + blockIdx.x;
   const int n = NT ? NT : L.n, hn = n / 2;
-  const long long base = L.off + (long long)(bid - L.first) * NCELL;
+  const long long base = L.poff + (long long)(bid - L.first) * NCELL;
   const int P = V.parent[bid], po = V.pofs[bid];
   const int pofs[3] = {po & 1023, (po >> 10) & 1023, (po >> 20) & 1023};
-  const long long pbase = Lp.off + (long long)(P - Lp.first) * Lp.ncell;
+  const long long pbase = Lp.poff + (long long)(P - Lp.first) * Lp.ncell;
   const int pn = Lp.n;
   const int ncq = D == 3 ? hn * hn * hn : hn * hn;
   const T w = T(1.0 / (1 << D));

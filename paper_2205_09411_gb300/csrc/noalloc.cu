@@ -91,11 +91,11 @@ void launch_resnorm(gmg_tree *t, int l, double *partials, cudaStream_t s) {
   V.wneu = 0;
   for (int w = 0; w < 6; w++) V.wneu |= (t->wall_type[w] == GMG_WALL_NEUMANN ? 1 : 0) << w;
   const gmg::LevelInfo &Li = t->lev(l);
-  gmg::LvArgs L{Li.first, Li.count, Li.n, Li.ncell, Li.off, Li.h};
+  gmg::LvArgs L{Li.first, Li.count, Li.n, Li.ncell, Li.off, Li.h, Li.off};
   gmg::LvArgs Lp = L;
   if (l > t->lmin) {
     const gmg::LevelInfo &Pi = t->lev(l - 1);
-    Lp = gmg::LvArgs{Pi.first, Pi.count, Pi.n, Pi.ncell, Pi.off, Pi.h};
+    Lp = gmg::LvArgs{Pi.first, Pi.count, Pi.n, Pi.ncell, Pi.off, Pi.h, Pi.off};
   }
   const size_t sm = gmg::level_smem_bytes<double>(D, Li.n);
   cudaFuncSetAttribute(gmg::k_resnorm<double, D, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
