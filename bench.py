@@ -144,7 +144,8 @@ def allreduce_max(x, world):
 
 
 def build_tree(G, p):
-    t = G.Tree(p["dim"], p["N"], p["cb"], p["lo"], p["h1"], p["max_level"])
+    t = G.Tree(p["dim"], p["N"], p["cb"], p["lo"], p["h1"], p["max_level"],
+               max_coarse_cells=p.get("max_coarse_cells") or 0)
     t.set_walls(p["walls"], values=p["wall_values"], fn=p["wall_fn"])
     t.store_stencils(p["lsf"], p["phib"])
     t.bind()

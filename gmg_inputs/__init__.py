@@ -9,8 +9,9 @@ analytic test problems, not datasets):
 * ``c1``  2D, [0,1]^2, 64^2 cells in 8^2 blocks (levels 8^2 .. 64^2); circle
   |x-(1/2,1/2)| - 1/4; manufactured u = sin(pi x) sin(pi y) + x^2 supplies
   g = Laplacian(u) everywhere, the circle's Dirichlet data and the walls'.
-* ``c2``  3D, [0,1]^3, 128^3 cells in 16^3 blocks; sphere |x-c| - 0.2;
-  Laplace (g = 0) with phi = 1 on the sphere and 0 on the walls.
+* ``c2``  3D, [0,1]^3, 128^3 cells in 16^3 blocks (coarse levels 8^3 and
+  4^3 inside the root block); sphere |x-c| - 0.2; Laplace (g = 0) with
+  phi = 1 on the sphere and 0 on the walls.
 * ``sphere2d`` / ``sphere3d``  the convergence test of Sec. 4.1: a domain of
   unit size centred at the origin, f = |x| - R with R = 1/4, walls given by
   the analytic solutions log(|x|/R) (2D) and 1 - R/|x| (3D), phi_b = 0.
@@ -66,7 +67,9 @@ def problem(name: str, **over) -> dict:
     Keys: dim, N (cells per block side), cb (root blocks per side), lo, h1
     (cell size on level 1), max_level, refine (None = uniform), lsf (kind,
     params), walls (types), wall_values or wall_fn, phib (value or callable),
-    rhs (callable centres -> g), n_vcycles, tol.
+    rhs (callable centres -> g), n_vcycles, tol, and optionally
+    max_coarse_cells (size of the coarsest level, default 64 in 2D and 512
+    in 3D).
     """
     if name == "c1":
         p = dict(dim=2, N=8, cb=(1, 1, 1), lo=(0.0, 0.0, 0.0), h1=1.0 / 8, max_level=4, refine=None,
@@ -76,7 +79,7 @@ def problem(name: str, **over) -> dict:
         p = dict(dim=3, N=16, cb=(1, 1, 1), lo=(0.0, 0.0, 0.0), h1=1.0 / 16, max_level=4, refine=None,
                  lsf=("sphere", (0.5, 0.5, 0.5, 0.2)), walls=(WALL_DIRICHLET,) * 6,
                  wall_values=(0.0,) * 6, wall_fn=None, phib=1.0,
-                 rhs=lambda xc: np.zeros(len(xc)), n_vcycles=12, tol=1e-8, index=1)
+                 rhs=lambda xc: np.zeros(len(xc)), n_vcycles=12, tol=1e-8, index=1, max_coarse_cells=64)
     elif name in ("sphere2d", "sphere3d"):
         dim = 2 if name == "sphere2d" else 3
         p = dict(dim=dim, N=8, cb=(1, 1, 1), lo=(-0.5, -0.5, -0.5 if dim == 3 else 0.0), h1=1.0 / 8,

@@ -69,6 +69,7 @@ struct CycleArgs {
   const double *cinv;
   GridBar *bar;
   long long spin_limit;
+  int l_one;  // levels l_lo .. l_one hold one block each and run on CTA 0 alone (-1 << 20: none)
 };
 
 // Block operations with the compile-time side NT for levels >= 1 and the
@@ -106,12 +107,29 @@ __device__ __forceinline__ void prolong_any(const GmgView<T> &V, const LvArgs &L
     prolong_block<T, D, 0>(V, L, Lp, bid, sm);
 }
 
+// Exact solve on level Lc by warps w0, w0 + nw, ... : phi = A^-1 b, one warp
+// per row, FP64 accumulation.
+template <typename T>
+__device__ __forceinline__ void coarse_rows(const GmgView<T> &V, const LvArgs &Lc, const double *cinv, int nc, int w0,
+                                            int nw) {
+  const int lane = threadIdx.x & 31;
+  for (int row = w0; row < nc; row += nw) {
+    const double *a = cinv + (size_t)row * nc;
+    double s = 0.0;
+    for (int j = lane; j < nc; j += 32) s += a[j] * (double)V.b[Lc.off + j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) V.phi[Lc.poff + row] = T(s);
+  }
+}
+
 template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kThreads) k_cycle_coop(GmgView<T> V, LevelSet LS, CycleArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const unsigned int G = gridDim.x;
 #define GMG_LV(l) LS.lv[(l)-LS.lmin]
-  for (int l = A.l_hi; l > A.l_lo; l--) {
+  // levels l_hi .. l_one + 1: every CTA, grid barrier between phases
+  for (int l = A.l_hi; l > A.l_lo && l > A.l_one; l--) {
     const LvArgs L = GMG_LV(l), Lp = GMG_LV(l - 1);
     for (int k = 0; k < A.n_down; k++)
       for (int c = 0; c < 2; c++) {
@@ -133,21 +151,44 @@ __global__ void __launch_bounds__(kThreads) k_cycle_coop(GmgView<T> V, LevelSet 
     }
     if (!grid_sync(A.bar, G, A.spin_limit)) return;
   }
-  {  // exact solve on l_lo: phi = A^-1 b, one warp per row (FP64 accumulation)
-    const LvArgs Lc = GMG_LV(A.l_lo);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nw = (int)G * (kThreads / 32);
-    for (int row = blockIdx.x * (kThreads / 32) + warp; row < A.nc; row += nw) {
-      const double *a = A.cinv + (size_t)row * A.nc;
-      double s = 0.0;
-      for (int j = lane; j < A.nc; j += 32) s += a[j] * (double)V.b[Lc.off + j];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) V.phi[Lc.poff + row] = T(s);
+  if (A.l_one >= A.l_lo) {
+    // single-block levels l_one .. l_lo: CTA 0 runs the bottom of the cycle
+    // (sweeps, restriction, FAS, coarse solve, prolongation, sweeps) with
+    // block-level barriers only
+    if (blockIdx.x == 0) {
+      const int top = A.l_one < A.l_hi ? A.l_one : A.l_hi;
+      for (int l = top; l > A.l_lo; l--) {
+        const LvArgs L = GMG_LV(l), Lp = GMG_LV(l - 1);
+        for (int k = 0; k < A.n_down; k++)
+          for (int c = 0; c < 2; c++) {
+            smooth_any<T, D, NT>(V, L, Lp, L.first, c, smem_raw);
+            __syncthreads();
+          }
+        resid_restrict_any<T, D, NT>(V, L, Lp, L.first, smem_raw);
+        __syncthreads();
+        const LvArgs Lpp = l - 2 >= LS.lmin ? GMG_LV(l - 2) : Lp;
+        fas_any<T, D, NT>(V, Lp, Lpp, Lp.first, smem_raw);
+        __syncthreads();
+      }
+      coarse_rows<T>(V, GMG_LV(A.l_lo), A.cinv, A.nc, threadIdx.x >> 5, kThreads / 32);
+      __syncthreads();
+      for (int l = A.l_lo + 1; l <= top; l++) {
+        const LvArgs L = GMG_LV(l), Lp = GMG_LV(l - 1);
+        prolong_any<T, D, NT>(V, L, Lp, L.first, smem_raw);
+        __syncthreads();
+        for (int k = 0; k < A.n_up; k++)
+          for (int c = 0; c < 2; c++) {
+            smooth_any<T, D, NT>(V, L, Lp, L.first, c, smem_raw);
+            __syncthreads();
+          }
+      }
     }
+  } else {
+    coarse_rows<T>(V, GMG_LV(A.l_lo), A.cinv, A.nc, blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5),
+                   (int)G * (kThreads / 32));
   }
-  if (!grid_sync(A.bar, G, A.spin_limit)) return;
-  for (int l = A.l_lo + 1; l <= A.l_hi; l++) {
+  if (A.l_hi > A.l_one && !grid_sync(A.bar, G, A.spin_limit)) return;
+  for (int l = (A.l_one >= A.l_lo ? A.l_one : A.l_lo) + 1; l <= A.l_hi; l++) {
     const LvArgs L = GMG_LV(l), Lp = GMG_LV(l - 1);
     for (int b = blockIdx.x; b < L.count; b += G) {
       prolong_any<T, D, NT>(V, L, Lp, L.first + b, smem_raw);

@@ -70,6 +70,9 @@ __global__ void __launch_bounds__(kThreads) k_smooth_tb(GmgView<T> V, LvArgs L, 
     whi[a] = s_nb[nbr_slot(a == 0 ? 1 : 0, a == 1 ? 1 : 0, a == 2 ? 1 : 0)] == -2;
   }
   const bool anywall = wlo[0] || whi[0] || wlo[1] || whi[1] || wlo[2] || whi[2];
+  // any cut block among the 27?  If not, every cell takes the regular stencil
+  bool cut_near = false;
+  for (int k = 0; k < kNbr; k++) cut_near = cut_near || s_stb[k] >= 0;
   const T h2 = T(L.h * L.h), inv2d = T(1.0 / (2 * D));
   for (int j = 0; j < K; j++) {
     const int color = j & 1;
@@ -111,27 +114,42 @@ __global__ void __launch_bounds__(kThreads) k_smooth_tb(GmgView<T> V, LvArgs L, 
     const int lx = wlo[0] ? 0 : -r, hx = whi[0] ? n : n + r;
     const int ly = wlo[1] ? 0 : -r, hy = whi[1] ? n : n + r;
     const int lz = D == 3 ? (wlo[2] ? 0 : -r) : 0, hz = D == 3 ? (whi[2] ? n : n + r) : 1;
-    const int ex = hx - lx, ey = hy - ly, ez = hz - lz;
-    const int exh = (ex + 1) / 2;
-    for (int i = threadIdx.x; i < exh * ey * ez; i += blockDim.x) {
-      const int xi = i % exh, rest = i / exh;
-      const int y = ly + rest % ey, z = D == 3 ? lz + rest / ey : 0;
-      const int x = lx + 2 * xi + ((lx + y + z + color) & 1);
-      if (x >= hx) continue;
-      const int t = F::idx(x, y, z);
-      const int ox = x < 0 ? -1 : (x >= n ? 1 : 0), oy = y < 0 ? -1 : (y >= n ? 1 : 0);
-      const int oz = D == 3 ? (z < 0 ? -1 : (z >= n ? 1 : 0)) : 0;
-      const long long stb = s_stb[nbr_slot(ox, oy, oz)];
-      T nv;
-      if (stb < 0) {
-        nv = (nb_sum<T, D>(tp, t, F::SY, F::SZ) - h2 * tb[t]) * inv2d;
-      } else {
-        const int c = (x - ox * n) + n * ((y - oy * n) + (D == 3 ? n * (z - oz * n) : 0));
-        T diag;
-        const T s = offdiag_st<T, D>(V.st + stb, tp, t, F::SY, F::SZ, F::NC, c, &diag);
-        nv = (tb[t] - s) / diag;
+    const int exh = (hx - lx + 1) / 2, ey = hy - ly;
+    // a thread's (x-pair, y) positions in a plane, computed once per half-sweep
+    constexpr int PL = ((NT + 2 * K) / 2 * (NT + 2 * K) + kThreads - 1) / kThreads;
+    int pxi[PL], py[PL];
+#pragma unroll
+    for (int k = 0; k < PL; k++) {
+      const int q = threadIdx.x + k * kThreads;
+      pxi[k] = q < exh * ey ? q % exh : -1;
+      py[k] = ly + q / exh;
+    }
+    for (int z = lz; z < hz; z++) {
+#pragma unroll
+      for (int k = 0; k < PL; k++) {
+        if (pxi[k] < 0) continue;
+        const int y = py[k];
+        const int x = lx + 2 * pxi[k] + ((lx + y + z + color) & 1);
+        if (x >= hx) continue;
+        const int t = F::idx(x, y, z);
+        T nv;
+        if (!cut_near) {
+          nv = (nb_sum<T, D>(tp, t, F::SY, F::SZ) - h2 * tb[t]) * inv2d;
+        } else {
+          const int ox = x < 0 ? -1 : (x >= n ? 1 : 0), oy = y < 0 ? -1 : (y >= n ? 1 : 0);
+          const int oz = D == 3 ? (z < 0 ? -1 : (z >= n ? 1 : 0)) : 0;
+          const long long stb = s_stb[nbr_slot(ox, oy, oz)];
+          if (stb < 0) {
+            nv = (nb_sum<T, D>(tp, t, F::SY, F::SZ) - h2 * tb[t]) * inv2d;
+          } else {
+            const int c = (x - ox * n) + n * ((y - oy * n) + (D == 3 ? n * (z - oz * n) : 0));
+            T diag;
+            const T sum = offdiag_st<T, D>(V.st + stb, tp, t, F::SY, F::SZ, F::NC, c, &diag);
+            nv = (tb[t] - sum) / diag;
+          }
+        }
+        tp[t] = nv;
       }
-      tp[t] = nv;
     }
     __syncthreads();
   }

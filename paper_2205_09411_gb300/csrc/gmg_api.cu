@@ -292,7 +292,12 @@ int coop_cycle(gmg_tree *t, cudaStream_t s, int ls) {
   LevelSet LS{};
   LS.lmin = t->lmin;
   for (int l = t->lmin; l <= t->lmax; l++) LS.lv[l - t->lmin] = lv(t, l);
-  CycleArgs A{t->lmin, ls, t->prm.n_down, t->prm.n_up, t->nc, t->d_cinv, t->d_bar, t->spin_limit};
+  // the single-block levels at the bottom run on one CTA when the coarse
+  // solve is small enough for one CTA
+  int l_one = t->lmin - 1;
+  if (t->nc <= 256)
+    for (int l = t->lmin; l <= ls && t->lev(l).count == 1; l++) l_one = l;
+  CycleArgs A{t->lmin, ls, t->prm.n_down, t->prm.n_up, t->nc, t->d_cinv, t->d_bar, t->spin_limit, l_one};
   size_t sm = 0;
   int maxb = 1;
   for (int l = t->lmin; l <= ls; l++) {

@@ -21,7 +21,8 @@ def oracle_problem(p, n_down=2, n_up=2, eps_tol=1e-8, mask_factor=1.5, w_min=0.0
     import oracle as O
     kinds = {"none": O.LSF_NONE, "sphere": O.LSF_SPHERE, "capsule": O.LSF_CAPSULE,
              "ellipsoid": O.LSF_ELLIPSOID}
-    t = O.OracleTree(p["dim"], p["N"], p["cb"], p["lo"], p["h1"], p["max_level"], refine=p["refine"])
+    t = O.OracleTree(p["dim"], p["N"], p["cb"], p["lo"], p["h1"], p["max_level"], refine=p["refine"],
+                     max_coarse_cells=p.get("max_coarse_cells"))
     t.set_params(n_down, n_up, eps_tol, mask_factor, w_min)
     kind, params = p["lsf"]
     t.set_lsf(kinds[kind], params)
@@ -36,6 +37,7 @@ def gpu_problem(p, n_down=2, n_up=2, eps_tol=1e-8, mask_factor=1.5, w_min=0.0, b
     """The same problem as oracle_problem, built through the CUDA library's C ABI."""
     import paper_2205_09411_gb300 as G
     t = G.Tree(p["dim"], p["N"], p["cb"], p["lo"], p["h1"], p["max_level"], refine=p["refine"],
+               max_coarse_cells=p.get("max_coarse_cells") or (64 if p["dim"] == 2 else 512),
                n_down=n_down, n_up=n_up, eps_tol=eps_tol, mask_factor=mask_factor, w_min=w_min)
     t.set_walls(p["walls"], values=p.get("wall_values"), fn=p.get("wall_fn"))
     kind, params = p["lsf"]
