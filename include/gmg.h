@@ -228,7 +228,7 @@ int gmg_profile_read(gmg_tree *tree, int cap, int *kind, int *prec, int *level, 
 #define GMG_OPT_GRAPHS 1
 #define GMG_OPT_COARSE_COOP 2
 #define GMG_OPT_SPIN_LIMIT 3
-#define GMG_OPT_FUSED_SWEEPS 4 /* [1] FP32 levels without refinement boundaries: all N_down (N_up)
+#define GMG_OPT_FUSED_SWEEPS 4 /* [0] FP32 levels without refinement boundaries: all N_down (N_up)
                                   half-sweeps of a visit in one pass over a tile with a halo */
 int gmg_set_option(gmg_tree *tree, int option, long long value);
 

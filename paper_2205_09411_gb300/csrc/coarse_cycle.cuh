@@ -123,6 +123,249 @@ __device__ __forceinline__ void coarse_rows(const GmgView<T> &V, const LvArgs &L
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Bottom of the cycle held in shared memory.  The single-block levels
+// l_lo .. l_one each cover the whole domain (root block and its coarsened
+// copies): all their faces are walls, and the child block of one covers its
+// parent entirely.  CTA 0 loads phi and the FAS right-hand side of l_one
+// once, runs sweeps, residual + restriction, FAS right-hand sides, the exact
+// solve, prolongation and sweeps on shared-memory copies of every level
+// (same formulas as the block kernels), and writes phi of l_one back.
+template <typename T, int D>
+struct TailLevel {
+  T *tile, *b, *old;
+  int n, ncell;
+  long long stb;  // stencil offset of the level's block (-1: regular)
+  LvArgs L;
+};
+
+template <typename T, int D>
+__device__ __forceinline__ size_t tail_level_elems(int n) {
+  return (size_t)TileGeo<T, D>(n).size + 2 * (size_t)(D == 3 ? n * n * n : n * n);
+}
+
+// wall ghosts of a single-block level (all faces are walls): sign * mirror
+template <typename T, int D>
+__device__ void tail_walls(const TailLevel<T, D> &Q, int wneu) {
+  const TileGeo<T, D> G(Q.n);
+  const int n = Q.n, nf = D == 3 ? n * n : n;
+  for (int i = threadIdx.x; i < 2 * D * nf; i += blockDim.x) {
+    const int f = i / nf, j = i - f * nf;
+    const int a = f >> 1, side = f & 1;
+    const int u = j % n, v = D == 3 ? j / n : 0;
+    const int gn = side ? n : -1, mn = side ? n - 1 : 0;
+    const int gx = a == 0 ? gn : u, gy = a == 1 ? gn : (a == 0 ? u : v), gz = a == 2 ? gn : v;
+    const int mx = a == 0 ? mn : u, my = a == 1 ? mn : (a == 0 ? u : v), mz = a == 2 ? mn : v;
+    Q.tile[G.idx(gx, gy, gz)] = (((wneu >> f) & 1) ? T(1) : T(-1)) * Q.tile[G.idx(mx, my, mz)];
+  }
+  __syncthreads();
+}
+
+template <typename T, int D>
+__device__ void tail_smooth(const GmgView<T> &V, const TailLevel<T, D> &Q, int color) {
+  tail_walls<T, D>(Q, V.wneu);
+  const TileGeo<T, D> G(Q.n);
+  const int n = Q.n, hn = n / 2;
+  const T h2 = T(Q.L.h * Q.L.h), inv2d = T(1.0 / (2 * D));
+  for (int j = threadIdx.x; j < Q.ncell / 2; j += blockDim.x) {
+    const int rest = j / hn;
+    const int y = rest % n, z = D == 3 ? rest / n : 0;
+    const int x = 2 * (j % hn) + ((y + z + color) & 1);
+    const int c = x + n * (y + n * z);
+    const int t = G.idx(x, y, z);
+    T nv;
+    if (Q.stb < 0) {
+      nv = (nb_sum<T, D>(Q.tile, t, G.sy, G.sz) - h2 * Q.b[c]) * inv2d;
+    } else {
+      T diag;
+      const T sum = offdiag_st<T, D>(V.st + Q.stb, Q.tile, t, G.sy, G.sz, Q.ncell, c, &diag);
+      nv = (Q.b[c] - sum) / diag;
+    }
+    Q.tile[t] = nv;
+  }
+  __syncthreads();
+}
+
+// residual of level F restricted into level C (C covered entirely by F):
+// phi_C <- mean phi_F, b_C <- mean r_F
+template <typename T, int D>
+__device__ void tail_resid_restrict(const GmgView<T> &V, const TailLevel<T, D> &F, const TailLevel<T, D> &Cq) {
+  tail_walls<T, D>(F, V.wneu);
+  const TileGeo<T, D> G(F.n), Gc(Cq.n);
+  const int n = F.n, hn = Cq.n;
+  const T inv_h2 = T(1.0 / (F.L.h * F.L.h)), w = T(1.0 / (1 << D));
+  for (int j = threadIdx.x; j < Cq.ncell; j += blockDim.x) {
+    const int qx = j % hn, qy = (j / hn) % hn, qz = D == 3 ? j / (hn * hn) : 0;
+    T sp = T(0), sr = T(0);
+#pragma unroll
+    for (int dz = 0; dz < (D == 3 ? 2 : 1); dz++)
+#pragma unroll
+      for (int dy = 0; dy < 2; dy++)
+#pragma unroll
+        for (int dx = 0; dx < 2; dx++) {
+          const int x = 2 * qx + dx, y = 2 * qy + dy, z = 2 * qz + dz;
+          const int c = x + n * (y + n * z);
+          const int t = G.idx(x, y, z);
+          sp = sp + F.tile[t];
+          sr = sr + resid_cell<T, D>(V.st, F.stb, F.tile, t, G.sy, G.sz, F.ncell, c, inv_h2, F.b[c]);
+        }
+    Cq.tile[Gc.idx(qx, qy, qz)] = sp * w;
+    Cq.b[j] = sr * w;
+  }
+  __syncthreads();
+}
+
+// FAS right-hand side b <- A phi + b (restricted residual), old <- phi
+template <typename T, int D>
+__device__ void tail_fas(const GmgView<T> &V, const TailLevel<T, D> &Q) {
+  tail_walls<T, D>(Q, V.wneu);
+  const TileGeo<T, D> G(Q.n);
+  const int n = Q.n;
+  const T inv_h2 = T(1.0 / (Q.L.h * Q.L.h));
+  for (int c = threadIdx.x; c < Q.ncell; c += blockDim.x) {
+    int x, y, z;
+    cell_xyz<D>(c, n, &x, &y, &z);
+    const int t = G.idx(x, y, z);
+    const T ph = Q.tile[t];
+    T ap;
+    if (Q.stb < 0) {
+      ap = inv_h2 * (nb_sum<T, D>(Q.tile, t, G.sy, G.sz) - T(2 * D) * ph);
+    } else {
+      T diag;
+      const T sum = offdiag_st<T, D>(V.st + Q.stb, Q.tile, t, G.sy, G.sz, Q.ncell, c, &diag);
+      ap = diag * ph + sum;
+    }
+    Q.b[c] = ap + Q.b[c];
+    Q.old[c] = ph;
+  }
+  __syncthreads();
+}
+
+// correction phi - old of a single-block level at (x,y,z) in [-1,n]^D,
+// reflected at the walls (reading P)
+template <typename T, int D>
+__device__ __forceinline__ T tail_corr(const TailLevel<T, D> &Q, int x, int y, int z, int wneu) {
+  const TileGeo<T, D> G(Q.n);
+  const int n = Q.n;
+  T sg = T(1);
+  int p[3] = {x, y, z};
+#pragma unroll
+  for (int d = 0; d < D; d++) {
+    if (p[d] < 0) {
+      p[d] = 0;
+      sg *= ((wneu >> (2 * d)) & 1) ? T(1) : T(-1);
+    } else if (p[d] >= n) {
+      p[d] = n - 1;
+      sg *= ((wneu >> (2 * d + 1)) & 1) ? T(1) : T(-1);
+    }
+  }
+  const int c = p[0] + n * (p[1] + (D == 3 ? n * p[2] : 0));
+  return sg * (Q.tile[G.idx(p[0], p[1], p[2])] - Q.old[c]);
+}
+
+// phi_F += trilinear prolongation of the correction of level C
+template <typename T, int D>
+__device__ void tail_prolong(const GmgView<T> &V, const TailLevel<T, D> &F, const TailLevel<T, D> &Cq) {
+  const TileGeo<T, D> G(F.n);
+  const int n = F.n;
+  for (int c = threadIdx.x; c < F.ncell; c += blockDim.x) {
+    int x, y, z;
+    cell_xyz<D>(c, n, &x, &y, &z);
+    const int u[3] = {x >> 1, y >> 1, z >> 1};
+    const int o[3] = {(x & 1) ? 1 : -1, (y & 1) ? 1 : -1, (z & 1) ? 1 : -1};
+    T v = T(0);
+#pragma unroll
+    for (int sz = 0; sz < (D == 3 ? 2 : 1); sz++)
+#pragma unroll
+      for (int sy = 0; sy < 2; sy++)
+#pragma unroll
+        for (int sx = 0; sx < 2; sx++) {
+          T wgt = (sx ? T(0.25) : T(0.75)) * (sy ? T(0.25) : T(0.75));
+          if (D == 3) wgt *= sz ? T(0.25) : T(0.75);
+          v = v + wgt * tail_corr<T, D>(Cq, u[0] + sx * o[0], u[1] + sy * o[1], D == 3 ? u[2] + sz * o[2] : 0, V.wneu);
+        }
+    F.tile[G.idx(x, y, z)] += v;
+  }
+  __syncthreads();
+}
+
+template <typename T, int D>
+__device__ void tail_cycle(const GmgView<T> &V, const LevelSet &LS, const CycleArgs &A, int top,
+                           unsigned char *smem_raw) {
+  constexpr int kMaxTail = 12;
+  TailLevel<T, D> Q[kMaxTail];
+  T *p = reinterpret_cast<T *>(smem_raw);
+  for (int l = top; l >= A.l_lo; l--) {
+    TailLevel<T, D> &q = Q[top - l];
+    q.L = LS.lv[l - LS.lmin];
+    q.n = q.L.n;
+    q.ncell = D == 3 ? q.n * q.n * q.n : q.n * q.n;
+    q.stb = V.st_base[q.L.first];
+    q.tile = p;
+    p += TileGeo<T, D>(q.n).size;
+    q.b = p;
+    p += q.ncell;
+    q.old = p;
+    p += q.ncell;
+  }
+  {  // phi and b of the top tail level from global memory
+    const TailLevel<T, D> &q = Q[0];
+    const TileGeo<T, D> G(q.n);
+    for (int c = threadIdx.x; c < q.ncell; c += blockDim.x) {
+      int x, y, z;
+      cell_xyz<D>(c, q.n, &x, &y, &z);
+      q.tile[G.idx(x, y, z)] = V.phi[q.L.poff + c];
+      q.b[c] = V.b[q.L.off + c];
+    }
+    __syncthreads();
+  }
+  for (int l = top; l > A.l_lo; l--) {
+    const TailLevel<T, D> &F = Q[top - l], &Cq = Q[top - l + 1];
+    for (int k = 0; k < A.n_down; k++) {
+      tail_smooth<T, D>(V, F, 0);
+      tail_smooth<T, D>(V, F, 1);
+    }
+    tail_resid_restrict<T, D>(V, F, Cq);
+    tail_fas<T, D>(V, Cq);
+  }
+  {  // exact solve on l_lo, FP64 accumulation, one warp per row
+    const TailLevel<T, D> &q = Q[top - A.l_lo];
+    const TileGeo<T, D> G(q.n);
+    const int lane = threadIdx.x & 31;
+    for (int row = threadIdx.x >> 5; row < A.nc; row += kThreads / 32) {
+      const double *a = A.cinv + (size_t)row * A.nc;
+      double s = 0.0;
+      for (int j = lane; j < A.nc; j += 32) s += a[j] * (double)q.b[j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) {
+        int x, y, z;
+        cell_xyz<D>(row, q.n, &x, &y, &z);
+        q.tile[G.idx(x, y, z)] = T(s);
+      }
+    }
+    __syncthreads();
+  }
+  for (int l = A.l_lo + 1; l <= top; l++) {
+    const TailLevel<T, D> &F = Q[top - l], &Cq = Q[top - l + 1];
+    tail_prolong<T, D>(V, F, Cq);
+    for (int k = 0; k < A.n_up; k++) {
+      tail_smooth<T, D>(V, F, 0);
+      tail_smooth<T, D>(V, F, 1);
+    }
+  }
+  {  // phi of the top tail level back to global memory
+    const TailLevel<T, D> &q = Q[0];
+    const TileGeo<T, D> G(q.n);
+    for (int c = threadIdx.x; c < q.ncell; c += blockDim.x) {
+      int x, y, z;
+      cell_xyz<D>(c, q.n, &x, &y, &z);
+      V.phi[q.L.poff + c] = q.tile[G.idx(x, y, z)];
+    }
+  }
+}
+
 template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kThreads) k_cycle_coop(GmgView<T> V, LevelSet LS, CycleArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -155,34 +398,7 @@ __global__ void __launch_bounds__(kThreads) k_cycle_coop(GmgView<T> V, LevelSet 
     // single-block levels l_one .. l_lo: CTA 0 runs the bottom of the cycle
     // (sweeps, restriction, FAS, coarse solve, prolongation, sweeps) with
     // block-level barriers only
-    if (blockIdx.x == 0) {
-      const int top = A.l_one < A.l_hi ? A.l_one : A.l_hi;
-      for (int l = top; l > A.l_lo; l--) {
-        const LvArgs L = GMG_LV(l), Lp = GMG_LV(l - 1);
-        for (int k = 0; k < A.n_down; k++)
-          for (int c = 0; c < 2; c++) {
-            smooth_any<T, D, NT>(V, L, Lp, L.first, c, smem_raw);
-            __syncthreads();
-          }
-        resid_restrict_any<T, D, NT>(V, L, Lp, L.first, smem_raw);
-        __syncthreads();
-        const LvArgs Lpp = l - 2 >= LS.lmin ? GMG_LV(l - 2) : Lp;
-        fas_any<T, D, NT>(V, Lp, Lpp, Lp.first, smem_raw);
-        __syncthreads();
-      }
-      coarse_rows<T>(V, GMG_LV(A.l_lo), A.cinv, A.nc, threadIdx.x >> 5, kThreads / 32);
-      __syncthreads();
-      for (int l = A.l_lo + 1; l <= top; l++) {
-        const LvArgs L = GMG_LV(l), Lp = GMG_LV(l - 1);
-        prolong_any<T, D, NT>(V, L, Lp, L.first, smem_raw);
-        __syncthreads();
-        for (int k = 0; k < A.n_up; k++)
-          for (int c = 0; c < 2; c++) {
-            smooth_any<T, D, NT>(V, L, Lp, L.first, c, smem_raw);
-            __syncthreads();
-          }
-      }
-    }
+    if (blockIdx.x == 0) tail_cycle<T, D>(V, LS, A, A.l_one < A.l_hi ? A.l_one : A.l_hi, smem_raw);
   } else {
     coarse_rows<T>(V, GMG_LV(A.l_lo), A.cinv, A.nc, blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5),
                    (int)G * (kThreads / 32));

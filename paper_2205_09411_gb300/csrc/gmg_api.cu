@@ -295,17 +295,26 @@ int coop_cycle(gmg_tree *t, cudaStream_t s, int ls) {
   // the single-block levels at the bottom run on one CTA when the coarse
   // solve is small enough for one CTA
   int l_one = t->lmin - 1;
-  if (t->nc <= 256)
-    for (int l = t->lmin; l <= ls && t->lev(l).count == 1; l++) l_one = l;
+  size_t tail_bytes = 0;
+  if (t->nc <= 256 && t->cb[0] * t->cb[1] * t->cb[2] == 1)
+    for (int l = t->lmin; l <= ls && t->lev(l).count == 1; l++) {
+      const int n = t->lev(l).n;
+      const size_t add = sizeof(T) * ((size_t)TileGeo<T, D>(n).size + 2 * (size_t)t->lev(l).ncell);
+      if (tail_bytes + add > 160 * 1024 || l - t->lmin >= 11) break;
+      tail_bytes += add;
+      l_one = l;
+    }
   CycleArgs A{t->lmin, ls, t->prm.n_down, t->prm.n_up, t->nc, t->d_cinv, t->d_bar, t->spin_limit, l_one};
   size_t sm = 0;
   int maxb = 1;
   for (int l = t->lmin; l <= ls; l++) {
+    if (l <= l_one) continue;  // held in shared memory by the tail
     const int hm = t->lev(l).n / 2 + 2;
     sm = std::max(sm, tile_bytes<T>(t, l));
     sm = std::max(sm, sizeof(T) * (size_t)(D == 3 ? hm * hm * hm : hm * hm));
     maxb = std::max(maxb, t->lev(l).count);
   }
+  sm = std::max(sm, tail_bytes);
   int rc = GMG_OK;
   with_nt<D>(t->N, [&](auto nt) {
     constexpr int NT = decltype(nt)::value;

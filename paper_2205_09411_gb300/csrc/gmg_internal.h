@@ -121,7 +121,7 @@ struct gmg_tree {
   GraphSlot graphs[kGraphSlots];
   bool use_graphs = true;
   bool use_coop = true;       // coarse levels in one cooperative launch
-  bool use_fused = true;      // temporally blocked FP32 sweeps on uniform levels
+  bool use_fused = false;     // temporally blocked FP32 sweeps on uniform levels
   std::vector<char> level_complete;  // every block has all 26 neighbours on its level (or walls)
   int coop_split = 0;         // highest level run inside that launch
   long long spin_limit = 1LL << 24;
