@@ -135,14 +135,16 @@ __device__ __forceinline__ void coarse_rows(const GmgView<T> &V, const LvArgs &L
 template <typename T, int D>
 struct TailLevel {
   T *tile, *b, *old;
+  unsigned char *flag;  // cells with a non-regular stencil (cut block)
   int n, ncell;
   long long stb;  // stencil offset of the level's block (-1: regular)
   LvArgs L;
 };
 
 template <typename T, int D>
-__device__ __forceinline__ size_t tail_level_elems(int n) {
-  return (size_t)TileGeo<T, D>(n).size + 2 * (size_t)(D == 3 ? n * n * n : n * n);
+__host__ __device__ __forceinline__ size_t tail_level_bytes(int n) {
+  const int nc = D == 3 ? n * n * n : n * n;
+  return sizeof(T) * ((size_t)TileGeo<T, D>(n).size + 2 * (size_t)nc) + (size_t)((nc + 15) / 16 * 16);
 }
 
 // wall ghosts of a single-block level (all faces are walls): sign * mirror
@@ -175,7 +177,7 @@ __device__ void tail_smooth(const GmgView<T> &V, const TailLevel<T, D> &Q, int c
     const int c = x + n * (y + n * z);
     const int t = G.idx(x, y, z);
     T nv;
-    if (Q.stb < 0) {
+    if (Q.stb < 0 || !Q.flag[c]) {
       nv = (nb_sum<T, D>(Q.tile, t, G.sy, G.sz) - h2 * Q.b[c]) * inv2d;
     } else {
       T diag;
@@ -208,7 +210,8 @@ __device__ void tail_resid_restrict(const GmgView<T> &V, const TailLevel<T, D> &
           const int c = x + n * (y + n * z);
           const int t = G.idx(x, y, z);
           sp = sp + F.tile[t];
-          sr = sr + resid_cell<T, D>(V.st, F.stb, F.tile, t, G.sy, G.sz, F.ncell, c, inv_h2, F.b[c]);
+          sr = sr + resid_cell<T, D>(V.st, (F.stb >= 0 && F.flag[c]) ? F.stb : -1, F.tile, t, G.sy, G.sz, F.ncell,
+                                     c, inv_h2, F.b[c]);
         }
     Cq.tile[Gc.idx(qx, qy, qz)] = sp * w;
     Cq.b[j] = sr * w;
@@ -229,7 +232,7 @@ __device__ void tail_fas(const GmgView<T> &V, const TailLevel<T, D> &Q) {
     const int t = G.idx(x, y, z);
     const T ph = Q.tile[t];
     T ap;
-    if (Q.stb < 0) {
+    if (Q.stb < 0 || !Q.flag[c]) {
       ap = inv_h2 * (nb_sum<T, D>(Q.tile, t, G.sy, G.sz) - T(2 * D) * ph);
     } else {
       T diag;
@@ -308,6 +311,13 @@ __device__ void tail_cycle(const GmgView<T> &V, const LevelSet &LS, const CycleA
     p += q.ncell;
     q.old = p;
     p += q.ncell;
+    q.flag = reinterpret_cast<unsigned char *>(p);
+    p += (q.ncell + 15) / 16 * 16 / sizeof(T);
+  }
+  for (int l = top; l >= A.l_lo; l--) {  // flags of cut levels
+    const TailLevel<T, D> &q = Q[top - l];
+    if (q.stb >= 0)
+      for (int c = threadIdx.x; c < q.ncell; c += blockDim.x) q.flag[c] = V.spec[q.stb / (2 * D + 1) + c];
   }
   {  // phi and b of the top tail level from global memory
     const TailLevel<T, D> &q = Q[0];

@@ -139,10 +139,10 @@ __global__ void __launch_bounds__(kThreads) k_smooth_tb(GmgView<T> V, LvArgs L, 
           const int ox = x < 0 ? -1 : (x >= n ? 1 : 0), oy = y < 0 ? -1 : (y >= n ? 1 : 0);
           const int oz = D == 3 ? (z < 0 ? -1 : (z >= n ? 1 : 0)) : 0;
           const long long stb = s_stb[nbr_slot(ox, oy, oz)];
-          if (stb < 0) {
+          const int c = (x - ox * n) + n * ((y - oy * n) + (D == 3 ? n * (z - oz * n) : 0));
+          if (stb < 0 || !V.spec[stb / (2 * D + 1) + c]) {
             nv = (nb_sum<T, D>(tp, t, F::SY, F::SZ) - h2 * tb[t]) * inv2d;
           } else {
-            const int c = (x - ox * n) + n * ((y - oy * n) + (D == 3 ? n * (z - oz * n) : 0));
             T diag;
             const T sum = offdiag_st<T, D>(V.st + stb, tp, t, F::SY, F::SZ, F::NC, c, &diag);
             nv = (tb[t] - sum) / diag;

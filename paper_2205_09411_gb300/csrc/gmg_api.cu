@@ -178,6 +178,7 @@ GmgView<double> view<double>(gmg_tree *t) {
   v.b = t->d_b;
   v.old = t->d_old;
   v.st = t->d_st;
+  v.spec = t->d_spec;
   v.wneu = 0;
   for (int w = 0; w < 6; w++) v.wneu |= (t->wall_type[w] == GMG_WALL_NEUMANN ? 1 : 0) << w;
   return v;
@@ -198,6 +199,7 @@ GmgView<float> view<float>(gmg_tree *t) {
   v.b = t->f_b;
   v.old = t->f_old;
   v.st = t->f_st;
+  v.spec = t->d_spec;
   v.wneu = 0;
   for (int w = 0; w < 6; w++) v.wneu |= (t->wall_type[w] == GMG_WALL_NEUMANN ? 1 : 0) << w;
   return v;
@@ -299,7 +301,7 @@ int coop_cycle(gmg_tree *t, cudaStream_t s, int ls) {
   if (t->nc <= 256 && t->cb[0] * t->cb[1] * t->cb[2] == 1)
     for (int l = t->lmin; l <= ls && t->lev(l).count == 1; l++) {
       const int n = t->lev(l).n;
-      const size_t add = sizeof(T) * ((size_t)TileGeo<T, D>(n).size + 2 * (size_t)t->lev(l).ncell);
+      const size_t add = tail_level_bytes<T, D>(n);
       if (tail_bytes + add > 160 * 1024 || l - t->lmin >= 11) break;
       tail_bytes += add;
       l_one = l;
@@ -571,7 +573,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t nbr, pnb, parent, pofs, flags, leaf, cbase, st_base, bt_base, phi, b, old, fphi, fb, fold, st, fst, bterm, cinv,
-      partials, red, bar, total;
+      partials, red, bar, spec, total;
 };
 
 Layout layout(const gmg_tree *t) {
@@ -605,6 +607,7 @@ Layout layout(const gmg_tree *t) {
   L.partials = take(nb * 3 * sizeof(double));
   L.red = take(4 * sizeof(double));
   L.bar = take(sizeof(GridBar));
+  L.spec = take(t->spec_h.size());
   L.total = o;
   return L;
 }
@@ -801,6 +804,7 @@ int gmg_tree_bind(gmg_tree *t, void *device_ptr, size_t bytes) {
   t->d_partials = reinterpret_cast<double *>(w + L.partials);
   t->d_red = reinterpret_cast<double *>(w + L.red);
   t->d_bar = reinterpret_cast<GridBar *>(w + L.bar);
+  t->d_spec = reinterpret_cast<unsigned char *>(w + L.spec);
   const size_t nb = t->blocks.size();
   std::vector<long long> cbase(nb);
   for (size_t i = 0; i < nb; i++) {
@@ -828,6 +832,7 @@ int gmg_tree_bind(gmg_tree *t, void *device_ptr, size_t bytes) {
     CUDA_TRY(cudaMemcpy(t->d_st, t->stencil_h.data(), t->stencil_h.size() * sizeof(double), cudaMemcpyHostToDevice));
     k_to_float<<<grid_for((long long)t->stencil_h.size()), 256>>>(t->d_st, t->f_st, (long long)t->stencil_h.size());
   }
+  if (!t->spec_h.empty()) CUDA_TRY(cudaMemcpy(t->d_spec, t->spec_h.data(), t->spec_h.size(), cudaMemcpyHostToDevice));
   if (!t->bterm_h.empty())
     CUDA_TRY(cudaMemcpy(t->d_bterm, t->bterm_h.data(), t->bterm_h.size() * sizeof(double), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(t->d_cinv, t->cinv_h.data(), (size_t)t->nc * t->nc * sizeof(double), cudaMemcpyHostToDevice));

@@ -61,6 +61,7 @@ struct GmgView {
   const int *leaf_ids;   // [n_leaf_blocks]
   T *phi, *b, *old;      // level fields (all levels, block-contiguous)
   const T *st;           // stencil pool: per cut block (2D+1) x ncell, [diag, -x, +x, -y, +y, -z, +z]
+  const unsigned char *spec;  // per cut block ncell flags at st_base/(2D+1): 1 = stencil differs from the regular one
   int wneu;              // bit w set: wall w is Neumann (ghost +phi), else Dirichlet (-phi)
 };
 
@@ -90,6 +91,7 @@ struct gmg_tree {
   std::vector<long long> st_base_h, bt_base_h;
   std::vector<double> stencil_h;  // concatenated per cut block: (2D+1) x ncell
   std::vector<double> bterm_h;    // concatenated per block with boundary terms: ncell
+  std::vector<uint8_t> spec_h;    // per cut block ncell flags (any d < 1), parallel to stencil_h
   std::vector<double> dist_h;     // per cut block: ncell x 2D distances (inspection)
   std::vector<long long> dist_base_h;
   std::vector<uint8_t> mask_h;    // per block ncell (inspection)
@@ -107,6 +109,7 @@ struct gmg_tree {
   float *f_phi = nullptr, *f_b = nullptr, *f_old = nullptr;
   double *d_st = nullptr, *d_bterm = nullptr, *d_cinv = nullptr, *d_partials = nullptr, *d_red = nullptr;
   float *f_st = nullptr;
+  unsigned char *d_spec = nullptr;
   double *h_red = nullptr;  // pinned host mirror of d_red
   long long launches = 0;
 

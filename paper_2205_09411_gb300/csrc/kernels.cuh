@@ -182,11 +182,20 @@ struct TileGeo {
   __host__ __device__ int idx(int x, int y, int z) const { return (x + X0) + sy * (y + 1) + (D == 3 ? sz * (z + 1) : 0); }
 };
 
-// Shared memory of the level kernels: the tile and the block's dense b.
+// Shared memory of the level kernels: the tile, the block's dense b and the
+// per-cell flags of a cut block (1 = the cell's stencil differs from the
+// regular one).
 template <typename T>
 __host__ __device__ inline size_t level_smem_bytes(int D, int n) {
   const int tile = D == 3 ? TileGeo<T, 3>(n).size : TileGeo<T, 2>(n).size;
-  return sizeof(T) * (size_t)(tile + (D == 3 ? n * n * n : n * n));
+  const int nc = D == 3 ? n * n * n : n * n;
+  return sizeof(T) * (size_t)(tile + nc) + (size_t)((nc + 15) / 16 * 16);
+}
+
+// The flags of a cut block follow its dense b in shared memory.
+template <typename T>
+__device__ __forceinline__ unsigned char *level_flags(T *sbv, int ncell) {
+  return reinterpret_cast<unsigned char *>(sbv + ncell);
 }
 
 // Stage phi of block `bid` with its face ghosts into the tile and, if
@@ -197,7 +206,7 @@ __host__ __device__ inline size_t level_smem_bytes(int D, int n) {
 // (reading G) are filled once the copies have landed.  Ends with a barrier.
 template <typename T, int D, int NT>
 __device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, T *tile,
-                          T *sbv = nullptr) {
+                          T *sbv = nullptr, unsigned char *sflag = nullptr, long long sb = -1) {
   __shared__ int s_nb[6];
   __shared__ int s_fl;
   const int n = NT ? NT : L.n;
@@ -224,6 +233,14 @@ __device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
       const int x = c % n, y = (c / n) % n, z = D == 3 ? c / (n * n) : 0;
       cp_async_elem(tile + G.idx(x, y, z), V.phi + pbase + c);
       if (sbv) cp_async_elem(sbv + c, V.b + base + c);
+    }
+  }
+  if (sflag && sb >= 0) {  // which cells of a cut block have a non-regular stencil
+    const unsigned char *src = V.spec + sb / (2 * D + 1);
+    if (ncell % 16 == 0 && ((size_t)src & 15) == 0) {
+      for (int i = threadIdx.x; i < ncell / 16; i += blockDim.x) cp_async16(sflag + 16 * i, src + 16 * i);
+    } else {
+      for (int c = threadIdx.x; c < ncell; c += blockDim.x) sflag[c] = src[c];
     }
   }
   __syncthreads();
@@ -314,9 +331,10 @@ __device__ void smooth_block(const GmgView<T> &V, const LvArgs &L, const LvArgs 
   const TileGeo<T, D> G(n);
   T *tile = reinterpret_cast<T *>(smem_raw);
   T *sbv = tile + G.size;
+  unsigned char *sfl = level_flags(sbv, NCELL);
   const long long pbase = L.poff + (long long)(bid - L.first) * NCELL;
   const long long sb = V.st_base[bid];
-  load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv);
+  load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv, sfl, sb);
   const T h2 = T(L.h * L.h), inv2d = T(1.0 / (2 * D));
   const int nhalf = NCELL / 2;
   for (int j = threadIdx.x; j < nhalf; j += blockDim.x) {
@@ -326,7 +344,7 @@ __device__ void smooth_block(const GmgView<T> &V, const LvArgs &L, const LvArgs 
     const int c = x + n * (y + n * z);
     const int t = G.idx(x, y, z);
     T nv;
-    if (sb < 0) {
+    if (sb < 0 || !sfl[c]) {
       nv = (nb_sum<T, D>(tile, t, G.sy, G.sz) - h2 * sbv[c]) * inv2d;
     } else {
       T diag;
@@ -352,9 +370,10 @@ __device__ void resid_restrict_block(const GmgView<T> &V, const LvArgs &L, const
   const TileGeo<T, D> G(n);
   T *tile = reinterpret_cast<T *>(smem_raw);
   T *sbv = tile + G.size;
+  unsigned char *sfl = level_flags(sbv, NCELL);
   const long long sb = V.st_base[bid];
   const int P = V.parent[bid], po = V.pofs[bid];
-  load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv);
+  load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv, sfl, sb);
   const T inv_h2 = T(1.0 / (L.h * L.h));
   const int pofs[3] = {po & 1023, (po >> 10) & 1023, (po >> 20) & 1023};
   const long long pbase = Lp.off + (long long)(P - Lp.first) * Lp.ncell;
@@ -375,7 +394,7 @@ __device__ void resid_restrict_block(const GmgView<T> &V, const LvArgs &L, const
           const int c = x + n * (y + n * z);
           const int t = G.idx(x, y, z);
           sp = sp + tile[t];
-          sr = sr + resid_cell<T, D>(V.st, sb, tile, t, G.sy, G.sz, NCELL, c, inv_h2, sbv[c]);
+          sr = sr + resid_cell<T, D>(V.st, (sb >= 0 && sfl[c]) ? sb : -1, tile, t, G.sy, G.sz, NCELL, c, inv_h2, sbv[c]);
         }
     const long long pc = pbase + (pofs[0] + qx) + pn * ((pofs[1] + qy) + (D == 3 ? pn * (pofs[2] + qz) : 0));
     V.phi[pc + pdelta] = sp * w;
@@ -406,8 +425,9 @@ __device__ void fas_block(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
   }
   T *tile = reinterpret_cast<T *>(smem_raw);
   T *sbv = tile + G.size;
+  unsigned char *sfl = level_flags(sbv, NCELL);
   const long long sb = V.st_base[bid];
-  load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv);
+  load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv, sfl, sb);
   const T inv_h2 = T(1.0 / (L.h * L.h));
   for (int c = threadIdx.x; c < NCELL; c += blockDim.x) {
     int x, y, z;
@@ -415,7 +435,7 @@ __device__ void fas_block(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
     const int t = G.idx(x, y, z);
     const T ph = tile[t];
     T ap;
-    if (sb < 0) {
+    if (sb < 0 || !sfl[c]) {
       ap = inv_h2 * (nb_sum<T, D>(tile, t, G.sy, G.sz) - T(2 * D) * ph);
     } else {
       T diag;
@@ -600,9 +620,10 @@ __global__ void __launch_bounds__(kThreads) k_resnorm(GmgView<T> V, LvArgs L, Lv
   const TileGeo<T, D> G(n);
   T *tile = reinterpret_cast<T *>(smem_raw);
   T *sbv = tile + G.size;
+  unsigned char *sfl = level_flags(sbv, NCELL);
   const long long base = L.off + (long long)(bid - L.first) * NCELL;
   const long long sb = V.st_base[bid];
-  load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv);
+  load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv, sfl, sb);
   const T inv_h2 = T(1.0 / (L.h * L.h));
   // the norms only steer the stopping test: squares and maxima of the
   // rounded residual are accumulated in FP32 per thread, then in FP64
@@ -611,7 +632,8 @@ __global__ void __launch_bounds__(kThreads) k_resnorm(GmgView<T> V, LvArgs L, Lv
     int x, y, z;
     cell_xyz<D>(c, n, &x, &y, &z);
     const T bb = sbv[c];
-    const float r = (float)resid_cell<T, D>(V.st, sb, tile, G.idx(x, y, z), G.sy, G.sz, NCELL, c, inv_h2, bb);
+    const float r = (float)resid_cell<T, D>(V.st, (sb >= 0 && sfl[c]) ? sb : -1, tile, G.idx(x, y, z), G.sy, G.sz,
+                                            NCELL, c, inv_h2, bb);
     if (rout) rout[base + c] = r;
     s2f = fmaf(r, r, s2f);
     mxf = fmaxf(mxf, fabsf(r));

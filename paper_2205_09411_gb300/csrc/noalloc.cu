@@ -88,6 +88,7 @@ void launch_resnorm(gmg_tree *t, int l, double *partials, cudaStream_t s) {
   V.b = t->d_b;
   V.old = t->d_old;
   V.st = t->d_st;
+  V.spec = t->d_spec;
   V.wneu = 0;
   for (int w = 0; w < 6; w++) V.wneu |= (t->wall_type[w] == GMG_WALL_NEUMANN ? 1 : 0) << w;
   const gmg::LevelInfo &Li = t->lev(l);

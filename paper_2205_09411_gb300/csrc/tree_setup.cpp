@@ -399,6 +399,7 @@ int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, do
   T->dist_base_h.assign(nb, -1);
   T->mask_base_h.assign(nb, -1);
   T->stencil_h.clear();
+  T->spec_h.clear();
   T->bterm_h.clear();
   T->dist_h.clear();
   T->mask_h.clear();
@@ -503,6 +504,11 @@ int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, do
     if (cut) {
       T->st_base_h[id] = (long long)T->stencil_h.size();
       T->stencil_h.insert(T->stencil_h.end(), st.begin(), st.end());
+      for (int c = 0; c < nc; c++) {  // cells whose stencil differs from the regular one
+        bool special = false;
+        for (int k = 0; k < 2 * D; k++) special = special || dd[(size_t)c * 2 * D + k] < 1.0;
+        T->spec_h.push_back(special ? 1 : 0);
+      }
       T->dist_base_h[id] = (long long)T->dist_h.size();
       T->dist_h.insert(T->dist_h.end(), dd.begin(), dd.end());
     }
