@@ -59,6 +59,7 @@ __device__ __forceinline__ bool grid_sync(GridBar *bar, unsigned int nctas, long
   return s_ok != 0;
 }
 
+// level descriptors of the cycle, staged in shared memory by the kernel
 struct LevelSet {
   LvArgs lv[kMaxLevels];
   int lmin;
@@ -297,7 +298,8 @@ template <typename T, int D>
 __device__ void tail_cycle(const GmgView<T> &V, const LevelSet &LS, const CycleArgs &A, int top,
                            unsigned char *smem_raw) {
   constexpr int kMaxTail = 12;
-  TailLevel<T, D> Q[kMaxTail];
+  __shared__ TailLevel<T, D> Q[kMaxTail];  // descriptors in shared memory, not per-thread local memory
+  if (threadIdx.x == 0) {
   T *p = reinterpret_cast<T *>(smem_raw);
   for (int l = top; l >= A.l_lo; l--) {
     TailLevel<T, D> &q = Q[top - l];
@@ -314,6 +316,8 @@ __device__ void tail_cycle(const GmgView<T> &V, const LevelSet &LS, const CycleA
     q.flag = reinterpret_cast<unsigned char *>(p);
     p += (q.ncell + 15) / 16 * 16 / sizeof(T);
   }
+  }
+  __syncthreads();
   for (int l = top; l >= A.l_lo; l--) {  // flags of cut levels
     const TailLevel<T, D> &q = Q[top - l];
     if (q.stb >= 0)
@@ -377,8 +381,13 @@ __device__ void tail_cycle(const GmgView<T> &V, const LevelSet &LS, const CycleA
 }
 
 template <typename T, int D, int NT>
-__global__ void __launch_bounds__(kThreads) k_cycle_coop(GmgView<T> V, LevelSet LS, CycleArgs A) {
+__global__ void __launch_bounds__(kThreads) k_cycle_coop(GmgView<T> V, const LvArgs *lvtab, int nlev, int lmin,
+                                                         CycleArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ LevelSet LS;  // level table in shared memory (indexed by level at run time)
+  if (threadIdx.x < nlev) LS.lv[threadIdx.x] = lvtab[threadIdx.x];
+  if (threadIdx.x == 0) LS.lmin = lmin;
+  __syncthreads();
   const unsigned int G = gridDim.x;
 #define GMG_LV(l) LS.lv[(l)-LS.lmin]
   // levels l_hi .. l_one + 1: every CTA, grid barrier between phases

@@ -291,9 +291,6 @@ size_t tile_bytes(const gmg_tree *t, int l) {
 template <typename T, int D>
 int coop_cycle(gmg_tree *t, cudaStream_t s, int ls) {
   GmgView<T> V = view<T>(t);
-  LevelSet LS{};
-  LS.lmin = t->lmin;
-  for (int l = t->lmin; l <= t->lmax; l++) LS.lv[l - t->lmin] = lv(t, l);
   // the single-block levels at the bottom run on one CTA when the coarse
   // solve is small enough for one CTA
   int l_one = t->lmin - 1;
@@ -345,7 +342,10 @@ int coop_cycle(gmg_tree *t, cudaStream_t s, int ls) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    launch(t, s, 3, prec_of<T>(), t->lmin, [&] { cudaLaunchKernelEx(&cfg, kern, V, LS, A); });
+    const LvArgs *tab = t->d_lvtab;
+    const int nlev = (int)t->levels.size();
+    const int lmin = t->lmin;
+    launch(t, s, 3, prec_of<T>(), t->lmin, [&] { cudaLaunchKernelEx(&cfg, kern, V, tab, nlev, lmin, A); });
   });
   if (rc) return rc;
   CUDA_TRY(cudaGetLastError());
@@ -573,7 +573,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t nbr, pnb, parent, pofs, flags, leaf, cbase, st_base, bt_base, phi, b, old, fphi, fb, fold, st, fst, bterm, cinv,
-      partials, red, bar, spec, total;
+      partials, red, bar, spec, lvtab, total;
 };
 
 Layout layout(const gmg_tree *t) {
@@ -608,6 +608,7 @@ Layout layout(const gmg_tree *t) {
   L.red = take(4 * sizeof(double));
   L.bar = take(sizeof(GridBar));
   L.spec = take(t->spec_h.size());
+  L.lvtab = take(kMaxLevels * sizeof(LvArgs));
   L.total = o;
   return L;
 }
@@ -805,6 +806,7 @@ int gmg_tree_bind(gmg_tree *t, void *device_ptr, size_t bytes) {
   t->d_red = reinterpret_cast<double *>(w + L.red);
   t->d_bar = reinterpret_cast<GridBar *>(w + L.bar);
   t->d_spec = reinterpret_cast<unsigned char *>(w + L.spec);
+  t->d_lvtab = reinterpret_cast<LvArgs *>(w + L.lvtab);
   const size_t nb = t->blocks.size();
   std::vector<long long> cbase(nb);
   for (size_t i = 0; i < nb; i++) {
@@ -833,6 +835,11 @@ int gmg_tree_bind(gmg_tree *t, void *device_ptr, size_t bytes) {
     k_to_float<<<grid_for((long long)t->stencil_h.size()), 256>>>(t->d_st, t->f_st, (long long)t->stencil_h.size());
   }
   if (!t->spec_h.empty()) CUDA_TRY(cudaMemcpy(t->d_spec, t->spec_h.data(), t->spec_h.size(), cudaMemcpyHostToDevice));
+  {
+    std::vector<LvArgs> tab(t->levels.size());
+    for (int l = t->lmin; l <= t->lmax; l++) tab[l - t->lmin] = lv(t, l);
+    CUDA_TRY(cudaMemcpy(t->d_lvtab, tab.data(), tab.size() * sizeof(LvArgs), cudaMemcpyHostToDevice));
+  }
   if (!t->bterm_h.empty())
     CUDA_TRY(cudaMemcpy(t->d_bterm, t->bterm_h.data(), t->bterm_h.size() * sizeof(double), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(t->d_cinv, t->cinv_h.data(), (size_t)t->nc * t->nc * sizeof(double), cudaMemcpyHostToDevice));

@@ -110,6 +110,7 @@ struct gmg_tree {
   double *d_st = nullptr, *d_bterm = nullptr, *d_cinv = nullptr, *d_partials = nullptr, *d_red = nullptr;
   float *f_st = nullptr;
   unsigned char *d_spec = nullptr;
+  gmg::LvArgs *d_lvtab = nullptr;  // per-level descriptors (phi in the first buffer)
   double *h_red = nullptr;  // pinned host mirror of d_red
   long long launches = 0;
 
