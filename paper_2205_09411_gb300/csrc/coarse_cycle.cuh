@@ -347,7 +347,7 @@ __device__ void tail_cycle(const GmgView<T> &V, const LevelSet &LS, const CycleA
     const TailLevel<T, D> &q = Q[top - A.l_lo];
     const TileGeo<T, D> G(q.n);
     const int lane = threadIdx.x & 31;
-    for (int row = threadIdx.x >> 5; row < A.nc; row += kThreads / 32) {
+    for (int row = threadIdx.x >> 5; row < A.nc; row += blockDim.x / 32) {
       const double *a = A.cinv + (size_t)row * A.nc;
       double s = 0.0;
       for (int j = lane; j < A.nc; j += 32) s += a[j] * (double)q.b[j];
@@ -381,7 +381,7 @@ __device__ void tail_cycle(const GmgView<T> &V, const LevelSet &LS, const CycleA
 }
 
 template <typename T, int D, int NT>
-__global__ void __launch_bounds__(kThreads) k_cycle_coop(GmgView<T> V, const LvArgs *lvtab, int nlev, int lmin,
+__global__ void __launch_bounds__(kCoopThreads) k_cycle_coop(GmgView<T> V, const LvArgs *lvtab, int nlev, int lmin,
                                                          CycleArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ LevelSet LS;  // level table in shared memory (indexed by level at run time)
@@ -419,8 +419,8 @@ __global__ void __launch_bounds__(kThreads) k_cycle_coop(GmgView<T> V, const LvA
     // block-level barriers only
     if (blockIdx.x == 0) tail_cycle<T, D>(V, LS, A, A.l_one < A.l_hi ? A.l_one : A.l_hi, smem_raw);
   } else {
-    coarse_rows<T>(V, GMG_LV(A.l_lo), A.cinv, A.nc, blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5),
-                   (int)G * (kThreads / 32));
+    coarse_rows<T>(V, GMG_LV(A.l_lo), A.cinv, A.nc, blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5),
+                   (int)(G * (blockDim.x / 32)));
   }
   if (A.l_hi > A.l_one && !grid_sync(A.bar, G, A.spin_limit)) return;
   for (int l = (A.l_one >= A.l_lo ? A.l_one : A.l_lo) + 1; l <= A.l_hi; l++) {

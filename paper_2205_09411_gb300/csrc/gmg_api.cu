@@ -321,7 +321,7 @@ int coop_cycle(gmg_tree *t, cudaStream_t s, int ls) {
     int per_sm = 0;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCoopThreads, sm);
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -334,7 +334,7 @@ int coop_cycle(gmg_tree *t, cudaStream_t s, int ls) {
     cudaMemsetAsync(&t->d_bar->count, 0, sizeof(unsigned int), s);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(G);
-    cfg.blockDim = dim3(kThreads);
+    cfg.blockDim = dim3(kCoopThreads);
     cfg.dynamicSmemBytes = sm;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];

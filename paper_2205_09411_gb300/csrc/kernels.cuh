@@ -11,7 +11,8 @@
 
 namespace gmg {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;      // threads per CTA of the per-level kernels
+constexpr int kCoopThreads = 512;  // threads per CTA of the cooperative coarse cycle
 
 // cells of a block of side n (compile-time when n is)
 #define NCELL (D == 3 ? n * n * n : n * n)
@@ -489,7 +490,7 @@ __device__ void prolong_block(const GmgView<T> &V, const LvArgs &L, const LvArgs
   if (NT) {
 #pragma unroll
     for (int k = 0; k < IV; k++) {
-      const int i = threadIdx.x + k * kThreads;
+      const int i = threadIdx.x + k * blockDim.x;
       if (i < NCELL / VEC) rv[k] = fine[i];
     }
   }
@@ -527,7 +528,7 @@ __device__ void prolong_block(const GmgView<T> &V, const LvArgs &L, const LvArgs
   if (NT) {
 #pragma unroll
     for (int k = 0; k < IV; k++) {
-      const int i = threadIdx.x + k * kThreads;
+      const int i = threadIdx.x + k * blockDim.x;
       if (i < NCELL / VEC) {
         T *e = reinterpret_cast<T *>(&rv[k]);
         const int c = i * VEC;
