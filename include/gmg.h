@@ -24,6 +24,12 @@
  *  - leaf-cell order: leaf blocks by increasing level, inside a level by
  *    increasing Morton code of the block's integer coordinates (x lowest
  *    bit); inside a block, cells x-fastest then y then z.
+ *  - right-hand-side slots: a tree holds nrhs (gmg_set_num_rhs, default 1)
+ *    independent copies of its level fields, one per right-hand side, that
+ *    share the tables, stencils and coarse inverse.  Every kernel runs the
+ *    (block, slot) pairs of a level in one launch.  Arrays that hold leaf
+ *    values of several slots are slot-major: slot r's leaf cells start at
+ *    r * n_leaf_cells.
  *  - a gmg_tree owns all the device memory it uses: either one workspace
  *    the caller binds (gmg_tree_bind with a device pointer) or one the
  *    library allocates itself (gmg_tree_bind with NULL).  It stays valid
@@ -103,7 +109,7 @@ typedef struct {
   double w_min;       /* unresolved-root threshold of Sec. 3.6.3 (0 = off)             */
 } gmg_params;
 
-typedef struct {
+typedef struct { /* per slot */
   int cycles;     /* V-cycles run (FP64) or defect-correction steps (mixed)    */
   double rel_l2;  /* final ||b - A phi||_2 / ||b||_2 over leaf cells           */
   double linf;    /* final max |b - A phi|                                      */
@@ -146,6 +152,11 @@ int gmg_set_walls(gmg_tree *tree, const int *types, const double *values, gmg_fn
  * (results are uploaded by gmg_tree_bind).  Errors: STATE if already bound. */
 int gmg_store_stencils(gmg_tree *tree, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, double phib_const);
 
+/* Number of right-hand-side slots (1 .. 65536) the workspace holds; call
+ * before gmg_tree_bind (default 1).  Errors: STATE after bind. */
+int gmg_set_num_rhs(gmg_tree *tree, int nrhs);
+int gmg_num_rhs(const gmg_tree *tree);
+
 /* Number of bytes of device workspace the tree needs (after
  * gmg_store_stencils): tables, FP64 and FP32 level fields, stencil pools,
  * coarse inverse, reduction scratch.  256-byte alignment is enough. */
@@ -157,21 +168,33 @@ int gmg_workspace_bytes(const gmg_tree *tree, size_t *bytes);
  * Errors: STATE before gmg_store_stencils, OOM, CUDA. */
 int gmg_tree_bind(gmg_tree *tree, void *device_ptr, size_t bytes);
 
-/* Right-hand side g on the leaf cells (leaf-cell order, FP64, host or device
- * by `where`): sets b = g - (moved boundary terms) - (Dirichlet wall terms)
- * and phi = 0 on every level (zero initial guess). */
+/* Right-hand sides g on the leaf cells (leaf-cell order, FP64, host or
+ * device by `where`; nrhs x n_leaf_cells values, slot-major): sets
+ * b = g - (moved boundary terms) - (Dirichlet wall terms) and phi = 0 on
+ * every level (zero initial guess) of every slot. */
 int gmg_set_rhs(gmg_tree *tree, const double *g, int where, void *stream);
-/* Initial guess on the leaf cells (covered cells get the mean of their children). */
+/* The same for slots slot0 .. slot0 + nslots - 1 only (g: nslots x
+ * n_leaf_cells); the other slots are untouched, so a slot can take a new
+ * right-hand side while the others are mid-solve.  Errors: INVALID_ARG for a
+ * slot range outside 0 .. nrhs - 1. */
+int gmg_set_rhs_slots(gmg_tree *tree, int slot0, int nslots, const double *g, int where, void *stream);
+/* Initial guess on the leaf cells of every slot (nrhs x n_leaf_cells;
+ * covered cells get the mean of their children). */
 int gmg_set_solution(gmg_tree *tree, const double *phi, int where, void *stream);
-/* Copies phi on the leaf cells to `phi` (host: synchronises the stream). */
+/* Copies phi on the leaf cells of every slot (nrhs x n_leaf_cells), or of
+ * slots slot0 .. slot0 + nslots - 1, to `phi` (host: synchronises the
+ * stream). */
 int gmg_get_solution(gmg_tree *tree, double *phi, int where, void *stream);
+int gmg_get_solution_slots(gmg_tree *tree, int slot0, int nslots, double *phi, int where, void *stream);
 
-/* n_cycles FAS V-cycles in FP64 (Sec. 2.2: N_down sweeps, restriction of
- * phi and of the residual, coarse right-hand side A phi + R r, exact coarse
- * solve, (bi/tri)linear prolongation of the correction, N_up sweeps). */
+/* n_cycles FAS V-cycles in FP64 on every slot (Sec. 2.2: N_down sweeps,
+ * restriction of phi and of the residual, coarse right-hand side
+ * A phi + R r, exact coarse solve, (bi/tri)linear prolongation of the
+ * correction, N_up sweeps). */
 int gmg_vcycle(gmg_tree *tree, int n_cycles, void *stream);
 /* Composite residual ||b - A phi||_2 over leaf cells, relative to ||b||_2,
- * and max |b - A phi|.  Synchronises the stream. */
+ * and max |b - A phi|, per slot (host arrays of nrhs doubles, or NULL).
+ * Synchronises the stream. */
 int gmg_residual(gmg_tree *tree, double *rel_l2, double *linf, void *stream);
 /* The same composite residual as gmg_residual, for callers that cannot
  * allocate device memory: code that runs inside another runtime's memory
@@ -188,13 +211,27 @@ int gmg_residual(gmg_tree *tree, double *rel_l2, double *linf, void *stream);
  * (cudaGetSymbolAddress), so make it before any stream capture.  All calls
  * share the array: calls that overlap on the GPU (several streams or host
  * threads at once) race and must be serialised by the caller.
+ * With several right-hand-side slots it evaluates slot 0.
  * Errors: INVALID_ARG, STATE (tree not bound), CUDA. */
 int gmg_residual_noalloc(gmg_tree *tree, double *out, void *stream);
-/* Solves to ||b - A phi||_2 <= rel_tol ||b||_2 from the current phi with
- * GMG_FP64 V-cycles or GMG_MIXED defect correction; stats may be NULL.
- * Synchronises once per cycle (the convergence test).
+/* Solves every slot to ||b - A phi||_2 <= rel_tol ||b||_2 from its current
+ * phi with GMG_FP64 V-cycles or GMG_MIXED defect correction.  A slot that
+ * reaches the tolerance is frozen: later cycles skip its blocks, so its
+ * result does not depend on the other slots.  stats: NULL or an array of
+ * nrhs entries.  Synchronises once per cycle (the convergence test).
  * Errors: NOT_CONVERGED after max_cycles, NONFINITE on NaN or growth. */
 int gmg_solve(gmg_tree *tree, int precision, double rel_tol, int max_cycles, gmg_stats *stats, void *stream);
+/* One step of the solve loop on the slots with active[r] != 0 (host array of
+ * nrhs ints; the other slots are left untouched): residual_only != 0 runs
+ * the composite residual only (the first step of a new right-hand side; in
+ * GMG_MIXED it also prepares the FP32 defect), else one V-cycle (FP64) or
+ * one defect-correction step (GMG_MIXED) followed by the residual.  Writes
+ * every slot's relative L2 and max residual into rel_l2 / linf (host arrays
+ * of nrhs doubles, or NULL; a slot not stepped keeps its last values).
+ * This is the unit a serving loop interleaves with gmg_set_rhs_slots.
+ * Synchronises the stream. */
+int gmg_iterate(gmg_tree *tree, int precision, const int *active, int residual_only, double *rel_l2, double *linf,
+                void *stream);
 
 /* Inspection (tests, tools): phi (which = 0) or b (which = 1) of every cell
  * of a level in canonical block order, FP64 host array; distances d

@@ -84,7 +84,12 @@ def load():
         "gmg_store_stencils": (C.c_int, [vp, C.POINTER(Lsf), FN, vp, C.c_double]),
         "gmg_workspace_bytes": (C.c_int, [vp, C.POINTER(sz)]),
         "gmg_tree_bind": (C.c_int, [vp, vp, sz]),
+        "gmg_set_num_rhs": (C.c_int, [vp, C.c_int]),
+        "gmg_num_rhs": (C.c_int, [vp]),
         "gmg_set_rhs": (C.c_int, [vp, vp, C.c_int, vp]),
+        "gmg_set_rhs_slots": (C.c_int, [vp, C.c_int, C.c_int, vp, C.c_int, vp]),
+        "gmg_get_solution_slots": (C.c_int, [vp, C.c_int, C.c_int, vp, C.c_int, vp]),
+        "gmg_iterate": (C.c_int, [vp, C.c_int, ip, C.c_int, dp, dp, vp]),
         "gmg_set_solution": (C.c_int, [vp, vp, C.c_int, vp]),
         "gmg_get_solution": (C.c_int, [vp, vp, C.c_int, vp]),
         "gmg_vcycle": (C.c_int, [vp, C.c_int, vp]),
@@ -139,11 +144,14 @@ class Tree:
 
     Life cycle: ``Tree(...)`` (host tree) -> ``set_walls`` -> ``store_stencils``
     (boundary set-up) -> ``bind()`` (device workspace) -> ``set_rhs`` ->
-    ``vcycle`` / ``solve`` -> ``solution``.
+    ``vcycle`` / ``solve`` -> ``solution``.  With ``nrhs`` > 1 the tree holds
+    that many right-hand-side slots: leaf arrays are then (nrhs, n_leaf_cells)
+    and residuals / statistics are per slot.
     """
 
     def __init__(self, dim, block_n, coarse_blocks=(1, 1, 1), lo=(0.0, 0.0, 0.0), h_root=None, max_level=1,
-                 refine=None, max_coarse_cells=0, n_down=2, n_up=2, eps_tol=1e-8, mask_factor=1.5, w_min=0.0):
+                 refine=None, max_coarse_cells=0, n_down=2, n_up=2, eps_tol=1e-8, mask_factor=1.5, w_min=0.0,
+                 nrhs=1):
         L = load()
         self.dim = dim
         cb = list(coarse_blocks) + [1] * (3 - len(coarse_blocks))
@@ -173,6 +181,14 @@ class Tree:
         _check(L.gmg_tree_info(self.h, C.byref(lmin), C.byref(lmax), C.byref(nleaf), C.byref(nb)))
         self.lmin, self.lmax, self.n_leaf_cells, self.n_blocks = lmin.value, lmax.value, nleaf.value, nb.value
         self.block_n = block_n
+        self.nrhs = 1
+        if nrhs != 1:
+            self.set_num_rhs(nrhs)
+
+    def set_num_rhs(self, nrhs):
+        """Right-hand-side slots of the workspace (before bind)."""
+        _check(load().gmg_set_num_rhs(self.h, int(nrhs)))
+        self.nrhs = int(nrhs)
 
     def close(self):
         if getattr(self, "h", None):
@@ -293,42 +309,81 @@ class Tree:
         assert a.dtype == torch.float64 and a.is_contiguous()
         return C.c_void_p(a.data_ptr()), (DEVICE if a.is_cuda else HOST)
 
+    def _leaf_shape(self, k):
+        return (self.n_leaf_cells,) if self.nrhs == 1 and k == 1 else (k, self.n_leaf_cells)
+
     def set_rhs(self, g, stream=None):
+        """g: (n_leaf_cells,) or (nrhs, n_leaf_cells), numpy or torch float64."""
+        assert int(np.prod(g.shape)) == self.nrhs * self.n_leaf_cells
         p, where = self._arr(g)
         _check(load().gmg_set_rhs(self.h, p, where, _stream_ptr(stream)))
 
+    def set_rhs_slots(self, slot0, g, stream=None):
+        """New right-hand sides for slots slot0 .. slot0 + k - 1 (g: (k, n) or (n,))."""
+        k = int(np.prod(g.shape)) // self.n_leaf_cells
+        assert k * self.n_leaf_cells == int(np.prod(g.shape))
+        p, where = self._arr(g)
+        _check(load().gmg_set_rhs_slots(self.h, int(slot0), k, p, where, _stream_ptr(stream)))
+
     def set_solution(self, phi, stream=None):
+        assert int(np.prod(phi.shape)) == self.nrhs * self.n_leaf_cells
         p, where = self._arr(phi)
         _check(load().gmg_set_solution(self.h, p, where, _stream_ptr(stream)))
 
     def solution(self, out=None, stream=None):
+        """Leaf values of every slot: (n_leaf_cells,) for one slot, else (nrhs, n_leaf_cells)."""
         if out is None:
-            out = np.zeros(self.n_leaf_cells)
+            out = np.zeros(self._leaf_shape(self.nrhs))
         p, where = self._arr(out)
         _check(load().gmg_get_solution(self.h, p, where, _stream_ptr(stream)))
         return out
 
+    def solution_slots(self, slot0, nslots=1, out=None, stream=None):
+        if out is None:
+            out = np.zeros((nslots, self.n_leaf_cells))
+        p, where = self._arr(out)
+        _check(load().gmg_get_solution_slots(self.h, int(slot0), int(nslots), p, where, _stream_ptr(stream)))
+        return out
+
     def get_level(self, level, which=0, stream=None):
+        """phi (which=0) or b (1) of every cell of a level (slot-major for several slots)."""
         nb, n = self.level_nblocks(level), self.level_n(level)
-        out = np.zeros(nb * n ** self.dim)
+        out = np.zeros(self.nrhs * nb * n ** self.dim)
         _check(load().gmg_get_level(self.h, level, which, out.ctypes.data_as(C.POINTER(C.c_double)),
                                     _stream_ptr(stream)))
-        return out
+        return out if self.nrhs == 1 else out.reshape(self.nrhs, -1)
 
     def vcycle(self, n=1, stream=None):
         _check(load().gmg_vcycle(self.h, n, _stream_ptr(stream)))
 
     def residual(self, stream=None):
-        r, m = C.c_double(), C.c_double()
-        _check(load().gmg_residual(self.h, C.byref(r), C.byref(m), _stream_ptr(stream)))
-        return r.value, m.value
+        """(relative L2, max) of the composite residual: floats for one slot, else arrays."""
+        r, m = np.zeros(self.nrhs), np.zeros(self.nrhs)
+        dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+        _check(load().gmg_residual(self.h, dp(r), dp(m), _stream_ptr(stream)))
+        return (float(r[0]), float(m[0])) if self.nrhs == 1 else (r, m)
+
+    def iterate(self, precision, active, residual_only=False, stream=None):
+        """One solve-loop step on the slots with active[r] != 0; returns (rel_l2, linf) arrays."""
+        a = np.ascontiguousarray(np.asarray(active, dtype=np.int32).reshape(self.nrhs))
+        r, m = np.zeros(self.nrhs), np.zeros(self.nrhs)
+        dp = lambda x: x.ctypes.data_as(C.POINTER(C.c_double))
+        _check(load().gmg_iterate(self.h, precision, a.ctypes.data_as(C.POINTER(C.c_int)), 1 if residual_only else 0,
+                                  dp(r), dp(m), _stream_ptr(stream)))
+        return r, m
 
     def solve(self, precision=FP64, rel_tol=1e-8, max_cycles=50, stream=None, check=True):
-        st = Stats()
-        rc = load().gmg_solve(self.h, precision, rel_tol, max_cycles, C.byref(st), _stream_ptr(stream))
+        """Solve every slot to rel_tol.  Returns rc, cycles, rel_l2, linf, bnorm (the
+        worst slot's for several slots) and, for several slots, 'slots': per-slot dicts."""
+        st = (Stats * self.nrhs)()
+        rc = load().gmg_solve(self.h, precision, rel_tol, max_cycles, st, _stream_ptr(stream))
         if check:
             _check(rc)
-        return dict(rc=rc, cycles=st.cycles, rel_l2=st.rel_l2, linf=st.linf, bnorm=st.bnorm)
+        slots = [dict(cycles=x.cycles, rel_l2=x.rel_l2, linf=x.linf, bnorm=x.bnorm) for x in st]
+        if self.nrhs == 1:
+            return dict(rc=rc, **slots[0])
+        return dict(rc=rc, cycles=max(x["cycles"] for x in slots), rel_l2=max(x["rel_l2"] for x in slots),
+                    linf=max(x["linf"] for x in slots), bnorm=min(x["bnorm"] for x in slots), slots=slots)
 
     OPTIONS = {"graphs": 1, "coarse_coop": 2, "spin_limit": 3, "fused_sweeps": 4}
 

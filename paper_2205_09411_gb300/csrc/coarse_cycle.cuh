@@ -66,11 +66,12 @@ struct LevelSet {
 };
 
 struct CycleArgs {
-  int l_lo, l_hi, n_down, n_up, nc;
+  int l_lo, l_hi, n_down, n_up;
+  int ncr, nroot;  // coarsest-level unknowns per root, independent roots (inverse per root)
   const double *cinv;
   GridBar *bar;
   long long spin_limit;
-  int l_one;  // levels l_lo .. l_one hold one block each and run on CTA 0 alone (-1 << 20: none)
+  int l_one;  // levels l_lo .. l_one hold one block per root and run one CTA per (root, slot) (< l_lo: none)
 };
 
 // Block operations with the compile-time side NT for levels >= 1 and the
@@ -108,31 +109,37 @@ __device__ __forceinline__ void prolong_any(const GmgView<T> &V, const LvArgs &L
     prolong_block<T, D, 0>(V, L, Lp, bid, sm);
 }
 
-// Exact solve on level Lc by warps w0, w0 + nw, ... : phi = A^-1 b, one warp
-// per row, FP64 accumulation.
+// Exact solve on level Lc by warps w0, w0 + nw, ... : phi = A^-1 b per root
+// and slot, one warp per row, FP64 accumulation.
 template <typename T>
-__device__ __forceinline__ void coarse_rows(const GmgView<T> &V, const LvArgs &Lc, const double *cinv, int nc, int w0,
+__device__ __forceinline__ void coarse_rows(const GmgView<T> &V, const LvArgs &Lc, const CycleArgs &A, int w0,
                                             int nw) {
   const int lane = threadIdx.x & 31;
-  for (int row = w0; row < nc; row += nw) {
-    const double *a = cinv + (size_t)row * nc;
+  const int M = A.ncr * A.nroot;
+  for (long long item = w0; item < (long long)M * V.nrhs; item += nw) {
+    const int r = (int)(item / M), row = (int)(item % M);
+    if (!V.active[r]) continue;
+    const int k = row / A.ncr, i = row - k * A.ncr;
+    const double *a = A.cinv + ((size_t)k * A.ncr + i) * A.ncr;
+    const T *b = V.b + r * V.rs_f + Lc.off + (size_t)k * A.ncr;
     double s = 0.0;
-    for (int j = lane; j < nc; j += 32) s += a[j] * (double)V.b[Lc.off + j];
+    for (int j = lane; j < A.ncr; j += 32) s += a[j] * (double)b[j];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) V.phi[Lc.poff + row] = T(s);
+    if (lane == 0) V.phi[r * V.rs_phi + Lc.poff + row] = T(s);
   }
 }
 
-
 // ---------------------------------------------------------------------------
-// Bottom of the cycle held in shared memory.  The single-block levels
-// l_lo .. l_one each cover the whole domain (root block and its coarsened
-// copies): all their faces are walls, and the child block of one covers its
-// parent entirely.  CTA 0 loads phi and the FAS right-hand side of l_one
-// once, runs sweeps, residual + restriction, FAS right-hand sides, the exact
-// solve, prolongation and sweeps on shared-memory copies of every level
-// (same formulas as the block kernels), and writes phi of l_one back.
+// Bottom of the cycle held in shared memory.  On levels l_lo .. l_one each
+// independent root (one tree of a forest, or the only root) holds one block
+// that covers its whole domain (the root block and its coarsened copies):
+// all its faces are walls, and its block on one level covers its parent
+// entirely; block k of each such level belongs to root k.  One CTA per
+// (root, slot) loads phi and the FAS right-hand side of l_one once, runs
+// sweeps, residual + restriction, FAS right-hand sides, the exact solve,
+// prolongation and sweeps on shared-memory copies of every level (same
+// formulas as the block kernels), and writes phi of l_one back.
 template <typename T, int D>
 struct TailLevel {
   T *tile, *b, *old;
@@ -295,7 +302,7 @@ __device__ void tail_prolong(const GmgView<T> &V, const TailLevel<T, D> &F, cons
 }
 
 template <typename T, int D>
-__device__ void tail_cycle(const GmgView<T> &V, const LevelSet &LS, const CycleArgs &A, int top,
+__device__ void tail_cycle(const GmgView<T> &V, const LevelSet &LS, const CycleArgs &A, int top, int root,
                            unsigned char *smem_raw) {
   constexpr int kMaxTail = 12;
   __shared__ TailLevel<T, D> Q[kMaxTail];  // descriptors in shared memory, not per-thread local memory
@@ -306,6 +313,9 @@ __device__ void tail_cycle(const GmgView<T> &V, const LevelSet &LS, const CycleA
     q.L = LS.lv[l - LS.lmin];
     q.n = q.L.n;
     q.ncell = D == 3 ? q.n * q.n * q.n : q.n * q.n;
+    q.L.first += root;  // this root's block of the level
+    q.L.off += (long long)root * q.ncell;
+    q.L.poff += (long long)root * q.ncell;
     q.stb = V.st_base[q.L.first];
     q.tile = p;
     p += TileGeo<T, D>(q.n).size;
@@ -347,10 +357,11 @@ __device__ void tail_cycle(const GmgView<T> &V, const LevelSet &LS, const CycleA
     const TailLevel<T, D> &q = Q[top - A.l_lo];
     const TileGeo<T, D> G(q.n);
     const int lane = threadIdx.x & 31;
-    for (int row = threadIdx.x >> 5; row < A.nc; row += blockDim.x / 32) {
-      const double *a = A.cinv + (size_t)row * A.nc;
+    const double *cinv = A.cinv + (size_t)root * A.ncr * A.ncr;
+    for (int row = threadIdx.x >> 5; row < A.ncr; row += blockDim.x / 32) {
+      const double *a = cinv + (size_t)row * A.ncr;
       double s = 0.0;
-      for (int j = lane; j < A.nc; j += 32) s += a[j] * (double)q.b[j];
+      for (int j = lane; j < A.ncr; j += 32) s += a[j] * (double)q.b[j];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) {
@@ -390,25 +401,31 @@ __global__ void __launch_bounds__(kCoopThreads) k_cycle_coop(GmgView<T> V, const
   __syncthreads();
   const unsigned int G = gridDim.x;
 #define GMG_LV(l) LS.lv[(l)-LS.lmin]
+  // (block, slot) items of level Lv handled by this CTA, slots fastest;
+  // frozen slots are skipped (W: the slot's view, bid: the block)
+#define GMG_ITEMS(Lv)                                                                          \
+  for (int item = blockIdx.x, bid = 0; item < (Lv).count * V.nrhs; item += G)                  \
+    if (const int r_ = item % V.nrhs; (bid = (Lv).first + item / V.nrhs, V.active[r_]))        \
+      if (const GmgView<T> W = slot_view(V, r_); true)
   // levels l_hi .. l_one + 1: every CTA, grid barrier between phases
   for (int l = A.l_hi; l > A.l_lo && l > A.l_one; l--) {
     const LvArgs L = GMG_LV(l), Lp = GMG_LV(l - 1);
     for (int k = 0; k < A.n_down; k++)
       for (int c = 0; c < 2; c++) {
-        for (int b = blockIdx.x; b < L.count; b += G) {
-          smooth_any<T, D, NT>(V, L, Lp, L.first + b, c, smem_raw);
+        GMG_ITEMS(L) {
+          smooth_any<T, D, NT>(W, L, Lp, bid, c, smem_raw);
           __syncthreads();
         }
         if (!grid_sync(A.bar, G, A.spin_limit)) return;
       }
-    for (int b = blockIdx.x; b < L.count; b += G) {
-      resid_restrict_any<T, D, NT>(V, L, Lp, L.first + b, smem_raw);
+    GMG_ITEMS(L) {
+      resid_restrict_any<T, D, NT>(W, L, Lp, bid, smem_raw);
       __syncthreads();
     }
     if (!grid_sync(A.bar, G, A.spin_limit)) return;
     const LvArgs Lpp = l - 2 >= LS.lmin ? GMG_LV(l - 2) : Lp;
-    for (int b = blockIdx.x; b < Lp.count; b += G) {
-      fas_any<T, D, NT>(V, Lp, Lpp, Lp.first + b, smem_raw);
+    GMG_ITEMS(Lp) {
+      fas_any<T, D, NT>(W, Lp, Lpp, bid, smem_raw);
       __syncthreads();
     }
     if (!grid_sync(A.bar, G, A.spin_limit)) return;
@@ -417,29 +434,34 @@ __global__ void __launch_bounds__(kCoopThreads) k_cycle_coop(GmgView<T> V, const
     // single-block levels l_one .. l_lo: CTA 0 runs the bottom of the cycle
     // (sweeps, restriction, FAS, coarse solve, prolongation, sweeps) with
     // block-level barriers only
-    if (blockIdx.x == 0) tail_cycle<T, D>(V, LS, A, A.l_one < A.l_hi ? A.l_one : A.l_hi, smem_raw);
+    for (int item = blockIdx.x; item < A.nroot * V.nrhs; item += G) {
+      const int r = item % V.nrhs, root = item / V.nrhs;
+      if (V.active[r]) tail_cycle<T, D>(slot_view(V, r), LS, A, A.l_one < A.l_hi ? A.l_one : A.l_hi, root, smem_raw);
+      __syncthreads();
+    }
   } else {
-    coarse_rows<T>(V, GMG_LV(A.l_lo), A.cinv, A.nc, blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5),
+    coarse_rows<T>(V, GMG_LV(A.l_lo), A, blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5),
                    (int)(G * (blockDim.x / 32)));
   }
   if (A.l_hi > A.l_one && !grid_sync(A.bar, G, A.spin_limit)) return;
   for (int l = (A.l_one >= A.l_lo ? A.l_one : A.l_lo) + 1; l <= A.l_hi; l++) {
     const LvArgs L = GMG_LV(l), Lp = GMG_LV(l - 1);
-    for (int b = blockIdx.x; b < L.count; b += G) {
-      prolong_any<T, D, NT>(V, L, Lp, L.first + b, smem_raw);
+    GMG_ITEMS(L) {
+      prolong_any<T, D, NT>(W, L, Lp, bid, smem_raw);
       __syncthreads();
     }
     if (!grid_sync(A.bar, G, A.spin_limit)) return;
     for (int k = 0; k < A.n_up; k++)
       for (int c = 0; c < 2; c++) {
-        for (int b = blockIdx.x; b < L.count; b += G) {
-          smooth_any<T, D, NT>(V, L, Lp, L.first + b, c, smem_raw);
+        GMG_ITEMS(L) {
+          smooth_any<T, D, NT>(W, L, Lp, bid, c, smem_raw);
           __syncthreads();
         }
         // the last sweep of the range needs no barrier: the kernel ends
         if (!(l == A.l_hi && k == A.n_up - 1 && c == 1) && !grid_sync(A.bar, G, A.spin_limit)) return;
       }
   }
+#undef GMG_ITEMS
 #undef GMG_LV
 }
 

@@ -30,7 +30,7 @@ struct FusedGeo {
 };
 
 template <typename T, int D, int NT, int K>
-__global__ void __launch_bounds__(kThreads) k_smooth_tb(GmgView<T> V, LvArgs L, long long out_poff) {
+__global__ void __launch_bounds__(kThreads) k_smooth_tb(GmgView<T> V0, LvArgs L, long long out_poff) {
   using F = FusedGeo<T, D, NT, K>;
   constexpr int n = NT, VEC = F::VEC;
   using VT = typename Vec16<T>::type;
@@ -39,7 +39,9 @@ __global__ void __launch_bounds__(kThreads) k_smooth_tb(GmgView<T> V, LvArgs L, 
   __shared__ long long s_stb[kNbr];
   T *tp = reinterpret_cast<T *>(smem_raw);
   T *tb = tp + F::TS;
-  const int bid = L.first + blockIdx.x;
+  int bid;
+  GmgView<T> V;
+  if (!slot_item(V0, L, &bid, &V)) return;
   if (threadIdx.x < kNbr) {
     const int id = V.nbr[(size_t)bid * kNbr + threadIdx.x];
     s_nb[threadIdx.x] = id;

@@ -32,6 +32,8 @@ void set_error(const std::string &msg) { g_last_error = msg; }
 __global__ void __launch_bounds__(1024) k_reduce_partials(const double *partials, int nb, double *out,
                                                           const GridBar *bar) {
   __shared__ double s[3][1024];
+  partials += (size_t)blockIdx.x * nb * 3;  // slot blockIdx.x
+  out += (size_t)blockIdx.x * 4;
   double a = 0.0, b = 0.0, c = 0.0;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
     a += partials[(size_t)i * 3];
@@ -58,24 +60,33 @@ __global__ void __launch_bounds__(1024) k_reduce_partials(const double *partials
   }
 }
 
+// Leaf-cell kernels over the slots r0 .. r0 + nr - 1: element k of the
+// leaf-ordered array io (nr x nleaf) is cell (k % nleaf) of slot
+// r0 + k / nleaf; field arrays of slot r start at r * rs.
+
 // b <- g - boundary terms on leaf cells (g in leaf-cell order)
 __global__ void k_leaf_rhs(const int *__restrict__ leaf_ids, const long long *__restrict__ cbase,
                            const long long *__restrict__ bt_base, const double *__restrict__ bterm,
-                           const double *__restrict__ g, double *__restrict__ b, long long ncells, int ncell) {
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ncells; k += (long long)gridDim.x * blockDim.x) {
-    const int id = leaf_ids[k / ncell];
-    const int c = (int)(k % ncell);
+                           const double *__restrict__ g, double *__restrict__ b, long long nleaf, int ncell,
+                           long long rs, int r0, int nr) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nleaf * nr;
+       k += (long long)gridDim.x * blockDim.x) {
+    const long long r = r0 + k / nleaf, kk = k % nleaf;
+    const int id = leaf_ids[kk / ncell];
+    const int c = (int)(kk % ncell);
     const long long bb = bt_base[id];
-    b[cbase[id] + c] = g[k] - (bb >= 0 ? bterm[bb + c] : 0.0);
+    b[r * rs + cbase[id] + c] = g[k] - (bb >= 0 ? bterm[bb + c] : 0.0);
   }
 }
 
-// leaf gather (dir 0: field -> out) / scatter (dir 1: in -> field)
+// leaf gather (dir 0: field -> io) / scatter (dir 1: io -> field)
 __global__ void k_leaf_copy(const int *__restrict__ leaf_ids, const long long *__restrict__ cbase, double *field,
-                            double *io, long long ncells, int ncell, int dir) {
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ncells; k += (long long)gridDim.x * blockDim.x) {
-    const int id = leaf_ids[k / ncell];
-    const long long f = cbase[id] + (k % ncell);
+                            double *io, long long nleaf, int ncell, long long rs, int r0, int nr, int dir) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nleaf * nr;
+       k += (long long)gridDim.x * blockDim.x) {
+    const long long r = r0 + k / nleaf, kk = k % nleaf;
+    const int id = leaf_ids[kk / ncell];
+    const long long f = r * rs + cbase[id] + (kk % ncell);
     if (dir == 0)
       io[k] = field[f];
     else
@@ -83,12 +94,17 @@ __global__ void k_leaf_copy(const int *__restrict__ leaf_ids, const long long *_
   }
 }
 
-// phi64 += e32 on leaf cells (mixed path: solution accumulation in FP64)
+// phi64 += e32 on leaf cells of the active slots (mixed path: solution
+// accumulation in FP64)
 __global__ void k_leaf_accumulate(const int *__restrict__ leaf_ids, const long long *__restrict__ cbase,
-                                  double *__restrict__ phi, const float *__restrict__ e, long long ncells, int ncell) {
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ncells; k += (long long)gridDim.x * blockDim.x) {
-    const int id = leaf_ids[k / ncell];
-    const long long f = cbase[id] + (k % ncell);
+                                  double *__restrict__ phi, const float *__restrict__ e, long long nleaf, int ncell,
+                                  long long rs, int nr, const int *__restrict__ active) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nleaf * nr;
+       k += (long long)gridDim.x * blockDim.x) {
+    const long long r = k / nleaf, kk = k % nleaf;
+    if (!active[r]) continue;
+    const int id = leaf_ids[kk / ncell];
+    const long long f = r * rs + cbase[id] + (kk % ncell);
     phi[f] += (double)e[f];
   }
 }
@@ -181,6 +197,10 @@ GmgView<double> view<double>(gmg_tree *t) {
   v.spec = t->d_spec;
   v.wneu = 0;
   for (int w = 0; w < 6; w++) v.wneu |= (t->wall_type[w] == GMG_WALL_NEUMANN ? 1 : 0) << w;
+  v.nrhs = t->nrhs;
+  v.rs_phi = t->total_cells;
+  v.rs_f = t->total_cells;
+  v.active = t->d_active;
   return v;
 }
 
@@ -202,6 +222,10 @@ GmgView<float> view<float>(gmg_tree *t) {
   v.spec = t->d_spec;
   v.wneu = 0;
   for (int w = 0; w < 6; w++) v.wneu |= (t->wall_type[w] == GMG_WALL_NEUMANN ? 1 : 0) << w;
+  v.nrhs = t->nrhs;
+  v.rs_phi = t->total_cells;
+  v.rs_f = t->total_cells;
+  v.active = t->d_active;
   return v;
 }
 
@@ -295,17 +319,17 @@ int coop_cycle(gmg_tree *t, cudaStream_t s, int ls) {
   // solve is small enough for one CTA
   int l_one = t->lmin - 1;
   size_t tail_bytes = 0;
-  if (t->nc <= 256 && t->cb[0] * t->cb[1] * t->cb[2] == 1)
-    for (int l = t->lmin; l <= ls && t->lev(l).count == 1; l++) {
+  if (t->ncr <= 256 && (t->nroot > 1 || t->cb[0] * t->cb[1] * t->cb[2] == 1))
+    for (int l = t->lmin; l <= ls && t->lev(l).count == t->nroot; l++) {
       const int n = t->lev(l).n;
       const size_t add = tail_level_bytes<T, D>(n);
       if (tail_bytes + add > 160 * 1024 || l - t->lmin >= 11) break;
       tail_bytes += add;
       l_one = l;
     }
-  CycleArgs A{t->lmin, ls, t->prm.n_down, t->prm.n_up, t->nc, t->d_cinv, t->d_bar, t->spin_limit, l_one};
+  CycleArgs A{t->lmin, ls, t->prm.n_down, t->prm.n_up, t->ncr, t->nroot, t->d_cinv, t->d_bar, t->spin_limit, l_one};
   size_t sm = 0;
-  int maxb = 1;
+  int maxb = l_one >= t->lmin ? t->nroot : 1;
   for (int l = t->lmin; l <= ls; l++) {
     if (l <= l_one) continue;  // held in shared memory by the tail
     const int hm = t->lev(l).n / 2 + 2;
@@ -313,6 +337,7 @@ int coop_cycle(gmg_tree *t, cudaStream_t s, int ls) {
     sm = std::max(sm, sizeof(T) * (size_t)(D == 3 ? hm * hm * hm : hm * hm));
     maxb = std::max(maxb, t->lev(l).count);
   }
+  maxb *= t->nrhs;  // work items: (block, slot) pairs
   sm = std::max(sm, tail_bytes);
   int rc = GMG_OK;
   with_nt<D>(t->N, [&](auto nt) {
@@ -373,7 +398,7 @@ void launch_fused(gmg_tree *t, cudaStream_t s, int l, int sweeps, long long in_p
     if constexpr (NT != 0) {
       const size_t sm = FusedGeo<T, D, NT, K>::smem_bytes();
       launch(t, s, 0, prec_of<T>(), l,
-             [&] { k_smooth_tb<T, D, NT, K><<<L.count, kThreads, sm, s>>>(V, L, out_poff); });
+             [&] { k_smooth_tb<T, D, NT, K><<<L.count * t->nrhs, kThreads, sm, s>>>(V, L, out_poff); });
     }
   };
   with_nt<D>(L.n, [&](auto nt) {
@@ -392,7 +417,8 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s) {
   GmgView<T> V = view<T>(t);
   const int P = prec_of<T>();
   const int ls = t->use_coop ? t->coop_split : t->lmin;
-  const long long other = t->total_cells;  // offset of the second FP32 phi buffer
+  const long long other = (long long)t->nrhs * t->total_cells;  // offset of the second FP32 phi buffer
+  const int R = t->nrhs;
   for (int l = t->lmax; l > ls; l--) {
     LvArgs L = lv(t, l), Lp = lv(t, l - 1);
     const size_t sm = tile_bytes<T>(t, l);
@@ -406,14 +432,14 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s) {
       if (!fused)
         for (int k = 0; k < t->prm.n_down; k++)
           for (int c = 0; c < 2; c++)
-            launch(t, s, 0, P, l, [&] { k_smooth<T, D, NT><<<L.count, kThreads, sm, s>>>(V, L, Lp, c); });
-      launch(t, s, 1, P, l, [&] { k_resid_restrict<T, D, NT><<<L.count, kThreads, sm, s>>>(V, L, Lp); });
+            launch(t, s, 0, P, l, [&] { k_smooth<T, D, NT><<<L.count * R, kThreads, sm, s>>>(V, L, Lp, c); });
+      launch(t, s, 1, P, l, [&] { k_resid_restrict<T, D, NT><<<L.count * R, kThreads, sm, s>>>(V, L, Lp); });
     });
     LvArgs Lpp = l - 2 >= t->lmin ? lv(t, l - 2) : Lp;
     const size_t smp = tile_bytes<T>(t, l - 1);
     with_nt<D>(Lp.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
-      launch(t, s, 2, P, l - 1, [&] { k_fas<T, D, NT><<<Lp.count, kThreads, smp, s>>>(V, Lp, Lpp); });
+      launch(t, s, 2, P, l - 1, [&] { k_fas<T, D, NT><<<Lp.count * R, kThreads, smp, s>>>(V, Lp, Lpp); });
     });
   }
   if (t->use_coop) {
@@ -421,10 +447,10 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s) {
     if (rc) return rc;
   } else {
     LvArgs Lc = lv(t, t->lmin);
-    const int M = t->nc;
+    const long long rows = (long long)t->nc * R;
     launch(t, s, 3, P, t->lmin, [&] {
-      k_coarse<T><<<(M + kThreads / 32 - 1) / (kThreads / 32), kThreads, 0, s>>>(t->d_cinv, M, V.b + Lc.off,
-                                                                                  V.phi + Lc.poff);
+      k_coarse<T><<<(unsigned)((rows + kThreads / 32 - 1) / (kThreads / 32)), kThreads, 0, s>>>(V, Lc, t->d_cinv,
+                                                                                              t->ncr, t->nroot);
     });
   }
   for (int l = ls + 1; l <= t->lmax; l++) {
@@ -436,11 +462,11 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s) {
     if (fused) L.poff = L.off + other;  // the down leg left phi in the second buffer
     with_nt<D>(L.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
-      launch(t, s, 4, P, l, [&] { k_prolong<T, D, NT><<<L.count, kThreads, psm, s>>>(V, L, Lp); });
+      launch(t, s, 4, P, l, [&] { k_prolong<T, D, NT><<<L.count * R, kThreads, psm, s>>>(V, L, Lp); });
       if (!fused)
         for (int k = 0; k < t->prm.n_up; k++)
           for (int c = 0; c < 2; c++)
-            launch(t, s, 0, P, l, [&] { k_smooth<T, D, NT><<<L.count, kThreads, sm, s>>>(V, L, Lp, c); });
+            launch(t, s, 0, P, l, [&] { k_smooth<T, D, NT><<<L.count * R, kThreads, sm, s>>>(V, L, Lp, c); });
     });
     if (fused) launch_fused<T, D>(t, s, l, t->prm.n_up, L.off + other, L.off);  // back to the first buffer
   }
@@ -449,7 +475,7 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s) {
       LvArgs L = lv(t, l), Lp = lv(t, l - 1);
       with_nt<D>(L.n, [&](auto nt) {
         constexpr int NT = decltype(nt)::value;
-        launch(t, s, 5, P, l, [&] { k_restrict_phi<T, D, NT><<<L.count, kThreads, 0, s>>>(V, L, Lp); });
+        launch(t, s, 5, P, l, [&] { k_restrict_phi<T, D, NT><<<L.count * R, kThreads, 0, s>>>(V, L, Lp); });
       });
     }
   }
@@ -474,14 +500,17 @@ int residual_impl(gmg_tree *t, cudaStream_t s, float *rout) {
     const size_t sm = tile_bytes<double>(t, l);
     with_nt<D>(L.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
-      launch(t, s, 6, 0, l,
-             [&] { k_resnorm<double, D, NT><<<L.count, kThreads, sm, s>>>(V, L, Lp, t->d_partials, rout); });
+      launch(t, s, 6, 0, l, [&] {
+        k_resnorm<double, D, NT><<<L.count * t->nrhs, kThreads, sm, s>>>(V, L, Lp, t->d_partials, rout,
+                                                                       (int)t->blocks.size());
+      });
     });
   }
-  launch(t, s, 7, 0, t->lmax,
-         [&] { k_reduce_partials<<<1, 1024, 0, s>>>(t->d_partials, (int)t->blocks.size(), t->d_red, t->d_bar); });
+  launch(t, s, 7, 0, t->lmax, [&] {
+    k_reduce_partials<<<t->nrhs, 1024, 0, s>>>(t->d_partials, (int)t->blocks.size(), t->d_red, t->d_bar);
+  });
   CUDA_TRY(cudaGetLastError());
-  CUDA_TRY(cudaMemcpyAsync(t->h_red, t->d_red, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(t->h_red, t->d_red, 4 * sizeof(double) * t->nrhs, cudaMemcpyDeviceToHost, s));
   return GMG_OK;
 }
 
@@ -496,7 +525,7 @@ int restrict_all_phi64(gmg_tree *t, cudaStream_t s) {
     LvArgs L = lv(t, l), Lp = lv(t, l - 1);
     with_nt<D>(L.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
-      launch(t, s, 5, 0, l, [&] { k_restrict_phi<double, D, NT><<<L.count, kThreads, 0, s>>>(V, L, Lp); });
+      launch(t, s, 5, 0, l, [&] { k_restrict_phi<double, D, NT><<<L.count * t->nrhs, kThreads, 0, s>>>(V, L, Lp); });
     });
   }
   CUDA_TRY(cudaGetLastError());
@@ -510,13 +539,14 @@ int restrict_all_phi64_any(gmg_tree *t, cudaStream_t s) {
 // one defect-correction step of the mixed path: e = 0, FP32 V-cycle on
 // A e = r, phi += e in FP64 (and covered cells restricted)
 int mixed_step(gmg_tree *t, cudaStream_t s) {
-  CUDA_TRY(cudaMemsetAsync(t->f_phi, 0, (size_t)t->total_cells * sizeof(float), s));
+  // e = 0 in the first FP32 phi buffer of every slot (frozen slots too: harmless)
+  CUDA_TRY(cudaMemsetAsync(t->f_phi, 0, (size_t)t->nrhs * t->total_cells * sizeof(float), s));
   int rc = vcycle_any<float>(t, s);
   if (rc) return rc;
   const long long n = t->n_leaf_cells;
   launch(t, s, 8, 0, t->lmax, [&] {
-    k_leaf_accumulate<<<grid_for(n), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, t->f_phi, n,
-                                                  t->lev(t->lmax).ncell);
+    k_leaf_accumulate<<<grid_for(n * t->nrhs), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, t->f_phi, n,
+                                                            t->leaf_ncell(), t->total_cells, t->nrhs, t->d_active);
   });
   CUDA_TRY(cudaGetLastError());
   if (t->adaptive) return restrict_all_phi64_any(t, s);
@@ -556,12 +586,13 @@ int run_graph(gmg_tree *t, int slot, cudaStream_t s, F &&enqueue) {
   return GMG_OK;
 }
 
-int read_red(gmg_tree *t, cudaStream_t s, double *s2, double *mx, double *b2) {
+// Waits for the stream and checks the barrier flag; the norms of slot r are
+// then h_red[4r .. 4r + 2] = (sum r^2, max |r|, sum b^2).
+int read_red(gmg_tree *t, cudaStream_t s) {
   CUDA_TRY(cudaStreamSynchronize(s));
-  *s2 = t->h_red[0];
-  *mx = t->h_red[1];
-  *b2 = t->h_red[2];
-  if (t->h_red[3] != 0.0) {  // a grid barrier timed out: report once, then clear
+  bool timeout = false;
+  for (int r = 0; r < t->nrhs; r++) timeout = timeout || t->h_red[4 * r + 3] != 0.0;
+  if (timeout) {  // a grid barrier timed out: report once, then clear
     CUDA_TRY(cudaMemset(t->d_bar, 0, sizeof(GridBar)));
     set_error("a grid barrier of the coarse-level cycle timed out");
     return GMG_ERR_TIMEOUT;
@@ -573,7 +604,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t nbr, pnb, parent, pofs, flags, leaf, cbase, st_base, bt_base, phi, b, old, fphi, fb, fold, st, fst, bterm, cinv,
-      partials, red, bar, spec, lvtab, total;
+      partials, red, active, bar, spec, lvtab, total;
 };
 
 Layout layout(const gmg_tree *t) {
@@ -584,7 +615,7 @@ Layout layout(const gmg_tree *t) {
     o = align256(o + bytes);
     return at;
   };
-  const size_t nb = t->blocks.size(), cells = (size_t)t->total_cells;
+  const size_t nb = t->blocks.size(), cells = (size_t)t->total_cells, R = (size_t)t->nrhs;
   L.nbr = take(nb * kNbr * sizeof(int));
   L.pnb = take(nb * kNbr * sizeof(int));
   L.parent = take(nb * sizeof(int));
@@ -594,18 +625,19 @@ Layout layout(const gmg_tree *t) {
   L.cbase = take(nb * sizeof(long long));
   L.st_base = take(nb * sizeof(long long));
   L.bt_base = take(nb * sizeof(long long));
-  L.phi = take(cells * sizeof(double));
-  L.b = take(cells * sizeof(double));
-  L.old = take(cells * sizeof(double));
-  L.fphi = take(2 * cells * sizeof(float));  // two buffers: fused sweeps write the other one
-  L.fb = take(cells * sizeof(float));
-  L.fold = take(cells * sizeof(float));
+  L.phi = take(R * cells * sizeof(double));  // per field: [nrhs][cells]
+  L.b = take(R * cells * sizeof(double));
+  L.old = take(R * cells * sizeof(double));
+  L.fphi = take(2 * R * cells * sizeof(float));  // two buffers [2][nrhs][cells]: fused sweeps write the other one
+  L.fb = take(R * cells * sizeof(float));
+  L.fold = take(R * cells * sizeof(float));
   L.st = take(t->stencil_h.size() * sizeof(double));
   L.fst = take(t->stencil_h.size() * sizeof(float));
   L.bterm = take(t->bterm_h.size() * sizeof(double));
-  L.cinv = take((size_t)t->nc * t->nc * sizeof(double));
-  L.partials = take(nb * 3 * sizeof(double));
-  L.red = take(4 * sizeof(double));
+  L.cinv = take(t->cinv_h.size() * sizeof(double));
+  L.partials = take(R * nb * 3 * sizeof(double));
+  L.red = take(R * 4 * sizeof(double));
+  L.active = take(R * sizeof(int));
   L.bar = take(sizeof(GridBar));
   L.spec = take(t->spec_h.size());
   L.lvtab = take(kMaxLevels * sizeof(LvArgs));
@@ -656,6 +688,7 @@ void gmg_tree_destroy(gmg_tree *t) {
   for (cudaEvent_t e : t->prof_pool) cudaEventDestroy(e);
   if (t->owns_ws && t->ws) cudaFree(t->ws);
   if (t->h_red) cudaFreeHost(t->h_red);
+  if (t->h_active) cudaFreeHost(t->h_active);
   delete t;
 }
 
@@ -804,6 +837,7 @@ int gmg_tree_bind(gmg_tree *t, void *device_ptr, size_t bytes) {
   t->d_cinv = reinterpret_cast<double *>(w + L.cinv);
   t->d_partials = reinterpret_cast<double *>(w + L.partials);
   t->d_red = reinterpret_cast<double *>(w + L.red);
+  t->d_active = reinterpret_cast<int *>(w + L.active);
   t->d_bar = reinterpret_cast<GridBar *>(w + L.bar);
   t->d_spec = reinterpret_cast<unsigned char *>(w + L.spec);
   t->d_lvtab = reinterpret_cast<LvArgs *>(w + L.lvtab);
@@ -842,23 +876,25 @@ int gmg_tree_bind(gmg_tree *t, void *device_ptr, size_t bytes) {
   }
   if (!t->bterm_h.empty())
     CUDA_TRY(cudaMemcpy(t->d_bterm, t->bterm_h.data(), t->bterm_h.size() * sizeof(double), cudaMemcpyHostToDevice));
-  CUDA_TRY(cudaMemcpy(t->d_cinv, t->cinv_h.data(), (size_t)t->nc * t->nc * sizeof(double), cudaMemcpyHostToDevice));
-  const size_t cells = (size_t)t->total_cells;
+  CUDA_TRY(cudaMemcpy(t->d_cinv, t->cinv_h.data(), t->cinv_h.size() * sizeof(double), cudaMemcpyHostToDevice));
+  const size_t cells = (size_t)t->total_cells * t->nrhs;
   CUDA_TRY(cudaMemset(t->d_phi, 0, cells * sizeof(double)));
   CUDA_TRY(cudaMemset(t->d_b, 0, cells * sizeof(double)));
   CUDA_TRY(cudaMemset(t->d_old, 0, cells * sizeof(double)));
-  CUDA_TRY(cudaMemset(t->f_phi, 0, cells * sizeof(float)));
+  CUDA_TRY(cudaMemset(t->f_phi, 0, 2 * cells * sizeof(float)));
   CUDA_TRY(cudaMemset(t->f_b, 0, cells * sizeof(float)));
   CUDA_TRY(cudaMemset(t->f_old, 0, cells * sizeof(float)));
   // blocks on levels without leaves never write their residual partials
-  CUDA_TRY(cudaMemset(t->d_partials, 0, nb * 3 * sizeof(double)));
-  CUDA_TRY(cudaMemset(t->d_red, 0, 4 * sizeof(double)));
+  CUDA_TRY(cudaMemset(t->d_partials, 0, (size_t)t->nrhs * nb * 3 * sizeof(double)));
+  CUDA_TRY(cudaMemset(t->d_red, 0, (size_t)t->nrhs * 4 * sizeof(double)));
+  CUDA_TRY(cudaMemset(t->d_active, 1, (size_t)t->nrhs * sizeof(int)));  // nonzero: active
   CUDA_TRY(cudaMemset(t->d_bar, 0, sizeof(GridBar)));
   // levels up to coop_split run inside one cooperative kernel (few blocks each)
   t->coop_split = t->lmin;
   for (int l = t->lmin; l <= t->lmax; l++)
     if (t->lev(l).count <= kCoopMaxBlocks) t->coop_split = l;
-  if (!t->h_red) CUDA_TRY(cudaMallocHost(&t->h_red, 4 * sizeof(double)));
+  if (!t->h_red) CUDA_TRY(cudaMallocHost(&t->h_red, (size_t)t->nrhs * 4 * sizeof(double)));
+  if (!t->h_active) CUDA_TRY(cudaMallocHost(&t->h_active, (size_t)t->nrhs * sizeof(int)));
   t->level_complete.assign(t->levels.size(), 1);
   for (size_t i = 0; i < nb; i++)
     for (int k = 0; k < kNbr; k++)
@@ -872,24 +908,40 @@ int gmg_tree_bind(gmg_tree *t, void *device_ptr, size_t bytes) {
 }
 
 
-int gmg_set_rhs(gmg_tree *t, const double *g, int where, void *stream) {
+int gmg_set_num_rhs(gmg_tree *t, int nrhs) {
+  if (!t || nrhs < 1 || nrhs > 65536) return set_error("bad arguments"), GMG_ERR_INVALID_ARG;
+  if (t->bound) return set_error("the slot count must be set before gmg_tree_bind"), GMG_ERR_STATE;
+  t->nrhs = nrhs;
+  return GMG_OK;
+}
+
+int gmg_num_rhs(const gmg_tree *t) { return t ? t->nrhs : 0; }
+
+int gmg_set_rhs_slots(gmg_tree *t, int slot0, int nslots, const double *g, int where, void *stream) {
   if (!t || !g) return set_error("null argument"), GMG_ERR_INVALID_ARG;
   if (!t->bound) return set_error("tree not bound"), GMG_ERR_STATE;
+  if (slot0 < 0 || nslots < 1 || slot0 + nslots > t->nrhs) return set_error("slot range"), GMG_ERR_INVALID_ARG;
   cudaStream_t s = as_stream(stream);
   const long long n = t->n_leaf_cells;
   const double *gd = g;
   if (where == GMG_HOST) {
-    // stage through the FP64 'old' field (scratch until the first V-cycle)
-    CUDA_TRY(cudaMemcpyAsync(t->d_old, g, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    // stage through the FP64 'old' field (scratch until the next V-cycle)
+    CUDA_TRY(cudaMemcpyAsync(t->d_old, g, (size_t)nslots * n * sizeof(double), cudaMemcpyHostToDevice, s));
     gd = t->d_old;
   } else if (where != GMG_DEVICE) {
     return set_error("where must be GMG_HOST or GMG_DEVICE"), GMG_ERR_INVALID_ARG;
   }
-  const int ncell = t->lev(t->lmax).ncell;
-  k_leaf_rhs<<<grid_for(n), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_bt_base, t->d_bterm, gd, t->d_b, n, ncell);
-  CUDA_TRY(cudaMemsetAsync(t->d_phi, 0, (size_t)t->total_cells * sizeof(double), s));
+  k_leaf_rhs<<<grid_for(n * nslots), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_bt_base, t->d_bterm, gd, t->d_b, n,
+                                                  t->leaf_ncell(), t->total_cells, slot0, nslots);
+  CUDA_TRY(cudaMemsetAsync(t->d_phi + (size_t)slot0 * t->total_cells, 0,
+                           (size_t)nslots * t->total_cells * sizeof(double), s));
   CUDA_TRY(cudaGetLastError());
   return GMG_OK;
+}
+
+int gmg_set_rhs(gmg_tree *t, const double *g, int where, void *stream) {
+  if (!t) return set_error("null tree"), GMG_ERR_INVALID_ARG;
+  return gmg_set_rhs_slots(t, 0, t->nrhs, g, where, stream);
 }
 
 int gmg_set_solution(gmg_tree *t, const double *phi, int where, void *stream) {
@@ -899,31 +951,40 @@ int gmg_set_solution(gmg_tree *t, const double *phi, int where, void *stream) {
   const long long n = t->n_leaf_cells;
   double *src = const_cast<double *>(phi);
   if (where == GMG_HOST) {
-    CUDA_TRY(cudaMemcpyAsync(t->d_old, phi, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(t->d_old, phi, (size_t)t->nrhs * n * sizeof(double), cudaMemcpyHostToDevice, s));
     src = t->d_old;
   }
-  const int ncell = t->lev(t->lmax).ncell;
-  k_leaf_copy<<<grid_for(n), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, src, n, ncell, 1);
+  k_leaf_copy<<<grid_for(n * t->nrhs), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, src, n, t->leaf_ncell(),
+                                                    t->total_cells, 0, t->nrhs, 1);
   CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemsetAsync(t->d_active, 1, (size_t)t->nrhs * sizeof(int), s));
   return restrict_all_phi64_any(t, s);
 }
 
-int gmg_get_solution(gmg_tree *t, double *phi, int where, void *stream) {
+int gmg_get_solution_slots(gmg_tree *t, int slot0, int nslots, double *phi, int where, void *stream) {
   if (!t || !phi) return set_error("null argument"), GMG_ERR_INVALID_ARG;
   if (!t->bound) return set_error("tree not bound"), GMG_ERR_STATE;
+  if (slot0 < 0 || nslots < 1 || slot0 + nslots > t->nrhs) return set_error("slot range"), GMG_ERR_INVALID_ARG;
   cudaStream_t s = as_stream(stream);
   const long long n = t->n_leaf_cells;
-  const int ncell = t->lev(t->lmax).ncell;
+  const int ncell = t->leaf_ncell();
   if (where == GMG_DEVICE) {
-    k_leaf_copy<<<grid_for(n), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, phi, n, ncell, 0);
+    k_leaf_copy<<<grid_for(n * nslots), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, phi, n, ncell, t->total_cells,
+                                                     slot0, nslots, 0);
     CUDA_TRY(cudaGetLastError());
     return GMG_OK;
   }
   // the FP64 'old' field is dead between V-cycles: stage the gather there
-  k_leaf_copy<<<grid_for(n), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, t->d_old, n, ncell, 0);
-  CUDA_TRY(cudaMemcpyAsync(phi, t->d_old, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  k_leaf_copy<<<grid_for(n * nslots), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, t->d_old, n, ncell,
+                                                   t->total_cells, slot0, nslots, 0);
+  CUDA_TRY(cudaMemcpyAsync(phi, t->d_old, (size_t)nslots * n * sizeof(double), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   return GMG_OK;
+}
+
+int gmg_get_solution(gmg_tree *t, double *phi, int where, void *stream) {
+  if (!t) return set_error("null tree"), GMG_ERR_INVALID_ARG;
+  return gmg_get_solution_slots(t, 0, t->nrhs, phi, where, stream);
 }
 
 int gmg_get_level(gmg_tree *t, int level, int which, double *out, void *stream) {
@@ -931,19 +992,46 @@ int gmg_get_level(gmg_tree *t, int level, int which, double *out, void *stream) 
   if (!t->bound) return set_error("tree not bound"), GMG_ERR_STATE;
   cudaStream_t s = as_stream(stream);
   const LevelInfo &L = t->lev(level);
-  const double *src = (which == 0 ? t->d_phi : t->d_b) + L.off;
-  CUDA_TRY(cudaMemcpyAsync(out, src, (size_t)L.count * L.ncell * sizeof(double), cudaMemcpyDeviceToHost, s));
+  const size_t cells = (size_t)L.count * L.ncell;
+  for (int r = 0; r < t->nrhs; r++) {
+    const double *src = (which == 0 ? t->d_phi : t->d_b) + (size_t)r * t->total_cells + L.off;
+    CUDA_TRY(cudaMemcpyAsync(out + r * cells, src, cells * sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
   CUDA_TRY(cudaStreamSynchronize(s));
   return GMG_OK;
 }
+
+namespace {
+// slot mask: all slots active, or the host array `mask` (nonzero = active)
+int upload_mask(gmg_tree *t, const int *mask, cudaStream_t s) {
+  if (!mask) {
+    CUDA_TRY(cudaMemsetAsync(t->d_active, 1, (size_t)t->nrhs * sizeof(int), s));
+    return GMG_OK;
+  }
+  // the pinned mirror may still feed an earlier copy: wait for the stream
+  CUDA_TRY(cudaStreamSynchronize(s));
+  for (int r = 0; r < t->nrhs; r++) t->h_active[r] = mask[r] ? 1 : 0;
+  CUDA_TRY(cudaMemcpyAsync(t->d_active, t->h_active, (size_t)t->nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
+  return GMG_OK;
+}
+
+void slot_norms(const gmg_tree *t, int r, double *rel, double *linf, double *bnorm) {
+  const double s2 = t->h_red[4 * r], mx = t->h_red[4 * r + 1], b2 = t->h_red[4 * r + 2];
+  if (rel) *rel = b2 > 0 ? std::sqrt(s2 / b2) : std::sqrt(s2);
+  if (linf) *linf = mx;
+  if (bnorm) *bnorm = std::sqrt(b2);
+}
+}  // namespace
 
 int gmg_vcycle(gmg_tree *t, int n_cycles, void *stream) {
   if (!t || n_cycles < 0) return set_error("bad arguments"), GMG_ERR_INVALID_ARG;
   if (!t->bound) return set_error("tree not bound"), GMG_ERR_STATE;
   t->launches = 0;
   cudaStream_t s = as_stream(stream);
+  int rc = upload_mask(t, nullptr, s);
+  if (rc) return rc;
   for (int k = 0; k < n_cycles; k++) {
-    int rc = run_graph(t, gmg_tree::kGraphVcycle64, s, [&](cudaStream_t cs) { return vcycle_any<double>(t, cs); });
+    rc = run_graph(t, gmg_tree::kGraphVcycle64, s, [&](cudaStream_t cs) { return vcycle_any<double>(t, cs); });
     if (rc) return rc;
   }
   return GMG_OK;
@@ -954,13 +1042,39 @@ int gmg_residual(gmg_tree *t, double *rel_l2, double *linf, void *stream) {
   if (!t->bound) return set_error("tree not bound"), GMG_ERR_STATE;
   cudaStream_t s = as_stream(stream);
   t->launches = 0;
-  int rc = run_graph(t, gmg_tree::kGraphResid64, s, [&](cudaStream_t cs) { return residual_any(t, cs, nullptr); });
+  int rc = upload_mask(t, nullptr, s);
   if (rc) return rc;
-  double s2, mx, b2;
-  rc = read_red(t, s, &s2, &mx, &b2);
+  rc = run_graph(t, gmg_tree::kGraphResid64, s, [&](cudaStream_t cs) { return residual_any(t, cs, nullptr); });
   if (rc) return rc;
-  if (rel_l2) *rel_l2 = b2 > 0 ? std::sqrt(s2 / b2) : std::sqrt(s2);
-  if (linf) *linf = mx;
+  rc = read_red(t, s);
+  if (rc) return rc;
+  for (int r = 0; r < t->nrhs; r++) slot_norms(t, r, rel_l2 ? rel_l2 + r : nullptr, linf ? linf + r : nullptr, nullptr);
+  return GMG_OK;
+}
+
+int gmg_iterate(gmg_tree *t, int precision, const int *active, int residual_only, double *rel_l2, double *linf,
+                void *stream) {
+  if (!t || !active) return set_error("null argument"), GMG_ERR_INVALID_ARG;
+  if (precision != GMG_FP64 && precision != GMG_MIXED) return set_error("bad precision"), GMG_ERR_INVALID_ARG;
+  if (!t->bound) return set_error("tree not bound"), GMG_ERR_STATE;
+  cudaStream_t s = as_stream(stream);
+  t->launches = 0;
+  const bool mixed = precision == GMG_MIXED;
+  float *rout = mixed ? t->f_b : nullptr;
+  int rc = upload_mask(t, active, s);
+  if (rc) return rc;
+  if (residual_only)
+    rc = run_graph(t, mixed ? gmg_tree::kGraphResidMixed : gmg_tree::kGraphResid64, s,
+                   [&](cudaStream_t cs) { return residual_any(t, cs, rout); });
+  else
+    rc = run_graph(t, mixed ? gmg_tree::kGraphCycleMixed : gmg_tree::kGraphCycle64, s, [&](cudaStream_t cs) {
+      int r = mixed ? mixed_step(t, cs) : vcycle_any<double>(t, cs);
+      return r ? r : residual_any(t, cs, rout);
+    });
+  if (rc) return rc;
+  rc = read_red(t, s);
+  if (rc) return rc;
+  for (int r = 0; r < t->nrhs; r++) slot_norms(t, r, rel_l2 ? rel_l2 + r : nullptr, linf ? linf + r : nullptr, nullptr);
   return GMG_OK;
 }
 
@@ -970,30 +1084,43 @@ int gmg_solve(gmg_tree *t, int precision, double rel_tol, int max_cycles, gmg_st
   if (!t->bound) return set_error("tree not bound"), GMG_ERR_STATE;
   cudaStream_t s = as_stream(stream);
   t->launches = 0;
-  double s2, mx, b2, rel = 0.0, prev = INFINITY;
+  const int R = t->nrhs;
+  std::vector<int> act(R, 1), cyc(R, 0);
+  std::vector<double> rel(R, 0.0), prev(R, INFINITY);
   int cycles = 0, rc = GMG_OK;
   const bool mixed = precision == GMG_MIXED;
   float *rout = mixed ? t->f_b : nullptr;
-  // first residual; then each iteration = one cycle + the residual after it
+  // first residual; then each iteration = one cycle + the residual after it,
+  // on the slots that have not reached the tolerance yet
+  rc = upload_mask(t, nullptr, s);
+  if (rc) return rc;
   rc = run_graph(t, mixed ? gmg_tree::kGraphResidMixed : gmg_tree::kGraphResid64, s,
                  [&](cudaStream_t cs) { return residual_any(t, cs, rout); });
   if (rc) return rc;
   for (;;) {
-    rc = read_red(t, s, &s2, &mx, &b2);
+    rc = read_red(t, s);
     if (rc) return rc;
-    const double bn = b2 > 0 ? std::sqrt(b2) : 1.0;
-    rel = std::sqrt(s2) / bn;
-    if (!std::isfinite(rel) || (cycles > 2 && rel > 1e3 * prev)) {
-      rc = GMG_ERR_NONFINITE;
-      set_error("residual norm is not finite or diverges");
-      break;
+    int left = 0;
+    for (int r = 0; r < R; r++) {
+      if (!act[r]) continue;
+      slot_norms(t, r, &rel[r], nullptr, nullptr);
+      if (!std::isfinite(rel[r]) || (cyc[r] > 2 && rel[r] > 1e3 * prev[r])) {
+        rc = GMG_ERR_NONFINITE;
+        set_error("residual norm is not finite or diverges");
+      }
+      prev[r] = std::min(prev[r], rel[r]);
+      if (rel[r] <= rel_tol) act[r] = 0;
+      left += act[r];
     }
-    prev = std::min(prev, rel);
-    if (rel <= rel_tol) break;
+    if (rc || left == 0) break;
     if (cycles >= max_cycles) {
       rc = GMG_ERR_NOT_CONVERGED;
       set_error("tolerance not reached within max_cycles");
       break;
+    }
+    if (R > 1 || !act[0]) {
+      rc = upload_mask(t, act.data(), s);
+      if (rc) return rc;
     }
     rc = run_graph(t, mixed ? gmg_tree::kGraphCycleMixed : gmg_tree::kGraphCycle64, s, [&](cudaStream_t cs) {
       int r = mixed ? mixed_step(t, cs) : vcycle_any<double>(t, cs);
@@ -1001,13 +1128,13 @@ int gmg_solve(gmg_tree *t, int precision, double rel_tol, int max_cycles, gmg_st
     });
     if (rc) return rc;
     cycles++;
+    for (int r = 0; r < R; r++) cyc[r] += act[r];
   }
-  if (stats) {
-    stats->cycles = cycles;
-    stats->rel_l2 = rel;
-    stats->linf = mx;
-    stats->bnorm = std::sqrt(b2);
-  }
+  if (stats)
+    for (int r = 0; r < R; r++) {
+      stats[r].cycles = cyc[r];
+      slot_norms(t, r, &stats[r].rel_l2, &stats[r].linf, &stats[r].bnorm);
+    }
   return rc;
 }
 

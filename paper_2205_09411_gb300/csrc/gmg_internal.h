@@ -63,7 +63,22 @@ struct GmgView {
   const T *st;           // stencil pool: per cut block (2D+1) x ncell, [diag, -x, +x, -y, +y, -z, +z]
   const unsigned char *spec;  // per cut block ncell flags at st_base/(2D+1): 1 = stencil differs from the regular one
   int wneu;              // bit w set: wall w is Neumann (ghost +phi), else Dirichlet (-phi)
+  // right-hand-side slots: slot r's fields start r * rs_phi (phi) and
+  // r * rs_f (b, old) elements after slot 0's; tables and stencils are shared
+  int nrhs;
+  long long rs_phi, rs_f;
+  const int *active;     // [nrhs] 0 = slot frozen (converged or empty): its CTAs return at once
 };
+
+// The view of one right-hand-side slot.
+template <typename T>
+__host__ __device__ __forceinline__ GmgView<T> slot_view(const GmgView<T> &V, int r) {
+  GmgView<T> W = V;
+  W.phi = V.phi + r * V.rs_phi;
+  W.b = V.b + r * V.rs_f;
+  W.old = V.old + r * V.rs_f;
+  return W;
+}
 
 struct gmg_tree_impl;
 
@@ -79,6 +94,9 @@ struct gmg_tree {
   std::vector<int> nbr_h, parent_h, pofs_h, flags_h, leaf_ids_h;
   long long total_cells = 0, n_leaf_cells = 0;
   bool adaptive = false;
+  int nrhs = 1;   // right-hand-side slots (fields are replicated per slot)
+  int nroot = 1;  // independent root blocks (trees of a forest), each with its own coarse solve
+  int ncr = 0;    // coarsest-level unknowns per root (nc = nroot * ncr)
 
   // walls
   int wall_type[6] = {0, 0, 0, 0, 0, 0};
@@ -97,7 +115,7 @@ struct gmg_tree {
   std::vector<uint8_t> mask_h;    // per block ncell (inspection)
   std::vector<long long> mask_base_h;
   int nc = 0;                     // coarsest-level unknowns
-  std::vector<double> cinv_h;     // inverse of the coarsest-level operator (nc x nc)
+  std::vector<double> cinv_h;     // inverses of the coarsest-level operator, per root (nroot x ncr x ncr)
 
   // device workspace
   bool bound = false, owns_ws = false;
@@ -108,10 +126,11 @@ struct gmg_tree {
   double *d_phi = nullptr, *d_b = nullptr, *d_old = nullptr;
   float *f_phi = nullptr, *f_b = nullptr, *f_old = nullptr;
   double *d_st = nullptr, *d_bterm = nullptr, *d_cinv = nullptr, *d_partials = nullptr, *d_red = nullptr;
+  int *d_active = nullptr, *h_active = nullptr;  // slot mask (device, pinned host mirror)
   float *f_st = nullptr;
   unsigned char *d_spec = nullptr;
   gmg::LvArgs *d_lvtab = nullptr;  // per-level descriptors (phi in the first buffer)
-  double *h_red = nullptr;  // pinned host mirror of d_red
+  double *h_red = nullptr;  // pinned host mirror of d_red ([nrhs][4])
   long long launches = 0;
 
   std::vector<char> level_has_leaves;  // index l - lmin
@@ -143,6 +162,7 @@ struct gmg_tree {
   size_t prof_used = 0;
 
   gmg::LevelInfo &lev(int l) { return levels[l - lmin]; }
+  int leaf_ncell() const { return levels.back().ncell; }  // cells of a leaf block (every leaf is on a level >= 1)
   const gmg::LevelInfo &lev(int l) const { return levels[l - lmin]; }
 };
 

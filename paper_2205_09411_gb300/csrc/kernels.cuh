@@ -323,6 +323,18 @@ __device__ __forceinline__ void cell_xyz(int c, int n, int *x, int *y, int *z) {
   *z = D == 3 ? c / (n * n) : 0;
 }
 
+// Work item of a per-level launch: the grid holds count x nrhs CTAs with the
+// slot index fastest, so that the slots of one block run side by side and
+// share its tables and stencil through L2.  Returns false for a frozen slot.
+template <typename T>
+__device__ __forceinline__ bool slot_item(const GmgView<T> &V, const LvArgs &L, int *bid, GmgView<T> *W) {
+  const int r = (int)(blockIdx.x % (unsigned)V.nrhs);
+  *bid = L.first + (int)(blockIdx.x / (unsigned)V.nrhs);
+  if (!V.active[r]) return false;
+  *W = slot_view(V, r);
+  return true;
+}
+
 // One red (color 0) or black (color 1) half-sweep of Gauss-Seidel on every
 // block of a level (Sec. 2.2, readings S and SW):
 // phi_i <- (b_i - sum_j c_ij phi_j) / c_ii on the cells of one colour.
@@ -359,7 +371,10 @@ __device__ void smooth_block(const GmgView<T> &V, const LvArgs &L, const LvArgs 
 template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kThreads) k_smooth(GmgView<T> V, LvArgs L, LvArgs Lp, int color) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  smooth_block<T, D, NT>(V, L, Lp, L.first + blockIdx.x, color, smem_raw);
+  int bid;
+  GmgView<T> W;
+  if (!slot_item(V, L, &bid, &W)) return;
+  smooth_block<T, D, NT>(W, L, Lp, bid, color, smem_raw);
 }
 
 // Residual r = b - A phi (Eq. (residual)) of every cell, restricted to the
@@ -406,7 +421,10 @@ __device__ void resid_restrict_block(const GmgView<T> &V, const LvArgs &L, const
 template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kThreads) k_resid_restrict(GmgView<T> V, LvArgs L, LvArgs Lp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  resid_restrict_block<T, D, NT>(V, L, Lp, L.first + blockIdx.x, smem_raw);
+  int bid;
+  GmgView<T> W;
+  if (!slot_item(V, L, &bid, &W)) return;
+  resid_restrict_block<T, D, NT>(W, L, Lp, bid, smem_raw);
 }
 
 // FAS coarse right-hand side on covered cells: b <- A phi + (restricted r);
@@ -451,22 +469,32 @@ __device__ void fas_block(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
 template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kThreads) k_fas(GmgView<T> V, LvArgs L, LvArgs Lp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  fas_block<T, D, NT>(V, L, Lp, L.first + blockIdx.x, smem_raw);
+  int bid;
+  GmgView<T> W;
+  if (!slot_item(V, L, &bid, &W)) return;
+  fas_block<T, D, NT>(W, L, Lp, bid, smem_raw);
 }
 
-// Coarsest level: phi = A^-1 b with the FP64 inverse, one warp per row.
+// Coarsest level: phi = A^-1 b with the FP64 inverse of each root's
+// operator (block-diagonal over the nroot independent roots), one warp per
+// row and slot.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_coarse(const double *__restrict__ Ainv, int M, const T *__restrict__ b,
-                                                     T *__restrict__ phi) {
+__global__ void __launch_bounds__(kThreads) k_coarse(GmgView<T> V, LvArgs Lc, const double *__restrict__ Ainv,
+                                                     int ncr, int nroot) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = blockIdx.x * (kThreads / 32) + warp;
-  if (row >= M) return;
-  const double *a = Ainv + (size_t)row * M;
+  const long long item = (long long)blockIdx.x * (kThreads / 32) + warp;
+  const int M = ncr * nroot;
+  if (item >= (long long)M * V.nrhs) return;
+  const int r = (int)(item / M), row = (int)(item % M);
+  if (!V.active[r]) return;
+  const int k = row / ncr, i = row - k * ncr;
+  const double *a = Ainv + ((size_t)k * ncr + i) * ncr;
+  const T *b = V.b + r * V.rs_f + Lc.off + (size_t)k * ncr;
   double s = 0.0;
-  for (int j = lane; j < M; j += 32) s += a[j] * (double)b[j];
+  for (int j = lane; j < ncr; j += 32) s += a[j] * (double)b[j];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) phi[row] = T(s);
+  if (lane == 0) V.phi[r * V.rs_phi + Lc.poff + row] = T(s);
 }
 
 // (Bi/tri)linear prolongation of the coarse correction phi - old
@@ -551,13 +579,18 @@ __device__ void prolong_block(const GmgView<T> &V, const LvArgs &L, const LvArgs
 template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kThreads) k_prolong(GmgView<T> V, LvArgs L, LvArgs Lp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  prolong_block<T, D, NT>(V, L, Lp, L.first + blockIdx.x, smem_raw);
+  int bid;
+  GmgView<T> W;
+  if (!slot_item(V, L, &bid, &W)) return;
+  prolong_block<T, D, NT>(W, L, Lp, bid, smem_raw);
 }
 
 // phi of covered cells <- mean of the children (composite consistency).
 template <typename T, int D, int NT>
-__global__ void __launch_bounds__(kThreads) k_restrict_phi(GmgView<T> V, LvArgs L, LvArgs Lp) {
-  const int bid = L.first + blockIdx.x;
+__global__ void __launch_bounds__(kThreads) k_restrict_phi(GmgView<T> V0, LvArgs L, LvArgs Lp) {
+  int bid;
+  GmgView<T> V;
+  if (!slot_item(V0, L, &bid, &V)) return;
   const int n = NT ? NT : L.n, hn = n / 2;
   const long long base = L.poff + (long long)(bid - L.first) * NCELL;
   const int P = V.parent[bid], po = V.pofs[bid];
@@ -609,14 +642,19 @@ __device__ __forceinline__ void block_reduce3(double s2, double mx, double b2, d
 // the residual itself is written as float (right-hand side of the FP32
 // correction V-cycle in the mixed path).
 template <typename T, int D, int NT>
-__global__ void __launch_bounds__(kThreads) k_resnorm(GmgView<T> V, LvArgs L, LvArgs Lp, double *partials,
-                                                      float *rout) {
+__global__ void __launch_bounds__(kThreads) k_resnorm(GmgView<T> V0, LvArgs L, LvArgs Lp, double *partials,
+                                                      float *rout, int nbt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int bid = L.first + blockIdx.x;
+  int bid;
+  GmgView<T> V;
+  const int slot = (int)(blockIdx.x % (unsigned)V0.nrhs);
+  if (!slot_item(V0, L, &bid, &V)) return;  // a frozen slot keeps its last partials
+  partials += ((size_t)slot * nbt + bid) * 3;
   if (V.flags[bid] & kHasChildren) {
-    if (threadIdx.x < 3) partials[(size_t)bid * 3 + threadIdx.x] = 0.0;
+    if (threadIdx.x < 3) partials[threadIdx.x] = 0.0;
     return;
   }
+  if (rout) rout += slot * V0.rs_f;
   const int n = NT ? NT : L.n;
   const TileGeo<T, D> G(n);
   T *tile = reinterpret_cast<T *>(smem_raw);
@@ -641,10 +679,11 @@ __global__ void __launch_bounds__(kThreads) k_resnorm(GmgView<T> V, LvArgs L, Lv
     const float bf = (float)bb;
     b2f = fmaf(bf, bf, b2f);
   }
-  block_reduce3((double)s2f, (double)mxf, (double)b2f, partials + (size_t)bid * 3);
+  block_reduce3((double)s2f, (double)mxf, (double)b2f, partials);
 }
 
-// Deterministic final reduction of the per-block partials (fixed order).
+// Deterministic final reduction of the per-block partials (fixed order),
+// one CTA per slot.
 __global__ void __launch_bounds__(1024) k_reduce_partials(const double *partials, int nb, double *out,
                                                           const GridBar *bar);
 

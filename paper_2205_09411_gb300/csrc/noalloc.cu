@@ -45,7 +45,8 @@ int scratch_address(double **out) {
   return GMG_OK;
 }
 
-// Fixed-order reduction of the partials held in the scratch array; writes
+// Fixed-order reduction of the partials held in the scratch array (slot 0
+// of a tree with several right-hand-side slots); writes
 // ||r||_2 / ||b||_2 (or ||r||_2 when b = 0) and max |r| to out[0], out[1].
 __global__ void __launch_bounds__(1024) k_reduce_noalloc(int nb, double *out) {
   __shared__ double s[3][1024];
@@ -91,6 +92,9 @@ void launch_resnorm(gmg_tree *t, int l, double *partials, cudaStream_t s) {
   V.spec = t->d_spec;
   V.wneu = 0;
   for (int w = 0; w < 6; w++) V.wneu |= (t->wall_type[w] == GMG_WALL_NEUMANN ? 1 : 0) << w;
+  V.nrhs = 1;  // slot 0 only
+  V.rs_phi = V.rs_f = t->total_cells;
+  V.active = t->d_active;
   const gmg::LevelInfo &Li = t->lev(l);
   gmg::LvArgs L{Li.first, Li.count, Li.n, Li.ncell, Li.off, Li.h, Li.off};
   gmg::LvArgs Lp = L;
@@ -102,7 +106,8 @@ void launch_resnorm(gmg_tree *t, int l, double *partials, cudaStream_t s) {
   cudaFuncSetAttribute(gmg::k_resnorm<double, D, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(gmg::k_resnorm<double, D, NT>, cudaFuncAttributePreferredSharedMemoryCarveout,
                        (int)cudaSharedmemCarveoutMaxShared);
-  gmg::k_resnorm<double, D, NT><<<L.count, gmg::kThreads, sm, s>>>(V, L, Lp, partials, nullptr);
+  gmg::k_resnorm<double, D, NT><<<L.count, gmg::kThreads, sm, s>>>(V, L, Lp, partials, nullptr,
+                                                                  (int)t->blocks.size());
 }
 
 template <int D>
@@ -131,6 +136,9 @@ extern "C" int gmg_residual_noalloc(gmg_tree *t, double *out, void *stream) {
   // blocks on levels without leaves write no partials: clear the previous
   // call's contents first
   cudaError_t e = cudaMemsetAsync(scratch, 0, (size_t)nb * 3 * sizeof(double), s);
+  if (e != cudaSuccess) return gmg::set_error(std::string("cudaMemsetAsync: ") + cudaGetErrorString(e)), GMG_ERR_CUDA;
+  // slot 0 active (the slot mask is set by every entry point that runs kernels)
+  e = cudaMemsetAsync(t->d_active, 1, sizeof(int), s);
   if (e != cudaSuccess) return gmg::set_error(std::string("cudaMemsetAsync: ") + cudaGetErrorString(e)), GMG_ERR_CUDA;
   for (int l = t->lmin; l <= t->lmax; l++) {
     bool leaves = false;

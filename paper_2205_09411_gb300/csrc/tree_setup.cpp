@@ -563,6 +563,8 @@ int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, do
     }
   }
   T->nc = M;
+  T->ncr = M;
+  T->nroot = 1;
   if (!invert(M, A, T->cinv_h)) return set_error("singular coarsest-level operator"), GMG_ERR_INVALID_ARG;
   T->stencils_ready = true;
   return GMG_OK;

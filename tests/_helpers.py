@@ -33,18 +33,19 @@ def oracle_problem(p, n_down=2, n_up=2, eps_tol=1e-8, mask_factor=1.5, w_min=0.0
     return t
 
 
-def gpu_problem(p, n_down=2, n_up=2, eps_tol=1e-8, mask_factor=1.5, w_min=0.0, bind=True, rhs=True):
-    """The same problem as oracle_problem, built through the CUDA library's C ABI."""
+def gpu_problem(p, n_down=2, n_up=2, eps_tol=1e-8, mask_factor=1.5, w_min=0.0, bind=True, rhs=True, nrhs=1):
+    """The same problem as oracle_problem, built through the CUDA library's C ABI
+    (with nrhs right-hand-side slots; rhs=True fills only a single slot)."""
     import paper_2205_09411_gb300 as G
     t = G.Tree(p["dim"], p["N"], p["cb"], p["lo"], p["h1"], p["max_level"], refine=p["refine"],
                max_coarse_cells=p.get("max_coarse_cells") or (64 if p["dim"] == 2 else 512),
-               n_down=n_down, n_up=n_up, eps_tol=eps_tol, mask_factor=mask_factor, w_min=w_min)
+               n_down=n_down, n_up=n_up, eps_tol=eps_tol, mask_factor=mask_factor, w_min=w_min, nrhs=nrhs)
     t.set_walls(p["walls"], values=p.get("wall_values"), fn=p.get("wall_fn"))
     kind, params = p["lsf"]
     t.store_stencils(None if kind == "none" else (kind, params), p["phib"])
     if bind:
         t.bind()
-        if rhs:
+        if rhs and nrhs == 1:
             t.set_rhs(np.asarray(p["rhs"](t.leaf_centers()), dtype=np.float64))
     return t
 
