@@ -17,6 +17,11 @@ before every timed step.  `e2e` repeats the measurement through the public
 API with the right-hand side copied from pinned host memory and the solution
 copied back inside the timed region.
 
+Beside the headline, `batched_needle` reports the batched workload: the
+adaptive 7-level needle-electrode tree (8^3 blocks, 30,195,712 leaf cells)
+holding 32 Gaussian-charge right-hand sides, each step one batched solve of
+all 32 to 1e-8 in one tree (mixed and FP64), with its own roofline.
+
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank solves its own replica (replicas only: the method
 has no cross-problem exchange); the value is the sum over ranks.
@@ -50,6 +55,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--skip-needle", action="store_true", help="leave out the batched needle workload")
     return ap.parse_args()
 
 
@@ -152,13 +158,33 @@ def build_tree(G, p):
     return t
 
 
-def algorithmic_bytes(kind, prec, level, t, leaf_level):
-    """Minimum HBM bytes one launch of a kernel must move (unique data)."""
+def coop_split(t):
+    """Highest level the cooperative coarse-cycle launch covers (levels with
+    at most 160 blocks, the library's rule)."""
+    return max(l for l in range(t.lmin, t.lmax + 1) if t.level_info(l)[0] <= 160)
+
+
+def algorithmic_bytes(kind, prec, level, t, leaf_level, nrhs=1):
+    """Minimum bytes one launch of a kernel must move (unique data), for
+    nrhs right-hand-side slots (stencils are shared by the slots)."""
     S = 8 if prec == "fp64" else 4
+    if kind == "coarse_solve":  # every phase of the coarse levels, per slot
+        tot = 0.0
+        sw = 2 * 2  # (n_down + n_up) full sweeps of two half-sweeps each, 2 + 2
+        for l in range(t.lmin, coop_split(t) + 1):
+            nb, n, _ = t.level_info(l)
+            cells = nb * n ** 3
+            if l == t.lmin:
+                tot += nrhs * cells * 2 * S
+                continue
+            pnb, pn, _ = t.level_info(l - 1)
+            tot += nrhs * (cells * (sw * 2 * S + 2.25 * S + 2.25 * S) + pnb * pn ** 3 * 4 * S)
+        nb0, n0, _ = t.level_info(t.lmin)
+        return tot + (nb0 * n0 ** 3) ** 2 * 8  # coarsest-level inverse, once
     nb, n, _ = t.level_info(level)
-    cells = nb * n ** 3
+    cells = nb * n ** 3 * nrhs
     cut_cells = t.num_cut_blocks(level) * n ** 3
-    st = 7 * S  # 7-point stencil per cut cell
+    st = 7 * S  # 7-point stencil per cut cell (read once for all slots)
     if kind == "smooth":  # read phi, read b and write phi of one colour
         return cells * 2 * S + cut_cells * st / 2
     if kind == "resid_restrict":  # read phi, b; write parent phi, b
@@ -169,8 +195,8 @@ def algorithmic_bytes(kind, prec, level, t, leaf_level):
         return cells * 4 * S + cut_cells * st
     if kind == "resid_norm":  # read phi64, b64 (+ write r32 in the mixed path)
         return cells * (16 + 4) + cut_cells * 7 * 8
-    if kind == "accumulate":  # read e32, read/write phi64 on leaf cells
-        return cells * 20
+    if kind == "accumulate":  # read e32, read/write phi64 on the leaf cells of all levels
+        return t.n_leaf_cells * nrhs * 20
     return 0
 
 
@@ -243,6 +269,104 @@ def run_reference(args):
                             "sample": "%d serial FP64 oracle V-cycles of the 128^3 workload" % args.steps},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+def roofline_of(prof, t, nrhs, peak, peak_kind):
+    """Roofline of the kernel with the largest total time in a profiled
+    pass: algorithmic bytes per launch / CUDA-event time per launch."""
+    by_kind = {}
+    for kind, prec, level, cnt, ms in prof:
+        by_kind.setdefault((kind, prec), 0.0)
+        by_kind[(kind, prec)] += ms
+    prof_total = sum(by_kind.values())
+    dom_kind, dom_prec = max(by_kind, key=by_kind.get)
+    rows = [r for r in prof if r[0] == dom_kind and r[1] == dom_prec]
+    lev = max(rows, key=lambda r: r[4])[2]
+    row = [r for r in rows if r[2] == lev][0]
+    per_launch_ms = row[4] / row[3]
+    alg = algorithmic_bytes(dom_kind, dom_prec, lev, t, t.lmax, nrhs)
+    achieved = alg / (per_launch_ms * 1e-3) / 1e9
+    traffic = ncu_traffic(dom_kind, dom_prec, lev)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": "%s_%s_level%d" % (dom_kind, dom_prec, lev),
+            "per_launch_us": per_launch_ms * 1e3, "algorithmic_bytes": alg,
+            "share_of_kernel_time": by_kind[(dom_kind, dom_prec)] / prof_total,
+            "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind}
+    return roof, by_kind
+
+
+def run_needle(G, args, world, flush, stream):
+    """Batched needle workload: the adaptive 7-level needle tree (8^3
+    blocks, 30,195,712 leaf cells) with 32 Gaussian-charge right-hand sides
+    in one tree, each step one batched solve of all 32 to 1e-8, mixed and
+    FP64.  Right-hand sides are generated on the device (seeded)."""
+    import torch
+    R = 32
+    p = I.problem("c3", n_rhs=R)
+    t0 = time.perf_counter()
+    t = G.Tree(p["dim"], p["N"], p["cb"], p["lo"], p["h1"], p["max_level"], refine=p["refine"],
+               max_coarse_cells=p["max_coarse_cells"], w_min=p["w_min"], nrhs=R)
+    t.set_walls(p["walls"], values=p["wall_values"], fn=p["wall_fn"])
+    t.store_stencils(p["lsf"], p["phib"])
+    t.bind()
+    setup_s = time.perf_counter() - t0
+    n = t.n_leaf_cells
+    xc = torch.tensor(t.leaf_centers(), device="cuda")
+    g = torch.empty((R, n), dtype=torch.float64, device="cuda")
+    for r in range(R):
+        g[r] = I.charge_density_torch(xc, p["charges"][r])
+    del xc
+    torch.cuda.synchronize()
+
+    def one(prec, profile=False):
+        if profile:
+            t.profile(True)
+            t.profile_read()
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t.set_rhs(g)
+        st = t.solve(prec, args.tol, 60)
+        e1.record(stream)
+        e1.synchronize()
+        prof = None
+        if profile:
+            prof = t.profile_read()
+            t.profile(False)
+        return e0.elapsed_time(e1), st, t.last_launch_count() + 1, prof
+
+    res = {}
+    for name, prec in (("mixed", G.MIXED), ("fp64", G.FP64)):
+        one(prec)  # warm-up (graph capture)
+        barrier(world)
+        times, cyc, worst, launches = [], 0, 0.0, 0
+        for _ in range(max(1, args.steps)):
+            ms, st, nl, _ = one(prec)
+            times.append(ms)
+            cyc += sum(x["cycles"] for x in st["slots"])
+            worst = max(worst, st["rel_l2"])
+            launches += nl
+        total = allreduce_max(sum(times), world)
+        ts = sorted(times)
+        res[name] = {"p50_ms": float(np.percentile(ts, 50)), "p99_ms": float(np.percentile(ts, 99)),
+                     "solves_per_s": world * R * len(ts) / (total * 1e-3),
+                     "munks": world * n * cyc / (total * 1e-3) / 1e6,
+                     "cycles_per_solve": cyc / (R * len(ts)), "worst_final_rel_residual": worst,
+                     "gpu_launches_per_batch": launches / len(ts)}
+    _, _, _, prof = one(G.MIXED, profile=True)
+    peak, peak_kind = peaks()
+    roof, by_kind = roofline_of(prof, t, R, peak, peak_kind)
+    out = {"workload": "needle3d_adaptive_7levels_8^3blocks_32rhs_gaussian_mixed_to_1e-8", "unknowns": n,
+           "rhs": R, "blocks": t.n_blocks, "levels": [t.lmin, t.lmax], "setup_s": setup_s,
+           "latency_is": "one batched solve of all 32 right-hand sides from phi = 0",
+           "mixed": res["mixed"], "fp64": res["fp64"], "roofline": roof,
+           "kernel_ms_by_kind": {"%s_%s" % k: v for k, v in sorted(by_kind.items(), key=lambda kv: -kv[1])},
+           "kernel_us_per_launch": {"%s_%s_l%d" % (k, p_, lv): round(ms * 1e3 / cnt, 2)
+                                    for k, p_, lv, cnt, ms in prof}}
+    t.close()
+    del g
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_ours(args):
@@ -326,24 +450,7 @@ def run_ours(args):
 
     # roofline of the dominant kernel (largest total time in the timed region)
     peak, peak_kind = peaks()
-    by_kind = {}
-    for kind, prec, level, cnt, ms in mixed["prof"]:
-        by_kind.setdefault((kind, prec), 0.0)
-        by_kind[(kind, prec)] += ms
-    prof_total = sum(by_kind.values())
-    dom_kind, dom_prec = max(by_kind, key=by_kind.get)
-    rows = [r for r in mixed["prof"] if r[0] == dom_kind and r[1] == dom_prec]
-    lev = max(rows, key=lambda r: r[4])[2]
-    row = [r for r in rows if r[2] == lev][0]
-    per_launch_ms = row[4] / row[3]
-    alg = algorithmic_bytes(dom_kind, dom_prec, lev, t, t.lmax)
-    achieved = alg / (per_launch_ms * 1e-3) / 1e9
-    traffic = ncu_traffic(dom_kind, dom_prec, lev)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "%s_%s_level%d" % (dom_kind, dom_prec, lev),
-                "per_launch_us": per_launch_ms * 1e3, "algorithmic_bytes": alg,
-                "share_of_kernel_time": by_kind[(dom_kind, dom_prec)] / prof_total,
-                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind}
+    roofline, by_kind = roofline_of(mixed["prof"], t, 1, peak, peak_kind)
 
     result = {
         "metric": METRIC, "value": munks(mixed), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -363,6 +470,9 @@ def run_ours(args):
                                  for k, p_, lv, cnt, ms in mixed["prof"]},
         "clocks": clk,
     }
+    t.close()
+    if not args.skip_needle:
+        result["batched_needle"] = run_needle(G, args, world, flush, stream)
     if rank == 0 and world == 1:
         result["cpu_baseline"] = cpu_baseline(p)
     if rank == 0:

@@ -12,6 +12,18 @@ analytic test problems, not datasets):
 * ``c2``  3D, [0,1]^3, 128^3 cells in 16^3 blocks (coarse levels 8^3 and
   4^3 inside the root block); sphere |x-c| - 0.2; Laplace (g = 0) with
   phi = 1 on the sphere and 0 on the walls.
+* ``c3``  3D adaptive needle electrode: [0,1]^3, 8^3-cell blocks, levels 1..7
+  (finest cell 1/512); capsule level set around the segment x = y = 1/2,
+  z in [0.6, 1] with radius 0.02 (hemispherical tip at z = 0.58), phi = 1 on
+  the needle, phi = 0 on the bottom wall, zero flux on the other walls.
+  Refinement rule of Sec. 4.1's refined test with r the distance to the
+  needle axis: refine while dx > dx_min max(1, r / R_ref), r measured from
+  the block; R_ref = NEEDLE_RREF gives about 3.0e7 leaf cells after 2:1
+  balance.  Right-hand sides: sums of 1..20 Gaussian charge clouds
+  (``gaussian_charges``).  The needle (diameter 0.04) is thinner than the
+  cells of levels 0..3, so the unresolved-boundary search of Sec. 3.6.3 is
+  on with w_min = 0.008 (the paper's 3D value); without it the V-cycle
+  diverges on this geometry.
 * ``sphere2d`` / ``sphere3d``  the convergence test of Sec. 4.1: a domain of
   unit size centred at the origin, f = |x| - R with R = 1/4, walls given by
   the analytic solutions log(|x|/R) (2D) and 1 - R/|x| (3D), phi_b = 0.
@@ -61,6 +73,68 @@ def sphere_solution_vec(xc, dim, R=0.25):
     return np.log(r / R) if dim == 2 else 1.0 - R / r
 
 
+# needle electrode: axis segment a -> b (along z), radius
+NEEDLE_A = (0.5, 0.5, 0.6)
+NEEDLE_B = (0.5, 0.5, 1.0)
+NEEDLE_RADIUS = 0.02
+NEEDLE_RREF = 0.13  # refinement scale: 30,195,712 leaf cells at 7 levels after 2:1 balance
+
+
+def needle_refine(r_ref, N=8, h1=1.0 / 8, max_level=7):
+    """refine(level, bix): dx_level > dx_min * max(1, r / r_ref), with r the
+    distance from the block to the needle's axis segment."""
+    dx_min = h1 / 2 ** (max_level - 1)
+
+    def f(level, bix):
+        dx = h1 / 2 ** (level - 1)
+        bs = N * dx
+        lo = [bix[d] * bs for d in range(3)]
+        ex = max(lo[0] - NEEDLE_A[0], NEEDLE_A[0] - (lo[0] + bs), 0.0)
+        ey = max(lo[1] - NEEDLE_A[1], NEEDLE_A[1] - (lo[1] + bs), 0.0)
+        ez = max(lo[2] - NEEDLE_B[2], NEEDLE_A[2] - (lo[2] + bs), 0.0)
+        r = math.sqrt(ex * ex + ey * ey + ez * ez)
+        return dx > dx_min * max(1.0, r / r_ref)
+    return f
+
+
+def gaussian_charges(n_rhs: int, index: int):
+    """Seeded charge clouds of the batched needle workload: per right-hand
+    side K ~ U{1..20} Gaussians with centres U[0,1]^3, widths U[0.01, 0.05]
+    and amplitudes N(0, 1e3^2) rounded to FP32.  Returns a list of
+    (centres K x 3, widths K, amplitudes K) per right-hand side."""
+    rng = rng_for(index)
+    out = []
+    for _ in range(n_rhs):
+        k = int(rng.integers(1, 21))
+        c = rng.uniform(0.0, 1.0, size=(k, 3))
+        w = rng.uniform(0.01, 0.05, size=k)
+        a = rng.normal(0.0, 1e3, size=k).astype(np.float32).astype(np.float64)
+        out.append((c, w, a))
+    return out
+
+
+def charge_density(xc, charges):
+    """g(x) = sum_k a_k exp(-|x - c_k|^2 / (2 w_k^2)) at the points xc (n x 3)."""
+    c, w, a = charges
+    g = np.zeros(len(xc))
+    for k in range(len(a)):
+        d2 = np.sum((xc - c[k]) ** 2, axis=1)
+        g += a[k] * np.exp(-d2 / (2.0 * w[k] ** 2))
+    return g
+
+
+def charge_density_torch(xc, charges):
+    """The same sum on a torch tensor of points (any device)."""
+    import torch
+    c, w, a = charges
+    g = torch.zeros(xc.shape[0], dtype=torch.float64, device=xc.device)
+    for k in range(len(a)):
+        ck = torch.tensor(c[k], dtype=torch.float64, device=xc.device)
+        d2 = ((xc - ck) ** 2).sum(dim=1)
+        g += float(a[k]) * torch.exp(-d2 / (2.0 * float(w[k]) ** 2))
+    return g
+
+
 def problem(name: str, **over) -> dict:
     """Problem definition: geometry, boundary data and right-hand side.
 
@@ -69,7 +143,8 @@ def problem(name: str, **over) -> dict:
     params), walls (types), wall_values or wall_fn, phib (value or callable),
     rhs (callable centres -> g), n_vcycles, tol, and optionally
     max_coarse_cells (size of the coarsest level, default 64 in 2D and 512
-    in 3D).
+    in 3D) and w_min (unresolved-boundary threshold of Sec. 3.6.3, default
+    0 = off).
     """
     if name == "c1":
         p = dict(dim=2, N=8, cb=(1, 1, 1), lo=(0.0, 0.0, 0.0), h1=1.0 / 8, max_level=4, refine=None,
@@ -80,6 +155,17 @@ def problem(name: str, **over) -> dict:
                  lsf=("sphere", (0.5, 0.5, 0.5, 0.2)), walls=(WALL_DIRICHLET,) * 6,
                  wall_values=(0.0,) * 6, wall_fn=None, phib=1.0,
                  rhs=lambda xc: np.zeros(len(xc)), n_vcycles=12, tol=1e-8, index=1, max_coarse_cells=64)
+    elif name == "c3":
+        ml = over.pop("max_level", 7)
+        rref = over.pop("r_ref", NEEDLE_RREF)
+        charges = gaussian_charges(over.pop("n_rhs", 32), 2)
+        p = dict(dim=3, N=8, cb=(1, 1, 1), lo=(0.0, 0.0, 0.0), h1=1.0 / 8, max_level=ml,
+                 refine=needle_refine(rref, max_level=ml),
+                 lsf=("capsule", NEEDLE_A + NEEDLE_B + (NEEDLE_RADIUS,)),
+                 walls=(WALL_NEUMANN, WALL_NEUMANN, WALL_NEUMANN, WALL_NEUMANN, WALL_DIRICHLET, WALL_NEUMANN),
+                 wall_values=(0.0,) * 6, wall_fn=None, phib=1.0, charges=charges,
+                 rhs=lambda xc, _c=charges: charge_density(xc, _c[0]), n_vcycles=12, tol=1e-8, index=2,
+                 max_coarse_cells=64, w_min=0.008)
     elif name in ("sphere2d", "sphere3d"):
         dim = 2 if name == "sphere2d" else 3
         p = dict(dim=dim, N=8, cb=(1, 1, 1), lo=(-0.5, -0.5, -0.5 if dim == 3 else 0.0), h1=1.0 / 8,

@@ -267,6 +267,9 @@ int gmg_profile_read(gmg_tree *tree, int cap, int *kind, int *prec, int *level, 
 #define GMG_OPT_SPIN_LIMIT 3
 #define GMG_OPT_FUSED_SWEEPS 4 /* [0] FP32 levels without refinement boundaries: all N_down (N_up)
                                   half-sweeps of a visit in one pass over a tile with a halo */
+#define GMG_OPT_CTA_THREADS 5  /* [0] threads per CTA of the smoothing, residual, restriction and
+                                  FAS kernels: 64, 128 or 256; 0 = 64 for blocks of at most 512
+                                  cells, 256 otherwise */
 int gmg_set_option(gmg_tree *tree, int option, long long value);
 
 /* Failure-detection self test: launches a cooperative kernel whose grid

@@ -385,7 +385,7 @@ class Tree:
         return dict(rc=rc, cycles=max(x["cycles"] for x in slots), rel_l2=max(x["rel_l2"] for x in slots),
                     linf=max(x["linf"] for x in slots), bnorm=min(x["bnorm"] for x in slots), slots=slots)
 
-    OPTIONS = {"graphs": 1, "coarse_coop": 2, "spin_limit": 3, "fused_sweeps": 4}
+    OPTIONS = {"graphs": 1, "coarse_coop": 2, "spin_limit": 3, "fused_sweeps": 4, "cta_threads": 5}
 
     def set_option(self, name, value):
         _check(load().gmg_set_option(self.h, self.OPTIONS[name], int(value)))

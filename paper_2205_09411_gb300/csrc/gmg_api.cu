@@ -422,6 +422,7 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s) {
   for (int l = t->lmax; l > ls; l--) {
     LvArgs L = lv(t, l), Lp = lv(t, l - 1);
     const size_t sm = tile_bytes<T>(t, l);
+    const int nt_l = cta_threads(t, l), nt_p = cta_threads(t, l - 1);
     const bool fused = fused_level<T>(t, l);
     if (fused) {  // N_down steps in one pass into the second buffer
       launch_fused<T, D>(t, s, l, t->prm.n_down, L.off, L.off + other);
@@ -432,14 +433,14 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s) {
       if (!fused)
         for (int k = 0; k < t->prm.n_down; k++)
           for (int c = 0; c < 2; c++)
-            launch(t, s, 0, P, l, [&] { k_smooth<T, D, NT><<<L.count * R, kThreads, sm, s>>>(V, L, Lp, c); });
-      launch(t, s, 1, P, l, [&] { k_resid_restrict<T, D, NT><<<L.count * R, kThreads, sm, s>>>(V, L, Lp); });
+            launch(t, s, 0, P, l, [&] { k_smooth<T, D, NT><<<L.count * R, nt_l, sm, s>>>(V, L, Lp, c); });
+      launch(t, s, 1, P, l, [&] { k_resid_restrict<T, D, NT><<<L.count * R, nt_l, sm, s>>>(V, L, Lp); });
     });
     LvArgs Lpp = l - 2 >= t->lmin ? lv(t, l - 2) : Lp;
     const size_t smp = tile_bytes<T>(t, l - 1);
     with_nt<D>(Lp.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
-      launch(t, s, 2, P, l - 1, [&] { k_fas<T, D, NT><<<Lp.count * R, kThreads, smp, s>>>(V, Lp, Lpp); });
+      launch(t, s, 2, P, l - 1, [&] { k_fas<T, D, NT><<<Lp.count * R, nt_p, smp, s>>>(V, Lp, Lpp); });
     });
   }
   if (t->use_coop) {
@@ -458,6 +459,7 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s) {
     const int hm = L.n / 2 + 2;
     const size_t psm = sizeof(T) * (size_t)(D == 3 ? hm * hm * hm : hm * hm);
     const size_t sm = tile_bytes<T>(t, l);
+    const int nt_l = cta_threads(t, l);
     const bool fused = fused_level<T>(t, l);
     if (fused) L.poff = L.off + other;  // the down leg left phi in the second buffer
     with_nt<D>(L.n, [&](auto nt) {
@@ -466,7 +468,7 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s) {
       if (!fused)
         for (int k = 0; k < t->prm.n_up; k++)
           for (int c = 0; c < 2; c++)
-            launch(t, s, 0, P, l, [&] { k_smooth<T, D, NT><<<L.count * R, kThreads, sm, s>>>(V, L, Lp, c); });
+            launch(t, s, 0, P, l, [&] { k_smooth<T, D, NT><<<L.count * R, nt_l, sm, s>>>(V, L, Lp, c); });
     });
     if (fused) launch_fused<T, D>(t, s, l, t->prm.n_up, L.off + other, L.off);  // back to the first buffer
   }
@@ -475,7 +477,8 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s) {
       LvArgs L = lv(t, l), Lp = lv(t, l - 1);
       with_nt<D>(L.n, [&](auto nt) {
         constexpr int NT = decltype(nt)::value;
-        launch(t, s, 5, P, l, [&] { k_restrict_phi<T, D, NT><<<L.count * R, kThreads, 0, s>>>(V, L, Lp); });
+        launch(t, s, 5, P, l,
+               [&] { k_restrict_phi<T, D, NT><<<L.count * R, cta_threads(t, l), 0, s>>>(V, L, Lp); });
       });
     }
   }
@@ -501,7 +504,7 @@ int residual_impl(gmg_tree *t, cudaStream_t s, float *rout) {
     with_nt<D>(L.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
       launch(t, s, 6, 0, l, [&] {
-        k_resnorm<double, D, NT><<<L.count * t->nrhs, kThreads, sm, s>>>(V, L, Lp, t->d_partials, rout,
+        k_resnorm<double, D, NT><<<L.count * t->nrhs, cta_threads(t, l), sm, s>>>(V, L, Lp, t->d_partials, rout,
                                                                        (int)t->blocks.size());
       });
     });
@@ -525,7 +528,9 @@ int restrict_all_phi64(gmg_tree *t, cudaStream_t s) {
     LvArgs L = lv(t, l), Lp = lv(t, l - 1);
     with_nt<D>(L.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
-      launch(t, s, 5, 0, l, [&] { k_restrict_phi<double, D, NT><<<L.count * t->nrhs, kThreads, 0, s>>>(V, L, Lp); });
+      launch(t, s, 5, 0, l, [&] {
+        k_restrict_phi<double, D, NT><<<L.count * t->nrhs, cta_threads(t, l), 0, s>>>(V, L, Lp);
+      });
     });
   }
   CUDA_TRY(cudaGetLastError());
@@ -1146,6 +1151,11 @@ int gmg_set_option(gmg_tree *t, int option, long long value) {
     case GMG_OPT_GRAPHS: t->use_graphs = value != 0; break;
     case GMG_OPT_COARSE_COOP: t->use_coop = value != 0; break;
     case GMG_OPT_FUSED_SWEEPS: t->use_fused = value != 0; break;
+    case GMG_OPT_CTA_THREADS:
+      if (value != 0 && value != 64 && value != 128 && value != 256)
+        return set_error("CTA threads must be 0 (by block size), 64, 128 or 256"), GMG_ERR_INVALID_ARG;
+      t->cta_threads = (int)value;
+      break;
     case GMG_OPT_SPIN_LIMIT:
       if (value < 1) return set_error("spin limit must be positive"), GMG_ERR_INVALID_ARG;
       t->spin_limit = value;

@@ -145,6 +145,7 @@ struct gmg_tree {
   bool use_graphs = true;
   bool use_coop = true;       // coarse levels in one cooperative launch
   bool use_fused = false;     // temporally blocked FP32 sweeps on uniform levels
+  int cta_threads = 0;        // threads per CTA of the block kernels (0: by block size)
   std::vector<char> level_complete;  // every block has all 26 neighbours on its level (or walls)
   int coop_split = 0;         // highest level run inside that launch
   long long spin_limit = 1LL << 24;
@@ -167,6 +168,14 @@ struct gmg_tree {
 };
 
 namespace gmg {
+// Threads per CTA of the smoothing, residual, restriction and FAS kernels on
+// level l: small blocks take smaller CTAs, so that more of them (and more of
+// their tile loads) are resident per SM.
+inline int cta_threads(const gmg_tree *t, int l) {
+  if (t->cta_threads) return t->cta_threads;
+  return t->lev(l).ncell <= 512 ? 64 : 256;
+}
+
 void set_error(const std::string &msg);
 int build_tree(gmg_tree *T, const gmg_domain *dom);
 int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, double phib_const);

@@ -11,7 +11,7 @@
 
 namespace gmg {
 
-constexpr int kThreads = 256;      // threads per CTA of the per-level kernels
+constexpr int kThreads = 256;      // threads per CTA of the per-level kernels (at most; see cta_threads)
 constexpr int kCoopThreads = 512;  // threads per CTA of the cooperative coarse cycle
 
 // cells of a block of side n (compile-time when n is)
@@ -100,13 +100,15 @@ __device__ __forceinline__ bool resolve_s(const int *s_nb, int bid, const LvArgs
 // Refinement-boundary ghost (reading G): g = f/3 + 2/3 c_hat, with f the
 // adjacent fine cell and c_hat the coarse cell containing the ghost centre
 // shifted by central tangential slopes (+-1/4 coarse cell).
+// `own` holds the block's own cells (phi, or old for a covered block in the
+// FAS kernel).
 template <typename T, int D>
 __device__ __noinline__ T refine_ghost(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, const int *p,
-                                       int a) {
+                                       int a, const T *own) {
   const int n = L.n;
   int q[3] = {p[0], p[1], p[2]};
   q[a] = p[a] < 0 ? 0 : n - 1;
-  const T f = V.phi[L.poff + (long long)(bid - L.first) * L.ncell + q[0] + n * (q[1] + (D == 3 ? n * q[2] : 0))];
+  const T f = own[q[0] + n * (q[1] + (D == 3 ? n * q[2] : 0))];
   const long long dp = Lp.poff - Lp.off;  // phi of the coarse level may live in the second buffer
   const int P = V.parent[bid], po = V.pofs[bid];
   const int pofs[3] = {po & 1023, (po >> 10) & 1023, (po >> 20) & 1023};
@@ -205,10 +207,14 @@ __device__ __forceinline__ unsigned char *level_flags(T *sbv, int ncell) {
 // the neighbours' faces follow as element cp.async; wall ghosts (reflection
 // of the adjacent cell, homogeneous sign) and refinement-boundary ghosts
 // (reading G) are filled once the copies have landed.  Ends with a barrier.
-template <typename T, int D, int NT>
+// FAS: the tile of a covered block for the FAS kernel, whose phi (and that
+// of covered neighbours) the restriction left in `old` (see
+// resid_restrict_block); leaf neighbours' phi is read from phi.
+template <typename T, int D, int NT, bool FAS = false>
 __device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, T *tile,
                           T *sbv = nullptr, unsigned char *sflag = nullptr, long long sb = -1) {
   __shared__ int s_nb[6];
+  __shared__ int s_cov[6];
   __shared__ int s_fl;
   const int n = NT ? NT : L.n;
   const TileGeo<T, D> G(n);
@@ -216,23 +222,26 @@ __device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
   if (threadIdx.x < 2 * D) {
     const int a = threadIdx.x >> 1, side = threadIdx.x & 1;
     const int o[3] = {a == 0 ? 2 * side - 1 : 0, a == 1 ? 2 * side - 1 : 0, a == 2 ? 2 * side - 1 : 0};
-    s_nb[threadIdx.x] = V.nbr[(size_t)bid * kNbr + nbr_slot(o[0], o[1], o[2])];
+    const int id = V.nbr[(size_t)bid * kNbr + nbr_slot(o[0], o[1], o[2])];
+    s_nb[threadIdx.x] = id;
+    s_cov[threadIdx.x] = FAS && id >= 0 ? (V.flags[id] & kHasChildren) : 0;
   }
   if (threadIdx.x == 0) s_fl = V.flags[bid];
   const long long base = L.off + (long long)(bid - L.first) * ncell;   // b
   const long long pbase = L.poff + (long long)(bid - L.first) * ncell; // phi
+  const T *own = FAS ? V.old + base : V.phi + pbase;  // the block's own cells
   constexpr int VEC = 16 / sizeof(T);
   if (n % VEC == 0) {  // 16-byte chunks never cross a row of the tile
     for (int i = threadIdx.x; i < ncell / VEC; i += blockDim.x) {
       const int c = i * VEC;
       const int x = c % n, y = (c / n) % n, z = D == 3 ? c / (n * n) : 0;
-      cp_async16(tile + G.idx(x, y, z), V.phi + pbase + c);
+      cp_async16(tile + G.idx(x, y, z), own + c);
       if (sbv) cp_async16(sbv + c, V.b + base + c);
     }
   } else {  // blocks narrower than one vector (coarse sub-levels)
     for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
       const int x = c % n, y = (c / n) % n, z = D == 3 ? c / (n * n) : 0;
-      cp_async_elem(tile + G.idx(x, y, z), V.phi + pbase + c);
+      cp_async_elem(tile + G.idx(x, y, z), own + c);
       if (sbv) cp_async_elem(sbv + c, V.b + base + c);
     }
   }
@@ -258,8 +267,9 @@ __device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
     const int gn = side ? n : -1, sn = side ? 0 : n - 1;
     const int gx = a == 0 ? gn : u, gy = a == 1 ? gn : (a == 0 ? u : v), gz = a == 2 ? gn : v;
     const int qx = a == 0 ? sn : u, qy = a == 1 ? sn : (a == 0 ? u : v), qz = a == 2 ? sn : v;
+    const T *src = s_cov[f] ? V.old + L.off : V.phi + L.poff;
     cp_async_elem(tile + G.idx(gx, gy, gz),
-                  V.phi + L.poff + (long long)(id - L.first) * ncell + qx + n * (qy + (D == 3 ? n * qz : 0)));
+                  src + (long long)(id - L.first) * ncell + qx + n * (qy + (D == 3 ? n * qz : 0)));
   }
   cp_async_wait_all();
   __syncthreads();
@@ -277,7 +287,7 @@ __device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
       val = (((V.wneu >> f) & 1) ? T(1) : T(-1)) * tile[G.idx(mx, my, mz)];
     } else {
       const int g[3] = {gx, gy, gz};
-      val = refine_ghost<T, D>(V, L, Lp, bid, g, a);
+      val = refine_ghost<T, D>(V, L, Lp, bid, g, a, own);
     }
     tile[G.idx(gx, gy, gz)] = val;
   }
@@ -380,6 +390,10 @@ __global__ void __launch_bounds__(kThreads) k_smooth(GmgView<T> V, LvArgs L, LvA
 // Residual r = b - A phi (Eq. (residual)) of every cell, restricted to the
 // parent as the mean of the 2^D children, together with phi (Sec. 2.2):
 // parent phi <- mean phi, parent b <- mean r (the FAS kernel adds A phi).
+// The restricted phi goes to the parent level's `old` field (dead until the
+// FAS kernel sets it): other CTAs of this launch may still read the parent
+// level's phi for their refinement-boundary ghosts, and must see the values
+// from before the restriction, as the sequential order has it.
 template <typename T, int D, int NT>
 __device__ void resid_restrict_block(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, unsigned char *smem_raw) {
   const int n = NT ? NT : L.n, hn = n / 2;
@@ -393,7 +407,6 @@ __device__ void resid_restrict_block(const GmgView<T> &V, const LvArgs &L, const
   const T inv_h2 = T(1.0 / (L.h * L.h));
   const int pofs[3] = {po & 1023, (po >> 10) & 1023, (po >> 20) & 1023};
   const long long pbase = Lp.off + (long long)(P - Lp.first) * Lp.ncell;
-  const long long pdelta = Lp.poff - Lp.off;
   const int pn = Lp.n;
   const int ncq = D == 3 ? hn * hn * hn : hn * hn;
   const T w = T(1.0 / (1 << D));
@@ -413,7 +426,7 @@ __device__ void resid_restrict_block(const GmgView<T> &V, const LvArgs &L, const
           sr = sr + resid_cell<T, D>(V.st, (sb >= 0 && sfl[c]) ? sb : -1, tile, t, G.sy, G.sz, NCELL, c, inv_h2, sbv[c]);
         }
     const long long pc = pbase + (pofs[0] + qx) + pn * ((pofs[1] + qy) + (D == 3 ? pn * (pofs[2] + qz) : 0));
-    V.phi[pc + pdelta] = sp * w;
+    V.old[pc] = sp * w;
     V.b[pc] = sr * w;
   }
 }
@@ -428,7 +441,9 @@ __global__ void __launch_bounds__(kThreads) k_resid_restrict(GmgView<T> V, LvArg
 }
 
 // FAS coarse right-hand side on covered cells: b <- A phi + (restricted r);
-// old <- phi on every cell of the level (start of the coarse visit).
+// old <- phi on every cell of the level (start of the coarse visit).  A
+// covered block's restricted phi arrives in old (resid_restrict_block) and
+// is copied to phi here; covered neighbours' ghosts are read from old too.
 template <typename T, int D, int NT>
 __device__ void fas_block(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, unsigned char *smem_raw) {
   const int n = NT ? NT : L.n;
@@ -446,8 +461,9 @@ __device__ void fas_block(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
   T *sbv = tile + G.size;
   unsigned char *sfl = level_flags(sbv, NCELL);
   const long long sb = V.st_base[bid];
-  load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv, sfl, sb);
+  load_tile<T, D, NT, true>(V, L, Lp, bid, tile, sbv, sfl, sb);
   const T inv_h2 = T(1.0 / (L.h * L.h));
+  const long long pbase = L.poff + (long long)(bid - L.first) * NCELL;
   for (int c = threadIdx.x; c < NCELL; c += blockDim.x) {
     int x, y, z;
     cell_xyz<D>(c, n, &x, &y, &z);
@@ -462,7 +478,7 @@ __device__ void fas_block(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
       ap = diag * ph + s;
     }
     V.b[base + c] = ap + sbv[c];
-    V.old[base + c] = ph;
+    V.phi[pbase + c] = ph;  // old already holds ph
   }
 }
 
@@ -609,7 +625,8 @@ __global__ void __launch_bounds__(kThreads) k_restrict_phi(GmgView<T> V0, LvArgs
   }
 }
 
-// Block reduction of (sum r^2, max |r|, sum b^2) into partials[bid*3 ..].
+// Block reduction of (sum r^2, max |r|, sum b^2) into out[0..2] (CTAs of
+// up to kThreads threads).
 __device__ __forceinline__ void block_reduce3(double s2, double mx, double b2, double *out) {
   __shared__ double red[3][kThreads / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -627,7 +644,7 @@ __device__ __forceinline__ void block_reduce3(double s2, double mx, double b2, d
   __syncthreads();
   if (threadIdx.x == 0) {
     double a = 0.0, b = 0.0, c = 0.0;
-    for (int i = 0; i < kThreads / 32; i++) {
+    for (int i = 0; i < (int)(blockDim.x / 32); i++) {
       a += red[0][i];
       b = fmax(b, red[1][i]);
       c += red[2][i];

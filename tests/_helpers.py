@@ -17,8 +17,10 @@ def paper_values():
     return out
 
 
-def oracle_problem(p, n_down=2, n_up=2, eps_tol=1e-8, mask_factor=1.5, w_min=0.0, rhs=True):
+def oracle_problem(p, n_down=2, n_up=2, eps_tol=1e-8, mask_factor=1.5, w_min=None, rhs=True):
     import oracle as O
+    if w_min is None:
+        w_min = p.get("w_min", 0.0)
     kinds = {"none": O.LSF_NONE, "sphere": O.LSF_SPHERE, "capsule": O.LSF_CAPSULE,
              "ellipsoid": O.LSF_ELLIPSOID}
     t = O.OracleTree(p["dim"], p["N"], p["cb"], p["lo"], p["h1"], p["max_level"], refine=p["refine"],
@@ -33,10 +35,12 @@ def oracle_problem(p, n_down=2, n_up=2, eps_tol=1e-8, mask_factor=1.5, w_min=0.0
     return t
 
 
-def gpu_problem(p, n_down=2, n_up=2, eps_tol=1e-8, mask_factor=1.5, w_min=0.0, bind=True, rhs=True, nrhs=1):
+def gpu_problem(p, n_down=2, n_up=2, eps_tol=1e-8, mask_factor=1.5, w_min=None, bind=True, rhs=True, nrhs=1):
     """The same problem as oracle_problem, built through the CUDA library's C ABI
     (with nrhs right-hand-side slots; rhs=True fills only a single slot)."""
     import paper_2205_09411_gb300 as G
+    if w_min is None:
+        w_min = p.get("w_min", 0.0)
     t = G.Tree(p["dim"], p["N"], p["cb"], p["lo"], p["h1"], p["max_level"], refine=p["refine"],
                max_coarse_cells=p.get("max_coarse_cells") or (64 if p["dim"] == 2 else 512),
                n_down=n_down, n_up=n_up, eps_tol=eps_tol, mask_factor=mask_factor, w_min=w_min, nrhs=nrhs)
@@ -91,6 +95,7 @@ def parity_cases():
         "object_outside": dict(dim=2, N=8, cb=(1, 1, 1), lo=(0.0, 0.0, 0.0), h1=1 / 8, max_level=3, refine=None,
                                lsf=("sphere", (3.0, 3.0, 0.0, 0.5)), walls=(0, 0, 1, 1), wall_values=(1, -1, 0, 0),
                                wall_fn=None, phib=0.0, rhs=rng_rhs(25), index=25),
+        "needle4": I.problem("c3", max_level=4, n_rhs=4),
         "single_level": dict(dim=2, N=8, cb=(1, 1, 1), lo=(0.0, 0.0, 0.0), h1=1 / 8, max_level=1, refine=None,
                              lsf=("sphere", (0.5, 0.5, 0.0, 0.3)), walls=(0, 0, 0, 0), wall_values=(0, 0, 0, 0),
                              wall_fn=None, phib=1.0, rhs=rng_rhs(26), index=26),

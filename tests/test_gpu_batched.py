@@ -154,3 +154,68 @@ def test_slot_bounds_rejected():
     t2.bind()
     with pytest.raises(G.GmgError):
         t2.set_num_rhs(4)  # after bind
+
+
+def test_needle_gaussian_slots_match_oracle():
+    """The batched needle workload at 4 levels: four Gaussian-charge
+    right-hand sides in one tree; FP64 iterates per slot against the oracle,
+    then a batched mixed solve whose every slot meets 1e-8 by the oracle's
+    own residual."""
+    import paper_2205_09411_gb300 as G
+    p = parity_cases()["needle4"]
+    R = 4
+    t = gpu_problem(p, nrhs=R)
+    xc = t.leaf_centers()
+    g = np.stack([I.charge_density(xc, p["charges"][r]) for r in range(R)])
+    t.set_rhs(g)
+    oracles = []
+    for r in range(R):
+        o = oracle_problem(p, rhs=False)
+        o.set_rhs(g[r])
+        oracles.append(o)
+    for k in range(4):
+        t.vcycle(1)
+        got = t.solution()
+        for r in range(R):
+            oracles[r].vcycle(1)
+            ref = oracles[r].solution()
+            err = np.abs(got[r] - ref).max() / np.abs(ref).max()
+            assert err <= 1e-12, "slot %d cycle %d: %.3e" % (r, k + 1, err)
+    t.set_rhs(g)
+    st = t.solve(G.MIXED, 1e-8, 60)
+    phi = t.solution()
+    for r in range(R):
+        assert st["slots"][r]["rel_l2"] <= 1e-8
+        oracles[r].set_solution(phi[r])
+        l2, _, bn = oracles[r].residual()
+        assert l2 / bn <= 1.05e-8, (r, l2 / bn)
+
+
+def test_many_waves_adaptive_slots_match_oracle():
+    """A launch many CTA waves deep (the 5-level needle tree with 16 slots:
+    about 16,000 CTAs per fine-level launch) still gives the oracle's
+    iterates: no CTA reads coarse values that another CTA of the same launch
+    rewrites (refinement-boundary ghosts during the restriction)."""
+    import gmg_inputs as Imod
+    p = Imod.problem("c3", max_level=5, n_rhs=2)
+    R = 16
+    t = gpu_problem(p, nrhs=R)
+    xc = t.leaf_centers()
+    g0 = I.charge_density(xc, p["charges"][0])
+    g1 = I.charge_density(xc, p["charges"][1])
+    g = np.stack([g0 if r % 2 == 0 else g1 for r in range(R)])
+    t.set_rhs(g)
+    refs = []
+    for gr in (g0, g1):
+        o = oracle_problem(p, rhs=False)
+        o.set_rhs(gr)
+        refs.append(o)
+    for k in range(2):
+        t.vcycle(1)
+        got = t.solution()
+        for i, o in enumerate(refs):
+            o.vcycle(1)
+            ref = o.solution()
+            for r in range(i, R, 2):
+                err = np.abs(got[r] - ref).max() / np.abs(ref).max()
+                assert err <= 1e-12, "slot %d cycle %d: %.3e" % (r, k + 1, err)

@@ -184,3 +184,22 @@ def test_fused_sweeps_equal_separate_half_sweeps(name):
         out.append(t.solution())
     scale = np.abs(out[1]).max()
     assert np.abs(out[0] - out[1]).max() <= 1e-6 * scale
+
+
+@pytest.mark.parametrize("name", ["c1", "needle4", "c2_64"])
+def test_cta_sizes_give_identical_results(name):
+    """The block kernels' CTA size (64, 128 or 256 threads) changes only
+    which thread handles which cell: FP64 iterates and mixed solves are bit
+    for bit the same."""
+    p = parity_cases()[name]
+    out = []
+    for nt in (64, 128, 256):
+        t = gpu_problem(p)
+        t.set_option("cta_threads", nt)
+        t.vcycle(3)
+        a = t.solution().copy()
+        t.set_rhs(np.asarray(p["rhs"](t.leaf_centers()), dtype=np.float64))
+        st = t.solve(1, 1e-8, 60)
+        out.append((a, t.solution().copy(), st["cycles"]))
+    for a, b, c in out[1:]:
+        assert np.array_equal(a, out[0][0]) and np.array_equal(b, out[0][1]) and c == out[0][2]

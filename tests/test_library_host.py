@@ -91,3 +91,16 @@ def test_invalid_arguments_are_rejected(G):
     t = G.Tree(2, 8, max_level=2)
     with pytest.raises(G.GmgError):
         t.workspace_bytes()             # before store_stencils
+
+
+def test_needle_tree_size():
+    """The batched needle workload's tree: 7 levels of 8^3 blocks refined
+    toward the needle axis hold 30,195,712 leaf cells after 2:1 balance
+    (about 3e7, 512^3 effective near the needle)."""
+    import gmg_inputs as I
+    import paper_2205_09411_gb300 as G
+    p = I.problem("c3", n_rhs=1)
+    t = G.Tree(3, 8, (1, 1, 1), (0, 0, 0), 1 / 8, 7, refine=p["refine"], max_coarse_cells=64)
+    assert t.n_leaf_cells == 30195712
+    assert (t.lmin, t.lmax) == (0, 7)
+    assert t.level_info(7)[2] == 1 / 512
