@@ -24,6 +24,12 @@ analytic test problems, not datasets):
   cells of levels 0..3, so the unresolved-boundary search of Sec. 3.6.3 is
   on with w_min = 0.008 (the paper's 3D value); without it the V-cycle
   diverges on this geometry.
+* ``forest_problems``  batched uneven trees: independent 3D problems on the
+  unit cube with n^3 cells, n drawn from {32, 64, 128, 256}, 8^3-cell blocks;
+  each a seeded ellipsoid level set (semi-axes U[0.1, 0.3], random
+  rotation, centre U[0.35, 0.65]^3) with phi_b ~ U[0,1] on it and
+  Dirichlet walls with values U[0,1] per wall; right-hand side white noise
+  N(0,1) averaged over 3^3 cells (zero outside the domain).
 * ``sphere2d`` / ``sphere3d``  the convergence test of Sec. 4.1: a domain of
   unit size centred at the origin, f = |x| - R with R = 1/4, walls given by
   the analytic solutions log(|x|/R) (2D) and 1 - R/|x| (3D), phi_b = 0.
@@ -133,6 +139,54 @@ def charge_density_torch(xc, charges):
         d2 = ((xc - ck) ** 2).sum(dim=1)
         g += float(a[k]) * torch.exp(-d2 / (2.0 * float(w[k]) ** 2))
     return g
+
+
+def random_rotation(rng) -> np.ndarray:
+    """A rotation matrix (det +1) from the QR factors of a Gaussian matrix."""
+    q, r = np.linalg.qr(rng.standard_normal((3, 3)))
+    q = q * np.sign(np.diag(r))
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    return q
+
+
+def forest_problems(n_trees: int, index: int = 3, sizes=(32, 64, 128, 256), N: int = 8) -> list:
+    """Seeded problems of the batched uneven-tree workload (one dict per
+    tree, keys as problem()); 'n' is the tree's cells per side and
+    'noise_seed' the seed of its right-hand side (box_noise_rhs)."""
+    rng = rng_for(index)
+    out = []
+    for i in range(n_trees):
+        n = int(rng.choice(sizes))
+        semi = rng.uniform(0.1, 0.3, size=3)
+        q = random_rotation(rng)
+        c = rng.uniform(0.35, 0.65, size=3)
+        phib = float(rng.uniform(0.0, 1.0))
+        walls = tuple(float(v) for v in rng.uniform(0.0, 1.0, size=6))
+        ml = int(round(math.log2(n / N))) + 1
+        seed = 10_000 + 97 * index + i
+        out.append(dict(dim=3, N=N, cb=(1, 1, 1), lo=(0.0, 0.0, 0.0), h1=1.0 / N, max_level=ml, refine=None,
+                        lsf=("ellipsoid", tuple(c) + tuple(q.reshape(-1)) + tuple(semi)),
+                        walls=(WALL_DIRICHLET,) * 6, wall_values=walls, wall_fn=None, phib=phib,
+                        rhs=lambda xc, _n=n, _s=seed: box_noise_rhs(xc, _n, _s), n=n, noise_seed=seed,
+                        n_vcycles=12, tol=1e-8, index=100 + i, max_coarse_cells=64))
+    return out
+
+
+def box_noise_rhs(xc, n: int, seed: int) -> np.ndarray:
+    """White noise N(0,1) on the n^3 grid of the unit cube, averaged over the
+    3^3 cells around each cell (cells outside the domain count as zero),
+    sampled at the cell centres xc (any order)."""
+    w = np.random.Generator(np.random.PCG64(seed)).standard_normal((n, n, n))  # [z, y, x]
+    p = np.pad(w, 1)
+    acc = np.zeros_like(w)
+    for dz in range(3):
+        for dy in range(3):
+            for dx in range(3):
+                acc += p[dz:dz + n, dy:dy + n, dx:dx + n]
+    g = acc / 27.0
+    ix = np.floor(np.asarray(xc) * n).astype(np.int64)
+    return g[ix[:, 2], ix[:, 1], ix[:, 0]]
 
 
 def problem(name: str, **over) -> dict:

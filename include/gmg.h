@@ -30,6 +30,10 @@
  *    (block, slot) pairs of a level in one launch.  Arrays that hold leaf
  *    values of several slots are slot-major: slot r's leaf cells start at
  *    r * n_leaf_cells.
+ *  - forests: gmg_forest_create merges many set-up trees (independent
+ *    problems) into one gmg_tree; a "unit" is one (slot, tree) pair, unit
+ *    r * n_trees + i.  Per-unit arrays (residuals, statistics, activity
+ *    masks) hold nrhs * n_trees entries; a single tree has one tree.
  *  - a gmg_tree owns all the device memory it uses: either one workspace
  *    the caller binds (gmg_tree_bind with a device pointer) or one the
  *    library allocates itself (gmg_tree_bind with NULL).  It stays valid
@@ -152,6 +156,24 @@ int gmg_set_walls(gmg_tree *tree, const int *types, const double *values, gmg_fn
  * (results are uploaded by gmg_tree_bind).  Errors: STATE if already bound. */
 int gmg_store_stencils(gmg_tree *tree, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, double phib_const);
 
+/* Forest of independent problems (the batched form of the method: many
+ * trees, each with its own level set, boundary values, refinement and size,
+ * in every launch).  `trees` are n_trees set-up trees (gmg_tree_create +
+ * gmg_set_walls + gmg_store_stencils, not bound), each with exactly one root
+ * block, and all with the same dimension, block size, root cell size,
+ * coarsest level, sweep counts and wall types (wall values, level sets and
+ * depths may differ).  The forest copies what it needs: the trees may be
+ * destroyed afterwards.  Level l of the forest holds the level-l blocks of
+ * every tree; the coarsest level holds one block per tree with that tree's
+ * direct-solve inverse.  Leaf cells are tree-major: tree i's leaves, in its
+ * own leaf order, start at the offset gmg_forest_tree_info returns.  Norms,
+ * convergence tests and freezing are per (slot, tree) unit, so each tree's
+ * result is that of its own solve.  Errors: INVALID_ARG (shapes differ, a
+ * tree has several roots), STATE (a tree not set up or already bound). */
+int gmg_forest_create(gmg_tree *const *trees, int n_trees, gmg_tree **out);
+int gmg_num_trees(const gmg_tree *tree);
+int gmg_forest_tree_info(const gmg_tree *forest, int tree, long long *leaf_offset, long long *n_leaf_cells);
+
 /* Number of right-hand-side slots (1 .. 65536) the workspace holds; call
  * before gmg_tree_bind (default 1).  Errors: STATE after bind. */
 int gmg_set_num_rhs(gmg_tree *tree, int nrhs);
@@ -193,8 +215,8 @@ int gmg_get_solution_slots(gmg_tree *tree, int slot0, int nslots, double *phi, i
  * correction, N_up sweeps). */
 int gmg_vcycle(gmg_tree *tree, int n_cycles, void *stream);
 /* Composite residual ||b - A phi||_2 over leaf cells, relative to ||b||_2,
- * and max |b - A phi|, per slot (host arrays of nrhs doubles, or NULL).
- * Synchronises the stream. */
+ * and max |b - A phi|, per unit (host arrays of nrhs * n_trees doubles, or
+ * NULL).  Synchronises the stream. */
 int gmg_residual(gmg_tree *tree, double *rel_l2, double *linf, void *stream);
 /* The same composite residual as gmg_residual, for callers that cannot
  * allocate device memory: code that runs inside another runtime's memory
@@ -211,23 +233,26 @@ int gmg_residual(gmg_tree *tree, double *rel_l2, double *linf, void *stream);
  * (cudaGetSymbolAddress), so make it before any stream capture.  All calls
  * share the array: calls that overlap on the GPU (several streams or host
  * threads at once) race and must be serialised by the caller.
- * With several right-hand-side slots it evaluates slot 0.
+ * With several right-hand-side slots it evaluates slot 0 (over all trees of
+ * a forest together).
  * Errors: INVALID_ARG, STATE (tree not bound), CUDA. */
 int gmg_residual_noalloc(gmg_tree *tree, double *out, void *stream);
-/* Solves every slot to ||b - A phi||_2 <= rel_tol ||b||_2 from its current
- * phi with GMG_FP64 V-cycles or GMG_MIXED defect correction.  A slot that
- * reaches the tolerance is frozen: later cycles skip its blocks, so its
- * result does not depend on the other slots.  stats: NULL or an array of
- * nrhs entries.  Synchronises once per cycle (the convergence test).
+/* Solves every unit (slot, tree) to ||b - A phi||_2 <= rel_tol ||b||_2 from
+ * its current phi with GMG_FP64 V-cycles or GMG_MIXED defect correction.  A
+ * unit that reaches the tolerance is frozen: later cycles skip its blocks,
+ * so its result does not depend on the other units.  stats: NULL or an
+ * array of nrhs * n_trees entries.  Synchronises once per cycle (the
+ * convergence test).
  * Errors: NOT_CONVERGED after max_cycles, NONFINITE on NaN or growth. */
 int gmg_solve(gmg_tree *tree, int precision, double rel_tol, int max_cycles, gmg_stats *stats, void *stream);
-/* One step of the solve loop on the slots with active[r] != 0 (host array of
- * nrhs ints; the other slots are left untouched): residual_only != 0 runs
+/* One step of the solve loop on the units with active[u] != 0 (host array
+ * of nrhs * n_trees ints; the other units are left untouched): residual_only != 0 runs
  * the composite residual only (the first step of a new right-hand side; in
  * GMG_MIXED it also prepares the FP32 defect), else one V-cycle (FP64) or
  * one defect-correction step (GMG_MIXED) followed by the residual.  Writes
- * every slot's relative L2 and max residual into rel_l2 / linf (host arrays
- * of nrhs doubles, or NULL; a slot not stepped keeps its last values).
+ * every unit's relative L2 and max residual into rel_l2 / linf (host arrays
+ * of nrhs * n_trees doubles, or NULL; a unit not stepped keeps its last
+ * values).
  * This is the unit a serving loop interleaves with gmg_set_rhs_slots.
  * Synchronises the stream. */
 int gmg_iterate(gmg_tree *tree, int precision, const int *active, int residual_only, double *rel_l2, double *linf,
@@ -270,7 +295,19 @@ int gmg_profile_read(gmg_tree *tree, int cap, int *kind, int *prec, int *level, 
 #define GMG_OPT_CTA_THREADS 5  /* [0] threads per CTA of the smoothing, residual, restriction and
                                   FAS kernels: 64, 128 or 256; 0 = 64 for blocks of at most 512
                                   cells, 256 otherwise */
+#define GMG_OPT_COOP_MAX_BLOCKS 6 /* [160] levels with at most this many blocks (from the coarsest
+                                     up to the last such level) join the cooperative launch */
 int gmg_set_option(gmg_tree *tree, int option, long long value);
+
+/* Sweep schedule: N_down / N_up red-black sweeps on one level (default: the
+ * parameters' n_down / n_up on every level; the coarsest level is solved
+ * exactly and ignores them).  A schedule that differs from level to level
+ * is a tuning choice outside the paper's uniform N_down / N_up: it changes
+ * the V-cycle (and its convergence rate), not the discretisation or the
+ * solution it converges to.  Before or after gmg_tree_bind.
+ * Errors: INVALID_ARG for a level out of range or counts outside 0..64. */
+int gmg_set_level_sweeps(gmg_tree *tree, int level, int n_down, int n_up);
+int gmg_get_level_sweeps(const gmg_tree *tree, int level, int *n_down, int *n_up);
 
 /* Failure-detection self test: launches a cooperative kernel whose grid
  * barrier waits for one CTA more than exist, so its bounded wait must run

@@ -17,7 +17,7 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Tree", "load", "build", "GmgError", "FP64", "MIXED", "LIB_PATH"]
+__all__ = ["Tree", "Forest", "load", "build", "GmgError", "FP64", "MIXED", "LIB_PATH"]
 
 LIB_PATH = _build.LIB
 FP64, MIXED = 0, 1
@@ -90,6 +90,11 @@ def load():
         "gmg_set_rhs_slots": (C.c_int, [vp, C.c_int, C.c_int, vp, C.c_int, vp]),
         "gmg_get_solution_slots": (C.c_int, [vp, C.c_int, C.c_int, vp, C.c_int, vp]),
         "gmg_iterate": (C.c_int, [vp, C.c_int, ip, C.c_int, dp, dp, vp]),
+        "gmg_forest_create": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(vp)]),
+        "gmg_set_level_sweeps": (C.c_int, [vp, C.c_int, C.c_int, C.c_int]),
+        "gmg_get_level_sweeps": (C.c_int, [vp, C.c_int, ip, ip]),
+        "gmg_num_trees": (C.c_int, [vp]),
+        "gmg_forest_tree_info": (C.c_int, [vp, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
         "gmg_set_solution": (C.c_int, [vp, vp, C.c_int, vp]),
         "gmg_get_solution": (C.c_int, [vp, vp, C.c_int, vp]),
         "gmg_vcycle": (C.c_int, [vp, C.c_int, vp]),
@@ -174,7 +179,14 @@ class Tree:
         prm = Params(n_down, n_up, eps_tol, mask_factor, w_min)
         h = C.c_void_p()
         _check(L.gmg_tree_create(C.byref(dom), C.byref(prm), C.byref(h)))
+        self._adopt(h, dim, block_n)
+        if nrhs != 1:
+            self.set_num_rhs(nrhs)
+
+    def _adopt(self, h, dim, block_n):
+        L = load()
         self.h = h
+        self.dim = dim
         self._keep = []
         self._ws = None
         lmin, lmax, nleaf, nb = C.c_int(), C.c_int(), C.c_longlong(), C.c_longlong()
@@ -182,8 +194,12 @@ class Tree:
         self.lmin, self.lmax, self.n_leaf_cells, self.n_blocks = lmin.value, lmax.value, nleaf.value, nb.value
         self.block_n = block_n
         self.nrhs = 1
-        if nrhs != 1:
-            self.set_num_rhs(nrhs)
+        self.ntree = L.gmg_num_trees(self.h)
+
+    @property
+    def units(self):
+        """(slot, tree) pairs: the independent problems the tree solves."""
+        return self.nrhs * self.ntree
 
     def set_num_rhs(self, nrhs):
         """Right-hand-side slots of the workspace (before bind)."""
@@ -357,35 +373,56 @@ class Tree:
         _check(load().gmg_vcycle(self.h, n, _stream_ptr(stream)))
 
     def residual(self, stream=None):
-        """(relative L2, max) of the composite residual: floats for one slot, else arrays."""
-        r, m = np.zeros(self.nrhs), np.zeros(self.nrhs)
+        """(relative L2, max) of the composite residual: floats for one unit, else
+        arrays over the units (slot r, tree i) at r * ntree + i."""
+        U = self.units
+        r, m = np.zeros(U), np.zeros(U)
         dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
         _check(load().gmg_residual(self.h, dp(r), dp(m), _stream_ptr(stream)))
-        return (float(r[0]), float(m[0])) if self.nrhs == 1 else (r, m)
+        return (float(r[0]), float(m[0])) if U == 1 else (r, m)
 
     def iterate(self, precision, active, residual_only=False, stream=None):
-        """One solve-loop step on the slots with active[r] != 0; returns (rel_l2, linf) arrays."""
-        a = np.ascontiguousarray(np.asarray(active, dtype=np.int32).reshape(self.nrhs))
-        r, m = np.zeros(self.nrhs), np.zeros(self.nrhs)
+        """One solve-loop step on the units with active[u] != 0; returns (rel_l2, linf) arrays."""
+        U = self.units
+        a = np.ascontiguousarray(np.asarray(active, dtype=np.int32).reshape(U))
+        r, m = np.zeros(U), np.zeros(U)
         dp = lambda x: x.ctypes.data_as(C.POINTER(C.c_double))
         _check(load().gmg_iterate(self.h, precision, a.ctypes.data_as(C.POINTER(C.c_int)), 1 if residual_only else 0,
                                   dp(r), dp(m), _stream_ptr(stream)))
         return r, m
 
     def solve(self, precision=FP64, rel_tol=1e-8, max_cycles=50, stream=None, check=True):
-        """Solve every slot to rel_tol.  Returns rc, cycles, rel_l2, linf, bnorm (the
-        worst slot's for several slots) and, for several slots, 'slots': per-slot dicts."""
-        st = (Stats * self.nrhs)()
+        """Solve every unit to rel_tol.  Returns rc, cycles, rel_l2, linf, bnorm (the
+        worst unit's for several units) and, for several units, 'slots' (also
+        'units'): per-unit dicts in unit order r * ntree + i."""
+        st = (Stats * self.units)()
         rc = load().gmg_solve(self.h, precision, rel_tol, max_cycles, st, _stream_ptr(stream))
         if check:
             _check(rc)
-        slots = [dict(cycles=x.cycles, rel_l2=x.rel_l2, linf=x.linf, bnorm=x.bnorm) for x in st]
-        if self.nrhs == 1:
-            return dict(rc=rc, **slots[0])
-        return dict(rc=rc, cycles=max(x["cycles"] for x in slots), rel_l2=max(x["rel_l2"] for x in slots),
-                    linf=max(x["linf"] for x in slots), bnorm=min(x["bnorm"] for x in slots), slots=slots)
+        units = [dict(cycles=x.cycles, rel_l2=x.rel_l2, linf=x.linf, bnorm=x.bnorm) for x in st]
+        if self.units == 1:
+            return dict(rc=rc, **units[0])
+        return dict(rc=rc, cycles=max(x["cycles"] for x in units), rel_l2=max(x["rel_l2"] for x in units),
+                    linf=max(x["linf"] for x in units), bnorm=min(x["bnorm"] for x in units), slots=units,
+                    units=units)
 
-    OPTIONS = {"graphs": 1, "coarse_coop": 2, "spin_limit": 3, "fused_sweeps": 4, "cta_threads": 5}
+    def tree_leaves(self, i):
+        """(offset, count) of tree i's leaf cells in the leaf arrays."""
+        off, n = C.c_longlong(), C.c_longlong()
+        _check(load().gmg_forest_tree_info(self.h, int(i), C.byref(off), C.byref(n)))
+        return off.value, n.value
+
+    OPTIONS = {"graphs": 1, "coarse_coop": 2, "spin_limit": 3, "fused_sweeps": 4, "cta_threads": 5,
+               "coop_max_blocks": 6}
+
+    def set_level_sweeps(self, level, n_down, n_up):
+        """N_down / N_up red-black sweeps on one level (a tuning schedule)."""
+        _check(load().gmg_set_level_sweeps(self.h, int(level), int(n_down), int(n_up)))
+
+    def level_sweeps(self, level):
+        a, b = C.c_int(), C.c_int()
+        _check(load().gmg_get_level_sweeps(self.h, int(level), C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def set_option(self, name, value):
         _check(load().gmg_set_option(self.h, self.OPTIONS[name], int(value)))
@@ -415,3 +452,20 @@ class Tree:
             _check(cnt)
         return [(self.KERNEL_KINDS[k[i]], "fp64" if p[i] == 0 else "fp32", int(lv[i]), int(n[i]), float(ms[i]))
                 for i in range(cnt)]
+
+
+class Forest(Tree):
+    """Independent problems in one block structure (gmg_forest_create): the
+    trees are set up (walls, stencils) but not bound; the forest copies what
+    it needs.  It then behaves as a Tree whose leaf arrays are tree-major
+    (``tree_leaves(i)`` gives tree i's range) and whose residuals and
+    statistics are per unit (slot r, tree i) = r * ntree + i."""
+
+    def __init__(self, trees, nrhs=1):
+        L = load()
+        arr = (C.c_void_p * len(trees))(*[t.h for t in trees])
+        h = C.c_void_p()
+        _check(L.gmg_forest_create(arr, len(trees), C.byref(h)))
+        self._adopt(h, trees[0].dim, trees[0].block_n)
+        if nrhs != 1:
+            self.set_num_rhs(nrhs)

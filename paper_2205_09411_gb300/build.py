@@ -20,7 +20,7 @@ LIB = os.path.join(OUT, "libgmg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
           "-I", os.path.join(ROOT, "include"), "-I", CSRC]
-SOURCES = ["gmg_api.cu", "tree_setup.cpp", "noalloc.cu"]
+SOURCES = ["gmg_api.cu", "tree_setup.cpp", "noalloc.cu", "forest.cpp"]
 
 
 def _nvcc():

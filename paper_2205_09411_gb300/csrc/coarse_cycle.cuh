@@ -66,7 +66,7 @@ struct LevelSet {
 };
 
 struct CycleArgs {
-  int l_lo, l_hi, n_down, n_up;
+  int l_lo, l_hi;
   int ncr, nroot;  // coarsest-level unknowns per root, independent roots (inverse per root)
   const double *cinv;
   GridBar *bar;
@@ -118,8 +118,8 @@ __device__ __forceinline__ void coarse_rows(const GmgView<T> &V, const LvArgs &L
   const int M = A.ncr * A.nroot;
   for (long long item = w0; item < (long long)M * V.nrhs; item += nw) {
     const int r = (int)(item / M), row = (int)(item % M);
-    if (!V.active[r]) continue;
     const int k = row / A.ncr, i = row - k * A.ncr;
+    if (!V.active[V.ntree > 1 ? r * V.ntree + k : r]) continue;  // root k = tree k of a forest
     const double *a = A.cinv + ((size_t)k * A.ncr + i) * A.ncr;
     const T *b = V.b + r * V.rs_f + Lc.off + (size_t)k * A.ncr;
     double s = 0.0;
@@ -346,7 +346,7 @@ __device__ void tail_cycle(const GmgView<T> &V, const LevelSet &LS, const CycleA
   }
   for (int l = top; l > A.l_lo; l--) {
     const TailLevel<T, D> &F = Q[top - l], &Cq = Q[top - l + 1];
-    for (int k = 0; k < A.n_down; k++) {
+    for (int k = 0; k < F.L.nd; k++) {
       tail_smooth<T, D>(V, F, 0);
       tail_smooth<T, D>(V, F, 1);
     }
@@ -375,7 +375,7 @@ __device__ void tail_cycle(const GmgView<T> &V, const LevelSet &LS, const CycleA
   for (int l = A.l_lo + 1; l <= top; l++) {
     const TailLevel<T, D> &F = Q[top - l], &Cq = Q[top - l + 1];
     tail_prolong<T, D>(V, F, Cq);
-    for (int k = 0; k < A.n_up; k++) {
+    for (int k = 0; k < F.L.nu; k++) {
       tail_smooth<T, D>(V, F, 0);
       tail_smooth<T, D>(V, F, 1);
     }
@@ -405,12 +405,12 @@ __global__ void __launch_bounds__(kCoopThreads) k_cycle_coop(GmgView<T> V, const
   // frozen slots are skipped (W: the slot's view, bid: the block)
 #define GMG_ITEMS(Lv)                                                                          \
   for (int item = blockIdx.x, bid = 0; item < (Lv).count * V.nrhs; item += G)                  \
-    if (const int r_ = item % V.nrhs; (bid = (Lv).first + item / V.nrhs, V.active[r_]))        \
+    if (const int r_ = item % V.nrhs; (bid = (Lv).first + item / V.nrhs, V.active[unit_of(V, r_, bid)])) \
       if (const GmgView<T> W = slot_view(V, r_); true)
   // levels l_hi .. l_one + 1: every CTA, grid barrier between phases
   for (int l = A.l_hi; l > A.l_lo && l > A.l_one; l--) {
     const LvArgs L = GMG_LV(l), Lp = GMG_LV(l - 1);
-    for (int k = 0; k < A.n_down; k++)
+    for (int k = 0; k < L.nd; k++)
       for (int c = 0; c < 2; c++) {
         GMG_ITEMS(L) {
           smooth_any<T, D, NT>(W, L, Lp, bid, c, smem_raw);
@@ -436,7 +436,8 @@ __global__ void __launch_bounds__(kCoopThreads) k_cycle_coop(GmgView<T> V, const
     // block-level barriers only
     for (int item = blockIdx.x; item < A.nroot * V.nrhs; item += G) {
       const int r = item % V.nrhs, root = item / V.nrhs;
-      if (V.active[r]) tail_cycle<T, D>(slot_view(V, r), LS, A, A.l_one < A.l_hi ? A.l_one : A.l_hi, root, smem_raw);
+      if (V.active[V.ntree > 1 ? r * V.ntree + root : r])
+        tail_cycle<T, D>(slot_view(V, r), LS, A, A.l_one < A.l_hi ? A.l_one : A.l_hi, root, smem_raw);
       __syncthreads();
     }
   } else {
@@ -451,14 +452,14 @@ __global__ void __launch_bounds__(kCoopThreads) k_cycle_coop(GmgView<T> V, const
       __syncthreads();
     }
     if (!grid_sync(A.bar, G, A.spin_limit)) return;
-    for (int k = 0; k < A.n_up; k++)
+    for (int k = 0; k < L.nu; k++)
       for (int c = 0; c < 2; c++) {
         GMG_ITEMS(L) {
           smooth_any<T, D, NT>(W, L, Lp, bid, c, smem_raw);
           __syncthreads();
         }
         // the last sweep of the range needs no barrier: the kernel ends
-        if (!(l == A.l_hi && k == A.n_up - 1 && c == 1) && !grid_sync(A.bar, G, A.spin_limit)) return;
+        if (!(l == A.l_hi && k == L.nu - 1 && c == 1) && !grid_sync(A.bar, G, A.spin_limit)) return;
       }
   }
 #undef GMG_ITEMS

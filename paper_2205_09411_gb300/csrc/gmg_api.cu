@@ -29,16 +29,21 @@ void set_error(const std::string &msg) { g_last_error = msg; }
     }                                                                                        \
   } while (0)
 
-__global__ void __launch_bounds__(1024) k_reduce_partials(const double *partials, int nb, double *out,
+__global__ void __launch_bounds__(1024) k_reduce_partials(const double *partials, int nb, const int *tree_blocks,
+                                                          const int *tree_boff, int ntree, double *out,
                                                           const GridBar *bar) {
   __shared__ double s[3][1024];
-  partials += (size_t)blockIdx.x * nb * 3;  // slot blockIdx.x
+  // unit blockIdx.x = (slot r, tree i): the blocks of tree i in slot r
+  const int r = blockIdx.x / ntree, tr = blockIdx.x % ntree;
+  partials += (size_t)r * nb * 3;
   out += (size_t)blockIdx.x * 4;
+  const int b0 = tree_boff[tr], b1 = tree_boff[tr + 1];
   double a = 0.0, b = 0.0, c = 0.0;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-    a += partials[(size_t)i * 3];
-    b = fmax(b, partials[(size_t)i * 3 + 1]);
-    c += partials[(size_t)i * 3 + 2];
+  for (int k = b0 + threadIdx.x; k < b1; k += blockDim.x) {
+    const size_t i = (size_t)tree_blocks[k];
+    a += partials[i * 3];
+    b = fmax(b, partials[i * 3 + 1]);
+    c += partials[i * 3 + 2];
   }
   s[0][threadIdx.x] = a;
   s[1][threadIdx.x] = b;
@@ -94,16 +99,17 @@ __global__ void k_leaf_copy(const int *__restrict__ leaf_ids, const long long *_
   }
 }
 
-// phi64 += e32 on leaf cells of the active slots (mixed path: solution
+// phi64 += e32 on leaf cells of the active units (mixed path: solution
 // accumulation in FP64)
 __global__ void k_leaf_accumulate(const int *__restrict__ leaf_ids, const long long *__restrict__ cbase,
                                   double *__restrict__ phi, const float *__restrict__ e, long long nleaf, int ncell,
-                                  long long rs, int nr, const int *__restrict__ active) {
+                                  long long rs, int nr, const int *__restrict__ active, const int *__restrict__ tree_of,
+                                  int ntree) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nleaf * nr;
        k += (long long)gridDim.x * blockDim.x) {
     const long long r = k / nleaf, kk = k % nleaf;
-    if (!active[r]) continue;
     const int id = leaf_ids[kk / ncell];
+    if (!active[ntree > 1 ? r * ntree + tree_of[id] : r]) continue;
     const long long f = r * rs + cbase[id] + (kk % ncell);
     phi[f] += (double)e[f];
   }
@@ -173,6 +179,8 @@ LvArgs lv(const gmg_tree *T, int l) {
   a.off = L.off;
   a.h = L.h;
   a.poff = L.off;
+  a.nd = T->n_down_at(l);
+  a.nu = T->n_up_at(l);
   return a;
 }
 
@@ -200,6 +208,8 @@ GmgView<double> view<double>(gmg_tree *t) {
   v.nrhs = t->nrhs;
   v.rs_phi = t->total_cells;
   v.rs_f = t->total_cells;
+  v.ntree = t->ntree;
+  v.tree_of = t->d_tree_of;
   v.active = t->d_active;
   return v;
 }
@@ -225,6 +235,8 @@ GmgView<float> view<float>(gmg_tree *t) {
   v.nrhs = t->nrhs;
   v.rs_phi = t->total_cells;
   v.rs_f = t->total_cells;
+  v.ntree = t->ntree;
+  v.tree_of = t->d_tree_of;
   v.active = t->d_active;
   return v;
 }
@@ -327,7 +339,7 @@ int coop_cycle(gmg_tree *t, cudaStream_t s, int ls) {
       tail_bytes += add;
       l_one = l;
     }
-  CycleArgs A{t->lmin, ls, t->prm.n_down, t->prm.n_up, t->ncr, t->nroot, t->d_cinv, t->d_bar, t->spin_limit, l_one};
+  CycleArgs A{t->lmin, ls, t->ncr, t->nroot, t->d_cinv, t->d_bar, t->spin_limit, l_one};
   size_t sm = 0;
   int maxb = l_one >= t->lmin ? t->nroot : 1;
   for (int l = t->lmin; l <= ls; l++) {
@@ -384,7 +396,8 @@ bool fused_level(const gmg_tree *t, int l) {
   if (!std::is_same<T, float>::value || !t->use_fused) return false;
   const int n = t->lev(l).n;
   const bool n_ok = t->D == 3 ? (n == 8 || n == 16) : (n == 8 || n == 16 || n == 32);
-  const bool k_ok = (t->prm.n_down == 1 || t->prm.n_down == 2) && (t->prm.n_up == 1 || t->prm.n_up == 2);
+  const int nd = t->n_down_at(l), nu = t->n_up_at(l);
+  const bool k_ok = (nd == 1 || nd == 2) && (nu == 1 || nu == 2);
   return n_ok && k_ok && t->level_complete[l - t->lmin];
 }
 
@@ -425,13 +438,13 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s) {
     const int nt_l = cta_threads(t, l), nt_p = cta_threads(t, l - 1);
     const bool fused = fused_level<T>(t, l);
     if (fused) {  // N_down steps in one pass into the second buffer
-      launch_fused<T, D>(t, s, l, t->prm.n_down, L.off, L.off + other);
+      launch_fused<T, D>(t, s, l, L.nd, L.off, L.off + other);
       L.poff = L.off + other;
     }
     with_nt<D>(L.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
       if (!fused)
-        for (int k = 0; k < t->prm.n_down; k++)
+        for (int k = 0; k < L.nd; k++)
           for (int c = 0; c < 2; c++)
             launch(t, s, 0, P, l, [&] { k_smooth<T, D, NT><<<L.count * R, nt_l, sm, s>>>(V, L, Lp, c); });
       launch(t, s, 1, P, l, [&] { k_resid_restrict<T, D, NT><<<L.count * R, nt_l, sm, s>>>(V, L, Lp); });
@@ -466,11 +479,11 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s) {
       constexpr int NT = decltype(nt)::value;
       launch(t, s, 4, P, l, [&] { k_prolong<T, D, NT><<<L.count * R, kThreads, psm, s>>>(V, L, Lp); });
       if (!fused)
-        for (int k = 0; k < t->prm.n_up; k++)
+        for (int k = 0; k < L.nu; k++)
           for (int c = 0; c < 2; c++)
             launch(t, s, 0, P, l, [&] { k_smooth<T, D, NT><<<L.count * R, nt_l, sm, s>>>(V, L, Lp, c); });
     });
-    if (fused) launch_fused<T, D>(t, s, l, t->prm.n_up, L.off + other, L.off);  // back to the first buffer
+    if (fused) launch_fused<T, D>(t, s, l, L.nu, L.off + other, L.off);  // back to the first buffer
   }
   if (t->adaptive) {
     for (int l = t->lmax; l >= 2 && l > t->lmin; l--) {
@@ -510,10 +523,11 @@ int residual_impl(gmg_tree *t, cudaStream_t s, float *rout) {
     });
   }
   launch(t, s, 7, 0, t->lmax, [&] {
-    k_reduce_partials<<<t->nrhs, 1024, 0, s>>>(t->d_partials, (int)t->blocks.size(), t->d_red, t->d_bar);
+    k_reduce_partials<<<t->units(), 1024, 0, s>>>(t->d_partials, (int)t->blocks.size(), t->d_tree_blocks,
+                                                  t->d_tree_boff, t->ntree, t->d_red, t->d_bar);
   });
   CUDA_TRY(cudaGetLastError());
-  CUDA_TRY(cudaMemcpyAsync(t->h_red, t->d_red, 4 * sizeof(double) * t->nrhs, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(t->h_red, t->d_red, 4 * sizeof(double) * t->units(), cudaMemcpyDeviceToHost, s));
   return GMG_OK;
 }
 
@@ -551,7 +565,8 @@ int mixed_step(gmg_tree *t, cudaStream_t s) {
   const long long n = t->n_leaf_cells;
   launch(t, s, 8, 0, t->lmax, [&] {
     k_leaf_accumulate<<<grid_for(n * t->nrhs), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, t->f_phi, n,
-                                                            t->leaf_ncell(), t->total_cells, t->nrhs, t->d_active);
+                                                            t->leaf_ncell(), t->total_cells, t->nrhs, t->d_active,
+                                                            t->d_tree_of, t->ntree);
   });
   CUDA_TRY(cudaGetLastError());
   if (t->adaptive) return restrict_all_phi64_any(t, s);
@@ -591,12 +606,12 @@ int run_graph(gmg_tree *t, int slot, cudaStream_t s, F &&enqueue) {
   return GMG_OK;
 }
 
-// Waits for the stream and checks the barrier flag; the norms of slot r are
-// then h_red[4r .. 4r + 2] = (sum r^2, max |r|, sum b^2).
+// Waits for the stream and checks the barrier flag; the norms of unit u
+// (slot, tree) are then h_red[4u .. 4u + 2] = (sum r^2, max |r|, sum b^2).
 int read_red(gmg_tree *t, cudaStream_t s) {
   CUDA_TRY(cudaStreamSynchronize(s));
   bool timeout = false;
-  for (int r = 0; r < t->nrhs; r++) timeout = timeout || t->h_red[4 * r + 3] != 0.0;
+  for (int u = 0; u < t->units(); u++) timeout = timeout || t->h_red[4 * u + 3] != 0.0;
   if (timeout) {  // a grid barrier timed out: report once, then clear
     CUDA_TRY(cudaMemset(t->d_bar, 0, sizeof(GridBar)));
     set_error("a grid barrier of the coarse-level cycle timed out");
@@ -609,7 +624,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t nbr, pnb, parent, pofs, flags, leaf, cbase, st_base, bt_base, phi, b, old, fphi, fb, fold, st, fst, bterm, cinv,
-      partials, red, active, bar, spec, lvtab, total;
+      partials, red, active, tree_of, tree_blocks, tree_boff, bar, spec, lvtab, total;
 };
 
 Layout layout(const gmg_tree *t) {
@@ -641,8 +656,12 @@ Layout layout(const gmg_tree *t) {
   L.bterm = take(t->bterm_h.size() * sizeof(double));
   L.cinv = take(t->cinv_h.size() * sizeof(double));
   L.partials = take(R * nb * 3 * sizeof(double));
-  L.red = take(R * 4 * sizeof(double));
-  L.active = take(R * sizeof(int));
+  const size_t U = (size_t)t->units();
+  L.red = take(U * 4 * sizeof(double));
+  L.active = take(U * sizeof(int));
+  L.tree_of = take(nb * sizeof(int));
+  L.tree_blocks = take(nb * sizeof(int));
+  L.tree_boff = take(((size_t)t->ntree + 1) * sizeof(int));
   L.bar = take(sizeof(GridBar));
   L.spec = take(t->spec_h.size());
   L.lvtab = take(kMaxLevels * sizeof(LvArgs));
@@ -651,6 +670,29 @@ Layout layout(const gmg_tree *t) {
 }
 
 cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// levels up to coop_split run inside one cooperative kernel (few blocks each)
+void set_coop_split(gmg_tree *t) {
+  t->coop_split = t->lmin;
+  for (int l = t->lmin; l <= t->lmax; l++)
+    if (t->lev(l).count <= t->coop_max_blocks) t->coop_split = l;
+}
+
+void drop_graphs(gmg_tree *t) {
+  for (auto &g : t->graphs)
+    if (g.exec) {
+      cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+    }
+}
+
+// per-level descriptors of the cooperative kernel (sweep counts included)
+int upload_lvtab(gmg_tree *t) {
+  std::vector<LvArgs> tab(t->levels.size());
+  for (int l = t->lmin; l <= t->lmax; l++) tab[l - t->lmin] = lv(t, l);
+  CUDA_TRY(cudaMemcpy(t->d_lvtab, tab.data(), tab.size() * sizeof(LvArgs), cudaMemcpyHostToDevice));
+  return GMG_OK;
+}
 
 }  // namespace
 
@@ -733,9 +775,10 @@ int gmg_leaf_centers(const gmg_tree *t, double *xyz) {
   for (int id : t->leaf_ids_h) {
     const HostBlock &B = t->blocks[id];
     const LevelInfo &L = t->lev(B.level);
+    const double *lo = t->ntree > 1 ? &t->tree_lo_h[3 * (size_t)t->tree_of_h[id]] : t->lo;
     for (int c = 0; c < L.ncell; c++) {
       int p[3] = {c % L.n, (c / L.n) % L.n, t->D == 3 ? c / (L.n * L.n) : 0};
-      for (int d = 0; d < t->D; d++) xyz[k * t->D + d] = t->lo[d] + ((double)(B.ix[d] * L.n + p[d]) + 0.5) * L.h;
+      for (int d = 0; d < t->D; d++) xyz[k * t->D + d] = lo[d] + ((double)(B.ix[d] * L.n + p[d]) + 0.5) * L.h;
       k++;
     }
   }
@@ -843,6 +886,9 @@ int gmg_tree_bind(gmg_tree *t, void *device_ptr, size_t bytes) {
   t->d_partials = reinterpret_cast<double *>(w + L.partials);
   t->d_red = reinterpret_cast<double *>(w + L.red);
   t->d_active = reinterpret_cast<int *>(w + L.active);
+  t->d_tree_of = reinterpret_cast<int *>(w + L.tree_of);
+  t->d_tree_blocks = reinterpret_cast<int *>(w + L.tree_blocks);
+  t->d_tree_boff = reinterpret_cast<int *>(w + L.tree_boff);
   t->d_bar = reinterpret_cast<GridBar *>(w + L.bar);
   t->d_spec = reinterpret_cast<unsigned char *>(w + L.spec);
   t->d_lvtab = reinterpret_cast<LvArgs *>(w + L.lvtab);
@@ -863,6 +909,16 @@ int gmg_tree_bind(gmg_tree *t, void *device_ptr, size_t bytes) {
     CUDA_TRY(cudaMemcpy(t->d_pnb, pnb.data(), nb * kNbr * sizeof(int), cudaMemcpyHostToDevice));
   }
   CUDA_TRY(cudaMemcpy(t->d_parent, t->parent_h.data(), nb * sizeof(int), cudaMemcpyHostToDevice));
+  if (t->ntree == 1) {  // a single tree: every block in tree 0
+    t->tree_of_h.assign(nb, 0);
+    t->tree_blocks_h.resize(nb);
+    for (size_t i = 0; i < nb; i++) t->tree_blocks_h[i] = (int)i;
+    t->tree_boff_h = {0, (int)nb};
+  }
+  CUDA_TRY(cudaMemcpy(t->d_tree_of, t->tree_of_h.data(), nb * sizeof(int), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(t->d_tree_blocks, t->tree_blocks_h.data(), nb * sizeof(int), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(t->d_tree_boff, t->tree_boff_h.data(), t->tree_boff_h.size() * sizeof(int),
+                      cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(t->d_pofs, t->pofs_h.data(), nb * sizeof(int), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(t->d_flags, t->flags_h.data(), nb * sizeof(int), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(t->d_leaf, t->leaf_ids_h.data(), t->leaf_ids_h.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -875,9 +931,8 @@ int gmg_tree_bind(gmg_tree *t, void *device_ptr, size_t bytes) {
   }
   if (!t->spec_h.empty()) CUDA_TRY(cudaMemcpy(t->d_spec, t->spec_h.data(), t->spec_h.size(), cudaMemcpyHostToDevice));
   {
-    std::vector<LvArgs> tab(t->levels.size());
-    for (int l = t->lmin; l <= t->lmax; l++) tab[l - t->lmin] = lv(t, l);
-    CUDA_TRY(cudaMemcpy(t->d_lvtab, tab.data(), tab.size() * sizeof(LvArgs), cudaMemcpyHostToDevice));
+    const int rc = upload_lvtab(t);
+    if (rc) return rc;
   }
   if (!t->bterm_h.empty())
     CUDA_TRY(cudaMemcpy(t->d_bterm, t->bterm_h.data(), t->bterm_h.size() * sizeof(double), cudaMemcpyHostToDevice));
@@ -891,15 +946,12 @@ int gmg_tree_bind(gmg_tree *t, void *device_ptr, size_t bytes) {
   CUDA_TRY(cudaMemset(t->f_old, 0, cells * sizeof(float)));
   // blocks on levels without leaves never write their residual partials
   CUDA_TRY(cudaMemset(t->d_partials, 0, (size_t)t->nrhs * nb * 3 * sizeof(double)));
-  CUDA_TRY(cudaMemset(t->d_red, 0, (size_t)t->nrhs * 4 * sizeof(double)));
-  CUDA_TRY(cudaMemset(t->d_active, 1, (size_t)t->nrhs * sizeof(int)));  // nonzero: active
+  CUDA_TRY(cudaMemset(t->d_red, 0, (size_t)t->units() * 4 * sizeof(double)));
+  CUDA_TRY(cudaMemset(t->d_active, 1, (size_t)t->units() * sizeof(int)));  // nonzero: active
   CUDA_TRY(cudaMemset(t->d_bar, 0, sizeof(GridBar)));
-  // levels up to coop_split run inside one cooperative kernel (few blocks each)
-  t->coop_split = t->lmin;
-  for (int l = t->lmin; l <= t->lmax; l++)
-    if (t->lev(l).count <= kCoopMaxBlocks) t->coop_split = l;
-  if (!t->h_red) CUDA_TRY(cudaMallocHost(&t->h_red, (size_t)t->nrhs * 4 * sizeof(double)));
-  if (!t->h_active) CUDA_TRY(cudaMallocHost(&t->h_active, (size_t)t->nrhs * sizeof(int)));
+  set_coop_split(t);
+  if (!t->h_red) CUDA_TRY(cudaMallocHost(&t->h_red, (size_t)t->units() * 4 * sizeof(double)));
+  if (!t->h_active) CUDA_TRY(cudaMallocHost(&t->h_active, (size_t)t->units() * sizeof(int)));
   t->level_complete.assign(t->levels.size(), 1);
   for (size_t i = 0; i < nb; i++)
     for (int k = 0; k < kNbr; k++)
@@ -962,7 +1014,7 @@ int gmg_set_solution(gmg_tree *t, const double *phi, int where, void *stream) {
   k_leaf_copy<<<grid_for(n * t->nrhs), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, src, n, t->leaf_ncell(),
                                                     t->total_cells, 0, t->nrhs, 1);
   CUDA_TRY(cudaGetLastError());
-  CUDA_TRY(cudaMemsetAsync(t->d_active, 1, (size_t)t->nrhs * sizeof(int), s));
+  CUDA_TRY(cudaMemsetAsync(t->d_active, 1, (size_t)t->units() * sizeof(int), s));
   return restrict_all_phi64_any(t, s);
 }
 
@@ -1007,21 +1059,22 @@ int gmg_get_level(gmg_tree *t, int level, int which, double *out, void *stream) 
 }
 
 namespace {
-// slot mask: all slots active, or the host array `mask` (nonzero = active)
+// unit mask: all units active, or the host array `mask` (nonzero = active)
 int upload_mask(gmg_tree *t, const int *mask, cudaStream_t s) {
+  const int U = t->units();
   if (!mask) {
-    CUDA_TRY(cudaMemsetAsync(t->d_active, 1, (size_t)t->nrhs * sizeof(int), s));
+    CUDA_TRY(cudaMemsetAsync(t->d_active, 1, (size_t)U * sizeof(int), s));
     return GMG_OK;
   }
   // the pinned mirror may still feed an earlier copy: wait for the stream
   CUDA_TRY(cudaStreamSynchronize(s));
-  for (int r = 0; r < t->nrhs; r++) t->h_active[r] = mask[r] ? 1 : 0;
-  CUDA_TRY(cudaMemcpyAsync(t->d_active, t->h_active, (size_t)t->nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
+  for (int u = 0; u < U; u++) t->h_active[u] = mask[u] ? 1 : 0;
+  CUDA_TRY(cudaMemcpyAsync(t->d_active, t->h_active, (size_t)U * sizeof(int), cudaMemcpyHostToDevice, s));
   return GMG_OK;
 }
 
-void slot_norms(const gmg_tree *t, int r, double *rel, double *linf, double *bnorm) {
-  const double s2 = t->h_red[4 * r], mx = t->h_red[4 * r + 1], b2 = t->h_red[4 * r + 2];
+void slot_norms(const gmg_tree *t, int u, double *rel, double *linf, double *bnorm) {
+  const double s2 = t->h_red[4 * u], mx = t->h_red[4 * u + 1], b2 = t->h_red[4 * u + 2];
   if (rel) *rel = b2 > 0 ? std::sqrt(s2 / b2) : std::sqrt(s2);
   if (linf) *linf = mx;
   if (bnorm) *bnorm = std::sqrt(b2);
@@ -1053,7 +1106,7 @@ int gmg_residual(gmg_tree *t, double *rel_l2, double *linf, void *stream) {
   if (rc) return rc;
   rc = read_red(t, s);
   if (rc) return rc;
-  for (int r = 0; r < t->nrhs; r++) slot_norms(t, r, rel_l2 ? rel_l2 + r : nullptr, linf ? linf + r : nullptr, nullptr);
+  for (int u = 0; u < t->units(); u++) slot_norms(t, u, rel_l2 ? rel_l2 + u : nullptr, linf ? linf + u : nullptr, nullptr);
   return GMG_OK;
 }
 
@@ -1079,7 +1132,7 @@ int gmg_iterate(gmg_tree *t, int precision, const int *active, int residual_only
   if (rc) return rc;
   rc = read_red(t, s);
   if (rc) return rc;
-  for (int r = 0; r < t->nrhs; r++) slot_norms(t, r, rel_l2 ? rel_l2 + r : nullptr, linf ? linf + r : nullptr, nullptr);
+  for (int u = 0; u < t->units(); u++) slot_norms(t, u, rel_l2 ? rel_l2 + u : nullptr, linf ? linf + u : nullptr, nullptr);
   return GMG_OK;
 }
 
@@ -1089,7 +1142,7 @@ int gmg_solve(gmg_tree *t, int precision, double rel_tol, int max_cycles, gmg_st
   if (!t->bound) return set_error("tree not bound"), GMG_ERR_STATE;
   cudaStream_t s = as_stream(stream);
   t->launches = 0;
-  const int R = t->nrhs;
+  const int R = t->units();
   std::vector<int> act(R, 1), cyc(R, 0);
   std::vector<double> rel(R, 0.0), prev(R, INFINITY);
   int cycles = 0, rc = GMG_OK;
@@ -1151,6 +1204,11 @@ int gmg_set_option(gmg_tree *t, int option, long long value) {
     case GMG_OPT_GRAPHS: t->use_graphs = value != 0; break;
     case GMG_OPT_COARSE_COOP: t->use_coop = value != 0; break;
     case GMG_OPT_FUSED_SWEEPS: t->use_fused = value != 0; break;
+    case GMG_OPT_COOP_MAX_BLOCKS:
+      if (value < 0) return set_error("block limit must be >= 0"), GMG_ERR_INVALID_ARG;
+      t->coop_max_blocks = (int)std::min<long long>(value, 1 << 30);
+      if (t->bound) set_coop_split(t);
+      break;
     case GMG_OPT_CTA_THREADS:
       if (value != 0 && value != 64 && value != 128 && value != 256)
         return set_error("CTA threads must be 0 (by block size), 64, 128 or 256"), GMG_ERR_INVALID_ARG;
@@ -1162,11 +1220,31 @@ int gmg_set_option(gmg_tree *t, int option, long long value) {
       break;
     default: return set_error("unknown option"), GMG_ERR_INVALID_ARG;
   }
-  for (auto &g : t->graphs)
-    if (g.exec) {
-      cudaGraphExecDestroy(g.exec);
-      g.exec = nullptr;
-    }
+  drop_graphs(t);
+  return GMG_OK;
+}
+
+int gmg_set_level_sweeps(gmg_tree *t, int level, int n_down, int n_up) {
+  if (!t || level < t->lmin || level > t->lmax || n_down < 0 || n_up < 0 || n_down > 64 || n_up > 64)
+    return set_error("bad arguments"), GMG_ERR_INVALID_ARG;
+  if (t->sweeps_down.empty()) {
+    t->sweeps_down.assign(t->levels.size(), t->prm.n_down);
+    t->sweeps_up.assign(t->levels.size(), t->prm.n_up);
+  }
+  t->sweeps_down[level - t->lmin] = n_down;
+  t->sweeps_up[level - t->lmin] = n_up;
+  if (t->bound) {
+    const int rc = upload_lvtab(t);
+    if (rc) return rc;
+  }
+  drop_graphs(t);
+  return GMG_OK;
+}
+
+int gmg_get_level_sweeps(const gmg_tree *t, int level, int *n_down, int *n_up) {
+  if (!t || level < t->lmin || level > t->lmax) return set_error("level out of range"), GMG_ERR_INVALID_ARG;
+  if (n_down) *n_down = t->n_down_at(level);
+  if (n_up) *n_up = t->n_up_at(level);
   return GMG_OK;
 }
 

@@ -46,6 +46,7 @@ struct LvArgs {
   long long off;   // first cell of the level in the b / old / stencil-indexed fields
   double h;
   long long poff;  // first cell of the level in phi (off, or off + total cells in the second buffer)
+  int nd, nu;      // red/black sweeps of the level on the way down / up
 };
 
 // Everything a kernel needs to address the tree in device memory.
@@ -67,8 +68,17 @@ struct GmgView {
   // r * rs_f (b, old) elements after slot 0's; tables and stencils are shared
   int nrhs;
   long long rs_phi, rs_f;
-  const int *active;     // [nrhs] 0 = slot frozen (converged or empty): its CTAs return at once
+  // independent problems: a forest holds ntree trees; (slot r, tree i) is
+  // unit r * ntree + i
+  int ntree;
+  const int *tree_of;    // [nb] tree of each block (forests; unused when ntree == 1)
+  const int *active;     // [nrhs * ntree] 0 = unit frozen (converged or empty): its CTAs return at once
 };
+
+template <typename T>
+__host__ __device__ __forceinline__ int unit_of(const GmgView<T> &V, int r, int bid) {
+  return V.ntree > 1 ? r * V.ntree + V.tree_of[bid] : r;
+}
 
 // The view of one right-hand-side slot.
 template <typename T>
@@ -97,6 +107,14 @@ struct gmg_tree {
   int nrhs = 1;   // right-hand-side slots (fields are replicated per slot)
   int nroot = 1;  // independent root blocks (trees of a forest), each with its own coarse solve
   int ncr = 0;    // coarsest-level unknowns per root (nc = nroot * ncr)
+  // forests (gmg_forest_create): ntree trees with one root each (root k =
+  // tree k); blocks of tree i: tree_blocks_h[tree_boff_h[i] .. tree_boff_h[i+1]);
+  // leaves are tree-major, tree i's leaf cells at tree_leaf_off_h[i]
+  int ntree = 1;
+  std::vector<int> tree_of_h, tree_blocks_h, tree_boff_h;
+  std::vector<long long> tree_leaf_off_h;
+  std::vector<double> tree_lo_h;  // [ntree][3] domain corners
+  int units() const { return nrhs * ntree; }
 
   // walls
   int wall_type[6] = {0, 0, 0, 0, 0, 0};
@@ -126,11 +144,12 @@ struct gmg_tree {
   double *d_phi = nullptr, *d_b = nullptr, *d_old = nullptr;
   float *f_phi = nullptr, *f_b = nullptr, *f_old = nullptr;
   double *d_st = nullptr, *d_bterm = nullptr, *d_cinv = nullptr, *d_partials = nullptr, *d_red = nullptr;
-  int *d_active = nullptr, *h_active = nullptr;  // slot mask (device, pinned host mirror)
+  int *d_active = nullptr, *h_active = nullptr;  // unit mask (device, pinned host mirror)
+  int *d_tree_of = nullptr, *d_tree_blocks = nullptr, *d_tree_boff = nullptr;
   float *f_st = nullptr;
   unsigned char *d_spec = nullptr;
   gmg::LvArgs *d_lvtab = nullptr;  // per-level descriptors (phi in the first buffer)
-  double *h_red = nullptr;  // pinned host mirror of d_red ([nrhs][4])
+  double *h_red = nullptr;  // pinned host mirror of d_red ([units][4])
   long long launches = 0;
 
   std::vector<char> level_has_leaves;  // index l - lmin
@@ -148,6 +167,10 @@ struct gmg_tree {
   int cta_threads = 0;        // threads per CTA of the block kernels (0: by block size)
   std::vector<char> level_complete;  // every block has all 26 neighbours on its level (or walls)
   int coop_split = 0;         // highest level run inside that launch
+  int coop_max_blocks = gmg::kCoopMaxBlocks;  // levels with at most this many blocks join it
+  std::vector<int> sweeps_down, sweeps_up;  // per level (index l - lmin); empty: the parameters'
+  int n_down_at(int l) const { return sweeps_down.empty() ? prm.n_down : sweeps_down[l - lmin]; }
+  int n_up_at(int l) const { return sweeps_up.empty() ? prm.n_up : sweeps_up[l - lmin]; }
   long long spin_limit = 1LL << 24;
   gmg::GridBar *d_bar = nullptr;
   cudaStream_t cap_stream = nullptr;

@@ -335,12 +335,13 @@ __device__ __forceinline__ void cell_xyz(int c, int n, int *x, int *y, int *z) {
 
 // Work item of a per-level launch: the grid holds count x nrhs CTAs with the
 // slot index fastest, so that the slots of one block run side by side and
-// share its tables and stencil through L2.  Returns false for a frozen slot.
+// share its tables and stencil through L2.  Returns false for a frozen unit
+// (slot, or slot and tree of a forest).
 template <typename T>
 __device__ __forceinline__ bool slot_item(const GmgView<T> &V, const LvArgs &L, int *bid, GmgView<T> *W) {
   const int r = (int)(blockIdx.x % (unsigned)V.nrhs);
   *bid = L.first + (int)(blockIdx.x / (unsigned)V.nrhs);
-  if (!V.active[r]) return false;
+  if (!V.active[unit_of(V, r, *bid)]) return false;
   *W = slot_view(V, r);
   return true;
 }
@@ -502,8 +503,8 @@ __global__ void __launch_bounds__(kThreads) k_coarse(GmgView<T> V, LvArgs Lc, co
   const int M = ncr * nroot;
   if (item >= (long long)M * V.nrhs) return;
   const int r = (int)(item / M), row = (int)(item % M);
-  if (!V.active[r]) return;
   const int k = row / ncr, i = row - k * ncr;
+  if (!V.active[V.ntree > 1 ? r * V.ntree + k : r]) return;  // root k = tree k of a forest
   const double *a = Ainv + ((size_t)k * ncr + i) * ncr;
   const T *b = V.b + r * V.rs_f + Lc.off + (size_t)k * ncr;
   double s = 0.0;
@@ -700,8 +701,9 @@ __global__ void __launch_bounds__(kThreads) k_resnorm(GmgView<T> V0, LvArgs L, L
 }
 
 // Deterministic final reduction of the per-block partials (fixed order),
-// one CTA per slot.
-__global__ void __launch_bounds__(1024) k_reduce_partials(const double *partials, int nb, double *out,
+// one CTA per unit (slot, tree).
+__global__ void __launch_bounds__(1024) k_reduce_partials(const double *partials, int nb, const int *tree_blocks,
+                                                          const int *tree_boff, int ntree, double *out,
                                                           const GridBar *bar);
 
 }  // namespace gmg

@@ -92,15 +92,17 @@ void launch_resnorm(gmg_tree *t, int l, double *partials, cudaStream_t s) {
   V.spec = t->d_spec;
   V.wneu = 0;
   for (int w = 0; w < 6; w++) V.wneu |= (t->wall_type[w] == GMG_WALL_NEUMANN ? 1 : 0) << w;
-  V.nrhs = 1;  // slot 0 only
+  V.nrhs = 1;  // slot 0 only (all trees of a forest)
   V.rs_phi = V.rs_f = t->total_cells;
+  V.ntree = t->ntree;
+  V.tree_of = t->d_tree_of;
   V.active = t->d_active;
   const gmg::LevelInfo &Li = t->lev(l);
-  gmg::LvArgs L{Li.first, Li.count, Li.n, Li.ncell, Li.off, Li.h, Li.off};
+  gmg::LvArgs L{Li.first, Li.count, Li.n, Li.ncell, Li.off, Li.h, Li.off, 0, 0};
   gmg::LvArgs Lp = L;
   if (l > t->lmin) {
     const gmg::LevelInfo &Pi = t->lev(l - 1);
-    Lp = gmg::LvArgs{Pi.first, Pi.count, Pi.n, Pi.ncell, Pi.off, Pi.h, Pi.off};
+    Lp = gmg::LvArgs{Pi.first, Pi.count, Pi.n, Pi.ncell, Pi.off, Pi.h, Pi.off, 0, 0};
   }
   const size_t sm = gmg::level_smem_bytes<double>(D, Li.n);
   cudaFuncSetAttribute(gmg::k_resnorm<double, D, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -137,8 +139,8 @@ extern "C" int gmg_residual_noalloc(gmg_tree *t, double *out, void *stream) {
   // call's contents first
   cudaError_t e = cudaMemsetAsync(scratch, 0, (size_t)nb * 3 * sizeof(double), s);
   if (e != cudaSuccess) return gmg::set_error(std::string("cudaMemsetAsync: ") + cudaGetErrorString(e)), GMG_ERR_CUDA;
-  // slot 0 active (the slot mask is set by every entry point that runs kernels)
-  e = cudaMemsetAsync(t->d_active, 1, sizeof(int), s);
+  // slot 0 active (the unit mask is set by every entry point that runs kernels)
+  e = cudaMemsetAsync(t->d_active, 1, (size_t)t->ntree * sizeof(int), s);
   if (e != cudaSuccess) return gmg::set_error(std::string("cudaMemsetAsync: ") + cudaGetErrorString(e)), GMG_ERR_CUDA;
   for (int l = t->lmin; l <= t->lmax; l++) {
     bool leaves = false;

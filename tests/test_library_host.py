@@ -104,3 +104,28 @@ def test_needle_tree_size():
     assert t.n_leaf_cells == 30195712
     assert (t.lmin, t.lmax) == (0, 7)
     assert t.level_info(7)[2] == 1 / 512
+
+
+def test_forest_structure():
+    """A forest holds every block of its trees level by level, tree by tree,
+    with tree-major leaves; its leaf centres are the trees' own."""
+    import gmg_inputs as I
+    import paper_2205_09411_gb300 as G
+    from _helpers import gpu_problem
+    ps = I.forest_problems(4, index=7, sizes=(16, 32, 64))
+    trees = [gpu_problem(p, bind=False) for p in ps]
+    F = G.Forest(trees)
+    assert F.ntree == 4 and F.units == 4
+    assert F.n_blocks == sum(t.n_blocks for t in trees)
+    assert F.n_leaf_cells == sum(t.n_leaf_cells for t in trees)
+    assert F.lmin == trees[0].lmin and F.lmax == max(t.lmax for t in trees)
+    for l in range(F.lmin, F.lmax + 1):
+        assert F.level_info(l)[0] == sum(t.level_info(l)[0] for t in trees if l <= t.lmax)
+    xc = F.leaf_centers()
+    off = 0
+    for i, t in enumerate(trees):
+        o, n = F.tree_leaves(i)
+        assert (o, n) == (off, t.n_leaf_cells)
+        assert np.array_equal(xc[o:o + n], t.leaf_centers())
+        off += n
+        assert F.num_cut_blocks(t.lmax) >= t.num_cut_blocks(t.lmax)
