@@ -20,7 +20,12 @@ copied back inside the timed region.
 Beside the headline, `batched_needle` reports the batched workload: the
 adaptive 7-level needle-electrode tree (8^3 blocks, 30,195,712 leaf cells)
 holding 32 Gaussian-charge right-hand sides, each step one batched solve of
-all 32 to 1e-8 in one tree (mixed and FP64), with its own roofline.
+all 32 to 1e-8 in one tree (mixed and FP64), with its own roofline, and
+`batched_forest` the forest of 64 uneven problems (32^3 .. 256^3 cells,
+ellipsoids) solved together, after the autotuner has picked the block tile
+and sweep schedule on a sample forest, and `serving` the continuous-batching
+request loop over seven resident sessions (p50/p99 latency and solves/s,
+mixed and FP64).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank solves its own replica (replicas only: the method
@@ -56,6 +61,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--skip-needle", action="store_true", help="leave out the batched needle workload")
+    ap.add_argument("--skip-forest", action="store_true", help="leave out the batched uneven-tree workload")
+    ap.add_argument("--skip-serving", action="store_true", help="leave out the serving-loop workload")
     return ap.parse_args()
 
 
@@ -369,6 +376,173 @@ def run_needle(G, args, world, flush, stream):
     return out
 
 
+def host_tree(G, p, N=None, nrhs=1):
+    """Set-up tree (walls, stencils), not bound."""
+    N = N or p["N"]
+    h1 = p["h1"] if N == p["N"] else 1.0 / N
+    t = G.Tree(p["dim"], N, p["cb"], p["lo"], h1, p["max_level"], refine=p["refine"],
+               max_coarse_cells=p.get("max_coarse_cells") or 0, w_min=p.get("w_min", 0.0), nrhs=nrhs)
+    t.set_walls(p["walls"], values=p["wall_values"], fn=p["wall_fn"])
+    t.store_stencils(p["lsf"], p["phib"])
+    return t
+
+
+def forest_of(G, ps, N, threads=16):
+    """Forest of the problems with N^3 blocks; the trees' host set-up runs
+    in parallel threads (the library's set-up calls release the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    qs = [dict(p, max_level=int(round(np.log2(p["n"] / N))) + 1) for p in ps]
+    with ThreadPoolExecutor(threads) as ex:
+        trees = list(ex.map(lambda p: host_tree(G, p, N), qs))
+    F = G.Forest(trees)
+    F.bind()
+    return F, trees, qs
+
+
+def forest_rhs_device(F, trees, qs, N):
+    import torch
+    g = torch.empty(F.n_leaf_cells, dtype=torch.float64, device="cuda")
+    for i, (t, q) in enumerate(zip(trees, qs)):
+        off, n = F.tree_leaves(i)
+        bix, _ = t.level_blocks(t.lmax)
+        g[off:off + n] = I.box_noise_rhs_torch(bix, N, q["n"], q["noise_seed"])
+    return g
+
+
+def run_forest(G, args, world, flush, stream):
+    """Batched uneven trees: 64 independent problems (n^3, n in {32, 64,
+    128, 256}, ellipsoids, random Dirichlet values, box-filtered noise) in
+    one forest, each step one solve of all 64 to 1e-8; block tile and sweep
+    schedule picked first by the autotuner on a sample forest of 8 problems
+    drawn from the same distribution."""
+    import torch
+    from paper_2205_09411_gb300 import autotune as AT
+    t0 = time.perf_counter()
+    sample = I.forest_problems(8, index=4)
+    log_lines = []
+
+    def build(N):
+        F, trees, qs = forest_of(G, sample, N)
+        F._rhs = forest_rhs_device(F, trees, qs, N)
+        return F
+
+    best = AT.tune_block_tile(build, lambda F: (lambda: F.set_rhs(F._rhs)), tiles=(8, 16), precision=G.MIXED,
+                              tol=args.tol, reps=1, log=log_lines.append)
+    tune_s = time.perf_counter() - t0
+    N = best.block_n
+    t0 = time.perf_counter()
+    F, trees, qs = forest_of(G, I.forest_problems(64, index=3), N)
+    AT.apply(F, best)
+    g = forest_rhs_device(F, trees, qs, N)
+    setup_s = time.perf_counter() - t0
+    n = F.n_leaf_cells
+    sizes = [q["n"] for q in qs]
+    del trees
+    res = {}
+    for name, prec in (("mixed", G.MIXED), ("fp64", G.FP64)):
+        F.set_rhs(g)
+        F.solve(prec, args.tol, 80)  # warm-up (graph capture)
+        barrier(world)
+        times, munk_cyc, worst = [], 0, 0.0
+        for _ in range(max(1, args.steps)):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            F.set_rhs(g)
+            st = F.solve(prec, args.tol, 80)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            for i, u in enumerate(st["units"]):
+                off, cnt = F.tree_leaves(i)
+                munk_cyc += cnt * u["cycles"]
+            worst = max(worst, st["rel_l2"])
+        total = allreduce_max(sum(times), world)
+        ts = sorted(times)
+        res[name] = {"p50_ms": float(np.percentile(ts, 50)), "p99_ms": float(np.percentile(ts, 99)),
+                     "solves_per_s": world * 64 * len(ts) / (total * 1e-3),
+                     "munks": world * munk_cyc / (total * 1e-3) / 1e6,
+                     "worst_final_rel_residual": worst}
+    F.profile(True)
+    F.profile_read()
+    F.set_rhs(g)
+    F.solve(G.MIXED, args.tol, 80)
+    prof = F.profile_read()
+    F.profile(False)
+    peak, peak_kind = peaks()
+    roof, by_kind = roofline_of(prof, F, 1, peak, peak_kind)
+    out = {"workload": "forest_64_uniform_trees_32^3-256^3_ellipsoids_mixed_to_1e-8", "unknowns": n,
+           "trees": 64, "tree_sizes": {str(k): sizes.count(k) for k in sorted(set(sizes))},
+           "latency_is": "one solve of all 64 problems (each to its own 1e-8) from phi = 0",
+           "autotuned": {"block_n": N, "fine_sweeps": list(best.fine_sweeps),
+                         "coarse_sweeps": list(best.coarse_sweeps), "cta_threads": best.cta_threads,
+                         "coop_max_blocks": best.coop_max_blocks, "fused": best.fused,
+                         "tuning_s": tune_s, "trials": len(best.trials),
+                         "sample": "8 problems of the same distribution (seed index 4), tiles 8 and 16"},
+           "setup_s": setup_s, "mixed": res["mixed"], "fp64": res["fp64"], "roofline": roof,
+           "kernel_ms_by_kind": {"%s_%s" % k: v for k, v in sorted(by_kind.items(), key=lambda kv: -kv[1])}}
+    F.close()
+    del g
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_serving(G, args, world):
+    """Serving loop: Poisson arrivals of Gaussian-charge right-hand sides for
+    seven resident sessions (the 2D circle at 512^2, spheres at 64^3, 128^3
+    and 256^3, the needle at 5, 6 and 7 levels), 8 slots each, HBM budget
+    160 GB; continuous batching (serving.Server).  Sessions are loaded and
+    their graphs captured by a warm-up request each; the timed run serves
+    a fresh seeded stream, mixed and FP64."""
+    import torch
+    from paper_2205_09411_gb300.serving import Request, Server, Session, poisson_arrivals, summarize
+    specs = {"circle2d_512": I.problem("c1", max_level=7),
+             "sphere_64": I.problem("c2", max_level=3),
+             "sphere_128": I.problem("c2"),
+             "sphere_256": I.problem("c2", max_level=5),
+             "needle_5lev": I.problem("c3", max_level=5, n_rhs=1),
+             "needle_6lev": I.problem("c3", max_level=6, n_rhs=1),
+             "needle_7lev": I.problem("c3", max_level=7, n_rhs=1)}
+    t0 = time.perf_counter()
+    sessions = [Session(name, make=lambda slots, p=p: host_tree(G, p, nrhs=slots)) for name, p in specs.items()]
+
+    def on_load(s):
+        s.ctx["xc"] = torch.tensor(s.tree.leaf_centers(), device="cuda")
+        s.ctx["out"] = torch.empty((1, s.tree.n_leaf_cells), dtype=torch.float64, device="cuda")
+
+    def result_to(s, slot):  # the solution gathered into a device buffer
+        s.tree.solution_slots(slot, 1, out=s.ctx["out"], stream=s.stream)
+        return None
+
+    names = list(specs)
+    n_req, rate = 160, 60.0
+    charges = I.gaussian_charges(n_req + len(names), 5)
+    pick = I.rng_for(6).integers(len(names), size=n_req)
+    arrive = poisson_arrivals(rate, n_req, 7)
+
+    def req(i, name, at):
+        return Request(name, lambda s, c=charges[i]: I.charge_density_torch(s.ctx["xc"], c), at)
+
+    out = {"sessions": {}, "rate_per_s": rate, "requests": n_req, "slots_per_session": 8, "budget_gb": 160.0}
+    for label, prec in (("mixed", G.MIXED), ("fp64", G.FP64)):
+        srv = Server(sessions, budget_bytes=160e9, slots=8, precision=prec, tol=args.tol, on_load=on_load,
+                     new_stream=lambda: torch.cuda.Stream(), result_to=result_to,
+                     stream_context=lambda s: torch.cuda.stream(s.stream))
+        srv.run([req(n_req + k, name, 0.0) for k, name in enumerate(names)])  # load + graph capture
+        torch.cuda.synchronize()
+        done = srv.run([req(i, names[int(pick[i])], float(arrive[i])) for i in range(n_req)])
+        torch.cuda.synchronize()
+        out[label] = summarize(done) | {"resident_gb": max(srv.peak_bytes, srv.resident_bytes()) / 1e9}
+    for s in sessions:
+        if s.resident:
+            out["sessions"][s.name] = {"leaf_cells": s.tree.n_leaf_cells, "workspace_gb": s.nbytes / 1e9}
+            s.tree.close()
+            s.tree = None
+    out["setup_and_run_s"] = time.perf_counter() - t0
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     import paper_2205_09411_gb300 as G
@@ -473,6 +647,10 @@ def run_ours(args):
     t.close()
     if not args.skip_needle:
         result["batched_needle"] = run_needle(G, args, world, flush, stream)
+    if not args.skip_forest:
+        result["batched_forest"] = run_forest(G, args, world, flush, stream)
+    if not args.skip_serving:
+        result["serving"] = run_serving(G, args, world)
     if rank == 0 and world == 1:
         result["cpu_baseline"] = cpu_baseline(p)
     if rank == 0:

@@ -120,11 +120,12 @@ def gaussian_charges(n_rhs: int, index: int):
 
 
 def charge_density(xc, charges):
-    """g(x) = sum_k a_k exp(-|x - c_k|^2 / (2 w_k^2)) at the points xc (n x 3)."""
+    """g(x) = sum_k a_k exp(-|x - c_k|^2 / (2 w_k^2)) at the points xc (n x 3,
+    or n x 2 with the centres' first two coordinates)."""
     c, w, a = charges
     g = np.zeros(len(xc))
     for k in range(len(a)):
-        d2 = np.sum((xc - c[k]) ** 2, axis=1)
+        d2 = np.sum((xc - c[k][:xc.shape[1]]) ** 2, axis=1)
         g += a[k] * np.exp(-d2 / (2.0 * w[k] ** 2))
     return g
 
@@ -135,7 +136,7 @@ def charge_density_torch(xc, charges):
     c, w, a = charges
     g = torch.zeros(xc.shape[0], dtype=torch.float64, device=xc.device)
     for k in range(len(a)):
-        ck = torch.tensor(c[k], dtype=torch.float64, device=xc.device)
+        ck = torch.tensor(c[k][:xc.shape[1]], dtype=torch.float64, device=xc.device)
         d2 = ((xc - ck) ** 2).sum(dim=1)
         g += float(a[k]) * torch.exp(-d2 / (2.0 * float(w[k]) ** 2))
     return g
@@ -177,16 +178,39 @@ def box_noise_rhs(xc, n: int, seed: int) -> np.ndarray:
     """White noise N(0,1) on the n^3 grid of the unit cube, averaged over the
     3^3 cells around each cell (cells outside the domain count as zero),
     sampled at the cell centres xc (any order)."""
-    w = np.random.Generator(np.random.PCG64(seed)).standard_normal((n, n, n))  # [z, y, x]
+    g = box_noise_grid(n, seed)
+    ix = np.floor(np.asarray(xc) * n).astype(np.int64)
+    return g[ix[:, 2], ix[:, 1], ix[:, 0]]
+
+
+def box_noise_grid(n: int, seed: int) -> np.ndarray:
+    """The filtered noise of box_noise_rhs on the whole n^3 grid, [z, y, x]."""
+    w = np.random.Generator(np.random.PCG64(seed)).standard_normal((n, n, n))
     p = np.pad(w, 1)
     acc = np.zeros_like(w)
     for dz in range(3):
         for dy in range(3):
             for dx in range(3):
                 acc += p[dz:dz + n, dy:dy + n, dx:dx + n]
-    g = acc / 27.0
-    ix = np.floor(np.asarray(xc) * n).astype(np.int64)
-    return g[ix[:, 2], ix[:, 1], ix[:, 0]]
+    return acc / 27.0
+
+
+def box_noise_rhs_torch(bix, N: int, n: int, seed: int, device="cuda"):
+    """box_noise_rhs of a uniform tree in leaf order, built on a torch device
+    from the leaf blocks' coordinates bix (k x 3, leaf order) and the block
+    side N: the same noise (numpy PCG64), the 3^3 mean taken by avg_pool3d
+    with zero padding."""
+    import torch
+    w = np.random.Generator(np.random.PCG64(seed)).standard_normal((n, n, n))
+    g = torch.nn.functional.avg_pool3d(torch.tensor(w, device=device)[None, None], 3, stride=1, padding=1,
+                                       count_include_pad=True)[0, 0]
+    b = torch.tensor(np.asarray(bix, dtype=np.int64), device=device)
+    c = torch.arange(N ** 3, device=device)
+    x, y, z = c % N, (c // N) % N, c // (N * N)
+    gx = (b[:, 0:1] * N + x[None, :]).reshape(-1)
+    gy = (b[:, 1:2] * N + y[None, :]).reshape(-1)
+    gz = (b[:, 2:3] * N + z[None, :]).reshape(-1)
+    return g[gz, gy, gx]
 
 
 def problem(name: str, **over) -> dict:

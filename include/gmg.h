@@ -257,6 +257,13 @@ int gmg_solve(gmg_tree *tree, int precision, double rel_tol, int max_cycles, gmg
  * Synchronises the stream. */
 int gmg_iterate(gmg_tree *tree, int precision, const int *active, int residual_only, double *rel_l2, double *linf,
                 void *stream);
+/* gmg_iterate in two halves, so that steps of several trees (each on its
+ * own stream) run on the device at the same time: _begin enqueues the step
+ * (it waits only for this tree's previous work on `stream`), _end waits for
+ * it and reads the norms.  A tree holds at most one step in flight.
+ * Errors: STATE for _begin with a step in flight or _end without one. */
+int gmg_iterate_begin(gmg_tree *tree, int precision, const int *active, int residual_only, void *stream);
+int gmg_iterate_end(gmg_tree *tree, double *rel_l2, double *linf);
 
 /* Inspection (tests, tools): phi (which = 0) or b (which = 1) of every cell
  * of a level in canonical block order, FP64 host array; distances d

@@ -91,6 +91,8 @@ def load():
         "gmg_get_solution_slots": (C.c_int, [vp, C.c_int, C.c_int, vp, C.c_int, vp]),
         "gmg_iterate": (C.c_int, [vp, C.c_int, ip, C.c_int, dp, dp, vp]),
         "gmg_forest_create": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(vp)]),
+        "gmg_iterate_begin": (C.c_int, [vp, C.c_int, ip, C.c_int, vp]),
+        "gmg_iterate_end": (C.c_int, [vp, dp, dp]),
         "gmg_set_level_sweeps": (C.c_int, [vp, C.c_int, C.c_int, C.c_int]),
         "gmg_get_level_sweeps": (C.c_int, [vp, C.c_int, ip, ip]),
         "gmg_num_trees": (C.c_int, [vp]),
@@ -389,6 +391,19 @@ class Tree:
         dp = lambda x: x.ctypes.data_as(C.POINTER(C.c_double))
         _check(load().gmg_iterate(self.h, precision, a.ctypes.data_as(C.POINTER(C.c_int)), 1 if residual_only else 0,
                                   dp(r), dp(m), _stream_ptr(stream)))
+        return r, m
+
+    def iterate_begin(self, precision, active, residual_only=False, stream=None):
+        """Enqueue one solve-loop step (see iterate) without waiting for it."""
+        a = np.ascontiguousarray(np.asarray(active, dtype=np.int32).reshape(self.units))
+        _check(load().gmg_iterate_begin(self.h, precision, a.ctypes.data_as(C.POINTER(C.c_int)),
+                                        1 if residual_only else 0, _stream_ptr(stream)))
+
+    def iterate_end(self):
+        """Wait for the step in flight; returns (rel_l2, linf) arrays over the units."""
+        r, m = np.zeros(self.units), np.zeros(self.units)
+        dp = lambda x: x.ctypes.data_as(C.POINTER(C.c_double))
+        _check(load().gmg_iterate_end(self.h, dp(r), dp(m)))
         return r, m
 
     def solve(self, precision=FP64, rel_tol=1e-8, max_cycles=50, stream=None, check=True):

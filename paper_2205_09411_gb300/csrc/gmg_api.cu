@@ -65,53 +65,57 @@ __global__ void __launch_bounds__(1024) k_reduce_partials(const double *partials
   }
 }
 
-// Leaf-cell kernels over the slots r0 .. r0 + nr - 1: element k of the
-// leaf-ordered array io (nr x nleaf) is cell (k % nleaf) of slot
-// r0 + k / nleaf; field arrays of slot r start at r * rs.
+// Leaf-cell kernels over the slots r0 .. r0 + nr - 1: a CTA takes leaf
+// blocks lb = blockIdx.x, +gridDim.x, ...; element k of the leaf-ordered
+// array io (nr x nleaf cells) is cell (k % nleaf) of slot r0 + k / nleaf;
+// field arrays of slot r start at r * rs.
 
 // b <- g - boundary terms on leaf cells (g in leaf-cell order)
 __global__ void k_leaf_rhs(const int *__restrict__ leaf_ids, const long long *__restrict__ cbase,
                            const long long *__restrict__ bt_base, const double *__restrict__ bterm,
-                           const double *__restrict__ g, double *__restrict__ b, long long nleaf, int ncell,
-                           long long rs, int r0, int nr) {
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nleaf * nr;
-       k += (long long)gridDim.x * blockDim.x) {
-    const long long r = r0 + k / nleaf, kk = k % nleaf;
-    const int id = leaf_ids[kk / ncell];
-    const int c = (int)(kk % ncell);
-    const long long bb = bt_base[id];
-    b[r * rs + cbase[id] + c] = g[k] - (bb >= 0 ? bterm[bb + c] : 0.0);
+                           const double *__restrict__ g, double *__restrict__ b, int nlb, int ncell, long long rs,
+                           int r0, int nr) {
+  const long long nleaf = (long long)nlb * ncell;
+  for (int lb = blockIdx.x; lb < nlb; lb += gridDim.x) {
+    const int id = leaf_ids[lb];
+    const long long base = cbase[id], bb = bt_base[id];
+    for (int r = 0; r < nr; r++)
+      for (int c = threadIdx.x; c < ncell; c += blockDim.x)
+        b[(r0 + r) * rs + base + c] = g[r * nleaf + (long long)lb * ncell + c] - (bb >= 0 ? bterm[bb + c] : 0.0);
   }
 }
 
 // leaf gather (dir 0: field -> io) / scatter (dir 1: io -> field)
 __global__ void k_leaf_copy(const int *__restrict__ leaf_ids, const long long *__restrict__ cbase, double *field,
-                            double *io, long long nleaf, int ncell, long long rs, int r0, int nr, int dir) {
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nleaf * nr;
-       k += (long long)gridDim.x * blockDim.x) {
-    const long long r = r0 + k / nleaf, kk = k % nleaf;
-    const int id = leaf_ids[kk / ncell];
-    const long long f = r * rs + cbase[id] + (kk % ncell);
-    if (dir == 0)
-      io[k] = field[f];
-    else
-      field[f] = io[k];
+                            double *io, int nlb, int ncell, long long rs, int r0, int nr, int dir) {
+  const long long nleaf = (long long)nlb * ncell;
+  for (int lb = blockIdx.x; lb < nlb; lb += gridDim.x) {
+    const long long base = cbase[leaf_ids[lb]];
+    for (int r = 0; r < nr; r++)
+      for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+        const long long f = (r0 + r) * rs + base + c, k = r * nleaf + (long long)lb * ncell + c;
+        if (dir == 0)
+          io[k] = field[f];
+        else
+          field[f] = io[k];
+      }
   }
 }
 
 // phi64 += e32 on leaf cells of the active units (mixed path: solution
 // accumulation in FP64)
 __global__ void k_leaf_accumulate(const int *__restrict__ leaf_ids, const long long *__restrict__ cbase,
-                                  double *__restrict__ phi, const float *__restrict__ e, long long nleaf, int ncell,
+                                  double *__restrict__ phi, const float *__restrict__ e, int nlb, int ncell,
                                   long long rs, int nr, const int *__restrict__ active, const int *__restrict__ tree_of,
                                   int ntree) {
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nleaf * nr;
-       k += (long long)gridDim.x * blockDim.x) {
-    const long long r = k / nleaf, kk = k % nleaf;
-    const int id = leaf_ids[kk / ncell];
-    if (!active[ntree > 1 ? r * ntree + tree_of[id] : r]) continue;
-    const long long f = r * rs + cbase[id] + (kk % ncell);
-    phi[f] += (double)e[f];
+  for (int lb = blockIdx.x; lb < nlb; lb += gridDim.x) {
+    const int id = leaf_ids[lb];
+    const long long base = cbase[id];
+    const int tr = ntree > 1 ? tree_of[id] : 0;
+    for (int r = 0; r < nr; r++) {
+      if (!active[r * ntree + tr]) continue;
+      for (int c = threadIdx.x; c < ncell; c += blockDim.x) phi[r * rs + base + c] += (double)e[r * rs + base + c];
+    }
   }
 }
 
@@ -134,6 +138,8 @@ using namespace gmg;
 namespace {
 
 int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 152LL * 16); }
+int n_leaf_blocks(const gmg_tree *t) { return (int)t->leaf_ids_h.size(); }
+int leaf_grid(const gmg_tree *t) { return std::max(1, std::min(n_leaf_blocks(t), 152 * 16)); }
 
 cudaEvent_t prof_event(gmg_tree *t) {
   if (t->prof_used == t->prof_pool.size()) {
@@ -562,11 +568,10 @@ int mixed_step(gmg_tree *t, cudaStream_t s) {
   CUDA_TRY(cudaMemsetAsync(t->f_phi, 0, (size_t)t->nrhs * t->total_cells * sizeof(float), s));
   int rc = vcycle_any<float>(t, s);
   if (rc) return rc;
-  const long long n = t->n_leaf_cells;
   launch(t, s, 8, 0, t->lmax, [&] {
-    k_leaf_accumulate<<<grid_for(n * t->nrhs), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, t->f_phi, n,
-                                                            t->leaf_ncell(), t->total_cells, t->nrhs, t->d_active,
-                                                            t->d_tree_of, t->ntree);
+    k_leaf_accumulate<<<leaf_grid(t), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, t->f_phi, n_leaf_blocks(t),
+                                                   t->leaf_ncell(), t->total_cells, t->nrhs, t->d_active, t->d_tree_of,
+                                                   t->ntree);
   });
   CUDA_TRY(cudaGetLastError());
   if (t->adaptive) return restrict_all_phi64_any(t, s);
@@ -920,7 +925,17 @@ int gmg_tree_bind(gmg_tree *t, void *device_ptr, size_t bytes) {
   CUDA_TRY(cudaMemcpy(t->d_tree_boff, t->tree_boff_h.data(), t->tree_boff_h.size() * sizeof(int),
                       cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(t->d_pofs, t->pofs_h.data(), nb * sizeof(int), cudaMemcpyHostToDevice));
-  CUDA_TRY(cudaMemcpy(t->d_flags, t->flags_h.data(), nb * sizeof(int), cudaMemcpyHostToDevice));
+  {  // block flags plus, per face, whether the same-level neighbour is covered
+    std::vector<int> fl(t->flags_h);
+    for (size_t i = 0; i < nb; i++)
+      for (int f = 0; f < 2 * t->D; f++) {
+        const int a = f >> 1, o = 2 * (f & 1) - 1;
+        const int slot = (a == 2 ? o + 1 : 1) * 9 + (a == 1 ? o + 1 : 1) * 3 + (a == 0 ? o + 1 : 1);
+        const int id = t->nbr_h[i * kNbr + slot];
+        if (id >= 0 && t->blocks[id].has_children) fl[i] |= face_covered_bit(f);
+      }
+    CUDA_TRY(cudaMemcpy(t->d_flags, fl.data(), nb * sizeof(int), cudaMemcpyHostToDevice));
+  }
   CUDA_TRY(cudaMemcpy(t->d_leaf, t->leaf_ids_h.data(), t->leaf_ids_h.size() * sizeof(int), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(d_cbase, cbase.data(), nb * sizeof(long long), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(t->d_st_base, t->st_base_h.data(), nb * sizeof(long long), cudaMemcpyHostToDevice));
@@ -988,8 +1003,8 @@ int gmg_set_rhs_slots(gmg_tree *t, int slot0, int nslots, const double *g, int w
   } else if (where != GMG_DEVICE) {
     return set_error("where must be GMG_HOST or GMG_DEVICE"), GMG_ERR_INVALID_ARG;
   }
-  k_leaf_rhs<<<grid_for(n * nslots), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_bt_base, t->d_bterm, gd, t->d_b, n,
-                                                  t->leaf_ncell(), t->total_cells, slot0, nslots);
+  k_leaf_rhs<<<leaf_grid(t), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_bt_base, t->d_bterm, gd, t->d_b,
+                                          n_leaf_blocks(t), t->leaf_ncell(), t->total_cells, slot0, nslots);
   CUDA_TRY(cudaMemsetAsync(t->d_phi + (size_t)slot0 * t->total_cells, 0,
                            (size_t)nslots * t->total_cells * sizeof(double), s));
   CUDA_TRY(cudaGetLastError());
@@ -1011,8 +1026,8 @@ int gmg_set_solution(gmg_tree *t, const double *phi, int where, void *stream) {
     CUDA_TRY(cudaMemcpyAsync(t->d_old, phi, (size_t)t->nrhs * n * sizeof(double), cudaMemcpyHostToDevice, s));
     src = t->d_old;
   }
-  k_leaf_copy<<<grid_for(n * t->nrhs), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, src, n, t->leaf_ncell(),
-                                                    t->total_cells, 0, t->nrhs, 1);
+  k_leaf_copy<<<leaf_grid(t), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, src, n_leaf_blocks(t), t->leaf_ncell(),
+                                           t->total_cells, 0, t->nrhs, 1);
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemsetAsync(t->d_active, 1, (size_t)t->units() * sizeof(int), s));
   return restrict_all_phi64_any(t, s);
@@ -1026,14 +1041,14 @@ int gmg_get_solution_slots(gmg_tree *t, int slot0, int nslots, double *phi, int 
   const long long n = t->n_leaf_cells;
   const int ncell = t->leaf_ncell();
   if (where == GMG_DEVICE) {
-    k_leaf_copy<<<grid_for(n * nslots), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, phi, n, ncell, t->total_cells,
-                                                     slot0, nslots, 0);
+    k_leaf_copy<<<leaf_grid(t), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, phi, n_leaf_blocks(t), ncell,
+                                             t->total_cells, slot0, nslots, 0);
     CUDA_TRY(cudaGetLastError());
     return GMG_OK;
   }
   // the FP64 'old' field is dead between V-cycles: stage the gather there
-  k_leaf_copy<<<grid_for(n * nslots), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, t->d_old, n, ncell,
-                                                   t->total_cells, slot0, nslots, 0);
+  k_leaf_copy<<<leaf_grid(t), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, t->d_old, n_leaf_blocks(t), ncell,
+                                           t->total_cells, slot0, nslots, 0);
   CUDA_TRY(cudaMemcpyAsync(phi, t->d_old, (size_t)nslots * n * sizeof(double), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   return GMG_OK;
@@ -1110,11 +1125,11 @@ int gmg_residual(gmg_tree *t, double *rel_l2, double *linf, void *stream) {
   return GMG_OK;
 }
 
-int gmg_iterate(gmg_tree *t, int precision, const int *active, int residual_only, double *rel_l2, double *linf,
-                void *stream) {
+int gmg_iterate_begin(gmg_tree *t, int precision, const int *active, int residual_only, void *stream) {
   if (!t || !active) return set_error("null argument"), GMG_ERR_INVALID_ARG;
   if (precision != GMG_FP64 && precision != GMG_MIXED) return set_error("bad precision"), GMG_ERR_INVALID_ARG;
   if (!t->bound) return set_error("tree not bound"), GMG_ERR_STATE;
+  if (t->step_pending) return set_error("gmg_iterate_end has not collected the previous step"), GMG_ERR_STATE;
   cudaStream_t s = as_stream(stream);
   t->launches = 0;
   const bool mixed = precision == GMG_MIXED;
@@ -1130,10 +1145,25 @@ int gmg_iterate(gmg_tree *t, int precision, const int *active, int residual_only
       return r ? r : residual_any(t, cs, rout);
     });
   if (rc) return rc;
-  rc = read_red(t, s);
+  t->step_pending = true;
+  t->step_stream = s;
+  return GMG_OK;
+}
+
+int gmg_iterate_end(gmg_tree *t, double *rel_l2, double *linf) {
+  if (!t) return set_error("null tree"), GMG_ERR_INVALID_ARG;
+  if (!t->step_pending) return set_error("no step in flight"), GMG_ERR_STATE;
+  t->step_pending = false;
+  const int rc = read_red(t, t->step_stream);
   if (rc) return rc;
   for (int u = 0; u < t->units(); u++) slot_norms(t, u, rel_l2 ? rel_l2 + u : nullptr, linf ? linf + u : nullptr, nullptr);
   return GMG_OK;
+}
+
+int gmg_iterate(gmg_tree *t, int precision, const int *active, int residual_only, double *rel_l2, double *linf,
+                void *stream) {
+  const int rc = gmg_iterate_begin(t, precision, active, residual_only, stream);
+  return rc ? rc : gmg_iterate_end(t, rel_l2, linf);
 }
 
 int gmg_solve(gmg_tree *t, int precision, double rel_tol, int max_cycles, gmg_stats *stats, void *stream) {

@@ -21,6 +21,8 @@ constexpr int kNbr = 27;  // 3x3x3 neighbour offsets (2D uses the dz = 0 plane)
 // block flags
 constexpr int kHasChildren = 1;
 inline __host__ __device__ int wall_bit(int axis, int side) { return 2 << (2 * axis + side); }
+// face f = 2 axis + side has a same-level neighbour with children (set at bind)
+inline __host__ __device__ int face_covered_bit(int f) { return 1 << (16 + f); }
 
 struct HostBlock {
   int level;
@@ -174,6 +176,8 @@ struct gmg_tree {
   long long spin_limit = 1LL << 24;
   gmg::GridBar *d_bar = nullptr;
   cudaStream_t cap_stream = nullptr;
+  bool step_pending = false;  // gmg_iterate_begin enqueued a step that gmg_iterate_end has not read
+  cudaStream_t step_stream = nullptr;
 
   // kernel timing (gmg_profile_enable)
   struct ProfRec {

@@ -101,24 +101,26 @@ __device__ __forceinline__ bool resolve_s(const int *s_nb, int bid, const LvArgs
 // adjacent fine cell and c_hat the coarse cell containing the ghost centre
 // shifted by central tangential slopes (+-1/4 coarse cell).
 // `own` holds the block's own cells (phi, or old for a covered block in the
-// FAS kernel).
+// FAS kernel).  The tables come as plain arguments (not the view), so that
+// callers can keep a per-slot view in registers.
 template <typename T, int D>
-__device__ __noinline__ T refine_ghost(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, const int *p,
-                                       int a, const T *own) {
+__device__ __noinline__ T refine_ghost(const T *phi, const int *nbr, const int *flags, const int *parent,
+                                       const int *pofs_t, int wneu, const LvArgs &L, const LvArgs &Lp, int bid,
+                                       const int *p, int a, const T *own) {
   const int n = L.n;
   int q[3] = {p[0], p[1], p[2]};
   q[a] = p[a] < 0 ? 0 : n - 1;
   const T f = own[q[0] + n * (q[1] + (D == 3 ? n * q[2] : 0))];
   const long long dp = Lp.poff - Lp.off;  // phi of the coarse level may live in the second buffer
-  const int P = V.parent[bid], po = V.pofs[bid];
+  const int P = parent[bid], po = pofs_t[bid];
   const int pofs[3] = {po & 1023, (po >> 10) & 1023, (po >> 20) & 1023};
   int cq[3] = {0, 0, 0};
 #pragma unroll
   for (int d = 0; d < D; d++) cq[d] = pofs[d] + (p[d] >> 1);
   long long ix;
   float sg;
-  if (!resolve<D>(V.nbr, V.flags, V.wneu, Lp, P, cq, &ix, &sg)) return T(NAN);
-  const T c = V.phi[ix + dp];
+  if (!resolve<D>(nbr, flags, wneu, Lp, P, cq, &ix, &sg)) return T(NAN);
+  const T c = phi[ix + dp];
   T chat = c;
 #pragma unroll
   for (int t = 0; t < D; t++) {
@@ -129,9 +131,9 @@ __device__ __noinline__ T refine_ghost(const GmgView<T> &V, const LvArgs &L, con
     qm[t] -= 1;
     long long ip, im;
     float sp, sm;
-    if (!resolve<D>(V.nbr, V.flags, V.wneu, Lp, P, qp, &ip, &sp)) return T(NAN);
-    if (!resolve<D>(V.nbr, V.flags, V.wneu, Lp, P, qm, &im, &sm)) return T(NAN);
-    const T cp = T(sp) * V.phi[ip + dp], cm = T(sm) * V.phi[im + dp];
+    if (!resolve<D>(nbr, flags, wneu, Lp, P, qp, &ip, &sp)) return T(NAN);
+    if (!resolve<D>(nbr, flags, wneu, Lp, P, qm, &im, &sm)) return T(NAN);
+    const T cp = T(sp) * phi[ip + dp], cm = T(sm) * phi[im + dp];
     chat = chat + o * (T(0.5) * (cp - cm));
   }
   return f / T(3) + T(2) * chat / T(3);
@@ -214,7 +216,6 @@ template <typename T, int D, int NT, bool FAS = false>
 __device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, T *tile,
                           T *sbv = nullptr, unsigned char *sflag = nullptr, long long sb = -1) {
   __shared__ int s_nb[6];
-  __shared__ int s_cov[6];
   __shared__ int s_fl;
   const int n = NT ? NT : L.n;
   const TileGeo<T, D> G(n);
@@ -222,9 +223,7 @@ __device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
   if (threadIdx.x < 2 * D) {
     const int a = threadIdx.x >> 1, side = threadIdx.x & 1;
     const int o[3] = {a == 0 ? 2 * side - 1 : 0, a == 1 ? 2 * side - 1 : 0, a == 2 ? 2 * side - 1 : 0};
-    const int id = V.nbr[(size_t)bid * kNbr + nbr_slot(o[0], o[1], o[2])];
-    s_nb[threadIdx.x] = id;
-    s_cov[threadIdx.x] = FAS && id >= 0 ? (V.flags[id] & kHasChildren) : 0;
+    s_nb[threadIdx.x] = V.nbr[(size_t)bid * kNbr + nbr_slot(o[0], o[1], o[2])];
   }
   if (threadIdx.x == 0) s_fl = V.flags[bid];
   const long long base = L.off + (long long)(bid - L.first) * ncell;   // b
@@ -267,7 +266,7 @@ __device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
     const int gn = side ? n : -1, sn = side ? 0 : n - 1;
     const int gx = a == 0 ? gn : u, gy = a == 1 ? gn : (a == 0 ? u : v), gz = a == 2 ? gn : v;
     const int qx = a == 0 ? sn : u, qy = a == 1 ? sn : (a == 0 ? u : v), qz = a == 2 ? sn : v;
-    const T *src = s_cov[f] ? V.old + L.off : V.phi + L.poff;
+    const T *src = (FAS && (fl & face_covered_bit(f))) ? V.old + L.off : V.phi + L.poff;
     cp_async_elem(tile + G.idx(gx, gy, gz),
                   src + (long long)(id - L.first) * ncell + qx + n * (qy + (D == 3 ? n * qz : 0)));
   }
@@ -287,7 +286,7 @@ __device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
       val = (((V.wneu >> f) & 1) ? T(1) : T(-1)) * tile[G.idx(mx, my, mz)];
     } else {
       const int g[3] = {gx, gy, gz};
-      val = refine_ghost<T, D>(V, L, Lp, bid, g, a, own);
+      val = refine_ghost<T, D>(V.phi, V.nbr, V.flags, V.parent, V.pofs, V.wneu, L, Lp, bid, g, a, own);
     }
     tile[G.idx(gx, gy, gz)] = val;
   }

@@ -100,3 +100,45 @@ def test_forest_rejects_mismatched_trees():
     c = gpu_problem(ps[2])  # bound
     with pytest.raises(G.GmgError):
         G.Forest([a, c])
+
+
+def test_sweep_schedule_default_is_unchanged_and_others_converge():
+    """Setting every level's sweeps to the parameters' (2, 2) gives the same
+    iterates bit for bit; a level-dependent schedule (1 + 1 on the fine
+    levels, 4 + 4 on the coarse ones) still solves to 1e-8 by the oracle's
+    own residual."""
+    import paper_2205_09411_gb300 as G
+    p = problems()[4]
+    a = gpu_problem(p)
+    b = gpu_problem(p)
+    for l in range(b.lmin, b.lmax + 1):
+        b.set_level_sweeps(l, 2, 2)
+    a.vcycle(3)
+    b.vcycle(3)
+    assert np.array_equal(a.solution(), b.solution())
+    for l in range(b.lmin, b.lmax + 1):
+        b.set_level_sweeps(l, *((1, 1) if l == b.lmax else (4, 4)))
+    assert b.level_sweeps(b.lmax) == (1, 1)
+    b.set_rhs(np.asarray(p["rhs"](b.leaf_centers()), dtype=np.float64))
+    st = b.solve(G.MIXED, 1e-8, 80)
+    o = oracle_problem(p)
+    o.set_solution(b.solution())
+    l2, _, bn = o.residual()
+    assert st["rel_l2"] <= 1e-8 and l2 / bn <= 1.05e-8
+
+
+def test_autotuner_returns_a_converging_schedule():
+    import paper_2205_09411_gb300 as G
+    from paper_2205_09411_gb300 import autotune as AT
+    ps = problems()[:3]
+    F, trees = make_forest(ps)
+    g = forest_rhs(F, ps, trees)
+    s = AT.tune(F, lambda: F.set_rhs(g), G.MIXED, 1e-8, reps=1)
+    assert len(s.trials) >= 10
+    assert all(x["seconds"] is None or x["seconds"] > 0 for x in s.trials)
+    F.set_rhs(g)
+    st = F.solve(G.MIXED, 1e-8, 80)
+    assert st["rel_l2"] <= 1e-8
+    split = AT.coop_levels(F, s.coop_max_blocks)
+    for l in range(F.lmin, F.lmax + 1):
+        assert F.level_sweeps(l) == tuple(s.coarse_sweeps if l <= split else s.fine_sweeps)

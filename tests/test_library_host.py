@@ -129,3 +129,22 @@ def test_forest_structure():
         assert np.array_equal(xc[o:o + n], t.leaf_centers())
         off += n
         assert F.num_cut_blocks(t.lmax) >= t.num_cut_blocks(t.lmax)
+
+
+def test_box_noise_generators_agree():
+    """The batched uneven-tree right-hand side: the leaf-order generator on
+    torch (used at full size) equals the point-sampled numpy one, and the
+    3^3 mean with zero padding is what it says (checked at a corner and an
+    interior cell)."""
+    import gmg_inputs as I
+    import paper_2205_09411_gb300 as G
+    n, N, seed = 16, 8, 1234
+    t = G.Tree(3, N, (1, 1, 1), (0, 0, 0), 1 / 8, 2)
+    bix, _ = t.level_blocks(t.lmax)
+    a = I.box_noise_rhs(t.leaf_centers(), n, seed)
+    b = I.box_noise_rhs_torch(bix, N, n, seed, device="cpu").numpy()
+    assert np.allclose(a, b, rtol=0, atol=1e-15)
+    w = np.random.Generator(np.random.PCG64(seed)).standard_normal((n, n, n))
+    g = I.box_noise_grid(n, seed)
+    assert abs(g[0, 0, 0] - w[:2, :2, :2].sum() / 27) < 1e-15
+    assert abs(g[5, 6, 7] - w[4:7, 5:8, 6:9].sum() / 27) < 1e-15
