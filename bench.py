@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--skip-needle", action="store_true", help="leave out the batched needle workload")
     ap.add_argument("--skip-forest", action="store_true", help="leave out the batched uneven-tree workload")
     ap.add_argument("--skip-serving", action="store_true", help="leave out the serving-loop workload")
+    ap.add_argument("--only", choices=["needle", "forest", "serving"], default=None,
+                    help="run one secondary workload alone (no headline line; for profiling)")
+    ap.add_argument("--needle-rhs", type=int, default=32, help="right-hand sides of the batched needle workload")
     return ap.parse_args()
 
 
@@ -308,7 +311,7 @@ def run_needle(G, args, world, flush, stream):
     in one tree, each step one batched solve of all 32 to 1e-8, mixed and
     FP64.  Right-hand sides are generated on the device (seeded)."""
     import torch
-    R = 32
+    R = args.needle_rhs
     p = I.problem("c3", n_rhs=R)
     t0 = time.perf_counter()
     t = G.Tree(p["dim"], p["N"], p["cb"], p["lo"], p["h1"], p["max_level"], refine=p["refine"],
@@ -324,6 +327,14 @@ def run_needle(G, args, world, flush, stream):
         g[r] = I.charge_density_torch(xc, p["charges"][r])
     del xc
     torch.cuda.synchronize()
+
+    # schedule: the autotuner's pick of sweeps and FP32 cycles per step for
+    # this tree (mixed path), kept for both precisions' timed runs
+    from paper_2205_09411_gb300 import autotune as AT
+    t1 = time.perf_counter()
+    sched = AT.tune(t, lambda: t.set_rhs(g), G.MIXED, args.tol, reps=1,
+                    axes=("fine_sweeps", "inner_cycles", "coarse_sweeps"))
+    tune_s = time.perf_counter() - t1
 
     def one(prec, profile=False):
         if profile:
@@ -355,18 +366,21 @@ def run_needle(G, args, world, flush, stream):
             launches += nl
         total = allreduce_max(sum(times), world)
         ts = sorted(times)
+        vc = cyc * (sched.inner_cycles if prec == G.MIXED else 1)  # V-cycles (FP32 ones in the mixed path)
         res[name] = {"p50_ms": float(np.percentile(ts, 50)), "p99_ms": float(np.percentile(ts, 99)),
                      "solves_per_s": world * R * len(ts) / (total * 1e-3),
-                     "munks": world * n * cyc / (total * 1e-3) / 1e6,
-                     "cycles_per_solve": cyc / (R * len(ts)), "worst_final_rel_residual": worst,
-                     "gpu_launches_per_batch": launches / len(ts)}
+                     "munks": world * n * vc / (total * 1e-3) / 1e6,
+                     "steps_per_solve": cyc / (R * len(ts)), "v_cycles_per_solve": vc / (R * len(ts)),
+                     "worst_final_rel_residual": worst, "gpu_launches_per_batch": launches / len(ts)}
     _, _, _, prof = one(G.MIXED, profile=True)
     peak, peak_kind = peaks()
     roof, by_kind = roofline_of(prof, t, R, peak, peak_kind)
-    out = {"workload": "needle3d_adaptive_7levels_8^3blocks_32rhs_gaussian_mixed_to_1e-8", "unknowns": n,
+    out = {"workload": "needle3d_adaptive_7levels_8^3blocks_%drhs_gaussian_mixed_to_1e-8" % R, "unknowns": n,
            "rhs": R, "blocks": t.n_blocks, "levels": [t.lmin, t.lmax], "setup_s": setup_s,
-           "latency_is": "one batched solve of all 32 right-hand sides from phi = 0",
+           "latency_is": "one batched solve of all %d right-hand sides from phi = 0" % R,
            "mixed": res["mixed"], "fp64": res["fp64"], "roofline": roof,
+           "autotuned": {"fine_sweeps": list(sched.fine_sweeps), "coarse_sweeps": list(sched.coarse_sweeps),
+                         "inner_cycles": sched.inner_cycles, "trials": len(sched.trials), "tuning_s": tune_s},
            "kernel_ms_by_kind": {"%s_%s" % k: v for k, v in sorted(by_kind.items(), key=lambda kv: -kv[1])},
            "kernel_us_per_launch": {"%s_%s_l%d" % (k, p_, lv): round(ms * 1e3 / cnt, 2)
                                     for k, p_, lv, cnt, ms in prof}}
@@ -455,7 +469,7 @@ def run_forest(G, args, world, flush, stream):
             times.append(e0.elapsed_time(e1))
             for i, u in enumerate(st["units"]):
                 off, cnt = F.tree_leaves(i)
-                munk_cyc += cnt * u["cycles"]
+                munk_cyc += cnt * u["cycles"] * (best.inner_cycles if prec == G.MIXED else 1)
             worst = max(worst, st["rel_l2"])
         total = allreduce_max(sum(times), world)
         ts = sorted(times)
@@ -477,6 +491,7 @@ def run_forest(G, args, world, flush, stream):
            "autotuned": {"block_n": N, "fine_sweeps": list(best.fine_sweeps),
                          "coarse_sweeps": list(best.coarse_sweeps), "cta_threads": best.cta_threads,
                          "coop_max_blocks": best.coop_max_blocks, "fused": best.fused,
+                         "inner_cycles": best.inner_cycles,
                          "tuning_s": tune_s, "trials": len(best.trials),
                          "sample": "8 problems of the same distribution (seed index 4), tiles 8 and 16"},
            "setup_s": setup_s, "mixed": res["mixed"], "fp64": res["fp64"], "roofline": roof,
@@ -550,6 +565,15 @@ def run_ours(args):
     assert torch.cuda.is_available(), "bench needs a CUDA device"
     torch.cuda.set_device(local)
     G.build()
+    if args.only:  # one secondary workload alone (profiling runs)
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        stream = torch.cuda.current_stream()
+        leg = {"needle": lambda: run_needle(G, args, world, flush, stream),
+               "forest": lambda: run_forest(G, args, world, flush, stream),
+               "serving": lambda: run_serving(G, args, world)}[args.only]()
+        if rank == 0:
+            print(json.dumps({"only": args.only, args.only: leg}))
+        return
     p = I.problem("c2")
     t_setup = time.perf_counter()
     t = build_tree(G, p)

@@ -304,6 +304,8 @@ int gmg_profile_read(gmg_tree *tree, int cap, int *kind, int *prec, int *level, 
                                   cells, 256 otherwise */
 #define GMG_OPT_COOP_MAX_BLOCKS 6 /* [160] levels with at most this many blocks (from the coarsest
                                      up to the last such level) join the cooperative launch */
+#define GMG_OPT_INNER_CYCLES 7   /* [1] FP32 V-cycles per defect-correction step of GMG_MIXED
+                                    (1 .. 8): more cycles per FP64 residual, fewer steps */
 int gmg_set_option(gmg_tree *tree, int option, long long value);
 
 /* Sweep schedule: N_down / N_up red-black sweeps on one level (default: the

@@ -7,6 +7,7 @@ fast a solve reaches its tolerance but not what it converges to:
 * the sweep schedule: N_down / N_up red-black sweeps on the fine levels
   (those launched one kernel per phase) and on the coarse levels (those in
   the cooperative launch), which trades cost per V-cycle against cycles,
+* the FP32 V-cycles per defect-correction step of the mixed path,
 * the CTA size of the block kernels, the block-count limit of the
   cooperative coarse launch and the fused FP32 sweeps.
 
@@ -37,10 +38,12 @@ class Schedule:
     cta_threads: int = 0               # 0: by block size
     coop_max_blocks: int = 160
     fused: bool = False
+    inner_cycles: int = 1              # FP32 V-cycles per defect-correction step (mixed)
     trials: list = field(default_factory=list, compare=False)
 
     def key(self):
-        return (self.fine_sweeps, self.coarse_sweeps, self.cta_threads, self.coop_max_blocks, self.fused)
+        return (self.fine_sweeps, self.coarse_sweeps, self.cta_threads, self.coop_max_blocks, self.fused,
+                self.inner_cycles)
 
 
 def coop_levels(tree, coop_max_blocks):
@@ -56,6 +59,7 @@ def apply(tree, s: Schedule):
     tree.set_option("cta_threads", s.cta_threads)
     tree.set_option("coop_max_blocks", s.coop_max_blocks)
     tree.set_option("fused_sweeps", 1 if s.fused else 0)
+    tree.set_option("inner_cycles", s.inner_cycles)
     split = coop_levels(tree, s.coop_max_blocks)
     for l in range(tree.lmin, tree.lmax + 1):
         nd, nu = s.coarse_sweeps if l <= split else s.fine_sweeps
@@ -80,9 +84,10 @@ def time_solve(tree, set_rhs, precision, tol, reps=2, max_cycles=80):
     return statistics.median(out), st
 
 
-def tune(tree, set_rhs, precision=MIXED, tol=1e-8, reps=2, log=None):
-    """Greedy search over the runtime knobs of a bound tree (or forest).
-    Returns the best Schedule (applied to the tree on return)."""
+def tune(tree, set_rhs, precision=MIXED, tol=1e-8, reps=2, log=None, axes=None):
+    """Greedy search over the runtime knobs of a bound tree (or forest)
+    (`axes`: names to search, default all).  Returns the best Schedule
+    (applied to the tree on return)."""
     best = Schedule()
     trials = []
 
@@ -95,14 +100,17 @@ def tune(tree, set_rhs, precision=MIXED, tol=1e-8, reps=2, log=None):
         return float("inf") if t is None else t
 
     best_t = score(best)
-    axes = [
+    space = [
         ("cta_threads", [64, 128, 256]),
         ("fine_sweeps", [(1, 1), (2, 1), (1, 2), (2, 2), (3, 3)]),
         ("coarse_sweeps", [(1, 1), (2, 2), (4, 4)]),
+        ("inner_cycles", [1, 2] if precision == MIXED else [1]),
         ("coop_max_blocks", [0, 64, 160, 640]),
         ("fused", [False, True]),
     ]
-    for name, values in axes:
+    for name, values in space:
+        if axes is not None and name not in axes:
+            continue
         for v in values:
             if getattr(best, name) == v:
                 continue
@@ -149,6 +157,7 @@ def load_cached(path, key):
     if v is None:
         return None
     v = dict(v)
+    v.setdefault("inner_cycles", 1)
     v["fine_sweeps"] = tuple(v["fine_sweeps"])
     v["coarse_sweeps"] = tuple(v["coarse_sweeps"])
     v["trials"] = []

@@ -432,7 +432,7 @@ void launch_fused(gmg_tree *t, cudaStream_t s, int l, int sweeps, long long in_p
 // fine levels with one launch per phase, the levels up to coop_split in
 // one cooperative launch.
 template <typename T, int D>
-int vcycle_impl(gmg_tree *t, cudaStream_t s) {
+int vcycle_impl(gmg_tree *t, cudaStream_t s, bool end_restrict) {
   GmgView<T> V = view<T>(t);
   const int P = prec_of<T>();
   const int ls = t->use_coop ? t->coop_split : t->lmin;
@@ -491,7 +491,7 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s) {
     });
     if (fused) launch_fused<T, D>(t, s, l, L.nu, L.off + other, L.off);  // back to the first buffer
   }
-  if (t->adaptive) {
+  if (t->adaptive && end_restrict) {
     for (int l = t->lmax; l >= 2 && l > t->lmin; l--) {
       LvArgs L = lv(t, l), Lp = lv(t, l - 1);
       with_nt<D>(L.n, [&](auto nt) {
@@ -506,8 +506,8 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s) {
 }
 
 template <typename T>
-int vcycle_any(gmg_tree *t, cudaStream_t s) {
-  return t->D == 3 ? vcycle_impl<T, 3>(t, s) : vcycle_impl<T, 2>(t, s);
+int vcycle_any(gmg_tree *t, cudaStream_t s, bool end_restrict = true) {
+  return t->D == 3 ? vcycle_impl<T, 3>(t, s, end_restrict) : vcycle_impl<T, 2>(t, s, end_restrict);
 }
 
 // Composite residual of the FP64 state over the leaf blocks: per-block
@@ -561,13 +561,17 @@ int restrict_all_phi64_any(gmg_tree *t, cudaStream_t s) {
   return t->D == 3 ? restrict_all_phi64<3>(t, s) : restrict_all_phi64<2>(t, s);
 }
 
-// one defect-correction step of the mixed path: e = 0, FP32 V-cycle on
-// A e = r, phi += e in FP64 (and covered cells restricted)
+// one defect-correction step of the mixed path: e = 0, inner_cycles FP32
+// V-cycles on A e = r, phi += e in FP64 (and covered cells restricted).  The
+// FP32 cycles skip their closing restriction into covered cells: only the
+// leaf values of e are used, and the next step starts again from e = 0.
 int mixed_step(gmg_tree *t, cudaStream_t s) {
   // e = 0 in the first FP32 phi buffer of every slot (frozen slots too: harmless)
   CUDA_TRY(cudaMemsetAsync(t->f_phi, 0, (size_t)t->nrhs * t->total_cells * sizeof(float), s));
-  int rc = vcycle_any<float>(t, s);
-  if (rc) return rc;
+  for (int k = 0; k < t->inner_cycles; k++) {
+    const int rc = vcycle_any<float>(t, s, k + 1 < t->inner_cycles);
+    if (rc) return rc;
+  }
   launch(t, s, 8, 0, t->lmax, [&] {
     k_leaf_accumulate<<<leaf_grid(t), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, t->f_phi, n_leaf_blocks(t),
                                                    t->leaf_ncell(), t->total_cells, t->nrhs, t->d_active, t->d_tree_of,
@@ -1238,6 +1242,10 @@ int gmg_set_option(gmg_tree *t, int option, long long value) {
       if (value < 0) return set_error("block limit must be >= 0"), GMG_ERR_INVALID_ARG;
       t->coop_max_blocks = (int)std::min<long long>(value, 1 << 30);
       if (t->bound) set_coop_split(t);
+      break;
+    case GMG_OPT_INNER_CYCLES:
+      if (value < 1 || value > 8) return set_error("inner cycles must be 1 .. 8"), GMG_ERR_INVALID_ARG;
+      t->inner_cycles = (int)value;
       break;
     case GMG_OPT_CTA_THREADS:
       if (value != 0 && value != 64 && value != 128 && value != 256)

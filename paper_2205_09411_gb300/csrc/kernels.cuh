@@ -172,18 +172,23 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // Tile of one block in shared memory: its cells plus one ghost layer.  Rows
 // along x are [.. ghost x=-1 | x = 0..n-1 | ghost x=n ..] with the first cell
 // at X0 = 16 / sizeof(T), so every row of cells starts on a 16-byte boundary
-// (16-byte cp.async); rows are R = n + 2 X0 long, y and z carry one ghost.
+// (16-byte cp.async); rows are R = n + 2 X0 (+ pad) long, y and z carry one
+// ghost.  FP32 rows of 8 cells get 4 more words, so that the 8 rows a warp
+// touches in a half-sweep (4 cells of one colour per row) fall on 32
+// different banks (row stride 20 words instead of 16).
 template <typename T, int D>
 struct TileGeo {
   int n, X0, R, sy, sz, size;
+  static __host__ __device__ int row(int n) {
+    return n + 2 * (16 / (int)sizeof(T)) + ((sizeof(T) == 4 && n == 8) ? 4 : 0);
+  }
   __host__ __device__ explicit TileGeo(int n_)
       : n(n_),
         X0(16 / (int)sizeof(T)),
-        R(n_ + 2 * (16 / (int)sizeof(T))),
-        sy(n_ + 2 * (16 / (int)sizeof(T))),
-        sz((n_ + 2 * (16 / (int)sizeof(T))) * (n_ + 2)),
-        size(D == 3 ? (n_ + 2 * (16 / (int)sizeof(T))) * (n_ + 2) * (n_ + 2)
-                    : (n_ + 2 * (16 / (int)sizeof(T))) * (n_ + 2)) {}
+        R(row(n_)),
+        sy(row(n_)),
+        sz(row(n_) * (n_ + 2)),
+        size(D == 3 ? row(n_) * (n_ + 2) * (n_ + 2) : row(n_) * (n_ + 2)) {}
   __host__ __device__ int idx(int x, int y, int z) const { return (x + X0) + sy * (y + 1) + (D == 3 ? sz * (z + 1) : 0); }
 };
 
@@ -255,9 +260,12 @@ __device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
   __syncthreads();
   const int fl = s_fl;
   const int nf = D == 3 ? n * n : n;
-  // face i: axis a, side; ghost cell (gx,gy,gz); source cell in the
-  // neighbour (sx,sy_,sz_) or, at a wall, the reflected cell of this block
-  for (int i = threadIdx.x; i < 2 * D * nf; i += blockDim.x) {
+  // face f = 2 axis + side: ghost cell (gx,gy,gz) from the cell (qx,qy,qz) of
+  // the same-level neighbour.  x faces cell by cell; the y and z faces are
+  // rows along x, copied in 16-byte chunks when a row is whole chunks.
+  constexpr bool kRows = NT != 0 && NT % VEC == 0;
+  const int nfx = kRows ? 2 * nf : 2 * D * nf;
+  for (int i = threadIdx.x; i < nfx; i += blockDim.x) {
     const int f = i / nf, j = i - f * nf;
     const int a = f >> 1, side = f & 1;
     const int id = s_nb[f];
@@ -270,8 +278,28 @@ __device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
     cp_async_elem(tile + G.idx(gx, gy, gz),
                   src + (long long)(id - L.first) * ncell + qx + n * (qy + (D == 3 ? n * qz : 0)));
   }
+  if (kRows) {
+    constexpr int cpr = kRows ? NT / VEC : 1;  // chunks per row
+    const int rows = D == 3 ? n : 1;           // rows per face
+    for (int i = threadIdx.x; i < (2 * D - 2) * rows * cpr; i += blockDim.x) {
+      const int f = 2 + i / (rows * cpr), rem = i - (f - 2) * rows * cpr;
+      const int row = rem / cpr, x0 = (rem - row * cpr) * VEC;
+      const int a = f >> 1, side = f & 1;
+      const int id = s_nb[f];
+      if ((fl & wall_bit(a, side)) || id < 0) continue;
+      const int gn = side ? n : -1, sn = side ? 0 : n - 1;
+      const int gy = a == 1 ? gn : row, gz = a == 2 ? gn : (D == 3 ? row : 0);
+      const int qy = a == 1 ? sn : row, qz = a == 2 ? sn : (D == 3 ? row : 0);
+      const T *src = (FAS && (fl & face_covered_bit(f))) ? V.old + L.off : V.phi + L.poff;
+      cp_async16(tile + G.idx(x0, gy, gz), src + (long long)(id - L.first) * ncell + x0 + n * (qy + (D == 3 ? n * qz : 0)));
+    }
+  }
   cp_async_wait_all();
   __syncthreads();
+  bool special = false;  // a wall or a refinement boundary on some face (same answer in every thread)
+#pragma unroll
+  for (int f = 0; f < 2 * D; f++) special = special || (fl & wall_bit(f >> 1, f & 1)) || s_nb[f] < 0;
+  if (!special) return;  // every ghost came from a same-level neighbour
   for (int i = threadIdx.x; i < 2 * D * nf; i += blockDim.x) {
     const int f = i / nf, j = i - f * nf;
     const int a = f >> 1, side = f & 1;

@@ -142,3 +142,24 @@ def test_autotuner_returns_a_converging_schedule():
     split = AT.coop_levels(F, s.coop_max_blocks)
     for l in range(F.lmin, F.lmax + 1):
         assert F.level_sweeps(l) == tuple(s.coarse_sweeps if l <= split else s.fine_sweeps)
+
+
+def test_inner_cycles_converge_with_fewer_steps():
+    """Two FP32 V-cycles per defect-correction step: the mixed solve still
+    meets 1e-8 by the oracle's own residual, in no more steps than with one."""
+    import paper_2205_09411_gb300 as G
+    p = problems()[3]
+    g = None
+    steps = []
+    for inner in (1, 2):
+        t = gpu_problem(p, rhs=False)
+        g = np.asarray(p["rhs"](t.leaf_centers()), dtype=np.float64)
+        t.set_option("inner_cycles", inner)
+        t.set_rhs(g)
+        st = t.solve(G.MIXED, 1e-8, 80)
+        steps.append(st["cycles"])
+        o = oracle_problem(p)
+        o.set_solution(t.solution())
+        l2, _, bn = o.residual()
+        assert st["rel_l2"] <= 1e-8 and l2 / bn <= 1.05e-8
+    assert steps[1] <= steps[0]
