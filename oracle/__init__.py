@@ -83,6 +83,7 @@ def lib():
                 "ot_get_solution": (None, [vp, dp]),
                 "ot_get_level": (None, [vp, C.c_int, C.c_int, dp]),
                 "ot_vcycle": (None, [vp, C.c_int]),
+                "ot_fmg": (None, [vp, C.c_int]),
                 "ot_residual": (C.c_double, [vp, dp, dp, dp]),
                 "ot_solve": (C.c_int, [vp, C.c_double, C.c_int, dp]),
                 "ot_line_search": (C.c_double, [FN, vp, C.c_int, dp, dp, C.c_double]),
@@ -296,6 +297,9 @@ class OracleTree:
 
     def vcycle(self, n=1):
         lib().ot_vcycle(self.h, n)
+
+    def fmg(self, n=1):
+        lib().ot_fmg(self.h, n)
 
     def residual(self, want_field=False):
         linf, bn = C.c_double(), C.c_double()

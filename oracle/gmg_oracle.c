@@ -46,6 +46,11 @@
  *  V   a V-cycle ends by restricting phi into covered cells, so that the
  *      composite operator sees covered values equal to the mean of their
  *      children (no effect on the iterates of a uniform tree).
+ *  FMG an FMG cycle carries residuals and FAS right-hand sides from the
+ *      finest level to the coarsest without smoothing, solves the coarsest
+ *      level, then for each finer level prolongs the coarse correction and
+ *      does one V-cycle with that level on top (which ends with reading V
+ *      up to that level).
  */
 #include "gmg_oracle.h"
 
@@ -1166,8 +1171,9 @@ static void restrict_all_phi(ot_tree *T) {
   for (int l = T->lmax; l >= 2; l--) restrict_level(T, l, 0);
 }
 
-static void vcycle_once(ot_tree *T) {
-  for (int l = T->lmax; l > T->lmin; l--) {
+/* one V-cycle on the levels lmin .. top (top = lmax: the solver's V-cycle) */
+static void vcycle_top(ot_tree *T, int top) {
+  for (int l = top; l > T->lmin; l--) {
     for (int s = 0; s < T->n_down; s++) {
       gsrb(T, l, 0);
       gsrb(T, l, 1);
@@ -1177,14 +1183,37 @@ static void vcycle_once(ot_tree *T) {
     fas_rhs(T, l - 1);
   }
   coarse_solve(T);
-  for (int l = T->lmin + 1; l <= T->lmax; l++) {
+  for (int l = T->lmin + 1; l <= top; l++) {
     prolong(T, l);
     for (int s = 0; s < T->n_up; s++) {
       gsrb(T, l, 0);
       gsrb(T, l, 1);
     }
   }
-  restrict_all_phi(T);
+  for (int l = top; l >= 2; l--) restrict_level(T, l, 0); /* reading V */
+}
+
+static void vcycle_once(ot_tree *T) { vcycle_top(T, T->lmax); }
+
+/* FMG cycle (Sec. 2.2 "Multigrid cycle": V-cycles from the coarsest grid
+   up to the finest), in FAS form (reading FMG): residuals and FAS right-hand
+   sides are carried from the finest level down to the coarsest without
+   smoothing, the coarsest level is solved, and then for each finer level in
+   turn the coarse correction is prolonged to it and one V-cycle is done
+   with that level on top. */
+void ot_fmg(ot_tree *T, int n) {
+  for (int it = 0; it < n; it++) {
+    for (int l = T->lmax; l > T->lmin; l--) {
+      residual_level(T, l);
+      restrict_level(T, l, 1);
+      fas_rhs(T, l - 1);
+    }
+    coarse_solve(T);
+    for (int l = T->lmin + 1; l <= T->lmax; l++) {
+      prolong(T, l);
+      vcycle_top(T, l);
+    }
+  }
 }
 
 void ot_vcycle(ot_tree *T, int n) {

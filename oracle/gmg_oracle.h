@@ -100,6 +100,11 @@ void ot_set_solution(ot_tree *T, const double *phi);
 void ot_get_solution(const ot_tree *T, double *phi);
 void ot_get_level(const ot_tree *T, int level, int which /*0 phi,1 b*/, double *out);
 void ot_vcycle(ot_tree *T, int n);
+/* n FMG cycles (Sec. 2.2 "Multigrid cycle"; reading FMG).  Pin: after two
+ * cycles from phi = 0 the error against the analytic sphere solution is
+ * that of the converged discrete solution (Sec. 4.1: the discretisation
+ * error dominates after two FMG iterations). */
+void ot_fmg(ot_tree *T, int n);
 /* composite residual over leaf cells: returns ||r||_2; linf, bnorm optional */
 double ot_residual(ot_tree *T, double *linf, double *bnorm, double *r_out);
 int ot_solve(ot_tree *T, double rel_tol, int max_cycles, double *hist);

@@ -57,7 +57,7 @@ def build(force=False, verbose=False):
         if p.wait() != 0:
             raise RuntimeError("compile failed: " + " ".join(cmd))
     tmp = LIB + ".%d.tmp" % os.getpid()
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
+    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lpthread"]
     if verbose:
         print(" ".join(cmd), flush=True)
     subprocess.run(cmd, check=True)

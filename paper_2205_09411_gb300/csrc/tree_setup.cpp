@@ -4,9 +4,12 @@
 // of the coarsest-level operator (Sec. 3.5).  Compiled with
 // -ffp-contract=off: the level-set arithmetic is plain IEEE.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <thread>
 #include <unordered_map>
 
 #include "gmg_internal.h"
@@ -403,17 +406,25 @@ int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, do
   T->bterm_h.clear();
   T->dist_h.clear();
   T->mask_h.clear();
-  std::vector<double> dd, st, bt;
-  for (int id = 0; id < nb; id++) {
+  // Per-block work (mask, line searches, stencils, boundary terms) runs in
+  // parallel threads when no host callback is involved (callbacks may not be
+  // thread-safe); the results are then concatenated in block order, so the
+  // stores are the same whatever the thread count.
+  struct BlockOut {
+    std::vector<uint8_t> mask;
+    std::vector<double> dd, st, bt;
+    bool cut = false, anybt = false;
+  };
+  std::vector<BlockOut> outs(nb);
+  auto process = [&](int id, BlockOut &o) {
     const HostBlock &B = T->blocks[id];
     const LevelInfo &L = T->lev(B.level);
     const int n = L.n, nc = L.ncell;
     const double h = L.h;
     const double Lmask = T->prm.mask_factor * std::sqrt((double)D) * h;
-    dd.assign((size_t)nc * 2 * D, 1.0);
-    T->mask_base_h[id] = (long long)T->mask_h.size();
-    T->mask_h.resize(T->mask_h.size() + nc, 0);
-    uint8_t *mask = &T->mask_h[T->mask_base_h[id]];
+    std::vector<double> dd((size_t)nc * 2 * D, 1.0), st, bt;
+    o.mask.assign(nc, 0);
+    uint8_t *mask = o.mask.data();
     bool cut = false;
     for (int c = 0; c < nc; c++) {
       int p[3] = {c % n, (c / n) % n, D == 3 ? c / (n * n) : 0};
@@ -501,23 +512,50 @@ int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, do
         }
       bt[c] = t;
     }
+    o.cut = cut;
     if (cut) {
+      o.st = std::move(st);
+      o.dd = std::move(dd);
+    }
+    for (int c = 0; c < nc; c++) o.anybt = o.anybt || bt[c] != 0.0;
+    if (o.anybt) o.bt = std::move(bt);
+  };
+  const bool callbacks = lsf->kind == GMG_LSF_CALLBACK || phib || T->wall_fn;
+  int nthreads = callbacks ? 1 : (int)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 64u);
+  if (const char *e = std::getenv("GMG_SETUP_THREADS")) nthreads = std::max(1, std::atoi(e));
+  if (nthreads <= 1 || nb < 64) {
+    for (int id = 0; id < nb; id++) process(id, outs[id]);
+  } else {
+    std::atomic<int> next{0};
+    std::vector<std::thread> pool;
+    for (int w = 0; w < nthreads; w++)
+      pool.emplace_back([&] {
+        for (int id; (id = next.fetch_add(16)) < nb;)
+          for (int k = id; k < std::min(nb, id + 16); k++) process(k, outs[k]);
+      });
+    for (auto &th : pool) th.join();
+  }
+  for (int id = 0; id < nb; id++) {
+    BlockOut &o = outs[id];
+    const int nc = (int)o.mask.size();
+    T->mask_base_h[id] = (long long)T->mask_h.size();
+    T->mask_h.insert(T->mask_h.end(), o.mask.begin(), o.mask.end());
+    if (o.cut) {
       T->st_base_h[id] = (long long)T->stencil_h.size();
-      T->stencil_h.insert(T->stencil_h.end(), st.begin(), st.end());
+      T->stencil_h.insert(T->stencil_h.end(), o.st.begin(), o.st.end());
       for (int c = 0; c < nc; c++) {  // cells whose stencil differs from the regular one
         bool special = false;
-        for (int k = 0; k < 2 * D; k++) special = special || dd[(size_t)c * 2 * D + k] < 1.0;
+        for (int k = 0; k < 2 * D; k++) special = special || o.dd[(size_t)c * 2 * D + k] < 1.0;
         T->spec_h.push_back(special ? 1 : 0);
       }
       T->dist_base_h[id] = (long long)T->dist_h.size();
-      T->dist_h.insert(T->dist_h.end(), dd.begin(), dd.end());
+      T->dist_h.insert(T->dist_h.end(), o.dd.begin(), o.dd.end());
     }
-    bool any = false;
-    for (int c = 0; c < nc; c++) any = any || bt[c] != 0.0;
-    if (any) {
+    if (o.anybt) {
       T->bt_base_h[id] = (long long)T->bterm_h.size();
-      T->bterm_h.insert(T->bterm_h.end(), bt.begin(), bt.end());
+      T->bterm_h.insert(T->bterm_h.end(), o.bt.begin(), o.bt.end());
     }
+    o = BlockOut();  // release the block's buffers
   }
   // coarsest level: explicit inverse of its operator (homogeneous walls)
   const LevelInfo &Lc = T->lev(T->lmin);

@@ -499,3 +499,30 @@ def test_unresolved_root_correction_places_virtual_boundary():
         assert np.all(others == 1.0)
         n_checked += 1
     assert n_checked >= 1
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fmg_reduction_per_cycle_in_the_printed_range(dim):
+    """Sec. 4.1 prints a residual reduction of about 40-80 (2D) and 30-40
+    (3D) per FMG iteration on the sphere test.  From phi = 0, FMG cycles 2-4
+    reduce the residual by factors within half to twice that range, and FMG
+    cycles converge to the same discrete solution as V-cycles (a broken FMG
+    - no coarse right-hand side, no prolongation, no V-cycle on the way up -
+    fails one of these)."""
+    p = I.problem("sphere2d" if dim == 2 else "sphere3d")
+    q = I.scaled(p, 5 if dim == 2 else 4)
+    lo, hi = (40, 80) if dim == 2 else (30, 40)
+    t = oracle_problem(q)
+    res = []
+    for k in range(4):
+        t.fmg(1)
+        l2, _, bn = t.residual()
+        res.append(l2 / bn)
+    factors = np.array(res[:-1]) / np.array(res[1:])
+    assert np.all(factors > lo / 2) and np.all(factors < hi * 2), factors
+    t.fmg(4)
+    ref, _ = _solve_error(p, q["max_level"], tol=1e-13)
+    a, b = t.solution(), ref.solution()
+    assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max()
+    t.close()
+    ref.close()
