@@ -25,7 +25,8 @@ all 32 to 1e-8 in one tree (mixed and FP64), with its own roofline, and
 ellipsoids) solved together, after the autotuner has picked the block tile
 and sweep schedule on a sample forest, and `serving` the continuous-batching
 request loop over seven resident sessions (p50/p99 latency and solves/s,
-mixed and FP64).
+mixed and FP64), and `paper_table1` the seconds per FMG cycle on the
+paper's Table 1 grid (512^3 sphere, 8^3 and 16^3 blocks), FP64.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank solves its own replica (replicas only: the method
@@ -63,7 +64,8 @@ def parse():
     ap.add_argument("--skip-needle", action="store_true", help="leave out the batched needle workload")
     ap.add_argument("--skip-forest", action="store_true", help="leave out the batched uneven-tree workload")
     ap.add_argument("--skip-serving", action="store_true", help="leave out the serving-loop workload")
-    ap.add_argument("--only", choices=["needle", "forest", "serving"], default=None,
+    ap.add_argument("--skip-table1", action="store_true", help="leave out the 512^3 FMG timing of the paper's Table 1")
+    ap.add_argument("--only", choices=["needle", "forest", "serving", "table1"], default=None,
                     help="run one secondary workload alone (no headline line; for profiling)")
     ap.add_argument("--needle-rhs", type=int, default=32, help="right-hand sides of the batched needle workload")
     return ap.parse_args()
@@ -558,6 +560,51 @@ def run_serving(G, args, world):
     return out
 
 
+PAPER_TABLE1_S_PER_FMG = {8: {4: 5.55, 8: 2.77, 16: 1.62, 32: 1.46}, 16: {4: 2.97, 8: 1.53, 16: 1.01, 32: 0.95},
+                          32: {4: 2.36, 8: 1.31, 16: 0.87, 32: 0.84}}
+
+
+def run_table1(G, args, world, stream):
+    """The timing workload of the paper's Table 1: the Sec. 4.1 sphere
+    geometry (domain [-1/2, 1/2]^3, sphere R = 1/4) on a uniform 512^3 grid
+    (134,217,728 cells), seconds per FMG cycle in FP64, with 8^3 and 16^3
+    blocks.  Boundary values here: phi = 1 on the sphere, 0 on the walls
+    (the timing does not depend on them).  The paper's times (Fortran/OpenMP
+    on an AMD EPYC 7H12, 4-32 cores) are quoted beside it as context."""
+    import torch
+    out = {"workload": "sphere3d_512^3_uniform_fmg_fp64", "cells": 512 ** 3, "blocks": {}}
+    for N in (8, 16):
+        ml = int(round(np.log2(512 / N))) + 1
+        p = I.problem("sphere3d", N=N, h1=1.0 / N, max_level=ml, wall_fn=None, wall_values=(0.0,) * 6, phib=1.0)
+        t0 = time.perf_counter()
+        t = host_tree(G, p)
+        t.bind()
+        setup = time.perf_counter() - t0
+        t.set_rhs(torch.zeros(t.n_leaf_cells, dtype=torch.float64, device="cuda"))
+        t.fmg(1)  # warm-up and graph capture
+        t.set_rhs(torch.zeros(t.n_leaf_cells, dtype=torch.float64, device="cuda"))
+        r0, _ = t.residual()
+        k = max(2, min(args.steps, 4))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        t.fmg(k)
+        e1.record(stream)
+        e1.synchronize()
+        per = e0.elapsed_time(e1) / k * 1e-3
+        r1, _ = t.residual()
+        out["blocks"]["%d^3" % N] = {"s_per_fmg_cycle": per, "munk_fmg_per_s": 512 ** 3 / per / 1e6,
+                                     "levels": [t.lmin, t.lmax], "fmg_cycles_timed": k,
+                                     "rel_residual_after": r1, "reduction_per_cycle": (r0 / r1) ** (1.0 / k),
+                                     "setup_s": setup,
+                                     "paper_s_per_fmg_cycle_by_cores": PAPER_TABLE1_S_PER_FMG.get(N)}
+        t.close()
+        torch.cuda.empty_cache()
+    out["paper_best_s_per_fmg_cycle"] = 0.84
+    out["paper_hardware"] = "AMD EPYC 7H12, 32 cores, 32^3 blocks (Table 1)"
+    return out
+
+
 def run_ours(args):
     import torch
     import paper_2205_09411_gb300 as G
@@ -570,7 +617,8 @@ def run_ours(args):
         stream = torch.cuda.current_stream()
         leg = {"needle": lambda: run_needle(G, args, world, flush, stream),
                "forest": lambda: run_forest(G, args, world, flush, stream),
-               "serving": lambda: run_serving(G, args, world)}[args.only]()
+               "serving": lambda: run_serving(G, args, world),
+               "table1": lambda: run_table1(G, args, world, stream)}[args.only]()
         if rank == 0:
             print(json.dumps({"only": args.only, args.only: leg}))
         return
@@ -675,6 +723,8 @@ def run_ours(args):
         result["batched_forest"] = run_forest(G, args, world, flush, stream)
     if not args.skip_serving:
         result["serving"] = run_serving(G, args, world)
+    if not args.skip_table1:
+        result["paper_table1"] = run_table1(G, args, world, stream)
     if rank == 0 and world == 1:
         result["cpu_baseline"] = cpu_baseline(p)
     if rank == 0:

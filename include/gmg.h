@@ -214,6 +214,13 @@ int gmg_get_solution_slots(gmg_tree *tree, int slot0, int nslots, double *phi, i
  * A phi + R r, exact coarse solve, (bi/tri)linear prolongation of the
  * correction, N_up sweeps). */
 int gmg_vcycle(gmg_tree *tree, int n_cycles, void *stream);
+/* n_cycles FMG cycles in FP64 on every slot (Sec. 2.2 "Multigrid cycle":
+ * V-cycles from the coarsest grid up to the finest).  FAS form: residuals
+ * and FAS right-hand sides are carried from the finest level to the
+ * coarsest without smoothing, the coarsest level is solved exactly, then
+ * for each finer level the coarse correction is prolonged to it and one
+ * V-cycle (N_down / N_up sweeps) is done with that level on top. */
+int gmg_fmg(gmg_tree *tree, int n_cycles, void *stream);
 /* Composite residual ||b - A phi||_2 over leaf cells, relative to ||b||_2,
  * and max |b - A phi|, per unit (host arrays of nrhs * n_trees doubles, or
  * NULL).  Synchronises the stream. */

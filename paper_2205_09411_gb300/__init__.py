@@ -100,6 +100,7 @@ def load():
         "gmg_set_solution": (C.c_int, [vp, vp, C.c_int, vp]),
         "gmg_get_solution": (C.c_int, [vp, vp, C.c_int, vp]),
         "gmg_vcycle": (C.c_int, [vp, C.c_int, vp]),
+        "gmg_fmg": (C.c_int, [vp, C.c_int, vp]),
         "gmg_residual": (C.c_int, [vp, dp, dp, vp]),
         "gmg_solve": (C.c_int, [vp, C.c_int, C.c_double, C.c_int, C.POINTER(Stats), vp]),
         "gmg_get_level": (C.c_int, [vp, C.c_int, C.c_int, dp, vp]),
@@ -373,6 +374,10 @@ class Tree:
 
     def vcycle(self, n=1, stream=None):
         _check(load().gmg_vcycle(self.h, n, _stream_ptr(stream)))
+
+    def fmg(self, n=1, stream=None):
+        """n FMG cycles in FP64 (Sec. 2.2)."""
+        _check(load().gmg_fmg(self.h, n, _stream_ptr(stream)))
 
     def residual(self, stream=None):
         """(relative L2, max) of the composite residual: floats for one unit, else

@@ -428,17 +428,18 @@ void launch_fused(gmg_tree *t, cudaStream_t s, int l, int sweeps, long long in_p
   });
 }
 
-// One FAS V-cycle on fields of type T (Sec. 2.2; readings UP and V): the
-// fine levels with one launch per phase, the levels up to coop_split in
-// one cooperative launch.
+// One FAS V-cycle on fields of type T (Sec. 2.2; readings UP and V) on the
+// levels lmin .. top (top < lmax inside an FMG cycle): the fine levels with
+// one launch per phase, the levels up to coop_split in one cooperative
+// launch.
 template <typename T, int D>
-int vcycle_impl(gmg_tree *t, cudaStream_t s, bool end_restrict) {
+int vcycle_impl(gmg_tree *t, cudaStream_t s, bool end_restrict, int top) {
   GmgView<T> V = view<T>(t);
   const int P = prec_of<T>();
-  const int ls = t->use_coop ? t->coop_split : t->lmin;
+  const int ls = std::min(t->use_coop ? t->coop_split : t->lmin, top);
   const long long other = (long long)t->nrhs * t->total_cells;  // offset of the second FP32 phi buffer
   const int R = t->nrhs;
-  for (int l = t->lmax; l > ls; l--) {
+  for (int l = top; l > ls; l--) {
     LvArgs L = lv(t, l), Lp = lv(t, l - 1);
     const size_t sm = tile_bytes<T>(t, l);
     const int nt_l = cta_threads(t, l), nt_p = cta_threads(t, l - 1);
@@ -473,7 +474,7 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s, bool end_restrict) {
                                                                                               t->ncr, t->nroot);
     });
   }
-  for (int l = ls + 1; l <= t->lmax; l++) {
+  for (int l = ls + 1; l <= top; l++) {
     LvArgs L = lv(t, l), Lp = lv(t, l - 1);
     const int hm = L.n / 2 + 2;
     const size_t psm = sizeof(T) * (size_t)(D == 3 ? hm * hm * hm : hm * hm);
@@ -492,7 +493,7 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s, bool end_restrict) {
     if (fused) launch_fused<T, D>(t, s, l, L.nu, L.off + other, L.off);  // back to the first buffer
   }
   if (t->adaptive && end_restrict) {
-    for (int l = t->lmax; l >= 2 && l > t->lmin; l--) {
+    for (int l = top; l >= 2 && l > t->lmin; l--) {
       LvArgs L = lv(t, l), Lp = lv(t, l - 1);
       with_nt<D>(L.n, [&](auto nt) {
         constexpr int NT = decltype(nt)::value;
@@ -507,7 +508,58 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s, bool end_restrict) {
 
 template <typename T>
 int vcycle_any(gmg_tree *t, cudaStream_t s, bool end_restrict = true) {
-  return t->D == 3 ? vcycle_impl<T, 3>(t, s, end_restrict) : vcycle_impl<T, 2>(t, s, end_restrict);
+  return t->D == 3 ? vcycle_impl<T, 3>(t, s, end_restrict, t->lmax) : vcycle_impl<T, 2>(t, s, end_restrict, t->lmax);
+}
+
+// One FMG cycle (Sec. 2.2 "Multigrid cycle"; reading FMG): residuals and FAS
+// right-hand sides from the finest level to the coarsest without smoothing,
+// the exact coarsest-level solve, then for each finer level the prolonged
+// coarse correction and one V-cycle with that level on top.
+template <typename T, int D>
+int fmg_impl(gmg_tree *t, cudaStream_t s) {
+  GmgView<T> V = view<T>(t);
+  const int P = prec_of<T>();
+  const int R = t->nrhs;
+  for (int l = t->lmax; l > t->lmin; l--) {
+    const LvArgs L = lv(t, l), Lp = lv(t, l - 1);
+    const LvArgs Lpp = l - 2 >= t->lmin ? lv(t, l - 2) : Lp;
+    const size_t sm = tile_bytes<T>(t, l), smp = tile_bytes<T>(t, l - 1);
+    const int nt_l = cta_threads(t, l), nt_p = cta_threads(t, l - 1);
+    with_nt<D>(L.n, [&](auto nt) {
+      constexpr int NT = decltype(nt)::value;
+      launch(t, s, 1, P, l, [&] { k_resid_restrict<T, D, NT><<<L.count * R, nt_l, sm, s>>>(V, L, Lp); });
+    });
+    with_nt<D>(Lp.n, [&](auto nt) {
+      constexpr int NT = decltype(nt)::value;
+      launch(t, s, 2, P, l - 1, [&] { k_fas<T, D, NT><<<Lp.count * R, nt_p, smp, s>>>(V, Lp, Lpp); });
+    });
+  }
+  {
+    const LvArgs Lc = lv(t, t->lmin);
+    const long long rows = (long long)t->nc * R;
+    launch(t, s, 3, P, t->lmin, [&] {
+      k_coarse<T><<<(unsigned)((rows + kThreads / 32 - 1) / (kThreads / 32)), kThreads, 0, s>>>(V, Lc, t->d_cinv,
+                                                                                              t->ncr, t->nroot);
+    });
+  }
+  for (int l = t->lmin + 1; l <= t->lmax; l++) {
+    const LvArgs L = lv(t, l), Lp = lv(t, l - 1);
+    const int hm = L.n / 2 + 2;
+    const size_t psm = sizeof(T) * (size_t)(D == 3 ? hm * hm * hm : hm * hm);
+    with_nt<D>(L.n, [&](auto nt) {
+      constexpr int NT = decltype(nt)::value;
+      launch(t, s, 4, P, l, [&] { k_prolong<T, D, NT><<<L.count * R, kThreads, psm, s>>>(V, L, Lp); });
+    });
+    const int rc = vcycle_impl<T, D>(t, s, true, l);
+    if (rc) return rc;
+  }
+  CUDA_TRY(cudaGetLastError());
+  return GMG_OK;
+}
+
+template <typename T>
+int fmg_any(gmg_tree *t, cudaStream_t s) {
+  return t->D == 3 ? fmg_impl<T, 3>(t, s) : fmg_impl<T, 2>(t, s);
 }
 
 // Composite residual of the FP64 state over the leaf blocks: per-block
@@ -1109,6 +1161,20 @@ int gmg_vcycle(gmg_tree *t, int n_cycles, void *stream) {
   if (rc) return rc;
   for (int k = 0; k < n_cycles; k++) {
     rc = run_graph(t, gmg_tree::kGraphVcycle64, s, [&](cudaStream_t cs) { return vcycle_any<double>(t, cs); });
+    if (rc) return rc;
+  }
+  return GMG_OK;
+}
+
+int gmg_fmg(gmg_tree *t, int n_cycles, void *stream) {
+  if (!t || n_cycles < 0) return set_error("bad arguments"), GMG_ERR_INVALID_ARG;
+  if (!t->bound) return set_error("tree not bound"), GMG_ERR_STATE;
+  t->launches = 0;
+  cudaStream_t s = as_stream(stream);
+  int rc = upload_mask(t, nullptr, s);
+  if (rc) return rc;
+  for (int k = 0; k < n_cycles; k++) {
+    rc = run_graph(t, gmg_tree::kGraphFmg64, s, [&](cudaStream_t cs) { return fmg_any<double>(t, cs); });
     if (rc) return rc;
   }
   return GMG_OK;

@@ -161,7 +161,7 @@ struct gmg_tree {
     cudaGraphExec_t exec = nullptr;
     long long kernels = 0;
   };
-  enum { kGraphResid64 = 0, kGraphResidMixed, kGraphCycle64, kGraphCycleMixed, kGraphVcycle64, kGraphSlots };
+  enum { kGraphResid64 = 0, kGraphResidMixed, kGraphCycle64, kGraphCycleMixed, kGraphVcycle64, kGraphFmg64, kGraphSlots };
   GraphSlot graphs[kGraphSlots];
   bool use_graphs = true;
   bool use_coop = true;       // coarse levels in one cooperative launch

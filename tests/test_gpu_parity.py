@@ -203,3 +203,30 @@ def test_cta_sizes_give_identical_results(name):
         out.append((a, t.solution().copy(), st["cycles"]))
     for a, b, c in out[1:]:
         assert np.array_equal(a, out[0][0]) and np.array_equal(b, out[0][1]) and c == out[0][2]
+
+
+@pytest.mark.parametrize("name", ["c1", "c2_32", "adaptive2d", "adaptive3d", "needle4", "ragged3d"])
+def test_fmg_iterates_match_oracle(name):
+    """FMG cycles (Sec. 2.2) through the C ABI give the oracle's FMG iterates
+    to 1e-12 after each of three cycles."""
+    p = parity_cases()[name]
+    o = oracle_problem(p)
+    t = gpu_problem(p)
+    for k in range(3):
+        o.fmg(1)
+        t.fmg(1)
+        ref = o.solution()
+        err = np.abs(t.solution() - ref).max() / max(np.abs(ref).max(), 1e-300)
+        assert err <= TOL_ITERATE, "FMG cycle %d: relative max difference %.3e" % (k + 1, err)
+
+
+def test_fmg_without_graphs_or_cooperative_launch():
+    p = parity_cases()["adaptive3d"]
+    o = oracle_problem(p)
+    t = gpu_problem(p)
+    t.set_option("graphs", 0)
+    t.set_option("coarse_coop", 0)
+    o.fmg(2)
+    t.fmg(2)
+    ref = o.solution()
+    assert np.abs(t.solution() - ref).max() <= TOL_ITERATE * np.abs(ref).max()
