@@ -84,6 +84,7 @@ def lib():
                 "ot_get_level": (None, [vp, C.c_int, C.c_int, dp]),
                 "ot_vcycle": (None, [vp, C.c_int]),
                 "ot_fmg": (None, [vp, C.c_int]),
+                "ot_efield": (None, [vp, dp]),
                 "ot_residual": (C.c_double, [vp, dp, dp, dp]),
                 "ot_solve": (C.c_int, [vp, C.c_double, C.c_int, dp]),
                 "ot_line_search": (C.c_double, [FN, vp, C.c_int, dp, dp, C.c_double]),
@@ -300,6 +301,11 @@ class OracleTree:
 
     def fmg(self, n=1):
         lib().ot_fmg(self.h, n)
+
+    def efield(self):
+        out = np.zeros((self.num_leaf_cells(), self.dim))
+        lib().ot_efield(self.h, out.ctypes.data_as(C.POINTER(C.c_double)))
+        return out
 
     def residual(self, want_field=False):
         linf, bn = C.c_double(), C.c_double()

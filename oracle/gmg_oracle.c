@@ -93,6 +93,10 @@ struct ot_tree {
   void *wall_user;
   ot_lsf lsf;
   int have_lsf;
+  /* boundary value on the object (gmg_store_stencils' phi_b) */
+  ot_fn phib_fn;
+  void *phib_user;
+  double phib_const;
   /* coarse level LU factors */
   int nc;
   double *lu;
@@ -649,6 +653,9 @@ static void build_coarse_matrix(ot_tree *T);
 
 int ot_store_stencils(ot_tree *T, ot_fn phib_fn, void *user, double phib_const) {
   int D = T->D;
+  T->phib_fn = phib_fn;
+  T->phib_user = user;
+  T->phib_const = phib_const;
   lsf_ctx ctx = {&T->lsf, D};
   for (int l = T->lmin; l <= T->lmax; l++) {
     double h = lvl_h(T, l);
@@ -1218,6 +1225,57 @@ void ot_fmg(ot_tree *T, int n) {
 
 void ot_vcycle(ot_tree *T, int n) {
   for (int i = 0; i < n; i++) vcycle_once(T);
+}
+
+/* E = -grad(phi) on the upper face of every leaf cell (Sec. 4.4: gradients
+ * on a staggered grid that take the stored boundary distances into
+ * account): (phi_b - phi)/(d dx) across the object's boundary, 2 (phi_w -
+ * phi)/dx at a Dirichlet domain wall, 0 at a Neumann wall, the difference
+ * to the neighbour's (ghost) value otherwise; 0 in cells whose centre lies
+ * inside the object.  out: leaf cells x D.  Pin: exact (-a) for a linear
+ * phi = a.x + c with matching boundary and wall values. */
+void ot_efield(ot_tree *T, double *out) {
+  int D = T->D;
+  for (int l = T->lmin; l <= T->lmax; l++) fill_ghosts(T, l, F_PHI, 0);
+  int64_t k = 0;
+  FOR_LEAF_BLOCKS(T, l, i, B) {
+    int n = B->n, e[3];
+    double h = lvl_h(T, l);
+    lvl_cext(T, l, e);
+    FOR_CELLS(T, n, p) {
+      int c = cidx(n, p);
+      double a[3], phi = B->phi[c];
+      cell_center(T, B, p, a);
+      int inside = T->have_lsf && ot_lsf_eval(&T->lsf, D, a) < 0.0;
+      for (int ax = 0; ax < D; ax++) {
+        double g, d = (B->cut && B->dd) ? B->dd[(size_t)c * 2 * D + 2 * ax + 1] : 1.0;
+        int G[3];
+        for (int q = 0; q < 3; q++) G[q] = q < D ? B->ix[q] * n + p[q] : 0;
+        G[ax] += 1;
+        if (inside) {
+          g = 0.0;
+        } else if (d < 1.0) {
+          double x0[3] = {a[0], a[1], a[2]};
+          x0[ax] = a[ax] + d * h;
+          g = (phib_at(T->phib_fn, T->phib_user, T->phib_const, x0) - phi) / (d * h);
+        } else if (G[ax] >= e[ax]) {
+          if (T->wall_type[2 * ax + 1] == OT_WALL_DIRICHLET) {
+            double xf[3] = {a[0], a[1], a[2]};
+            xf[ax] = a[ax] + 0.5 * h;
+            g = 2.0 * (wall_value_at(T, 2 * ax + 1, xf) - phi) / h;
+          } else {
+            g = 0.0;
+          }
+        } else {
+          int q[3] = {p[0], p[1], p[2]};
+          q[ax] += 1;
+          g = (B->gh[gidx(T, n, q)] - phi) / h;
+        }
+        out[k * D + ax] = -g;
+      }
+      k++;
+    }
+  }
 }
 
 void ot_set_rhs(ot_tree *T, const double *g) {

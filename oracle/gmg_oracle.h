@@ -105,6 +105,9 @@ void ot_vcycle(ot_tree *T, int n);
  * that of the converged discrete solution (Sec. 4.1: the discretisation
  * error dominates after two FMG iterations). */
 void ot_fmg(ot_tree *T, int n);
+/* E = -grad(phi) on the upper face of every leaf cell (Sec. 4.4), leaf
+ * cells x D.  Pin: -a exactly for phi = a.x + c. */
+void ot_efield(ot_tree *T, double *out);
 /* composite residual over leaf cells: returns ||r||_2; linf, bnorm optional */
 double ot_residual(ot_tree *T, double *linf, double *bnorm, double *r_out);
 int ot_solve(ot_tree *T, double rel_tol, int max_cycles, double *hist);

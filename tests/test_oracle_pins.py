@@ -526,3 +526,34 @@ def test_fmg_reduction_per_cycle_in_the_printed_range(dim):
     assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max()
     t.close()
     ref.close()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_efield_exact_for_linear_phi(dim):
+    """Sec. 4.4: the face gradients use the boundary distance next to the
+    object.  For phi = a.x + c with phi_b and Dirichlet wall values taken
+    from the same linear function, every face value - regular, across the
+    object's boundary, at refinement boundaries (reading G) and at the walls
+    - is exactly -a; cells inside the object get 0.  (The refinement region
+    stays away from the walls: a refinement ghost whose tangential slope
+    reaches a Dirichlet wall uses the operator's homogeneous reflection.)"""
+    from _helpers import refine_near
+    N, h1 = 8, 1 / 16
+    c, R = (0.47, 0.52, 0.5)[:dim], 0.13
+    a = np.array([0.7, -1.3, 0.4][:dim])
+    lin = lambda x: float(np.dot(a, np.asarray(x)[:dim]) + 0.25)
+    p = dict(dim=dim, N=N, cb=(2, 2, 2 if dim == 3 else 1), lo=(0.0, 0.0, 0.0), h1=h1, max_level=3,
+             refine=refine_near([0.5, 0.5, 0.5][:dim], 0.16, N, h1, dim),
+             lsf=("sphere", tuple(c) + (0.0,) * (3 - dim) + (R,)), walls=(0,) * (2 * dim), wall_values=None,
+             wall_fn=lin, phib=lin, rhs=lambda xc: np.zeros(len(xc)), index=40)
+    t = oracle_problem(p, rhs=False)
+    levels = set(t.leaf_levels())
+    assert len(levels) > 1  # refinement boundaries present
+    xc = t.leaf_centers()
+    t.set_solution(xc @ a + 0.25)
+    E = t.efield()
+    inside = np.sqrt(np.sum((xc - np.array(c)) ** 2, 1)) < R
+    assert inside.any() and (~inside).any()
+    assert np.abs(E[inside]).max() == 0.0
+    err = np.abs(E[~inside] + a).max()
+    assert err < 1e-9, err
