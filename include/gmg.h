@@ -272,6 +272,19 @@ int gmg_iterate(gmg_tree *tree, int precision, const int *active, int residual_o
 int gmg_iterate_begin(gmg_tree *tree, int precision, const int *active, int residual_only, void *stream);
 int gmg_iterate_end(gmg_tree *tree, double *rel_l2, double *linf);
 
+/* Field E = -grad(phi) on the upper faces of every leaf cell (Sec. 4.4: the
+ * components of grad(phi) on a staggered grid, taking the stored boundary
+ * distances into account): for axis k of leaf cell i, the face i + 1/2 e_k.
+ * Where the irregular boundary lies between i and its +k neighbour at
+ * relative distance d < 1 the gradient is (phi_b - phi_i) / (d dx); at a
+ * Dirichlet domain wall 2 (phi_w - phi_i) / dx, at a Neumann wall 0;
+ * elsewhere (phi_neighbour - phi_i) / dx with the operator's ghost value
+ * (same-level neighbour or refinement-boundary ghost).  Cells whose centre
+ * lies inside the object get E = 0.  out: nrhs x n_leaf_cells x dim
+ * doubles (leaf-cell order, components x fastest), host or device by
+ * `where` (host: synchronises the stream). */
+int gmg_efield(gmg_tree *tree, double *out, int where, void *stream);
+
 /* Inspection (tests, tools): phi (which = 0) or b (which = 1) of every cell
  * of a level in canonical block order, FP64 host array; distances d
  * (nb * N^D * 2D) and mask flags (nb * N^D) of a level. */

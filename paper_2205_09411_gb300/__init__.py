@@ -101,6 +101,7 @@ def load():
         "gmg_get_solution": (C.c_int, [vp, vp, C.c_int, vp]),
         "gmg_vcycle": (C.c_int, [vp, C.c_int, vp]),
         "gmg_fmg": (C.c_int, [vp, C.c_int, vp]),
+        "gmg_efield": (C.c_int, [vp, vp, C.c_int, vp]),
         "gmg_residual": (C.c_int, [vp, dp, dp, vp]),
         "gmg_solve": (C.c_int, [vp, C.c_int, C.c_double, C.c_int, C.POINTER(Stats), vp]),
         "gmg_get_level": (C.c_int, [vp, C.c_int, C.c_int, dp, vp]),
@@ -374,6 +375,16 @@ class Tree:
 
     def vcycle(self, n=1, stream=None):
         _check(load().gmg_vcycle(self.h, n, _stream_ptr(stream)))
+
+    def efield(self, out=None, stream=None):
+        """E = -grad(phi) on the upper faces of every leaf cell: (n_leaf, dim),
+        or (nrhs, n_leaf, dim) for several slots."""
+        if out is None:
+            shape = (self.n_leaf_cells, self.dim) if self.nrhs == 1 else (self.nrhs, self.n_leaf_cells, self.dim)
+            out = np.zeros(shape)
+        p, where = self._arr(out)
+        _check(load().gmg_efield(self.h, p, where, _stream_ptr(stream)))
+        return out
 
     def fmg(self, n=1, stream=None):
         """n FMG cycles in FP64 (Sec. 2.2)."""

@@ -100,12 +100,13 @@ int forest_merge(gmg_tree *const *trees, int n, gmg_tree **out) {
   F->st_base_h.assign(nb, -1);
   F->bt_base_h.assign(nb, -1);
   F->dist_base_h.assign(nb, -1);
+  F->wallv_base_h.assign(nb, -1);
   F->mask_base_h.assign(nb, -1);
   F->tree_of_h.assign(nb, 0);
   F->tree_boff_h.assign(n + 1, 0);
   F->tree_leaf_off_h.assign(n + 1, 0);
   F->tree_lo_h.assign((size_t)3 * n, 0.0);
-  long long st_off = 0, bt_off = 0, di_off = 0, ma_off = 0, sp_off = 0;
+  long long st_off = 0, bt_off = 0, di_off = 0, ma_off = 0, sp_off = 0, wv_off = 0;
   for (int i = 0; i < n; i++) {
     const gmg_tree *t = trees[i];
     for (int d = 0; d < 3; d++) F->tree_lo_h[3 * i + d] = t->lo[d];
@@ -125,6 +126,7 @@ int forest_merge(gmg_tree *const *trees, int n, gmg_tree **out) {
       if (t->bt_base_h[b] >= 0) F->bt_base_h[g] = t->bt_base_h[b] + bt_off;
       if (t->dist_base_h[b] >= 0) F->dist_base_h[g] = t->dist_base_h[b] + di_off;
       if (t->mask_base_h[b] >= 0) F->mask_base_h[g] = t->mask_base_h[b] + ma_off;
+      if (t->wallv_base_h[b] >= 0) F->wallv_base_h[g] = t->wallv_base_h[b] + wv_off;
     }
     // spec flags run parallel to the stencil pool (one flag per cell and
     // cut block, at st_base / (2D + 1))
@@ -135,12 +137,15 @@ int forest_merge(gmg_tree *const *trees, int n, gmg_tree **out) {
     F->spec_h.insert(F->spec_h.end(), t->spec_h.begin(), t->spec_h.end());
     F->bterm_h.insert(F->bterm_h.end(), t->bterm_h.begin(), t->bterm_h.end());
     F->dist_h.insert(F->dist_h.end(), t->dist_h.begin(), t->dist_h.end());
+    F->bphib_h.insert(F->bphib_h.end(), t->bphib_h.begin(), t->bphib_h.end());
+    F->wallv_h.insert(F->wallv_h.end(), t->wallv_h.begin(), t->wallv_h.end());
     F->mask_h.insert(F->mask_h.end(), t->mask_h.begin(), t->mask_h.end());
     st_off += (long long)t->stencil_h.size();
     sp_off += (long long)t->spec_h.size();
     bt_off += (long long)t->bterm_h.size();
     di_off += (long long)t->dist_h.size();
     ma_off += (long long)t->mask_h.size();
+    wv_off += (long long)t->wallv_h.size();
     // the coarsest level's inverse of tree i (root i)
     F->cinv_h.insert(F->cinv_h.end(), t->cinv_h.begin(), t->cinv_h.end());
     // leaves tree-major, each tree in its own leaf order

@@ -12,6 +12,7 @@
 
 #include "gmg_internal.h"
 #include "coarse_cycle.cuh"
+#include "efield.cuh"
 #include "fused_sweeps.cuh"
 #include "kernels.cuh"
 
@@ -319,6 +320,10 @@ void set_all_smem_limits() {
   kernel_attrs(k_leaf_copy, false);
   kernel_attrs(k_leaf_accumulate, false);
   kernel_attrs(k_to_float, false);
+  for (int n : {4, 8, 16, 32, 2}) {
+    with_nt<3>(n, [&](auto nt) { kernel_attrs(k_efield<3, decltype(nt)::value>, true); });
+    with_nt<2>(n, [&](auto nt) { kernel_attrs(k_efield<2, decltype(nt)::value>, true); });
+  }
   kernel_attrs(k_delay, false);
   done = true;
 }
@@ -685,7 +690,8 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t nbr, pnb, parent, pofs, flags, leaf, cbase, st_base, bt_base, phi, b, old, fphi, fb, fold, st, fst, bterm, cinv,
-      partials, red, active, tree_of, tree_blocks, tree_boff, bar, spec, lvtab, total;
+      partials, red, active, tree_of, tree_blocks, tree_boff, bar, spec, lvtab, cellflag, mask_base, dist, bphib,
+      dist_base, wallv, wallv_base, leafpos, total;
 };
 
 Layout layout(const gmg_tree *t) {
@@ -723,6 +729,14 @@ Layout layout(const gmg_tree *t) {
   L.tree_of = take(nb * sizeof(int));
   L.tree_blocks = take(nb * sizeof(int));
   L.tree_boff = take(((size_t)t->ntree + 1) * sizeof(int));
+  L.cellflag = take(t->mask_h.size());
+  L.mask_base = take(nb * sizeof(long long));
+  L.dist = take(t->dist_h.size() * sizeof(double));
+  L.bphib = take(t->bphib_h.size() * sizeof(double));
+  L.dist_base = take(nb * sizeof(long long));
+  L.wallv = take(t->wallv_h.size() * sizeof(double));
+  L.wallv_base = take(nb * sizeof(long long));
+  L.leafpos = take(nb * sizeof(int));
   L.bar = take(sizeof(GridBar));
   L.spec = take(t->spec_h.size());
   L.lvtab = take(kMaxLevels * sizeof(LvArgs));
@@ -895,7 +909,7 @@ int gmg_get_mask(const gmg_tree *t, int level, int *out) {
   size_t k = 0;
   for (int i = 0; i < L.count; i++) {
     long long mb = t->mask_base_h[L.first + i];
-    for (int c = 0; c < L.ncell; c++) out[k++] = t->mask_h[mb + c];
+    for (int c = 0; c < L.ncell; c++) out[k++] = t->mask_h[mb + c] & 1;
   }
   return GMG_OK;
 }
@@ -950,6 +964,14 @@ int gmg_tree_bind(gmg_tree *t, void *device_ptr, size_t bytes) {
   t->d_tree_of = reinterpret_cast<int *>(w + L.tree_of);
   t->d_tree_blocks = reinterpret_cast<int *>(w + L.tree_blocks);
   t->d_tree_boff = reinterpret_cast<int *>(w + L.tree_boff);
+  t->d_cellflag = reinterpret_cast<unsigned char *>(w + L.cellflag);
+  t->d_mask_base = reinterpret_cast<long long *>(w + L.mask_base);
+  t->d_dist = reinterpret_cast<double *>(w + L.dist);
+  t->d_bphib = reinterpret_cast<double *>(w + L.bphib);
+  t->d_dist_base = reinterpret_cast<long long *>(w + L.dist_base);
+  t->d_wallv = reinterpret_cast<double *>(w + L.wallv);
+  t->d_wallv_base = reinterpret_cast<long long *>(w + L.wallv_base);
+  t->d_leafpos = reinterpret_cast<int *>(w + L.leafpos);
   t->d_bar = reinterpret_cast<GridBar *>(w + L.bar);
   t->d_spec = reinterpret_cast<unsigned char *>(w + L.spec);
   t->d_lvtab = reinterpret_cast<LvArgs *>(w + L.lvtab);
@@ -1007,6 +1029,21 @@ int gmg_tree_bind(gmg_tree *t, void *device_ptr, size_t bytes) {
   }
   if (!t->bterm_h.empty())
     CUDA_TRY(cudaMemcpy(t->d_bterm, t->bterm_h.data(), t->bterm_h.size() * sizeof(double), cudaMemcpyHostToDevice));
+  {  // field evaluation tables
+    auto up = [](void *d, const void *h, size_t bytes) {
+      return bytes ? cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
+    };
+    std::vector<int> leafpos(nb, -1);
+    for (size_t k = 0; k < t->leaf_ids_h.size(); k++) leafpos[t->leaf_ids_h[k]] = (int)k;
+    CUDA_TRY(up(t->d_cellflag, t->mask_h.data(), t->mask_h.size()));
+    CUDA_TRY(up(t->d_mask_base, t->mask_base_h.data(), nb * sizeof(long long)));
+    CUDA_TRY(up(t->d_dist, t->dist_h.data(), t->dist_h.size() * sizeof(double)));
+    CUDA_TRY(up(t->d_bphib, t->bphib_h.data(), t->bphib_h.size() * sizeof(double)));
+    CUDA_TRY(up(t->d_dist_base, t->dist_base_h.data(), nb * sizeof(long long)));
+    CUDA_TRY(up(t->d_wallv, t->wallv_h.data(), t->wallv_h.size() * sizeof(double)));
+    CUDA_TRY(up(t->d_wallv_base, t->wallv_base_h.data(), nb * sizeof(long long)));
+    CUDA_TRY(up(t->d_leafpos, leafpos.data(), nb * sizeof(int)));
+  }
   CUDA_TRY(cudaMemcpy(t->d_cinv, t->cinv_h.data(), t->cinv_h.size() * sizeof(double), cudaMemcpyHostToDevice));
   const size_t cells = (size_t)t->total_cells * t->nrhs;
   CUDA_TRY(cudaMemset(t->d_phi, 0, cells * sizeof(double)));
@@ -1176,6 +1213,51 @@ int gmg_fmg(gmg_tree *t, int n_cycles, void *stream) {
   for (int k = 0; k < n_cycles; k++) {
     rc = run_graph(t, gmg_tree::kGraphFmg64, s, [&](cudaStream_t cs) { return fmg_any<double>(t, cs); });
     if (rc) return rc;
+  }
+  return GMG_OK;
+}
+
+int gmg_efield(gmg_tree *t, double *out, int where, void *stream) {
+  if (!t || !out) return set_error("null argument"), GMG_ERR_INVALID_ARG;
+  if (!t->bound) return set_error("tree not bound"), GMG_ERR_STATE;
+  if (where != GMG_HOST && where != GMG_DEVICE) return set_error("where must be GMG_HOST or GMG_DEVICE"), GMG_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  const size_t n = (size_t)t->nrhs * t->n_leaf_cells * t->D;
+  double *dst = out;
+  if (where == GMG_HOST) {  // staged in the dead FP64 'old' field when it is large enough, else allocated
+    if (n <= (size_t)t->nrhs * t->total_cells) {
+      dst = t->d_old;
+    } else {
+      CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&dst), n * sizeof(double), s));
+    }
+  }
+  int rc = upload_mask(t, nullptr, s);
+  if (rc) return rc;
+  EfieldArgs E{t->d_cellflag, t->d_mask_base, t->d_dist, t->d_bphib, t->d_dist_base, t->d_wallv, t->d_wallv_base,
+               t->d_leafpos, dst, t->n_leaf_cells, 0};
+  for (int k = 0; k < t->D; k++) E.dirichlet_upper |= (t->wall_type[2 * k + 1] == GMG_WALL_DIRICHLET ? 1 : 0) << k;
+  GmgView<double> V = view<double>(t);
+  for (int l = t->lmin; l <= t->lmax; l++) {
+    if (!t->level_has_leaves[l - t->lmin]) continue;
+    const LvArgs L = lv(t, l), Lp = l > t->lmin ? lv(t, l - 1) : L;
+    const size_t sm = tile_bytes<double>(t, l);
+    auto go = [&](auto nt) {
+      constexpr int NT = decltype(nt)::value;
+      if (t->D == 3)
+        k_efield<3, NT><<<L.count * t->nrhs, cta_threads(t, l), sm, s>>>(V, L, Lp, E);
+      else
+        k_efield<2, NT><<<L.count * t->nrhs, cta_threads(t, l), sm, s>>>(V, L, Lp, E);
+    };
+    if (t->D == 3)
+      with_nt<3>(L.n, go);
+    else
+      with_nt<2>(L.n, go);
+  }
+  CUDA_TRY(cudaGetLastError());
+  if (where == GMG_HOST) {
+    CUDA_TRY(cudaMemcpyAsync(out, dst, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (dst != t->d_old) CUDA_TRY(cudaFreeAsync(dst, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
   }
   return GMG_OK;
 }

@@ -130,8 +130,11 @@ struct gmg_tree {
   std::vector<double> stencil_h;  // concatenated per cut block: (2D+1) x ncell
   std::vector<double> bterm_h;    // concatenated per block with boundary terms: ncell
   std::vector<uint8_t> spec_h;    // per cut block ncell flags (any d < 1), parallel to stencil_h
-  std::vector<double> dist_h;     // per cut block: ncell x 2D distances (inspection)
+  std::vector<double> dist_h;     // per cut block: ncell x 2D distances (inspection, field evaluation)
+  std::vector<double> bphib_h;    // parallel to dist_h: boundary value phi_b(x0) where d < 1
   std::vector<long long> dist_base_h;
+  std::vector<double> wallv_h;    // per block on an upper domain wall: D x n^(D-1) Dirichlet face values
+  std::vector<long long> wallv_base_h;
   std::vector<uint8_t> mask_h;    // per block ncell (inspection)
   std::vector<long long> mask_base_h;
   int nc = 0;                     // coarsest-level unknowns
@@ -148,6 +151,12 @@ struct gmg_tree {
   double *d_st = nullptr, *d_bterm = nullptr, *d_cinv = nullptr, *d_partials = nullptr, *d_red = nullptr;
   int *d_active = nullptr, *h_active = nullptr;  // unit mask (device, pinned host mirror)
   int *d_tree_of = nullptr, *d_tree_blocks = nullptr, *d_tree_boff = nullptr;
+  // field evaluation (gmg_efield): per-cell flags, distances and boundary
+  // values of cut blocks, upper-wall values, leaf position of each block
+  unsigned char *d_cellflag = nullptr;
+  double *d_dist = nullptr, *d_bphib = nullptr, *d_wallv = nullptr;
+  long long *d_dist_base = nullptr, *d_wallv_base = nullptr, *d_mask_base = nullptr;
+  int *d_leafpos = nullptr;
   float *f_st = nullptr;
   unsigned char *d_spec = nullptr;
   gmg::LvArgs *d_lvtab = nullptr;  // per-level descriptors (phi in the first buffer)

@@ -399,6 +399,9 @@ int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, do
   const int nb = (int)T->blocks.size();
   T->st_base_h.assign(nb, -1);
   T->bt_base_h.assign(nb, -1);
+  T->wallv_base_h.assign(nb, -1);
+  T->wallv_h.clear();
+  T->bphib_h.clear();
   T->dist_base_h.assign(nb, -1);
   T->mask_base_h.assign(nb, -1);
   T->stencil_h.clear();
@@ -411,8 +414,8 @@ int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, do
   // thread-safe); the results are then concatenated in block order, so the
   // stores are the same whatever the thread count.
   struct BlockOut {
-    std::vector<uint8_t> mask;
-    std::vector<double> dd, st, bt;
+    std::vector<uint8_t> mask;   // bit 0: Eq. (boundary-mask); bit 1: cell centre inside the object
+    std::vector<double> dd, st, bt, pb, wv;
     bool cut = false, anybt = false;
   };
   std::vector<BlockOut> outs(nb);
@@ -422,7 +425,7 @@ int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, do
     const int n = L.n, nc = L.ncell;
     const double h = L.h;
     const double Lmask = T->prm.mask_factor * std::sqrt((double)D) * h;
-    std::vector<double> dd((size_t)nc * 2 * D, 1.0), st, bt;
+    std::vector<double> dd((size_t)nc * 2 * D, 1.0), pb((size_t)nc * 2 * D, 0.0), st, bt;
     o.mask.assign(nc, 0);
     uint8_t *mask = o.mask.data();
     bool cut = false;
@@ -432,6 +435,7 @@ int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, do
       double a[3];
       cell_center(T, B, L, p, a);
       double fa = f(a);
+      if (fa < 0.0) mask[c] |= 2;
       // Eq. (boundary-mask) with a central-difference gradient
       double gn = 0.0;
       for (int k = 0; k < D; k++) {
@@ -443,7 +447,7 @@ int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, do
       }
       gn = std::sqrt(gn);
       if (!(std::fabs(fa) < Lmask * gn)) continue;
-      mask[c] = 1;
+      mask[c] |= 1;
       double *dc = &dd[(size_t)c * 2 * D];
       bool found = false;
       for (int k = 0; k < D; k++)
@@ -480,13 +484,15 @@ int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, do
         if (dm < 1.0) {
           double x0[3] = {a[0], a[1], a[2]};
           x0[k] = a[k] - dm * h;
-          bnd = bnd + cm * (phib ? phib(x0, phib_user) : phib_const);
+          pb[(size_t)c * 2 * D + 2 * k] = phib ? phib(x0, phib_user) : phib_const;
+          bnd = bnd + cm * pb[(size_t)c * 2 * D + 2 * k];
           cm = 0.0;
         }
         if (dp < 1.0) {
           double x0[3] = {a[0], a[1], a[2]};
           x0[k] = a[k] + dp * h;
-          bnd = bnd + cp * (phib ? phib(x0, phib_user) : phib_const);
+          pb[(size_t)c * 2 * D + 2 * k + 1] = phib ? phib(x0, phib_user) : phib_const;
+          bnd = bnd + cp * pb[(size_t)c * 2 * D + 2 * k + 1];
           cp = 0.0;
         }
         coef[2 * k] = cm;
@@ -516,8 +522,36 @@ int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, do
     if (cut) {
       o.st = std::move(st);
       o.dd = std::move(dd);
+      o.pb = std::move(pb);
     }
     for (int c = 0; c < nc; c++) o.anybt = o.anybt || bt[c] != 0.0;
+    // Dirichlet values at the centres of the block's faces on upper domain
+    // walls (axis k, face cell j over the other axes in increasing order),
+    // for the field evaluation on upper cell faces
+    {
+      const int nf = D == 3 ? n * n : n;
+      bool upper = false;
+      std::vector<double> wv((size_t)D * nf, 0.0);
+      for (int k = 0; k < D; k++)
+        for (int j = 0; j < nf; j++) {
+          const int u = j % n, v = D == 3 ? j / n : 0;
+          int p[3] = {0, 0, 0};
+          p[k] = n - 1;
+          p[k == 0 ? 1 : 0] = u;
+          if (D == 3) p[k == 2 ? 1 : 2] = v;
+          int G[3];
+          for (int d = 0; d < 3; d++) G[d] = d < D ? B.ix[d] * n + p[d] : 0;
+          G[k] += 1;
+          if (in_domain(L, D, G)) continue;
+          upper = true;
+          if (T->wall_type[2 * k + 1] != GMG_WALL_DIRICHLET) continue;
+          double a[3];
+          cell_center(T, B, L, p, a);
+          a[k] += 0.5 * h;
+          wv[(size_t)k * nf + j] = T->wall_fn ? T->wall_fn(a, T->wall_user) : T->wall_val[2 * k + 1];
+        }
+      if (upper) o.wv = std::move(wv);
+    }
     if (o.anybt) o.bt = std::move(bt);
   };
   const bool callbacks = lsf->kind == GMG_LSF_CALLBACK || phib || T->wall_fn;
@@ -550,6 +584,11 @@ int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, do
       }
       T->dist_base_h[id] = (long long)T->dist_h.size();
       T->dist_h.insert(T->dist_h.end(), o.dd.begin(), o.dd.end());
+      T->bphib_h.insert(T->bphib_h.end(), o.pb.begin(), o.pb.end());
+    }
+    if (!o.wv.empty()) {
+      T->wallv_base_h[id] = (long long)T->wallv_h.size();
+      T->wallv_h.insert(T->wallv_h.end(), o.wv.begin(), o.wv.end());
     }
     if (o.anybt) {
       T->bt_base_h[id] = (long long)T->bterm_h.size();

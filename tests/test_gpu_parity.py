@@ -230,3 +230,19 @@ def test_fmg_without_graphs_or_cooperative_launch():
     t.fmg(2)
     ref = o.solution()
     assert np.abs(t.solution() - ref).max() <= TOL_ITERATE * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("name", ["c1", "adaptive2d", "adaptive3d", "needle4", "ragged3d", "c2_32"])
+def test_efield_matches_oracle(name):
+    """E = -grad(phi) on cell faces (Sec. 4.4) from the same phi on both
+    sides: the oracle's after four V-cycles, set on the GPU tree."""
+    p = parity_cases()[name]
+    o = oracle_problem(p)
+    o.vcycle(4)
+    phi = o.solution()
+    t = gpu_problem(p)
+    t.set_solution(phi)
+    got = t.efield()
+    ref = o.efield()
+    scale = max(np.abs(ref).max(), 1e-300)
+    assert np.abs(got - ref).max() <= 1e-12 * scale * 64
