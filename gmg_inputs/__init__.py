@@ -30,6 +30,8 @@ analytic test problems, not datasets):
   rotation, centre U[0.35, 0.65]^3) with phi_b ~ U[0,1] on it and
   Dirichlet walls with values U[0,1] per wall; right-hand side white noise
   N(0,1) averaged over 3^3 cells (zero outside the domain).
+* ``sharp_problem``  the sharp shapes of Sec. 4.3 (spheroid, rhombus, heart,
+  astroid) on the unit square, or revolved about the z axis in 3D.
 * ``sphere2d`` / ``sphere3d``  the convergence test of Sec. 4.1: a domain of
   unit size centred at the origin, f = |x| - R with R = 1/4, walls given by
   the analytic solutions log(|x|/R) (2D) and 1 - R/|x| (3D), phi_b = 0.
@@ -211,6 +213,21 @@ def box_noise_rhs_torch(bix, N: int, n: int, seed: int, device="cuda"):
     gy = (b[:, 1:2] * N + y[None, :]).reshape(-1)
     gz = (b[:, 2:3] * N + z[None, :]).reshape(-1)
     return g[gz, gy, gx]
+
+
+SHAPES = {"spheroid": 0, "rhombus": 1, "heart": 2, "astroid": 3}
+
+
+def sharp_problem(shape: str, dim: int = 2, max_level: int = 8) -> dict:
+    """The sharp-boundary tests of Sec. 4.3: the unit square (cube) with
+    8^2 (8^3) root cells, uniform refinement to max_level, phi = 1 on the
+    shape and 0 on the walls, g = 0, w_min = 4e-3 in 2D and 8e-3 in 3D; in
+    3D the shape is revolved about the z axis (reading SH)."""
+    return dict(dim=dim, N=8, cb=(1, 1, 1), lo=(0.0, 0.0, 0.0), h1=1.0 / 8, max_level=max_level, refine=None,
+                lsf=("shape", (float(SHAPES[shape]), 1.0 if dim == 3 else 0.0)), walls=(WALL_DIRICHLET,) * (2 * dim),
+                wall_values=(0.0,) * 6, wall_fn=None, phib=1.0, rhs=lambda xc: np.zeros(len(xc)),
+                n_vcycles=12, tol=1e-8, index=60 + SHAPES[shape], max_coarse_cells=64 if dim == 2 else 512,
+                w_min=4e-3 if dim == 2 else 8e-3)
 
 
 def problem(name: str, **over) -> dict:

@@ -29,7 +29,7 @@ _LIB_PATH = os.path.join(_OUT_DIR, "libgmg_oracle.so")
 _lib = None
 _lock = threading.Lock()
 
-LSF_NONE, LSF_SPHERE, LSF_CAPSULE, LSF_ELLIPSOID, LSF_CALLBACK = 0, 1, 2, 3, 4
+LSF_NONE, LSF_SPHERE, LSF_CAPSULE, LSF_ELLIPSOID, LSF_CALLBACK, LSF_SHAPE = 0, 1, 2, 3, 4, 5
 WALL_DIRICHLET, WALL_NEUMANN = 0, 1
 
 FN = C.CFUNCTYPE(C.c_double, C.POINTER(C.c_double), C.c_void_p)

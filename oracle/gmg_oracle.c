@@ -485,6 +485,25 @@ double ot_lsf_eval(const ot_lsf *L, int D, const double *x) {
     }
     return amin * (sqrt(s) - 1.0);
   }
+  case OT_LSF_SHAPE: {
+    /* Eqs. (spheroid)-(astroid) of Sec. 4.3 in (p, q) = 4 (x - 1/2, y - 1/2),
+     * or 4 (r - 1/2, z - 1/2) with r = sqrt(x^2 + y^2) (reading SH) */
+    double P, Q;
+    if (p[1] != 0.0) {
+      P = 4.0 * (sqrt(x[0] * x[0] + x[1] * x[1]) - 0.5);
+      Q = 4.0 * (x[2] - 0.5);
+    } else {
+      P = 4.0 * (x[0] - 0.5);
+      Q = 4.0 * (x[1] - 0.5);
+    }
+    if (p[0] == 0.0) return sqrt(8.0 * P * P + Q * Q) - 1.0;
+    if (p[0] == 1.0) return 8.0 * fabs(P) + fabs(Q) - 1.5;
+    if (p[0] == 2.0) {
+      double w = Q - cbrt(P * P);
+      return P * P + w * w - 1.0;
+    }
+    return cbrt(P * P) / 0.8 + cbrt(Q * Q) / 1.5 - 0.8;
+  }
   case OT_LSF_CALLBACK:
     return L->fn(x, L->user);
   default:

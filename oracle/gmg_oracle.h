@@ -48,7 +48,9 @@ enum {
   OT_LSF_SPHERE = 1,    /* p[0..2] centre, p[3] radius: |x-c| - R, Eq. (lsf-example) */
   OT_LSF_CAPSULE = 2,   /* p[0..2] a, p[3..5] b, p[6] r: dist(x, segment ab) - r   */
   OT_LSF_ELLIPSOID = 3, /* p[0..2] c, p[3..11] Q row-major, p[12..14] semi-axes     */
-  OT_LSF_CALLBACK = 4   /* user function                                          */
+  OT_LSF_CALLBACK = 4,  /* user function                                          */
+  OT_LSF_SHAPE = 5      /* Sec. 4.3 shapes: p[0] 0 spheroid, 1 rhombus, 2 heart, 3 astroid;
+                           p[1] = 1: revolved about the z axis (3D)                */
 };
 
 typedef struct {

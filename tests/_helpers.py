@@ -22,7 +22,7 @@ def oracle_problem(p, n_down=2, n_up=2, eps_tol=1e-8, mask_factor=1.5, w_min=Non
     if w_min is None:
         w_min = p.get("w_min", 0.0)
     kinds = {"none": O.LSF_NONE, "sphere": O.LSF_SPHERE, "capsule": O.LSF_CAPSULE,
-             "ellipsoid": O.LSF_ELLIPSOID}
+             "ellipsoid": O.LSF_ELLIPSOID, "shape": O.LSF_SHAPE}
     t = O.OracleTree(p["dim"], p["N"], p["cb"], p["lo"], p["h1"], p["max_level"], refine=p["refine"],
                      max_coarse_cells=p.get("max_coarse_cells"))
     t.set_params(n_down, n_up, eps_tol, mask_factor, w_min)

@@ -557,3 +557,56 @@ def test_efield_exact_for_linear_phi(dim):
     assert np.abs(E[inside]).max() == 0.0
     err = np.abs(E[~inside] + a).max()
     assert err < 1e-9, err
+
+
+@pytest.mark.parametrize("shape", ["spheroid", "rhombus", "heart", "astroid"])
+def test_sharp_shape_distances_match_closed_form_roots(shape):
+    """Sec. 4.3 shapes on a 64^2 grid: every line-search distance across the
+    boundary equals the root solved by hand from the shape's equation -
+    along x for the spheroid (|p| = sqrt((1 - q^2)/8)), the rhombus
+    (|p| = (1.5 - |q|)/8) and the astroid (|p| = (0.8 (0.8 - |q|^(2/3)/1.5))^(3/2)),
+    along y for the heart (q = |p|^(2/3) +- sqrt(1 - p^2)) - to 2 eps_tol."""
+    q = I.sharp_problem(shape, 2, 4)
+    q["w_min"] = 0.0
+    t = oracle_problem(q, rhs=False)
+    l = t.levels()[1]
+    h = 1 / 64
+    d = t.get_d(l).reshape(-1, 4)
+    # leaf order of a uniform tree: blocks in Morton order, cells x fastest
+    xc = t.leaf_centers()
+    checked = 0
+    for c in range(len(xc)):
+        x, y = xc[c]
+        P, Q = 4 * (x - 0.5), 4 * (y - 0.5)
+        if shape == "heart":
+            if abs(P) >= 1:
+                continue
+            roots = [abs(P) ** (2 / 3) + s * np.sqrt(1 - P * P) for s in (1, -1)]
+            for k, step in ((3, 1), (2, -1)):  # +y and -y neighbours
+                ts = [(0.5 + r / 4 - y) / (step * h) for r in roots]
+                ts = [v for v in ts if 0 < v < 1]
+                if ts and d[c, k] < 1:  # two roots in one segment: the nearer one
+                    assert abs(d[c, k] - min(ts)) < 2e-8, (c, k, d[c, k], ts)
+                    checked += 1
+            continue
+        if shape == "spheroid":
+            if abs(Q) >= 1:
+                continue
+            pr = np.sqrt((1 - Q * Q) / 8)
+        elif shape == "rhombus":
+            if abs(Q) >= 1.5:
+                continue
+            pr = (1.5 - abs(Q)) / 8
+        else:
+            v = 0.8 * (0.8 - abs(Q) ** (2 / 3) / 1.5)
+            if v <= 0:
+                continue
+            pr = v ** 1.5
+        for k, step in ((1, 1), (0, -1)):  # +x and -x neighbours
+            ts = [(xr - x) / (step * h) for xr in (0.5 + pr / 4, 0.5 - pr / 4)]
+            ts = [v for v in ts if 0 < v < 1]
+            if ts and d[c, k] < 1:  # two roots in one segment: the nearer one
+                assert abs(d[c, k] - min(ts)) < 2e-8, (c, k, d[c, k], ts)
+                checked += 1
+    assert checked >= 8, checked
+    t.close()
