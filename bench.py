@@ -26,7 +26,9 @@ ellipsoids) solved together, after the autotuner has picked the block tile
 and sweep schedule on a sample forest, and `serving` the continuous-batching
 request loop over seven resident sessions (p50/p99 latency and solves/s,
 mixed and FP64), and `paper_table1` the seconds per FMG cycle on the
-paper's Table 1 grid (512^3 sphere, 8^3 and 16^3 blocks), FP64.
+paper's Table 1 grid (512^3 sphere, 8^3 and 16^3 blocks), FP64, and
+`sharp_shapes` the residual reduction per FMG cycle for the sharp
+boundaries of Sec. 4.3.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank solves its own replica (replicas only: the method
@@ -65,7 +67,8 @@ def parse():
     ap.add_argument("--skip-forest", action="store_true", help="leave out the batched uneven-tree workload")
     ap.add_argument("--skip-serving", action="store_true", help="leave out the serving-loop workload")
     ap.add_argument("--skip-table1", action="store_true", help="leave out the 512^3 FMG timing of the paper's Table 1")
-    ap.add_argument("--only", choices=["needle", "forest", "serving", "table1"], default=None,
+    ap.add_argument("--skip-shapes", action="store_true", help="leave out the sharp-boundary FMG runs")
+    ap.add_argument("--only", choices=["needle", "forest", "serving", "table1", "shapes"], default=None,
                     help="run one secondary workload alone (no headline line; for profiling)")
     ap.add_argument("--needle-rhs", type=int, default=32, help="right-hand sides of the batched needle workload")
     return ap.parse_args()
@@ -605,6 +608,39 @@ def run_table1(G, args, world, stream):
     return out
 
 
+def run_shapes(G, args, world, stream):
+    """Sharp boundaries of Sec. 4.3 (spheroid, rhombus, heart, astroid):
+    residual reduction per FMG cycle from phi = 0 on uniform 1024^2 and
+    2048^2 grids (8^2 coarse grid, w_min = 4e-3) and, revolved, on 256^3
+    (8^3 coarse grid, w_min = 8e-3), FP64, with the time per FMG cycle.  The
+    paper shows these reductions as a figure (no printed numbers); it notes
+    that the astroid's is lowest and changes with the refinement level."""
+    import torch
+    out = {}
+    for dim, ml, label in ((2, 8, "1024^2"), (2, 9, "2048^2"), (3, 6, "256^3")):
+        for shape in I.SHAPES:
+            p = I.sharp_problem(shape, dim, ml)
+            t = host_tree(G, p)
+            t.bind()
+            t.set_rhs(torch.zeros(t.n_leaf_cells, dtype=torch.float64, device="cuda"))
+            r = [t.residual()[0]]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            times = []
+            for k in range(4):
+                e0.record(stream)
+                t.fmg(1)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+                r.append(t.residual()[0])
+            out["%s_%s" % (shape, label)] = {"reduction_per_fmg": [r[k] / r[k + 1] for k in range(4)],
+                                             "rel_residual": r[-1], "ms_per_fmg_cycle": float(np.median(times[1:])),
+                                             "cells": t.n_leaf_cells}
+            t.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     import paper_2205_09411_gb300 as G
@@ -618,7 +654,8 @@ def run_ours(args):
         leg = {"needle": lambda: run_needle(G, args, world, flush, stream),
                "forest": lambda: run_forest(G, args, world, flush, stream),
                "serving": lambda: run_serving(G, args, world),
-               "table1": lambda: run_table1(G, args, world, stream)}[args.only]()
+               "table1": lambda: run_table1(G, args, world, stream),
+               "shapes": lambda: run_shapes(G, args, world, stream)}[args.only]()
         if rank == 0:
             print(json.dumps({"only": args.only, args.only: leg}))
         return
@@ -725,6 +762,8 @@ def run_ours(args):
         result["serving"] = run_serving(G, args, world)
     if not args.skip_table1:
         result["paper_table1"] = run_table1(G, args, world, stream)
+    if not args.skip_shapes:
+        result["sharp_shapes"] = run_shapes(G, args, world, stream)
     if rank == 0 and world == 1:
         result["cpu_baseline"] = cpu_baseline(p)
     if rank == 0:

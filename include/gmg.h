@@ -69,6 +69,9 @@ extern "C" {
 #define GMG_LSF_ELLIPSOID 3 /* p[0..2] c, p[3..11] rotation Q (row-major), p[12..14] semi-axes s:
                                min(s) * (|diag(s)^-1 Q^T (x - c)| - 1)                         */
 #define GMG_LSF_CALLBACK 4  /* the host function `fn` */
+#define GMG_LSF_SHAPE 5     /* the sharp shapes of Sec. 4.3: p[0] = 0 spheroid, 1 rhombus, 2 heart,
+                               3 astroid in the coordinates (p, q) = (4 (x - 1/2), 4 (y - 1/2)),
+                               or with p[1] = 1 revolved: (4 (sqrt(x^2 + y^2) - 1/2), 4 (z - 1/2)) */
 
 /* solver arithmetic */
 #define GMG_FP64 0  /* FAS V-cycles in FP64                                            */

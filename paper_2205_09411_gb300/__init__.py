@@ -23,7 +23,7 @@ LIB_PATH = _build.LIB
 FP64, MIXED = 0, 1
 HOST, DEVICE = 0, 1
 WALL_DIRICHLET, WALL_NEUMANN = 0, 1
-LSF_KINDS = {"none": 0, "sphere": 1, "capsule": 2, "ellipsoid": 3, "callback": 4}
+LSF_KINDS = {"none": 0, "sphere": 1, "capsule": 2, "ellipsoid": 3, "callback": 4, "shape": 5}
 
 FN = C.CFUNCTYPE(C.c_double, C.POINTER(C.c_double), C.c_void_p)
 REFINE_FN = C.CFUNCTYPE(C.c_int, C.c_int, C.POINTER(C.c_int), C.c_void_p)

@@ -55,6 +55,25 @@ __host__ __device__ inline double lsf_builtin(const LsfSpec &L, int D, const dou
       }
       return amin * (sqrt(s) - 1.0);
     }
+    case GMG_LSF_SHAPE: {  // Sec. 4.3, Eqs. (spheroid) .. (astroid); reading SH for the coordinates
+      double u, v;
+      if (p[1] != 0.0) {
+        u = 4.0 * (sqrt(x[0] * x[0] + x[1] * x[1]) - 0.5);
+        v = 4.0 * (x[2] - 0.5);
+      } else {
+        u = 4.0 * (x[0] - 0.5);
+        v = 4.0 * (x[1] - 0.5);
+      }
+      switch ((int)p[0]) {
+        case 0: return sqrt(8.0 * u * u + v * v) - 1.0;
+        case 1: return 8.0 * fabs(u) + fabs(v) - 1.5;
+        case 2: {
+          const double w = v - cbrt(u * u);
+          return u * u + w * w - 1.0;
+        }
+        default: return cbrt(u * u) / 0.8 + cbrt(v * v) / 1.5 - 0.8;
+      }
+    }
     default:
       return 1.0;
   }

@@ -390,7 +390,7 @@ int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, do
   gmg_lsf none{};
   none.kind = GMG_LSF_NONE;
   if (!lsf) lsf = &none;
-  if (lsf->kind < GMG_LSF_NONE || lsf->kind > GMG_LSF_CALLBACK || (lsf->kind == GMG_LSF_CALLBACK && !lsf->fn))
+  if (lsf->kind < GMG_LSF_NONE || lsf->kind > GMG_LSF_SHAPE || (lsf->kind == GMG_LSF_CALLBACK && !lsf->fn))
     return set_error("invalid level-set specification"), GMG_ERR_INVALID_ARG;
   HostLsf f{lsf, LsfSpec{}, D};
   f.spec.kind = lsf->kind;
