@@ -177,6 +177,24 @@ int gmg_forest_create(gmg_tree *const *trees, int n_trees, gmg_tree **out);
 int gmg_num_trees(const gmg_tree *tree);
 int gmg_forest_tree_info(const gmg_tree *forest, int tree, long long *leaf_offset, long long *n_leaf_cells);
 
+/* Re-meshing (Sec. 4.5: boundary detection is done for newly added cells;
+ * removing refinement costs nothing): a new tree on the same domain, level
+ * set, boundary values, walls and parameters as `old`, refined by `refine`
+ * up to max_level, with its set-up done.  Blocks that exist in `old` (same
+ * level and coordinates) take old's set-up (it depends only on the block's
+ * own cells); only new blocks run the mask, line searches and stencils.
+ * The result equals a set-up from scratch.  `old` must have been set up with
+ * built-in or still valid callbacks; the new tree is not bound.
+ * gmg_setup_counts tells how many blocks were set up and how many reused.
+ * Errors: STATE (old not set up), INVALID_ARG (a forest). */
+int gmg_tree_remesh(const gmg_tree *old, gmg_refine_fn refine, void *refine_user, int max_level, gmg_tree **out);
+int gmg_setup_counts(const gmg_tree *tree, long long *computed, long long *reused);
+/* Initial guess of a re-meshed tree from the previous tree's solution, for
+ * every slot: blocks that exist in both copy their values, new blocks take
+ * the value of the parent cell containing each cell, covered cells are then
+ * restricted.  Both trees bound, same slot count.  Synchronises. */
+int gmg_transfer_solution(const gmg_tree *old, gmg_tree *tree, void *stream);
+
 /* Number of right-hand-side slots (1 .. 65536) the workspace holds; call
  * before gmg_tree_bind (default 1).  Errors: STATE after bind. */
 int gmg_set_num_rhs(gmg_tree *tree, int nrhs);

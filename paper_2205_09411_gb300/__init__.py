@@ -91,6 +91,9 @@ def load():
         "gmg_get_solution_slots": (C.c_int, [vp, C.c_int, C.c_int, vp, C.c_int, vp]),
         "gmg_iterate": (C.c_int, [vp, C.c_int, ip, C.c_int, dp, dp, vp]),
         "gmg_forest_create": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(vp)]),
+        "gmg_tree_remesh": (C.c_int, [vp, REFINE_FN, vp, C.c_int, C.POINTER(vp)]),
+        "gmg_setup_counts": (C.c_int, [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+        "gmg_transfer_solution": (C.c_int, [vp, vp, vp]),
         "gmg_iterate_begin": (C.c_int, [vp, C.c_int, ip, C.c_int, vp]),
         "gmg_iterate_end": (C.c_int, [vp, dp, dp]),
         "gmg_set_level_sweeps": (C.c_int, [vp, C.c_int, C.c_int, C.c_int]),
@@ -204,6 +207,27 @@ class Tree:
     def units(self):
         """(slot, tree) pairs: the independent problems the tree solves."""
         return self.nrhs * self.ntree
+
+    def remesh(self, refine, max_level):
+        """A new (unbound) tree on this tree's domain and set-up, refined by
+        refine(level, bix) -> bool; blocks present here reuse their set-up."""
+        L = load()
+        cb = REFINE_FN(lambda level, bix, _u: 1 if refine(level, (bix[0], bix[1], bix[2])) else 0)
+        h = C.c_void_p()
+        _check(L.gmg_tree_remesh(self.h, cb, None, int(max_level), C.byref(h)))
+        t = Tree.__new__(Tree)
+        t._adopt(h, self.dim, self.block_n)
+        t._keep = list(self._keep) + [cb]
+        return t
+
+    def setup_counts(self):
+        """(blocks set up, blocks taken from the previous tree)."""
+        a, b = C.c_longlong(), C.c_longlong()
+        _check(load().gmg_setup_counts(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def transfer_solution_from(self, old, stream=None):
+        _check(load().gmg_transfer_solution(old.h, self.h, _stream_ptr(stream)))
 
     def set_num_rhs(self, nrhs):
         """Right-hand-side slots of the workspace (before bind)."""

@@ -9,6 +9,8 @@
 #include <cstring>
 #include <string>
 #include <type_traits>
+#include <unordered_map>
+#include <vector>
 
 #include "gmg_internal.h"
 #include "coarse_cycle.cuh"
@@ -879,6 +881,96 @@ int gmg_store_stencils(gmg_tree *t, const gmg_lsf *lsf, gmg_fn phib, void *phib_
   if (!t) return set_error("null tree"), GMG_ERR_INVALID_ARG;
   if (t->bound) return set_error("stencils must be stored before gmg_tree_bind"), GMG_ERR_STATE;
   return host_setup(t, lsf, phib, phib_user, phib_const);
+}
+
+int gmg_tree_remesh(const gmg_tree *old, gmg_refine_fn refine, void *refine_user, int max_level, gmg_tree **out) {
+  if (!old || !out) return set_error("null argument"), GMG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!old->stencils_ready) return set_error("the previous tree has no set-up"), GMG_ERR_STATE;
+  if (old->ntree != 1) return set_error("forests are re-meshed tree by tree"), GMG_ERR_INVALID_ARG;
+  gmg_domain dom{};
+  dom.dim = old->D;
+  dom.block_n = old->N;
+  for (int d = 0; d < 3; d++) {
+    dom.coarse_blocks[d] = old->cb[d];
+    dom.lo[d] = old->lo[d];
+  }
+  dom.h_root = old->h1;
+  dom.max_level = max_level;
+  dom.max_coarse_cells = old->max_coarse;
+  dom.refine = refine;
+  dom.refine_user = refine_user;
+  gmg_tree *t = nullptr;
+  int rc = gmg_tree_create(&dom, &old->prm, &t);
+  if (rc) return rc;
+  for (int w = 0; w < 6; w++) {
+    t->wall_type[w] = old->wall_type[w];
+    t->wall_val[w] = old->wall_val[w];
+  }
+  t->wall_fn = old->wall_fn;
+  t->wall_user = old->wall_user;
+  rc = host_setup(t, &old->lsf_spec, old->phib_fn, old->phib_user, old->phib_const, old);
+  if (rc) {
+    gmg_tree_destroy(t);
+    return rc;
+  }
+  *out = t;
+  return GMG_OK;
+}
+
+int gmg_setup_counts(const gmg_tree *t, long long *computed, long long *reused) {
+  if (!t) return set_error("null tree"), GMG_ERR_INVALID_ARG;
+  if (computed) *computed = t->setup_computed;
+  if (reused) *reused = t->setup_reused;
+  return GMG_OK;
+}
+
+int gmg_transfer_solution(const gmg_tree *old, gmg_tree *t, void *stream) {
+  if (!old || !t) return set_error("null argument"), GMG_ERR_INVALID_ARG;
+  if (!old->bound || !t->bound) return set_error("both trees must be bound"), GMG_ERR_STATE;
+  if (old->nrhs != t->nrhs || old->D != t->D || old->N != t->N || old->ntree != 1 || t->ntree != 1)
+    return set_error("trees of different shape"), GMG_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  const size_t R = (size_t)t->nrhs, no = (size_t)old->total_cells, nn = (size_t)t->total_cells;
+  std::vector<double> src(R * no), dst(R * nn, 0.0);
+  CUDA_TRY(cudaMemcpyAsync(src.data(), old->d_phi, R * no * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  std::unordered_map<long long, int> old_ids;
+  auto key = [](int level, const int *ix) {
+    return ((long long)(level + 64) << 57) | ((long long)ix[2] << 38) | ((long long)ix[1] << 19) | (long long)ix[0];
+  };
+  for (size_t b = 0; b < old->blocks.size(); b++) old_ids[key(old->blocks[b].level, old->blocks[b].ix)] = (int)b;
+  auto cbase = [](const gmg_tree *T, int id) {
+    const LevelInfo &L = T->lev(T->blocks[id].level);
+    return L.off + (long long)(id - L.first) * L.ncell;
+  };
+  const int D = t->D;
+  for (size_t id = 0; id < t->blocks.size(); id++) {  // levels ascending: parents first
+    const HostBlock &B = t->blocks[id];
+    const LevelInfo &L = t->lev(B.level);
+    const long long nb0 = cbase(t, (int)id);
+    auto it = old_ids.find(key(B.level, B.ix));
+    for (size_t r = 0; r < R; r++) {
+      if (it != old_ids.end()) {
+        const long long ob = cbase(old, it->second);
+        std::memcpy(&dst[r * nn + nb0], &src[r * no + ob], (size_t)L.ncell * sizeof(double));
+      } else if (B.parent >= 0) {  // new refinement: the parent's value (injection)
+        const LevelInfo &P = t->lev(t->blocks[B.parent].level);
+        const long long pb = cbase(t, B.parent);
+        for (int c = 0; c < L.ncell; c++) {
+          const int x = c % L.n, y = (c / L.n) % L.n, z = D == 3 ? c / (L.n * L.n) : 0;
+          const int px = B.pofs[0] + x / 2, py = B.pofs[1] + y / 2, pz = D == 3 ? B.pofs[2] + z / 2 : 0;
+          dst[r * nn + nb0 + c] = dst[r * nn + pb + px + P.n * (py + P.n * pz)];
+        }
+      }
+    }
+  }
+  CUDA_TRY(cudaMemcpyAsync(t->d_phi, dst.data(), R * nn * sizeof(double), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemsetAsync(t->d_active, 1, (size_t)t->units() * sizeof(int), s));
+  int rc = restrict_all_phi64_any(t, s);
+  if (rc) return rc;
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return GMG_OK;
 }
 
 int gmg_num_cut_blocks(const gmg_tree *t, int level) {

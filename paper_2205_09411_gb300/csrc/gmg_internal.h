@@ -126,6 +126,11 @@ struct gmg_tree {
 
   // set-up results (host)
   bool stencils_ready = false;
+  gmg_lsf lsf_spec{};             // the level set and boundary value the set-up used (for re-meshing)
+  gmg_fn phib_fn = nullptr;
+  void *phib_user = nullptr;
+  double phib_const = 0.0;
+  long long setup_computed = 0, setup_reused = 0;  // blocks set up / taken from the previous tree
   std::vector<long long> st_base_h, bt_base_h;
   std::vector<double> stencil_h;  // concatenated per cut block: (2D+1) x ncell
   std::vector<double> bterm_h;    // concatenated per block with boundary terms: ncell
@@ -215,5 +220,6 @@ inline int cta_threads(const gmg_tree *t, int l) {
 
 void set_error(const std::string &msg);
 int build_tree(gmg_tree *T, const gmg_domain *dom);
-int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, double phib_const);
+int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, double phib_const,
+               const gmg_tree *reuse = nullptr);
 }  // namespace gmg

@@ -385,13 +385,18 @@ bool invert(int n, std::vector<double> &A, std::vector<double> &inv) {
 
 }  // namespace
 
-int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, double phib_const) {
+int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, double phib_const,
+               const gmg_tree *reuse) {
   const int D = T->D, S = 2 * D + 1;
   gmg_lsf none{};
   none.kind = GMG_LSF_NONE;
   if (!lsf) lsf = &none;
   if (lsf->kind < GMG_LSF_NONE || lsf->kind > GMG_LSF_SHAPE || (lsf->kind == GMG_LSF_CALLBACK && !lsf->fn))
     return set_error("invalid level-set specification"), GMG_ERR_INVALID_ARG;
+  T->lsf_spec = *lsf;
+  T->phib_fn = phib;
+  T->phib_user = phib_user;
+  T->phib_const = phib_const;
   HostLsf f{lsf, LsfSpec{}, D};
   f.spec.kind = lsf->kind;
   std::memcpy(f.spec.p, lsf->p, sizeof(f.spec.p));
@@ -554,21 +559,60 @@ int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, do
     }
     if (o.anybt) o.bt = std::move(bt);
   };
+  // Re-meshing (Sec. 4.5: boundary detection only for newly added cells):
+  // a block that also exists in `reuse` (same level and coordinates) takes
+  // that tree's set-up, which depends only on the block's own cells.
+  std::unordered_map<long long, int> old_ids;
+  auto key = [](int level, const int *ix) {
+    return ((long long)(level + 64) << 57) | ((long long)ix[2] << 38) | ((long long)ix[1] << 19) | (long long)ix[0];
+  };
+  if (reuse)
+    for (size_t b = 0; b < reuse->blocks.size(); b++) old_ids[key(reuse->blocks[b].level, reuse->blocks[b].ix)] = (int)b;
+  auto reuse_block = [&](int id, BlockOut &o) {
+    if (!reuse) return false;
+    const HostBlock &B = T->blocks[id];
+    auto it = old_ids.find(key(B.level, B.ix));
+    if (it == old_ids.end()) return false;
+    const gmg_tree *R = reuse;
+    const int b = it->second, nc = T->lev(B.level).ncell, nf = D == 3 ? T->lev(B.level).n * T->lev(B.level).n
+                                                                      : T->lev(B.level).n;
+    o.mask.assign(R->mask_h.begin() + R->mask_base_h[b], R->mask_h.begin() + R->mask_base_h[b] + nc);
+    o.cut = R->st_base_h[b] >= 0;
+    if (o.cut) {
+      o.st.assign(R->stencil_h.begin() + R->st_base_h[b], R->stencil_h.begin() + R->st_base_h[b] + (size_t)S * nc);
+      o.dd.assign(R->dist_h.begin() + R->dist_base_h[b], R->dist_h.begin() + R->dist_base_h[b] + (size_t)2 * D * nc);
+      o.pb.assign(R->bphib_h.begin() + R->dist_base_h[b], R->bphib_h.begin() + R->dist_base_h[b] + (size_t)2 * D * nc);
+    }
+    o.anybt = R->bt_base_h[b] >= 0;
+    if (o.anybt) o.bt.assign(R->bterm_h.begin() + R->bt_base_h[b], R->bterm_h.begin() + R->bt_base_h[b] + nc);
+    if (R->wallv_base_h[b] >= 0)
+      o.wv.assign(R->wallv_h.begin() + R->wallv_base_h[b], R->wallv_h.begin() + R->wallv_base_h[b] + (size_t)D * nf);
+    return true;
+  };
+  std::atomic<long long> n_reused{0};
+  auto setup_block = [&](int id, BlockOut &o) {
+    if (reuse_block(id, o))
+      n_reused.fetch_add(1);
+    else
+      process(id, o);
+  };
   const bool callbacks = lsf->kind == GMG_LSF_CALLBACK || phib || T->wall_fn;
   int nthreads = callbacks ? 1 : (int)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 64u);
   if (const char *e = std::getenv("GMG_SETUP_THREADS")) nthreads = std::max(1, std::atoi(e));
   if (nthreads <= 1 || nb < 64) {
-    for (int id = 0; id < nb; id++) process(id, outs[id]);
+    for (int id = 0; id < nb; id++) setup_block(id, outs[id]);
   } else {
     std::atomic<int> next{0};
     std::vector<std::thread> pool;
     for (int w = 0; w < nthreads; w++)
       pool.emplace_back([&] {
         for (int id; (id = next.fetch_add(16)) < nb;)
-          for (int k = id; k < std::min(nb, id + 16); k++) process(k, outs[k]);
+          for (int k = id; k < std::min(nb, id + 16); k++) setup_block(k, outs[k]);
       });
     for (auto &th : pool) th.join();
   }
+  T->setup_reused = n_reused.load();
+  T->setup_computed = nb - T->setup_reused;
   for (int id = 0; id < nb; id++) {
     BlockOut &o = outs[id];
     const int nc = (int)o.mask.size();

@@ -163,3 +163,29 @@ def test_inner_cycles_converge_with_fewer_steps():
         l2, _, bn = o.residual()
         assert st["rel_l2"] <= 1e-8 and l2 / bn <= 1.05e-8
     assert steps[1] <= steps[0]
+
+
+def test_remesh_tree_solves_like_a_fresh_tree_and_transfer_helps():
+    """A re-meshed tree (needle, one level deeper) gives bit for bit the
+    V-cycle iterates of the same tree set up from scratch, and the previous
+    solution transferred to it as the initial guess needs fewer cycles than
+    phi = 0."""
+    import paper_2205_09411_gb300 as G
+    p4 = I.problem("c3", max_level=4, n_rhs=1)
+    p5 = I.problem("c3", max_level=5, n_rhs=1)
+    old = gpu_problem(p4)
+    old.solve(G.FP64, 1e-10, 80)
+    new = old.remesh(p5["refine"], 5)
+    new.bind()
+    ref = gpu_problem(p5)
+    g = np.asarray(p5["rhs"](new.leaf_centers()), dtype=np.float64)
+    for t in (new, ref):
+        t.set_rhs(g)
+        t.vcycle(3)
+    assert np.array_equal(new.solution(), ref.solution())
+    new.set_rhs(g)
+    st0 = new.solve(G.FP64, 1e-8, 80)
+    new.set_rhs(g)
+    new.transfer_solution_from(old)
+    st1 = new.solve(G.FP64, 1e-8, 80)
+    assert st1["cycles"] < st0["cycles"], (st1, st0)

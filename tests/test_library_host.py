@@ -148,3 +148,27 @@ def test_box_noise_generators_agree():
     g = I.box_noise_grid(n, seed)
     assert abs(g[0, 0, 0] - w[:2, :2, :2].sum() / 27) < 1e-15
     assert abs(g[5, 6, 7] - w[4:7, 5:8, 6:9].sum() / 27) < 1e-15
+
+
+def test_remesh_setup_equals_full_setup():
+    """Re-meshing (Sec. 4.5): the needle tree refined one level deeper.
+    Blocks that already existed reuse their set-up; the result equals a
+    set-up from scratch of the new tree (distances and masks on every level,
+    cut blocks), and only the new blocks were set up."""
+    import gmg_inputs as I
+    import paper_2205_09411_gb300 as G
+    from _helpers import gpu_problem
+    p4 = I.problem("c3", max_level=4, n_rhs=1)
+    p5 = I.problem("c3", max_level=5, n_rhs=1)
+    old = gpu_problem(p4, bind=False)
+    new = old.remesh(p5["refine"], 5)
+    ref = gpu_problem(p5, bind=False)
+    assert (new.lmin, new.lmax, new.n_blocks) == (ref.lmin, ref.lmax, ref.n_blocks)
+    for l in range(ref.lmin, ref.lmax + 1):
+        assert np.array_equal(new.distances(l), ref.distances(l))
+        assert np.array_equal(new.mask(l), ref.mask(l))
+        assert new.num_cut_blocks(l) == ref.num_cut_blocks(l)
+    computed, reused = new.setup_counts()
+    assert reused > 0 and computed + reused == new.n_blocks
+    assert computed <= new.n_blocks - old.n_blocks + 8  # new blocks only (a few may be removed ones)
+    assert ref.setup_counts() == (ref.n_blocks, 0)
