@@ -177,7 +177,7 @@ __device__ void tail_smooth(const GmgView<T> &V, const TailLevel<T, D> &Q, int c
   tail_walls<T, D>(Q, V.wneu);
   const TileGeo<T, D> G(Q.n);
   const int n = Q.n, hn = n / 2;
-  const T h2 = T(Q.L.h * Q.L.h), inv2d = T(1.0 / (2 * D));
+  const T h2 = T(Q.L.h2), inv2d = T(1.0 / (2 * D));
   for (int j = threadIdx.x; j < Q.ncell / 2; j += blockDim.x) {
     const int rest = j / hn;
     const int y = rest % n, z = D == 3 ? rest / n : 0;
@@ -204,7 +204,7 @@ __device__ void tail_resid_restrict(const GmgView<T> &V, const TailLevel<T, D> &
   tail_walls<T, D>(F, V.wneu);
   const TileGeo<T, D> G(F.n), Gc(Cq.n);
   const int n = F.n, hn = Cq.n;
-  const T inv_h2 = T(1.0 / (F.L.h * F.L.h)), w = T(1.0 / (1 << D));
+  const T inv_h2 = T(F.L.ih2), w = T(1.0 / (1 << D));
   for (int j = threadIdx.x; j < Cq.ncell; j += blockDim.x) {
     const int qx = j % hn, qy = (j / hn) % hn, qz = D == 3 ? j / (hn * hn) : 0;
     T sp = T(0), sr = T(0);
@@ -233,7 +233,7 @@ __device__ void tail_fas(const GmgView<T> &V, const TailLevel<T, D> &Q) {
   tail_walls<T, D>(Q, V.wneu);
   const TileGeo<T, D> G(Q.n);
   const int n = Q.n;
-  const T inv_h2 = T(1.0 / (Q.L.h * Q.L.h));
+  const T inv_h2 = T(Q.L.ih2);
   for (int c = threadIdx.x; c < Q.ncell; c += blockDim.x) {
     int x, y, z;
     cell_xyz<D>(c, n, &x, &y, &z);

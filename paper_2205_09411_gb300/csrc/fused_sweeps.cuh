@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kThreads) k_smooth_tb(GmgView<T> V0, LvArgs L,
   // any cut block among the 27?  If not, every cell takes the regular stencil
   bool cut_near = false;
   for (int k = 0; k < kNbr; k++) cut_near = cut_near || s_stb[k] >= 0;
-  const T h2 = T(L.h * L.h), inv2d = T(1.0 / (2 * D));
+  const T h2 = T(L.h2), inv2d = T(1.0 / (2 * D));
   for (int j = 0; j < K; j++) {
     const int color = j & 1;
     if (anywall) {

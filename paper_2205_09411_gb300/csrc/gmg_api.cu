@@ -190,6 +190,8 @@ LvArgs lv(const gmg_tree *T, int l) {
   a.poff = L.off;
   a.nd = T->n_down_at(l);
   a.nu = T->n_up_at(l);
+  a.h2 = L.h * L.h;
+  a.ih2 = 1.0 / (L.h * L.h);
   return a;
 }
 
@@ -286,7 +288,9 @@ void set_smem_limits_nt() {
   kernel_attrs(k_smooth<T, D, NT>, true);
   kernel_attrs(k_resid_restrict<T, D, NT>, true);
   kernel_attrs(k_fas<T, D, NT>, true);
-  kernel_attrs(k_prolong<T, D, NT>, true);
+  kernel_attrs(k_prolong<T, D, NT, 64>, true);
+  kernel_attrs(k_prolong<T, D, NT, 128>, true);
+  kernel_attrs(k_prolong<T, D, NT, 256>, true);
   kernel_attrs(k_resnorm<T, D, NT>, true);
   kernel_attrs(k_restrict_phi<T, D, NT>, false);
 }
@@ -328,6 +332,18 @@ void set_all_smem_limits() {
   }
   kernel_attrs(k_delay, false);
   done = true;
+}
+
+// k_prolong with the CTA size of the level's block kernels
+template <typename T, int D, int NT>
+void launch_prolong(int threads, int grid, size_t sm, cudaStream_t s, const GmgView<T> &V, const LvArgs &L,
+                    const LvArgs &Lp) {
+  if (threads == 64)
+    k_prolong<T, D, NT, 64><<<grid, 64, sm, s>>>(V, L, Lp);
+  else if (threads == 128)
+    k_prolong<T, D, NT, 128><<<grid, 128, sm, s>>>(V, L, Lp);
+  else
+    k_prolong<T, D, NT, 256><<<grid, 256, sm, s>>>(V, L, Lp);
 }
 
 template <typename T>
@@ -491,7 +507,7 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s, bool end_restrict, int top) {
     if (fused) L.poff = L.off + other;  // the down leg left phi in the second buffer
     with_nt<D>(L.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
-      launch(t, s, 4, P, l, [&] { k_prolong<T, D, NT><<<L.count * R, kThreads, psm, s>>>(V, L, Lp); });
+      launch(t, s, 4, P, l, [&] { launch_prolong<T, D, NT>(cta_threads(t, l), L.count * R, psm, s, V, L, Lp); });
       if (!fused)
         for (int k = 0; k < L.nu; k++)
           for (int c = 0; c < 2; c++)
@@ -555,7 +571,7 @@ int fmg_impl(gmg_tree *t, cudaStream_t s) {
     const size_t psm = sizeof(T) * (size_t)(D == 3 ? hm * hm * hm : hm * hm);
     with_nt<D>(L.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
-      launch(t, s, 4, P, l, [&] { k_prolong<T, D, NT><<<L.count * R, kThreads, psm, s>>>(V, L, Lp); });
+      launch(t, s, 4, P, l, [&] { launch_prolong<T, D, NT>(cta_threads(t, l), L.count * R, psm, s, V, L, Lp); });
     });
     const int rc = vcycle_impl<T, D>(t, s, true, l);
     if (rc) return rc;

@@ -49,6 +49,7 @@ struct LvArgs {
   double h;
   long long poff;  // first cell of the level in phi (off, or off + total cells in the second buffer)
   int nd, nu;      // red/black sweeps of the level on the way down / up
+  double h2, ih2;  // h^2 and 1 / h^2, computed on the host (no FP64 division on the device)
 };
 
 // Everything a kernel needs to address the tree in device memory.

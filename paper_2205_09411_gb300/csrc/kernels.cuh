@@ -386,7 +386,7 @@ __device__ void smooth_block(const GmgView<T> &V, const LvArgs &L, const LvArgs 
   const long long pbase = L.poff + (long long)(bid - L.first) * NCELL;
   const long long sb = V.st_base[bid];
   load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv, sfl, sb);
-  const T h2 = T(L.h * L.h), inv2d = T(1.0 / (2 * D));
+  const T h2 = T(L.h2), inv2d = T(1.0 / (2 * D));
   const int nhalf = NCELL / 2;
   for (int j = threadIdx.x; j < nhalf; j += blockDim.x) {
     const int rest = j / hn;
@@ -432,7 +432,7 @@ __device__ void resid_restrict_block(const GmgView<T> &V, const LvArgs &L, const
   const long long sb = V.st_base[bid];
   const int P = V.parent[bid], po = V.pofs[bid];
   load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv, sfl, sb);
-  const T inv_h2 = T(1.0 / (L.h * L.h));
+  const T inv_h2 = T(L.ih2);
   const int pofs[3] = {po & 1023, (po >> 10) & 1023, (po >> 20) & 1023};
   const long long pbase = Lp.off + (long long)(P - Lp.first) * Lp.ncell;
   const int pn = Lp.n;
@@ -490,7 +490,7 @@ __device__ void fas_block(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
   unsigned char *sfl = level_flags(sbv, NCELL);
   const long long sb = V.st_base[bid];
   load_tile<T, D, NT, true>(V, L, Lp, bid, tile, sbv, sfl, sb);
-  const T inv_h2 = T(1.0 / (L.h * L.h));
+  const T inv_h2 = T(L.ih2);
   const long long pbase = L.poff + (long long)(bid - L.first) * NCELL;
   for (int c = threadIdx.x; c < NCELL; c += blockDim.x) {
     int x, y, z;
@@ -543,8 +543,9 @@ __global__ void __launch_bounds__(kThreads) k_coarse(GmgView<T> V, LvArgs Lc, co
 
 // (Bi/tri)linear prolongation of the coarse correction phi - old
 // (Sec. 2.2, 3.4): weights 3/4 and 1/4 per dimension from the parent cell
-// and its neighbours toward the fine cell (reading P).
-template <typename T, int D, int NT>
+// and its neighbours toward the fine cell (reading P).  The block's own
+// cells are held in registers, sized for CTAs of at least PT threads.
+template <typename T, int D, int NT, int PT = kThreads>
 __device__ void prolong_block(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, unsigned char *smem_raw) {
   __shared__ int s_nb[kNbr];
   T *tile = reinterpret_cast<T *>(smem_raw);
@@ -557,7 +558,7 @@ __device__ void prolong_block(const GmgView<T> &V, const LvArgs &L, const LvArgs
   using VT = typename Vec16<T>::type;
   const long long base = L.poff + (long long)(bid - L.first) * NCELL;
   VT *__restrict__ fine = reinterpret_cast<VT *>(V.phi + base);
-  constexpr int IV = NT ? ((D == 3 ? NT * NT * NT : NT * NT) / VEC + kThreads - 1) / kThreads : 1;
+  constexpr int IV = NT ? ((D == 3 ? NT * NT * NT : NT * NT) / VEC + PT - 1) / PT : 1;
   VT rv[IV];
   if (NT) {
 #pragma unroll
@@ -620,13 +621,13 @@ __device__ void prolong_block(const GmgView<T> &V, const LvArgs &L, const LvArgs
   }
 }
 
-template <typename T, int D, int NT>
-__global__ void __launch_bounds__(kThreads) k_prolong(GmgView<T> V, LvArgs L, LvArgs Lp) {
+template <typename T, int D, int NT, int PT>
+__global__ void __launch_bounds__(PT) k_prolong(GmgView<T> V, LvArgs L, LvArgs Lp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int bid;
   GmgView<T> W;
   if (!slot_item(V, L, &bid, &W)) return;
-  prolong_block<T, D, NT>(W, L, Lp, bid, smem_raw);
+  prolong_block<T, D, NT, PT>(W, L, Lp, bid, smem_raw);
 }
 
 // phi of covered cells <- mean of the children (composite consistency).
@@ -708,7 +709,7 @@ __global__ void __launch_bounds__(kThreads) k_resnorm(GmgView<T> V0, LvArgs L, L
   const long long base = L.off + (long long)(bid - L.first) * NCELL;
   const long long sb = V.st_base[bid];
   load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv, sfl, sb);
-  const T inv_h2 = T(1.0 / (L.h * L.h));
+  const T inv_h2 = T(L.ih2);
   // the norms only steer the stopping test: squares and maxima of the
   // rounded residual are accumulated in FP32 per thread, then in FP64
   float s2f = 0.f, mxf = 0.f, b2f = 0.f;

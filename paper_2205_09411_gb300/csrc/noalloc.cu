@@ -98,11 +98,11 @@ void launch_resnorm(gmg_tree *t, int l, double *partials, cudaStream_t s) {
   V.tree_of = t->d_tree_of;
   V.active = t->d_active;
   const gmg::LevelInfo &Li = t->lev(l);
-  gmg::LvArgs L{Li.first, Li.count, Li.n, Li.ncell, Li.off, Li.h, Li.off, 0, 0};
+  gmg::LvArgs L{Li.first, Li.count, Li.n, Li.ncell, Li.off, Li.h, Li.off, 0, 0, Li.h * Li.h, 1.0 / (Li.h * Li.h)};
   gmg::LvArgs Lp = L;
   if (l > t->lmin) {
     const gmg::LevelInfo &Pi = t->lev(l - 1);
-    Lp = gmg::LvArgs{Pi.first, Pi.count, Pi.n, Pi.ncell, Pi.off, Pi.h, Pi.off, 0, 0};
+    Lp = gmg::LvArgs{Pi.first, Pi.count, Pi.n, Pi.ncell, Pi.off, Pi.h, Pi.off, 0, 0, Pi.h * Pi.h, 1.0 / (Pi.h * Pi.h)};
   }
   const size_t sm = gmg::level_smem_bytes<double>(D, Li.n);
   cudaFuncSetAttribute(gmg::k_resnorm<double, D, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
