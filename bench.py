@@ -512,8 +512,10 @@ def run_serving(G, args, world):
     seven resident sessions (the 2D circle at 512^2, spheres at 64^3, 128^3
     and 256^3, the needle at 5, 6 and 7 levels), 8 slots each, HBM budget
     160 GB; continuous batching (serving.Server).  Sessions are loaded and
-    their graphs captured by a warm-up request each; the timed run serves
-    a fresh seeded stream, mixed and FP64."""
+    their graphs captured by a warm-up request each, then the autotuner picks
+    each session's sweep schedule; the timed run serves a fresh seeded
+    stream, mixed and FP64, then the same stream at ten times the rate (the
+    loop's capacity)."""
     import torch
     from paper_2205_09411_gb300.serving import Request, Server, Session, poisson_arrivals, summarize
     specs = {"circle2d_512": I.problem("c1", max_level=7),
@@ -543,16 +545,35 @@ def run_serving(G, args, world):
     def req(i, name, at):
         return Request(name, lambda s, c=charges[i]: I.charge_density_torch(s.ctx["xc"], c), at)
 
-    out = {"sessions": {}, "rate_per_s": rate, "requests": n_req, "slots_per_session": 8, "budget_gb": 160.0}
+    from paper_2205_09411_gb300 import autotune as AT
+    out = {"sessions": {}, "rate_per_s": rate, "requests": n_req, "slots_per_session": 8, "budget_gb": 160.0,
+           "schedules_mixed": {}, "schedules_fp64": {}}
     for label, prec in (("mixed", G.MIXED), ("fp64", G.FP64)):
         srv = Server(sessions, budget_bytes=160e9, slots=8, precision=prec, tol=args.tol, on_load=on_load,
                      new_stream=lambda: torch.cuda.Stream(), result_to=result_to,
                      stream_context=lambda s: torch.cuda.stream(s.stream))
         srv.run([req(n_req + k, name, 0.0) for k, name in enumerate(names)])  # load + graph capture
         torch.cuda.synchronize()
+        # each session's sweep schedule (and, mixed, FP32 cycles per step) by
+        # the autotuner, on a sample right-hand side in all its slots
+        t1 = time.perf_counter()
+        for k, s_ in enumerate(sessions):
+            g_ = I.charge_density_torch(s_.ctx["xc"], charges[n_req + k]).repeat(8, 1).contiguous()
+            sched = AT.tune(s_.tree, lambda: s_.tree.set_rhs(g_), prec, args.tol, reps=1,
+                            axes=("fine_sweeps", "coarse_sweeps", "inner_cycles"))
+            out["schedules_%s" % label][s_.name] = {"fine_sweeps": list(sched.fine_sweeps),
+                                                     "coarse_sweeps": list(sched.coarse_sweeps),
+                                                     "inner_cycles": sched.inner_cycles}
+        out["tuning_s_%s" % label] = time.perf_counter() - t1
+        srv.run([req(n_req + k, name, 0.0) for k, name in enumerate(names)])  # graphs of the tuned schedules
+        torch.cuda.synchronize()
         done = srv.run([req(i, names[int(pick[i])], float(arrive[i])) for i in range(n_req)])
         torch.cuda.synchronize()
         out[label] = summarize(done) | {"resident_gb": max(srv.peak_bytes, srv.resident_bytes()) / 1e9}
+        # the same requests arriving ten times faster: the loop's capacity
+        done = srv.run([req(i, names[int(pick[i])], float(arrive[i]) / 10) for i in range(n_req)])
+        torch.cuda.synchronize()
+        out[label + "_at_10x_rate"] = summarize(done)
     for s in sessions:
         if s.resident:
             out["sessions"][s.name] = {"leaf_cells": s.tree.n_leaf_cells, "workspace_gb": s.nbytes / 1e9}
