@@ -8,6 +8,7 @@ fast a solve reaches its tolerance but not what it converges to:
   (those launched one kernel per phase) and on the coarse levels (those in
   the cooperative launch), which trades cost per V-cycle against cycles,
 * the FP32 V-cycles per defect-correction step of the mixed path,
+* with several right-hand-side slots, the slots of a block per CTA,
 * the CTA size of the block kernels, the block-count limit of the
   cooperative coarse launch and the fused FP32 sweeps.
 
@@ -39,11 +40,12 @@ class Schedule:
     coop_max_blocks: int = 160
     fused: bool = False
     inner_cycles: int = 1              # FP32 V-cycles per defect-correction step (mixed)
+    slots_per_cta: int = 1             # slots of a block per CTA in the half-sweeps
     trials: list = field(default_factory=list, compare=False)
 
     def key(self):
         return (self.fine_sweeps, self.coarse_sweeps, self.cta_threads, self.coop_max_blocks, self.fused,
-                self.inner_cycles)
+                self.inner_cycles, self.slots_per_cta)
 
 
 def coop_levels(tree, coop_max_blocks):
@@ -60,6 +62,7 @@ def apply(tree, s: Schedule):
     tree.set_option("coop_max_blocks", s.coop_max_blocks)
     tree.set_option("fused_sweeps", 1 if s.fused else 0)
     tree.set_option("inner_cycles", s.inner_cycles)
+    tree.set_option("slots_per_cta", s.slots_per_cta)
     split = coop_levels(tree, s.coop_max_blocks)
     for l in range(tree.lmin, tree.lmax + 1):
         nd, nu = s.coarse_sweeps if l <= split else s.fine_sweeps
@@ -105,6 +108,7 @@ def tune(tree, set_rhs, precision=MIXED, tol=1e-8, reps=2, log=None, axes=None):
         ("fine_sweeps", [(1, 1), (2, 1), (1, 2), (2, 2), (3, 3)]),
         ("coarse_sweeps", [(1, 1), (2, 2), (4, 4)]),
         ("inner_cycles", [1, 2] if precision == MIXED else [1]),
+        ("slots_per_cta", [1, 2, 4] if tree.nrhs > 1 else [1]),
         ("coop_max_blocks", [0, 64, 160, 640]),
         ("fused", [False, True]),
     ]
@@ -158,6 +162,7 @@ def load_cached(path, key):
         return None
     v = dict(v)
     v.setdefault("inner_cycles", 1)
+    v.setdefault("slots_per_cta", 1)
     v["fine_sweeps"] = tuple(v["fine_sweeps"])
     v["coarse_sweeps"] = tuple(v["coarse_sweeps"])
     v["trials"] = []

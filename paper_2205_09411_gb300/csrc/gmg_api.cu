@@ -15,6 +15,7 @@
 #include "gmg_internal.h"
 #include "coarse_cycle.cuh"
 #include "efield.cuh"
+#include "slot_groups.cuh"
 #include "fused_sweeps.cuh"
 #include "kernels.cuh"
 
@@ -289,6 +290,10 @@ void set_smem_limits_nt() {
   kernel_attrs(k_resid_restrict<T, D, NT>, true);
   kernel_attrs(k_fas<T, D, NT>, true);
   kernel_attrs(k_prolong<T, D, NT, 64>, true);
+  if constexpr (NT == 8 || NT == 16) {
+    kernel_attrs(k_smooth_sg<T, D, NT, 2>, true);
+    kernel_attrs(k_smooth_sg<T, D, NT, 4>, true);
+  }
   kernel_attrs(k_prolong<T, D, NT, 128>, true);
   kernel_attrs(k_prolong<T, D, NT, 256>, true);
   kernel_attrs(k_resnorm<T, D, NT>, true);
@@ -332,6 +337,27 @@ void set_all_smem_limits() {
   }
   kernel_attrs(k_delay, false);
   done = true;
+}
+
+// Half-sweep of a level: one CTA per (block, slot), or per (block, group of
+// slots_per_cta slots) when the tree has several slots and the group's
+// tiles fit in shared memory.
+template <typename T, int D, int NT>
+void launch_smooth(const gmg_tree *t, const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int c, int threads,
+                   size_t sm, cudaStream_t s) {
+  const int sg = t->slots_per_cta;
+  if constexpr (NT == 8 || NT == 16) {
+    if (sg > 1 && t->nrhs > 1 && sg_smem_bytes<T>(D, NT, sg) <= 200 * 1024) {
+      const int grid = L.count * ((t->nrhs + sg - 1) / sg);
+      const size_t sms = sg_smem_bytes<T>(D, NT, sg);
+      if (sg == 2)
+        k_smooth_sg<T, D, NT, 2><<<grid, threads, sms, s>>>(V, L, Lp, c);
+      else
+        k_smooth_sg<T, D, NT, 4><<<grid, threads, sms, s>>>(V, L, Lp, c);
+      return;
+    }
+  }
+  k_smooth<T, D, NT><<<L.count * t->nrhs, threads, sm, s>>>(V, L, Lp, c);
 }
 
 // k_prolong with the CTA size of the level's block kernels
@@ -476,7 +502,7 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s, bool end_restrict, int top) {
       if (!fused)
         for (int k = 0; k < L.nd; k++)
           for (int c = 0; c < 2; c++)
-            launch(t, s, 0, P, l, [&] { k_smooth<T, D, NT><<<L.count * R, nt_l, sm, s>>>(V, L, Lp, c); });
+            launch(t, s, 0, P, l, [&] { launch_smooth<T, D, NT>(t, V, L, Lp, c, nt_l, sm, s); });
       launch(t, s, 1, P, l, [&] { k_resid_restrict<T, D, NT><<<L.count * R, nt_l, sm, s>>>(V, L, Lp); });
     });
     LvArgs Lpp = l - 2 >= t->lmin ? lv(t, l - 2) : Lp;
@@ -511,7 +537,7 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s, bool end_restrict, int top) {
       if (!fused)
         for (int k = 0; k < L.nu; k++)
           for (int c = 0; c < 2; c++)
-            launch(t, s, 0, P, l, [&] { k_smooth<T, D, NT><<<L.count * R, nt_l, sm, s>>>(V, L, Lp, c); });
+            launch(t, s, 0, P, l, [&] { launch_smooth<T, D, NT>(t, V, L, Lp, c, nt_l, sm, s); });
     });
     if (fused) launch_fused<T, D>(t, s, l, L.nu, L.off + other, L.off);  // back to the first buffer
   }
@@ -1498,6 +1524,10 @@ int gmg_set_option(gmg_tree *t, int option, long long value) {
       if (value < 0) return set_error("block limit must be >= 0"), GMG_ERR_INVALID_ARG;
       t->coop_max_blocks = (int)std::min<long long>(value, 1 << 30);
       if (t->bound) set_coop_split(t);
+      break;
+    case GMG_OPT_SLOTS_PER_CTA:
+      if (value != 1 && value != 2 && value != 4) return set_error("slots per CTA must be 1, 2 or 4"), GMG_ERR_INVALID_ARG;
+      t->slots_per_cta = (int)value;
       break;
     case GMG_OPT_INNER_CYCLES:
       if (value < 1 || value > 8) return set_error("inner cycles must be 1 .. 8"), GMG_ERR_INVALID_ARG;

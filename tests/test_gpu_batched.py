@@ -219,3 +219,26 @@ def test_many_waves_adaptive_slots_match_oracle():
             for r in range(i, R, 2):
                 err = np.abs(got[r] - ref).max() / np.abs(ref).max()
                 assert err <= 1e-12, "slot %d cycle %d: %.3e" % (r, k + 1, err)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_slot_groups_per_cta_give_identical_results(prec):
+    """Half-sweeps that take 2 or 4 slots of a block per CTA (five slots, so
+    one group is partial, and slots freeze at different cycles) give bit for
+    bit the solutions and cycle counts of one slot per CTA."""
+    import paper_2205_09411_gb300 as G
+    P = G.FP64 if prec == "fp64" else G.MIXED
+    p = parity_cases()["needle4"]
+    R = 5
+    out = []
+    for spc in (1, 2, 4):
+        t = gpu_problem(p, nrhs=R)
+        t.set_option("slots_per_cta", spc)
+        xc = t.leaf_centers()
+        g = np.stack([I.charge_density(xc, p["charges"][r % 4]) * (1 + r) for r in range(R)])
+        t.set_rhs(g)
+        st = t.solve(P, 1e-8, 80)
+        out.append((t.solution().copy(), [u["cycles"] for u in st["slots"]]))
+    for sol, cyc in out[1:]:
+        assert cyc == out[0][1]
+        assert np.array_equal(sol, out[0][0])
