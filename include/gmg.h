@@ -347,6 +347,8 @@ int gmg_profile_read(gmg_tree *tree, int cap, int *kind, int *prec, int *level, 
                                      up to the last such level) join the cooperative launch */
 #define GMG_OPT_INNER_CYCLES 7   /* [1] FP32 V-cycles per defect-correction step of GMG_MIXED
                                     (1 .. 8): more cycles per FP64 residual, fewer steps */
+#define GMG_OPT_FMG_STEPS 9      /* [0] each step of gmg_solve / gmg_iterate is an FMG cycle (FP64,
+                                    or the FP32 inner cycles of GMG_MIXED) instead of a V-cycle */
 #define GMG_OPT_SLOTS_PER_CTA 8  /* [1] with several slots, the half-sweeps of 8^3 / 16^3 blocks
                                     stage and update 1, 2 or 4 slots of a block per CTA (the
                                     block's tables and index arithmetic shared); same results */

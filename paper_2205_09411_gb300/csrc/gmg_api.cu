@@ -670,7 +670,7 @@ int mixed_step(gmg_tree *t, cudaStream_t s) {
   // e = 0 in the first FP32 phi buffer of every slot (frozen slots too: harmless)
   CUDA_TRY(cudaMemsetAsync(t->f_phi, 0, (size_t)t->nrhs * t->total_cells * sizeof(float), s));
   for (int k = 0; k < t->inner_cycles; k++) {
-    const int rc = vcycle_any<float>(t, s, k + 1 < t->inner_cycles);
+    const int rc = t->fmg_steps ? fmg_any<float>(t, s) : vcycle_any<float>(t, s, k + 1 < t->inner_cycles);
     if (rc) return rc;
   }
   launch(t, s, 8, 0, t->lmax, [&] {
@@ -1427,7 +1427,7 @@ int gmg_iterate_begin(gmg_tree *t, int precision, const int *active, int residua
                    [&](cudaStream_t cs) { return residual_any(t, cs, rout); });
   else
     rc = run_graph(t, mixed ? gmg_tree::kGraphCycleMixed : gmg_tree::kGraphCycle64, s, [&](cudaStream_t cs) {
-      int r = mixed ? mixed_step(t, cs) : vcycle_any<double>(t, cs);
+      int r = mixed ? mixed_step(t, cs) : (t->fmg_steps ? fmg_any<double>(t, cs) : vcycle_any<double>(t, cs));
       return r ? r : residual_any(t, cs, rout);
     });
   if (rc) return rc;
@@ -1497,7 +1497,7 @@ int gmg_solve(gmg_tree *t, int precision, double rel_tol, int max_cycles, gmg_st
       if (rc) return rc;
     }
     rc = run_graph(t, mixed ? gmg_tree::kGraphCycleMixed : gmg_tree::kGraphCycle64, s, [&](cudaStream_t cs) {
-      int r = mixed ? mixed_step(t, cs) : vcycle_any<double>(t, cs);
+      int r = mixed ? mixed_step(t, cs) : (t->fmg_steps ? fmg_any<double>(t, cs) : vcycle_any<double>(t, cs));
       return r ? r : residual_any(t, cs, rout);
     });
     if (rc) return rc;
@@ -1525,6 +1525,7 @@ int gmg_set_option(gmg_tree *t, int option, long long value) {
       t->coop_max_blocks = (int)std::min<long long>(value, 1 << 30);
       if (t->bound) set_coop_split(t);
       break;
+    case GMG_OPT_FMG_STEPS: t->fmg_steps = value != 0; break;
     case GMG_OPT_SLOTS_PER_CTA:
       if (value != 1 && value != 2 && value != 4) return set_error("slots per CTA must be 1, 2 or 4"), GMG_ERR_INVALID_ARG;
       t->slots_per_cta = (int)value;

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import gmg_inputs as I
-from _helpers import gpu_problem, oracle_problem
+from _helpers import gpu_problem, oracle_problem, parity_cases
 
 pytestmark = pytest.mark.gpu
 
@@ -189,3 +189,24 @@ def test_remesh_tree_solves_like_a_fresh_tree_and_transfer_helps():
     new.transfer_solution_from(old)
     st1 = new.solve(G.FP64, 1e-8, 80)
     assert st1["cycles"] < st0["cycles"], (st1, st0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_fmg_steps_solve(prec):
+    """Solve steps made of FMG cycles (FP64, or FP32 FMG inside the mixed
+    defect correction) reach 1e-8 by the oracle's own residual, in fewer
+    steps than V-cycle steps at most."""
+    import paper_2205_09411_gb300 as G
+    P = G.FP64 if prec == "fp64" else G.MIXED
+    p = parity_cases()["adaptive3d"]
+    steps = {}
+    for fmg in (0, 1):
+        t = gpu_problem(p)
+        t.set_option("fmg_steps", fmg)
+        st = t.solve(P, 1e-8, 80)
+        steps[fmg] = st["cycles"]
+        o = oracle_problem(p)
+        o.set_solution(t.solution())
+        l2, _, bn = o.residual()
+        assert st["rel_l2"] <= 1e-8 and l2 / bn <= 1.05e-8
+    assert steps[1] <= steps[0], steps
