@@ -21,36 +21,31 @@ struct GridBar {
   int pad;
 };
 
-constexpr long long kSpinLimit = 1LL << 24;  // ~1.7 s of 100 ns sleeps
+constexpr long long kSpinLimit = 1LL << 24;  // polls of a barrier before it reports a timeout (seconds)
 
-// Grid-wide barrier of a cooperative launch (all CTAs co-resident).  Thread
-// 0 of each CTA arrives on the counter; the last arrival resets it and
-// advances the generation; the others poll the generation with a bounded
-// number of sleeps and record GMG_ERR_TIMEOUT when it runs out, so a barrier
-// that can never complete ends the kernel instead of hanging it.  Returns
-// the same verdict to every thread of the CTA: false once any CTA has
-// recorded an error.
+// Grid-wide barrier of a cooperative launch (all CTAs co-resident).  The
+// arrival counter only grows during a launch (the host zeroes it before
+// each one): thread 0 of each CTA adds one and waits, with a bounded number
+// of short sleeps, until the counter reaches the next multiple of the CTA
+// count, so that one atomic and the polls are the barrier's whole cost.  A
+// wait that runs out records GMG_ERR_TIMEOUT, so a barrier that can never
+// complete ends the kernel instead of hanging it.  Returns the same verdict
+// to every thread of the CTA: false once any CTA has recorded an error.
 __device__ __forceinline__ bool grid_sync(GridBar *bar, unsigned int nctas, long long spin_limit) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int *vgen = &bar->gen;
+    volatile unsigned int *vcount = &bar->count;
     volatile int *verr = &bar->err;
-    const unsigned int g = *vgen;
     __threadfence();
-    if (atomicAdd(&bar->count, 1u) == nctas - 1) {
-      atomicExch(&bar->count, 0u);
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
-      long long spins = 0;
-      while (*vgen == g && *verr == 0) {
-        if (++spins > spin_limit) {
-          atomicCAS(&bar->err, 0, GMG_ERR_TIMEOUT);
-          break;
-        }
-        __nanosleep(100);
+    const unsigned int target = (atomicAdd(&bar->count, 1u) / nctas + 1) * nctas;
+    long long spins = 0;
+    while ((int)(*vcount - target) < 0 && *verr == 0) {
+      if (++spins > spin_limit) {
+        atomicCAS(&bar->err, 0, GMG_ERR_TIMEOUT);
+        break;
       }
+      __nanosleep(32);
     }
     __threadfence();
     s_ok = *verr == 0;
@@ -72,6 +67,7 @@ struct CycleArgs {
   GridBar *bar;
   long long spin_limit;
   int l_one;  // levels l_lo .. l_one hold one block per root and run one CTA per (root, slot) (< l_lo: none)
+  int cinv_off;  // byte offset of the tail's copy of its root's inverse in shared memory (-1: read from global)
 };
 
 // Block operations with the compile-time side NT for levels >= 1 and the
@@ -143,27 +139,78 @@ __device__ __forceinline__ void coarse_rows(const GmgView<T> &V, const LvArgs &L
 template <typename T, int D>
 struct TailLevel {
   T *tile, *b, *old;
-  unsigned char *flag;  // cells with a non-regular stencil (cut block)
-  int n, ncell;
-  long long stb;  // stencil offset of the level's block (-1: regular)
+  unsigned short *eidx;  // per cell: 0 regular stencil, e + 1 entry e of the block's cut list
+  T *cf;                 // the list's coefficients, coefficient k of entry e at cf[k * m + e]
+  int n, ncell, m;       // m: entries of the cut list (0: regular block)
   LvArgs L;
 };
 
+// shared memory of one tail level whose block lists at most mmax cells
 template <typename T, int D>
-__host__ __device__ __forceinline__ size_t tail_level_bytes(int n) {
+__host__ __device__ __forceinline__ size_t tail_level_bytes(int n, int mmax) {
   const int nc = D == 3 ? n * n * n : n * n;
-  return sizeof(T) * ((size_t)TileGeo<T, D>(n).size + 2 * (size_t)nc) + (size_t)((nc + 15) / 16 * 16);
+  const size_t cf = (sizeof(T) * (size_t)mmax * (2 * D + 1) + 15) / 16 * 16;
+  return sizeof(T) * ((size_t)TileGeo<T, D>(n).size + 2 * (size_t)nc) + (size_t)((2 * nc + 15) / 16 * 16) + cf;
+}
+
+// The tail functions take their level descriptors by value: the copies sit
+// in registers, where stores through the level's pointers cannot alias
+// them (descriptors read from shared memory would be reloaded after every
+// store).
+
+// stencil of cell c of a tail level: false for the regular one
+template <typename T, int D>
+__device__ __forceinline__ bool tail_cut(const TailLevel<T, D> &Q, int c, int *e) {
+  if (Q.m == 0) return false;
+  *e = (int)Q.eidx[c] - 1;
+  return *e >= 0;
+}
+
+// (x, y, z) of cell c of a block of side n: shifts and masks when n is a
+// power of two, divisions otherwise
+template <int D>
+__device__ __forceinline__ void cell_xyz_rt(int c, int n, int *x, int *y, int *z) {
+  if ((n & (n - 1)) == 0) {
+    const int lg = __ffs(n) - 1;
+    *x = c & (n - 1);
+    *y = (c >> lg) & (n - 1);
+    *z = D == 3 ? c >> (2 * lg) : 0;
+  } else {
+    cell_xyz<D>(c, n, x, y, z);
+  }
+}
+
+// the j-th cell of colour `color` ((x + y + z) mod 2) of a block of side n
+template <int D>
+__device__ __forceinline__ void colour_xyz(int j, int n, int color, int *x, int *y, int *z) {
+  const int hn = n / 2;
+  int xp;
+  if ((n & (n - 1)) == 0) {
+    const int lh = __ffs(hn) - 1;
+    xp = j & (hn - 1);
+    const int rest = j >> lh;
+    *y = rest & (n - 1);
+    *z = D == 3 ? rest >> (lh + 1) : 0;
+  } else {
+    xp = j % hn;
+    const int rest = j / hn;
+    *y = rest % n;
+    *z = D == 3 ? rest / n : 0;
+  }
+  *x = 2 * xp + ((*y + *z + color) & 1);
 }
 
 // wall ghosts of a single-block level (all faces are walls): sign * mirror
 template <typename T, int D>
-__device__ void tail_walls(const TailLevel<T, D> &Q, int wneu) {
+__device__ __forceinline__ void tail_walls(const TailLevel<T, D> Q, int wneu) {
   const TileGeo<T, D> G(Q.n);
   const int n = Q.n, nf = D == 3 ? n * n : n;
   for (int i = threadIdx.x; i < 2 * D * nf; i += blockDim.x) {
     const int f = i / nf, j = i - f * nf;
     const int a = f >> 1, side = f & 1;
-    const int u = j % n, v = D == 3 ? j / n : 0;
+    int u, v, dummy;
+    cell_xyz_rt<2>(j, n, &u, &v, &dummy);
+    if (D == 2) v = 0;
     const int gn = side ? n : -1, mn = side ? n - 1 : 0;
     const int gx = a == 0 ? gn : u, gy = a == 1 ? gn : (a == 0 ? u : v), gz = a == 2 ? gn : v;
     const int mx = a == 0 ? mn : u, my = a == 1 ? mn : (a == 0 ? u : v), mz = a == 2 ? mn : v;
@@ -173,23 +220,23 @@ __device__ void tail_walls(const TailLevel<T, D> &Q, int wneu) {
 }
 
 template <typename T, int D>
-__device__ void tail_smooth(const GmgView<T> &V, const TailLevel<T, D> &Q, int color) {
+__device__ __forceinline__ void tail_smooth(const GmgView<T> &V, const TailLevel<T, D> Q, int color) {
   tail_walls<T, D>(Q, V.wneu);
   const TileGeo<T, D> G(Q.n);
-  const int n = Q.n, hn = n / 2;
+  const int n = Q.n;
   const T h2 = T(Q.L.h2), inv2d = T(1.0 / (2 * D));
   for (int j = threadIdx.x; j < Q.ncell / 2; j += blockDim.x) {
-    const int rest = j / hn;
-    const int y = rest % n, z = D == 3 ? rest / n : 0;
-    const int x = 2 * (j % hn) + ((y + z + color) & 1);
+    int x, y, z;
+    colour_xyz<D>(j, n, color, &x, &y, &z);
     const int c = x + n * (y + n * z);
     const int t = G.idx(x, y, z);
     T nv;
-    if (Q.stb < 0 || !Q.flag[c]) {
+    int e;
+    if (!tail_cut(Q, c, &e)) {
       nv = (nb_sum<T, D>(Q.tile, t, G.sy, G.sz) - h2 * Q.b[c]) * inv2d;
     } else {
       T diag;
-      const T sum = offdiag_st<T, D>(V.st + Q.stb, Q.tile, t, G.sy, G.sz, Q.ncell, c, &diag);
+      const T sum = offdiag_st<T, D>(Q.cf, Q.tile, t, G.sy, G.sz, Q.m, e, &diag);
       nv = (Q.b[c] - sum) / diag;
     }
     Q.tile[t] = nv;
@@ -200,13 +247,15 @@ __device__ void tail_smooth(const GmgView<T> &V, const TailLevel<T, D> &Q, int c
 // residual of level F restricted into level C (C covered entirely by F):
 // phi_C <- mean phi_F, b_C <- mean r_F
 template <typename T, int D>
-__device__ void tail_resid_restrict(const GmgView<T> &V, const TailLevel<T, D> &F, const TailLevel<T, D> &Cq) {
+__device__ __forceinline__ void tail_resid_restrict(const GmgView<T> &V, const TailLevel<T, D> F,
+                                                    const TailLevel<T, D> Cq) {
   tail_walls<T, D>(F, V.wneu);
   const TileGeo<T, D> G(F.n), Gc(Cq.n);
   const int n = F.n, hn = Cq.n;
   const T inv_h2 = T(F.L.ih2), w = T(1.0 / (1 << D));
   for (int j = threadIdx.x; j < Cq.ncell; j += blockDim.x) {
-    const int qx = j % hn, qy = (j / hn) % hn, qz = D == 3 ? j / (hn * hn) : 0;
+    int qx, qy, qz;
+    cell_xyz_rt<D>(j, hn, &qx, &qy, &qz);
     T sp = T(0), sr = T(0);
 #pragma unroll
     for (int dz = 0; dz < (D == 3 ? 2 : 1); dz++)
@@ -218,8 +267,9 @@ __device__ void tail_resid_restrict(const GmgView<T> &V, const TailLevel<T, D> &
           const int c = x + n * (y + n * z);
           const int t = G.idx(x, y, z);
           sp = sp + F.tile[t];
-          sr = sr + resid_cell<T, D>(V.st, (F.stb >= 0 && F.flag[c]) ? F.stb : -1, F.tile, t, G.sy, G.sz, F.ncell,
-                                     c, inv_h2, F.b[c]);
+          int e;
+          const bool cut = tail_cut(F, c, &e);
+          sr = sr + resid_cell<T, D>(F.cf, cut ? 0 : -1, F.tile, t, G.sy, G.sz, F.m, e, inv_h2, F.b[c]);
         }
     Cq.tile[Gc.idx(qx, qy, qz)] = sp * w;
     Cq.b[j] = sr * w;
@@ -229,22 +279,23 @@ __device__ void tail_resid_restrict(const GmgView<T> &V, const TailLevel<T, D> &
 
 // FAS right-hand side b <- A phi + b (restricted residual), old <- phi
 template <typename T, int D>
-__device__ void tail_fas(const GmgView<T> &V, const TailLevel<T, D> &Q) {
+__device__ __forceinline__ void tail_fas(const GmgView<T> &V, const TailLevel<T, D> Q) {
   tail_walls<T, D>(Q, V.wneu);
   const TileGeo<T, D> G(Q.n);
   const int n = Q.n;
   const T inv_h2 = T(Q.L.ih2);
   for (int c = threadIdx.x; c < Q.ncell; c += blockDim.x) {
     int x, y, z;
-    cell_xyz<D>(c, n, &x, &y, &z);
+    cell_xyz_rt<D>(c, n, &x, &y, &z);
     const int t = G.idx(x, y, z);
     const T ph = Q.tile[t];
     T ap;
-    if (Q.stb < 0 || !Q.flag[c]) {
+    int e;
+    if (!tail_cut(Q, c, &e)) {
       ap = inv_h2 * (nb_sum<T, D>(Q.tile, t, G.sy, G.sz) - T(2 * D) * ph);
     } else {
       T diag;
-      const T sum = offdiag_st<T, D>(V.st + Q.stb, Q.tile, t, G.sy, G.sz, Q.ncell, c, &diag);
+      const T sum = offdiag_st<T, D>(Q.cf, Q.tile, t, G.sy, G.sz, Q.m, e, &diag);
       ap = diag * ph + sum;
     }
     Q.b[c] = ap + Q.b[c];
@@ -253,36 +304,53 @@ __device__ void tail_fas(const GmgView<T> &V, const TailLevel<T, D> &Q) {
   __syncthreads();
 }
 
-// correction phi - old of a single-block level at (x,y,z) in [-1,n]^D,
-// reflected at the walls (reading P)
+// The correction phi - old of a single-block level, in place in its tile
+// (the level is dead once it has been prolongated), with its ghost layer:
+// outside the block the correction is reflected at the walls, with the
+// homogeneous sign of each wall crossed (reading P).
 template <typename T, int D>
-__device__ __forceinline__ T tail_corr(const TailLevel<T, D> &Q, int x, int y, int z, int wneu) {
-  const TileGeo<T, D> G(Q.n);
-  const int n = Q.n;
-  T sg = T(1);
-  int p[3] = {x, y, z};
-#pragma unroll
-  for (int d = 0; d < D; d++) {
-    if (p[d] < 0) {
-      p[d] = 0;
-      sg *= ((wneu >> (2 * d)) & 1) ? T(1) : T(-1);
-    } else if (p[d] >= n) {
-      p[d] = n - 1;
-      sg *= ((wneu >> (2 * d + 1)) & 1) ? T(1) : T(-1);
-    }
+__device__ __forceinline__ void tail_corr_fill(const TailLevel<T, D> C, int wneu) {
+  const TileGeo<T, D> G(C.n);
+  const int n = C.n;
+  for (int c = threadIdx.x; c < C.ncell; c += blockDim.x) {
+    int x, y, z;
+    cell_xyz_rt<D>(c, n, &x, &y, &z);
+    const int t = G.idx(x, y, z);
+    C.tile[t] = C.tile[t] - C.old[c];
   }
-  const int c = p[0] + n * (p[1] + (D == 3 ? n * p[2] : 0));
-  return sg * (Q.tile[G.idx(p[0], p[1], p[2])] - Q.old[c]);
+  __syncthreads();
+  const int m = n + 2, tot = D == 3 ? m * m * m : m * m;
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    const int p[3] = {i % m - 1, (i / m) % m - 1, D == 3 ? i / (m * m) - 1 : 0};
+    int q[3] = {p[0], p[1], p[2]};
+    T sg = T(1);
+    bool out = false;
+#pragma unroll
+    for (int d = 0; d < D; d++) {
+      if (p[d] < 0) {
+        q[d] = 0;
+        sg *= ((wneu >> (2 * d)) & 1) ? T(1) : T(-1);
+        out = true;
+      } else if (p[d] >= n) {
+        q[d] = n - 1;
+        sg *= ((wneu >> (2 * d + 1)) & 1) ? T(1) : T(-1);
+        out = true;
+      }
+    }
+    if (out) C.tile[G.idx(p[0], p[1], p[2])] = sg * C.tile[G.idx(q[0], q[1], q[2])];
+  }
+  __syncthreads();
 }
 
 // phi_F += trilinear prolongation of the correction of level C
 template <typename T, int D>
-__device__ void tail_prolong(const GmgView<T> &V, const TailLevel<T, D> &F, const TailLevel<T, D> &Cq) {
-  const TileGeo<T, D> G(F.n);
+__device__ __forceinline__ void tail_prolong(const GmgView<T> &V, const TailLevel<T, D> F, const TailLevel<T, D> Cq) {
+  tail_corr_fill<T, D>(Cq, V.wneu);
+  const TileGeo<T, D> G(F.n), Gc(Cq.n);
   const int n = F.n;
   for (int c = threadIdx.x; c < F.ncell; c += blockDim.x) {
     int x, y, z;
-    cell_xyz<D>(c, n, &x, &y, &z);
+    cell_xyz_rt<D>(c, n, &x, &y, &z);
     const int u[3] = {x >> 1, y >> 1, z >> 1};
     const int o[3] = {(x & 1) ? 1 : -1, (y & 1) ? 1 : -1, (z & 1) ? 1 : -1};
     T v = T(0);
@@ -294,7 +362,7 @@ __device__ void tail_prolong(const GmgView<T> &V, const TailLevel<T, D> &F, cons
         for (int sx = 0; sx < 2; sx++) {
           T wgt = (sx ? T(0.25) : T(0.75)) * (sy ? T(0.25) : T(0.75));
           if (D == 3) wgt *= sz ? T(0.25) : T(0.75);
-          v = v + wgt * tail_corr<T, D>(Cq, u[0] + sx * o[0], u[1] + sy * o[1], D == 3 ? u[2] + sz * o[2] : 0, V.wneu);
+          v = v + wgt * Cq.tile[Gc.idx(u[0] + sx * o[0], u[1] + sy * o[1], D == 3 ? u[2] + sz * o[2] : 0)];
         }
     F.tile[G.idx(x, y, z)] += v;
   }
@@ -306,39 +374,69 @@ __device__ void tail_cycle(const GmgView<T> &V, const LevelSet &LS, const CycleA
                            unsigned char *smem_raw) {
   constexpr int kMaxTail = 12;
   __shared__ TailLevel<T, D> Q[kMaxTail];  // descriptors in shared memory, not per-thread local memory
-  if (threadIdx.x == 0) {
-  T *p = reinterpret_cast<T *>(smem_raw);
-  for (int l = top; l >= A.l_lo; l--) {
-    TailLevel<T, D> &q = Q[top - l];
-    q.L = LS.lv[l - LS.lmin];
-    q.n = q.L.n;
-    q.ncell = D == 3 ? q.n * q.n * q.n : q.n * q.n;
-    q.L.first += root;  // this root's block of the level
-    q.L.off += (long long)root * q.ncell;
-    q.L.poff += (long long)root * q.ncell;
-    q.stb = V.st_base[q.L.first];
-    q.tile = p;
-    p += TileGeo<T, D>(q.n).size;
-    q.b = p;
-    p += q.ncell;
-    q.old = p;
-    p += q.ncell;
-    q.flag = reinterpret_cast<unsigned char *>(p);
-    p += (q.ncell + 15) / 16 * 16 / sizeof(T);
-  }
+  __shared__ int s_m[kMaxTail], s_e0[kMaxTail];
+  const int ntl = top - A.l_lo + 1;
+  if ((int)threadIdx.x < ntl) {  // the levels' cut lists, read in parallel
+    const int4 cl = V.cut_list[LS.lv[top - (int)threadIdx.x - LS.lmin].first + root];
+    s_m[threadIdx.x] = cl.y + cl.z;
+    s_e0[threadIdx.x] = cl.x;
   }
   __syncthreads();
-  for (int l = top; l >= A.l_lo; l--) {  // flags of cut levels
-    const TailLevel<T, D> &q = Q[top - l];
-    if (q.stb >= 0)
-      for (int c = threadIdx.x; c < q.ncell; c += blockDim.x) q.flag[c] = V.spec[q.stb / (2 * D + 1) + c];
+  if (threadIdx.x == 0) {
+    T *p = reinterpret_cast<T *>(smem_raw);
+    for (int l = top; l >= A.l_lo; l--) {
+      TailLevel<T, D> &q = Q[top - l];
+      q.L = LS.lv[l - LS.lmin];
+      q.n = q.L.n;
+      q.ncell = D == 3 ? q.n * q.n * q.n : q.n * q.n;
+      q.L.first += root;  // this root's block of the level
+      q.L.off += (long long)root * q.ncell;
+      q.L.poff += (long long)root * q.ncell;
+      q.m = s_m[top - l];
+      q.tile = p;
+      p += TileGeo<T, D>(q.n).size;
+      q.b = p;
+      p += q.ncell;
+      q.old = p;
+      p += q.ncell;
+      q.eidx = reinterpret_cast<unsigned short *>(p);
+      p += (2 * q.ncell + 15) / 16 * 16 / sizeof(T);
+      q.cf = p;
+      p += (sizeof(T) * (size_t)q.m * (2 * D + 1) + 15) / 16 * 16 / sizeof(T);
+    }
+  }
+  __syncthreads();
+  // cut lists of the tail levels: entry index per cell, coefficients
+  for (int l = top; l >= A.l_lo; l--) {
+    const TailLevel<T, D> q = Q[top - l];
+    if (q.m)
+      for (int c = threadIdx.x; c < q.ncell; c += blockDim.x) q.eidx[c] = 0;
+  }
+  __syncthreads();
+  for (int l = top; l >= A.l_lo; l--) {
+    const TailLevel<T, D> q = Q[top - l];
+    if (!q.m) continue;
+    const int e0 = s_e0[top - l];
+    for (int e = threadIdx.x; e < q.m; e += blockDim.x) {
+      q.eidx[V.cut_cell[e0 + e]] = (unsigned short)(e + 1);
+#pragma unroll
+      for (int k = 0; k < 2 * D + 1; k++) q.cf[k * q.m + e] = V.cut_coef[k * V.n_cut + e0 + e];
+    }
+  }
+  // the root's coarse inverse, copied while the tail smooths its way down
+  const double *cinv = A.cinv + (size_t)root * A.ncr * A.ncr;
+  if (A.cinv_off >= 0) {
+    double *dst = reinterpret_cast<double *>(smem_raw + A.cinv_off);
+    for (int i = threadIdx.x; i < A.ncr * A.ncr; i += blockDim.x) cp_async_elem(dst + i, cinv + i);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    cinv = dst;
   }
   {  // phi and b of the top tail level from global memory
     const TailLevel<T, D> &q = Q[0];
     const TileGeo<T, D> G(q.n);
     for (int c = threadIdx.x; c < q.ncell; c += blockDim.x) {
       int x, y, z;
-      cell_xyz<D>(c, q.n, &x, &y, &z);
+      cell_xyz_rt<D>(c, q.n, &x, &y, &z);
       q.tile[G.idx(x, y, z)] = V.phi[q.L.poff + c];
       q.b[c] = V.b[q.L.off + c];
     }
@@ -354,10 +452,13 @@ __device__ void tail_cycle(const GmgView<T> &V, const LevelSet &LS, const CycleA
     tail_fas<T, D>(V, Cq);
   }
   {  // exact solve on l_lo, FP64 accumulation, one warp per row
+    if (A.cinv_off >= 0) {
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
+      __syncthreads();
+    }
     const TailLevel<T, D> &q = Q[top - A.l_lo];
     const TileGeo<T, D> G(q.n);
     const int lane = threadIdx.x & 31;
-    const double *cinv = A.cinv + (size_t)root * A.ncr * A.ncr;
     for (int row = threadIdx.x >> 5; row < A.ncr; row += blockDim.x / 32) {
       const double *a = cinv + (size_t)row * A.ncr;
       double s = 0.0;
@@ -385,7 +486,7 @@ __device__ void tail_cycle(const GmgView<T> &V, const LevelSet &LS, const CycleA
     const TileGeo<T, D> G(q.n);
     for (int c = threadIdx.x; c < q.ncell; c += blockDim.x) {
       int x, y, z;
-      cell_xyz<D>(c, q.n, &x, &y, &z);
+      cell_xyz_rt<D>(c, q.n, &x, &y, &z);
       V.phi[q.L.poff + c] = q.tile[G.idx(x, y, z)];
     }
   }
@@ -409,7 +510,7 @@ __global__ void __launch_bounds__(kCoopThreads) k_cycle_coop(GmgView<T> V, const
       if (const GmgView<T> W = slot_view(V, r_); true)
   // levels l_hi .. l_one + 1: every CTA, grid barrier between phases
   for (int l = A.l_hi; l > A.l_lo && l > A.l_one; l--) {
-    const LvArgs L = GMG_LV(l), Lp = GMG_LV(l - 1);
+    const LvArgs &L = GMG_LV(l), &Lp = GMG_LV(l - 1);  // read from shared memory, not held in registers
     for (int k = 0; k < L.nd; k++)
       for (int c = 0; c < 2; c++) {
         GMG_ITEMS(L) {
@@ -423,7 +524,7 @@ __global__ void __launch_bounds__(kCoopThreads) k_cycle_coop(GmgView<T> V, const
       __syncthreads();
     }
     if (!grid_sync(A.bar, G, A.spin_limit)) return;
-    const LvArgs Lpp = l - 2 >= LS.lmin ? GMG_LV(l - 2) : Lp;
+    const LvArgs &Lpp = l - 2 >= LS.lmin ? GMG_LV(l - 2) : Lp;
     GMG_ITEMS(Lp) {
       fas_any<T, D, NT>(W, Lp, Lpp, bid, smem_raw);
       __syncthreads();
@@ -446,7 +547,7 @@ __global__ void __launch_bounds__(kCoopThreads) k_cycle_coop(GmgView<T> V, const
   }
   if (A.l_hi > A.l_one && !grid_sync(A.bar, G, A.spin_limit)) return;
   for (int l = (A.l_one >= A.l_lo ? A.l_one : A.l_lo) + 1; l <= A.l_hi; l++) {
-    const LvArgs L = GMG_LV(l), Lp = GMG_LV(l - 1);
+    const LvArgs &L = GMG_LV(l), &Lp = GMG_LV(l - 1);  // read from shared memory, not held in registers
     GMG_ITEMS(L) {
       prolong_any<T, D, NT>(W, L, Lp, bid, smem_raw);
       __syncthreads();

@@ -163,6 +163,7 @@ int forest_merge(gmg_tree *const *trees, int n, gmg_tree **out) {
   F->adaptive = false;
   for (int id : F->leaf_ids_h)
     if (F->blocks[id].level != F->lmax) F->adaptive = true;
+  build_cut_lists(F);
   F->stencils_ready = true;
   *out = F;
   return GMG_OK;

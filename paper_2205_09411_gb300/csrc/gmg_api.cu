@@ -202,6 +202,10 @@ GmgView<T> view(gmg_tree *t);
 template <>
 GmgView<double> view<double>(gmg_tree *t) {
   GmgView<double> v;
+  v.cut_list = t->d_cut_list;
+  v.cut_cell = t->d_cut_cell;
+  v.cut_coef = t->d_cut_coef;
+  v.n_cut = t->n_cut;
   v.nbr = t->d_nbr;
   v.pnb = t->d_pnb;
   v.parent = t->d_parent;
@@ -229,6 +233,10 @@ GmgView<double> view<double>(gmg_tree *t) {
 template <>
 GmgView<float> view<float>(gmg_tree *t) {
   GmgView<float> v;
+  v.cut_list = t->d_cut_list;
+  v.cut_cell = t->d_cut_cell;
+  v.cut_coef = t->f_cut_coef;
+  v.n_cut = t->n_cut;
   v.nbr = t->d_nbr;
   v.pnb = t->d_pnb;
   v.parent = t->d_parent;
@@ -389,12 +397,19 @@ int coop_cycle(gmg_tree *t, cudaStream_t s, int ls) {
   if (t->ncr <= 256 && (t->nroot > 1 || t->cb[0] * t->cb[1] * t->cb[2] == 1))
     for (int l = t->lmin; l <= ls && t->lev(l).count == t->nroot; l++) {
       const int n = t->lev(l).n;
-      const size_t add = tail_level_bytes<T, D>(n);
+      const size_t add = tail_level_bytes<T, D>(n, t->cut_max_h[l - t->lmin]);
       if (tail_bytes + add > 160 * 1024 || l - t->lmin >= 11) break;
       tail_bytes += add;
       l_one = l;
     }
-  CycleArgs A{t->lmin, ls, t->ncr, t->nroot, t->d_cinv, t->d_bar, t->spin_limit, l_one};
+  // the tail's coarse inverse in shared memory when it fits beside the levels
+  int cinv_off = -1;
+  const size_t cinv_bytes = sizeof(double) * (size_t)t->ncr * t->ncr;
+  if (l_one >= t->lmin && tail_bytes + cinv_bytes <= 192 * 1024) {
+    cinv_off = (int)tail_bytes;
+    tail_bytes += cinv_bytes;
+  }
+  CycleArgs A{t->lmin, ls, t->ncr, t->nroot, t->d_cinv, t->d_bar, t->spin_limit, l_one, cinv_off};
   size_t sm = 0;
   int maxb = l_one >= t->lmin ? t->nroot : 1;
   for (int l = t->lmin; l <= ls; l++) {
@@ -735,7 +750,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
   size_t nbr, pnb, parent, pofs, flags, leaf, cbase, st_base, bt_base, phi, b, old, fphi, fb, fold, st, fst, bterm, cinv,
       partials, red, active, tree_of, tree_blocks, tree_boff, bar, spec, lvtab, cellflag, mask_base, dist, bphib,
-      dist_base, wallv, wallv_base, leafpos, total;
+      dist_base, wallv, wallv_base, leafpos, cut_list, cut_cell, cut_coef, fcut_coef, total;
 };
 
 Layout layout(const gmg_tree *t) {
@@ -783,6 +798,10 @@ Layout layout(const gmg_tree *t) {
   L.leafpos = take(nb * sizeof(int));
   L.bar = take(sizeof(GridBar));
   L.spec = take(t->spec_h.size());
+  L.cut_list = take(nb * sizeof(int4));
+  L.cut_cell = take((size_t)t->n_cut * sizeof(int));
+  L.cut_coef = take(t->cut_coef_h.size() * sizeof(double));
+  L.fcut_coef = take(t->cut_coef_h.size() * sizeof(float));
   L.lvtab = take(kMaxLevels * sizeof(LvArgs));
   L.total = o;
   return L;
@@ -1108,6 +1127,10 @@ int gmg_tree_bind(gmg_tree *t, void *device_ptr, size_t bytes) {
   t->d_leafpos = reinterpret_cast<int *>(w + L.leafpos);
   t->d_bar = reinterpret_cast<GridBar *>(w + L.bar);
   t->d_spec = reinterpret_cast<unsigned char *>(w + L.spec);
+  t->d_cut_list = reinterpret_cast<int4 *>(w + L.cut_list);
+  t->d_cut_cell = reinterpret_cast<int *>(w + L.cut_cell);
+  t->d_cut_coef = reinterpret_cast<double *>(w + L.cut_coef);
+  t->f_cut_coef = reinterpret_cast<float *>(w + L.fcut_coef);
   t->d_lvtab = reinterpret_cast<LvArgs *>(w + L.lvtab);
   const size_t nb = t->blocks.size();
   std::vector<long long> cbase(nb);
@@ -1157,6 +1180,13 @@ int gmg_tree_bind(gmg_tree *t, void *device_ptr, size_t bytes) {
     k_to_float<<<grid_for((long long)t->stencil_h.size()), 256>>>(t->d_st, t->f_st, (long long)t->stencil_h.size());
   }
   if (!t->spec_h.empty()) CUDA_TRY(cudaMemcpy(t->d_spec, t->spec_h.data(), t->spec_h.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(t->d_cut_list, t->cut_list_h.data(), nb * sizeof(int4), cudaMemcpyHostToDevice));
+  if (t->n_cut) {
+    CUDA_TRY(cudaMemcpy(t->d_cut_cell, t->cut_cell_h.data(), (size_t)t->n_cut * sizeof(int), cudaMemcpyHostToDevice));
+    const long long nco = (long long)t->cut_coef_h.size();
+    CUDA_TRY(cudaMemcpy(t->d_cut_coef, t->cut_coef_h.data(), nco * sizeof(double), cudaMemcpyHostToDevice));
+    k_to_float<<<grid_for(nco), 256>>>(t->d_cut_coef, t->f_cut_coef, nco);
+  }
   {
     const int rc = upload_lvtab(t);
     if (rc) return rc;

@@ -66,6 +66,14 @@ struct GmgView {
   T *phi, *b, *old;      // level fields (all levels, block-contiguous)
   const T *st;           // stencil pool: per cut block (2D+1) x ncell, [diag, -x, +x, -y, +y, -z, +z]
   const unsigned char *spec;  // per cut block ncell flags at st_base/(2D+1): 1 = stencil differs from the regular one
+  // cut lists: the flagged cells of each cut block, colour 0 ((x+y+z) even)
+  // then colour 1; cut_list[b] = {first entry, colour-0 count, colour-1
+  // count, 0}; entry e holds its cell index cut_cell[e] and its 2D+1
+  // coefficients cut_coef[k * n_cut + e] (k as in st)
+  const int4 *cut_list;
+  const int *cut_cell;
+  const T *cut_coef;
+  long long n_cut;
   int wneu;              // bit w set: wall w is Neumann (ghost +phi), else Dirichlet (-phi)
   // right-hand-side slots: slot r's fields start r * rs_phi (phi) and
   // r * rs_f (b, old) elements after slot 0's; tables and stencils are shared
@@ -136,6 +144,12 @@ struct gmg_tree {
   std::vector<double> stencil_h;  // concatenated per cut block: (2D+1) x ncell
   std::vector<double> bterm_h;    // concatenated per block with boundary terms: ncell
   std::vector<uint8_t> spec_h;    // per cut block ncell flags (any d < 1), parallel to stencil_h
+  // cut lists (the device's copy of the flagged cells, per colour; see GmgView)
+  std::vector<int> cut_list_h;     // [nb][4]
+  std::vector<int> cut_cell_h;     // [n_cut]
+  std::vector<double> cut_coef_h;  // [(2D+1) * n_cut]
+  std::vector<int> cut_max_h;      // per level (l - lmin): largest entry count of one block
+  long long n_cut = 0;
   std::vector<double> dist_h;     // per cut block: ncell x 2D distances (inspection, field evaluation)
   std::vector<double> bphib_h;    // parallel to dist_h: boundary value phi_b(x0) where d < 1
   std::vector<long long> dist_base_h;
@@ -165,6 +179,10 @@ struct gmg_tree {
   int *d_leafpos = nullptr;
   float *f_st = nullptr;
   unsigned char *d_spec = nullptr;
+  int4 *d_cut_list = nullptr;
+  int *d_cut_cell = nullptr;
+  double *d_cut_coef = nullptr;
+  float *f_cut_coef = nullptr;
   gmg::LvArgs *d_lvtab = nullptr;  // per-level descriptors (phi in the first buffer)
   double *h_red = nullptr;  // pinned host mirror of d_red ([units][4])
   long long launches = 0;
@@ -225,4 +243,5 @@ void set_error(const std::string &msg);
 int build_tree(gmg_tree *T, const gmg_domain *dom);
 int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, double phib_const,
                const gmg_tree *reuse = nullptr);
+void build_cut_lists(gmg_tree *T);
 }  // namespace gmg

@@ -217,9 +217,14 @@ __device__ __forceinline__ unsigned char *level_flags(T *sbv, int ncell) {
 // FAS: the tile of a covered block for the FAS kernel, whose phi (and that
 // of covered neighbours) the restriction left in `old` (see
 // resid_restrict_block); leaf neighbours' phi is read from phi.
-template <typename T, int D, int NT, bool FAS = false>
-__device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, T *tile,
-                          T *sbv = nullptr, unsigned char *sflag = nullptr, long long sb = -1) {
+struct NoMid {
+  __device__ void operator()() const {}
+};
+
+template <typename T, int D, int NT, bool FAS = false, typename Mid = NoMid>
+__device__ __forceinline__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, T *tile,
+                                          T *sbv = nullptr, unsigned char *sflag = nullptr, long long sb = -1,
+                                          Mid mid = Mid()) {
   __shared__ int s_nb[6];
   __shared__ int s_fl;
   const int n = NT ? NT : L.n;
@@ -258,6 +263,7 @@ __device__ void load_tile(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
     }
   }
   __syncthreads();
+  mid();
   const int fl = s_fl;
   const int nf = D == 3 ? n * n : n;
   // face f = 2 axis + side: ghost cell (gx,gy,gz) from the cell (qx,qy,qz) of
@@ -328,19 +334,40 @@ __device__ __forceinline__ T nb_sum(const T *tile, int t, int sy, int sz) {
   return s;
 }
 
-// Off-diagonal sum and diagonal from a cut block's stored stencil (read
-// from global memory, the 2D + 1 coefficients of a cell in one batch).
+// Off-diagonal sum of a stored stencil a[0 .. 2D] (diagonal first, then the
+// faces -x, +x, -y, +y, -z, +z) at tile index t.
+template <typename T, int D>
+__device__ __forceinline__ T offdiag_of(const T *a, const T *tile, int t, int sy, int sz) {
+  T s = a[1] * tile[t - 1] + a[2] * tile[t + 1] + a[3] * tile[t - sy] + a[4] * tile[t + sy];
+  if (D == 3) s += a[5] * tile[t - sz] + a[6] * tile[t + sz];
+  return s;
+}
+
+// Off-diagonal sum and diagonal of cell c from a stencil array with
+// coefficient k at st[k * ncell + c].
 template <typename T, int D>
 __device__ __forceinline__ T offdiag_st(const T *__restrict__ st, const T *tile, int t, int sy, int sz, int ncell,
                                         int c, T *diag) {
   T cf[2 * D + 1];
 #pragma unroll
   for (int k = 0; k < 2 * D + 1; k++) cf[k] = st[k * ncell + c];
-  T s = cf[1] * tile[t - 1] + cf[2] * tile[t + 1] + cf[3] * tile[t - sy] + cf[4] * tile[t + sy];
-  if (D == 3) s += cf[5] * tile[t - sz] + cf[6] * tile[t + sz];
   *diag = cf[0];
-  return s;
+  return offdiag_of<T, D>(cf, tile, t, sy, sz);
 }
+
+// One entry of a cut list in registers: the cell (index in its block) and
+// its 2D + 1 coefficients.  A CTA fetches its block's entries while the
+// tile loads, so that no cell waits on a stencil read.
+template <typename T, int D>
+struct CutCell {
+  int c;
+  T a[2 * D + 1];
+  __device__ __forceinline__ void fetch(const GmgView<T> &V, long long e) {
+    c = V.cut_cell[e];
+#pragma unroll
+    for (int k = 0; k < 2 * D + 1; k++) a[k] = V.cut_coef[k * V.n_cut + e];
+  }
+};
 
 // r = b - A phi at cell c (tile index t); the regular 5/7-point form costs
 // 2D - 1 adds and two fused multiply-adds (FP64 throughput bounds that path).
@@ -385,7 +412,13 @@ __device__ void smooth_block(const GmgView<T> &V, const LvArgs &L, const LvArgs 
   unsigned char *sfl = level_flags(sbv, NCELL);
   const long long pbase = L.poff + (long long)(bid - L.first) * NCELL;
   const long long sb = V.st_base[bid];
-  load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv, sfl, sb);
+  // this colour's cut list: entry e0 + i goes to thread i (prefetched)
+  const int4 cl = V.cut_list[bid];
+  const int e0 = cl.x + (color ? cl.y : 0), m = color ? cl.z : cl.y;
+  CutCell<T, D> q;
+  load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv, sfl, sb, [&] {
+    if ((int)threadIdx.x < m) q.fetch(V, e0 + threadIdx.x);
+  });
   const T h2 = T(L.h2), inv2d = T(1.0 / (2 * D));
   const int nhalf = NCELL / 2;
   for (int j = threadIdx.x; j < nhalf; j += blockDim.x) {
@@ -393,16 +426,20 @@ __device__ void smooth_block(const GmgView<T> &V, const LvArgs &L, const LvArgs 
     const int y = rest % n, z = D == 3 ? rest / n : 0;
     const int x = 2 * (j % hn) + ((y + z + color) & 1);
     const int c = x + n * (y + n * z);
+    if (sb >= 0 && sfl[c]) continue;  // a listed cell
+    V.phi[pbase + c] = (nb_sum<T, D>(tile, G.idx(x, y, z), G.sy, G.sz) - h2 * sbv[c]) * inv2d;
+  }
+  auto upd = [&](const CutCell<T, D> &u) {
+    int x, y, z;
+    cell_xyz<D>(u.c, n, &x, &y, &z);
     const int t = G.idx(x, y, z);
-    T nv;
-    if (sb < 0 || !sfl[c]) {
-      nv = (nb_sum<T, D>(tile, t, G.sy, G.sz) - h2 * sbv[c]) * inv2d;
-    } else {
-      T diag;
-      const T s = offdiag_st<T, D>(V.st + sb, tile, t, G.sy, G.sz, NCELL, c, &diag);
-      nv = (sbv[c] - s) / diag;
-    }
-    V.phi[pbase + c] = nv;
+    V.phi[pbase + u.c] = (sbv[u.c] - offdiag_of<T, D>(u.a, tile, t, G.sy, G.sz)) / u.a[0];
+  };
+  if ((int)threadIdx.x < m) upd(q);
+  for (int i = threadIdx.x + blockDim.x; i < m; i += blockDim.x) {  // lists longer than the CTA
+    CutCell<T, D> u;
+    u.fetch(V, e0 + i);
+    upd(u);
   }
 }
 
@@ -413,6 +450,32 @@ __global__ void __launch_bounds__(kThreads) k_smooth(GmgView<T> V, LvArgs L, LvA
   GmgView<T> W;
   if (!slot_item(V, L, &bid, &W)) return;
   smooth_block<T, D, NT>(W, L, Lp, bid, color, smem_raw);
+}
+
+// Residuals of a block's listed cells (both colours) in place of their b
+// in shared memory: sbv[c] <- b_c - (diag phi_c + off-diagonal sum), the
+// stencil branch of resid_cell.  Entry i of thread i arrives prefetched in
+// q; longer lists are fetched here.  Ends with a barrier when the block has
+// a list (m is the same in every thread).
+template <typename T, int D>
+__device__ __forceinline__ void cut_residuals(const GmgView<T> &V, const TileGeo<T, D> &G, int n, const T *tile,
+                                              T *sbv, int4 cl, const CutCell<T, D> &q) {
+  const int m = cl.y + cl.z;
+  if (m == 0) return;
+  auto res = [&](const CutCell<T, D> &u) {
+    int x, y, z;
+    cell_xyz<D>(u.c, n, &x, &y, &z);
+    const int t = G.idx(x, y, z);
+    sbv[u.c] = sbv[u.c] - (u.a[0] * tile[t] + offdiag_of<T, D>(u.a, tile, t, G.sy, G.sz));
+  };
+  const int i = threadIdx.x, bd = blockDim.x;
+  if (i < m) res(q);
+  for (int k = i + bd; k < m; k += bd) {
+    CutCell<T, D> u;
+    u.fetch(V, cl.x + k);
+    res(u);
+  }
+  __syncthreads();
 }
 
 // Residual r = b - A phi (Eq. (residual)) of every cell, restricted to the
@@ -431,7 +494,13 @@ __device__ void resid_restrict_block(const GmgView<T> &V, const LvArgs &L, const
   unsigned char *sfl = level_flags(sbv, NCELL);
   const long long sb = V.st_base[bid];
   const int P = V.parent[bid], po = V.pofs[bid];
-  load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv, sfl, sb);
+  const int4 cl = V.cut_list[bid];
+  const int m = cl.y + cl.z;
+  CutCell<T, D> q;
+  load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv, sfl, sb, [&] {
+    if ((int)threadIdx.x < m) q.fetch(V, cl.x + threadIdx.x);
+  });
+  cut_residuals<T, D>(V, G, n, tile, sbv, cl, q);
   const T inv_h2 = T(L.ih2);
   const int pofs[3] = {po & 1023, (po >> 10) & 1023, (po >> 20) & 1023};
   const long long pbase = Lp.off + (long long)(P - Lp.first) * Lp.ncell;
@@ -451,7 +520,8 @@ __device__ void resid_restrict_block(const GmgView<T> &V, const LvArgs &L, const
           const int c = x + n * (y + n * z);
           const int t = G.idx(x, y, z);
           sp = sp + tile[t];
-          sr = sr + resid_cell<T, D>(V.st, (sb >= 0 && sfl[c]) ? sb : -1, tile, t, G.sy, G.sz, NCELL, c, inv_h2, sbv[c]);
+          sr = sr + ((sb >= 0 && sfl[c]) ? sbv[c]  // a listed cell: its residual
+                                         : resid_cell<T, D>(nullptr, -1, tile, t, G.sy, G.sz, NCELL, c, inv_h2, sbv[c]));
         }
     const long long pc = pbase + (pofs[0] + qx) + pn * ((pofs[1] + qy) + (D == 3 ? pn * (pofs[2] + qz) : 0));
     V.old[pc] = sp * w;
@@ -489,7 +559,28 @@ __device__ void fas_block(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
   T *sbv = tile + G.size;
   unsigned char *sfl = level_flags(sbv, NCELL);
   const long long sb = V.st_base[bid];
-  load_tile<T, D, NT, true>(V, L, Lp, bid, tile, sbv, sfl, sb);
+  const int4 cl = V.cut_list[bid];
+  const int m = cl.y + cl.z;
+  CutCell<T, D> q;
+  load_tile<T, D, NT, true>(V, L, Lp, bid, tile, sbv, sfl, sb, [&] {
+    if ((int)threadIdx.x < m) q.fetch(V, cl.x + threadIdx.x);
+  });
+  if (m) {  // listed cells: sbv[c] <- A phi + sbv[c] with the stored stencil
+    auto fas = [&](const CutCell<T, D> &u) {
+      int x, y, z;
+      cell_xyz<D>(u.c, n, &x, &y, &z);
+      const int t = G.idx(x, y, z);
+      sbv[u.c] = (u.a[0] * tile[t] + offdiag_of<T, D>(u.a, tile, t, G.sy, G.sz)) + sbv[u.c];
+    };
+    const int i = threadIdx.x, bd = blockDim.x;
+    if (i < m) fas(q);
+    for (int k = i + bd; k < m; k += bd) {
+      CutCell<T, D> u;
+      u.fetch(V, cl.x + k);
+      fas(u);
+    }
+    __syncthreads();
+  }
   const T inv_h2 = T(L.ih2);
   const long long pbase = L.poff + (long long)(bid - L.first) * NCELL;
   for (int c = threadIdx.x; c < NCELL; c += blockDim.x) {
@@ -497,15 +588,7 @@ __device__ void fas_block(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
     cell_xyz<D>(c, n, &x, &y, &z);
     const int t = G.idx(x, y, z);
     const T ph = tile[t];
-    T ap;
-    if (sb < 0 || !sfl[c]) {
-      ap = inv_h2 * (nb_sum<T, D>(tile, t, G.sy, G.sz) - T(2 * D) * ph);
-    } else {
-      T diag;
-      const T s = offdiag_st<T, D>(V.st + sb, tile, t, G.sy, G.sz, NCELL, c, &diag);
-      ap = diag * ph + s;
-    }
-    V.b[base + c] = ap + sbv[c];
+    V.b[base + c] = (sb >= 0 && sfl[c]) ? sbv[c] : inv_h2 * (nb_sum<T, D>(tile, t, G.sy, G.sz) - T(2 * D) * ph) + sbv[c];
     V.phi[pbase + c] = ph;  // old already holds ph
   }
 }
@@ -708,22 +791,45 @@ __global__ void __launch_bounds__(kThreads) k_resnorm(GmgView<T> V0, LvArgs L, L
   unsigned char *sfl = level_flags(sbv, NCELL);
   const long long base = L.off + (long long)(bid - L.first) * NCELL;
   const long long sb = V.st_base[bid];
-  load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv, sfl, sb);
+  const int4 cl = V.cut_list[bid];
+  const int m = cl.y + cl.z;
+  CutCell<T, D> q;
+  load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv, sfl, sb, [&] {
+    if ((int)threadIdx.x < m) q.fetch(V, cl.x + threadIdx.x);
+  });
   const T inv_h2 = T(L.ih2);
   // the norms only steer the stopping test: squares and maxima of the
   // rounded residual are accumulated in FP32 per thread, then in FP64
   float s2f = 0.f, mxf = 0.f, b2f = 0.f;
-  for (int c = threadIdx.x; c < NCELL; c += blockDim.x) {
-    int x, y, z;
-    cell_xyz<D>(c, n, &x, &y, &z);
-    const T bb = sbv[c];
-    const float r = (float)resid_cell<T, D>(V.st, (sb >= 0 && sfl[c]) ? sb : -1, tile, G.idx(x, y, z), G.sy, G.sz,
-                                            NCELL, c, inv_h2, bb);
+  auto acc = [&](int c, float r, T bb) {
     if (rout) rout[base + c] = r;
     s2f = fmaf(r, r, s2f);
     mxf = fmaxf(mxf, fabsf(r));
     const float bf = (float)bb;
     b2f = fmaf(bf, bf, b2f);
+  };
+  {  // listed cells first (stored stencils)
+    auto res = [&](const CutCell<T, D> &u) {
+      int x, y, z;
+      cell_xyz<D>(u.c, n, &x, &y, &z);
+      const int t = G.idx(x, y, z);
+      const T bb = sbv[u.c];
+      acc(u.c, (float)(bb - (u.a[0] * tile[t] + offdiag_of<T, D>(u.a, tile, t, G.sy, G.sz))), bb);
+    };
+    const int i = threadIdx.x, bd = blockDim.x;
+    if (i < m) res(q);
+    for (int k = i + bd; k < m; k += bd) {
+      CutCell<T, D> u;
+      u.fetch(V, cl.x + k);
+      res(u);
+    }
+  }
+  for (int c = threadIdx.x; c < NCELL; c += blockDim.x) {
+    if (sb >= 0 && sfl[c]) continue;
+    int x, y, z;
+    cell_xyz<D>(c, n, &x, &y, &z);
+    const T bb = sbv[c];
+    acc(c, (float)resid_cell<T, D>(nullptr, -1, tile, G.idx(x, y, z), G.sy, G.sz, NCELL, c, inv_h2, bb), bb);
   }
   block_reduce3((double)s2f, (double)mxf, (double)b2f, partials);
 }

@@ -90,6 +90,10 @@ void launch_resnorm(gmg_tree *t, int l, double *partials, cudaStream_t s) {
   V.old = t->d_old;
   V.st = t->d_st;
   V.spec = t->d_spec;
+  V.cut_list = t->d_cut_list;
+  V.cut_cell = t->d_cut_cell;
+  V.cut_coef = t->d_cut_coef;
+  V.n_cut = t->n_cut;
   V.wneu = 0;
   for (int w = 0; w < 6; w++) V.wneu |= (t->wall_type[w] == GMG_WALL_NEUMANN ? 1 : 0) << w;
   V.nrhs = 1;  // slot 0 only (all trees of a forest)

@@ -22,10 +22,12 @@ __host__ __device__ inline size_t sg_smem_bytes(int D, int n, int SG) {
 }
 
 // load_tile for the slots slot[0..SG) of block bid (slot < 0: skipped):
-// slot s's tile at tiles + s * G.size, its b at bs + s * ncell.
-template <typename T, int D, int NT, int SG>
-__device__ void load_tiles(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, const int *slot,
-                           T *tiles, T *bs, unsigned char *sflag, long long sb) {
+// slot s's tile at tiles + s * G.size, its b at bs + s * ncell; mid() runs
+// once the neighbour ids have arrived.
+template <typename T, int D, int NT, int SG, typename Mid>
+__device__ __forceinline__ void load_tiles(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid,
+                                           const int *slot, T *tiles, T *bs, unsigned char *sflag, long long sb,
+                                           Mid mid) {
   static_assert(NT != 0, "slot groups need a compile-time block size");
   __shared__ int s_nb[6];
   __shared__ int s_fl;
@@ -60,6 +62,7 @@ __device__ void load_tiles(const GmgView<T> &V, const LvArgs &L, const LvArgs &L
     }
   }
   __syncthreads();
+  mid();
   const int fl = s_fl;
   // x faces cell by cell
   for (int i = threadIdx.x; i < 2 * nf; i += blockDim.x) {
@@ -147,29 +150,44 @@ __global__ void __launch_bounds__(kThreads) k_smooth_sg(GmgView<T> V, LvArgs L, 
   unsigned char *sfl = reinterpret_cast<unsigned char *>(bs + SG * ncell);
   const long long pbase = L.poff + (long long)(bid - L.first) * ncell;
   const long long sb = V.st_base[bid];
-  load_tiles<T, D, NT, SG>(V, L, Lp, bid, slot, tiles, bs, sfl, sb);
+  const int4 cl = V.cut_list[bid];
+  const int e0 = cl.x + (color ? cl.y : 0), m = color ? cl.z : cl.y;
+  CutCell<T, D> q;
+  load_tiles<T, D, NT, SG>(V, L, Lp, bid, slot, tiles, bs, sfl, sb, [&] {
+    if ((int)threadIdx.x < m) q.fetch(V, e0 + threadIdx.x);
+  });
   const T h2 = T(L.h2), inv2d = T(1.0 / (2 * D));
   for (int j = threadIdx.x; j < ncell / 2; j += blockDim.x) {
     const int rest = j / hn;
     const int y = rest % n, z = D == 3 ? rest / n : 0;
     const int x = 2 * (j % hn) + ((y + z + color) & 1);
     const int c = x + n * (y + n * z);
+    if (sb >= 0 && sfl[c]) continue;  // a listed cell
     const int t = G.idx(x, y, z);
-    const bool reg = sb < 0 || !sfl[c];
 #pragma unroll
     for (int s = 0; s < SG; s++) {
       if (slot[s] < 0) continue;
       const T *tile = tiles + s * G.size;
-      T nv;
-      if (reg) {
-        nv = (nb_sum<T, D>(tile, t, G.sy, G.sz) - h2 * bs[s * ncell + c]) * inv2d;
-      } else {
-        T diag;
-        const T sum = offdiag_st<T, D>(V.st + sb, tile, t, G.sy, G.sz, ncell, c, &diag);
-        nv = (bs[s * ncell + c] - sum) / diag;
-      }
-      V.phi[slot[s] * V.rs_phi + pbase + c] = nv;
+      V.phi[slot[s] * V.rs_phi + pbase + c] = (nb_sum<T, D>(tile, t, G.sy, G.sz) - h2 * bs[s * ncell + c]) * inv2d;
     }
+  }
+  // the colour's listed cells, one stencil for all SG slots
+  auto upd = [&](const CutCell<T, D> &u) {
+    int x, y, z;
+    cell_xyz<D>(u.c, n, &x, &y, &z);
+    const int t = G.idx(x, y, z);
+#pragma unroll
+    for (int s = 0; s < SG; s++) {
+      if (slot[s] < 0) continue;
+      const T *tile = tiles + s * G.size;
+      V.phi[slot[s] * V.rs_phi + pbase + u.c] = (bs[s * ncell + u.c] - offdiag_of<T, D>(u.a, tile, t, G.sy, G.sz)) / u.a[0];
+    }
+  };
+  if ((int)threadIdx.x < m) upd(q);
+  for (int i = threadIdx.x + blockDim.x; i < m; i += blockDim.x) {
+    CutCell<T, D> u;
+    u.fetch(V, e0 + i);
+    upd(u);
   }
 }
 

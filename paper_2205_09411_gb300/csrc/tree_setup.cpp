@@ -687,8 +687,48 @@ int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, do
   T->ncr = M;
   T->nroot = 1;
   if (!invert(M, A, T->cinv_h)) return set_error("singular coarsest-level operator"), GMG_ERR_INVALID_ARG;
+  build_cut_lists(T);
   T->stencils_ready = true;
   return GMG_OK;
+}
+
+// The cells of every cut block whose stencil differs from the regular one
+// (spec flag set), listed per colour in cell order, with their stored
+// coefficients: the kernels fetch a block's short lists up front instead of
+// reading the dense stencil pool cell by cell.
+void build_cut_lists(gmg_tree *T) {
+  const int D = T->D, S = 2 * D + 1;
+  const size_t nb = T->blocks.size();
+  T->cut_list_h.assign(4 * nb, 0);
+  T->cut_cell_h.clear();
+  T->cut_max_h.assign(T->levels.size(), 0);
+  std::vector<std::vector<double>> coef(S);
+  for (size_t b = 0; b < nb; b++) {
+    const long long sb = T->st_base_h[b];
+    if (sb < 0) continue;
+    const int lv = T->blocks[b].level;
+    const int n = T->lev(lv).n, nc = T->lev(lv).ncell;
+    const long long fb = sb / S;
+    int *ent = &T->cut_list_h[4 * b];
+    ent[0] = (int)T->cut_cell_h.size();
+    for (int col = 0; col < 2; col++) {
+      int m = 0;
+      for (int c = 0; c < nc; c++) {
+        const int x = c % n, y = (c / n) % n, z = D == 3 ? c / (n * n) : 0;
+        if (((x + y + z) & 1) != col || !T->spec_h[fb + c]) continue;
+        T->cut_cell_h.push_back(c);
+        for (int k = 0; k < S; k++) coef[k].push_back(T->stencil_h[sb + (size_t)k * nc + c]);
+        m++;
+      }
+      ent[1 + col] = m;
+    }
+    int &mx = T->cut_max_h[lv - T->lmin];
+    mx = std::max(mx, ent[1] + ent[2]);
+  }
+  T->n_cut = (long long)T->cut_cell_h.size();
+  T->cut_coef_h.clear();
+  T->cut_coef_h.reserve((size_t)S * T->n_cut);
+  for (int k = 0; k < S; k++) T->cut_coef_h.insert(T->cut_coef_h.end(), coef[k].begin(), coef[k].end());
 }
 
 }  // namespace gmg
