@@ -639,7 +639,7 @@ int residual_impl(gmg_tree *t, cudaStream_t s, float *rout) {
     with_nt<D>(L.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
       launch(t, s, 6, 0, l, [&] {
-        k_resnorm<double, D, NT><<<L.count * t->nrhs, cta_threads(t, l), sm, s>>>(V, L, Lp, t->d_partials, rout,
+        k_resnorm<double, D, NT><<<L.count * t->nrhs, resnorm_threads(t, l), sm, s>>>(V, L, Lp, t->d_partials, rout,
                                                                        (int)t->blocks.size());
       });
     });

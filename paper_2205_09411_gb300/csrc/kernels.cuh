@@ -13,6 +13,7 @@ namespace gmg {
 
 constexpr int kThreads = 256;      // threads per CTA of the per-level kernels (at most; see cta_threads)
 constexpr int kCoopThreads = 512;  // threads per CTA of the cooperative coarse cycle
+constexpr int kResThreads = 512;   // threads per CTA of the residual-norm kernel (at most)
 
 // cells of a block of side n (compile-time when n is)
 #define NCELL (D == 3 ? n * n * n : n * n)
@@ -302,15 +303,19 @@ __device__ __forceinline__ void load_tile(const GmgView<T> &V, const LvArgs &L, 
   }
   cp_async_wait_all();
   __syncthreads();
-  bool special = false;  // a wall or a refinement boundary on some face (same answer in every thread)
+  // faces with a wall or a refinement boundary (same list in every thread)
+  // (face ids packed 4 bits each, so that the list stays in a register)
+  unsigned sf = 0;
+  int nsf = 0;
 #pragma unroll
-  for (int f = 0; f < 2 * D; f++) special = special || (fl & wall_bit(f >> 1, f & 1)) || s_nb[f] < 0;
-  if (!special) return;  // every ghost came from a same-level neighbour
-  for (int i = threadIdx.x; i < 2 * D * nf; i += blockDim.x) {
-    const int f = i / nf, j = i - f * nf;
+  for (int f = 0; f < 2 * D; f++)
+    if ((fl & wall_bit(f >> 1, f & 1)) || s_nb[f] < 0) sf |= (unsigned)f << (4 * nsf++);
+  if (nsf == 0) return;  // every ghost came from a same-level neighbour
+  for (int i = threadIdx.x; i < nsf * nf; i += blockDim.x) {
+    const int k = i / nf, j = i - k * nf;
+    const int f = (int)((sf >> (4 * k)) & 15u);
     const int a = f >> 1, side = f & 1;
     const bool wall = (fl & wall_bit(a, side)) != 0;
-    if (!wall && s_nb[f] >= 0) continue;
     const int u = j % n, v = D == 3 ? j / n : 0;
     const int gn = side ? n : -1, mn = side ? n - 1 : 0;
     const int gx = a == 0 ? gn : u, gy = a == 1 ? gn : (a == 0 ? u : v), gz = a == 2 ? gn : v;
@@ -738,9 +743,9 @@ __global__ void __launch_bounds__(kThreads) k_restrict_phi(GmgView<T> V0, LvArgs
 }
 
 // Block reduction of (sum r^2, max |r|, sum b^2) into out[0..2] (CTAs of
-// up to kThreads threads).
+// up to kResThreads threads).
 __device__ __forceinline__ void block_reduce3(double s2, double mx, double b2, double *out) {
-  __shared__ double red[3][kThreads / 32];
+  __shared__ double red[3][kResThreads / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -771,7 +776,7 @@ __device__ __forceinline__ void block_reduce3(double s2, double mx, double b2, d
 // the residual itself is written as float (right-hand side of the FP32
 // correction V-cycle in the mixed path).
 template <typename T, int D, int NT>
-__global__ void __launch_bounds__(kThreads) k_resnorm(GmgView<T> V0, LvArgs L, LvArgs Lp, double *partials,
+__global__ void __launch_bounds__(kResThreads, 2) k_resnorm(GmgView<T> V0, LvArgs L, LvArgs Lp, double *partials,
                                                       float *rout, int nbt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int bid;

@@ -112,7 +112,7 @@ void launch_resnorm(gmg_tree *t, int l, double *partials, cudaStream_t s) {
   cudaFuncSetAttribute(gmg::k_resnorm<double, D, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(gmg::k_resnorm<double, D, NT>, cudaFuncAttributePreferredSharedMemoryCarveout,
                        (int)cudaSharedmemCarveoutMaxShared);
-  gmg::k_resnorm<double, D, NT><<<L.count, gmg::cta_threads(t, l), sm, s>>>(V, L, Lp, partials, nullptr,
+  gmg::k_resnorm<double, D, NT><<<L.count, gmg::resnorm_threads(t, l), sm, s>>>(V, L, Lp, partials, nullptr,
                                                                   (int)t->blocks.size());
 }
 
