@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--skip-serving", action="store_true", help="leave out the serving-loop workload")
     ap.add_argument("--skip-table1", action="store_true", help="leave out the 512^3 FMG timing of the paper's Table 1")
     ap.add_argument("--skip-shapes", action="store_true", help="leave out the sharp-boundary FMG runs")
+    ap.add_argument("--skip-tuned", action="store_true", help="leave out the autotuned headline solve")
     ap.add_argument("--only", choices=["needle", "forest", "serving", "table1", "shapes"], default=None,
                     help="run one secondary workload alone (no headline line; for profiling)")
     ap.add_argument("--needle-rhs", type=int, default=32, help="right-hand sides of the batched needle workload")
@@ -794,23 +795,24 @@ def run_ours(args):
                                  for k, p_, lv, cnt, ms in mixed["prof"]},
         "clocks": clk,
     }
-    # the same solve with the autotuner's schedule for this tree (sweeps per
-    # level group, FP32 cycles per step, CTA size, cooperative block limit);
-    # the headline above keeps the paper's 2 + 2 sweeps on every level
-    from paper_2205_09411_gb300 import autotune as AT
-    t1 = time.perf_counter()
-    sched = AT.tune(t, lambda: t.set_rhs(g_dev), G.MIXED, args.tol, reps=2)
-    tune_s = time.perf_counter() - t1
-    for _ in range(args.warmup):
-        solve(G.MIXED)
-    tuned = timed(G.MIXED)
-    tv = tuned["cycles"] * sched.inner_cycles
-    result["tuned"] = lat(tuned) | {
-        "munks": world * n * tv / (tuned["total_ms"] * 1e-3) / 1e6, "final_rel_residual": tuned["rel"],
-        "v_cycles_per_solve": tv / len(tuned["times"]), "schedule": {
-            "fine_sweeps": list(sched.fine_sweeps), "coarse_sweeps": list(sched.coarse_sweeps),
-            "inner_cycles": sched.inner_cycles, "cta_threads": sched.cta_threads,
-            "coop_max_blocks": sched.coop_max_blocks, "fused": sched.fused}, "tuning_s": tune_s}
+    if not args.skip_tuned:
+        # the same solve with the autotuner's schedule for this tree (sweeps per
+        # level group, FP32 cycles per step, CTA size, cooperative block limit);
+        # the headline above keeps the paper's 2 + 2 sweeps on every level
+        from paper_2205_09411_gb300 import autotune as AT
+        t1 = time.perf_counter()
+        sched = AT.tune(t, lambda: t.set_rhs(g_dev), G.MIXED, args.tol, reps=2)
+        tune_s = time.perf_counter() - t1
+        for _ in range(args.warmup):
+            solve(G.MIXED)
+        tuned = timed(G.MIXED)
+        tv = tuned["cycles"] * sched.inner_cycles
+        result["tuned"] = lat(tuned) | {
+            "munks": world * n * tv / (tuned["total_ms"] * 1e-3) / 1e6, "final_rel_residual": tuned["rel"],
+            "v_cycles_per_solve": tv / len(tuned["times"]), "schedule": {
+                "fine_sweeps": list(sched.fine_sweeps), "coarse_sweeps": list(sched.coarse_sweeps),
+                "inner_cycles": sched.inner_cycles, "cta_threads": sched.cta_threads,
+                "coop_max_blocks": sched.coop_max_blocks, "fused": sched.fused}, "tuning_s": tune_s}
     t.close()
     if not args.skip_needle:
         result["batched_needle"] = run_needle(G, args, world, flush, stream)

@@ -497,16 +497,25 @@ __global__ void __launch_bounds__(kCoopThreads) k_cycle_coop(GmgView<T> V, const
                                                          CycleArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ LevelSet LS;  // level table in shared memory (indexed by level at run time)
+  // the units' activity flags, fixed during the launch: read once here, not
+  // once per phase before each tile load
+  constexpr int kActCache = 256;
+  __shared__ int s_act[kActCache];
+  const int nunits = V.nrhs * V.ntree;
+  const bool act_cached = nunits <= kActCache;
   if (threadIdx.x < nlev) LS.lv[threadIdx.x] = lvtab[threadIdx.x];
   if (threadIdx.x == 0) LS.lmin = lmin;
+  if (act_cached)
+    for (int i = threadIdx.x; i < nunits; i += blockDim.x) s_act[i] = V.active[i];
   __syncthreads();
+  auto is_active = [&](int u) { return act_cached ? s_act[u] != 0 : V.active[u] != 0; };
   const unsigned int G = gridDim.x;
 #define GMG_LV(l) LS.lv[(l)-LS.lmin]
   // (block, slot) items of level Lv handled by this CTA, slots fastest;
   // frozen slots are skipped (W: the slot's view, bid: the block)
 #define GMG_ITEMS(Lv)                                                                          \
   for (int item = blockIdx.x, bid = 0; item < (Lv).count * V.nrhs; item += G)                  \
-    if (const int r_ = item % V.nrhs; (bid = (Lv).first + item / V.nrhs, V.active[unit_of(V, r_, bid)])) \
+    if (const int r_ = item % V.nrhs; (bid = (Lv).first + item / V.nrhs, is_active(unit_of(V, r_, bid)))) \
       if (const GmgView<T> W = slot_view(V, r_); true)
   // levels l_hi .. l_one + 1: every CTA, grid barrier between phases
   for (int l = A.l_hi; l > A.l_lo && l > A.l_one; l--) {
@@ -537,7 +546,7 @@ __global__ void __launch_bounds__(kCoopThreads) k_cycle_coop(GmgView<T> V, const
     // block-level barriers only
     for (int item = blockIdx.x; item < A.nroot * V.nrhs; item += G) {
       const int r = item % V.nrhs, root = item / V.nrhs;
-      if (V.active[V.ntree > 1 ? r * V.ntree + root : r])
+      if (is_active(V.ntree > 1 ? r * V.ntree + root : r))
         tail_cycle<T, D>(slot_view(V, r), LS, A, A.l_one < A.l_hi ? A.l_one : A.l_hi, root, smem_raw);
       __syncthreads();
     }
