@@ -25,29 +25,32 @@ constexpr long long kSpinLimit = 1LL << 24;  // polls of a barrier before it rep
 
 // Grid-wide barrier of a cooperative launch (all CTAs co-resident).  The
 // arrival counter only grows during a launch (the host zeroes it before
-// each one): thread 0 of each CTA adds one and waits, with a bounded number
-// of short sleeps, until the counter reaches the next multiple of the CTA
-// count, so that one atomic and the polls are the barrier's whole cost.  A
-// wait that runs out records GMG_ERR_TIMEOUT, so a barrier that can never
+// each one).  Thread 0 of each CTA counts the barriers its CTA has passed
+// (`epoch`, the same in every CTA), adds one to the counter with a release
+// reduction (no reply to wait for) and polls with acquire loads and short
+// sleeps until the counter reaches epoch x CTA count.  The wait is bounded:
+// when it runs out it records GMG_ERR_TIMEOUT, so a barrier that can never
 // complete ends the kernel instead of hanging it.  Returns the same verdict
 // to every thread of the CTA: false once any CTA has recorded an error.
-__device__ __forceinline__ bool grid_sync(GridBar *bar, unsigned int nctas, long long spin_limit) {
+__device__ __forceinline__ bool grid_sync(GridBar *bar, unsigned int nctas, long long spin_limit,
+                                          unsigned int *epoch) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int *vcount = &bar->count;
     volatile int *verr = &bar->err;
-    __threadfence();
-    const unsigned int target = (atomicAdd(&bar->count, 1u) / nctas + 1) * nctas;
+    const unsigned int target = ++*epoch * nctas;
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;\n" ::"l"(&bar->count) : "memory");
     long long spins = 0;
-    while ((int)(*vcount - target) < 0 && *verr == 0) {
+    for (;;) {
+      unsigned int cur;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(cur) : "l"(&bar->count) : "memory");
+      if ((int)(cur - target) >= 0 || *verr != 0) break;
       if (++spins > spin_limit) {
         atomicCAS(&bar->err, 0, GMG_ERR_TIMEOUT);
         break;
       }
       __nanosleep(32);
     }
-    __threadfence();
     s_ok = *verr == 0;
   }
   __syncthreads();
@@ -67,7 +70,7 @@ struct CycleArgs {
   GridBar *bar;
   long long spin_limit;
   int l_one;  // levels l_lo .. l_one hold one block per root and run one CTA per (root, slot) (< l_lo: none)
-  int cinv_off;  // byte offset of the tail's copy of its root's inverse in shared memory (-1: read from global)
+  int cinv_off;  // byte offset of the tail's FP64 b and copy of its root's inverse in shared memory (-1: none)
 };
 
 // Block operations with the compile-time side NT for levels >= 1 and the
@@ -219,25 +222,45 @@ __device__ __forceinline__ void tail_walls(const TailLevel<T, D> Q, int wneu) {
   __syncthreads();
 }
 
+// One half-sweep of a single-block level.  Every face is a wall, and a wall
+// ghost is the sign times the cell that reads it (reading W), so the
+// neighbour values are formed on the fly from the cell's own value instead
+// of a separate ghost pass and barrier; the sums are those of nb_sum and
+// offdiag_of.
 template <typename T, int D>
 __device__ __forceinline__ void tail_smooth(const GmgView<T> &V, const TailLevel<T, D> Q, int color) {
-  tail_walls<T, D>(Q, V.wneu);
   const TileGeo<T, D> G(Q.n);
   const int n = Q.n;
   const T h2 = T(Q.L.h2), inv2d = T(1.0 / (2 * D));
+  T sg[2 * D];
+#pragma unroll
+  for (int f = 0; f < 2 * D; f++) sg[f] = ((V.wneu >> f) & 1) ? T(1) : T(-1);
   for (int j = threadIdx.x; j < Q.ncell / 2; j += blockDim.x) {
     int x, y, z;
     colour_xyz<D>(j, n, color, &x, &y, &z);
     const int c = x + n * (y + n * z);
     const int t = G.idx(x, y, z);
+    const T own = Q.tile[t];
+    const T xm = x > 0 ? Q.tile[t - 1] : sg[0] * own, xp = x < n - 1 ? Q.tile[t + 1] : sg[1] * own;
+    const T ym = y > 0 ? Q.tile[t - G.sy] : sg[2] * own, yp = y < n - 1 ? Q.tile[t + G.sy] : sg[3] * own;
+    T zm = T(0), zp = T(0);
+    if (D == 3) {
+      zm = z > 0 ? Q.tile[t - G.sz] : sg[4] * own;
+      zp = z < n - 1 ? Q.tile[t + G.sz] : sg[5] * own;
+    }
     T nv;
     int e;
     if (!tail_cut(Q, c, &e)) {
-      nv = (nb_sum<T, D>(Q.tile, t, G.sy, G.sz) - h2 * Q.b[c]) * inv2d;
+      T sum = (xm + xp) + (ym + yp);
+      if (D == 3) sum += zm + zp;
+      nv = (sum - h2 * Q.b[c]) * inv2d;
     } else {
-      T diag;
-      const T sum = offdiag_st<T, D>(Q.cf, Q.tile, t, G.sy, G.sz, Q.m, e, &diag);
-      nv = (Q.b[c] - sum) / diag;
+      T a[2 * D + 1];
+#pragma unroll
+      for (int k = 0; k < 2 * D + 1; k++) a[k] = Q.cf[k * Q.m + e];
+      T sum = a[1] * xm + a[2] * xp + a[3] * ym + a[4] * yp;
+      if (D == 3) sum += a[5] * zm + a[6] * zp;
+      nv = (Q.b[c] - sum) / a[0];
     }
     Q.tile[t] = nv;
   }
@@ -376,6 +399,34 @@ __device__ void tail_cycle(const GmgView<T> &V, const LevelSet &LS, const CycleA
   __shared__ TailLevel<T, D> Q[kMaxTail];  // descriptors in shared memory, not per-thread local memory
   __shared__ int s_m[kMaxTail], s_e0[kMaxTail];
   const int ntl = top - A.l_lo + 1;
+  {  // phi and b of the top tail level: cp.async, in flight during the set-up
+    const LvArgs &L0 = LS.lv[top - LS.lmin];
+    const int n = L0.n, nc = D == 3 ? n * n * n : n * n;
+    // the tile's layout as the descriptors below will carve it: the top
+    // level's tile first, its b right after
+    T *tile = reinterpret_cast<T *>(smem_raw);
+    T *bq = tile + TileGeo<T, D>(n).size;
+    const TileGeo<T, D> G(n);
+    const T *phi = V.phi + L0.poff + (long long)root * nc;
+    const T *b = V.b + L0.off + (long long)root * nc;
+    constexpr int VEC = 16 / sizeof(T);
+    if (n % VEC == 0) {
+      for (int i = threadIdx.x; i < nc / VEC; i += blockDim.x) {
+        int x, y, z;
+        cell_xyz_rt<D>(i * VEC, n, &x, &y, &z);
+        cp_async16(tile + G.idx(x, y, z), phi + i * VEC);
+        cp_async16(bq + i * VEC, b + i * VEC);
+      }
+    } else {
+      for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        int x, y, z;
+        cell_xyz_rt<D>(c, n, &x, &y, &z);
+        cp_async_elem(tile + G.idx(x, y, z), phi + c);
+        cp_async_elem(bq + c, b + c);
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
   if ((int)threadIdx.x < ntl) {  // the levels' cut lists, read in parallel
     const int4 cl = V.cut_list[LS.lv[top - (int)threadIdx.x - LS.lmin].first + root];
     s_m[threadIdx.x] = cl.y + cl.z;
@@ -425,23 +476,18 @@ __device__ void tail_cycle(const GmgView<T> &V, const LevelSet &LS, const CycleA
   }
   // the root's coarse inverse, copied while the tail smooths its way down
   const double *cinv = A.cinv + (size_t)root * A.ncr * A.ncr;
-  if (A.cinv_off >= 0) {
-    double *dst = reinterpret_cast<double *>(smem_raw + A.cinv_off);
+  if (A.cinv_off >= 0) {  // [b in FP64 (ncr) | inverse (ncr x ncr)]
+    double *dst = reinterpret_cast<double *>(smem_raw + A.cinv_off) + A.ncr;
     for (int i = threadIdx.x; i < A.ncr * A.ncr; i += blockDim.x) cp_async_elem(dst + i, cinv + i);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     cinv = dst;
   }
-  {  // phi and b of the top tail level from global memory
-    const TailLevel<T, D> &q = Q[0];
-    const TileGeo<T, D> G(q.n);
-    for (int c = threadIdx.x; c < q.ncell; c += blockDim.x) {
-      int x, y, z;
-      cell_xyz_rt<D>(c, q.n, &x, &y, &z);
-      q.tile[G.idx(x, y, z)] = V.phi[q.L.poff + c];
-      q.b[c] = V.b[q.L.off + c];
-    }
-    __syncthreads();
-  }
+  // the top level's phi and b have landed (the inverse may still be in flight)
+  if (A.cinv_off >= 0)
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+  else
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
   for (int l = top; l > A.l_lo; l--) {
     const TailLevel<T, D> &F = Q[top - l], &Cq = Q[top - l + 1];
     for (int k = 0; k < F.L.nd; k++) {
@@ -451,21 +497,38 @@ __device__ void tail_cycle(const GmgView<T> &V, const LevelSet &LS, const CycleA
     tail_resid_restrict<T, D>(V, F, Cq);
     tail_fas<T, D>(V, Cq);
   }
-  {  // exact solve on l_lo, FP64 accumulation, one warp per row
+  {  // exact solve on l_lo, FP64 accumulation
     if (A.cinv_off >= 0) {
       asm volatile("cp.async.wait_all;\n" ::: "memory");
       __syncthreads();
     }
     const TailLevel<T, D> &q = Q[top - A.l_lo];
     const TileGeo<T, D> G(q.n);
-    const int lane = threadIdx.x & 31;
-    for (int row = threadIdx.x >> 5; row < A.ncr; row += blockDim.x / 32) {
-      const double *a = cinv + (size_t)row * A.ncr;
+    // b in FP64 once, not once per row (beside the staged inverse)
+    double *bd = reinterpret_cast<double *>(smem_raw + A.cinv_off);
+    const bool bd_ok = A.cinv_off >= 0;
+    if (bd_ok) {
+      for (int j = threadIdx.x; j < A.ncr; j += blockDim.x) bd[j] = (double)q.b[j];
+      __syncthreads();
+    }
+    // 8 threads per row, each summing every 8th column, then a 3-step
+    // reduction: on one SM the FP64 adds of a 32-lane reduction tree would
+    // cost more than the multiply-adds themselves
+    const int part = threadIdx.x & 7;
+    const int rows_per_pass = blockDim.x >> 3;
+    for (int r0 = 0; r0 < A.ncr; r0 += rows_per_pass) {
+      const int row = r0 + (threadIdx.x >> 3);
       double s = 0.0;
-      for (int j = lane; j < A.ncr; j += 32) s += a[j] * (double)q.b[j];
+      if (row < A.ncr) {
+        const double *a = cinv + (size_t)row * A.ncr;
+        if (bd_ok)
+          for (int j = part; j < A.ncr; j += 8) s += a[j] * bd[j];
+        else
+          for (int j = part; j < A.ncr; j += 8) s += a[j] * (double)q.b[j];
+      }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) {
+      for (int o = 4; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (row < A.ncr && part == 0) {
         int x, y, z;
         cell_xyz<D>(row, q.n, &x, &y, &z);
         q.tile[G.idx(x, y, z)] = T(s);
@@ -510,6 +573,7 @@ __global__ void __launch_bounds__(kCoopThreads) k_cycle_coop(GmgView<T> V, const
   __syncthreads();
   auto is_active = [&](int u) { return act_cached ? s_act[u] != 0 : V.active[u] != 0; };
   const unsigned int G = gridDim.x;
+  unsigned int epoch = 0;  // grid barriers passed (thread 0 keeps the count)
 #define GMG_LV(l) LS.lv[(l)-LS.lmin]
   // (block, slot) items of level Lv handled by this CTA, slots fastest;
   // frozen slots are skipped (W: the slot's view, bid: the block)
@@ -526,19 +590,19 @@ __global__ void __launch_bounds__(kCoopThreads) k_cycle_coop(GmgView<T> V, const
           smooth_any<T, D, NT>(W, L, Lp, bid, c, smem_raw);
           __syncthreads();
         }
-        if (!grid_sync(A.bar, G, A.spin_limit)) return;
+        if (!grid_sync(A.bar, G, A.spin_limit, &epoch)) return;
       }
     GMG_ITEMS(L) {
       resid_restrict_any<T, D, NT>(W, L, Lp, bid, smem_raw);
       __syncthreads();
     }
-    if (!grid_sync(A.bar, G, A.spin_limit)) return;
+    if (!grid_sync(A.bar, G, A.spin_limit, &epoch)) return;
     const LvArgs &Lpp = l - 2 >= LS.lmin ? GMG_LV(l - 2) : Lp;
     GMG_ITEMS(Lp) {
       fas_any<T, D, NT>(W, Lp, Lpp, bid, smem_raw);
       __syncthreads();
     }
-    if (!grid_sync(A.bar, G, A.spin_limit)) return;
+    if (!grid_sync(A.bar, G, A.spin_limit, &epoch)) return;
   }
   if (A.l_one >= A.l_lo) {
     // single-block levels l_one .. l_lo: CTA 0 runs the bottom of the cycle
@@ -554,14 +618,14 @@ __global__ void __launch_bounds__(kCoopThreads) k_cycle_coop(GmgView<T> V, const
     coarse_rows<T>(V, GMG_LV(A.l_lo), A, blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5),
                    (int)(G * (blockDim.x / 32)));
   }
-  if (A.l_hi > A.l_one && !grid_sync(A.bar, G, A.spin_limit)) return;
+  if (A.l_hi > A.l_one && !grid_sync(A.bar, G, A.spin_limit, &epoch)) return;
   for (int l = (A.l_one >= A.l_lo ? A.l_one : A.l_lo) + 1; l <= A.l_hi; l++) {
     const LvArgs &L = GMG_LV(l), &Lp = GMG_LV(l - 1);  // read from shared memory, not held in registers
     GMG_ITEMS(L) {
       prolong_any<T, D, NT>(W, L, Lp, bid, smem_raw);
       __syncthreads();
     }
-    if (!grid_sync(A.bar, G, A.spin_limit)) return;
+    if (!grid_sync(A.bar, G, A.spin_limit, &epoch)) return;
     for (int k = 0; k < L.nu; k++)
       for (int c = 0; c < 2; c++) {
         GMG_ITEMS(L) {
@@ -569,7 +633,7 @@ __global__ void __launch_bounds__(kCoopThreads) k_cycle_coop(GmgView<T> V, const
           __syncthreads();
         }
         // the last sweep of the range needs no barrier: the kernel ends
-        if (!(l == A.l_hi && k == L.nu - 1 && c == 1) && !grid_sync(A.bar, G, A.spin_limit)) return;
+        if (!(l == A.l_hi && k == L.nu - 1 && c == 1) && !grid_sync(A.bar, G, A.spin_limit, &epoch)) return;
       }
   }
 #undef GMG_ITEMS
@@ -579,7 +643,8 @@ __global__ void __launch_bounds__(kCoopThreads) k_cycle_coop(GmgView<T> V, const
 // A cooperative kernel whose barrier waits for one CTA more than it has:
 // the wait must run out and record GMG_ERR_TIMEOUT (failure-detection test).
 __global__ void k_barrier_selftest(GridBar *bar, long long spin_limit) {
-  grid_sync(bar, gridDim.x + 1, spin_limit);
+  unsigned int epoch = 0;
+  grid_sync(bar, gridDim.x + 1, spin_limit, &epoch);
 }
 
 }  // namespace gmg

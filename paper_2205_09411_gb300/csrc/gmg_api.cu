@@ -404,7 +404,7 @@ int coop_cycle(gmg_tree *t, cudaStream_t s, int ls) {
     }
   // the tail's coarse inverse in shared memory when it fits beside the levels
   int cinv_off = -1;
-  const size_t cinv_bytes = sizeof(double) * (size_t)t->ncr * t->ncr;
+  const size_t cinv_bytes = sizeof(double) * ((size_t)t->ncr * t->ncr + t->ncr);  // inverse and b in FP64
   if (l_one >= t->lmin && tail_bytes + cinv_bytes <= 192 * 1024) {
     cinv_off = (int)tail_bytes;
     tail_bytes += cinv_bytes;
