@@ -352,6 +352,10 @@ int gmg_profile_read(gmg_tree *tree, int cap, int *kind, int *prec, int *level, 
 #define GMG_OPT_SLOTS_PER_CTA 8  /* [1] with several slots, the half-sweeps of 8^3 / 16^3 blocks
                                     stage and update 1, 2 or 4 slots of a block per CTA (the
                                     block's tables and index arithmetic shared); same results */
+#define GMG_OPT_PDL 10           /* [1] the per-level kernels of a solve step are launched with
+                                    programmatic dependent launch: each is dispatched as its
+                                    predecessor's CTAs exit and waits for it on the device before
+                                    reading its results; same results */
 int gmg_set_option(gmg_tree *tree, int option, long long value);
 
 /* Sweep schedule: N_down / N_up red-black sweeps on one level (default: the

@@ -559,6 +559,7 @@ template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kCoopThreads) k_cycle_coop(GmgView<T> V, const LvArgs *lvtab, int nlev, int lmin,
                                                          CycleArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_start();
   __shared__ LevelSet LS;  // level table in shared memory (indexed by level at run time)
   // the units' activity flags, fixed during the launch: read once here, not
   // once per phase before each tile load

@@ -31,6 +31,7 @@ struct FusedGeo {
 
 template <typename T, int D, int NT, int K>
 __global__ void __launch_bounds__(kThreads) k_smooth_tb(GmgView<T> V0, LvArgs L, long long out_poff) {
+  pdl_start();
   using F = FusedGeo<T, D, NT, K>;
   constexpr int n = NT, VEC = F::VEC;
   using VT = typename Vec16<T>::type;

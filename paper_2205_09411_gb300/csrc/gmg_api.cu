@@ -36,6 +36,7 @@ void set_error(const std::string &msg) { g_last_error = msg; }
 __global__ void __launch_bounds__(1024) k_reduce_partials(const double *partials, int nb, const int *tree_blocks,
                                                           const int *tree_boff, int ntree, double *out,
                                                           const GridBar *bar) {
+  pdl_start();
   __shared__ double s[3][1024];
   // unit blockIdx.x = (slot r, tree i): the blocks of tree i in slot r
   const int r = blockIdx.x / ntree, tr = blockIdx.x % ntree;
@@ -112,6 +113,7 @@ __global__ void k_leaf_accumulate(const int *__restrict__ leaf_ids, const long l
                                   double *__restrict__ phi, const float *__restrict__ e, int nlb, int ncell,
                                   long long rs, int nr, const int *__restrict__ active, const int *__restrict__ tree_of,
                                   int ntree) {
+  pdl_start();
   for (int lb = blockIdx.x; lb < nlb; lb += gridDim.x) {
     const int id = leaf_ids[lb];
     const long long base = cbase[id];
@@ -172,6 +174,25 @@ void launch(gmg_tree *t, cudaStream_t s, int kind, int prec, int level, F &&f) {
     f();
   }
   t->launches += 1;
+}
+
+// Launch of a solve-step kernel: with programmatic dependent launch (the
+// kernel starts with pdl_start) unless the option is off or kernel timing
+// is on (events between kernels).
+template <typename... KArgs, typename... Args>
+void klaunch(const gmg_tree *t, dim3 grid, dim3 block, size_t smem, cudaStream_t s, void (*k)(KArgs...),
+             Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = (t->use_pdl && !t->prof_on) ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, k, args...);
 }
 
 template <typename T>
@@ -359,25 +380,25 @@ void launch_smooth(const gmg_tree *t, const GmgView<T> &V, const LvArgs &L, cons
       const int grid = L.count * ((t->nrhs + sg - 1) / sg);
       const size_t sms = sg_smem_bytes<T>(D, NT, sg);
       if (sg == 2)
-        k_smooth_sg<T, D, NT, 2><<<grid, threads, sms, s>>>(V, L, Lp, c);
+        klaunch(t, grid, threads, sms, s, k_smooth_sg<T, D, NT, 2>, V, L, Lp, c);
       else
-        k_smooth_sg<T, D, NT, 4><<<grid, threads, sms, s>>>(V, L, Lp, c);
+        klaunch(t, grid, threads, sms, s, k_smooth_sg<T, D, NT, 4>, V, L, Lp, c);
       return;
     }
   }
-  k_smooth<T, D, NT><<<L.count * t->nrhs, threads, sm, s>>>(V, L, Lp, c);
+  klaunch(t, L.count * t->nrhs, threads, sm, s, k_smooth<T, D, NT>, V, L, Lp, c);
 }
 
 // k_prolong with the CTA size of the level's block kernels
 template <typename T, int D, int NT>
-void launch_prolong(int threads, int grid, size_t sm, cudaStream_t s, const GmgView<T> &V, const LvArgs &L,
-                    const LvArgs &Lp) {
+void launch_prolong(const gmg_tree *t, int threads, int grid, size_t sm, cudaStream_t s, const GmgView<T> &V,
+                    const LvArgs &L, const LvArgs &Lp) {
   if (threads == 64)
-    k_prolong<T, D, NT, 64><<<grid, 64, sm, s>>>(V, L, Lp);
+    klaunch(t, grid, 64, sm, s, k_prolong<T, D, NT, 64>, V, L, Lp);
   else if (threads == 128)
-    k_prolong<T, D, NT, 128><<<grid, 128, sm, s>>>(V, L, Lp);
+    klaunch(t, grid, 128, sm, s, k_prolong<T, D, NT, 128>, V, L, Lp);
   else
-    k_prolong<T, D, NT, 256><<<grid, 256, sm, s>>>(V, L, Lp);
+    klaunch(t, grid, 256, sm, s, k_prolong<T, D, NT, 256>, V, L, Lp);
 }
 
 template <typename T>
@@ -481,7 +502,7 @@ void launch_fused(gmg_tree *t, cudaStream_t s, int l, int sweeps, long long in_p
     if constexpr (NT != 0) {
       const size_t sm = FusedGeo<T, D, NT, K>::smem_bytes();
       launch(t, s, 0, prec_of<T>(), l,
-             [&] { k_smooth_tb<T, D, NT, K><<<L.count * t->nrhs, kThreads, sm, s>>>(V, L, out_poff); });
+             [&] { klaunch(t, L.count * t->nrhs, kThreads, sm, s, k_smooth_tb<T, D, NT, K>, V, L, out_poff); });
     }
   };
   with_nt<D>(L.n, [&](auto nt) {
@@ -518,13 +539,13 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s, bool end_restrict, int top) {
         for (int k = 0; k < L.nd; k++)
           for (int c = 0; c < 2; c++)
             launch(t, s, 0, P, l, [&] { launch_smooth<T, D, NT>(t, V, L, Lp, c, nt_l, sm, s); });
-      launch(t, s, 1, P, l, [&] { k_resid_restrict<T, D, NT><<<L.count * R, nt_l, sm, s>>>(V, L, Lp); });
+      launch(t, s, 1, P, l, [&] { klaunch(t, L.count * R, nt_l, sm, s, k_resid_restrict<T, D, NT>, V, L, Lp); });
     });
     LvArgs Lpp = l - 2 >= t->lmin ? lv(t, l - 2) : Lp;
     const size_t smp = tile_bytes<T>(t, l - 1);
     with_nt<D>(Lp.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
-      launch(t, s, 2, P, l - 1, [&] { k_fas<T, D, NT><<<Lp.count * R, nt_p, smp, s>>>(V, Lp, Lpp); });
+      launch(t, s, 2, P, l - 1, [&] { klaunch(t, Lp.count * R, nt_p, smp, s, k_fas<T, D, NT>, V, Lp, Lpp); });
     });
   }
   if (t->use_coop) {
@@ -534,7 +555,7 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s, bool end_restrict, int top) {
     LvArgs Lc = lv(t, t->lmin);
     const long long rows = (long long)t->nc * R;
     launch(t, s, 3, P, t->lmin, [&] {
-      k_coarse<T><<<(unsigned)((rows + kThreads / 32 - 1) / (kThreads / 32)), kThreads, 0, s>>>(V, Lc, t->d_cinv,
+      klaunch(t, (unsigned)((rows + kThreads / 32 - 1) / (kThreads / 32)), kThreads, 0, s, k_coarse<T>, V, Lc, t->d_cinv,
                                                                                               t->ncr, t->nroot);
     });
   }
@@ -548,7 +569,7 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s, bool end_restrict, int top) {
     if (fused) L.poff = L.off + other;  // the down leg left phi in the second buffer
     with_nt<D>(L.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
-      launch(t, s, 4, P, l, [&] { launch_prolong<T, D, NT>(cta_threads(t, l), L.count * R, psm, s, V, L, Lp); });
+      launch(t, s, 4, P, l, [&] { launch_prolong<T, D, NT>(t, cta_threads(t, l), L.count * R, psm, s, V, L, Lp); });
       if (!fused)
         for (int k = 0; k < L.nu; k++)
           for (int c = 0; c < 2; c++)
@@ -562,7 +583,7 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s, bool end_restrict, int top) {
       with_nt<D>(L.n, [&](auto nt) {
         constexpr int NT = decltype(nt)::value;
         launch(t, s, 5, P, l,
-               [&] { k_restrict_phi<T, D, NT><<<L.count * R, cta_threads(t, l), 0, s>>>(V, L, Lp); });
+               [&] { klaunch(t, L.count * R, cta_threads(t, l), 0, s, k_restrict_phi<T, D, NT>, V, L, Lp); });
       });
     }
   }
@@ -591,18 +612,18 @@ int fmg_impl(gmg_tree *t, cudaStream_t s) {
     const int nt_l = cta_threads(t, l), nt_p = cta_threads(t, l - 1);
     with_nt<D>(L.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
-      launch(t, s, 1, P, l, [&] { k_resid_restrict<T, D, NT><<<L.count * R, nt_l, sm, s>>>(V, L, Lp); });
+      launch(t, s, 1, P, l, [&] { klaunch(t, L.count * R, nt_l, sm, s, k_resid_restrict<T, D, NT>, V, L, Lp); });
     });
     with_nt<D>(Lp.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
-      launch(t, s, 2, P, l - 1, [&] { k_fas<T, D, NT><<<Lp.count * R, nt_p, smp, s>>>(V, Lp, Lpp); });
+      launch(t, s, 2, P, l - 1, [&] { klaunch(t, Lp.count * R, nt_p, smp, s, k_fas<T, D, NT>, V, Lp, Lpp); });
     });
   }
   {
     const LvArgs Lc = lv(t, t->lmin);
     const long long rows = (long long)t->nc * R;
     launch(t, s, 3, P, t->lmin, [&] {
-      k_coarse<T><<<(unsigned)((rows + kThreads / 32 - 1) / (kThreads / 32)), kThreads, 0, s>>>(V, Lc, t->d_cinv,
+      klaunch(t, (unsigned)((rows + kThreads / 32 - 1) / (kThreads / 32)), kThreads, 0, s, k_coarse<T>, V, Lc, t->d_cinv,
                                                                                               t->ncr, t->nroot);
     });
   }
@@ -612,7 +633,7 @@ int fmg_impl(gmg_tree *t, cudaStream_t s) {
     const size_t psm = sizeof(T) * (size_t)(D == 3 ? hm * hm * hm : hm * hm);
     with_nt<D>(L.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
-      launch(t, s, 4, P, l, [&] { launch_prolong<T, D, NT>(cta_threads(t, l), L.count * R, psm, s, V, L, Lp); });
+      launch(t, s, 4, P, l, [&] { launch_prolong<T, D, NT>(t, cta_threads(t, l), L.count * R, psm, s, V, L, Lp); });
     });
     const int rc = vcycle_impl<T, D>(t, s, true, l);
     if (rc) return rc;
@@ -639,13 +660,13 @@ int residual_impl(gmg_tree *t, cudaStream_t s, float *rout) {
     with_nt<D>(L.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
       launch(t, s, 6, 0, l, [&] {
-        k_resnorm<double, D, NT><<<L.count * t->nrhs, resnorm_threads(t, l), sm, s>>>(V, L, Lp, t->d_partials, rout,
+        klaunch(t, L.count * t->nrhs, resnorm_threads(t, l), sm, s, k_resnorm<double, D, NT>, V, L, Lp, t->d_partials, rout,
                                                                        (int)t->blocks.size());
       });
     });
   }
   launch(t, s, 7, 0, t->lmax, [&] {
-    k_reduce_partials<<<t->units(), 1024, 0, s>>>(t->d_partials, (int)t->blocks.size(), t->d_tree_blocks,
+    klaunch(t, t->units(), 1024, 0, s, k_reduce_partials, (const double *)t->d_partials, (int)t->blocks.size(), (const int *)t->d_tree_blocks,
                                                   t->d_tree_boff, t->ntree, t->d_red, t->d_bar);
   });
   CUDA_TRY(cudaGetLastError());
@@ -665,7 +686,7 @@ int restrict_all_phi64(gmg_tree *t, cudaStream_t s) {
     with_nt<D>(L.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
       launch(t, s, 5, 0, l, [&] {
-        k_restrict_phi<double, D, NT><<<L.count * t->nrhs, cta_threads(t, l), 0, s>>>(V, L, Lp);
+        klaunch(t, L.count * t->nrhs, cta_threads(t, l), 0, s, k_restrict_phi<double, D, NT>, V, L, Lp);
       });
     });
   }
@@ -689,7 +710,7 @@ int mixed_step(gmg_tree *t, cudaStream_t s) {
     if (rc) return rc;
   }
   launch(t, s, 8, 0, t->lmax, [&] {
-    k_leaf_accumulate<<<leaf_grid(t), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, t->f_phi, n_leaf_blocks(t),
+    klaunch(t, leaf_grid(t), 256, 0, s, k_leaf_accumulate, (const int *)t->d_leaf, (const long long *)t->d_cbase, t->d_phi, (const float *)t->f_phi, n_leaf_blocks(t),
                                                    t->leaf_ncell(), t->total_cells, t->nrhs, t->d_active, t->d_tree_of,
                                                    t->ntree);
   });
@@ -1556,6 +1577,10 @@ int gmg_set_option(gmg_tree *t, int option, long long value) {
       if (t->bound) set_coop_split(t);
       break;
     case GMG_OPT_FMG_STEPS: t->fmg_steps = value != 0; break;
+    case GMG_OPT_PDL:
+      t->use_pdl = value != 0;
+      drop_graphs(t);
+      break;
     case GMG_OPT_SLOTS_PER_CTA:
       if (value != 1 && value != 2 && value != 4) return set_error("slots per CTA must be 1, 2 or 4"), GMG_ERR_INVALID_ARG;
       t->slots_per_cta = (int)value;

@@ -203,6 +203,7 @@ struct gmg_tree {
   int inner_cycles = 1;       // FP32 V-cycles per defect-correction step of the mixed path
   int slots_per_cta = 1;      // right-hand-side slots of a block per CTA in the half-sweeps (1, 2, 4)
   bool fmg_steps = false;     // solve steps are FMG cycles instead of V-cycles
+  bool use_pdl = true;        // per-level kernels with programmatic dependent launch
   std::vector<char> level_complete;  // every block has all 26 neighbours on its level (or walls)
   int coop_split = 0;         // highest level run inside that launch
   int coop_max_blocks = gmg::kCoopMaxBlocks;  // levels with at most this many blocks join it

@@ -18,6 +18,17 @@ constexpr int kResThreads = 512;   // threads per CTA of the residual-norm kerne
 // cells of a block of side n (compile-time when n is)
 #define NCELL (D == 3 ? n * n * n : n * n)
 
+// Programmatic dependent launch: a solve-step kernel launched with the
+// attribute is dispatched as soon as the previous kernel's CTAs have all
+// exited, and waits here until that grid has finished and its writes are
+// visible (a no-op without the attribute).  Every kernel of a solve step
+// starts with this, before it reads any field.  No kernel triggers its
+// dependents early: CTAs dispatched early would sit resident while they
+// wait, and measured slower (2.20 ms against 2.14 ms per 128^3 solve).
+__device__ __forceinline__ void pdl_start() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+
 __device__ __forceinline__ int nbr_slot(int ox, int oy, int oz) { return (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1); }
 
 // Local coordinate p (each component in [-1, n]) of block `bid` on level L:
@@ -450,6 +461,7 @@ __device__ void smooth_block(const GmgView<T> &V, const LvArgs &L, const LvArgs 
 
 template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kThreads) k_smooth(GmgView<T> V, LvArgs L, LvArgs Lp, int color) {
+  pdl_start();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int bid;
   GmgView<T> W;
@@ -536,6 +548,7 @@ __device__ void resid_restrict_block(const GmgView<T> &V, const LvArgs &L, const
 
 template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kThreads) k_resid_restrict(GmgView<T> V, LvArgs L, LvArgs Lp) {
+  pdl_start();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int bid;
   GmgView<T> W;
@@ -600,6 +613,7 @@ __device__ void fas_block(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
 
 template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kThreads) k_fas(GmgView<T> V, LvArgs L, LvArgs Lp) {
+  pdl_start();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int bid;
   GmgView<T> W;
@@ -613,6 +627,7 @@ __global__ void __launch_bounds__(kThreads) k_fas(GmgView<T> V, LvArgs L, LvArgs
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_coarse(GmgView<T> V, LvArgs Lc, const double *__restrict__ Ainv,
                                                      int ncr, int nroot) {
+  pdl_start();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long item = (long long)blockIdx.x * (kThreads / 32) + warp;
   const int M = ncr * nroot;
@@ -711,6 +726,7 @@ __device__ void prolong_block(const GmgView<T> &V, const LvArgs &L, const LvArgs
 
 template <typename T, int D, int NT, int PT>
 __global__ void __launch_bounds__(PT) k_prolong(GmgView<T> V, LvArgs L, LvArgs Lp) {
+  pdl_start();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int bid;
   GmgView<T> W;
@@ -721,6 +737,7 @@ __global__ void __launch_bounds__(PT) k_prolong(GmgView<T> V, LvArgs L, LvArgs L
 // phi of covered cells <- mean of the children (composite consistency).
 template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kThreads) k_restrict_phi(GmgView<T> V0, LvArgs L, LvArgs Lp) {
+  pdl_start();
   int bid;
   GmgView<T> V;
   if (!slot_item(V0, L, &bid, &V)) return;
@@ -778,6 +795,7 @@ __device__ __forceinline__ void block_reduce3(double s2, double mx, double b2, d
 template <typename T, int D, int NT>
 __global__ void __launch_bounds__(kResThreads, 2) k_resnorm(GmgView<T> V0, LvArgs L, LvArgs Lp, double *partials,
                                                       float *rout, int nbt) {
+  pdl_start();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int bid;
   GmgView<T> V;

@@ -131,6 +131,7 @@ __device__ __forceinline__ void load_tiles(const GmgView<T> &V, const LvArgs &L,
 // groups fastest.
 template <typename T, int D, int NT, int SG>
 __global__ void __launch_bounds__(kThreads) k_smooth_sg(GmgView<T> V, LvArgs L, LvArgs Lp, int color) {
+  pdl_start();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ngrp = (V.nrhs + SG - 1) / SG;
   const int grp = (int)(blockIdx.x % (unsigned)ngrp), bid = L.first + (int)(blockIdx.x / (unsigned)ngrp);

@@ -205,6 +205,28 @@ def test_cta_sizes_give_identical_results(name):
         assert np.array_equal(a, out[0][0]) and np.array_equal(b, out[0][1]) and c == out[0][2]
 
 
+@pytest.mark.parametrize("name", ["c1", "needle4", "c2_64", "adaptive3d"])
+def test_dependent_launch_gives_identical_results(name):
+    """Programmatic dependent launch only lets a kernel be dispatched as its
+    predecessor's CTAs exit; every kernel waits for its predecessor before
+    reading a field.  FP64 iterates, FMG iterates and mixed solves are bit
+    for bit the same with it on and off."""
+    p = parity_cases()[name]
+    out = []
+    for pdl in (1, 0):
+        t = gpu_problem(p)
+        t.set_option("pdl", pdl)
+        t.vcycle(3)
+        a = t.solution().copy()
+        t.fmg(1)
+        f = t.solution().copy()
+        t.set_rhs(np.asarray(p["rhs"](t.leaf_centers()), dtype=np.float64))
+        st = t.solve(1, 1e-8, 60)
+        out.append((a, f, t.solution().copy(), st["cycles"]))
+    for x, y in zip(out[0], out[1]):
+        assert np.array_equal(x, y)
+
+
 @pytest.mark.parametrize("name", ["c1", "c2_32", "adaptive2d", "adaptive3d", "needle4", "ragged3d"])
 def test_fmg_iterates_match_oracle(name):
     """FMG cycles (Sec. 2.2) through the C ABI give the oracle's FMG iterates
