@@ -1267,6 +1267,23 @@ int gmg_set_num_rhs(gmg_tree *t, int nrhs) {
 
 int gmg_num_rhs(const gmg_tree *t) { return t ? t->nrhs : 0; }
 
+namespace {
+// The device-side address of host memory that kernels can read and write
+// directly: page-locked memory mapped into the device's address space (what
+// cudaHostAlloc and cudaHostRegister give under unified addressing, and
+// what pinned PyTorch tensors use).  The leaf gather and scatter kernels
+// then move a host array over the CPU-GPU link themselves, with no staging
+// copy.  nullptr for pageable memory, which is staged with cudaMemcpyAsync.
+void *mapped_host(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // clear: an unknown pointer is pageable host memory
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+}  // namespace
+
 int gmg_set_rhs_slots(gmg_tree *t, int slot0, int nslots, const double *g, int where, void *stream) {
   if (!t || !g) return set_error("null argument"), GMG_ERR_INVALID_ARG;
   if (!t->bound) return set_error("tree not bound"), GMG_ERR_STATE;
@@ -1275,9 +1292,13 @@ int gmg_set_rhs_slots(gmg_tree *t, int slot0, int nslots, const double *g, int w
   const long long n = t->n_leaf_cells;
   const double *gd = g;
   if (where == GMG_HOST) {
-    // stage through the FP64 'old' field (scratch until the next V-cycle)
-    CUDA_TRY(cudaMemcpyAsync(t->d_old, g, (size_t)nslots * n * sizeof(double), cudaMemcpyHostToDevice, s));
-    gd = t->d_old;
+    if (const void *m = mapped_host(g)) {
+      gd = static_cast<const double *>(m);  // read by the scatter kernel itself
+    } else {
+      // stage through the FP64 'old' field (scratch until the next V-cycle)
+      CUDA_TRY(cudaMemcpyAsync(t->d_old, g, (size_t)nslots * n * sizeof(double), cudaMemcpyHostToDevice, s));
+      gd = t->d_old;
+    }
   } else if (where != GMG_DEVICE) {
     return set_error("where must be GMG_HOST or GMG_DEVICE"), GMG_ERR_INVALID_ARG;
   }
@@ -1301,8 +1322,12 @@ int gmg_set_solution(gmg_tree *t, const double *phi, int where, void *stream) {
   const long long n = t->n_leaf_cells;
   double *src = const_cast<double *>(phi);
   if (where == GMG_HOST) {
-    CUDA_TRY(cudaMemcpyAsync(t->d_old, phi, (size_t)t->nrhs * n * sizeof(double), cudaMemcpyHostToDevice, s));
-    src = t->d_old;
+    if (void *m = mapped_host(phi)) {
+      src = static_cast<double *>(m);
+    } else {
+      CUDA_TRY(cudaMemcpyAsync(t->d_old, phi, (size_t)t->nrhs * n * sizeof(double), cudaMemcpyHostToDevice, s));
+      src = t->d_old;
+    }
   }
   k_leaf_copy<<<leaf_grid(t), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, src, n_leaf_blocks(t), t->leaf_ncell(),
                                            t->total_cells, 0, t->nrhs, 1);
@@ -1322,6 +1347,13 @@ int gmg_get_solution_slots(gmg_tree *t, int slot0, int nslots, double *phi, int 
     k_leaf_copy<<<leaf_grid(t), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, phi, n_leaf_blocks(t), ncell,
                                              t->total_cells, slot0, nslots, 0);
     CUDA_TRY(cudaGetLastError());
+    return GMG_OK;
+  }
+  if (void *m = mapped_host(phi)) {  // the gather kernel writes the host array itself
+    k_leaf_copy<<<leaf_grid(t), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, static_cast<double *>(m),
+                                             n_leaf_blocks(t), ncell, t->total_cells, slot0, nslots, 0);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(s));
     return GMG_OK;
   }
   // the FP64 'old' field is dead between V-cycles: stage the gather there

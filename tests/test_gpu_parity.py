@@ -135,6 +135,44 @@ def test_device_arrays_round_trip():
     assert np.array_equal(out.cpu().numpy(), t.solution())
 
 
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_pinned_host_arrays_round_trip(nrhs):
+    """Pinned host arrays are read and written by the leaf scatter and gather
+    kernels directly (no staging copy); pageable ones are staged.  Both give
+    the device path's right-hand side and solution bit for bit, also for a
+    range of slots."""
+    import torch
+    p = parity_cases()["needle4"]
+    t = gpu_problem(p, nrhs=nrhs, rhs=False)
+    n = t.n_leaf_cells
+    rng = np.random.default_rng(7)
+    g = rng.standard_normal((nrhs, n)) if nrhs > 1 else rng.standard_normal(n)
+    outs = []
+    for kind in ("device", "pinned", "pageable"):
+        if kind == "device":
+            gin = torch.tensor(g, device="cuda")
+        elif kind == "pinned":
+            gin = torch.tensor(g).pin_memory()
+        else:
+            gin = g.copy()
+        t.set_rhs(gin)
+        t.vcycle(2)
+        if kind == "device":
+            out = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+        elif kind == "pinned":
+            out = torch.zeros(g.shape, dtype=torch.float64).pin_memory()
+        else:
+            out = np.zeros(g.shape)
+        t.solution(out)
+        torch.cuda.synchronize()
+        outs.append(out.cpu().numpy() if isinstance(out, torch.Tensor) else out)
+        if nrhs > 1:  # one slot into a pinned buffer
+            one = torch.zeros((1, n), dtype=torch.float64).pin_memory()
+            t.solution_slots(nrhs - 1, 1, one)
+            assert np.array_equal(one.numpy()[0], outs[-1][nrhs - 1])
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
 @pytest.mark.parametrize("name", ["c2_64", "adaptive3d", "ragged3d", "c1"])
 @pytest.mark.parametrize("graphs,coop", [(0, 0), (1, 0), (0, 1)])
 def test_execution_paths_give_the_oracle_iterates(name, graphs, coop):
