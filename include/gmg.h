@@ -78,7 +78,11 @@ extern "C" {
 #define GMG_MIXED 1 /* FP64 defect correction around FP32 V-cycles; the fine residual,
                        the solution update and the coarsest-level solve stay in FP64  */
 
-/* where a caller's array lives */
+/* where a caller's array lives.  A GMG_HOST array in page-locked memory
+ * mapped into the device's address space (cudaHostAlloc, cudaHostRegister,
+ * pinned PyTorch tensors) is read or written by the library's kernels
+ * directly over the CPU-GPU link; pageable host memory is staged through
+ * device memory with cudaMemcpyAsync.  Same values either way. */
 #define GMG_HOST 0
 #define GMG_DEVICE 1
 
