@@ -317,6 +317,13 @@ int gmg_get_level(gmg_tree *tree, int level, int which, double *out, void *strea
 int gmg_get_distances(const gmg_tree *tree, int level, double *out);
 int gmg_get_mask(const gmg_tree *tree, int level, int *out);
 int gmg_num_cut_blocks(const gmg_tree *tree, int level);
+/* Cut lists of a level (host, after gmg_store_stencils): for block i of the
+ * level in canonical order, counts[2i] and counts[2i+1] receive how many of
+ * its cells of colour 0 ((x+y+z) even) and colour 1 have a stencil that
+ * differs from the regular one (some d < 1, Sec. 3.3); the kernels keep those
+ * cells and their coefficients in per-colour lists.  counts: 2 * (blocks of
+ * the level) ints, caller-owned. */
+int gmg_cut_counts(const gmg_tree *tree, int level, int *counts);
 
 /* Number of kernels the last gmg_vcycle / gmg_solve call enqueued. */
 long long gmg_last_launch_count(const gmg_tree *tree);

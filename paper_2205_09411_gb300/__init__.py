@@ -111,6 +111,7 @@ def load():
         "gmg_get_distances": (C.c_int, [vp, C.c_int, dp]),
         "gmg_get_mask": (C.c_int, [vp, C.c_int, ip]),
         "gmg_num_cut_blocks": (C.c_int, [vp, C.c_int]),
+        "gmg_cut_counts": (C.c_int, [vp, C.c_int, ip]),
         "gmg_last_launch_count": (C.c_longlong, [vp]),
         "gmg_profile_enable": (C.c_int, [vp, C.c_int]),
         "gmg_profile_read": (C.c_int, [vp, C.c_int, ip, ip, ip, C.POINTER(C.c_longlong), dp]),
@@ -317,6 +318,13 @@ class Tree:
         out = np.zeros(nb * n ** self.dim * 2 * self.dim)
         _check(load().gmg_get_distances(self.h, level, out.ctypes.data_as(C.POINTER(C.c_double))))
         return out.reshape(nb, n ** self.dim, 2 * self.dim)
+
+    def cut_counts(self, level):
+        """(blocks, 2): per block of the level, the cells of colour 0 and 1
+        ((x+y+z) even / odd) that the kernels' cut lists hold."""
+        out = np.zeros(2 * self.level_nblocks(level), dtype=np.int32)
+        _check(load().gmg_cut_counts(self.h, level, out.ctypes.data_as(C.POINTER(C.c_int))))
+        return out.reshape(-1, 2)
 
     def mask(self, level):
         nb, n = self.level_nblocks(level), self.level_n(level)

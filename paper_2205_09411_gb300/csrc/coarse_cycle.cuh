@@ -1,13 +1,15 @@
 // The coarse part of the V-cycle in one cooperative launch.
 //
 // The levels with few blocks (the root grid and the first refinement levels)
-// hold little data, so one kernel launch per phase would cost far more than
-// the work.  This kernel runs, for levels l_hi .. l_lo, the same sequence as
-// the per-level kernels (Sec. 2.2: N_down red/black sweeps, residual +
-// restriction, FAS right-hand side; exact solve on l_lo; prolongation and
-// N_up sweeps on the way up) with a grid-wide barrier between dependent
-// phases.  Each CTA works through the blocks b = blockIdx.x, +gridDim.x, ...
-// of a phase, so the arithmetic is exactly that of the per-level kernels.
+// hold little data: their phases cost latency, not bandwidth.  This kernel
+// runs, for levels l_hi .. l_lo, the same sequence as the per-level kernels
+// (Sec. 2.2: N_down red/black sweeps, residual + restriction, FAS right-hand
+// side; exact solve on l_lo; prolongation and N_up sweeps on the way up)
+// with a grid-wide barrier between dependent phases; the levels with one
+// block per root run on one CTA per (root, slot) in shared memory (the
+// tail), with CTA barriers only.  In the grid-synced part each CTA works
+// through the blocks b = blockIdx.x, +gridDim.x, ... of a phase, so the
+// arithmetic is exactly that of the per-level kernels.
 #pragma once
 
 #include "kernels.cuh"
@@ -15,9 +17,9 @@
 namespace gmg {
 
 struct GridBar {
-  unsigned int count;
-  unsigned int gen;
-  int err;
+  unsigned int count;  // arrivals during the current launch
+  unsigned int unused;
+  int err;             // first error recorded by a wait that ran out
   int pad;
 };
 

@@ -1076,6 +1076,17 @@ int gmg_get_distances(const gmg_tree *t, int level, double *out) {
   return GMG_OK;
 }
 
+int gmg_cut_counts(const gmg_tree *t, int level, int *counts) {
+  if (!t || !counts || !t->stencils_ready || level < t->lmin || level > t->lmax)
+    return set_error("bad arguments or stencils not stored"), GMG_ERR_INVALID_ARG;
+  const LevelInfo &L = t->lev(level);
+  for (int i = 0; i < L.count; i++) {
+    counts[2 * i] = t->cut_list_h[4 * (size_t)(L.first + i) + 1];
+    counts[2 * i + 1] = t->cut_list_h[4 * (size_t)(L.first + i) + 2];
+  }
+  return GMG_OK;
+}
+
 int gmg_get_mask(const gmg_tree *t, int level, int *out) {
   if (!t || !out || !t->stencils_ready || level < t->lmin || level > t->lmax)
     return set_error("bad arguments or stencils not stored"), GMG_ERR_INVALID_ARG;

@@ -1,7 +1,8 @@
 """CPU tests of the CUDA library's host logic: the shared library loads and
 exports every function of include/gmg.h, and its block tree, leaf order and
-boundary set-up (mask, line-search distances, cut-block counts) equal the
-oracle's bit for bit.  No device call is made."""
+boundary set-up (mask, line-search distances, cut-block counts, the
+kernels' per-colour cut lists) equal the oracle's bit for bit.  No device
+call is made."""
 import ctypes
 import os
 import re
@@ -64,6 +65,15 @@ def test_tree_and_setup_equal_oracle(G, name):
         dg, do = t.distances(lev), o.get_d(lev)
         assert np.array_equal(dg, do), np.abs(dg - do).max()
         assert t.num_cut_blocks(lev) == o.num_cut_blocks(lev)
+        # the kernels' cut lists hold, per block and colour, exactly the
+        # cells with some line-search distance below 1 (counted here from
+        # the oracle's distances)
+        n, D = t.level_n(lev), p["dim"]
+        c = np.arange(n ** D)
+        colour = (c % n + (c // n) % n + (c // (n * n) if D == 3 else 0)) % 2
+        flagged = (do < 1.0).any(axis=2)
+        expect = np.stack([(flagged & (colour == 0)).sum(1), (flagged & (colour == 1)).sum(1)], axis=1)
+        assert np.array_equal(t.cut_counts(lev), expect)
     assert np.array_equal(t.leaf_centers(), o.leaf_centers())
 
 
@@ -121,6 +131,9 @@ def test_forest_structure():
     assert F.lmin == trees[0].lmin and F.lmax == max(t.lmax for t in trees)
     for l in range(F.lmin, F.lmax + 1):
         assert F.level_info(l)[0] == sum(t.level_info(l)[0] for t in trees if l <= t.lmax)
+        # the forest's cut lists are its trees', level by level, tree by tree
+        want = np.concatenate([t.cut_counts(l) for t in trees if l <= t.lmax])
+        assert np.array_equal(F.cut_counts(l), want)
     xc = F.leaf_centers()
     off = 0
     for i, t in enumerate(trees):
