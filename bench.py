@@ -144,7 +144,8 @@ def dist_setup(n_gpus):
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     return world, rank, local
 
@@ -155,14 +156,34 @@ def barrier(world):
         dist.barrier()
 
 
-def allreduce_max(x, world):
+def _allreduce(x, world, op):
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def allreduce_max(x, world):
+    """The largest x over the ranks (the job's time is its slowest replica's)."""
+    import torch.distributed as dist
+    return _allreduce(x, world, dist.ReduceOp.MAX if world > 1 else None)
+
+
+def allreduce_sum(x, world):
+    """The sum of x over the ranks (work done by all replicas)."""
+    import torch.distributed as dist
+    return _allreduce(x, world, dist.ReduceOp.SUM if world > 1 else None)
+
+
+def replica_rate(units, ms, world):
+    """Whole-job throughput of independent replicas, in millions per second:
+    the units all ranks processed over the slowest rank's time (each rank
+    passes its own units and milliseconds)."""
+    return allreduce_sum(units, world) / (allreduce_max(ms, world) * 1e-3) / 1e6
 
 
 def build_tree(G, p):
@@ -765,8 +786,8 @@ def run_ours(args):
     # time the kernels and not the host)
     mixed["prof"] = timed(G.MIXED, profile=True)["prof"]
 
-    def munks(r):
-        return world * n * r["cycles"] / (r["total_ms"] * 1e-3) / 1e6
+    def munks(r):  # r["total_ms"] is already the maximum over the ranks
+        return replica_rate(n * r["cycles"], r["total_ms"], world)
 
     def lat(r):
         ts = sorted(r["times"])
