@@ -82,7 +82,10 @@ extern "C" {
  * mapped into the device's address space (cudaHostAlloc, cudaHostRegister,
  * pinned PyTorch tensors) is read or written by the library's kernels
  * directly over the CPU-GPU link; pageable host memory is staged through
- * device memory with cudaMemcpyAsync.  Same values either way. */
+ * device memory with cudaMemcpyAsync.  Same values either way.  As with any
+ * asynchronous copy from page-locked memory, a page-locked input must stay
+ * unchanged until the stream has passed the call (calls that return host
+ * results synchronise the stream before they return). */
 #define GMG_HOST 0
 #define GMG_DEVICE 1
 
