@@ -238,11 +238,15 @@ def algorithmic_bytes(kind, prec, level, t, leaf_level, nrhs=1):
 
 
 def source_hash():
+    """Hash of the library's device code (the .cu, .cuh and .h files of csrc,
+    which hold every kernel and its launches); the host-only set-up (.cpp)
+    does not enter it."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2205_09411_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
     return h.hexdigest()[:16]
 
 
