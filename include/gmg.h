@@ -58,7 +58,7 @@ extern "C" {
 #define GMG_ERR_STATE (-6)         /* call out of order (e.g. solve before bind)   */
 #define GMG_ERR_TIMEOUT (-7)       /* a bounded device-side wait ran out           */
 
-/* domain wall boundary conditions (reading W of the design notes) */
+/* domain wall boundary conditions: Dirichlet ghost 2 phi_w - phi_i, Neumann ghost phi_i */
 #define GMG_WALL_DIRICHLET 0
 #define GMG_WALL_NEUMANN 1 /* zero normal derivative */
 
@@ -72,6 +72,11 @@ extern "C" {
 #define GMG_LSF_SHAPE 5     /* the sharp shapes of Sec. 4.3: p[0] = 0 spheroid, 1 rhombus, 2 heart,
                                3 astroid in the coordinates (p, q) = (4 (x - 1/2), 4 (y - 1/2)),
                                or with p[1] = 1 revolved: (4 (sqrt(x^2 + y^2) - 1/2), 4 (z - 1/2)) */
+#define GMG_LSF_GRID 6      /* samples of f on a uniform grid, interpolated (bi/tri)linearly:
+                               p[0..2] sample counts (>= 2 on each used axis), p[3..5] position of
+                               sample 0, p[6..8] spacing (> 0); `user` points to the samples
+                               (double, x fastest), caller-owned, alive while the tree may set up
+                               or re-mesh; points outside the sampled box take the nearest face */
 
 /* solver arithmetic */
 #define GMG_FP64 0  /* FAS V-cycles in FP64                                            */
@@ -165,6 +170,15 @@ int gmg_set_walls(gmg_tree *tree, const int *types, const double *values, gmg_fn
  * and the coarsest-level inverse.  Runs on the host before gmg_tree_bind
  * (results are uploaded by gmg_tree_bind).  Errors: STATE if already bound. */
 int gmg_store_stencils(gmg_tree *tree, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, double phib_const);
+
+/* A new boundary value phi_b (phib(x0, user), or phib_const when phib ==
+ * NULL) on the stored boundary: phi_b at every located root and the moved
+ * coefficients' right-hand-side terms are recomputed from the stored
+ * distances, without new line searches (the stencils do not depend on
+ * phi_b).  Gives the boundary terms a full gmg_store_stencils with the new
+ * value gives.  After gmg_store_stencils, before gmg_tree_bind (a single
+ * tree; forests take trees set up this way).  Errors: STATE otherwise. */
+int gmg_set_boundary_value(gmg_tree *tree, gmg_fn phib, void *phib_user, double phib_const);
 
 /* Forest of independent problems (the batched form of the method: many
  * trees, each with its own level set, boundary values, refinement and size,
@@ -327,6 +341,10 @@ int gmg_num_cut_blocks(const gmg_tree *tree, int level);
  * cells and their coefficients in per-colour lists.  counts: 2 * (blocks of
  * the level) ints, caller-owned. */
 int gmg_cut_counts(const gmg_tree *tree, int level, int *counts);
+/* Right-hand-side boundary terms of a level (host, after gmg_store_stencils):
+ * nb * N^D values in canonical block order (0 for blocks without any), the
+ * term subtracted from the source g of each leaf cell. */
+int gmg_get_boundary_terms(const gmg_tree *tree, int level, double *out);
 
 /* Number of kernels the last gmg_vcycle / gmg_solve call enqueued. */
 long long gmg_last_launch_count(const gmg_tree *tree);

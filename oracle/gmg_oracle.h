@@ -25,7 +25,7 @@
  *   unresolved roots on coarse grids ................ Sec. 3.6.3
  *
  * Where the paper is silent or ambiguous the oracle takes the readings listed
- * at the top of gmg_oracle.c (same identifiers as in the design notes).
+ * at the top of gmg_oracle.c.
  *
  * Parity pins: see the comment above each exported function; the only
  * function without an independent pin is the per-V-cycle convergence rate

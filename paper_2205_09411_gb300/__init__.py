@@ -23,7 +23,7 @@ LIB_PATH = _build.LIB
 FP64, MIXED = 0, 1
 HOST, DEVICE = 0, 1
 WALL_DIRICHLET, WALL_NEUMANN = 0, 1
-LSF_KINDS = {"none": 0, "sphere": 1, "capsule": 2, "ellipsoid": 3, "callback": 4, "shape": 5}
+LSF_KINDS = {"none": 0, "sphere": 1, "capsule": 2, "ellipsoid": 3, "callback": 4, "shape": 5, "grid": 6}
 
 FN = C.CFUNCTYPE(C.c_double, C.POINTER(C.c_double), C.c_void_p)
 REFINE_FN = C.CFUNCTYPE(C.c_int, C.c_int, C.POINTER(C.c_int), C.c_void_p)
@@ -82,6 +82,8 @@ def load():
         "gmg_leaf_centers": (C.c_int, [vp, dp]),
         "gmg_set_walls": (C.c_int, [vp, ip, dp, FN, vp]),
         "gmg_store_stencils": (C.c_int, [vp, C.POINTER(Lsf), FN, vp, C.c_double]),
+        "gmg_set_boundary_value": (C.c_int, [vp, FN, vp, C.c_double]),
+        "gmg_get_boundary_terms": (C.c_int, [vp, C.c_int, dp]),
         "gmg_workspace_bytes": (C.c_int, [vp, C.POINTER(sz)]),
         "gmg_tree_bind": (C.c_int, [vp, vp, sz]),
         "gmg_set_num_rhs": (C.c_int, [vp, C.c_int]),
@@ -288,7 +290,9 @@ class Tree:
                                     v.ctypes.data_as(C.POINTER(C.c_double)), cb, None))
 
     def store_stencils(self, lsf=None, phib=0.0):
-        """lsf: None, (kind, params) with kind in LSF_KINDS, or a callable f(x)."""
+        """lsf: None, (kind, params) with kind in LSF_KINDS, a callable f(x), or
+        ("grid", (values, origin, spacing)) with values[i, j(, k)] the level set
+        at origin + (i, j, k) * spacing (interpolated (bi/tri)linearly)."""
         s = Lsf()
         if lsf is None:
             s.kind = 0
@@ -296,6 +300,19 @@ class Tree:
             s.kind = LSF_KINDS["callback"]
             s.fn = _fn(lsf)
             self._keep.append(s.fn)
+        elif lsf[0] == "grid":
+            values, origin, spacing = lsf[1]
+            values = np.asarray(values, dtype=np.float64)
+            assert values.ndim == self.dim
+            samples = np.ascontiguousarray(values.transpose())  # x fastest
+            self._keep.append(samples)
+            s.kind = LSF_KINDS["grid"]
+            for d in range(self.dim):
+                s.p[d] = float(values.shape[d])
+                s.p[3 + d] = float(origin[d])
+                s.p[6 + d] = float(spacing[d] if np.ndim(spacing) else spacing)
+            s.user = samples.ctypes.data
+            s.fn = FN()
         else:
             kind, params = lsf
             s.kind = LSF_KINDS[kind]
@@ -309,6 +326,23 @@ class Tree:
             _check(load().gmg_store_stencils(self.h, C.byref(s), cb, None, 0.0))
         else:
             _check(load().gmg_store_stencils(self.h, C.byref(s), FN(), None, float(phib)))
+
+    def set_boundary_value(self, phib):
+        """New boundary value (constant or callable f(x)) on the stored boundary:
+        boundary terms recomputed from the stored distances, no line search."""
+        if callable(phib):
+            cb = _fn(phib)
+            self._keep.append(cb)
+            _check(load().gmg_set_boundary_value(self.h, cb, None, 0.0))
+        else:
+            _check(load().gmg_set_boundary_value(self.h, FN(), None, float(phib)))
+
+    def boundary_terms(self, level):
+        """(blocks, n^dim): the right-hand-side boundary term of every cell of a level."""
+        nb, n = self.level_nblocks(level), self.level_n(level)
+        out = np.zeros(nb * n ** self.dim)
+        _check(load().gmg_get_boundary_terms(self.h, level, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out.reshape(nb, n ** self.dim)
 
     def num_cut_blocks(self, level):
         return load().gmg_num_cut_blocks(self.h, level)

@@ -266,6 +266,36 @@ int build_tree(gmg_tree *T, const gmg_domain *dom) {
 
 namespace {
 
+// Level set sampled on a uniform grid (GMG_LSF_GRID): (bi/tri)linear
+// interpolation between the 2^D samples around x; coordinates outside the
+// sampled box are clamped to it.  p[0..2] counts, p[3..5] position of
+// sample 0, p[6..8] spacing; samples x fastest.
+double grid_lsf(const double *p, const double *v, int D, const double *x) {
+  int i0[3] = {0, 0, 0};
+  double w[3] = {0.0, 0.0, 0.0};
+  const long long stride[3] = {1, (long long)p[0], (long long)p[0] * (long long)p[1]};
+  for (int d = 0; d < D; d++) {
+    const int n = (int)p[d];
+    double t = (x[d] - p[3 + d]) / p[6 + d];
+    t = std::min(std::max(t, 0.0), (double)(n - 1));
+    const int i = std::min((int)std::floor(t), n - 2);
+    i0[d] = i;
+    w[d] = t - i;
+  }
+  double s = 0.0;
+  for (int corner = 0; corner < (1 << D); corner++) {
+    double wt = 1.0;
+    long long idx = 0;
+    for (int d = 0; d < D; d++) {
+      const int b = (corner >> d) & 1;
+      wt *= b ? w[d] : 1.0 - w[d];
+      idx += (long long)(i0[d] + b) * stride[d];
+    }
+    s += wt * v[idx];
+  }
+  return s;
+}
+
 struct HostLsf {
   const gmg_lsf *L;
   LsfSpec spec;
@@ -275,6 +305,7 @@ struct HostLsf {
       double xx[3] = {x[0], D > 1 ? x[1] : 0.0, D > 2 ? x[2] : 0.0};
       return L->fn(xx, L->user);
     }
+    if (L->kind == GMG_LSF_GRID) return grid_lsf(L->p, static_cast<const double *>(L->user), D, x);
     return lsf_builtin(spec, D, x);
   }
 };
@@ -383,6 +414,71 @@ bool invert(int n, std::vector<double> &A, std::vector<double> &inv) {
   return true;
 }
 
+// Eq. (lpl-1d-lsf) per dimension for every cell of block B from its distances
+// dd[nc x 2D]: the stencil st[(2D+1) x nc], the boundary value phi_b(x0) at
+// each located root pb[nc x 2D] (0 where d = 1) and the right-hand-side term
+// bt[nc] (moved coefficients times phi_b, plus the Dirichlet wall terms).
+// The full set-up and gmg_set_boundary_value share it.
+void block_terms(const gmg_tree *T, const HostBlock &B, const LevelInfo &L, const double *dd, bool cut, gmg_fn phib,
+                 void *phib_user, double phib_const, std::vector<double> &st, std::vector<double> &bt,
+                 std::vector<double> &pb) {
+  const int D = T->D, S = 2 * D + 1, n = L.n, nc = L.ncell;
+  const double h = L.h;
+  pb.assign((size_t)nc * 2 * D, 0.0);
+  st.assign((size_t)S * nc, 0.0);
+  bt.assign(nc, 0.0);
+  const double inv_h2 = 1.0 / (h * h);
+  for (int c = 0; c < nc; c++) {
+    int p[3] = {c % n, (c / n) % n, D == 3 ? c / (n * n) : 0};
+    double a[3];
+    cell_center(T, B, L, p, a);
+    const double *dc = &dd[(size_t)c * 2 * D];
+    double diag = 0.0, bnd = 0.0;
+    double coef[6];
+    for (int k = 0; k < D; k++) {
+      double dm = dc[2 * k], dp = dc[2 * k + 1];
+      double cm = 2.0 * inv_h2 / ((dp + dm) * dm);
+      double cp = 2.0 * inv_h2 / ((dp + dm) * dp);
+      diag = diag - (cm + cp);
+      if (dm < 1.0) {
+        double x0[3] = {a[0], a[1], a[2]};
+        x0[k] = a[k] - dm * h;
+        pb[(size_t)c * 2 * D + 2 * k] = phib ? phib(x0, phib_user) : phib_const;
+        bnd = bnd + cm * pb[(size_t)c * 2 * D + 2 * k];
+        cm = 0.0;
+      }
+      if (dp < 1.0) {
+        double x0[3] = {a[0], a[1], a[2]};
+        x0[k] = a[k] + dp * h;
+        pb[(size_t)c * 2 * D + 2 * k + 1] = phib ? phib(x0, phib_user) : phib_const;
+        bnd = bnd + cp * pb[(size_t)c * 2 * D + 2 * k + 1];
+        cp = 0.0;
+      }
+      coef[2 * k] = cm;
+      coef[2 * k + 1] = cp;
+    }
+    st[c] = diag;
+    for (int k = 0; k < 2 * D; k++) st[(size_t)(1 + k) * nc + c] = coef[k];
+    // Dirichlet wall terms (ghost 2 phi_w - phi_i): coefficient * 2 phi_w
+    double t = cut ? bnd : 0.0;
+    for (int k = 0; k < D; k++)
+      for (int s = 0; s < 2; s++) {
+        int G[3];
+        for (int d = 0; d < 3; d++) G[d] = d < D ? B.ix[d] * n + p[d] : 0;
+        G[k] += s ? 1 : -1;
+        if (in_domain(L, D, G)) continue;
+        int w = 2 * k + s;
+        if (T->wall_type[w] != GMG_WALL_DIRICHLET) continue;
+        double cw = cut ? coef[2 * k + s] : inv_h2;
+        double xf[3] = {a[0], a[1], a[2]};
+        xf[k] = s ? a[k] + 0.5 * h : a[k] - 0.5 * h;
+        double v = T->wall_fn ? T->wall_fn(xf, T->wall_user) : T->wall_val[w];
+        t = t + cw * (2.0 * v);
+      }
+    bt[c] = t;
+  }
+}
+
 }  // namespace
 
 int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, double phib_const,
@@ -391,8 +487,13 @@ int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, do
   gmg_lsf none{};
   none.kind = GMG_LSF_NONE;
   if (!lsf) lsf = &none;
-  if (lsf->kind < GMG_LSF_NONE || lsf->kind > GMG_LSF_SHAPE || (lsf->kind == GMG_LSF_CALLBACK && !lsf->fn))
+  if (lsf->kind < GMG_LSF_NONE || lsf->kind > GMG_LSF_GRID || (lsf->kind == GMG_LSF_CALLBACK && !lsf->fn))
     return set_error("invalid level-set specification"), GMG_ERR_INVALID_ARG;
+  if (lsf->kind == GMG_LSF_GRID) {
+    bool ok = lsf->user != nullptr;
+    for (int d = 0; d < D; d++) ok = ok && lsf->p[d] >= 2.0 && lsf->p[6 + d] > 0.0;
+    if (!ok) return set_error("grid level set: samples, counts >= 2 and spacings > 0 needed"), GMG_ERR_INVALID_ARG;
+  }
   T->lsf_spec = *lsf;
   T->phib_fn = phib;
   T->phib_user = phib_user;
@@ -470,59 +571,7 @@ int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, do
       for (int k = 0; k < 2 * D; k++)
         if (dc[k] < 1.0) cut = true;
     }
-    // Eq. (lpl-1d-lsf) per dimension; boundary neighbours go to the RHS
-    st.assign((size_t)S * nc, 0.0);
-    bt.assign(nc, 0.0);
-    const double inv_h2 = 1.0 / (h * h);
-    for (int c = 0; c < nc; c++) {
-      int p[3] = {c % n, (c / n) % n, D == 3 ? c / (n * n) : 0};
-      double a[3];
-      cell_center(T, B, L, p, a);
-      const double *dc = &dd[(size_t)c * 2 * D];
-      double diag = 0.0, bnd = 0.0;
-      double coef[6];
-      for (int k = 0; k < D; k++) {
-        double dm = dc[2 * k], dp = dc[2 * k + 1];
-        double cm = 2.0 * inv_h2 / ((dp + dm) * dm);
-        double cp = 2.0 * inv_h2 / ((dp + dm) * dp);
-        diag = diag - (cm + cp);
-        if (dm < 1.0) {
-          double x0[3] = {a[0], a[1], a[2]};
-          x0[k] = a[k] - dm * h;
-          pb[(size_t)c * 2 * D + 2 * k] = phib ? phib(x0, phib_user) : phib_const;
-          bnd = bnd + cm * pb[(size_t)c * 2 * D + 2 * k];
-          cm = 0.0;
-        }
-        if (dp < 1.0) {
-          double x0[3] = {a[0], a[1], a[2]};
-          x0[k] = a[k] + dp * h;
-          pb[(size_t)c * 2 * D + 2 * k + 1] = phib ? phib(x0, phib_user) : phib_const;
-          bnd = bnd + cp * pb[(size_t)c * 2 * D + 2 * k + 1];
-          cp = 0.0;
-        }
-        coef[2 * k] = cm;
-        coef[2 * k + 1] = cp;
-      }
-      st[c] = diag;
-      for (int k = 0; k < 2 * D; k++) st[(size_t)(1 + k) * nc + c] = coef[k];
-      // Dirichlet wall terms (ghost 2 phi_w - phi_i): coefficient * 2 phi_w
-      double t = cut ? bnd : 0.0;
-      for (int k = 0; k < D; k++)
-        for (int s = 0; s < 2; s++) {
-          int G[3];
-          for (int d = 0; d < 3; d++) G[d] = d < D ? B.ix[d] * n + p[d] : 0;
-          G[k] += s ? 1 : -1;
-          if (in_domain(L, D, G)) continue;
-          int w = 2 * k + s;
-          if (T->wall_type[w] != GMG_WALL_DIRICHLET) continue;
-          double cw = cut ? coef[2 * k + s] : inv_h2;
-          double xf[3] = {a[0], a[1], a[2]};
-          xf[k] = s ? a[k] + 0.5 * h : a[k] - 0.5 * h;
-          double v = T->wall_fn ? T->wall_fn(xf, T->wall_user) : T->wall_val[w];
-          t = t + cw * (2.0 * v);
-        }
-      bt[c] = t;
-    }
+    block_terms(T, B, L, dd.data(), cut, phib, phib_user, phib_const, st, bt, pb);
     o.cut = cut;
     if (cut) {
       o.st = std::move(st);
@@ -732,3 +781,50 @@ void build_cut_lists(gmg_tree *T) {
 }
 
 }  // namespace gmg
+
+extern "C" {
+
+int gmg_set_boundary_value(gmg_tree *t, gmg_fn phib, void *phib_user, double phib_const) {
+  using namespace gmg;
+  if (!t) return set_error("null tree"), GMG_ERR_INVALID_ARG;
+  if (!t->stencils_ready || t->bound || t->ntree != 1)
+    return set_error("the boundary value changes after gmg_store_stencils and before gmg_tree_bind, on a single tree"),
+           GMG_ERR_STATE;
+  std::vector<double> st, bt, pb;
+  for (size_t id = 0; id < t->blocks.size(); id++) {
+    const long long db = t->dist_base_h[id];
+    if (db < 0) continue;  // no cut: the block's terms do not involve phi_b
+    const HostBlock &B = t->blocks[id];
+    const LevelInfo &L = t->lev(B.level);
+    const int nc = L.ncell;
+    block_terms(t, B, L, &t->dist_h[db], true, phib, phib_user, phib_const, st, bt, pb);
+    std::copy(pb.begin(), pb.end(), t->bphib_h.begin() + db);
+    bool any = false;
+    for (int c = 0; c < nc; c++) any = any || bt[c] != 0.0;
+    if (t->bt_base_h[id] >= 0) {
+      std::copy(bt.begin(), bt.end(), t->bterm_h.begin() + t->bt_base_h[id]);
+    } else if (any) {
+      t->bt_base_h[id] = (long long)t->bterm_h.size();
+      t->bterm_h.insert(t->bterm_h.end(), bt.begin(), bt.end());
+    }
+  }
+  t->phib_fn = phib;
+  t->phib_user = phib_user;
+  t->phib_const = phib_const;
+  return GMG_OK;
+}
+
+int gmg_get_boundary_terms(const gmg_tree *t, int level, double *out) {
+  using namespace gmg;
+  if (!t || !out || !t->stencils_ready || level < t->lmin || level > t->lmax)
+    return set_error("bad arguments or stencils not stored"), GMG_ERR_INVALID_ARG;
+  const LevelInfo &L = t->lev(level);
+  size_t k = 0;
+  for (int i = 0; i < L.count; i++) {
+    const long long bb = t->bt_base_h[L.first + i];
+    for (int c = 0; c < L.ncell; c++) out[k++] = bb >= 0 ? t->bterm_h[bb + c] : 0.0;
+  }
+  return GMG_OK;
+}
+
+}  // extern "C"

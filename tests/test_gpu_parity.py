@@ -324,3 +324,20 @@ def test_sharp_shapes_match_oracle(shape, dim):
     t.fmg(2)
     ref = o.solution()
     assert np.abs(t.solution() - ref).max() <= TOL_ITERATE * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("name", ["c1", "adaptive3d"])
+def test_solve_after_new_boundary_value(name):
+    """A tree whose boundary value was changed after its set-up solves to
+    the same solution, bit for bit, as a tree set up with that value."""
+    p = parity_cases()[name]
+    out = []
+    for changed in (True, False):
+        t = gpu_problem(dict(p, phib=0.7) if changed else dict(p, phib=1.9), bind=False)
+        if changed:
+            t.set_boundary_value(1.9)
+        t.bind()
+        t.set_rhs(np.asarray(p["rhs"](t.leaf_centers()), dtype=np.float64))
+        st = t.solve(0, 1e-10, 40)
+        out.append((t.solution().copy(), st["cycles"]))
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]

@@ -185,3 +185,107 @@ def test_remesh_setup_equals_full_setup():
     assert reused > 0 and computed + reused == new.n_blocks
     assert computed <= new.n_blocks - old.n_blocks + 8  # new blocks only (a few may be removed ones)
     assert ref.setup_counts() == (ref.n_blocks, 0)
+
+
+@pytest.mark.parametrize("name", ["c1", "adaptive3d", "needle4"])
+def test_set_boundary_value_equals_full_setup(G, name):
+    """A new boundary value on the stored boundary (no new line searches)
+    gives the boundary terms, distances and cut lists of a full set-up with
+    that value, bit for bit: a constant, and a function of x."""
+    p = parity_cases()[name]
+    for new in (2.5, lambda x: 1.0 + x[0] - 0.5 * x[1] + x[0] * x[1]):
+        a = gpu_problem(dict(p, phib=0.3 if callable(p["phib"]) else p["phib"]), bind=False)
+        a.set_boundary_value(new)
+        b = gpu_problem(dict(p, phib=new), bind=False)
+        for lev in range(a.lmin, a.lmax + 1):
+            assert np.array_equal(a.boundary_terms(lev), b.boundary_terms(lev))
+            assert np.array_equal(a.distances(lev), b.distances(lev))
+            assert np.array_equal(a.cut_counts(lev), b.cut_counts(lev))
+
+
+def test_set_boundary_value_needs_stored_stencils(G):
+    p = parity_cases()["c1"]
+    t = G.Tree(p["dim"], p["N"], p["cb"], p["lo"], p["h1"], p["max_level"])
+    with pytest.raises(G.GmgError):
+        t.set_boundary_value(1.0)
+
+
+def _multilinear(values, origin, spacing, x):
+    """Reference interpolation of gridded samples (numpy, independent of the
+    library's): clamp to the sampled box, weights from the cell position."""
+    dim = values.ndim
+    i0, w = [], []
+    for d in range(dim):
+        n = values.shape[d]
+        t = min(max((x[d] - origin[d]) / spacing, 0.0), n - 1.0)
+        i = min(int(np.floor(t)), n - 2)
+        i0.append(i)
+        w.append(t - i)
+    s = 0.0
+    for corner in range(1 << dim):
+        wt, idx = 1.0, []
+        for d in range(dim):
+            bit = (corner >> d) & 1
+            wt *= w[d] if bit else 1.0 - w[d]
+            idx.append(i0[d] + bit)
+        s += wt * values[tuple(idx)]
+    return s
+
+
+def _grid_tree(G, p, lsf):
+    t = G.Tree(p["dim"], p["N"], p["cb"], p["lo"], p["h1"], p["max_level"], refine=p["refine"],
+               max_coarse_cells=p.get("max_coarse_cells") or (64 if p["dim"] == 2 else 512))
+    t.set_walls(p["walls"], values=p.get("wall_values"), fn=p.get("wall_fn"))
+    t.store_stencils(lsf, p["phib"])
+    return t
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_grid_level_set_reproduces_a_plane(G, dim):
+    """Multilinear interpolation is exact on linear data: a plane sampled on
+    a coarse grid gives the line-search distances of the plane itself (to
+    the search tolerance)."""
+    p = dict(parity_cases()["c1" if dim == 2 else "c2_32"])
+    nrm = np.array([0.6, -0.48, 0.64][:dim])
+    c = -0.2
+
+    def plane(x):
+        return float(np.dot(nrm, np.asarray(x)[:dim]) + c)
+    m = 9
+    axes = [np.linspace(0.0, 1.0, m)] * dim
+    grid = np.meshgrid(*axes, indexing="ij")
+    values = sum(nrm[d] * grid[d] for d in range(dim)) + c
+    a = _grid_tree(G, p, ("grid", (values, [0.0] * dim, 1.0 / (m - 1))))
+    b = _grid_tree(G, p, plane)
+    for lev in range(a.lmin, a.lmax + 1):
+        da, db = a.distances(lev), b.distances(lev)
+        assert np.abs(da - db).max() <= 2e-8
+        assert a.num_cut_blocks(lev) == b.num_cut_blocks(lev)
+
+
+@pytest.mark.parametrize("name", ["c1", "adaptive3d"])
+def test_grid_level_set_equals_oracle(G, name):
+    """A sphere sampled on a grid: the library's set-up with the grid level
+    set equals the oracle's with an independent numpy interpolation of the
+    same samples (distances to the search tolerance, masks exactly)."""
+    import oracle as O
+    p = parity_cases()[name]
+    dim = p["dim"]
+    centre, radius = np.asarray(p["lsf"][1][:dim]), p["lsf"][1][3] if len(p["lsf"][1]) > 3 else 0.25
+    m = 65
+    lo = np.asarray(p["lo"][:dim])
+    span = 1.0 / (m - 1) * 1.2
+    axes = [lo[d] - 0.1 + np.arange(m) * span for d in range(dim)]
+    grid = np.meshgrid(*axes, indexing="ij")
+    values = np.sqrt(sum((grid[d] - centre[d]) ** 2 for d in range(dim))) - radius
+    origin = [axes[d][0] for d in range(dim)]
+    t = _grid_tree(G, p, ("grid", (values, origin, span)))
+    o = O.OracleTree(dim, p["N"], p["cb"], p["lo"], p["h1"], p["max_level"], refine=p["refine"],
+                     max_coarse_cells=p.get("max_coarse_cells"))
+    o.set_params(2, 2, 1e-8, 1.5, p.get("w_min", 0.0))
+    o.set_lsf(O.LSF_CALLBACK, (), fn=lambda x: _multilinear(values, origin, span, x))
+    o.set_walls(p["walls"], values=p.get("wall_values"), fn=p.get("wall_fn"))
+    o.store_stencils(p["phib"])
+    for lev in range(t.lmin, t.lmax + 1):
+        assert np.array_equal(t.mask(lev), o.get_mask(lev))
+        assert np.abs(t.distances(lev) - o.get_d(lev)).max() <= 2e-8
