@@ -294,6 +294,14 @@ int gmg_residual_noalloc(gmg_tree *tree, double *out, void *stream);
  * convergence test).
  * Errors: NOT_CONVERGED after max_cycles, NONFINITE on NaN or growth. */
 int gmg_solve(gmg_tree *tree, int precision, double rel_tol, int max_cycles, gmg_stats *stats, void *stream);
+/* gmg_solve with the residual history: the same loop, stopping and failure
+ * rules, and device work per step, run through gmg_iterate.  history:
+ * (max_cycles + 1) x (nrhs * n_trees) doubles, caller-owned, step-major:
+ * history[k * units + u] is unit u's relative L2 residual after step k
+ * (step 0: the first residual; a unit keeps its value once it has
+ * converged), NaN after the last step.  stats as in gmg_solve. */
+int gmg_solve_history(gmg_tree *tree, int precision, double rel_tol, int max_cycles, double *history,
+                      gmg_stats *stats, void *stream);
 /* One step of the solve loop on the units with active[u] != 0 (host array
  * of nrhs * n_trees ints; the other units are left untouched): residual_only != 0 runs
  * the composite residual only (the first step of a new right-hand side; in

@@ -109,6 +109,7 @@ def load():
         "gmg_efield": (C.c_int, [vp, vp, C.c_int, vp]),
         "gmg_residual": (C.c_int, [vp, dp, dp, vp]),
         "gmg_solve": (C.c_int, [vp, C.c_int, C.c_double, C.c_int, C.POINTER(Stats), vp]),
+        "gmg_solve_history": (C.c_int, [vp, C.c_int, C.c_double, C.c_int, dp, C.POINTER(Stats), vp]),
         "gmg_get_level": (C.c_int, [vp, C.c_int, C.c_int, dp, vp]),
         "gmg_get_distances": (C.c_int, [vp, C.c_int, dp]),
         "gmg_get_mask": (C.c_int, [vp, C.c_int, ip]),
@@ -502,6 +503,22 @@ class Tree:
         return dict(rc=rc, cycles=max(x["cycles"] for x in units), rel_l2=max(x["rel_l2"] for x in units),
                     linf=max(x["linf"] for x in units), bnorm=min(x["bnorm"] for x in units), slots=units,
                     units=units)
+
+    def solve_history(self, precision=FP64, rel_tol=1e-8, max_cycles=50, stream=None, check=True):
+        """solve() through gmg_solve_history: the same result, plus 'history',
+        an array (steps + 1, units) of relative residuals after every step."""
+        st = (Stats * self.units)()
+        hist = np.full((max_cycles + 1) * self.units, np.nan)
+        rc = load().gmg_solve_history(self.h, precision, rel_tol, max_cycles,
+                                      hist.ctypes.data_as(C.POINTER(C.c_double)), st, _stream_ptr(stream))
+        if check:
+            _check(rc)
+        hist = hist.reshape(max_cycles + 1, self.units)
+        steps = int(np.isfinite(hist[:, 0]).sum())
+        units = [dict(cycles=x.cycles, rel_l2=x.rel_l2, linf=x.linf, bnorm=x.bnorm) for x in st]
+        out = dict(rc=rc, history=hist[:steps], units=units)
+        out.update(units[0] if self.units == 1 else dict(cycles=max(x["cycles"] for x in units)))
+        return out
 
     def tree_leaves(self, i):
         """(offset, count) of tree i's leaf cells in the leaf arrays."""

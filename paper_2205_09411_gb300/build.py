@@ -7,6 +7,8 @@ shared library with a plain C ABI (include/gmg.h):
 * csrc/tree_setup.cpp  - block tree and boundary set-up on the host
   (-ffp-contract=off: the level-set arithmetic is plain IEEE)
 * csrc/noalloc.cu      - residual norm with a static scratch array (no allocation)
+* csrc/forest.cpp      - forests of independent trees (host)
+* csrc/solve_history.cpp - the solve loop with its residual history (host)
 """
 import os
 import subprocess
@@ -20,7 +22,7 @@ LIB = os.path.join(OUT, "libgmg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
           "-I", os.path.join(ROOT, "include"), "-I", CSRC]
-SOURCES = ["gmg_api.cu", "tree_setup.cpp", "noalloc.cu", "forest.cpp"]
+SOURCES = ["gmg_api.cu", "tree_setup.cpp", "noalloc.cu", "forest.cpp", "solve_history.cpp"]
 
 
 def _nvcc():

@@ -341,3 +341,20 @@ def test_solve_after_new_boundary_value(name):
         st = t.solve(0, 1e-10, 40)
         out.append((t.solution().copy(), st["cycles"]))
     assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+
+
+@pytest.mark.parametrize("name,prec", [("c1", 0), ("needle4", 1), ("adaptive3d", 0)])
+def test_solve_history_equals_solve(name, prec):
+    """The solve loop run step by step with its residual history gives
+    gmg_solve's solution and cycle count bit for bit; the history starts at
+    1 (phi = 0), ends at the returned residual and falls every step."""
+    p = parity_cases()[name]
+    t = gpu_problem(p)
+    st = t.solve(prec, 1e-9, 60)
+    ref = t.solution().copy()
+    t.set_rhs(np.asarray(p["rhs"](t.leaf_centers()), dtype=np.float64))
+    h = t.solve_history(prec, 1e-9, 60)
+    assert np.array_equal(t.solution(), ref) and h["cycles"] == st["cycles"]
+    hist = h["history"][:, 0]
+    assert len(hist) == st["cycles"] + 1 and hist[0] == 1.0 and hist[-1] == h["rel_l2"] <= 1e-9
+    assert np.all(np.diff(hist) < 0)
