@@ -131,7 +131,17 @@ def load():
     return L
 
 
+# Exceptions raised by Python callbacks while the library runs them: ctypes
+# cannot let them cross the C frames, so the callback records the exception,
+# returns a neutral value, and _check raises it once the library call is over.
+_callback_errors = []
+
+
 def _check(rc):
+    if _callback_errors:
+        err = _callback_errors[0]
+        _callback_errors.clear()
+        raise RuntimeError("a Python callback raised during the library call: %r" % (err,)) from err
     if rc != 0:
         L = load()
         raise GmgError(rc, "%s: %s" % (L.gmg_error_string(rc).decode(), L.gmg_last_error().decode()))
@@ -142,8 +152,22 @@ def _fn(f):
         return FN()
 
     def cb(xp, _u):
-        return float(f(np.ctypeslib.as_array(xp, shape=(3,)).copy()))
+        try:
+            return float(f(np.ctypeslib.as_array(xp, shape=(3,)).copy()))
+        except BaseException as e:  # noqa: BLE001 - re-raised by _check
+            _callback_errors.append(e)
+            return float("nan")
     return FN(cb)
+
+
+def _refine_fn(refine):
+    def cb(level, bix, _u):
+        try:
+            return 1 if refine(level, (bix[0], bix[1], bix[2])) else 0
+        except BaseException as e:  # noqa: BLE001 - re-raised by _check
+            _callback_errors.append(e)
+            return 0
+    return REFINE_FN(cb)
 
 
 def _stream_ptr(stream):
@@ -181,9 +205,7 @@ class Tree:
             dom.lo[d] = float(lo[d])
         dom.h_root, dom.max_level, dom.max_coarse_cells = float(h_root), int(max_level), int(max_coarse_cells)
         if refine is not None:
-            def rcb(level, bix, _u):
-                return 1 if refine(level, (bix[0], bix[1], bix[2])) else 0
-            self._refine = REFINE_FN(rcb)
+            self._refine = _refine_fn(refine)
         else:
             self._refine = REFINE_FN()
         dom.refine = self._refine
@@ -216,7 +238,7 @@ class Tree:
         """A new (unbound) tree on this tree's domain and set-up, refined by
         refine(level, bix) -> bool; blocks present here reuse their set-up."""
         L = load()
-        cb = REFINE_FN(lambda level, bix, _u: 1 if refine(level, (bix[0], bix[1], bix[2])) else 0)
+        cb = _refine_fn(refine)
         h = C.c_void_p()
         _check(L.gmg_tree_remesh(self.h, cb, None, int(max_level), C.byref(h)))
         t = Tree.__new__(Tree)

@@ -289,3 +289,47 @@ def test_grid_level_set_equals_oracle(G, name):
     for lev in range(t.lmin, t.lmax + 1):
         assert np.array_equal(t.mask(lev), o.get_mask(lev))
         assert np.abs(t.distances(lev) - o.get_d(lev)).max() <= 2e-8
+
+
+def test_remesh_with_grid_level_set(G):
+    """Re-meshing keeps the level set it was set up with, including a
+    sampled one (the caller's samples stay alive): a refined tree re-meshed
+    from a grid-level-set tree equals a fresh set-up of the refined tree,
+    boundary terms and cut lists included."""
+    from _helpers import refine_near
+    p = dict(parity_cases()["c1"])
+    m = 33
+    ax = np.linspace(-0.05, 1.05, m)
+    X, Y = np.meshgrid(ax, ax, indexing="ij")
+    values = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2) - 0.25
+    lsf = ("grid", (values, [ax[0], ax[0]], ax[1] - ax[0]))
+    old = _grid_tree(G, p, lsf)
+    rule = refine_near((0.75, 0.5), 0.12, p["N"], p["h1"], 2)
+    new = old.remesh(rule, p["max_level"] + 1)
+    fresh = dict(p, refine=rule, max_level=p["max_level"] + 1)
+    ref = _grid_tree(G, fresh, lsf)
+    assert (new.lmin, new.lmax, new.n_blocks) == (ref.lmin, ref.lmax, ref.n_blocks)
+    for lev in range(ref.lmin, ref.lmax + 1):
+        assert np.array_equal(new.distances(lev), ref.distances(lev))
+        assert np.array_equal(new.boundary_terms(lev), ref.boundary_terms(lev))
+        assert np.array_equal(new.cut_counts(lev), ref.cut_counts(lev))
+    assert new.setup_counts()[1] > 0 and new.lmax == old.lmax + 1
+
+
+def test_callback_errors_are_raised(G):
+    """An exception inside a Python callback (refinement rule, level set,
+    boundary value) is raised to the caller once the library call returns,
+    instead of being swallowed by ctypes."""
+    p = parity_cases()["c1"]
+
+    def bad_rule(level, bix):
+        raise ValueError("rule")
+    with pytest.raises(RuntimeError, match="rule"):
+        G.Tree(p["dim"], p["N"], p["cb"], p["lo"], p["h1"], p["max_level"], refine=bad_rule)
+    t = G.Tree(p["dim"], p["N"], p["cb"], p["lo"], p["h1"], p["max_level"])
+    t.set_walls(p["walls"], fn=p["wall_fn"])
+
+    def bad_lsf(x):
+        raise ValueError("lsf")
+    with pytest.raises(RuntimeError, match="lsf"):
+        t.store_stencils(bad_lsf, 1.0)
