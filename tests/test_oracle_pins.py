@@ -131,6 +131,38 @@ def test_distances_and_mask_match_sphere_intersections(dim):
     assert checked > 50
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_distances_from_both_sides_add_to_one(dim):
+    """Invariant of the line search (Sec. 3.2): where the boundary crosses
+    the segment between two neighbouring cell centres once (f changes sign),
+    the relative distances searched from either end add up to 1 (to twice
+    the search tolerance)."""
+    c = np.array([0.52, 0.46, 0.49])[:dim]
+    R = 0.27
+    t = mk(dim, 8, (1, 1, 1), 1 / 8, 3 if dim == 2 else 2)
+    t.set_lsf(O.LSF_SPHERE, tuple(np.r_[c, np.zeros(3 - dim)]) + (R,))
+    t.set_walls([0] * (2 * dim), values=[0.0] * (2 * dim))
+    t.store_stencils(1.0)
+    lmin, lmax = t.levels()
+    pairs = 0
+    for lev in range(lmin, lmax + 1):
+        d = t.get_d(lev).reshape(-1, 2 * dim)
+        xc = t.level_centers(lev)
+        h = t.level_h(lev)
+        where = {tuple(np.round(a / h * 2).astype(int)): i for i, a in enumerate(xc)}
+        f = np.linalg.norm(xc - c, axis=1) - R
+        for i, a in enumerate(xc):
+            for k in range(dim):
+                b = a.copy()
+                b[k] += h
+                j = where.get(tuple(np.round(b / h * 2).astype(int)))
+                if j is None or np.sign(f[i]) == np.sign(f[j]):
+                    continue
+                assert abs(d[i, 2 * k + 1] + d[j, 2 * k] - 1.0) <= 2 * EPS
+                pairs += 1
+    assert pairs > 50
+
+
 # ------------------------------------------------------------ discretisation
 @pytest.mark.parametrize("dim", [2, 3])
 def test_cut_cell_operator_is_exact_for_quadratics(dim):
