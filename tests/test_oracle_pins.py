@@ -242,6 +242,43 @@ def test_uniform_operator_equals_textbook_laplacian(dim):
     np.testing.assert_allclose(r, expect, rtol=1e-13, atol=1e-9)
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_operator_is_regular_where_no_distance_is_below_one(dim):
+    """Eq. (lpl-1d-lsf) with d_- = d_+ = 1 is Eq. (lpl-1d): on a uniform
+    tree cut by a sphere, every cell whose 2D distances are all 1 and which
+    has no wall neighbour has the textbook row (-2D on the diagonal, 1 to
+    each neighbour, over h^2), whether or not its block is cut."""
+    c = np.array([0.5, 0.5, 0.5])[:dim]
+    t = mk(dim, 4, (1, 1, 1), 1 / 4, 3 if dim == 2 else 2)
+    t.set_lsf(O.LSF_SPHERE, tuple(np.r_[c, np.zeros(3 - dim)]) + (0.3,))
+    t.set_walls([0] * (2 * dim), values=[0.0] * (2 * dim))
+    t.store_stencils(1.0)
+    lmin, lmax = t.levels()
+    A, _ = t.composite_matrix()
+    xc = t.leaf_centers()
+    h = t.level_h(lmax)
+    d = t.get_d(lmax).reshape(-1, 2 * dim)
+    xl = t.level_centers(lmax)
+    dist_of = {tuple(np.round(a / h * 2).astype(int)): d[i] for i, a in enumerate(xl)}
+    where = {tuple(np.round(a / h * 2).astype(int)): i for i, a in enumerate(xc)}
+    regular = cut_rows = 0
+    for i, a in enumerate(xc):
+        key = tuple(np.round(a / h * 2).astype(int))
+        if np.any(dist_of[key] < 1.0) or np.any(a < h) or np.any(a > 1 - h):
+            continue
+        row = np.zeros(A.shape[1])
+        row[i] = -2 * dim / (h * h)
+        for k in range(dim):
+            for s in (-1, 1):
+                b = a.copy()
+                b[k] += s * h
+                row[where[tuple(np.round(b / h * 2).astype(int))]] = 1 / (h * h)
+        assert np.array_equal(A[i], row)
+        regular += 1
+        cut_rows += 1 if np.linalg.norm(a - c) < 0.3 + 2 * h and np.linalg.norm(a - c) > 0.3 - 2 * h else 0
+    assert regular > 20 and cut_rows > 0
+
+
 def _refine_near(point, radius, N, h1, dim):
     point = np.asarray(point)
 
