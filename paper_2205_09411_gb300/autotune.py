@@ -87,20 +87,27 @@ def time_solve(tree, set_rhs, precision, tol, reps=2, max_cycles=80):
     return statistics.median(out), st
 
 
-def tune(tree, set_rhs, precision=MIXED, tol=1e-8, reps=2, log=None, axes=None):
+def tune(tree, set_rhs, precision=MIXED, tol=1e-8, reps=2, log=None, axes=None, timer=None):
     """Greedy search over the runtime knobs of a bound tree (or forest)
     (`axes`: names to search, default all).  Returns the best Schedule
-    (applied to the tree on return)."""
+    (applied to the tree on return).  `timer(tree, set_rhs, precision, tol,
+    reps)` -> (seconds or None, solve stats) scores a candidate (default:
+    time_solve, real timed solves)."""
+    timer = timer or time_solve
     best = Schedule()
     trials = []
+    scored = {}  # schedule key -> seconds: a schedule is timed once
 
     def score(s):
+        if s.key() in scored:
+            return scored[s.key()]
         apply(tree, s)
-        t, st = time_solve(tree, set_rhs, precision, tol, reps)
+        t, st = timer(tree, set_rhs, precision, tol, reps)
         trials.append(dict(asdict(s) | {"trials": None}, seconds=t, cycles=st.get("cycles")))
         if log:
             log("%-60s %s" % (s.key(), "diverged" if t is None else "%.4f s, %d cycles" % (t, st["cycles"])))
-        return float("inf") if t is None else t
+        scored[s.key()] = float("inf") if t is None else t
+        return scored[s.key()]
 
     best_t = score(best)
     space = [
