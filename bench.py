@@ -220,18 +220,20 @@ def algorithmic_bytes(kind, prec, level, t, leaf_level, nrhs=1):
         return tot + (nb0 * n0 ** 3) ** 2 * 8  # coarsest-level inverse, once
     nb, n, _ = t.level_info(level)
     cells = nb * n ** 3 * nrhs
-    cut_cells = t.num_cut_blocks(level) * n ** 3
-    st = 7 * S  # 7-point stencil per cut cell (read once for all slots)
-    if kind == "smooth":  # read phi, read b and write phi of one colour
-        return cells * 2 * S + cut_cells * st / 2
+    # the cut lists: each listed cell (stencil differs from the regular one)
+    # brings its 7 coefficients and its 4-byte index, read once for all slots
+    listed = int(t.cut_counts(level).sum())
+    entry = 7 * S + 4
+    if kind == "smooth":  # read phi, read b and write phi of one colour; one colour's list
+        return cells * 2 * S + listed * entry / 2
     if kind == "resid_restrict":  # read phi, b; write parent phi, b
-        return cells * (2 * S + 2 * S / 8) + cut_cells * st
+        return cells * (2 * S + 2 * S / 8) + listed * entry
     if kind == "prolong":  # read/write phi, read parent phi, old
         return cells * (2 * S + 2 * S / 8)
     if kind == "fas_rhs":  # read phi, b; write b, old
-        return cells * 4 * S + cut_cells * st
+        return cells * 4 * S + listed * entry
     if kind == "resid_norm":  # read phi64, b64 (+ write r32 in the mixed path)
-        return cells * (16 + 4) + cut_cells * 7 * 8
+        return cells * (16 + 4) + listed * (7 * 8 + 4)
     if kind == "accumulate":  # read e32, read/write phi64 on the leaf cells of all levels
         return t.n_leaf_cells * nrhs * 20
     return 0

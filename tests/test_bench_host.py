@@ -1,0 +1,64 @@
+"""bench.py's measurement arithmetic on the CPU: the algorithmic bytes of
+each kernel kind (the roofline's numerator) from a fake tree, and the
+roofline of the dominant kernel from a fake kernel-time table."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+class FakeTree:
+    """Levels 0..2 of 16^3 blocks (1, 8, 64 blocks); 10 listed cells per
+    block of level 2 (6 of colour 0, 4 of colour 1), none elsewhere."""
+    lmin, lmax, n_leaf_cells = 0, 2, 64 * 16 ** 3
+
+    def level_info(self, l):
+        return (8 ** l, 16, 1.0 / (16 * 2 ** l))
+
+    def num_cut_blocks(self, l):
+        return 64 if l == 2 else 0
+
+    def cut_counts(self, l):
+        return np.tile([6, 4], (8 ** l, 1)) if l == 2 else np.zeros((8 ** l, 2), dtype=int)
+
+
+def test_algorithmic_bytes_per_kind():
+    t = FakeTree()
+    cells = 64 * 4096
+    listed = 640
+    S = 4
+    assert bench.algorithmic_bytes("smooth", "fp32", 2, t, 2) == cells * 2 * S + listed * (7 * S + 4) / 2
+    assert bench.algorithmic_bytes("smooth", "fp32", 2, t, 2, nrhs=3) == 3 * cells * 2 * S + listed * (7 * S + 4) / 2
+    assert bench.algorithmic_bytes("resid_restrict", "fp32", 2, t, 2) == cells * 2.25 * S + listed * (7 * S + 4)
+    assert bench.algorithmic_bytes("prolong", "fp32", 2, t, 2) == cells * 2.25 * S
+    assert bench.algorithmic_bytes("fas_rhs", "fp32", 1, t, 2) == 8 * 4096 * 4 * S
+    assert bench.algorithmic_bytes("resid_norm", "fp64", 2, t, 2) == cells * 20 + listed * 60
+    assert bench.algorithmic_bytes("accumulate", "fp64", 2, t, 2, nrhs=2) == t.n_leaf_cells * 2 * 20
+
+
+def test_coarse_cycle_bytes_cover_the_cooperative_levels():
+    t = FakeTree()
+    S = 4
+    split = bench.coop_split(t)
+    assert split == 2  # every level has at most 160 blocks
+    c0, c1, c2 = 4096, 8 * 4096, 64 * 4096
+    per_level = lambda c, cp: c * (4 * 2 * S + 4.5 * S) + cp * 4 * S
+    want = c0 * 2 * S + per_level(c1, c0) + per_level(c2, c1) + c0 ** 2 * 8
+    assert bench.algorithmic_bytes("coarse_solve", "fp32", -1, t, 2) == pytest.approx(want)
+
+
+def test_roofline_of_picks_the_dominant_kernel():
+    t = FakeTree()
+    prof = [("smooth", "fp32", 2, 8, 0.080), ("resid_norm", "fp64", 2, 1, 0.050), ("prolong", "fp32", 2, 1, 0.01)]
+    roof, by_kind = bench.roofline_of(prof, t, 1, 6784.2, "measured")
+    assert roof["kernel"] == "smooth_fp32_level2" and roof["bound"] == "hbm"
+    per_launch_s = 0.080 / 8 * 1e-3
+    alg = bench.algorithmic_bytes("smooth", "fp32", 2, t, 2)
+    assert roof["achieved"] == pytest.approx(alg / per_launch_s / 1e9)
+    assert roof["frac"] == pytest.approx(roof["achieved"] / 6784.2)
+    assert roof["share_of_kernel_time"] == pytest.approx(0.080 / 0.140)
