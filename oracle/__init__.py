@@ -29,7 +29,7 @@ _LIB_PATH = os.path.join(_OUT_DIR, "libgmg_oracle.so")
 _lib = None
 _lock = threading.Lock()
 
-LSF_NONE, LSF_SPHERE, LSF_CAPSULE, LSF_ELLIPSOID, LSF_CALLBACK, LSF_SHAPE = 0, 1, 2, 3, 4, 5
+LSF_NONE, LSF_SPHERE, LSF_CAPSULE, LSF_ELLIPSOID, LSF_CALLBACK, LSF_SHAPE, LSF_GRID = 0, 1, 2, 3, 4, 5, 6
 WALL_DIRICHLET, WALL_NEUMANN = 0, 1
 
 FN = C.CFUNCTYPE(C.c_double, C.POINTER(C.c_double), C.c_void_p)
@@ -134,6 +134,23 @@ def make_lsf(kind, params=(), fn=None):
         s.p[i] = float(v)
     s.fn = _as_fn(fn) if fn is not None else FN()
     s._keep = s.fn
+    return s
+
+
+def make_grid_lsf(values, origin, spacing):
+    """LSF_GRID from samples values[i, j(, k)] at origin + (i, j, k) * spacing
+    (the samples are kept alive with the struct)."""
+    values = np.asarray(values, dtype=np.float64)
+    samples = np.ascontiguousarray(values.transpose())  # x fastest
+    s = LSF()
+    s.kind = LSF_GRID
+    for d in range(values.ndim):
+        s.p[d] = float(values.shape[d])
+        s.p[3 + d] = float(origin[d])
+        s.p[6 + d] = float(spacing)
+    s.fn = FN()
+    s.user = samples.ctypes.data
+    s._keep = samples
     return s
 
 
@@ -250,6 +267,12 @@ class OracleTree:
 
     def set_lsf(self, kind, params=(), fn=None):
         s = make_lsf(kind, params, fn)
+        self._keep.append(s)
+        lib().ot_set_lsf(self.h, C.byref(s))
+
+    def set_lsf_grid(self, values, origin, spacing):
+        """Level set sampled at origin + (i, j[, k]) * spacing: values[i, j(, k)]."""
+        s = make_grid_lsf(values, origin, spacing)
         self._keep.append(s)
         lib().ot_set_lsf(self.h, C.byref(s))
 

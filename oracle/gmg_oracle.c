@@ -506,6 +506,41 @@ double ot_lsf_eval(const ot_lsf *L, int D, const double *x) {
   }
   case OT_LSF_CALLBACK:
     return L->fn(x, L->user);
+  case OT_LSF_GRID: {
+    /* multilinear interpolant of gridded samples: locate the grid cell of x
+     * (clamped to the sampled box), then sum the 2^D corner samples with
+     * weights prod_d (w_d or 1 - w_d), corners in order with the x bit
+     * fastest */
+    const double *v = (const double *)L->user;
+    int lo[3] = {0, 0, 0};
+    double w[3] = {0.0, 0.0, 0.0};
+    long long stride[3];
+    stride[0] = 1;
+    stride[1] = (long long)p[0];
+    stride[2] = (long long)p[0] * (long long)p[1];
+    for (int d = 0; d < D; d++) {
+      const int n = (int)p[d];
+      double t = (x[d] - p[3 + d]) / p[6 + d];
+      if (t < 0.0) t = 0.0;
+      if (t > n - 1.0) t = n - 1.0;
+      int i = (int)floor(t);
+      if (i > n - 2) i = n - 2;
+      lo[d] = i;
+      w[d] = t - i;
+    }
+    double f = 0.0;
+    for (int corner = 0; corner < (1 << D); corner++) {
+      double weight = 1.0;
+      long long at = 0;
+      for (int d = 0; d < D; d++) {
+        const int up = (corner >> d) & 1;
+        weight = weight * (up ? w[d] : 1.0 - w[d]);
+        at = at + (long long)(lo[d] + up) * stride[d];
+      }
+      f = f + weight * v[at];
+    }
+    return f;
+  }
   default:
     return 1.0;
   }

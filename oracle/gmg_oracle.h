@@ -49,8 +49,11 @@ enum {
   OT_LSF_CAPSULE = 2,   /* p[0..2] a, p[3..5] b, p[6] r: dist(x, segment ab) - r   */
   OT_LSF_ELLIPSOID = 3, /* p[0..2] c, p[3..11] Q row-major, p[12..14] semi-axes     */
   OT_LSF_CALLBACK = 4,  /* user function                                          */
-  OT_LSF_SHAPE = 5      /* Sec. 4.3 shapes: p[0] 0 spheroid, 1 rhombus, 2 heart, 3 astroid;
+  OT_LSF_SHAPE = 5,     /* Sec. 4.3 shapes: p[0] 0 spheroid, 1 rhombus, 2 heart, 3 astroid;
                            p[1] = 1: revolved about the z axis (3D)                */
+  OT_LSF_GRID = 6       /* samples on a uniform grid (user: doubles, x fastest), the
+                           (bi/tri)linear interpolant; p[0..2] counts, p[3..5] sample 0,
+                           p[6..8] spacing; outside the box: the nearest face      */
 };
 
 typedef struct {

@@ -234,7 +234,8 @@ def _multilinear(values, origin, spacing, x):
 
 def _grid_tree(G, p, lsf):
     t = G.Tree(p["dim"], p["N"], p["cb"], p["lo"], p["h1"], p["max_level"], refine=p["refine"],
-               max_coarse_cells=p.get("max_coarse_cells") or (64 if p["dim"] == 2 else 512))
+               max_coarse_cells=p.get("max_coarse_cells") or (64 if p["dim"] == 2 else 512),
+               w_min=p.get("w_min", 0.0))
     t.set_walls(p["walls"], values=p.get("wall_values"), fn=p.get("wall_fn"))
     t.store_stencils(lsf, p["phib"])
     return t
@@ -261,6 +262,35 @@ def test_grid_level_set_reproduces_a_plane(G, dim):
         da, db = a.distances(lev), b.distances(lev)
         assert np.abs(da - db).max() <= 2e-8
         assert a.num_cut_blocks(lev) == b.num_cut_blocks(lev)
+
+
+@pytest.mark.parametrize("name", ["c1", "adaptive3d", "needle4"])
+def test_grid_level_set_setup_equals_oracle_grid(G, name):
+    """The library's and the oracle's set-ups with the same sampled level set
+    (each interpolating it in its own code) agree bit for bit: masks,
+    distances, cut-block counts and the kernels' cut lists."""
+    import oracle as O
+    p = parity_cases()[name]
+    dim = p["dim"]
+    m = 41
+    lo = np.asarray(p["lo"][:dim]) - 0.05
+    span = 1.1 / (m - 1)
+    axes = [lo[d] + np.arange(m) * span for d in range(dim)]
+    grid = np.meshgrid(*axes, indexing="ij")
+    c = np.array([0.47, 0.52, 0.55])[:dim]
+    values = np.sqrt(sum((grid[d] - c[d]) ** 2 for d in range(dim))) - 0.23
+    t = _grid_tree(G, p, ("grid", (values, lo, span)))
+    o = O.OracleTree(dim, p["N"], p["cb"], p["lo"], p["h1"], p["max_level"], refine=p["refine"],
+                     max_coarse_cells=p.get("max_coarse_cells"))
+    o.set_params(2, 2, 1e-8, 1.5, p.get("w_min", 0.0))
+    o.set_lsf_grid(values, lo, span)
+    o.set_walls(p["walls"], values=p.get("wall_values"), fn=p.get("wall_fn"))
+    o.store_stencils(p["phib"])
+    assert (t.lmin, t.lmax) == o.levels()
+    for lev in range(t.lmin, t.lmax + 1):
+        assert np.array_equal(t.mask(lev), o.get_mask(lev))
+        assert np.array_equal(t.distances(lev), o.get_d(lev))
+        assert t.num_cut_blocks(lev) == o.num_cut_blocks(lev)
 
 
 @pytest.mark.parametrize("name", ["c1", "adaptive3d"])

@@ -132,6 +132,32 @@ def test_distances_and_mask_match_sphere_intersections(dim):
 
 
 @pytest.mark.parametrize("dim", [2, 3])
+def test_grid_level_set_interpolates(dim):
+    """The sampled level set (OT_LSF_GRID) is the multilinear interpolant of
+    its samples: it returns the samples at the sample points, any linear
+    function exactly (to rounding) everywhere in the box, and outside the
+    box the value at the nearest point of the box."""
+    rng = np.random.default_rng(5)
+    m = [5, 6, 7][:dim]
+    origin = np.array([-0.2, 0.1, 0.3])[:dim]
+    h = 0.25
+    axes = [origin[d] + h * np.arange(m[d]) for d in range(dim)]
+    grid = np.meshgrid(*axes, indexing="ij")
+    vals = rng.standard_normal(m)
+    lsf = O.make_grid_lsf(vals, origin, h)
+    for idx in [(0,) * dim, tuple(x - 1 for x in m), tuple(x // 2 for x in m)]:
+        x = np.array([axes[d][idx[d]] for d in range(dim)])
+        assert O.lsf_eval(lsf, dim, x) == vals[idx]
+    a, c = rng.standard_normal(dim), 0.37
+    lin = O.make_grid_lsf(sum(a[d] * grid[d] for d in range(dim)) + c, origin, h)
+    hi = origin + h * (np.array(m) - 1)
+    for x in rng.uniform(origin, hi, size=(50, dim)):
+        assert abs(O.lsf_eval(lin, dim, x) - (a @ x + c)) <= 1e-14
+    for x in rng.uniform(origin - 1.0, hi + 1.0, size=(50, dim)):
+        assert O.lsf_eval(lin, dim, x) == O.lsf_eval(lin, dim, np.clip(x, origin, hi))
+
+
+@pytest.mark.parametrize("dim", [2, 3])
 def test_distances_from_both_sides_add_to_one(dim):
     """Invariant of the line search (Sec. 3.2): where the boundary crosses
     the segment between two neighbouring cell centres once (f changes sign),
