@@ -358,3 +358,47 @@ def test_solve_history_equals_solve(name, prec):
     hist = h["history"][:, 0]
     assert len(hist) == st["cycles"] + 1 and hist[0] == 1.0 and hist[-1] == h["rel_l2"] <= 1e-9
     assert np.all(np.diff(hist) < 0)
+
+
+def _grid_case(name):
+    """A parity case whose level set is a sphere sampled on a 41^D grid."""
+    p = dict(parity_cases()[name])
+    dim = p["dim"]
+    m = 41
+    lo = np.asarray(p["lo"][:dim]) - 0.05
+    span = 1.1 / (m - 1)
+    axes = [lo[d] + np.arange(m) * span for d in range(dim)]
+    grid = np.meshgrid(*axes, indexing="ij")
+    c = np.array([0.47, 0.52, 0.55])[:dim]
+    values = np.sqrt(sum((grid[d] - c[d]) ** 2 for d in range(dim))) - 0.23
+    return p, values, lo, span
+
+
+@pytest.mark.parametrize("name", ["c1", "adaptive3d"])
+def test_grid_level_set_iterates_match_oracle(name):
+    """With a sampled level set (GMG_LSF_GRID / OT_LSF_GRID, set-ups equal bit
+    for bit on the host) the FP64 V-cycle iterates through the C ABI equal
+    the oracle's to 1e-12."""
+    import oracle as O
+    import paper_2205_09411_gb300 as G
+    p, values, lo, span = _grid_case(name)
+    dim = p["dim"]
+    t = G.Tree(dim, p["N"], p["cb"], p["lo"], p["h1"], p["max_level"], refine=p["refine"],
+               max_coarse_cells=p.get("max_coarse_cells") or (64 if dim == 2 else 512), w_min=p.get("w_min", 0.0))
+    t.set_walls(p["walls"], values=p.get("wall_values"), fn=p.get("wall_fn"))
+    t.store_stencils(("grid", (values, lo, span)), p["phib"])
+    t.bind()
+    g = np.asarray(p["rhs"](t.leaf_centers()), dtype=np.float64)
+    t.set_rhs(g)
+    o = O.OracleTree(dim, p["N"], p["cb"], p["lo"], p["h1"], p["max_level"], refine=p["refine"],
+                     max_coarse_cells=p.get("max_coarse_cells"))
+    o.set_params(2, 2, 1e-8, 1.5, p.get("w_min", 0.0))
+    o.set_lsf_grid(values, lo, span)
+    o.set_walls(p["walls"], values=p.get("wall_values"), fn=p.get("wall_fn"))
+    o.store_stencils(p["phib"])
+    o.set_rhs(g)
+    for k in range(4):
+        o.vcycle(1)
+        t.vcycle(1)
+        ref = o.solution()
+        assert np.abs(t.solution() - ref).max() <= TOL_ITERATE * np.abs(ref).max()
