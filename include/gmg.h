@@ -299,7 +299,10 @@ int gmg_solve(gmg_tree *tree, int precision, double rel_tol, int max_cycles, gmg
  * (max_cycles + 1) x (nrhs * n_trees) doubles, caller-owned, step-major:
  * history[k * units + u] is unit u's relative L2 residual after step k
  * (step 0: the first residual; a unit keeps its value once it has
- * converged), NaN after the last step.  stats as in gmg_solve. */
+ * converged), NaN after the last step.  stats as in gmg_solve.  Cite: the
+ * residual-per-cycle curves of Sec. 4.  Synchronises once per step.
+ * Errors: as gmg_solve (INVALID_ARG, STATE if not bound, NOT_CONVERGED,
+ * NONFINITE); the history holds the steps run. */
 int gmg_solve_history(gmg_tree *tree, int precision, double rel_tol, int max_cycles, double *history,
                       gmg_stats *stats, void *stream);
 /* One step of the solve loop on the units with active[u] != 0 (host array
