@@ -101,6 +101,30 @@ def test_invalid_arguments_are_rejected(G):
     t = G.Tree(2, 8, max_level=2)
     with pytest.raises(G.GmgError):
         t.workspace_bytes()             # before store_stencils
+    with pytest.raises(G.GmgError):
+        t.cut_counts(1)                 # before store_stencils
+    t.set_walls([0] * 4, values=[0.0] * 4)
+    few = np.zeros((1, 5))              # one sample along x: not a grid
+    with pytest.raises(G.GmgError):
+        t.store_stencils(("grid", (few, [0.0, 0.0], 0.25)), 1.0)
+    t.store_stencils(("sphere", (0.5, 0.5, 0.0, 0.25)), 1.0)
+    with pytest.raises(G.GmgError):
+        t.boundary_terms(t.lmax + 1)    # no such level
+
+
+def test_forest_rejects_unlike_trees_and_new_boundary_values(G):
+    """Trees of a forest share block size and sweeps; a forest's boundary
+    value is set tree by tree before merging."""
+    import gmg_inputs as I
+    ps = I.forest_problems(2, index=3, sizes=(16, 32))
+    a = gpu_problem(ps[0], bind=False)
+    b = gpu_problem(dict(ps[1], N=16), bind=False)
+    with pytest.raises(G.GmgError, match="block size"):
+        G.Forest([a, b])
+    b = gpu_problem(ps[1], bind=False)
+    F = G.Forest([a, b])
+    with pytest.raises(G.GmgError, match="single tree"):
+        F.set_boundary_value(2.0)
 
 
 def test_needle_tree_size():
