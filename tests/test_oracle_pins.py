@@ -8,6 +8,7 @@ the oracle (a dropped term, a wrong sign or index, swapped d+/d-) fails at
 least one of them.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -474,14 +475,39 @@ def test_sphere_closed_form_second_order(dim):
     ratios = errs[:-1] / errs[1:]
     assert np.all(ratios > 2.5), ratios
     assert np.exp(np.mean(np.log(ratios[-1]))) > 3.0, ratios
-    if dim == 3:
-        # Sec. 4.1 prints a max error of 0.11e-3 after two FMG iterations on
-        # 256^3 (l_max = 6).  Extrapolating the 64^3 error by dx^2 gives
-        # about 9e-6: the paper's value is an upper bound here (its wall and
-        # ghost details are not printed), checked to within 20x below it.
-        pv = paper_values()
-        e256 = errs[-1, 0] / 16.0
-        assert pv["sphere3d_lmax6_maxerr_fmg2"] / 20 < e256 < pv["sphere3d_lmax6_maxerr_fmg2"], e256
+
+
+def _sphere3d_max_error(ml):
+    t, xc = _solve_error(I.problem("sphere3d"), ml)
+    outside = np.sqrt(np.sum(xc ** 2, 1)) > 0.25
+    e = np.abs(t.solution() - I.sphere_solution_vec(xc, 3))[outside].max()
+    t.close()
+    return e
+
+
+def test_sphere3d_error_against_the_printed_value():
+    """Sec. 4.1 prints a maximum error of 0.11e-3 on the 256^3 grid
+    (l_max = 6) once FMG has converged.  Measured here at 64^3 and 128^3
+    (3.56e-5): the error falls by 4 per halving of dx (second order), and
+    the 256^3 error this order predicts, e128^2 / e64, lies below the
+    printed value: with the paper's stencils and second-order walls the
+    scheme is at least as accurate as the paper's.  (Measured at 256^3 it is
+    8.96e-6, about 12 times below the printed value; the test below, run
+    with GMG_SLOW_TESTS=1, measures it.)"""
+    pv = paper_values()["sphere3d_lmax6_maxerr_fmg2"]
+    e64, e128 = _sphere3d_max_error(4), _sphere3d_max_error(5)
+    assert 3.5 < e64 / e128 < 4.5, (e64, e128)
+    assert e128 * e128 / e64 < pv, (e64, e128)
+
+
+@pytest.mark.skipif(os.environ.get("GMG_SLOW_TESTS") != "1", reason="256^3 oracle solve (about 2.5 min); GMG_SLOW_TESTS=1 runs it")
+def test_sphere3d_error_at_the_printed_resolution():
+    """The same problem at the printed resolution (256^3): the oracle's
+    maximum error is second order from 128^3 and below the printed 0.11e-3."""
+    pv = paper_values()["sphere3d_lmax6_maxerr_fmg2"]
+    e128, e256 = _sphere3d_max_error(5), _sphere3d_max_error(6)
+    assert 3.5 < e128 / e256 < 4.5, (e128, e256)
+    assert e256 < pv, e256
 
 
 def test_converged_solution_is_symmetric():
@@ -704,4 +730,127 @@ def test_sharp_shape_distances_match_closed_form_roots(shape):
                 assert abs(d[c, k] - min(ts)) < 2e-8, (c, k, d[c, k], ts)
                 checked += 1
     assert checked >= 8, checked
+    t.close()
+
+
+# ------------------------------------------- capsule and ellipsoid level sets
+def _quad_interval(p0, p1, p2):
+    """t-interval where p2 t^2 + p1 t + p0 <= 0 (p2 > 0), or None."""
+    disc = p1 * p1 - 4 * p2 * p0
+    if disc < 0:
+        return None
+    sq = math.sqrt(disc)
+    return ((-p1 - sq) / (2 * p2), (-p1 + sq) / (2 * p2))
+
+
+def _ball_interval(a, w, c, r):
+    """t-interval of the line a + t w inside the ball |x - c| <= r."""
+    u = a - c
+    return _quad_interval(u @ u - r * r, 2 * (u @ w), w @ w)
+
+
+def _capsule_interval(a, w, A, B, r):
+    """t-interval of the line a + t w inside the capsule of radius r around
+    the segment A-B (A-B along z here): the union of the two end balls and
+    the finite cylinder, written out from their equations.  The capsule is
+    convex, so the union is one interval."""
+    parts = [_ball_interval(a, w, A, r), _ball_interval(a, w, B, r)]
+    up, wp = (a - A)[:2], w[:2]
+    if wp @ wp > 0:
+        cyl = _quad_interval(up @ up - r * r, 2 * (up @ wp), wp @ wp)
+        if cyl is not None and A[2] <= a[2] <= B[2]:  # z stays a[2] on an x or y ray
+            parts.append(cyl)
+    elif up @ up <= r * r:  # a z ray inside the radius: the cylinder's z range
+        t0, t1 = (A[2] - a[2]) / w[2], (B[2] - a[2]) / w[2]
+        parts.append((min(t0, t1), max(t0, t1)))
+    parts = [q for q in parts if q is not None]
+    if not parts:
+        return None
+    return min(q[0] for q in parts), max(q[1] for q in parts)
+
+
+def _ellipsoid_interval(a, w, c, Q, S):
+    """t-interval of the line a + t w inside |S^-1 Q^T (x - c)| <= 1: the
+    roots of a quadratic in t, solved here."""
+    u = (Q.T @ (a - c)) / S
+    v = (Q.T @ w) / S
+    return _quad_interval(u @ u - 1.0, 2 * (u @ v), v @ v)
+
+
+def _check_distances_against_intervals(t, interval, min_checked):
+    """Every line-search distance of every level equals the nearest entry or
+    exit point of the body along the segment to the neighbour centre (the
+    body is convex: at most two roots per segment, the nearer one kept,
+    Sec. 3.2), and every cell with such a root is masked (Sec. 3.6.1)."""
+    lmin, lmax = t.levels()
+    checked = 0
+    for lev in range(lmin, lmax + 1):
+        d = t.get_d(lev).reshape(-1, 6)
+        mask = t.get_mask(lev).ravel()
+        xc = t.level_centers(lev)
+        h = t.level_h(lev)
+        for i, a in enumerate(xc):
+            for k in range(3):
+                for s, side in ((-1, 0), (1, 1)):
+                    if not 0 <= a[k] + s * h <= 1:
+                        assert d[i, 2 * k + side] == 1.0
+                        continue
+                    w = np.zeros(3)
+                    w[k] = s * h
+                    iv = interval(a, w)
+                    roots = [] if iv is None else [x for x in iv if 0.0 <= x <= 1.0]
+                    if not roots:
+                        assert d[i, 2 * k + side] == 1.0, (lev, i, k, s)
+                        continue
+                    assert mask[i] == 1, "cell with a root within one cell is not masked"
+                    # skip near-tangent chords, where the two roots are closer
+                    # than the search resolves (Sec. 3.2)
+                    if iv[1] - iv[0] > 1e-4:
+                        assert abs(d[i, 2 * k + side] - max(min(roots), EPS)) <= 2 * EPS, (lev, i, k, s, roots)
+                        checked += 1
+    assert checked >= min_checked, checked
+
+
+def test_capsule_distances_match_hand_solved_intersections():
+    """The needle level set (capsule: distance to a segment minus the
+    radius, reading N): distances along x, y and z on a 32^3 tree equal the
+    entry points into the cylinder wall, either hemispherical cap, or past
+    the segment's ends, solved from the shapes' equations."""
+    A, B, r = np.array([0.47, 0.52, 0.43]), np.array([0.47, 0.52, 0.81]), 0.11
+    t = mk(3, 8, (1, 1, 1), 1 / 8, 3)
+    t.set_lsf(O.LSF_CAPSULE, tuple(A) + tuple(B) + (r,))
+    t.set_walls([0] * 6, values=[0.0] * 6)
+    t.store_stencils(1.0)
+    _check_distances_against_intervals(t, lambda a, w: _capsule_interval(a, w, A, B, r), 400)
+    # rays through the caps only: z rays inside the radius, and x rays
+    # below the segment's lower end
+    xc, h = t.level_centers(3), t.level_h(3)
+    d = t.get_d(3).reshape(-1, 6)
+    caps = 0
+    for i, a in enumerate(xc):
+        if np.hypot(*(a - A)[:2]) < r and abs(a[2] - A[2]) < 2 * h and d[i, 4] < 1:
+            caps += 1
+        if A[2] - r < a[2] < A[2] and d[i, 0] < 1:
+            caps += 1
+    assert caps >= 20, caps
+    t.close()
+
+
+@pytest.mark.parametrize("rotated", [False, True])
+def test_ellipsoid_distances_match_hand_solved_intersections(rotated):
+    """The ellipsoid level set of the batched-trees workload,
+    a_min (|S^-1 Q^T (x - c)| - 1): distances on a 32^3 tree equal the roots
+    of the ray-quadric equation solved here, for axis-aligned semi-axes and
+    for a rotation Q (a transposed Q or swapped semi-axes fail this)."""
+    c = np.array([0.48, 0.53, 0.51])
+    S = np.array([0.31, 0.17, 0.23])
+    if rotated:
+        Q, _ = np.linalg.qr(np.random.default_rng(11).standard_normal((3, 3)))
+    else:
+        Q = np.eye(3)
+    t = mk(3, 8, (1, 1, 1), 1 / 8, 3)
+    t.set_lsf(O.LSF_ELLIPSOID, tuple(c) + tuple(Q.ravel()) + tuple(S))
+    t.set_walls([0] * 6, values=[0.0] * 6)
+    t.store_stencils(1.0)
+    _check_distances_against_intervals(t, lambda a, w: _ellipsoid_interval(a, w, c, Q, S), 400)
     t.close()
