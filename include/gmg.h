@@ -368,7 +368,8 @@ long long gmg_last_launch_count(const gmg_tree *tree);
  * entries (or a negative error).  Kinds: 0 smooth, 1 residual+restrict,
  * 2 FAS right-hand side, 3 coarse solve, 4 prolongation, 5 restriction of
  * phi, 6 residual norm, 7 norm reduction, 8 mixed-path accumulation,
- * 9 right-hand side / copies. */
+ * 9 right-hand side / copies, 10 bottom of the cycle on a thread-block
+ * cluster (GMG_OPT_CLUSTER_TAIL). */
 int gmg_profile_enable(gmg_tree *tree, int enable);
 int gmg_profile_read(gmg_tree *tree, int cap, int *kind, int *prec, int *level, long long *launches, double *ms);
 
@@ -399,6 +400,15 @@ int gmg_profile_read(gmg_tree *tree, int cap, int *kind, int *prec, int *level, 
                                     programmatic dependent launch: each is dispatched as its
                                     predecessor's CTAs exit and waits for it on the device before
                                     reading its results; same results */
+#define GMG_OPT_CLUSTER_TAIL 11  /* [1] the bottom of the V-cycle (the levels holding one block per
+                                    root, and the level of each root's 2^D children when it is
+                                    complete) on a cluster of 2^D CTAs per (root, slot), each CTA
+                                    holding one octant of every such level in shared memory and
+                                    reading its neighbours' ghost cells through distributed shared
+                                    memory: 0 off (one CTA per (root, slot) inside the cooperative
+                                    launch), 1 when every unit's cluster is resident at once, 2
+                                    whenever the tree qualifies (sides multiples of 4, octants
+                                    within one CTA's shared memory); same arithmetic */
 int gmg_set_option(gmg_tree *tree, int option, long long value);
 
 /* Sweep schedule: N_down / N_up red-black sweeps on one level (default: the

@@ -6,6 +6,7 @@ shared library with a plain C ABI (include/gmg.h):
 * csrc/gmg_api.cu      - kernels, V-cycle schedule, solve loops, C entry points
 * csrc/tree_setup.cpp  - block tree and boundary set-up on the host
   (-ffp-contract=off: the level-set arithmetic is plain IEEE)
+* csrc/cluster_tail.cu - the bottom of the V-cycle on a thread-block cluster
 * csrc/noalloc.cu      - residual norm with a static scratch array (no allocation)
 * csrc/forest.cpp      - forests of independent trees (host)
 * csrc/solve_history.cpp - the solve loop with its residual history (host)
@@ -22,7 +23,7 @@ LIB = os.path.join(OUT, "libgmg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
           "-I", os.path.join(ROOT, "include"), "-I", CSRC]
-SOURCES = ["gmg_api.cu", "tree_setup.cpp", "noalloc.cu", "forest.cpp", "solve_history.cpp"]
+SOURCES = ["gmg_api.cu", "cluster_tail.cu", "tree_setup.cpp", "noalloc.cu", "forest.cpp", "solve_history.cpp"]
 
 
 def _nvcc():

@@ -73,6 +73,7 @@ struct CycleArgs {
   long long spin_limit;
   int l_one;  // levels l_lo .. l_one hold one block per root and run one CTA per (root, slot) (< l_lo: none)
   int cinv_off;  // byte offset of the tail's FP64 b and copy of its root's inverse in shared memory (-1: none)
+  int mode;      // 0 whole coarse cycle; 1 down leg to the FAS of l_one (no tail); 2 up leg from l_one + 1
 };
 
 // Block operations with the compile-time side NT for levels >= 1 and the
@@ -169,40 +170,6 @@ __device__ __forceinline__ bool tail_cut(const TailLevel<T, D> &Q, int c, int *e
   if (Q.m == 0) return false;
   *e = (int)Q.eidx[c] - 1;
   return *e >= 0;
-}
-
-// (x, y, z) of cell c of a block of side n: shifts and masks when n is a
-// power of two, divisions otherwise
-template <int D>
-__device__ __forceinline__ void cell_xyz_rt(int c, int n, int *x, int *y, int *z) {
-  if ((n & (n - 1)) == 0) {
-    const int lg = __ffs(n) - 1;
-    *x = c & (n - 1);
-    *y = (c >> lg) & (n - 1);
-    *z = D == 3 ? c >> (2 * lg) : 0;
-  } else {
-    cell_xyz<D>(c, n, x, y, z);
-  }
-}
-
-// the j-th cell of colour `color` ((x + y + z) mod 2) of a block of side n
-template <int D>
-__device__ __forceinline__ void colour_xyz(int j, int n, int color, int *x, int *y, int *z) {
-  const int hn = n / 2;
-  int xp;
-  if ((n & (n - 1)) == 0) {
-    const int lh = __ffs(hn) - 1;
-    xp = j & (hn - 1);
-    const int rest = j >> lh;
-    *y = rest & (n - 1);
-    *z = D == 3 ? rest >> (lh + 1) : 0;
-  } else {
-    xp = j % hn;
-    const int rest = j / hn;
-    *y = rest % n;
-    *z = D == 3 ? rest / n : 0;
-  }
-  *x = 2 * xp + ((*y + *z + color) & 1);
 }
 
 // wall ghosts of a single-block level (all faces are walls): sign * mirror
@@ -585,7 +552,7 @@ __global__ void __launch_bounds__(kCoopThreads) k_cycle_coop(GmgView<T> V, const
     if (const int r_ = item % V.nrhs; (bid = (Lv).first + item / V.nrhs, is_active(unit_of(V, r_, bid)))) \
       if (const GmgView<T> W = slot_view(V, r_); true)
   // levels l_hi .. l_one + 1: every CTA, grid barrier between phases
-  for (int l = A.l_hi; l > A.l_lo && l > A.l_one; l--) {
+  for (int l = A.l_hi; A.mode != 2 && l > A.l_lo && l > A.l_one; l--) {
     const LvArgs &L = GMG_LV(l), &Lp = GMG_LV(l - 1);  // read from shared memory, not held in registers
     for (int k = 0; k < L.nd; k++)
       for (int c = 0; c < 2; c++) {
@@ -605,9 +572,13 @@ __global__ void __launch_bounds__(kCoopThreads) k_cycle_coop(GmgView<T> V, const
       fas_any<T, D, NT>(W, Lp, Lpp, bid, smem_raw);
       __syncthreads();
     }
+    if (A.mode == 1 && l == A.l_one + 1) return;  // the kernel ends: no barrier
     if (!grid_sync(A.bar, G, A.spin_limit, &epoch)) return;
   }
-  if (A.l_one >= A.l_lo) {
+  if (A.mode == 1) return;  // the cluster kernel runs the bottom of the cycle next
+  if (A.mode == 2) {
+    // up leg only: the bottom levels were done by the cluster kernel
+  } else if (A.l_one >= A.l_lo) {
     // single-block levels l_one .. l_lo: CTA 0 runs the bottom of the cycle
     // (sweeps, restriction, FAS, coarse solve, prolongation, sweeps) with
     // block-level barriers only
@@ -621,7 +592,7 @@ __global__ void __launch_bounds__(kCoopThreads) k_cycle_coop(GmgView<T> V, const
     coarse_rows<T>(V, GMG_LV(A.l_lo), A, blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5),
                    (int)(G * (blockDim.x / 32)));
   }
-  if (A.l_hi > A.l_one && !grid_sync(A.bar, G, A.spin_limit, &epoch)) return;
+  if (A.mode == 0 && A.l_hi > A.l_one && !grid_sync(A.bar, G, A.spin_limit, &epoch)) return;
   for (int l = (A.l_one >= A.l_lo ? A.l_one : A.l_lo) + 1; l <= A.l_hi; l++) {
     const LvArgs &L = GMG_LV(l), &Lp = GMG_LV(l - 1);  // read from shared memory, not held in registers
     GMG_ITEMS(L) {

@@ -406,35 +406,43 @@ size_t tile_bytes(const gmg_tree *t, int l) {
   return level_smem_bytes<T>(t->D, t->lev(l).n);
 }
 
-// One FAS V-cycle on fields of type T (Sec. 2.2; readings UP and V).
-// Levels lmin .. ls in one cooperative launch (coarse_cycle.cuh).
+// The cooperative launch of the coarse part of a V-cycle (coarse_cycle.cuh)
+// on levels lmin .. ls.  mode 0: the whole coarse cycle, with the
+// single-block levels at the bottom on one CTA per (root, slot) when they fit
+// (the tail); mode 1: the down leg to the FAS right-hand side of level
+// l_stop; mode 2: the up leg from level l_stop + 1 (the cluster kernel did
+// the levels up to l_stop in between).
 template <typename T, int D>
-int coop_cycle(gmg_tree *t, cudaStream_t s, int ls) {
+int coop_launch(gmg_tree *t, cudaStream_t s, int ls, int mode, int l_stop) {
   GmgView<T> V = view<T>(t);
-  // the single-block levels at the bottom run on one CTA when the coarse
-  // solve is small enough for one CTA
   int l_one = t->lmin - 1;
   size_t tail_bytes = 0;
-  if (t->ncr <= 256 && (t->nroot > 1 || t->cb[0] * t->cb[1] * t->cb[2] == 1))
-    for (int l = t->lmin; l <= ls && t->lev(l).count == t->nroot; l++) {
-      const int n = t->lev(l).n;
-      const size_t add = tail_level_bytes<T, D>(n, t->cut_max_h[l - t->lmin]);
-      if (tail_bytes + add > 160 * 1024 || l - t->lmin >= 11) break;
-      tail_bytes += add;
-      l_one = l;
-    }
-  // the tail's coarse inverse in shared memory when it fits beside the levels
   int cinv_off = -1;
-  const size_t cinv_bytes = sizeof(double) * ((size_t)t->ncr * t->ncr + t->ncr);  // inverse and b in FP64
-  if (l_one >= t->lmin && tail_bytes + cinv_bytes <= 192 * 1024) {
-    cinv_off = (int)tail_bytes;
-    tail_bytes += cinv_bytes;
+  if (mode != 0) {
+    l_one = l_stop;
+  } else {
+    // the single-block levels at the bottom run on one CTA when the coarse
+    // solve is small enough for one CTA
+    if (t->ncr <= 256 && (t->nroot > 1 || t->cb[0] * t->cb[1] * t->cb[2] == 1))
+      for (int l = t->lmin; l <= ls && t->lev(l).count == t->nroot; l++) {
+        const int n = t->lev(l).n;
+        const size_t add = tail_level_bytes<T, D>(n, t->cut_max_h[l - t->lmin]);
+        if (tail_bytes + add > 160 * 1024 || l - t->lmin >= 11) break;
+        tail_bytes += add;
+        l_one = l;
+      }
+    // the tail's coarse inverse in shared memory when it fits beside the levels
+    const size_t cinv_bytes = sizeof(double) * ((size_t)t->ncr * t->ncr + t->ncr);  // inverse and b in FP64
+    if (l_one >= t->lmin && tail_bytes + cinv_bytes <= 192 * 1024) {
+      cinv_off = (int)tail_bytes;
+      tail_bytes += cinv_bytes;
+    }
   }
-  CycleArgs A{t->lmin, ls, t->ncr, t->nroot, t->d_cinv, t->d_bar, t->spin_limit, l_one, cinv_off};
+  CycleArgs A{t->lmin, ls, t->ncr, t->nroot, t->d_cinv, t->d_bar, t->spin_limit, l_one, cinv_off, mode};
   size_t sm = 0;
-  int maxb = l_one >= t->lmin ? t->nroot : 1;
+  int maxb = (mode == 0 && l_one >= t->lmin) ? t->nroot : 1;
   for (int l = t->lmin; l <= ls; l++) {
-    if (l <= l_one) continue;  // held in shared memory by the tail
+    if (l <= l_one) continue;  // held in shared memory by the tail, or done by the cluster kernel
     const int hm = t->lev(l).n / 2 + 2;
     sm = std::max(sm, tile_bytes<T>(t, l));
     sm = std::max(sm, sizeof(T) * (size_t)(D == 3 ? hm * hm * hm : hm * hm));
@@ -477,6 +485,118 @@ int coop_cycle(gmg_tree *t, cudaStream_t s, int ls) {
   });
   if (rc) return rc;
   CUDA_TRY(cudaGetLastError());
+  return GMG_OK;
+}
+
+// Plan of the cluster kernel (cluster_tail.cuh) for the bottom of a V-cycle
+// whose coarse part covers levels lmin .. ls: the single-block levels from
+// lmin up, and above them the level of the roots' 2^D children when it is
+// complete; every level's side a multiple of 4 (octants of even side); the
+// octants' arrays within one CTA's shared memory; all units' clusters
+// resident at once.  Returns false when the tree does not qualify (the
+// cooperative kernel's own tail then runs).
+template <typename T, int D>
+bool plan_cluster(gmg_tree *t, int ls, ClusterArgs *A, size_t *smem) {
+  constexpr int P = 1 << D;
+  if (t->cluster_mode == 0) return false;
+  if (!(t->nroot > 1 || t->cb[0] * t->cb[1] * t->cb[2] == 1)) return false;
+  int l_single = t->lmin - 1;
+  for (int l = t->lmin; l <= ls && t->lev(l).count == t->nroot; l++) l_single = l;
+  if (l_single < t->lmin) return false;
+  // split levels (more than 8 cells a side) need octants of even side; the
+  // levels of at most 8 a side are held whole by every CTA and need an even side
+  for (int l = t->lmin; l <= l_single; l++)
+    if (t->lev(l).n % (t->lev(l).n > 8 ? 4 : 2)) return false;
+  bool children = false;
+  if (l_single + 1 <= ls && t->lev(l_single + 1).count == t->nroot * P) {
+    children = true;
+    const LevelInfo &R = t->lev(l_single), &Cl = t->lev(l_single + 1);
+    for (int r = 0; r < t->nroot && children; r++)
+      for (int k = 0; k < P && children; k++) {
+        const HostBlock &b = t->blocks[Cl.first + P * r + k];
+        const HostBlock &p = t->blocks[R.first + r];
+        if (b.parent != R.first + r) children = false;
+        for (int d = 0; d < D; d++)
+          if (b.ix[d] - 2 * p.ix[d] != ((k >> d) & 1)) children = false;
+      }
+  }
+  const size_t limit = 224 * 1024;
+  for (int attempt = 0; attempt < 2; attempt++) {
+    const int l_top = children ? l_single + 1 : l_single;
+    if (l_top - t->lmin + 1 > kClusterMaxLevels) return false;
+    ClusterArgs a{};
+    a.l_lo = t->lmin;
+    a.l_top = l_top;
+    a.children = children ? 1 : 0;
+    a.ncr = t->ncr;
+    a.nroot = t->nroot;
+    a.cinv = t->d_cinv;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+      const size_t at = o;
+      o = (o + bytes + 15) / 16 * 16;
+      return (unsigned int)at;
+    };
+    bool ok = true;
+    int nlo = 0;
+    a.full_from = l_top - t->lmin + 1;
+    for (int l = l_top; l >= t->lmin; l--) {
+      const int i = l_top - l;
+      const int N = (children && l == l_top) ? 2 * t->lev(l).n : t->lev(l).n;
+      const bool full = i > 0 && N <= 8;
+      if (full && a.full_from > i) a.full_from = i;
+      if (!full && i > a.full_from) ok = false;  // full levels form the bottom of the range
+      if (i == 0 && N <= 8) ok = false;          // the top level is split
+      const int m = full ? N : N / 2, nc = D == 3 ? m * m * m : m * m, R = m + 2;
+      const int cap = t->cut_max_h[l - t->lmin];
+      if (cap > 65534) ok = false;
+      a.off_tile[i] = take(sizeof(T) * (size_t)(D == 3 ? R * R * R : R * R));
+      a.off_b[i] = take(sizeof(T) * (size_t)nc);
+      a.off_old[i] = take(sizeof(T) * (size_t)nc);
+      a.off_eidx[i] = take(2 * (size_t)nc);
+      a.off_cf[i] = take(sizeof(T) * (size_t)cap * (2 * D + 1));
+      nlo = full ? (t->ncr + P - 1) / P : nc;  // rows of the coarse solve per CTA
+    }
+    a.off_bd = take(sizeof(double) * (size_t)t->ncr);
+    const size_t rows = sizeof(double) * (size_t)nlo * t->ncr;
+    a.stage_rows = (o + rows <= limit && rows <= 64 * 1024) ? 1 : 0;
+    a.off_rows = a.stage_rows ? take(rows) : 0;
+    if (ok && o <= limit) {
+      const int units = t->nrhs * t->nroot;
+      if (t->cluster_mode == 1 && units > cycle_cluster_capacity<T, D>(o)) return false;
+      *A = a;
+      *smem = o;
+      return true;
+    }
+    if (!children) return false;
+    children = false;  // retry without the children level
+  }
+  return false;
+}
+
+// One FAS V-cycle on fields of type T (Sec. 2.2; readings UP and V).
+// Levels lmin .. ls: with the cluster kernel at the bottom (and the
+// cooperative kernel's down and up legs around it when ls is above the
+// cluster's levels), else in one cooperative launch.
+template <typename T, int D>
+int coop_cycle(gmg_tree *t, cudaStream_t s, int ls) {
+  ClusterArgs CA;
+  size_t csm = 0;
+  if (!plan_cluster<T, D>(t, ls, &CA, &csm)) return coop_launch<T, D>(t, s, ls, 0, 0);
+  if (ls > CA.l_top) {
+    const int rc = coop_launch<T, D>(t, s, ls, 1, CA.l_top);
+    if (rc) return rc;
+  }
+  cudaError_t e = cudaSuccess;
+  const GmgView<T> V = view<T>(t);
+  launch(t, s, 10, prec_of<T>(), t->lmin, [&] {
+    e = launch_cycle_cluster<T, D>(V, t->d_lvtab, t->lmin, CA, t->nrhs * t->nroot, csm, s, t->use_pdl && !t->prof_on);
+  });
+  if (e != cudaSuccess) {
+    set_error(std::string("cluster kernel of the coarse cycle: ") + cudaGetErrorString(e));
+    return GMG_ERR_CUDA;
+  }
+  if (ls > CA.l_top) return coop_launch<T, D>(t, s, ls, 2, CA.l_top);
   return GMG_OK;
 }
 
@@ -1620,6 +1740,10 @@ int gmg_set_option(gmg_tree *t, int option, long long value) {
       if (t->bound) set_coop_split(t);
       break;
     case GMG_OPT_FMG_STEPS: t->fmg_steps = value != 0; break;
+    case GMG_OPT_CLUSTER_TAIL:
+      if (value < 0 || value > 2) return set_error("cluster tail must be 0 (off), 1 (auto) or 2 (whenever the tree qualifies)"), GMG_ERR_INVALID_ARG;
+      t->cluster_mode = (int)value;
+      break;
     case GMG_OPT_PDL:
       t->use_pdl = value != 0;
       drop_graphs(t);

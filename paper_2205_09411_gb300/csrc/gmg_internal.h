@@ -103,6 +103,34 @@ __host__ __device__ __forceinline__ GmgView<T> slot_view(const GmgView<T> &V, in
 
 struct gmg_tree_impl;
 
+// Plan of one launch of the cluster kernel for the bottom of the V-cycle
+// (cluster_tail.cuh): levels l_lo .. l_top, each split into 2^D octants, one
+// per CTA of a cluster; byte offsets of each level's arrays in shared memory,
+// level index i = l_top - l.
+constexpr int kClusterThreads = 512;
+constexpr int kClusterMaxLevels = 12;
+struct ClusterArgs {
+  int l_lo, l_top;
+  int children;    // level l_top holds the 2^D children of each root: octant k = block first + P root + k
+  int ncr, nroot;  // coarsest-level unknowns per root, roots
+  const double *cinv;
+  int stage_rows;  // this CTA's rows of the coarse inverse are staged in shared memory
+  int full_from;   // levels i >= full_from (at most 8 cells a side) are held whole by every CTA
+  unsigned int off_tile[kClusterMaxLevels], off_b[kClusterMaxLevels], off_old[kClusterMaxLevels];
+  unsigned int off_eidx[kClusterMaxLevels], off_cf[kClusterMaxLevels];
+  unsigned int off_bd, off_rows;  // FP64 b of the coarsest level (all octants); staged inverse rows
+};
+
+// Launches the cluster kernel: nunits clusters of 2^D CTAs (cluster_tail.cu).
+template <typename T, int D>
+cudaError_t launch_cycle_cluster(const GmgView<T> &V, const LvArgs *lvtab, int lmin, const ClusterArgs &A,
+                                 int nunits, size_t smem, cudaStream_t s, bool pdl);
+// Clusters of the kernel with `smem` dynamic bytes that fit on the device at
+// once (0 if none does).
+template <typename T, int D>
+int cycle_cluster_capacity(size_t smem);
+
+
 }  // namespace gmg
 
 struct gmg_tree {
@@ -204,6 +232,7 @@ struct gmg_tree {
   int slots_per_cta = 1;      // right-hand-side slots of a block per CTA in the half-sweeps (1, 2, 4)
   bool fmg_steps = false;     // solve steps are FMG cycles instead of V-cycles
   bool use_pdl = true;        // per-level kernels with programmatic dependent launch
+  int cluster_mode = 1;       // bottom of the cycle on a thread-block cluster: 0 off, 1 when all units fit at once, 2 whenever eligible
   std::vector<char> level_complete;  // every block has all 26 neighbours on its level (or walls)
   int coop_split = 0;         // highest level run inside that launch
   int coop_max_blocks = gmg::kCoopMaxBlocks;  // levels with at most this many blocks join it

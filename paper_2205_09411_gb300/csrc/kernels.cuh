@@ -403,6 +403,40 @@ __device__ __forceinline__ void cell_xyz(int c, int n, int *x, int *y, int *z) {
   *z = D == 3 ? c / (n * n) : 0;
 }
 
+// (x, y, z) of cell c of a block of side n: shifts and masks when n is a
+// power of two, divisions otherwise
+template <int D>
+__device__ __forceinline__ void cell_xyz_rt(int c, int n, int *x, int *y, int *z) {
+  if ((n & (n - 1)) == 0) {
+    const int lg = __ffs(n) - 1;
+    *x = c & (n - 1);
+    *y = (c >> lg) & (n - 1);
+    *z = D == 3 ? c >> (2 * lg) : 0;
+  } else {
+    cell_xyz<D>(c, n, x, y, z);
+  }
+}
+
+// the j-th cell of colour `color` ((x + y + z) mod 2) of a block of side n
+template <int D>
+__device__ __forceinline__ void colour_xyz(int j, int n, int color, int *x, int *y, int *z) {
+  const int hn = n / 2;
+  int xp;
+  if ((n & (n - 1)) == 0) {
+    const int lh = __ffs(hn) - 1;
+    xp = j & (hn - 1);
+    const int rest = j >> lh;
+    *y = rest & (n - 1);
+    *z = D == 3 ? rest >> (lh + 1) : 0;
+  } else {
+    xp = j % hn;
+    const int rest = j / hn;
+    *y = rest % n;
+    *z = D == 3 ? rest / n : 0;
+  }
+  *x = 2 * xp + ((*y + *z + color) & 1);
+}
+
 // Work item of a per-level launch: the grid holds count x nrhs CTAs with the
 // slot index fastest, so that the slots of one block run side by side and
 // share its tables and stencil through L2.  Returns false for a frozen unit

@@ -193,6 +193,45 @@ def test_execution_paths_give_the_oracle_iterates(name, graphs, coop):
     assert st["rel_l2"] <= 1e-8
 
 
+@pytest.mark.parametrize("name", ["c2_64", "c2_32", "c1", "needle4", "adaptive3d", "no_boundary"])
+def test_cluster_tail_gives_the_oracle_iterates(name):
+    """The bottom of the V-cycle on a thread-block cluster (each CTA one
+    octant of the single-block levels and of the roots' children level, in
+    shared memory, ghosts through distributed shared memory) gives the
+    oracle's FP64 iterates after each of 6 V-cycles, FP64 and FMG; where the
+    coarse solve of both paths sums a row the same way (at most 256
+    coarsest-level cells), the iterates and a mixed solve equal the
+    single-CTA bottom's bit for bit."""
+    p = parity_cases()[name]
+    o = oracle_problem(p)
+    out = []
+    for mode in (2, 0):
+        t = gpu_problem(p)
+        t.set_option("cluster_tail", mode)
+        its = []
+        for k in range(6):
+            t.vcycle(1)
+            its.append(t.solution().copy())
+        t.fmg(1)
+        its.append(t.solution().copy())
+        t.set_rhs(np.asarray(p["rhs"](t.leaf_centers()), dtype=np.float64))
+        st = t.solve(1, 1e-8, 60)
+        assert st["rel_l2"] <= 1e-8
+        its.append(t.solution().copy())
+        out.append(its)
+    for k in range(6):
+        o.vcycle(1)
+        ref = o.solution()
+        assert np.abs(out[0][k] - ref).max() <= TOL_ITERATE * np.abs(ref).max(), k
+    o.fmg(1)
+    ref = o.solution()
+    assert np.abs(out[0][6] - ref).max() <= TOL_ITERATE * np.abs(ref).max()
+    q = gpu_problem(p, bind=False, rhs=False)
+    if q.level_info(q.lmin)[1] ** p["dim"] <= 256:
+        for a, b in zip(out[0], out[1]):
+            assert np.array_equal(a, b)
+
+
 def test_bounded_barrier_wait_reports_timeout_and_context_survives():
     """Failure detection without a fault: a grid barrier that can never
     complete ends its bounded wait with GMG_ERR_TIMEOUT; the device stays
