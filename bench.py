@@ -38,6 +38,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -201,23 +202,46 @@ def coop_split(t):
     return max(l for l in range(t.lmin, t.lmax + 1) if t.level_info(l)[0] <= 160)
 
 
-def algorithmic_bytes(kind, prec, level, t, leaf_level, nrhs=1):
+def cluster_top(t):
+    """Highest level of the cluster kernel at the bottom of the cycle (the
+    library's rule: the single-block levels from the coarsest up, and the
+    level of the roots' 2^D children when it holds exactly those)."""
+    nroot = t.level_info(t.lmin)[0]
+    l = t.lmin
+    while l + 1 <= t.lmax and t.level_info(l + 1)[0] == nroot:
+        l += 1
+    if l + 1 <= coop_split(t) and t.level_info(l + 1)[0] == nroot * 2 ** t.dim:
+        l += 1
+    return l
+
+
+# Bytes per cell of one level visit of the V-cycle (Sec. 2.2), S bytes a
+# value: the down leg reads phi and b and writes phi (3S), plus the coarse
+# level's restricted phi, b and old (3S/8); the up leg reads phi and b and
+# writes phi (3S), plus the coarse correction's phi and old (2S/8).
+LEVEL_VISIT_S = 3 + 3 / 8 + 3 + 2 / 8
+
+
+def algorithmic_bytes(kind, prec, level, t, leaf_level, nrhs=1, cluster=False):
     """Minimum bytes one launch of a kernel must move (unique data), for
-    nrhs right-hand-side slots (stencils are shared by the slots)."""
+    nrhs right-hand-side slots (stencils are shared by the slots).  The
+    coarse kernels count LEVEL_VISIT_S bytes a cell on every level they
+    cover, plus the coarsest-level inverse once; with the cluster kernel at
+    the bottom (cluster=True) the cooperative kernel runs twice per cycle
+    (down and up leg) and each launch counts half of its levels' bytes."""
     S = 8 if prec == "fp64" else 4
-    if kind == "coarse_solve":  # every phase of the coarse levels, per slot
+    D = t.dim
+    if kind in ("coarse_solve", "coarse_cluster"):
+        top = cluster_top(t) if cluster else t.lmin - 1
+        lo, hi = (t.lmin, top) if kind == "coarse_cluster" else (top + 1, coop_split(t))
         tot = 0.0
-        sw = 2 * 2  # (n_down + n_up) full sweeps of two half-sweeps each, 2 + 2
-        for l in range(t.lmin, coop_split(t) + 1):
+        for l in range(lo, hi + 1):
             nb, n, _ = t.level_info(l)
-            cells = nb * n ** 3
-            if l == t.lmin:
-                tot += nrhs * cells * 2 * S
-                continue
-            pnb, pn, _ = t.level_info(l - 1)
-            tot += nrhs * (cells * (sw * 2 * S + 2.25 * S + 2.25 * S) + pnb * pn ** 3 * 4 * S)
+            tot += nrhs * nb * n ** D * LEVEL_VISIT_S * S
+        if kind == "coarse_solve" and cluster:
+            return tot / 2
         nb0, n0, _ = t.level_info(t.lmin)
-        return tot + (nb0 * n0 ** 3) ** 2 * 8  # coarsest-level inverse, once
+        return tot + nb0 * (n0 ** D) ** 2 * 8  # coarsest-level inverses, once
     nb, n, _ = t.level_info(level)
     cells = nb * n ** 3 * nrhs
     # the cut lists: each listed cell (stencil differs from the regular one)
@@ -269,12 +293,15 @@ def ncu_traffic(kernel_kind, prec, level):
     return None
 
 
-def cpu_baseline(p, budget_s=12.0):
-    """The oracle as it stands (serial FP64 C), on one host core: V-cycles of
-    the same workload from phi = 0 until the time budget is used."""
+def _oracle_vcycles(budget_s):
+    """One oracle instance of the 128^3 workload doing FP64 V-cycles from
+    phi = 0 until the time budget is used: (cell updates, seconds, cycles).
+    Runs in a worker process of cpu_baseline's pool."""
+    sys.path.insert(0, ROOT)
     sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import gmg_inputs as In
     from _helpers import oracle_problem
-    o = oracle_problem(p)
+    o = oracle_problem(In.problem("c2"))
     n = o.num_leaf_cells()
     k, t0 = 0, time.perf_counter()
     while True:
@@ -283,8 +310,40 @@ def cpu_baseline(p, budget_s=12.0):
         el = time.perf_counter() - t0
         if el > budget_s or k >= 12:
             break
-    return {"value": n * k / el / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d FP64 oracle V-cycles of the 128^3 workload from phi=0 (%.1f s, serial C)" % (k, el)}
+    o.close()
+    return n * k, el, k
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(p, budget_s=8.0):
+    """The oracle as it stands (serial FP64 C): V-cycles of the same workload
+    from phi = 0, (1) on one host core, and (2) one independent oracle
+    instance per host core in a process pool (spawned, so that no worker
+    inherits the CUDA context), whose summed cell updates over the slowest
+    worker's time give the all-core throughput."""
+    import multiprocessing as mp
+    units, el, k = _oracle_vcycles(budget_s)
+    serial = units / el / 1e6
+    cores = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_vcycles, [budget_s] * cores)
+    total = sum(r[0] for r in res) / max(r[1] for r in res) / 1e6
+    return {"value": total, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+            "sample": "one oracle instance per core (%d processes), each %d-%d FP64 V-cycles of the 128^3 "
+                      "workload from phi=0 (about %.0f s each, serial C)" % (cores, min(r[2] for r in res),
+                                                                            max(r[2] for r in res), budget_s),
+            "serial": {"value": serial, "unit": UNIT, "cores": 1,
+                       "sample": "%d FP64 oracle V-cycles of the 128^3 workload from phi=0 (%.1f s, one core)" % (k, el)}}
 
 
 def run_reference(args):
@@ -327,7 +386,8 @@ def roofline_of(prof, t, nrhs, peak, peak_kind):
     lev = max(rows, key=lambda r: r[4])[2]
     row = [r for r in rows if r[2] == lev][0]
     per_launch_ms = row[4] / row[3]
-    alg = algorithmic_bytes(dom_kind, dom_prec, lev, t, t.lmax, nrhs)
+    cluster = any(r[0] == "coarse_cluster" for r in prof)
+    alg = algorithmic_bytes(dom_kind, dom_prec, lev, t, t.lmax, nrhs, cluster)
     achieved = alg / (per_launch_ms * 1e-3) / 1e9
     traffic = ncu_traffic(dom_kind, dom_prec, lev)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

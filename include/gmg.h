@@ -278,8 +278,11 @@ int gmg_residual(gmg_tree *tree, double *rel_l2, double *linf, void *stream);
  * partial sums live in one static device array of the library (3 MiB, held
  * on every device that loads the library until the process exits), which
  * limits the tree to 131072 blocks (larger trees: GMG_ERR_INVALID_ARG).
- * The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress), so make it before any stream capture.  All calls
+ * The first call on a device sets that device up: it looks up the device
+ * addresses of that array and of a constant activity flag
+ * (cudaGetSymbolAddress) and sets the kernels' shared-memory attributes, so
+ * make it before any stream capture.  The call writes no state of the tree
+ * (solves of the same tree on other streams are not disturbed).  All calls
  * share the array: calls that overlap on the GPU (several streams or host
  * threads at once) race and must be serialised by the caller.
  * With several right-hand-side slots it evaluates slot 0 (over all trees of

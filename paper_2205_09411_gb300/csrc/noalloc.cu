@@ -22,29 +22,6 @@ namespace {
 constexpr int kNoAllocMaxBlocks = 131072;
 __device__ __align__(256) double g_noalloc_scratch[3 * kNoAllocMaxBlocks + 2];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_addr_mutex;
-double *g_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device, looked up once
-// per device (host code only holds a host-side stand-in for the symbol).
-int scratch_address(double **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return gmg::set_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e)), GMG_ERR_CUDA;
-  if (dev < 0 || dev >= kMaxDevices) return gmg::set_error("device index out of range"), GMG_ERR_INVALID_ARG;
-  std::lock_guard<std::mutex> lock(g_addr_mutex);
-  if (!g_addr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess)
-      return gmg::set_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e)), GMG_ERR_CUDA;
-    g_addr[dev] = static_cast<double *>(p);
-  }
-  *out = g_addr[dev];
-  return GMG_OK;
-}
-
 // Fixed-order reduction of the partials held in the scratch array (slot 0
 // of a tree with several right-hand-side slots); writes
 // ||r||_2 / ||b||_2 (or ||r||_2 when b = 0) and max |r| to out[0], out[1].
@@ -74,8 +51,63 @@ __global__ void __launch_bounds__(1024) k_reduce_noalloc(int nb, double *out) {
   }
 }
 
+// The activity flag the residual kernel reads for its one unit: the call
+// evaluates slot 0 of every tree together, always, and leaves the tree's
+// own unit mask (which a solve on another stream may be using) untouched.
+__device__ const int g_noalloc_active = 1;
+
+constexpr int kMaxDevices = 64;
+std::mutex g_addr_mutex;
+struct DeviceState {
+  double *scratch = nullptr;
+  const int *active = nullptr;
+};
+DeviceState g_dev[kMaxDevices];
+
 template <int D, int NT>
-void launch_resnorm(gmg_tree *t, int l, double *partials, cudaStream_t s) {
+cudaError_t resnorm_attrs() {
+  cudaError_t e = cudaFuncSetAttribute(gmg::k_resnorm<double, D, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gmg::k_resnorm<double, D, NT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  return e;
+}
+
+// Set-up of the current device, once per device: the device addresses of
+// the scratch array and of the activity flag (host code holds only
+// host-side stand-ins for these symbols), and the shared-memory attributes
+// of every kernel variant the call launches.
+int device_state(DeviceState *out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return gmg::set_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e)), GMG_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) return gmg::set_error("device index out of range"), GMG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_addr_mutex);
+  DeviceState &st = g_dev[dev];
+  if (!st.scratch) {
+    void *p = nullptr, *a = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e == cudaSuccess) e = cudaGetSymbolAddress(&a, g_noalloc_active);
+    if (e != cudaSuccess)
+      return gmg::set_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e)), GMG_ERR_CUDA;
+    const cudaError_t attrs[] = {resnorm_attrs<3, 4>(), resnorm_attrs<3, 8>(), resnorm_attrs<3, 16>(),
+                                 resnorm_attrs<3, 0>(), resnorm_attrs<2, 8>(), resnorm_attrs<2, 16>(),
+                                 resnorm_attrs<2, 32>(), resnorm_attrs<2, 0>(),
+                                 cudaFuncSetAttribute(k_reduce_noalloc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                                      (int)cudaSharedmemCarveoutMaxShared)};
+    for (cudaError_t ea : attrs)
+      if (ea != cudaSuccess)
+        return gmg::set_error(std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ea)), GMG_ERR_CUDA;
+    st.scratch = static_cast<double *>(p);
+    st.active = static_cast<const int *>(a);
+  }
+  *out = st;
+  return GMG_OK;
+}
+
+template <int D, int NT>
+void launch_resnorm(gmg_tree *t, int l, double *partials, const int *active, cudaStream_t s) {
   gmg::GmgView<double> V;
   V.nbr = t->d_nbr;
   V.pnb = t->d_pnb;
@@ -96,11 +128,11 @@ void launch_resnorm(gmg_tree *t, int l, double *partials, cudaStream_t s) {
   V.n_cut = t->n_cut;
   V.wneu = 0;
   for (int w = 0; w < 6; w++) V.wneu |= (t->wall_type[w] == GMG_WALL_NEUMANN ? 1 : 0) << w;
-  V.nrhs = 1;  // slot 0 only (all trees of a forest)
+  V.nrhs = 1;  // slot 0 only, all trees of a forest as one unit
   V.rs_phi = V.rs_f = t->total_cells;
-  V.ntree = t->ntree;
+  V.ntree = 1;
   V.tree_of = t->d_tree_of;
-  V.active = t->d_active;
+  V.active = active;
   const gmg::LevelInfo &Li = t->lev(l);
   gmg::LvArgs L{Li.first, Li.count, Li.n, Li.ncell, Li.off, Li.h, Li.off, 0, 0, Li.h * Li.h, 1.0 / (Li.h * Li.h)};
   gmg::LvArgs Lp = L;
@@ -109,20 +141,19 @@ void launch_resnorm(gmg_tree *t, int l, double *partials, cudaStream_t s) {
     Lp = gmg::LvArgs{Pi.first, Pi.count, Pi.n, Pi.ncell, Pi.off, Pi.h, Pi.off, 0, 0, Pi.h * Pi.h, 1.0 / (Pi.h * Pi.h)};
   }
   const size_t sm = gmg::level_smem_bytes<double>(D, Li.n);
-  cudaFuncSetAttribute(gmg::k_resnorm<double, D, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(gmg::k_resnorm<double, D, NT>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                       (int)cudaSharedmemCarveoutMaxShared);
   gmg::k_resnorm<double, D, NT><<<L.count, gmg::resnorm_threads(t, l), sm, s>>>(V, L, Lp, partials, nullptr,
                                                                   (int)t->blocks.size());
 }
 
+// the block sides the library's own residual launch specialises
 template <int D>
-void launch_resnorm_any(gmg_tree *t, int l, double *partials, cudaStream_t s) {
-  switch (t->lev(l).n) {
-    case 8: launch_resnorm<D, 8>(t, l, partials, s); break;
-    case 16: launch_resnorm<D, 16>(t, l, partials, s); break;
-    default: launch_resnorm<D, 0>(t, l, partials, s); break;
-  }
+void launch_resnorm_any(gmg_tree *t, int l, double *partials, const int *active, cudaStream_t s) {
+  const int n = t->lev(l).n;
+  if (D == 3 && n == 4) return launch_resnorm<D, 4>(t, l, partials, active, s);
+  if (n == 8) return launch_resnorm<D, 8>(t, l, partials, active, s);
+  if (n == 16) return launch_resnorm<D, 16>(t, l, partials, active, s);
+  if (D == 2 && n == 32) return launch_resnorm<D, 32>(t, l, partials, active, s);
+  launch_resnorm<D, 0>(t, l, partials, active, s);
 }
 
 }  // namespace
@@ -135,16 +166,14 @@ extern "C" int gmg_residual_noalloc(gmg_tree *t, double *out, void *stream) {
                           " blocks, more than the fixed scratch holds (" + std::to_string(kNoAllocMaxBlocks) + ")"),
            GMG_ERR_INVALID_ARG;
   if (!t->bound) return gmg::set_error("tree not bound"), GMG_ERR_STATE;
-  double *scratch = nullptr;
-  int rc = scratch_address(&scratch);
+  DeviceState st;
+  int rc = device_state(&st);
   if (rc) return rc;
+  double *scratch = st.scratch;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   // blocks on levels without leaves write no partials: clear the previous
   // call's contents first
   cudaError_t e = cudaMemsetAsync(scratch, 0, (size_t)nb * 3 * sizeof(double), s);
-  if (e != cudaSuccess) return gmg::set_error(std::string("cudaMemsetAsync: ") + cudaGetErrorString(e)), GMG_ERR_CUDA;
-  // slot 0 active (the unit mask is set by every entry point that runs kernels)
-  e = cudaMemsetAsync(t->d_active, 1, (size_t)t->ntree * sizeof(int), s);
   if (e != cudaSuccess) return gmg::set_error(std::string("cudaMemsetAsync: ") + cudaGetErrorString(e)), GMG_ERR_CUDA;
   for (int l = t->lmin; l <= t->lmax; l++) {
     bool leaves = false;
@@ -152,12 +181,10 @@ extern "C" int gmg_residual_noalloc(gmg_tree *t, double *out, void *stream) {
     for (int i = 0; i < Li.count && !leaves; i++) leaves = !t->blocks[Li.first + i].has_children;
     if (!leaves) continue;
     if (t->D == 3)
-      launch_resnorm_any<3>(t, l, scratch, s);
+      launch_resnorm_any<3>(t, l, scratch, st.active, s);
     else
-      launch_resnorm_any<2>(t, l, scratch, s);
+      launch_resnorm_any<2>(t, l, scratch, st.active, s);
   }
-  cudaFuncSetAttribute(k_reduce_noalloc, cudaFuncAttributePreferredSharedMemoryCarveout,
-                       (int)cudaSharedmemCarveoutMaxShared);
   k_reduce_noalloc<<<1, 1024, 0, s>>>((int)nb, out);
   e = cudaGetLastError();
   if (e != cudaSuccess) return gmg::set_error(std::string("kernel launch: ") + cudaGetErrorString(e)), GMG_ERR_CUDA;

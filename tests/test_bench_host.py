@@ -15,7 +15,7 @@ import bench  # noqa: E402
 class FakeTree:
     """Levels 0..2 of 16^3 blocks (1, 8, 64 blocks); 10 listed cells per
     block of level 2 (6 of colour 0, 4 of colour 1), none elsewhere."""
-    lmin, lmax, n_leaf_cells = 0, 2, 64 * 16 ** 3
+    lmin, lmax, n_leaf_cells, dim = 0, 2, 64 * 16 ** 3, 3
 
     def level_info(self, l):
         return (8 ** l, 16, 1.0 / (16 * 2 ** l))
@@ -41,15 +41,24 @@ def test_algorithmic_bytes_per_kind():
     assert bench.algorithmic_bytes("accumulate", "fp64", 2, t, 2, nrhs=2) == t.n_leaf_cells * 2 * 20
 
 
-def test_coarse_cycle_bytes_cover_the_cooperative_levels():
+def test_coarse_cycle_bytes_follow_the_level_visit_model():
+    """The coarse kernels count 3S + 3S/8 (down leg) + 3S + 2S/8 (up leg)
+    bytes a cell on each level they cover, plus the coarsest-level inverse
+    once; with the cluster kernel at the bottom it takes the levels up to
+    the roots' children level and the cooperative kernel, launched for the
+    down and the up leg, the levels above, half of them per launch."""
     t = FakeTree()
     S = 4
     split = bench.coop_split(t)
     assert split == 2  # every level has at most 160 blocks
     c0, c1, c2 = 4096, 8 * 4096, 64 * 4096
-    per_level = lambda c, cp: c * (4 * 2 * S + 4.5 * S) + cp * 4 * S
-    want = c0 * 2 * S + per_level(c1, c0) + per_level(c2, c1) + c0 ** 2 * 8
-    assert bench.algorithmic_bytes("coarse_solve", "fp32", -1, t, 2) == pytest.approx(want)
+    v = (3 + 3 / 8 + 3 + 2 / 8) * S
+    inv = c0 ** 2 * 8
+    assert bench.algorithmic_bytes("coarse_solve", "fp32", -1, t, 2) == pytest.approx((c0 + c1 + c2) * v + inv)
+    assert bench.cluster_top(t) == 1  # level 1 holds the root's 8 children
+    assert bench.algorithmic_bytes("coarse_cluster", "fp32", -1, t, 2, cluster=True) == pytest.approx((c0 + c1) * v + inv)
+    assert bench.algorithmic_bytes("coarse_solve", "fp32", -1, t, 2, cluster=True) == pytest.approx(c2 * v / 2)
+    assert bench.algorithmic_bytes("coarse_solve", "fp64", -1, t, 2, nrhs=2) == pytest.approx(2 * (c0 + c1 + c2) * 2 * v + inv)
 
 
 def test_roofline_of_picks_the_dominant_kernel():

@@ -210,3 +210,26 @@ def test_fmg_steps_solve(prec):
         l2, _, bn = o.residual()
         assert st["rel_l2"] <= 1e-8 and l2 / bn <= 1.05e-8
     assert steps[1] <= steps[0], steps
+
+
+def test_forest_256_tree_at_the_tuned_schedule_matches_oracle():
+    """The batched-trees workload's largest member: a 256^3 ellipsoid tree in
+    a forest of 16^3-cell blocks run with 128-thread CTAs (the schedule the
+    autotuner picks for that workload), beside a 32^3 and a 64^3 tree; FP64
+    iterates of every tree against the oracle after each of 3 V-cycles."""
+    ps = I.forest_problems(3, index=4, sizes=(256,), N=16)
+    ps[1] = I.forest_problems(1, index=5, sizes=(32,), N=16)[0]
+    ps[2] = I.forest_problems(1, index=6, sizes=(64,), N=16)[0]
+    F, trees = make_forest(ps)
+    F.set_option("cta_threads", 128)
+    F.set_rhs(forest_rhs(F, ps, trees))
+    oracles = [oracle_problem(p) for p in ps]
+    for k in range(3):
+        F.vcycle(1)
+        got = F.solution()
+        for i, o in enumerate(oracles):
+            o.vcycle(1)
+            ref = o.solution()
+            off, n = F.tree_leaves(i)
+            err = np.abs(got[off:off + n] - ref).max() / np.abs(ref).max()
+            assert err <= 1e-12, "tree %d (n=%d) cycle %d: %.3e" % (i, ps[i]["n"], k + 1, err)
