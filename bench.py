@@ -495,15 +495,24 @@ def host_tree(G, p, N=None, nrhs=1):
     return t
 
 
-def forest_of(G, ps, N, threads=16):
-    """Forest of the problems with N^3 blocks; the trees' host set-up runs
-    in parallel threads (the library's set-up calls release the GIL)."""
+def forest_of(G, ps, N, threads=16, times=None):
+    """Forest of the problems with N^3 blocks; the trees' set-up calls run
+    in parallel threads (they release the GIL; the boundary detection of
+    the built-in level sets runs on the device).  times: a dict that
+    receives the seconds of the trees' set-up and of the forest's creation
+    and binding."""
     from concurrent.futures import ThreadPoolExecutor
     qs = [dict(p, max_level=int(round(np.log2(p["n"] / N))) + 1) for p in ps]
+    t0 = time.perf_counter()
     with ThreadPoolExecutor(threads) as ex:
         trees = list(ex.map(lambda p: host_tree(G, p, N), qs))
+    t1 = time.perf_counter()
     F = G.Forest(trees)
     F.bind()
+    if times is not None:
+        times["trees_s"] = t1 - t0
+        times["forest_and_bind_s"] = time.perf_counter() - t1
+        times["boundary_detection"] = "device" if all(t.setup_on_device() for t in trees) else "host"
     return F, trees, qs
 
 
@@ -539,9 +548,12 @@ def run_forest(G, args, world, flush, stream):
     tune_s = time.perf_counter() - t0
     N = best.block_n
     t0 = time.perf_counter()
-    F, trees, qs = forest_of(G, I.forest_problems(64, index=3), N)
+    setup_parts = {}
+    F, trees, qs = forest_of(G, I.forest_problems(64, index=3), N, times=setup_parts)
     AT.apply(F, best)
+    t1 = time.perf_counter()
     g = forest_rhs_device(F, trees, qs, N)
+    setup_parts["rhs_s"] = time.perf_counter() - t1
     setup_s = time.perf_counter() - t0
     n = F.n_leaf_cells
     sizes = [q["n"] for q in qs]
@@ -588,7 +600,7 @@ def run_forest(G, args, world, flush, stream):
                          "inner_cycles": best.inner_cycles,
                          "tuning_s": tune_s, "trials": len(best.trials),
                          "sample": "8 problems of the same distribution (seed index 4), tiles 8 and 16"},
-           "setup_s": setup_s, "mixed": res["mixed"], "fp64": res["fp64"], "roofline": roof,
+           "setup_s": setup_s, "setup_parts": setup_parts, "mixed": res["mixed"], "fp64": res["fp64"], "roofline": roof,
            "kernel_ms_by_kind": {"%s_%s" % k: v for k, v in sorted(by_kind.items(), key=lambda kv: -kv[1])}}
     F.close()
     del g

@@ -167,9 +167,19 @@ int gmg_set_walls(gmg_tree *tree, const int *types, const double *values, gmg_fn
  * cut-cell coefficients of Eq. (lpl-1d-lsf) with the coefficients of
  * boundary neighbours moved to the right-hand side (value phib(x0, user) at
  * the root x0, or phib_const when phib == NULL), the Dirichlet wall terms,
- * and the coarsest-level inverse.  Runs on the host before gmg_tree_bind
- * (results are uploaded by gmg_tree_bind).  Errors: STATE if already bound. */
+ * and the coarsest-level inverse.  Runs before gmg_tree_bind (results are
+ * uploaded by gmg_tree_bind).  With a built-in sphere, capsule or ellipsoid
+ * and a CUDA device present (option GMG_OPT_DEVICE_SETUP, default on) the
+ * mask, line searches and unresolved-root search run as device kernels on
+ * the current device (temporary device memory, freed before the call
+ * returns; the call synchronises); callbacks, sampled level sets and sharp
+ * shapes run on the host.  Both give the same values bit for bit.  The
+ * stencils and terms are assembled on the host.
+ * Errors: STATE if already bound, CUDA (device set-up). */
 int gmg_store_stencils(gmg_tree *tree, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, double phib_const);
+/* 1 when the tree's last gmg_store_stencils ran its boundary detection on
+ * the device, else 0. */
+int gmg_setup_on_device(const gmg_tree *tree);
 
 /* A new boundary value phi_b (phib(x0, user), or phib_const when phib ==
  * NULL) on the stored boundary: phi_b at every located root and the moved
@@ -412,6 +422,11 @@ int gmg_profile_read(gmg_tree *tree, int cap, int *kind, int *prec, int *level, 
                                     launch), 1 when every unit's cluster is resident at once, 2
                                     whenever the tree qualifies (sides multiples of 4, octants
                                     within one CTA's shared memory); same arithmetic */
+#define GMG_OPT_DEVICE_SETUP 12  /* [1] gmg_store_stencils with a built-in sphere, capsule or ellipsoid
+                                    level set runs the boundary mask, the line searches and the
+                                    unresolved-root search on the device when a CUDA device is
+                                    present (the same values bit for bit); 0 on the host.  Set it
+                                    before gmg_store_stencils. */
 int gmg_set_option(gmg_tree *tree, int option, long long value);
 
 /* Sweep schedule: N_down / N_up red-black sweeps on one level (default: the

@@ -95,6 +95,7 @@ def load():
         "gmg_forest_create": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(vp)]),
         "gmg_tree_remesh": (C.c_int, [vp, REFINE_FN, vp, C.c_int, C.POINTER(vp)]),
         "gmg_setup_counts": (C.c_int, [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+        "gmg_setup_on_device": (C.c_int, [vp]),
         "gmg_transfer_solution": (C.c_int, [vp, vp, vp]),
         "gmg_iterate_begin": (C.c_int, [vp, C.c_int, ip, C.c_int, vp]),
         "gmg_iterate_end": (C.c_int, [vp, dp, dp]),
@@ -245,6 +246,10 @@ class Tree:
         t._adopt(h, self.dim, self.block_n)
         t._keep = list(self._keep) + [cb]
         return t
+
+    def setup_on_device(self):
+        """True when the last store_stencils ran its boundary detection on the device."""
+        return bool(load().gmg_setup_on_device(self.h))
 
     def setup_counts(self):
         """(blocks set up, blocks taken from the previous tree)."""
@@ -550,7 +555,7 @@ class Tree:
 
     OPTIONS = {"graphs": 1, "coarse_coop": 2, "spin_limit": 3, "fused_sweeps": 4, "cta_threads": 5,
                "coop_max_blocks": 6, "inner_cycles": 7, "slots_per_cta": 8, "fmg_steps": 9, "pdl": 10,
-               "cluster_tail": 11}
+               "cluster_tail": 11, "device_setup": 12}
 
     def set_level_sweeps(self, level, n_down, n_up):
         """N_down / N_up red-black sweeps on one level (a tuning schedule)."""

@@ -7,6 +7,8 @@ shared library with a plain C ABI (include/gmg.h):
 * csrc/tree_setup.cpp  - block tree and boundary set-up on the host
   (-ffp-contract=off: the level-set arithmetic is plain IEEE)
 * csrc/cluster_tail.cu - the bottom of the V-cycle on a thread-block cluster
+* csrc/setup_dev.cu    - boundary detection of built-in level sets on the device
+  (--fmad=false: the same arithmetic as the host set-up)
 * csrc/noalloc.cu      - residual norm with a static scratch array (no allocation)
 * csrc/forest.cpp      - forests of independent trees (host)
 * csrc/solve_history.cpp - the solve loop with its residual history (host)
@@ -23,7 +25,10 @@ LIB = os.path.join(OUT, "libgmg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
           "-I", os.path.join(ROOT, "include"), "-I", CSRC]
-SOURCES = ["gmg_api.cu", "cluster_tail.cu", "tree_setup.cpp", "noalloc.cu", "forest.cpp", "solve_history.cpp"]
+SOURCES = ["gmg_api.cu", "cluster_tail.cu", "setup_dev.cu", "tree_setup.cpp", "noalloc.cu", "forest.cpp",
+           "solve_history.cpp"]
+# device code whose arithmetic must equal the host set-up's: no multiply-add contraction
+NO_FMAD = {"setup_dev.cu"}
 
 
 def _nvcc():
@@ -49,7 +54,7 @@ def build(force=False, verbose=False):
     procs, objs = [], []
     for src in SOURCES:
         obj = os.path.join(OUT, src + ".o")
-        cmd = [nvcc] + ARCH + COMMON + ["-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc] + ARCH + COMMON + (["--fmad=false"] if src in NO_FMAD else []) + ["-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cpp"):
             cmd = [nvcc] + COMMON + ["-x", "c++", "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:

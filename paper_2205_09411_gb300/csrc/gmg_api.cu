@@ -1120,6 +1120,8 @@ int gmg_tree_remesh(const gmg_tree *old, gmg_refine_fn refine, void *refine_user
   return GMG_OK;
 }
 
+int gmg_setup_on_device(const gmg_tree *t) { return t && t->setup_device ? 1 : 0; }
+
 int gmg_setup_counts(const gmg_tree *t, long long *computed, long long *reused) {
   if (!t) return set_error("null tree"), GMG_ERR_INVALID_ARG;
   if (computed) *computed = t->setup_computed;
@@ -1740,6 +1742,7 @@ int gmg_set_option(gmg_tree *t, int option, long long value) {
       if (t->bound) set_coop_split(t);
       break;
     case GMG_OPT_FMG_STEPS: t->fmg_steps = value != 0; break;
+    case GMG_OPT_DEVICE_SETUP: t->setup_on_device = value != 0; break;
     case GMG_OPT_CLUSTER_TAIL:
       if (value < 0 || value > 2) return set_error("cluster tail must be 0 (off), 1 (auto) or 2 (whenever the tree qualifies)"), GMG_ERR_INVALID_ARG;
       t->cluster_mode = (int)value;

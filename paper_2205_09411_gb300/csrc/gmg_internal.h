@@ -232,6 +232,8 @@ struct gmg_tree {
   int slots_per_cta = 1;      // right-hand-side slots of a block per CTA in the half-sweeps (1, 2, 4)
   bool fmg_steps = false;     // solve steps are FMG cycles instead of V-cycles
   bool use_pdl = true;        // per-level kernels with programmatic dependent launch
+  bool setup_on_device = true;  // boundary detection of built-in level sets on the device when one is present
+  bool setup_device = false;    // the last set-up ran its boundary detection on the device
   int cluster_mode = 1;       // bottom of the cycle on a thread-block cluster: 0 off, 1 when all units fit at once, 2 whenever eligible
   std::vector<char> level_complete;  // every block has all 26 neighbours on its level (or walls)
   int coop_split = 0;         // highest level run inside that launch
@@ -282,4 +284,12 @@ int build_tree(gmg_tree *T, const gmg_domain *dom);
 int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, double phib_const,
                const gmg_tree *reuse = nullptr);
 void build_cut_lists(gmg_tree *T);
+struct LsfSpec;
+// Boundary detection on the device for a built-in level set (setup_dev.cu):
+// mask[cell] for every cell in block order (bit 0 Eq. (boundary-mask), bit
+// 1 centre inside), the masked cells (index in that order, ascending) and
+// their 2D relative distances.  Bit for bit the host set-up's values.
+bool device_setup_available();
+int device_boundary_detection(const gmg_tree *T, const LsfSpec &spec, std::vector<uint8_t> &mask,
+                              std::vector<long long> &masked_cells, std::vector<double> &dist);
 }  // namespace gmg

@@ -479,6 +479,47 @@ void block_terms(const gmg_tree *T, const HostBlock &B, const LevelInfo &L, cons
   }
 }
 
+// The right-hand-side terms of a block no boundary crosses: only the
+// Dirichlet wall terms of the cells beside a domain wall, with the regular
+// coefficient 1 / dx^2 (block_terms' values for such a block, in its order).
+// Returns false when every term is zero.
+bool wall_terms(const gmg_tree *T, const HostBlock &B, const LevelInfo &L, std::vector<double> &bt) {
+  const int D = T->D, n = L.n, nc = L.ncell;
+  const double h = L.h, inv_h2 = 1.0 / (h * h);
+  bool touches = false;
+  for (int k = 0; k < D && !touches; k++)
+    touches = (T->wall_type[2 * k] == GMG_WALL_DIRICHLET && B.ix[k] == 0) ||
+              (T->wall_type[2 * k + 1] == GMG_WALL_DIRICHLET && B.ix[k] + 1 >= L.bext[k]);
+  if (!touches) return false;
+  bt.assign(nc, 0.0);
+  bool any = false;
+  for (int c = 0; c < nc; c++) {
+    int p[3] = {c % n, (c / n) % n, D == 3 ? c / (n * n) : 0};
+    bool shell = false;  // beside one of the block's faces (others have no wall term)
+    for (int k = 0; k < D; k++) shell = shell || p[k] == 0 || p[k] == n - 1;
+    if (!shell) continue;
+    double t = 0.0;
+    for (int k = 0; k < D; k++)
+      for (int s = 0; s < 2; s++) {
+        int G[3];
+        for (int d = 0; d < 3; d++) G[d] = d < D ? B.ix[d] * n + p[d] : 0;
+        G[k] += s ? 1 : -1;
+        if (in_domain(L, D, G)) continue;
+        int w = 2 * k + s;
+        if (T->wall_type[w] != GMG_WALL_DIRICHLET) continue;
+        double a[3];
+        cell_center(T, B, L, p, a);
+        double xf[3] = {a[0], a[1], a[2]};
+        xf[k] = s ? a[k] + 0.5 * h : a[k] - 0.5 * h;
+        double v = T->wall_fn ? T->wall_fn(xf, T->wall_user) : T->wall_val[w];
+        t = t + inv_h2 * (2.0 * v);
+      }
+    bt[c] = t;
+    any = any || t != 0.0;
+  }
+  return any;
+}
+
 }  // namespace
 
 int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, double phib_const,
@@ -525,19 +566,54 @@ int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, do
     bool cut = false, anybt = false;
   };
   std::vector<BlockOut> outs(nb);
+  // boundary detection of a built-in level set on the device (bit for bit
+  // the loops below); the host keeps callbacks and sampled level sets
+  std::vector<uint8_t> dev_mask;
+  std::vector<long long> dev_cells, cell_first, entry_first;
+  std::vector<double> dev_dist;
+  const bool on_device = T->setup_on_device && !reuse &&
+                         (lsf->kind == GMG_LSF_SPHERE || lsf->kind == GMG_LSF_CAPSULE ||
+                          lsf->kind == GMG_LSF_ELLIPSOID) && device_setup_available();
+  if (on_device) {
+    const int rc = device_boundary_detection(T, f.spec, dev_mask, dev_cells, dev_dist);
+    if (rc) return rc;
+    cell_first.assign(nb + 1, 0);
+    for (int b = 0; b < nb; b++) cell_first[b + 1] = cell_first[b] + T->lev(T->blocks[b].level).ncell;
+    entry_first.assign(nb + 1, 0);
+    for (int b = 0; b < nb; b++)
+      entry_first[b + 1] =
+          std::lower_bound(dev_cells.begin(), dev_cells.end(), cell_first[b + 1]) - dev_cells.begin();
+  }
+  T->setup_device = on_device;
   auto process = [&](int id, BlockOut &o) {
     const HostBlock &B = T->blocks[id];
     const LevelInfo &L = T->lev(B.level);
     const int n = L.n, nc = L.ncell;
     const double h = L.h;
     const double Lmask = T->prm.mask_factor * std::sqrt((double)D) * h;
-    std::vector<double> dd((size_t)nc * 2 * D, 1.0), pb((size_t)nc * 2 * D, 0.0), st, bt;
-    o.mask.assign(nc, 0);
-    uint8_t *mask = o.mask.data();
+    // distances (1 = no root) only for blocks with a masked cell
+    std::vector<double> dd, pb, st, bt;
+    auto dist_of = [&](int c) {
+      if (dd.empty()) dd.assign((size_t)nc * 2 * D, 1.0);
+      return &dd[(size_t)c * 2 * D];
+    };
     bool cut = false;
+    if (on_device) {
+      o.mask.assign(dev_mask.begin() + cell_first[id], dev_mask.begin() + cell_first[id + 1]);
+      for (long long e = entry_first[id]; e < entry_first[id + 1]; e++) {
+        double *dc = dist_of((int)(dev_cells[e] - cell_first[id]));
+        for (int k = 0; k < 2 * D; k++) {
+          dc[k] = dev_dist[(size_t)e * 2 * D + k];
+          if (dc[k] < 1.0) cut = true;
+        }
+      }
+    } else {
+      o.mask.assign(nc, 0);
+    }
+    uint8_t *mask = o.mask.data();
     for (int c = 0; c < nc; c++) {
       int p[3] = {c % n, (c / n) % n, D == 3 ? c / (n * n) : 0};
-      if (!have) break;
+      if (!have || on_device) break;
       double a[3];
       cell_center(T, B, L, p, a);
       double fa = f(a);
@@ -554,7 +630,7 @@ int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, do
       gn = std::sqrt(gn);
       if (!(std::fabs(fa) < Lmask * gn)) continue;
       mask[c] |= 1;
-      double *dc = &dd[(size_t)c * 2 * D];
+      double *dc = dist_of(c);
       bool found = false;
       for (int k = 0; k < D; k++)
         for (int s = 0; s < 2; s++) {
@@ -571,14 +647,16 @@ int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, do
       for (int k = 0; k < 2 * D; k++)
         if (dc[k] < 1.0) cut = true;
     }
-    block_terms(T, B, L, dd.data(), cut, phib, phib_user, phib_const, st, bt, pb);
-    o.cut = cut;
-    if (cut) {
+    if (cut) {  // Eq. (lpl-1d-lsf) stencils and the moved terms
+      block_terms(T, B, L, dd.data(), cut, phib, phib_user, phib_const, st, bt, pb);
+      for (int c = 0; c < nc; c++) o.anybt = o.anybt || bt[c] != 0.0;
       o.st = std::move(st);
       o.dd = std::move(dd);
       o.pb = std::move(pb);
+    } else {  // the regular stencil: only Dirichlet wall terms
+      o.anybt = wall_terms(T, B, L, bt);
     }
-    for (int c = 0; c < nc; c++) o.anybt = o.anybt || bt[c] != 0.0;
+    o.cut = cut;
     // Dirichlet values at the centres of the block's faces on upper domain
     // walls (axis k, face cell j over the other axes in increasing order),
     // for the field evaluation on upper cell faces
