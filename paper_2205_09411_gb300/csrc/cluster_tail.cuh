@@ -336,9 +336,9 @@ __device__ __forceinline__ void oct_prolong(const Oct<T, D> &F, const Oct<T, D> 
 // phi adds L.poff - L.off)
 template <typename T, int D>
 __device__ __forceinline__ long long oct_gidx(const Oct<T, D> &Q, int children, int x, int y, int z) {
-  if (children) return Q.L.off + (long long)(Q.bid - Q.L.first) * Q.L.ncell + x + Q.m * (y + (D == 3 ? Q.m * z : 0));
-  const int X = Q.o[0] + x, Y = Q.o[1] + y, Z = Q.o[2] + z;
-  return Q.L.off + (long long)(Q.bid - Q.L.first) * Q.L.ncell + X + Q.N * (Y + (D == 3 ? Q.N * Z : 0));
+  const long long base = Q.L.off + (long long)(Q.bid - Q.L.first) * Q.L.ncell;
+  if (children) return base + cs_pos_xyz(x, y, D == 3 ? z : 0, Q.m, Q.L.ncell);
+  return base + cs_pos_xyz(Q.o[0] + x, Q.o[1] + y, D == 3 ? Q.o[2] + z : 0, Q.N, Q.L.ncell);
 }
 
 template <typename T, int D>

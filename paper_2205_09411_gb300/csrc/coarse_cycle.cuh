@@ -12,7 +12,7 @@
 // arithmetic is exactly that of the per-level kernels.
 #pragma once
 
-#include "kernels.cuh"
+#include "csweep.cuh"
 
 namespace gmg {
 
@@ -81,10 +81,14 @@ struct CycleArgs {
 template <typename T, int D, int NT>
 __device__ __forceinline__ void smooth_any(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, int c,
                                            unsigned char *sm) {
-  if (NT && L.n == NT)
-    smooth_block<T, D, NT>(V, L, Lp, bid, c, sm);
-  else
-    smooth_block<T, D, 0>(V, L, Lp, bid, c, sm);
+  if constexpr (NT != 0) {
+    if (L.n == NT) {  // the colour-split half-sweep, on the slot view (slot 0 of it)
+      const int slot0[1] = {0};
+      smooth_cs_block<T, D, NT, 1>(V, L, Lp, bid, slot0, c, sm);
+      return;
+    }
+  }
+  smooth_block<T, D, 0>(V, L, Lp, bid, c, sm);
 }
 template <typename T, int D, int NT>
 __device__ __forceinline__ void resid_restrict_any(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid,
@@ -125,10 +129,10 @@ __device__ __forceinline__ void coarse_rows(const GmgView<T> &V, const LvArgs &L
     const double *a = A.cinv + ((size_t)k * A.ncr + i) * A.ncr;
     const T *b = V.b + r * V.rs_f + Lc.off + (size_t)k * A.ncr;
     double s = 0.0;
-    for (int j = lane; j < A.ncr; j += 32) s += a[j] * (double)b[j];
+    for (int j = lane; j < A.ncr; j += 32) s += a[j] * (double)b[coarse_pos(j, Lc)];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) V.phi[r * V.rs_phi + Lc.poff + row] = T(s);
+    if (lane == 0) V.phi[r * V.rs_phi + Lc.poff + (size_t)k * A.ncr + coarse_pos(i, Lc)] = T(s);
   }
 }
 
@@ -378,21 +382,11 @@ __device__ void tail_cycle(const GmgView<T> &V, const LevelSet &LS, const CycleA
     const TileGeo<T, D> G(n);
     const T *phi = V.phi + L0.poff + (long long)root * nc;
     const T *b = V.b + L0.off + (long long)root * nc;
-    constexpr int VEC = 16 / sizeof(T);
-    if (n % VEC == 0) {
-      for (int i = threadIdx.x; i < nc / VEC; i += blockDim.x) {
-        int x, y, z;
-        cell_xyz_rt<D>(i * VEC, n, &x, &y, &z);
-        cp_async16(tile + G.idx(x, y, z), phi + i * VEC);
-        cp_async16(bq + i * VEC, b + i * VEC);
-      }
-    } else {
-      for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-        int x, y, z;
-        cell_xyz_rt<D>(c, n, &x, &y, &z);
-        cp_async_elem(tile + G.idx(x, y, z), phi + c);
-        cp_async_elem(bq + c, b + c);
-      }
+    for (int q = threadIdx.x; q < nc; q += blockDim.x) {  // the block's colour-split run in order
+      int x, y, z;
+      cs_xyz(q, n, nc, D, &x, &y, &z);
+      cp_async_elem(tile + G.idx(x, y, z), phi + q);
+      cp_async_elem(bq + x + n * (y + n * z), b + q);
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
@@ -519,7 +513,7 @@ __device__ void tail_cycle(const GmgView<T> &V, const LevelSet &LS, const CycleA
     for (int c = threadIdx.x; c < q.ncell; c += blockDim.x) {
       int x, y, z;
       cell_xyz_rt<D>(c, q.n, &x, &y, &z);
-      V.phi[q.L.poff + c] = q.tile[G.idx(x, y, z)];
+      V.phi[q.L.poff + cs_pos_xyz(x, y, z, q.n, q.ncell)] = q.tile[G.idx(x, y, z)];
     }
   }
 }

@@ -1,0 +1,278 @@
+// Red/black half-sweep on the colour-split block layout (Sec. 2.2,
+// readings S and SW; Eqs. (lpl-1d-lsf) for listed cells).
+//
+// A cell of colour c has only cells of colour 1 - c as neighbours.  With the
+// fields stored per block as the red half then the black half (cs_pos), a
+// half-sweep of colour c stages in shared memory only the other colour's
+// half of the block and of its face neighbours, plus its own colour's b,
+// and writes its own colour's half back as one contiguous run: about 1.5
+// values a cell move instead of 3 for the interleaved layout, in whole
+// sectors.
+//
+// The other colour is kept in rows: row (y, z) holds, at k = 0 .. n/2 - 1,
+// the other colour's cells x = 2k + q' of that row of the block (q' = (y +
+// z + 1 - c) mod 2), and at k = -1 and k = n/2 the x ghosts.  An own cell x
+// = 2k + q (q = 1 - q') then finds its x neighbours at k - 1 + q and k + q
+// of its row and its y and z neighbours at k of the adjacent rows.  Rows
+// outside the block (y or z = -1 or n) hold the face ghosts: a same-level
+// neighbour's boundary run, the wall reflection of the own cell beside it
+// (reading W), or the refinement-boundary value (reading G).
+#pragma once
+
+#include "kernels.cuh"
+
+namespace gmg {
+
+template <typename T, int D, int NT>
+struct CsGeo {
+  static constexpr int H = (D == 3 ? NT * NT * NT : NT * NT) / 2;  // cells of one colour
+  static constexpr int HN = NT / 2;                                 // a row's cells of one colour
+  static constexpr int X0 = 16 / (int)sizeof(T);                    // k = 0 on a 16-byte boundary
+  static constexpr int RO = HN + 2 * X0;                            // row stride
+  static constexpr int NR = D == 3 ? (NT + 2) * (NT + 2) : NT + 2;  // rows, ghost rows included
+  static constexpr int OS = NR * RO;                                // other-colour tile
+  // the tile's row of cells (y, z) of the block (each in -1 .. NT)
+  static __device__ __forceinline__ int row(int y, int z) { return (y + 1) + (D == 3 ? (NT + 2) * (z + 1) : 0); }
+  static __device__ __forceinline__ int at(int r, int k) { return r * RO + X0 + k; }
+  // shared memory of SG slots: the other-colour tiles, the own colour's b,
+  // the block's stencil flags
+  static constexpr size_t smem_bytes(int sg) {
+    return sizeof(T) * (size_t)sg * (OS + H) + (size_t)((2 * H + 15) / 16 * 16);
+  }
+};
+
+template <typename T, int D, int NT>
+inline size_t cs_smem_bytes(int sg) {
+  return CsGeo<T, D, NT>::smem_bytes(sg);
+}
+
+// Stages slot s's other-colour half, face ghosts and own-colour b for a
+// half-sweep of colour c of block bid.  cp.async for everything that comes
+// from a same-level block; wall and refinement ghosts need the copies done
+// and are filled by cs_special_ghosts.
+template <typename T, int D, int NT>
+__device__ __forceinline__ void cs_stage(const GmgView<T> &V, const LvArgs &L, int bid, int c, const int *s_nb, int fl,
+                                         long long rs_phi, long long rs_f, T *O, T *B) {
+  using G = CsGeo<T, D, NT>;
+  constexpr int VEC = 16 / sizeof(T);
+  constexpr bool kChunks = (G::HN % VEC) == 0;
+  const long long pbase = rs_phi + L.poff + (long long)(bid - L.first) * (2 * G::H);
+  const long long base = rs_f + L.off + (long long)(bid - L.first) * (2 * G::H);
+  const T *oth = V.phi + pbase + (1 - c) * G::H;
+  const T *bown = V.b + base + c * G::H;
+  // the block's other colour, rows (y, z) of the block, and its own b
+  if (kChunks) {
+    for (int i = threadIdx.x; i < G::H / VEC; i += blockDim.x) {
+      const int j = i * VEC, r = j / G::HN, k = j - r * G::HN;
+      cp_async16(O + G::at(G::row(r % NT, D == 3 ? r / NT : 0), k), oth + j);
+      cp_async16(B + j, bown + j);
+    }
+  } else {
+    for (int j = threadIdx.x; j < G::H; j += blockDim.x) {
+      const int r = j / G::HN, k = j - r * G::HN;
+      cp_async_elem(O + G::at(G::row(r % NT, D == 3 ? r / NT : 0), k), oth + j);
+      cp_async_elem(B + j, bown + j);
+    }
+  }
+  // y and z faces toward same-level neighbours: the neighbour's boundary
+  // row of the other colour, one contiguous run of HN cells per row
+  constexpr int FR = D == 3 ? NT : 1;  // rows per face
+  for (int i = threadIdx.x; i < (2 * D - 2) * FR * G::HN; i += blockDim.x) {
+    const int f = 2 + i / (FR * G::HN), rem = i - (f - 2) * FR * G::HN;
+    const int u = rem / G::HN, k = rem - u * G::HN;  // u: the face's row, k: cell in it
+    const int a = f >> 1, side = f & 1;
+    const int id = s_nb[f];
+    if ((fl & wall_bit(a, side)) || id < 0) continue;
+    const int ys = a == 1 ? (side ? 0 : NT - 1) : u, zs = a == 2 ? (side ? 0 : NT - 1) : u;
+    const int yg = a == 1 ? (side ? NT : -1) : u, zg = a == 2 ? (side ? NT : -1) : u;
+    const T *src = V.phi + rs_phi + L.poff + (long long)(id - L.first) * (2 * G::H) + (1 - c) * G::H +
+                   G::HN * (ys + (D == 3 ? NT * zs : 0));
+    cp_async_elem(O + G::at(G::row(yg, D == 3 ? zg : 0), k), src + k);
+  }
+  // x faces: in a row whose other-colour parity is 1 the ghost x = -1 is
+  // read (at k = -1), in the other rows the ghost x = NT (at k = HN)
+  for (int r = threadIdx.x; r < G::H / G::HN; r += blockDim.x) {
+    const int y = r % NT, z = D == 3 ? r / NT : 0;
+    const int qo = (y + z + 1 - c) & 1;
+    const int side = qo ? 0 : 1;
+    const int id = s_nb[side];
+    if ((fl & wall_bit(0, side)) || id < 0) continue;
+    // the neighbour's cell (NT - 1, y, z) or (0, y, z): both of colour 1 - c
+    const long long q = rs_phi + L.poff + (long long)(id - L.first) * (2 * G::H) + (1 - c) * G::H +
+                        G::HN * (y + NT * z) + (side ? 0 : G::HN - 1);
+    cp_async_elem(O + G::at(G::row(y, z), side ? G::HN : -1), V.phi + q);
+  }
+}
+
+// Wall and refinement-boundary ghosts of the other colour (after the
+// staged copies have landed): a wall ghost is the sign times the own cell
+// beside it, a refinement ghost follows reading G (refine_ghost, on the
+// slot's own block).
+template <typename T, int D, int NT>
+__device__ __forceinline__ void cs_special_ghosts(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid,
+                                                  int c, const int *s_nb, int fl, long long rs_phi, T *O) {
+  using G = CsGeo<T, D, NT>;
+  const long long pbase = rs_phi + L.poff + (long long)(bid - L.first) * (2 * G::H);
+  const T *phi = V.phi + rs_phi;
+  const T *own = V.phi + pbase;
+  constexpr int FR = D == 3 ? NT : 1;
+  // y and z faces: ghost (x, -1 or NT, z) / (x, y, -1 or NT) with x = 2k + qg
+  for (int i = threadIdx.x; i < (2 * D - 2) * FR * G::HN; i += blockDim.x) {
+    const int f = 2 + i / (FR * G::HN), rem = i - (f - 2) * FR * G::HN;
+    const int u = rem / G::HN, k = rem - u * G::HN;
+    const int a = f >> 1, side = f & 1;
+    const bool wall = (fl & wall_bit(a, side)) != 0;
+    if (!wall && s_nb[f] >= 0) continue;
+    const int yg = a == 1 ? (side ? NT : -1) : u, zg = a == 2 ? (side ? NT : -1) : (D == 3 ? u : 0);
+    const int qg = (yg + zg + 1 - c) & 1;  // the ghost row's other-colour parity
+    const int x = 2 * k + qg;
+    const int yi = a == 1 ? (side ? NT - 1 : 0) : yg, zi = a == 2 ? (side ? NT - 1 : 0) : zg;
+    T val;
+    if (wall) {
+      val = (((V.wneu >> f) & 1) ? T(1) : T(-1)) * own[cs_pos_xyz(x, yi, zi, NT, 2 * G::H)];
+    } else {
+      const int g[3] = {x, yg, zg};
+      val = refine_ghost<T, D>(phi, V.nbr, V.flags, V.parent, V.pofs, V.wneu, L, Lp, bid, g, a, own);
+    }
+    O[G::at(G::row(yg, zg), k)] = val;
+  }
+  for (int r = threadIdx.x; r < G::H / G::HN; r += blockDim.x) {
+    const int y = r % NT, z = D == 3 ? r / NT : 0;
+    const int side = ((y + z + 1 - c) & 1) ? 0 : 1;
+    const bool wall = (fl & wall_bit(0, side)) != 0;
+    if (!wall && s_nb[side] >= 0) continue;
+    const int xg = side ? NT : -1, xi = side ? NT - 1 : 0;
+    T val;
+    if (wall) {
+      val = (((V.wneu >> side) & 1) ? T(1) : T(-1)) * own[cs_pos_xyz(xi, y, z, NT, 2 * G::H)];
+    } else {
+      const int g[3] = {xg, y, z};
+      val = refine_ghost<T, D>(phi, V.nbr, V.flags, V.parent, V.pofs, V.wneu, L, Lp, bid, g, 0, own);
+    }
+    O[G::at(G::row(y, z), side ? G::HN : -1)] = val;
+  }
+}
+
+// One half-sweep of colour `color` on block bid for the slots slot[0 ..
+// SG - 1] (-1: skipped); shared memory as CsGeo::smem_bytes(SG).  Used by
+// the per-level kernel below and by the cooperative coarse cycle.
+template <typename T, int D, int NT, int SG>
+__device__ __forceinline__ void smooth_cs_block(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid,
+                                                const int *slot, int color, unsigned char *smem_raw) {
+  using G = CsGeo<T, D, NT>;
+  __shared__ int s_nb[6];
+  __shared__ int s_fl;
+  T *O = reinterpret_cast<T *>(smem_raw);
+  T *B = O + SG * G::OS;
+  unsigned char *sfl = reinterpret_cast<unsigned char *>(B + SG * G::H);
+  const long long sb = V.st_base[bid];
+  // this colour's cut list: entry e0 + i goes to thread i (fetched while the
+  // tile loads)
+  const int4 cl = V.cut_list[bid];
+  const int e0 = cl.x + (color ? cl.y : 0), m = color ? cl.z : cl.y;
+  CutCell<T, D> cq;
+  if ((int)threadIdx.x < m) cq.fetch(V, e0 + threadIdx.x);
+  if (threadIdx.x < 2 * D) {
+    const int a = threadIdx.x >> 1, side = threadIdx.x & 1;
+    const int o[3] = {a == 0 ? 2 * side - 1 : 0, a == 1 ? 2 * side - 1 : 0, a == 2 ? 2 * side - 1 : 0};
+    s_nb[threadIdx.x] = V.nbr[(size_t)bid * kNbr + nbr_slot(o[0], o[1], o[2])];
+  }
+  if (threadIdx.x == 0) s_fl = V.flags[bid];
+  if (sb >= 0) {  // which cells of a cut block have a listed stencil
+    const unsigned char *src = V.spec + sb / (2 * D + 1);
+    if ((2 * G::H) % 16 == 0 && ((size_t)src & 15) == 0) {
+      for (int i = threadIdx.x; i < 2 * G::H / 16; i += blockDim.x) cp_async16(sfl + 16 * i, src + 16 * i);
+    } else {
+      for (int i = threadIdx.x; i < 2 * G::H; i += blockDim.x) sfl[i] = src[i];
+    }
+  }
+  __syncthreads();
+  const int fl = s_fl;
+#pragma unroll
+  for (int s = 0; s < SG; s++)
+    if (slot[s] >= 0) cs_stage<T, D, NT>(V, L, bid, color, s_nb, fl, slot[s] * V.rs_phi, slot[s] * V.rs_f, O + s * G::OS,
+                                         B + s * G::H);
+  cp_async_wait_all();
+  __syncthreads();
+  bool special = false;
+#pragma unroll
+  for (int f = 0; f < 2 * D; f++) special = special || (fl & wall_bit(f >> 1, f & 1)) || s_nb[f] < 0;
+  if (special) {
+#pragma unroll
+    for (int s = 0; s < SG; s++)
+      if (slot[s] >= 0) cs_special_ghosts<T, D, NT>(V, L, Lp, bid, color, s_nb, fl, slot[s] * V.rs_phi, O + s * G::OS);
+    __syncthreads();
+  }
+  const T h2 = T(L.h2), inv2d = T(1.0 / (2 * D));
+  const long long pown = L.poff + (long long)(bid - L.first) * (2 * G::H) + color * G::H;
+  // the six neighbours of own cell j (row r, position k) in the tile
+  auto nbrs = [&](int j, int *t) {
+    const int r = j / G::HN, k = j - r * G::HN;
+    const int y = r % NT, z = D == 3 ? r / NT : 0;
+    const int q = (y + z + color) & 1;
+    const int rr = G::row(y, z);
+    t[0] = G::at(rr, k - 1 + q);
+    t[1] = G::at(rr, k + q);
+    t[2] = G::at(G::row(y - 1, z), k);
+    t[3] = G::at(G::row(y + 1, z), k);
+    t[4] = D == 3 ? G::at(G::row(y, z - 1), k) : 0;
+    t[5] = D == 3 ? G::at(G::row(y, z + 1), k) : 0;
+    return 2 * k + q + NT * (y + NT * z);  // natural index of the cell
+  };
+  for (int j = threadIdx.x; j < G::H; j += blockDim.x) {
+    int t[6];
+    const int cn = nbrs(j, t);
+    if (sb >= 0 && sfl[cn]) continue;  // a listed cell
+#pragma unroll
+    for (int s = 0; s < SG; s++) {
+      if (slot[s] < 0) continue;
+      const T *o = O + s * G::OS;
+      T sum = (o[t[0]] + o[t[1]]) + (o[t[2]] + o[t[3]]);
+      if (D == 3) sum += o[t[4]] + o[t[5]];
+      V.phi[slot[s] * V.rs_phi + pown + j] = (sum - h2 * B[s * G::H + j]) * inv2d;
+    }
+  }
+  auto upd = [&](const CutCell<T, D> &u) {
+    const int j = u.c >> 1;  // within its colour: the row pair's index
+    int t[6];
+    nbrs(j, t);
+#pragma unroll
+    for (int s = 0; s < SG; s++) {
+      if (slot[s] < 0) continue;
+      const T *o = O + s * G::OS;
+      T sum = u.a[1] * o[t[0]] + u.a[2] * o[t[1]] + u.a[3] * o[t[2]] + u.a[4] * o[t[3]];
+      if (D == 3) sum += u.a[5] * o[t[4]] + u.a[6] * o[t[5]];
+      V.phi[slot[s] * V.rs_phi + pown + j] = (B[s * G::H + j] - sum) / u.a[0];
+    }
+  };
+  if ((int)threadIdx.x < m) upd(cq);
+  for (int i = threadIdx.x + blockDim.x; i < m; i += blockDim.x) {  // lists longer than the CTA
+    CutCell<T, D> u;
+    u.fetch(V, e0 + i);
+    upd(u);
+  }
+}
+
+// The half-sweep kernel: one CTA per (block, group of SG slots); the grid
+// holds count x ceil(nrhs / SG) CTAs, slot groups fastest.  Frozen units
+// are skipped per slot.
+template <typename T, int D, int NT, int SG>
+__global__ void __launch_bounds__(kThreads) k_smooth_cs(GmgView<T> V, LvArgs L, LvArgs Lp, int color) {
+  pdl_start();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ngrp = (V.nrhs + SG - 1) / SG;
+  const int grp = (int)(blockIdx.x % (unsigned)ngrp);
+  const int bid = L.first + (int)(blockIdx.x / (unsigned)ngrp);
+  int slot[SG];
+  bool any = false;
+#pragma unroll
+  for (int s = 0; s < SG; s++) {
+    const int r = grp * SG + s;
+    slot[s] = (r < V.nrhs && V.active[unit_of(V, r, bid)]) ? r : -1;
+    any = any || slot[s] >= 0;
+  }
+  if (!any) return;
+  smooth_cs_block<T, D, NT, SG>(V, L, Lp, bid, slot, color, smem_raw);
+}
+
+}  // namespace gmg

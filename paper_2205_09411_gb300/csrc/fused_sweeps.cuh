@@ -33,8 +33,7 @@ template <typename T, int D, int NT, int K>
 __global__ void __launch_bounds__(kThreads) k_smooth_tb(GmgView<T> V0, LvArgs L, long long out_poff) {
   pdl_start();
   using F = FusedGeo<T, D, NT, K>;
-  constexpr int n = NT, VEC = F::VEC;
-  using VT = typename Vec16<T>::type;
+  constexpr int n = NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_nb[kNbr];
   __shared__ long long s_stb[kNbr];
@@ -49,20 +48,21 @@ __global__ void __launch_bounds__(kThreads) k_smooth_tb(GmgView<T> V0, LvArgs L,
     s_stb[threadIdx.x] = id >= 0 ? V.st_base[id] : -1;
   }
   __syncthreads();
-  // stage phi and b of the block and its neighbours in 16-byte chunks (a
-  // chunk never crosses a block boundary: XH and n are multiples of VEC)
-  constexpr int CX = F::RX / VEC, ROWS = F::RY * F::RZ;
+  // stage phi and b of the block and its neighbours cell by cell (the
+  // fields' colour-split layout puts a row's cells in two runs)
+  constexpr int CX = F::RX, ROWS = F::RY * F::RZ;
   for (int i = threadIdx.x; i < CX * ROWS; i += blockDim.x) {
     const int cx = i % CX, row = i / CX;
-    const int x = cx * VEC - F::XH, y = row % F::RY - K, z = D == 3 ? row / F::RY - K : 0;
+    const int x = cx - F::XH, y = row % F::RY - K, z = D == 3 ? row / F::RY - K : 0;
+    if (x < -K || x >= n + K) continue;  // beyond the halo (x rounded to 16 bytes)
     const int ox = x < 0 ? -1 : (x >= n ? 1 : 0), oy = y < 0 ? -1 : (y >= n ? 1 : 0);
     const int oz = D == 3 ? (z < 0 ? -1 : (z >= n ? 1 : 0)) : 0;
     const int id = s_nb[nbr_slot(ox, oy, oz)];
     if (id < 0) continue;  // outside the domain
-    const long long c = (long long)(id - L.first) * F::NC + (x - ox * n) +
-                        n * ((y - oy * n) + (D == 3 ? n * (z - oz * n) : 0));
-    cp_async16(tp + F::idx(x, y, z), V.phi + L.poff + c);
-    cp_async16(tb + F::idx(x, y, z), V.b + L.off + c);
+    const long long c = (long long)(id - L.first) * F::NC +
+                        cs_pos_xyz(x - ox * n, y - oy * n, D == 3 ? z - oz * n : 0, n, F::NC);
+    cp_async_elem(tp + F::idx(x, y, z), V.phi + L.poff + c);
+    cp_async_elem(tb + F::idx(x, y, z), V.b + L.off + c);
   }
   cp_async_wait_all();
   __syncthreads();
@@ -156,11 +156,11 @@ __global__ void __launch_bounds__(kThreads) k_smooth_tb(GmgView<T> V0, LvArgs L,
     }
     __syncthreads();
   }
-  VT *out = reinterpret_cast<VT *>(V.phi + out_poff + (long long)(bid - L.first) * F::NC);
-  for (int i = threadIdx.x; i < F::NC / VEC; i += blockDim.x) {
-    const int c = i * VEC;
-    const int x = c % n, y = (c / n) % n, z = D == 3 ? c / (n * n) : 0;
-    out[i] = *reinterpret_cast<const VT *>(tp + F::idx(x, y, z));
+  T *out = V.phi + out_poff + (long long)(bid - L.first) * F::NC;
+  for (int q = threadIdx.x; q < F::NC; q += blockDim.x) {  // the colour-split run in order
+    int x, y, z;
+    cs_xyz(q, n, F::NC, D, &x, &y, &z);
+    out[q] = tp[F::idx(x, y, z)];
   }
 }
 

@@ -15,7 +15,7 @@
 #include "gmg_internal.h"
 #include "coarse_cycle.cuh"
 #include "efield.cuh"
-#include "slot_groups.cuh"
+#include "csweep.cuh"
 #include "fused_sweeps.cuh"
 #include "kernels.cuh"
 
@@ -79,26 +79,26 @@ __global__ void __launch_bounds__(1024) k_reduce_partials(const double *partials
 __global__ void k_leaf_rhs(const int *__restrict__ leaf_ids, const long long *__restrict__ cbase,
                            const long long *__restrict__ bt_base, const double *__restrict__ bterm,
                            const double *__restrict__ g, double *__restrict__ b, int nlb, int ncell, long long rs,
-                           int r0, int nr) {
+                           int r0, int nr, int n, int D) {
   const long long nleaf = (long long)nlb * ncell;
   for (int lb = blockIdx.x; lb < nlb; lb += gridDim.x) {
     const int id = leaf_ids[lb];
     const long long base = cbase[id], bb = bt_base[id];
     for (int r = 0; r < nr; r++)
       for (int c = threadIdx.x; c < ncell; c += blockDim.x)
-        b[(r0 + r) * rs + base + c] = g[r * nleaf + (long long)lb * ncell + c] - (bb >= 0 ? bterm[bb + c] : 0.0);
+        b[(r0 + r) * rs + base + cs_pos(c, n, ncell, D)] = g[r * nleaf + (long long)lb * ncell + c] - (bb >= 0 ? bterm[bb + c] : 0.0);
   }
 }
 
 // leaf gather (dir 0: field -> io) / scatter (dir 1: io -> field)
 __global__ void k_leaf_copy(const int *__restrict__ leaf_ids, const long long *__restrict__ cbase, double *field,
-                            double *io, int nlb, int ncell, long long rs, int r0, int nr, int dir) {
+                            double *io, int nlb, int ncell, long long rs, int r0, int nr, int dir, int n, int D) {
   const long long nleaf = (long long)nlb * ncell;
   for (int lb = blockIdx.x; lb < nlb; lb += gridDim.x) {
     const long long base = cbase[leaf_ids[lb]];
     for (int r = 0; r < nr; r++)
       for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
-        const long long f = (r0 + r) * rs + base + c, k = r * nleaf + (long long)lb * ncell + c;
+        const long long f = (r0 + r) * rs + base + cs_pos(c, n, ncell, D), k = r * nleaf + (long long)lb * ncell + c;
         if (dir == 0)
           io[k] = field[f];
         else
@@ -319,9 +319,10 @@ void set_smem_limits_nt() {
   kernel_attrs(k_resid_restrict<T, D, NT>, true);
   kernel_attrs(k_fas<T, D, NT>, true);
   kernel_attrs(k_prolong<T, D, NT, 64>, true);
-  if constexpr (NT == 8 || NT == 16) {
-    kernel_attrs(k_smooth_sg<T, D, NT, 2>, true);
-    kernel_attrs(k_smooth_sg<T, D, NT, 4>, true);
+  if constexpr (NT != 0) {
+    kernel_attrs(k_smooth_cs<T, D, NT, 1>, true);
+    kernel_attrs(k_smooth_cs<T, D, NT, 2>, true);
+    kernel_attrs(k_smooth_cs<T, D, NT, 4>, true);
   }
   kernel_attrs(k_prolong<T, D, NT, 128>, true);
   kernel_attrs(k_prolong<T, D, NT, 256>, true);
@@ -368,23 +369,25 @@ void set_all_smem_limits() {
   done = true;
 }
 
-// Half-sweep of a level: one CTA per (block, slot), or per (block, group of
-// slots_per_cta slots) when the tree has several slots and the group's
-// tiles fit in shared memory.
+// Half-sweep of a level on the colour-split layout (csweep.cuh): one CTA
+// per (block, slot), or per (block, group of slots_per_cta slots) when the
+// tree has several slots and the group's tiles fit in shared memory; blocks
+// of a side without a compiled kernel take the tile-based smooth_block.
 template <typename T, int D, int NT>
 void launch_smooth(const gmg_tree *t, const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int c, int threads,
                    size_t sm, cudaStream_t s) {
-  const int sg = t->slots_per_cta;
-  if constexpr (NT == 8 || NT == 16) {
-    if (sg > 1 && t->nrhs > 1 && sg_smem_bytes<T>(D, NT, sg) <= 200 * 1024) {
-      const int grid = L.count * ((t->nrhs + sg - 1) / sg);
-      const size_t sms = sg_smem_bytes<T>(D, NT, sg);
-      if (sg == 2)
-        klaunch(t, grid, threads, sms, s, k_smooth_sg<T, D, NT, 2>, V, L, Lp, c);
-      else
-        klaunch(t, grid, threads, sms, s, k_smooth_sg<T, D, NT, 4>, V, L, Lp, c);
-      return;
-    }
+  if constexpr (NT != 0) {
+    int sg = t->nrhs > 1 ? t->slots_per_cta : 1;
+    while (sg > 1 && cs_smem_bytes<T, D, NT>(sg) > 200 * 1024) sg /= 2;
+    const int grid = L.count * ((t->nrhs + sg - 1) / sg);
+    const size_t sms = cs_smem_bytes<T, D, NT>(sg);
+    if (sg == 4)
+      klaunch(t, grid, threads, sms, s, k_smooth_cs<T, D, NT, 4>, V, L, Lp, c);
+    else if (sg == 2)
+      klaunch(t, grid, threads, sms, s, k_smooth_cs<T, D, NT, 2>, V, L, Lp, c);
+    else
+      klaunch(t, grid, threads, sms, s, k_smooth_cs<T, D, NT, 1>, V, L, Lp, c);
+    return;
   }
   klaunch(t, L.count * t->nrhs, threads, sm, s, k_smooth<T, D, NT>, V, L, Lp, c);
 }
@@ -1164,7 +1167,7 @@ int gmg_transfer_solution(const gmg_tree *old, gmg_tree *t, void *stream) {
         for (int c = 0; c < L.ncell; c++) {
           const int x = c % L.n, y = (c / L.n) % L.n, z = D == 3 ? c / (L.n * L.n) : 0;
           const int px = B.pofs[0] + x / 2, py = B.pofs[1] + y / 2, pz = D == 3 ? B.pofs[2] + z / 2 : 0;
-          dst[r * nn + nb0 + c] = dst[r * nn + pb + px + P.n * (py + P.n * pz)];
+          dst[r * nn + nb0 + cs_pos_xyz(x, y, z, L.n, L.ncell)] = dst[r * nn + pb + cs_pos_xyz(px, py, pz, P.n, P.ncell)];
         }
       }
     }
@@ -1436,7 +1439,7 @@ int gmg_set_rhs_slots(gmg_tree *t, int slot0, int nslots, const double *g, int w
     return set_error("where must be GMG_HOST or GMG_DEVICE"), GMG_ERR_INVALID_ARG;
   }
   k_leaf_rhs<<<leaf_grid(t), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_bt_base, t->d_bterm, gd, t->d_b,
-                                          n_leaf_blocks(t), t->leaf_ncell(), t->total_cells, slot0, nslots);
+                                          n_leaf_blocks(t), t->leaf_ncell(), t->total_cells, slot0, nslots, t->N, t->D);
   CUDA_TRY(cudaMemsetAsync(t->d_phi + (size_t)slot0 * t->total_cells, 0,
                            (size_t)nslots * t->total_cells * sizeof(double), s));
   CUDA_TRY(cudaGetLastError());
@@ -1463,7 +1466,7 @@ int gmg_set_solution(gmg_tree *t, const double *phi, int where, void *stream) {
     }
   }
   k_leaf_copy<<<leaf_grid(t), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, src, n_leaf_blocks(t), t->leaf_ncell(),
-                                           t->total_cells, 0, t->nrhs, 1);
+                                           t->total_cells, 0, t->nrhs, 1, t->N, t->D);
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemsetAsync(t->d_active, 1, (size_t)t->units() * sizeof(int), s));
   return restrict_all_phi64_any(t, s);
@@ -1478,20 +1481,20 @@ int gmg_get_solution_slots(gmg_tree *t, int slot0, int nslots, double *phi, int 
   const int ncell = t->leaf_ncell();
   if (where == GMG_DEVICE) {
     k_leaf_copy<<<leaf_grid(t), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, phi, n_leaf_blocks(t), ncell,
-                                             t->total_cells, slot0, nslots, 0);
+                                             t->total_cells, slot0, nslots, 0, t->N, t->D);
     CUDA_TRY(cudaGetLastError());
     return GMG_OK;
   }
   if (void *m = mapped_host(phi)) {  // the gather kernel writes the host array itself
     k_leaf_copy<<<leaf_grid(t), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, static_cast<double *>(m),
-                                             n_leaf_blocks(t), ncell, t->total_cells, slot0, nslots, 0);
+                                             n_leaf_blocks(t), ncell, t->total_cells, slot0, nslots, 0, t->N, t->D);
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaStreamSynchronize(s));
     return GMG_OK;
   }
   // the FP64 'old' field is dead between V-cycles: stage the gather there
   k_leaf_copy<<<leaf_grid(t), 256, 0, s>>>(t->d_leaf, t->d_cbase, t->d_phi, t->d_old, n_leaf_blocks(t), ncell,
-                                           t->total_cells, slot0, nslots, 0);
+                                           t->total_cells, slot0, nslots, 0, t->N, t->D);
   CUDA_TRY(cudaMemcpyAsync(phi, t->d_old, (size_t)nslots * n * sizeof(double), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   return GMG_OK;
@@ -1508,11 +1511,16 @@ int gmg_get_level(gmg_tree *t, int level, int which, double *out, void *stream) 
   cudaStream_t s = as_stream(stream);
   const LevelInfo &L = t->lev(level);
   const size_t cells = (size_t)L.count * L.ncell;
+  std::vector<double> run(cells);
   for (int r = 0; r < t->nrhs; r++) {
     const double *src = (which == 0 ? t->d_phi : t->d_b) + (size_t)r * t->total_cells + L.off;
-    CUDA_TRY(cudaMemcpyAsync(out + r * cells, src, cells * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(run.data(), src, cells * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    // blocks in order, each from the colour-split layout to natural cell order
+    for (size_t k = 0; k < (size_t)L.count; k++)
+      for (int c = 0; c < L.ncell; c++)
+        out[r * cells + k * L.ncell + c] = run[k * L.ncell + cs_pos(c, L.n, L.ncell, t->D)];
   }
-  CUDA_TRY(cudaStreamSynchronize(s));
   return GMG_OK;
 }
 

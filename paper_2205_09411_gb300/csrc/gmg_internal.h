@@ -86,6 +86,32 @@ struct GmgView {
   const int *active;     // [nrhs * ntree] 0 = unit frozen (converged or empty): its CTAs return at once
 };
 
+// Layout of a block inside a level field (phi, b, old; every level, both
+// precisions): the block's ncell cells form one run in which the cells of
+// colour 0 ((x + y + z) even, red) come first and those of colour 1 (black)
+// after them, each colour in the natural order x fastest.  A half-sweep of
+// one colour then reads the other colour's contiguous half and writes its
+// own, in whole sectors.  Cell c = x + n (y + n z) of a block of side n
+// (even, or n = 1) sits at cs_pos(c) = colour * ncell / 2 + c / 2: the two
+// cells x = 2i and 2i + 1 of a row share c / 2 and differ in colour.
+__host__ __device__ __forceinline__ int cs_pos_xyz(int x, int y, int z, int n, int ncell) {
+  return ((x + y + z) & 1) * (ncell >> 1) + ((x + n * (y + n * z)) >> 1);
+}
+__host__ __device__ __forceinline__ int cs_pos(int c, int n, int ncell, int D) {
+  const int x = c % n, y = (c / n) % n, z = D == 3 ? c / (n * n) : 0;
+  return cs_pos_xyz(x, y, z, n, ncell);
+}
+// the inverse: natural coordinates of position p of the run
+__host__ __device__ __forceinline__ void cs_xyz(int p, int n, int ncell, int D, int *x, int *y, int *z) {
+  const int half = ncell >> 1;
+  const int colour = (half > 0 && p >= half) ? 1 : 0;
+  const int c2 = 2 * (p - colour * half);  // natural index of the row pair's even cell
+  const int x0 = c2 % n;
+  *y = (c2 / n) % n;
+  *z = D == 3 ? c2 / (n * n) : 0;
+  *x = x0 + ((colour + *y + *z) & 1);
+}
+
 template <typename T>
 __host__ __device__ __forceinline__ int unit_of(const GmgView<T> &V, int r, int bid) {
   return V.ntree > 1 ? r * V.ntree + V.tree_of[bid] : r;

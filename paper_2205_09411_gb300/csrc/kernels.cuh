@@ -29,6 +29,16 @@ __device__ __forceinline__ void pdl_start() {
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
 }
 
+// Position of cell j of a run of whole blocks of level L (the coarsest
+// level's unknowns of one root: blocks one after the other, natural cell
+// order inside each, as the coarse inverse numbers them) in the fields'
+// colour-split layout.
+__host__ __device__ __forceinline__ int coarse_pos(int j, const LvArgs &L) {
+  const int jb = j / L.ncell, jc = j - jb * L.ncell;
+  const int D = L.ncell == L.n * L.n ? 2 : 3;
+  return jb * L.ncell + cs_pos(jc, L.n, L.ncell, D);
+}
+
 __device__ __forceinline__ int nbr_slot(int ox, int oy, int oz) { return (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1); }
 
 // Local coordinate p (each component in [-1, n]) of block `bid` on level L:
@@ -67,7 +77,7 @@ __device__ __forceinline__ bool resolve(const int *__restrict__ nbr, const int *
     id = nbr[(size_t)bid * kNbr + nbr_slot(o[0], o[1], o[2])];
     if (id < 0) return false;
   }
-  *idx = L.off + (long long)(id - L.first) * L.ncell + p[0] + n * (p[1] + (D == 3 ? n * p[2] : 0));
+  *idx = L.off + (long long)(id - L.first) * L.ncell + cs_pos_xyz(p[0], p[1], D == 3 ? p[2] : 0, n, L.ncell);
   *sign = sg;
   return true;
 }
@@ -104,7 +114,7 @@ __device__ __forceinline__ bool resolve_s(const int *s_nb, int bid, const LvArgs
   }
   const int id = (o[0] | o[1] | o[2]) ? s_nb[nbr_slot(o[0], o[1], o[2])] : bid;
   if (id < 0) return false;
-  *idx = L.off + (long long)(id - L.first) * L.ncell + p[0] + n * (p[1] + (D == 3 ? n * p[2] : 0));
+  *idx = L.off + (long long)(id - L.first) * L.ncell + cs_pos_xyz(p[0], p[1], D == 3 ? p[2] : 0, n, L.ncell);
   *sign = sg;
   return true;
 }
@@ -122,7 +132,7 @@ __device__ __noinline__ T refine_ghost(const T *phi, const int *nbr, const int *
   const int n = L.n;
   int q[3] = {p[0], p[1], p[2]};
   q[a] = p[a] < 0 ? 0 : n - 1;
-  const T f = own[q[0] + n * (q[1] + (D == 3 ? n * q[2] : 0))];
+  const T f = own[cs_pos_xyz(q[0], q[1], D == 3 ? q[2] : 0, n, L.ncell)];
   const long long dp = Lp.poff - Lp.off;  // phi of the coarse level may live in the second buffer
   const int P = parent[bid], po = pofs_t[bid];
   const int pofs[3] = {po & 1023, (po >> 10) & 1023, (po >> 20) & 1023};
@@ -221,9 +231,11 @@ __device__ __forceinline__ unsigned char *level_flags(T *sbv, int ncell) {
 }
 
 // Stage phi of block `bid` with its face ghosts into the tile and, if
-// sbv != nullptr, the block's b into the dense array sbv[n^D].  The cells and
-// b are copied with 16-byte cp.async while the face neighbours' ids are read;
-// the neighbours' faces follow as element cp.async; wall ghosts (reflection
+// sbv != nullptr, the block's b into the dense array sbv[n^D], in the
+// fields' colour-split order (sbv[cs_pos(c)] is cell c's).  The cells come
+// as 16-byte vectors of one colour scattered into the tile, b as 16-byte
+// cp.async, while the face neighbours' ids are read; the neighbours' faces
+// follow as element cp.async; wall ghosts (reflection
 // of the adjacent cell, homogeneous sign) and refinement-boundary ghosts
 // (reading G) are filled once the copies have landed.  Ends with a barrier.
 // FAS: the tile of a covered block for the FAS kernel, whose phi (and that
@@ -252,18 +264,27 @@ __device__ __forceinline__ void load_tile(const GmgView<T> &V, const LvArgs &L, 
   const long long pbase = L.poff + (long long)(bid - L.first) * ncell; // phi
   const T *own = FAS ? V.old + base : V.phi + pbase;  // the block's own cells
   constexpr int VEC = 16 / sizeof(T);
-  if (n % VEC == 0) {  // 16-byte chunks never cross a row of the tile
+  // the block's run in the colour-split layout, read in order: 16-byte
+  // vectors of one colour (cells x0, x0 + 2, ... of one row) scattered to
+  // the tile; b kept in the run's order (the dense b is indexed by cs_pos)
+  if (n % (2 * VEC) == 0) {
+    using VT = typename Vec16<T>::type;
+    const VT *ownv = reinterpret_cast<const VT *>(own);
     for (int i = threadIdx.x; i < ncell / VEC; i += blockDim.x) {
-      const int c = i * VEC;
-      const int x = c % n, y = (c / n) % n, z = D == 3 ? c / (n * n) : 0;
-      cp_async16(tile + G.idx(x, y, z), own + c);
-      if (sbv) cp_async16(sbv + c, V.b + base + c);
+      if (sbv) cp_async16(sbv + i * VEC, V.b + base + i * VEC);
+      const VT v = __ldcg(ownv + i);
+      int x, y, z;
+      cs_xyz(i * VEC, n, ncell, D, &x, &y, &z);
+      const T *e = reinterpret_cast<const T *>(&v);
+#pragma unroll
+      for (int q = 0; q < VEC; q++) tile[G.idx(x + 2 * q, y, z)] = e[q];
     }
-  } else {  // blocks narrower than one vector (coarse sub-levels)
-    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
-      const int x = c % n, y = (c / n) % n, z = D == 3 ? c / (n * n) : 0;
-      cp_async_elem(tile + G.idx(x, y, z), own + c);
-      if (sbv) cp_async_elem(sbv + c, V.b + base + c);
+  } else {  // rows narrower than two vectors (coarse sub-levels)
+    for (int q = threadIdx.x; q < ncell; q += blockDim.x) {
+      int x, y, z;
+      cs_xyz(q, n, ncell, D, &x, &y, &z);
+      cp_async_elem(tile + G.idx(x, y, z), own + q);
+      if (sbv) cp_async_elem(sbv + q, V.b + base + q);
     }
   }
   if (sflag && sb >= 0) {  // which cells of a cut block have a non-regular stencil
@@ -280,8 +301,10 @@ __device__ __forceinline__ void load_tile(const GmgView<T> &V, const LvArgs &L, 
   const int nf = D == 3 ? n * n : n;
   // face f = 2 axis + side: ghost cell (gx,gy,gz) from the cell (qx,qy,qz) of
   // the same-level neighbour.  x faces cell by cell; the y and z faces are
-  // rows along x, copied in 16-byte chunks when a row is whole chunks.
-  constexpr bool kRows = NT != 0 && NT % VEC == 0;
+  // rows along x whose two colours are each a contiguous run of n/2 cells
+  // in the neighbour's block: 16-byte vectors of one colour scattered to
+  // every other cell of the tile row, when a run is whole vectors.
+  constexpr bool kRows = NT != 0 && NT % (2 * VEC) == 0;
   const int nfx = kRows ? 2 * nf : 2 * D * nf;
   for (int i = threadIdx.x; i < nfx; i += blockDim.x) {
     const int f = i / nf, j = i - f * nf;
@@ -293,15 +316,17 @@ __device__ __forceinline__ void load_tile(const GmgView<T> &V, const LvArgs &L, 
     const int gx = a == 0 ? gn : u, gy = a == 1 ? gn : (a == 0 ? u : v), gz = a == 2 ? gn : v;
     const int qx = a == 0 ? sn : u, qy = a == 1 ? sn : (a == 0 ? u : v), qz = a == 2 ? sn : v;
     const T *src = (FAS && (fl & face_covered_bit(f))) ? V.old + L.off : V.phi + L.poff;
-    cp_async_elem(tile + G.idx(gx, gy, gz),
-                  src + (long long)(id - L.first) * ncell + qx + n * (qy + (D == 3 ? n * qz : 0)));
+    cp_async_elem(tile + G.idx(gx, gy, gz), src + (long long)(id - L.first) * ncell + cs_pos_xyz(qx, qy, qz, n, ncell));
   }
   if (kRows) {
-    constexpr int cpr = kRows ? NT / VEC : 1;  // chunks per row
+    using VT = typename Vec16<T>::type;
+    constexpr int hn = kRows ? NT / 2 : 2;      // a row's cells of one colour
+    constexpr int vpr = kRows ? hn / VEC : 1;  // vectors per colour run
     const int rows = D == 3 ? n : 1;           // rows per face
-    for (int i = threadIdx.x; i < (2 * D - 2) * rows * cpr; i += blockDim.x) {
-      const int f = 2 + i / (rows * cpr), rem = i - (f - 2) * rows * cpr;
-      const int row = rem / cpr, x0 = (rem - row * cpr) * VEC;
+    for (int i = threadIdx.x; i < (2 * D - 2) * rows * 2 * vpr; i += blockDim.x) {
+      const int f = 2 + i / (rows * 2 * vpr), rem = i - (f - 2) * rows * 2 * vpr;
+      const int row = rem / (2 * vpr), cv = rem - row * 2 * vpr;
+      const int col = cv / vpr, k0 = (cv - col * vpr) * VEC;  // colour of the run, first cell in it
       const int a = f >> 1, side = f & 1;
       const int id = s_nb[f];
       if ((fl & wall_bit(a, side)) || id < 0) continue;
@@ -309,7 +334,12 @@ __device__ __forceinline__ void load_tile(const GmgView<T> &V, const LvArgs &L, 
       const int gy = a == 1 ? gn : row, gz = a == 2 ? gn : (D == 3 ? row : 0);
       const int qy = a == 1 ? sn : row, qz = a == 2 ? sn : (D == 3 ? row : 0);
       const T *src = (FAS && (fl & face_covered_bit(f))) ? V.old + L.off : V.phi + L.poff;
-      cp_async16(tile + G.idx(x0, gy, gz), src + (long long)(id - L.first) * ncell + x0 + n * (qy + (D == 3 ? n * qz : 0)));
+      const VT w = __ldcg(reinterpret_cast<const VT *>(src + (long long)(id - L.first) * ncell + col * (ncell / 2) +
+                                                        hn * (qy + (D == 3 ? n * qz : 0)) + k0));
+      const int x0 = 2 * k0 + ((qy + qz + col) & 1);  // x of the run's first cell (same x in the ghost row)
+      const T *e = reinterpret_cast<const T *>(&w);
+#pragma unroll
+      for (int q = 0; q < VEC; q++) tile[G.idx(x0 + 2 * q, gy, gz)] = e[q];
     }
   }
   cp_async_wait_all();
@@ -477,13 +507,15 @@ __device__ void smooth_block(const GmgView<T> &V, const LvArgs &L, const LvArgs 
     const int x = 2 * (j % hn) + ((y + z + color) & 1);
     const int c = x + n * (y + n * z);
     if (sb >= 0 && sfl[c]) continue;  // a listed cell
-    V.phi[pbase + c] = (nb_sum<T, D>(tile, G.idx(x, y, z), G.sy, G.sz) - h2 * sbv[c]) * inv2d;
+    const int q = cs_pos_xyz(x, y, z, n, NCELL);
+    V.phi[pbase + q] = (nb_sum<T, D>(tile, G.idx(x, y, z), G.sy, G.sz) - h2 * sbv[q]) * inv2d;
   }
   auto upd = [&](const CutCell<T, D> &u) {
     int x, y, z;
     cell_xyz<D>(u.c, n, &x, &y, &z);
     const int t = G.idx(x, y, z);
-    V.phi[pbase + u.c] = (sbv[u.c] - offdiag_of<T, D>(u.a, tile, t, G.sy, G.sz)) / u.a[0];
+    const int q = cs_pos_xyz(x, y, z, n, NCELL);
+    V.phi[pbase + q] = (sbv[q] - offdiag_of<T, D>(u.a, tile, t, G.sy, G.sz)) / u.a[0];
   };
   if ((int)threadIdx.x < m) upd(q);
   for (int i = threadIdx.x + blockDim.x; i < m; i += blockDim.x) {  // lists longer than the CTA
@@ -517,7 +549,8 @@ __device__ __forceinline__ void cut_residuals(const GmgView<T> &V, const TileGeo
     int x, y, z;
     cell_xyz<D>(u.c, n, &x, &y, &z);
     const int t = G.idx(x, y, z);
-    sbv[u.c] = sbv[u.c] - (u.a[0] * tile[t] + offdiag_of<T, D>(u.a, tile, t, G.sy, G.sz));
+    const int q = cs_pos_xyz(x, y, z, n, D == 3 ? n * n * n : n * n);
+    sbv[q] = sbv[q] - (u.a[0] * tile[t] + offdiag_of<T, D>(u.a, tile, t, G.sy, G.sz));
   };
   const int i = threadIdx.x, bd = blockDim.x;
   if (i < m) res(q);
@@ -571,10 +604,11 @@ __device__ void resid_restrict_block(const GmgView<T> &V, const LvArgs &L, const
           const int c = x + n * (y + n * z);
           const int t = G.idx(x, y, z);
           sp = sp + tile[t];
-          sr = sr + ((sb >= 0 && sfl[c]) ? sbv[c]  // a listed cell: its residual
-                                         : resid_cell<T, D>(nullptr, -1, tile, t, G.sy, G.sz, NCELL, c, inv_h2, sbv[c]));
+          const int p = cs_pos_xyz(x, y, z, n, NCELL);
+          sr = sr + ((sb >= 0 && sfl[c]) ? sbv[p]  // a listed cell: its residual
+                                         : resid_cell<T, D>(nullptr, -1, tile, t, G.sy, G.sz, NCELL, c, inv_h2, sbv[p]));
         }
-    const long long pc = pbase + (pofs[0] + qx) + pn * ((pofs[1] + qy) + (D == 3 ? pn * (pofs[2] + qz) : 0));
+    const long long pc = pbase + cs_pos_xyz(pofs[0] + qx, pofs[1] + qy, D == 3 ? pofs[2] + qz : 0, pn, Lp.ncell);
     V.old[pc] = sp * w;
     V.b[pc] = sr * w;
   }
@@ -622,7 +656,8 @@ __device__ void fas_block(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
       int x, y, z;
       cell_xyz<D>(u.c, n, &x, &y, &z);
       const int t = G.idx(x, y, z);
-      sbv[u.c] = (u.a[0] * tile[t] + offdiag_of<T, D>(u.a, tile, t, G.sy, G.sz)) + sbv[u.c];
+      const int q = cs_pos_xyz(x, y, z, n, NCELL);
+      sbv[q] = (u.a[0] * tile[t] + offdiag_of<T, D>(u.a, tile, t, G.sy, G.sz)) + sbv[q];
     };
     const int i = threadIdx.x, bd = blockDim.x;
     if (i < m) fas(q);
@@ -640,8 +675,9 @@ __device__ void fas_block(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp
     cell_xyz<D>(c, n, &x, &y, &z);
     const int t = G.idx(x, y, z);
     const T ph = tile[t];
-    V.b[base + c] = (sb >= 0 && sfl[c]) ? sbv[c] : inv_h2 * (nb_sum<T, D>(tile, t, G.sy, G.sz) - T(2 * D) * ph) + sbv[c];
-    V.phi[pbase + c] = ph;  // old already holds ph
+    const int q = cs_pos_xyz(x, y, z, n, NCELL);
+    V.b[base + q] = (sb >= 0 && sfl[c]) ? sbv[q] : inv_h2 * (nb_sum<T, D>(tile, t, G.sy, G.sz) - T(2 * D) * ph) + sbv[q];
+    V.phi[pbase + q] = ph;  // old already holds ph
   }
 }
 
@@ -672,10 +708,10 @@ __global__ void __launch_bounds__(kThreads) k_coarse(GmgView<T> V, LvArgs Lc, co
   const double *a = Ainv + ((size_t)k * ncr + i) * ncr;
   const T *b = V.b + r * V.rs_f + Lc.off + (size_t)k * ncr;
   double s = 0.0;
-  for (int j = lane; j < ncr; j += 32) s += a[j] * (double)b[j];
+  for (int j = lane; j < ncr; j += 32) s += a[j] * (double)b[coarse_pos(j, Lc)];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) V.phi[r * V.rs_phi + Lc.poff + row] = T(s);
+  if (lane == 0) V.phi[r * V.rs_phi + Lc.poff + (size_t)k * ncr + coarse_pos(i, Lc)] = T(s);
 }
 
 // (Bi/tri)linear prolongation of the coarse correction phi - old
@@ -695,13 +731,21 @@ __device__ void prolong_block(const GmgView<T> &V, const LvArgs &L, const LvArgs
   using VT = typename Vec16<T>::type;
   const long long base = L.poff + (long long)(bid - L.first) * NCELL;
   VT *__restrict__ fine = reinterpret_cast<VT *>(V.phi + base);
-  constexpr int IV = NT ? ((D == 3 ? NT * NT * NT : NT * NT) / VEC + PT - 1) / PT : 1;
-  VT rv[IV];
-  if (NT) {
+  // vectors in pairs: vector i of the red half and vector i of the black
+  // half hold the two colours of the same 2 VEC consecutive cells of a row
+  // (when a row's colour half is whole vectors)
+  constexpr bool kPairs = NT != 0 && NT % (2 * VEC) == 0;
+  constexpr int HV = NT ? (D == 3 ? NT * NT * NT : NT * NT) / 2 / VEC : 1;  // vectors of one colour
+  constexpr int IV = kPairs ? (HV + PT - 1) / PT : 1;
+  VT rv[IV], rw[IV];
+  if (kPairs) {
 #pragma unroll
     for (int k = 0; k < IV; k++) {
       const int i = threadIdx.x + k * blockDim.x;
-      if (i < NCELL / VEC) rv[k] = fine[i];
+      if (i < HV) {
+        rv[k] = fine[i];
+        rw[k] = fine[HV + i];
+      }
     }
   }
   __syncthreads();
@@ -735,25 +779,36 @@ __device__ void prolong_block(const GmgView<T> &V, const LvArgs &L, const LvArgs
         }
     return v;
   };
-  if (NT) {
+  if (kPairs) {
 #pragma unroll
     for (int k = 0; k < IV; k++) {
       const int i = threadIdx.x + k * blockDim.x;
-      if (i < NCELL / VEC) {
-        T *e = reinterpret_cast<T *>(&rv[k]);
-        const int c = i * VEC;
+      if (i < HV) {
+        T *e0 = reinterpret_cast<T *>(&rv[k]);  // red cells x0 + 2q (x0 = first red x)
+        T *e1 = reinterpret_cast<T *>(&rw[k]);  // black cells x0 + 1 - 2 (x0 & 1) + 2q
         int x, y, z;
-        cell_xyz<D>(c, n, &x, &y, &z);
+        cs_xyz(i * VEC, n, NCELL, D, &x, &y, &z);
+        const int xe = x & ~1;                  // the pair's even cell
 #pragma unroll
-        for (int q = 0; q < VEC; q++) e[q] += interp(x + q, y, z);
+        for (int q = 0; q < VEC; q++) {         // cells xe + 2q and xe + 2q + 1, in x order
+          const T a = interp(xe + 2 * q, y, z), b = interp(xe + 2 * q + 1, y, z);
+          if (x & 1) {
+            e1[q] += a;
+            e0[q] += b;
+          } else {
+            e0[q] += a;
+            e1[q] += b;
+          }
+        }
         fine[i] = rv[k];
+        fine[HV + i] = rw[k];
       }
     }
   } else {
-    for (int c = threadIdx.x; c < NCELL; c += blockDim.x) {
+    for (int q = threadIdx.x; q < NCELL; q += blockDim.x) {
       int x, y, z;
-      cell_xyz<D>(c, n, &x, &y, &z);
-      V.phi[base + c] += interp(x, y, z);
+      cs_xyz(q, n, NCELL, D, &x, &y, &z);
+      V.phi[base + q] += interp(x, y, z);
     }
   }
 }
@@ -788,8 +843,8 @@ __global__ void __launch_bounds__(kThreads) k_restrict_phi(GmgView<T> V0, LvArgs
     T sp = T(0);
     for (int dz = 0; dz < (D == 3 ? 2 : 1); dz++)
       for (int dy = 0; dy < 2; dy++)
-        for (int dx = 0; dx < 2; dx++) sp = sp + V.phi[base + (2 * qx + dx) + n * ((2 * qy + dy) + n * (2 * qz + dz))];
-    V.phi[pbase + (pofs[0] + qx) + pn * ((pofs[1] + qy) + (D == 3 ? pn * (pofs[2] + qz) : 0))] = sp * w;
+        for (int dx = 0; dx < 2; dx++) sp = sp + V.phi[base + cs_pos_xyz(2 * qx + dx, 2 * qy + dy, 2 * qz + dz, n, NCELL)];
+    V.phi[pbase + cs_pos_xyz(pofs[0] + qx, pofs[1] + qy, D == 3 ? pofs[2] + qz : 0, pn, Lp.ncell)] = sp * w;
   }
 }
 
@@ -859,7 +914,7 @@ __global__ void __launch_bounds__(kResThreads, 2) k_resnorm(GmgView<T> V0, LvArg
   // rounded residual are accumulated in FP32 per thread, then in FP64
   float s2f = 0.f, mxf = 0.f, b2f = 0.f;
   auto acc = [&](int c, float r, T bb) {
-    if (rout) rout[base + c] = r;
+    if (rout) rout[base + cs_pos(c, n, NCELL, D)] = r;
     s2f = fmaf(r, r, s2f);
     mxf = fmaxf(mxf, fabsf(r));
     const float bf = (float)bb;
@@ -870,7 +925,7 @@ __global__ void __launch_bounds__(kResThreads, 2) k_resnorm(GmgView<T> V0, LvArg
       int x, y, z;
       cell_xyz<D>(u.c, n, &x, &y, &z);
       const int t = G.idx(x, y, z);
-      const T bb = sbv[u.c];
+      const T bb = sbv[cs_pos_xyz(x, y, z, n, NCELL)];
       acc(u.c, (float)(bb - (u.a[0] * tile[t] + offdiag_of<T, D>(u.a, tile, t, G.sy, G.sz))), bb);
     };
     const int i = threadIdx.x, bd = blockDim.x;
@@ -885,7 +940,7 @@ __global__ void __launch_bounds__(kResThreads, 2) k_resnorm(GmgView<T> V0, LvArg
     if (sb >= 0 && sfl[c]) continue;
     int x, y, z;
     cell_xyz<D>(c, n, &x, &y, &z);
-    const T bb = sbv[c];
+    const T bb = sbv[cs_pos_xyz(x, y, z, n, NCELL)];
     acc(c, (float)resid_cell<T, D>(nullptr, -1, tile, G.idx(x, y, z), G.sy, G.sz, NCELL, c, inv_h2, bb), bb);
   }
   block_reduce3((double)s2f, (double)mxf, (double)b2f, partials);
