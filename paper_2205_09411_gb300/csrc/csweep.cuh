@@ -75,11 +75,14 @@ __device__ __forceinline__ void cs_stage(const GmgView<T> &V, const LvArgs &L, i
     }
   }
   // y and z faces toward same-level neighbours: the neighbour's boundary
-  // row of the other colour, one contiguous run of HN cells per row
+  // row of the other colour, one contiguous run of HN cells per row (in
+  // 16-byte pieces when the run is whole vectors)
   constexpr int FR = D == 3 ? NT : 1;  // rows per face
-  for (int i = threadIdx.x; i < (2 * D - 2) * FR * G::HN; i += blockDim.x) {
-    const int f = 2 + i / (FR * G::HN), rem = i - (f - 2) * FR * G::HN;
-    const int u = rem / G::HN, k = rem - u * G::HN;  // u: the face's row, k: cell in it
+  constexpr int PW = kChunks ? VEC : 1;  // cells per piece
+  constexpr int PR = G::HN / PW;         // pieces per row
+  for (int i = threadIdx.x; i < (2 * D - 2) * FR * PR; i += blockDim.x) {
+    const int f = 2 + i / (FR * PR), rem = i - (f - 2) * FR * PR;
+    const int u = rem / PR, k = (rem - u * PR) * PW;  // u: the face's row, k: first cell of the piece
     const int a = f >> 1, side = f & 1;
     const int id = s_nb[f];
     if ((fl & wall_bit(a, side)) || id < 0) continue;
@@ -87,7 +90,11 @@ __device__ __forceinline__ void cs_stage(const GmgView<T> &V, const LvArgs &L, i
     const int yg = a == 1 ? (side ? NT : -1) : u, zg = a == 2 ? (side ? NT : -1) : u;
     const T *src = V.phi + rs_phi + L.poff + (long long)(id - L.first) * (2 * G::H) + (1 - c) * G::H +
                    G::HN * (ys + (D == 3 ? NT * zs : 0));
-    cp_async_elem(O + G::at(G::row(yg, D == 3 ? zg : 0), k), src + k);
+    T *dst = O + G::at(G::row(yg, D == 3 ? zg : 0), k);
+    if (kChunks)
+      cp_async16(dst, src + k);
+    else
+      cp_async_elem(dst, src + k);
   }
   // x faces: in a row whose other-colour parity is 1 the ghost x = -1 is
   // read (at k = -1), in the other rows the ghost x = NT (at k = HN)
