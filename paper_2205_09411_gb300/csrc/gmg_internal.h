@@ -315,7 +315,17 @@ struct LsfSpec;
 // mask[cell] for every cell in block order (bit 0 Eq. (boundary-mask), bit
 // 1 centre inside), the masked cells (index in that order, ascending) and
 // their 2D relative distances.  Bit for bit the host set-up's values.
+// With `terms`, also the stencils and right-hand-side terms of the cut
+// blocks (blocks with a distance below 1) for a constant boundary value
+// phib and constant wall values, dense per cut block in block order: the
+// host's block_terms bit for bit.
+struct DeviceTerms {
+  std::vector<int> cut_ids;          // cut blocks, ascending
+  std::vector<long long> cell_off;   // [ncut + 1] first cell of each in the arrays below
+  std::vector<double> dd, st, bt, pb;  // distances (2D), stencil (coefficient-major per block), terms, phi_b at roots (2D)
+};
 bool device_setup_available();
 int device_boundary_detection(const gmg_tree *T, const LsfSpec &spec, std::vector<uint8_t> &mask,
-                              std::vector<long long> &masked_cells, std::vector<double> &dist);
+                              std::vector<long long> &masked_cells, std::vector<double> &dist, DeviceTerms *terms,
+                              double phib);
 }  // namespace gmg

@@ -207,6 +207,95 @@ __global__ void __launch_bounds__(128) k_setup_dist(DevSetupArgs A, const long l
   }
 }
 
+// Blocks with a located root: cut[b] <- 1 when a masked cell of block b has
+// a distance below 1 (every writer stores the same value).
+__global__ void k_setup_cutflag(const int *blk_of, const double *dist, long long m, int D, unsigned char *cut) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m; e += (long long)gridDim.x * blockDim.x) {
+    bool any = false;
+    for (int k = 0; k < 2 * D; k++) any = any || dist[e * 2 * D + k] < 1.0;
+    if (any) cut[blk_of[e]] = 1;
+  }
+}
+
+struct DevTermsArgs {
+  int D, ncut;
+  double phib;                  // the constant boundary value
+  double wall_val[6];
+  int wall_dirichlet;           // bit w: wall w is Dirichlet
+  const int *cut_ids;           // [ncut] block ids, block order
+  const long long *cut_off;     // [ncut + 1] first cell of each cut block in the dense arrays
+  const long long *ent_first;   // [nb + 1] the block's entries in the masked-cell list
+  const long long *cells;       // masked cells (block-order cell index)
+  const double *dist;           // their distances
+};
+
+// One CTA per cut block: its distances made dense (1 where no root, the
+// masked cells' values scattered in), then per cell the coefficients of
+// Eq. (lpl-1d-lsf) with those toward a located root moved to the right-hand
+// side at the constant boundary value (Sec. 3.3, 3.6.2), and the Dirichlet
+// wall terms: the host's block_terms, in its order.
+__global__ void __launch_bounds__(256) k_setup_terms(DevSetupArgs A, DevTermsArgs B, double *dd, double *stc, double *bt,
+                                                     double *pb) {
+  const int D = A.D, S = 2 * D + 1;
+  for (int i = blockIdx.x; i < B.ncut; i += gridDim.x) {
+    const int b = B.cut_ids[i];
+    const int *bx = A.ix + 3 * (size_t)b;
+    const DevLevel L = A.levels[A.lev[b]];
+    const int n = L.n, nc = L.ncell;
+    const long long o = B.cut_off[i];
+    double *d = dd + o * 2 * D;
+    for (int k = threadIdx.x; k < nc * 2 * D; k += blockDim.x) d[k] = 1.0;
+    __syncthreads();
+    for (long long e = B.ent_first[b] + threadIdx.x; e < B.ent_first[b + 1]; e += blockDim.x) {
+      const int c = (int)(B.cells[e] - A.cofs[b]);
+      for (int k = 0; k < 2 * D; k++) d[(size_t)c * 2 * D + k] = B.dist[e * 2 * D + k];
+    }
+    __syncthreads();
+    const double h = L.h, inv_h2 = 1.0 / (h * h);
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+      const int p[3] = {c % n, (c / n) % n, D == 3 ? c / (n * n) : 0};
+      const double *dc = d + (size_t)c * 2 * D;
+      double diag = 0.0, bnd = 0.0, coef[6];
+      for (int k = 0; k < D; k++) {
+        const double dm = dc[2 * k], dp = dc[2 * k + 1];
+        double cm = 2.0 * inv_h2 / ((dp + dm) * dm);
+        double cp = 2.0 * inv_h2 / ((dp + dm) * dp);
+        diag = diag - (cm + cp);
+        double pm = 0.0, pp = 0.0;
+        if (dm < 1.0) {
+          pm = B.phib;
+          bnd = bnd + cm * pm;
+          cm = 0.0;
+        }
+        if (dp < 1.0) {
+          pp = B.phib;
+          bnd = bnd + cp * pp;
+          cp = 0.0;
+        }
+        pb[(o + c) * 2 * D + 2 * k] = pm;
+        pb[(o + c) * 2 * D + 2 * k + 1] = pp;
+        coef[2 * k] = cm;
+        coef[2 * k + 1] = cp;
+      }
+      stc[o * S + c] = diag;
+      for (int k = 0; k < 2 * D; k++) stc[o * S + (size_t)(1 + k) * nc + c] = coef[k];
+      double t = bnd;
+      for (int k = 0; k < D; k++)
+        for (int s = 0; s < 2; s++) {
+          int G[3];
+          for (int q = 0; q < 3; q++) G[q] = q < D ? bx[q] * n + p[q] : 0;
+          G[k] += s ? 1 : -1;
+          if (in_dom(L, D, G)) continue;
+          const int w = 2 * k + s;
+          if (!((B.wall_dirichlet >> w) & 1)) continue;
+          t = t + coef[2 * k + s] * (2.0 * B.wall_val[w]);
+        }
+      bt[o + c] = t;
+    }
+    __syncthreads();
+  }
+}
+
 // entry e's block: the block whose cell range holds cells[e]
 __global__ void k_setup_blk(const long long *cofs, int nb, const long long *cells, long long m, int *blk_of) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m; e += (long long)gridDim.x * blockDim.x) {
@@ -257,7 +346,8 @@ bool device_setup_available() {
 }
 
 int device_boundary_detection(const gmg_tree *T, const LsfSpec &spec, std::vector<uint8_t> &mask,
-                              std::vector<long long> &masked_cells, std::vector<double> &dist) {
+                              std::vector<long long> &masked_cells, std::vector<double> &dist, DeviceTerms *terms,
+                              double phib) {
 #define SETUP_TRY(expr)                                                                   \
   do {                                                                                    \
     const cudaError_t _e = (expr);                                                        \
@@ -341,6 +431,71 @@ int device_boundary_detection(const gmg_tree *T, const LsfSpec &spec, std::vecto
     k_setup_blk<<<g2, 128, 0, st>>>(d_cofs, nb, d_cells, m, d_blk);
     k_setup_dist<<<g2, 128, 0, st>>>(A, d_cells, m, d_blk, d_dist);
     SETUP_TRY(cudaGetLastError());
+  }
+  if (terms) {  // stencils and terms of the cut blocks (constant boundary and wall values)
+    unsigned char *d_cut;
+    SETUP_TRY(buf.alloc(&d_cut, (size_t)nb));
+    SETUP_TRY(cudaMemsetAsync(d_cut, 0, (size_t)nb, st));
+    if (m > 0) {
+      const int g2 = (int)std::min<long long>((m + 127) / 128, 152LL * 32);
+      k_setup_cutflag<<<g2, 128, 0, st>>>(d_blk, d_dist, m, D, d_cut);
+      SETUP_TRY(cudaGetLastError());
+    }
+    std::vector<unsigned char> cut(nb);
+    SETUP_TRY(cudaMemcpyAsync(cut.data(), d_cut, (size_t)nb, cudaMemcpyDeviceToHost, st));
+    SETUP_TRY(cudaStreamSynchronize(st));
+    terms->cut_ids.clear();
+    terms->cell_off.assign(1, 0);
+    for (int b = 0; b < nb; b++)
+      if (cut[b]) {
+        terms->cut_ids.push_back(b);
+        terms->cell_off.push_back(terms->cell_off.back() + (cofs[b + 1] - cofs[b]));
+      }
+    const int ncut = (int)terms->cut_ids.size();
+    const long long cc = terms->cell_off.back();
+    const int S = 2 * D + 1;
+    terms->dd.resize((size_t)cc * 2 * D);
+    terms->st.resize((size_t)cc * S);
+    terms->bt.resize((size_t)cc);
+    terms->pb.resize((size_t)cc * 2 * D);
+    if (ncut > 0) {
+      std::vector<long long> ent_first(nb + 1);
+      for (int b = 0; b < nb; b++) ent_first[b] = first[b];
+      ent_first[nb] = m;
+      int *d_ids;
+      long long *d_off, *d_ef;
+      double *d_dd, *d_st, *d_bt, *d_pb;
+      SETUP_TRY(buf.alloc(&d_ids, (size_t)ncut));
+      SETUP_TRY(buf.alloc(&d_off, (size_t)ncut + 1));
+      SETUP_TRY(buf.alloc(&d_ef, (size_t)nb + 1));
+      SETUP_TRY(buf.alloc(&d_dd, terms->dd.size()));
+      SETUP_TRY(buf.alloc(&d_st, terms->st.size()));
+      SETUP_TRY(buf.alloc(&d_bt, terms->bt.size()));
+      SETUP_TRY(buf.alloc(&d_pb, terms->pb.size()));
+      SETUP_TRY(cudaMemcpyAsync(d_ids, terms->cut_ids.data(), (size_t)ncut * sizeof(int), cudaMemcpyHostToDevice, st));
+      SETUP_TRY(cudaMemcpyAsync(d_off, terms->cell_off.data(), ((size_t)ncut + 1) * sizeof(long long),
+                                cudaMemcpyHostToDevice, st));
+      SETUP_TRY(cudaMemcpyAsync(d_ef, ent_first.data(), ((size_t)nb + 1) * sizeof(long long), cudaMemcpyHostToDevice, st));
+      DevTermsArgs B{};
+      B.D = D;
+      B.ncut = ncut;
+      B.phib = phib;
+      for (int w = 0; w < 6; w++) {
+        B.wall_val[w] = T->wall_val[w];
+        if (w < 2 * D && T->wall_type[w] == GMG_WALL_DIRICHLET) B.wall_dirichlet |= 1 << w;
+      }
+      B.cut_ids = d_ids;
+      B.cut_off = d_off;
+      B.ent_first = d_ef;
+      B.cells = d_cells;
+      B.dist = d_dist;
+      k_setup_terms<<<std::min(ncut, 152 * 8), 256, 0, st>>>(A, B, d_dd, d_st, d_bt, d_pb);
+      SETUP_TRY(cudaGetLastError());
+      SETUP_TRY(cudaMemcpyAsync(terms->dd.data(), d_dd, terms->dd.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+      SETUP_TRY(cudaMemcpyAsync(terms->st.data(), d_st, terms->st.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+      SETUP_TRY(cudaMemcpyAsync(terms->bt.data(), d_bt, terms->bt.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+      SETUP_TRY(cudaMemcpyAsync(terms->pb.data(), d_pb, terms->pb.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
   }
   mask.resize((size_t)ncells);
   masked_cells.resize((size_t)m);

@@ -571,12 +571,21 @@ int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, do
   std::vector<uint8_t> dev_mask;
   std::vector<long long> dev_cells, cell_first, entry_first;
   std::vector<double> dev_dist;
+  DeviceTerms dev_terms;
+  std::vector<int> dev_cut_index;  // block -> its index among the device's cut blocks, -1 none
   const bool on_device = T->setup_on_device && !reuse &&
                          (lsf->kind == GMG_LSF_SPHERE || lsf->kind == GMG_LSF_CAPSULE ||
                           lsf->kind == GMG_LSF_ELLIPSOID) && device_setup_available();
   if (on_device) {
-    const int rc = device_boundary_detection(T, f.spec, dev_mask, dev_cells, dev_dist);
+    // the stencils and terms too when the boundary and wall values are constants
+    const bool terms = !phib && !T->wall_fn;
+    const int rc = device_boundary_detection(T, f.spec, dev_mask, dev_cells, dev_dist, terms ? &dev_terms : nullptr,
+                                             phib_const);
     if (rc) return rc;
+    if (terms) {
+      dev_cut_index.assign(nb, -1);
+      for (size_t i = 0; i < dev_terms.cut_ids.size(); i++) dev_cut_index[dev_terms.cut_ids[i]] = (int)i;
+    }
     cell_first.assign(nb + 1, 0);
     for (int b = 0; b < nb; b++) cell_first[b + 1] = cell_first[b] + T->lev(T->blocks[b].level).ncell;
     entry_first.assign(nb + 1, 0);
@@ -585,6 +594,37 @@ int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, do
           std::lower_bound(dev_cells.begin(), dev_cells.end(), cell_first[b + 1]) - dev_cells.begin();
   }
   T->setup_device = on_device;
+  // Dirichlet values at the centres of a block's faces on upper domain walls
+  // (axis k, face cell j over the other axes in increasing order), for the
+  // field evaluation on upper cell faces
+  auto wall_values = [&](BlockOut &o, const HostBlock &B, const LevelInfo &L) {
+    const int n = L.n;
+    const double h = L.h;
+    {
+      const int nf = D == 3 ? n * n : n;
+      bool upper = false;
+      std::vector<double> wv((size_t)D * nf, 0.0);
+      for (int k = 0; k < D; k++)
+        for (int j = 0; j < nf; j++) {
+          const int u = j % n, v = D == 3 ? j / n : 0;
+          int p[3] = {0, 0, 0};
+          p[k] = n - 1;
+          p[k == 0 ? 1 : 0] = u;
+          if (D == 3) p[k == 2 ? 1 : 2] = v;
+          int G[3];
+          for (int d = 0; d < 3; d++) G[d] = d < D ? B.ix[d] * n + p[d] : 0;
+          G[k] += 1;
+          if (in_domain(L, D, G)) continue;
+          upper = true;
+          if (T->wall_type[2 * k + 1] != GMG_WALL_DIRICHLET) continue;
+          double a[3];
+          cell_center(T, B, L, p, a);
+          a[k] += 0.5 * h;
+          wv[(size_t)k * nf + j] = T->wall_fn ? T->wall_fn(a, T->wall_user) : T->wall_val[2 * k + 1];
+        }
+      if (upper) o.wv = std::move(wv);
+    }
+  };
   auto process = [&](int id, BlockOut &o) {
     const HostBlock &B = T->blocks[id];
     const LevelInfo &L = T->lev(B.level);
@@ -598,6 +638,24 @@ int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, do
       return &dd[(size_t)c * 2 * D];
     };
     bool cut = false;
+    if (on_device && !dev_cut_index.empty()) {  // everything from the device
+      o.mask.assign(dev_mask.begin() + cell_first[id], dev_mask.begin() + cell_first[id + 1]);
+      const int ci = dev_cut_index[id];
+      if (ci >= 0) {
+        const long long a = dev_terms.cell_off[ci], e = dev_terms.cell_off[ci + 1];
+        o.cut = true;
+        o.dd.assign(dev_terms.dd.begin() + a * 2 * D, dev_terms.dd.begin() + e * 2 * D);
+        o.pb.assign(dev_terms.pb.begin() + a * 2 * D, dev_terms.pb.begin() + e * 2 * D);
+        o.st.assign(dev_terms.st.begin() + a * S, dev_terms.st.begin() + e * S);
+        bt.assign(dev_terms.bt.begin() + a, dev_terms.bt.begin() + e);
+        for (int c = 0; c < nc; c++) o.anybt = o.anybt || bt[c] != 0.0;
+      } else {
+        o.anybt = wall_terms(T, B, L, bt);
+      }
+      wall_values(o, B, L);
+      if (o.anybt) o.bt = std::move(bt);
+      return;
+    }
     if (on_device) {
       o.mask.assign(dev_mask.begin() + cell_first[id], dev_mask.begin() + cell_first[id + 1]);
       for (long long e = entry_first[id]; e < entry_first[id + 1]; e++) {
@@ -657,33 +715,7 @@ int host_setup(gmg_tree *T, const gmg_lsf *lsf, gmg_fn phib, void *phib_user, do
       o.anybt = wall_terms(T, B, L, bt);
     }
     o.cut = cut;
-    // Dirichlet values at the centres of the block's faces on upper domain
-    // walls (axis k, face cell j over the other axes in increasing order),
-    // for the field evaluation on upper cell faces
-    {
-      const int nf = D == 3 ? n * n : n;
-      bool upper = false;
-      std::vector<double> wv((size_t)D * nf, 0.0);
-      for (int k = 0; k < D; k++)
-        for (int j = 0; j < nf; j++) {
-          const int u = j % n, v = D == 3 ? j / n : 0;
-          int p[3] = {0, 0, 0};
-          p[k] = n - 1;
-          p[k == 0 ? 1 : 0] = u;
-          if (D == 3) p[k == 2 ? 1 : 2] = v;
-          int G[3];
-          for (int d = 0; d < 3; d++) G[d] = d < D ? B.ix[d] * n + p[d] : 0;
-          G[k] += 1;
-          if (in_domain(L, D, G)) continue;
-          upper = true;
-          if (T->wall_type[2 * k + 1] != GMG_WALL_DIRICHLET) continue;
-          double a[3];
-          cell_center(T, B, L, p, a);
-          a[k] += 0.5 * h;
-          wv[(size_t)k * nf + j] = T->wall_fn ? T->wall_fn(a, T->wall_user) : T->wall_val[2 * k + 1];
-        }
-      if (upper) o.wv = std::move(wv);
-    }
+    wall_values(o, B, L);
     if (o.anybt) o.bt = std::move(bt);
   };
   // Re-meshing (Sec. 4.5: boundary detection only for newly added cells):
