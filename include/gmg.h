@@ -415,18 +415,23 @@ int gmg_profile_read(gmg_tree *tree, int cap, int *kind, int *prec, int *level, 
                                     reading its results; same results */
 #define GMG_OPT_CLUSTER_TAIL 11  /* [1] the bottom of the V-cycle (the levels holding one block per
                                     root, and the level of each root's 2^D children when it is
-                                    complete) on a cluster of 2^D CTAs per (root, slot), each CTA
-                                    holding one octant of every such level in shared memory and
-                                    reading its neighbours' ghost cells through distributed shared
-                                    memory: 0 off (one CTA per (root, slot) inside the cooperative
-                                    launch), 1 when every unit's cluster is resident at once, 2
-                                    whenever the tree qualifies (sides multiples of 4, octants
-                                    within one CTA's shared memory); same arithmetic */
+                                    complete) on a cluster of CTAs per (root, slot) (4 in 2D; 8 or
+                                    16 in 3D, GMG_OPT_CLUSTER_PARTS), each CTA holding one part of
+                                    every such level in shared memory and writing its neighbours'
+                                    ghost cells through distributed shared memory: 0 off (one CTA
+                                    per (root, slot) inside the cooperative launch), 1 when every
+                                    unit's cluster is resident at once, 2 whenever the tree
+                                    qualifies (parts of even side, within one CTA's shared
+                                    memory); same arithmetic */
 #define GMG_OPT_DEVICE_SETUP 12  /* [1] gmg_store_stencils with a built-in sphere, capsule or ellipsoid
                                     level set runs the boundary mask, the line searches and the
                                     unresolved-root search on the device when a CUDA device is
                                     present (the same values bit for bit); 0 on the host.  Set it
                                     before gmg_store_stencils. */
+#define GMG_OPT_CLUSTER_PARTS 13 /* [0] CTAs of the 3D cluster of GMG_OPT_CLUSTER_TAIL: 8 (octants of
+                                    N/2 cells a side), 16 (parts of N/2 x N/2 x N/4; non-portable
+                                    cluster size, split levels' sides multiples of 8), or 0: 16
+                                    when the tree and the device allow it, else 8; same arithmetic */
 int gmg_set_option(gmg_tree *tree, int option, long long value);
 
 /* Sweep schedule: N_down / N_up red-black sweeps on one level (default: the

@@ -555,7 +555,7 @@ class Tree:
 
     OPTIONS = {"graphs": 1, "coarse_coop": 2, "spin_limit": 3, "fused_sweeps": 4, "cta_threads": 5,
                "coop_max_blocks": 6, "inner_cycles": 7, "slots_per_cta": 8, "fmg_steps": 9, "pdl": 10,
-               "cluster_tail": 11, "device_setup": 12}
+               "cluster_tail": 11, "device_setup": 12, "cluster_parts": 13}
 
     def set_level_sweeps(self, level, n_down, n_up):
         """N_down / N_up red-black sweeps on one level (a tuning schedule)."""

@@ -7,10 +7,12 @@ namespace gmg {
 namespace {
 
 template <typename T, int D>
-void cluster_attrs(size_t smem) {
+void cluster_attrs(size_t smem, int P) {
   auto kern = k_cycle_cluster<T, D>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+  // clusters of 16 CTAs are beyond the portable size of 8
+  if (P > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
 }  // namespace
@@ -18,8 +20,8 @@ void cluster_attrs(size_t smem) {
 template <typename T, int D>
 cudaError_t launch_cycle_cluster(const GmgView<T> &V, const LvArgs *lvtab, int lmin, const ClusterArgs &A,
                                  int nunits, size_t smem, cudaStream_t s, bool pdl) {
-  constexpr int P = 1 << D;
-  cluster_attrs<T, D>(smem);
+  const int P = D == 3 ? 4 * A.pz : 4;
+  cluster_attrs<T, D>(smem, P);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(P * nunits);
   cfg.blockDim = dim3(kClusterThreads);
@@ -38,9 +40,8 @@ cudaError_t launch_cycle_cluster(const GmgView<T> &V, const LvArgs *lvtab, int l
 }
 
 template <typename T, int D>
-int cycle_cluster_capacity(size_t smem) {
-  constexpr int P = 1 << D;
-  cluster_attrs<T, D>(smem);
+int cycle_cluster_capacity(size_t smem, int P) {
+  cluster_attrs<T, D>(smem, P);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(P);
   cfg.blockDim = dim3(kClusterThreads);
@@ -68,9 +69,9 @@ template cudaError_t launch_cycle_cluster<double, 2>(const GmgView<double> &, co
                                                      const ClusterArgs &, int, size_t, cudaStream_t, bool);
 template cudaError_t launch_cycle_cluster<double, 3>(const GmgView<double> &, const LvArgs *, int,
                                                      const ClusterArgs &, int, size_t, cudaStream_t, bool);
-template int cycle_cluster_capacity<float, 2>(size_t);
-template int cycle_cluster_capacity<float, 3>(size_t);
-template int cycle_cluster_capacity<double, 2>(size_t);
-template int cycle_cluster_capacity<double, 3>(size_t);
+template int cycle_cluster_capacity<float, 2>(size_t, int);
+template int cycle_cluster_capacity<float, 3>(size_t, int);
+template int cycle_cluster_capacity<double, 2>(size_t, int);
+template int cycle_cluster_capacity<double, 3>(size_t, int);
 
 }  // namespace gmg

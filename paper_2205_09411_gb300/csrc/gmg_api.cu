@@ -494,34 +494,39 @@ int coop_launch(gmg_tree *t, cudaStream_t s, int ls, int mode, int l_stop) {
 // Plan of the cluster kernel (cluster_tail.cuh) for the bottom of a V-cycle
 // whose coarse part covers levels lmin .. ls: the single-block levels from
 // lmin up, and above them the level of the roots' 2^D children when it is
-// complete; every level's side a multiple of 4 (octants of even side); the
-// octants' arrays within one CTA's shared memory; all units' clusters
-// resident at once.  Returns false when the tree does not qualify (the
-// cooperative kernel's own tail then runs).
+// complete.  A cluster of P CTAs splits each level of more than 8 cells a
+// side into parts of N/2 x N/2 (x N/pz in 3D) cells, whose sides must be
+// even; the parts' arrays must fit one CTA's shared memory and, with
+// cluster_mode 1, all units' clusters must be resident at once.  In 3D,
+// clusters of 16 CTAs (pz = 4) are tried first unless cluster_parts asks
+// for 8.  Returns false when the tree does not qualify (the cooperative
+// kernel's own tail then runs).
 template <typename T, int D>
-bool plan_cluster(gmg_tree *t, int ls, ClusterArgs *A, size_t *smem) {
-  constexpr int P = 1 << D;
-  if (t->cluster_mode == 0) return false;
-  if (!(t->nroot > 1 || t->cb[0] * t->cb[1] * t->cb[2] == 1)) return false;
+bool plan_cluster_pz(gmg_tree *t, int ls, int pz, ClusterArgs *A, size_t *smem) {
+  const int P = D == 3 ? 4 * pz : 4;
   int l_single = t->lmin - 1;
   for (int l = t->lmin; l <= ls && t->lev(l).count == t->nroot; l++) l_single = l;
   if (l_single < t->lmin) return false;
-  // split levels (more than 8 cells a side) need octants of even side; the
+  // split levels (more than 8 cells a side) need parts of even side; the
   // levels of at most 8 a side are held whole by every CTA and need an even side
+  const int split_mod = D == 3 && pz == 4 ? 8 : 4;
   for (int l = t->lmin; l <= l_single; l++)
-    if (t->lev(l).n % (t->lev(l).n > 8 ? 4 : 2)) return false;
+    if (t->lev(l).n % (t->lev(l).n > 8 ? split_mod : 2)) return false;
   bool children = false;
-  if (l_single + 1 <= ls && t->lev(l_single + 1).count == t->nroot * P) {
+  constexpr int NCH = 1 << D;
+  if (l_single + 1 <= ls && t->lev(l_single + 1).count == t->nroot * NCH) {
     children = true;
     const LevelInfo &R = t->lev(l_single), &Cl = t->lev(l_single + 1);
     for (int r = 0; r < t->nroot && children; r++)
-      for (int k = 0; k < P && children; k++) {
-        const HostBlock &b = t->blocks[Cl.first + P * r + k];
+      for (int k = 0; k < NCH && children; k++) {
+        const HostBlock &b = t->blocks[Cl.first + NCH * r + k];
         const HostBlock &p = t->blocks[R.first + r];
         if (b.parent != R.first + r) children = false;
         for (int d = 0; d < D; d++)
           if (b.ix[d] - 2 * p.ix[d] != ((k >> d) & 1)) children = false;
       }
+    // the children level's parts lie within one child each
+    if (children && (2 * Cl.n) % split_mod) children = false;
   }
   const size_t limit = 224 * 1024;
   for (int attempt = 0; attempt < 2; attempt++) {
@@ -531,6 +536,7 @@ bool plan_cluster(gmg_tree *t, int ls, ClusterArgs *A, size_t *smem) {
     a.l_lo = t->lmin;
     a.l_top = l_top;
     a.children = children ? 1 : 0;
+    a.pz = D == 3 ? pz : 1;
     a.ncr = t->ncr;
     a.nroot = t->nroot;
     a.cinv = t->d_cinv;
@@ -550,10 +556,12 @@ bool plan_cluster(gmg_tree *t, int ls, ClusterArgs *A, size_t *smem) {
       if (full && a.full_from > i) a.full_from = i;
       if (!full && i > a.full_from) ok = false;  // full levels form the bottom of the range
       if (i == 0 && N <= 8) ok = false;          // the top level is split
-      const int m = full ? N : N / 2, nc = D == 3 ? m * m * m : m * m, R = m + 2;
+      const int m0 = full ? N : N / 2, m2 = D == 3 ? (full ? N : N / a.pz) : 1;
+      const int nc = m0 * m0 * m2;
+      const size_t ring = (size_t)(m0 + 2) * (m0 + 2) * (D == 3 ? m2 + 2 : 1);
       const int cap = t->cut_max_h[l - t->lmin];
       if (cap > 65534) ok = false;
-      a.off_tile[i] = take(sizeof(T) * (size_t)(D == 3 ? R * R * R : R * R));
+      a.off_tile[i] = take(sizeof(T) * ring);
       a.off_b[i] = take(sizeof(T) * (size_t)nc);
       a.off_old[i] = take(sizeof(T) * (size_t)nc);
       a.off_eidx[i] = take(2 * (size_t)nc);
@@ -566,7 +574,7 @@ bool plan_cluster(gmg_tree *t, int ls, ClusterArgs *A, size_t *smem) {
     a.off_rows = a.stage_rows ? take(rows) : 0;
     if (ok && o <= limit) {
       const int units = t->nrhs * t->nroot;
-      if (t->cluster_mode == 1 && units > cycle_cluster_capacity<T, D>(o)) return false;
+      if (t->cluster_mode == 1 && units > cycle_cluster_capacity<T, D>(o, P)) return false;
       *A = a;
       *smem = o;
       return true;
@@ -575,6 +583,15 @@ bool plan_cluster(gmg_tree *t, int ls, ClusterArgs *A, size_t *smem) {
     children = false;  // retry without the children level
   }
   return false;
+}
+
+template <typename T, int D>
+bool plan_cluster(gmg_tree *t, int ls, ClusterArgs *A, size_t *smem) {
+  if (t->cluster_mode == 0) return false;
+  if (!(t->nroot > 1 || t->cb[0] * t->cb[1] * t->cb[2] == 1)) return false;
+  if (D == 2) return plan_cluster_pz<T, D>(t, ls, 1, A, smem);
+  if (t->cluster_parts != 8 && plan_cluster_pz<T, D>(t, ls, 4, A, smem)) return true;
+  return t->cluster_parts != 16 && plan_cluster_pz<T, D>(t, ls, 2, A, smem);
 }
 
 // One FAS V-cycle on fields of type T (Sec. 2.2; readings UP and V).
@@ -1754,6 +1771,10 @@ int gmg_set_option(gmg_tree *t, int option, long long value) {
     case GMG_OPT_CLUSTER_TAIL:
       if (value < 0 || value > 2) return set_error("cluster tail must be 0 (off), 1 (auto) or 2 (whenever the tree qualifies)"), GMG_ERR_INVALID_ARG;
       t->cluster_mode = (int)value;
+      break;
+    case GMG_OPT_CLUSTER_PARTS:
+      if (value != 0 && value != 8 && value != 16) return set_error("cluster parts must be 0 (auto), 8 or 16"), GMG_ERR_INVALID_ARG;
+      t->cluster_parts = (int)value;
       break;
     case GMG_OPT_PDL:
       t->use_pdl = value != 0;

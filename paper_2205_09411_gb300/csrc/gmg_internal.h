@@ -137,24 +137,26 @@ constexpr int kClusterThreads = 512;
 constexpr int kClusterMaxLevels = 12;
 struct ClusterArgs {
   int l_lo, l_top;
-  int children;    // level l_top holds the 2^D children of each root: octant k = block first + P root + k
+  int children;    // level l_top holds the 2^D children of each root: child k = block first + 2^D root + k
+  int pz;          // parts along z in 3D (2 or 4): clusters of 4 pz CTAs; 2D: 4 CTAs
   int ncr, nroot;  // coarsest-level unknowns per root, roots
   const double *cinv;
   int stage_rows;  // this CTA's rows of the coarse inverse are staged in shared memory
   int full_from;   // levels i >= full_from (at most 8 cells a side) are held whole by every CTA
   unsigned int off_tile[kClusterMaxLevels], off_b[kClusterMaxLevels], off_old[kClusterMaxLevels];
   unsigned int off_eidx[kClusterMaxLevels], off_cf[kClusterMaxLevels];
-  unsigned int off_bd, off_rows;  // FP64 b of the coarsest level (all octants); staged inverse rows
+  unsigned int off_bd, off_rows;  // FP64 b of the coarsest level (all parts); staged inverse rows
 };
 
-// Launches the cluster kernel: nunits clusters of 2^D CTAs (cluster_tail.cu).
+// Launches the cluster kernel: nunits clusters of A.pz 4 CTAs in 3D, 4 in
+// 2D (cluster_tail.cu).
 template <typename T, int D>
 cudaError_t launch_cycle_cluster(const GmgView<T> &V, const LvArgs *lvtab, int lmin, const ClusterArgs &A,
                                  int nunits, size_t smem, cudaStream_t s, bool pdl);
-// Clusters of the kernel with `smem` dynamic bytes that fit on the device at
-// once (0 if none does).
+// Clusters of P CTAs with `smem` dynamic bytes each that fit on the device
+// at once (0 if none does).
 template <typename T, int D>
-int cycle_cluster_capacity(size_t smem);
+int cycle_cluster_capacity(size_t smem, int P);
 
 
 }  // namespace gmg
@@ -261,6 +263,7 @@ struct gmg_tree {
   bool setup_on_device = true;  // boundary detection of built-in level sets on the device when one is present
   bool setup_device = false;    // the last set-up ran its boundary detection on the device
   int cluster_mode = 1;       // bottom of the cycle on a thread-block cluster: 0 off, 1 when all units fit at once, 2 whenever eligible
+  int cluster_parts = 0;      // CTAs of the cluster in 3D: 8, 16, or 0 for 16 when the tree and the device allow it
   std::vector<char> level_complete;  // every block has all 26 neighbours on its level (or walls)
   int coop_split = 0;         // highest level run inside that launch
   int coop_max_blocks = gmg::kCoopMaxBlocks;  // levels with at most this many blocks join it

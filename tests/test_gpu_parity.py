@@ -219,18 +219,20 @@ def test_execution_paths_give_the_oracle_iterates(name, graphs, coop):
 @pytest.mark.parametrize("name", ["c2_64", "c2_32", "c1", "needle4", "adaptive3d", "no_boundary"])
 def test_cluster_tail_gives_the_oracle_iterates(name):
     """The bottom of the V-cycle on a thread-block cluster (each CTA one
-    octant of the single-block levels and of the roots' children level, in
+    part of the single-block levels and of the roots' children level, in
     shared memory, ghosts through distributed shared memory) gives the
-    oracle's FP64 iterates after each of 6 V-cycles, FP64 and FMG; where the
-    coarse solve of both paths sums a row the same way (at most 256
-    coarsest-level cells), the iterates and a mixed solve equal the
+    oracle's FP64 iterates after each of 6 V-cycles, FP64 and FMG, with
+    clusters of 16 and of 8 CTAs in 3D (the same arithmetic: equal bit for
+    bit); where the coarse solve of both paths sums a row the same way (at
+    most 256 coarsest-level cells), the iterates and a mixed solve equal the
     single-CTA bottom's bit for bit."""
     p = parity_cases()[name]
     o = oracle_problem(p)
     out = []
-    for mode in (2, 0):
+    for mode, parts in ((2, 16), (2, 8), (0, 0)):
         t = gpu_problem(p)
         t.set_option("cluster_tail", mode)
+        t.set_option("cluster_parts", parts)
         its = []
         for k in range(6):
             t.vcycle(1)
@@ -249,9 +251,11 @@ def test_cluster_tail_gives_the_oracle_iterates(name):
     o.fmg(1)
     ref = o.solution()
     assert np.abs(out[0][6] - ref).max() <= TOL_ITERATE * np.abs(ref).max()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
     q = gpu_problem(p, bind=False, rhs=False)
     if q.level_info(q.lmin)[1] ** p["dim"] <= 256:
-        for a, b in zip(out[0], out[1]):
+        for a, b in zip(out[0], out[2]):
             assert np.array_equal(a, b)
 
 
