@@ -450,6 +450,16 @@ int gmg_get_level_sweeps(const gmg_tree *tree, int level, int *n_down, int *n_up
  * as designed (the context stays usable), GMG_OK if it did not. */
 int gmg_selftest_barrier_timeout(gmg_tree *tree, long long spin_limit, void *stream);
 
+/* Self test of the integer-operation conversions that the FP64 residual and
+ * the FP64 update of the mixed path use (double -> float rounded to nearest
+ * even, float -> double): converts the n doubles x and the n floats f (device
+ * arrays) both ways and by the hardware, and writes to mismatches[0] and
+ * mismatches[1] (device array of 2, overwritten) how many results differ bit
+ * for bit.  Synchronises the stream.  Errors: INVALID_ARG for null arrays or
+ * n < 0; CUDA on a failed launch. */
+int gmg_selftest_conversions(const double *x, const float *f, long long n, unsigned long long *mismatches,
+                             void *stream);
+
 const char *gmg_error_string(int code);
 const char *gmg_last_error(void);
 

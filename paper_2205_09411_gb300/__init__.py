@@ -121,6 +121,7 @@ def load():
         "gmg_profile_read": (C.c_int, [vp, C.c_int, ip, ip, ip, C.POINTER(C.c_longlong), dp]),
         "gmg_set_option": (C.c_int, [vp, C.c_int, C.c_longlong]),
         "gmg_selftest_barrier_timeout": (C.c_int, [vp, C.c_longlong, vp]),
+        "gmg_selftest_conversions": (C.c_int, [vp, vp, C.c_longlong, vp, vp]),
         "gmg_error_string": (C.c_char_p, [C.c_int]),
         "gmg_last_error": (C.c_char_p, []),
     }
@@ -178,6 +179,15 @@ def _stream_ptr(stream):
     if isinstance(stream, int):
         return C.c_void_p(stream)
     return C.c_void_p(stream.cuda_stream)
+
+
+def selftest_conversions(x, f, mismatches, stream=None):
+    """gmg_selftest_conversions on device tensors: x float64 and f float32 of
+    one length, mismatches int64 of 2 (overwritten with the counts)."""
+    n = x.numel()
+    assert f.numel() == n and mismatches.numel() == 2
+    _check(load().gmg_selftest_conversions(C.c_void_p(x.data_ptr()), C.c_void_p(f.data_ptr()), n,
+                                           C.c_void_p(mismatches.data_ptr()), _stream_ptr(stream)))
 
 
 class Tree:

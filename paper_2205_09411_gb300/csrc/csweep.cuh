@@ -46,13 +46,12 @@ inline size_t cs_smem_bytes(int sg) {
   return CsGeo<T, D, NT>::smem_bytes(sg);
 }
 
-// Stages slot s's other-colour half, face ghosts and own-colour b for a
-// half-sweep of colour c of block bid.  cp.async for everything that comes
-// from a same-level block; wall and refinement ghosts need the copies done
-// and are filled by cs_special_ghosts.
+// Stages slot s's other-colour half and own-colour b for a half-sweep of
+// colour c of block bid (cp.async; nothing here depends on the neighbour
+// table, so the copies start before it is read).
 template <typename T, int D, int NT>
-__device__ __forceinline__ void cs_stage(const GmgView<T> &V, const LvArgs &L, int bid, int c, const int *s_nb, int fl,
-                                         long long rs_phi, long long rs_f, T *O, T *B) {
+__device__ __forceinline__ void cs_stage_interior(const GmgView<T> &V, const LvArgs &L, int bid, int c,
+                                                  long long rs_phi, long long rs_f, T *O, T *B) {
   using G = CsGeo<T, D, NT>;
   constexpr int VEC = 16 / sizeof(T);
   constexpr bool kChunks = (G::HN % VEC) == 0;
@@ -74,9 +73,25 @@ __device__ __forceinline__ void cs_stage(const GmgView<T> &V, const LvArgs &L, i
       cp_async_elem(B + j, bown + j);
     }
   }
+}
+
+// Stages slot s's face ghosts that come from same-level blocks, and on a
+// wall face the block's own cells beside the wall (cp.async); the wall
+// sign and the refinement ghosts need the copies done and are applied by
+// cs_special_ghosts.  A wall ghost reflects the own-colour cell beside it
+// (reading W), which sits at the same position k of its row's own-colour
+// run as the ghost in the ghost row: the run is copied whole.
+template <typename T, int D, int NT>
+__device__ __forceinline__ void cs_stage_faces(const GmgView<T> &V, const LvArgs &L, int bid, int c, const int *s_nb,
+                                               int fl, long long rs_phi, T *O) {
+  using G = CsGeo<T, D, NT>;
+  constexpr int VEC = 16 / sizeof(T);
+  constexpr bool kChunks = (G::HN % VEC) == 0;
+  const long long pown = rs_phi + L.poff + (long long)(bid - L.first) * (2 * G::H) + c * G::H;  // own colour
   // y and z faces toward same-level neighbours: the neighbour's boundary
   // row of the other colour, one contiguous run of HN cells per row (in
-  // 16-byte pieces when the run is whole vectors)
+  // 16-byte pieces when the run is whole vectors); toward a wall, the own
+  // colour's row beside it
   constexpr int FR = D == 3 ? NT : 1;  // rows per face
   constexpr int PW = kChunks ? VEC : 1;  // cells per piece
   constexpr int PR = G::HN / PW;         // pieces per row
@@ -85,11 +100,18 @@ __device__ __forceinline__ void cs_stage(const GmgView<T> &V, const LvArgs &L, i
     const int u = rem / PR, k = (rem - u * PR) * PW;  // u: the face's row, k: first cell of the piece
     const int a = f >> 1, side = f & 1;
     const int id = s_nb[f];
-    if ((fl & wall_bit(a, side)) || id < 0) continue;
-    const int ys = a == 1 ? (side ? 0 : NT - 1) : u, zs = a == 2 ? (side ? 0 : NT - 1) : u;
+    const bool wall = (fl & wall_bit(a, side)) != 0;
+    if (!wall && id < 0) continue;  // a refinement boundary
     const int yg = a == 1 ? (side ? NT : -1) : u, zg = a == 2 ? (side ? NT : -1) : u;
-    const T *src = V.phi + rs_phi + L.poff + (long long)(id - L.first) * (2 * G::H) + (1 - c) * G::H +
-                   G::HN * (ys + (D == 3 ? NT * zs : 0));
+    const T *src;
+    if (wall) {
+      const int yi = a == 1 ? (side ? NT - 1 : 0) : u, zi = a == 2 ? (side ? NT - 1 : 0) : u;
+      src = V.phi + pown + G::HN * (yi + (D == 3 ? NT * zi : 0));
+    } else {
+      const int ys = a == 1 ? (side ? 0 : NT - 1) : u, zs = a == 2 ? (side ? 0 : NT - 1) : u;
+      src = V.phi + rs_phi + L.poff + (long long)(id - L.first) * (2 * G::H) + (1 - c) * G::H +
+            G::HN * (ys + (D == 3 ? NT * zs : 0));
+    }
     T *dst = O + G::at(G::row(yg, D == 3 ? zg : 0), k);
     if (kChunks)
       cp_async16(dst, src + k);
@@ -103,18 +125,22 @@ __device__ __forceinline__ void cs_stage(const GmgView<T> &V, const LvArgs &L, i
     const int qo = (y + z + 1 - c) & 1;
     const int side = qo ? 0 : 1;
     const int id = s_nb[side];
-    if ((fl & wall_bit(0, side)) || id < 0) continue;
-    // the neighbour's cell (NT - 1, y, z) or (0, y, z): both of colour 1 - c
-    const long long q = rs_phi + L.poff + (long long)(id - L.first) * (2 * G::H) + (1 - c) * G::H +
-                        G::HN * (y + NT * z) + (side ? 0 : G::HN - 1);
+    const bool wall = (fl & wall_bit(0, side)) != 0;
+    if (!wall && id < 0) continue;
+    // the neighbour's cell (NT - 1, y, z) or (0, y, z): both of colour 1 -
+    // c; at a wall the own cell (0, y, z) or (NT - 1, y, z) of colour c,
+    // first or last of its row's own-colour run
+    const long long q = wall ? pown + G::HN * (y + NT * z) + (side ? G::HN - 1 : 0)
+                             : rs_phi + L.poff + (long long)(id - L.first) * (2 * G::H) + (1 - c) * G::H +
+                                   G::HN * (y + NT * z) + (side ? 0 : G::HN - 1);
     cp_async_elem(O + G::at(G::row(y, z), side ? G::HN : -1), V.phi + q);
   }
 }
 
 // Wall and refinement-boundary ghosts of the other colour (after the
 // staged copies have landed): a wall ghost is the sign times the own cell
-// beside it, a refinement ghost follows reading G (refine_ghost, on the
-// slot's own block).
+// beside it (staged in the ghost's place by cs_stage_faces), a refinement
+// ghost follows reading G (refine_ghost, on the slot's own block).
 template <typename T, int D, int NT>
 __device__ __forceinline__ void cs_special_ghosts(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid,
                                                   int c, const int *s_nb, int fl, long long rs_phi, T *O) {
@@ -133,30 +159,27 @@ __device__ __forceinline__ void cs_special_ghosts(const GmgView<T> &V, const LvA
     const int yg = a == 1 ? (side ? NT : -1) : u, zg = a == 2 ? (side ? NT : -1) : (D == 3 ? u : 0);
     const int qg = (yg + zg + 1 - c) & 1;  // the ghost row's other-colour parity
     const int x = 2 * k + qg;
-    const int yi = a == 1 ? (side ? NT - 1 : 0) : yg, zi = a == 2 ? (side ? NT - 1 : 0) : zg;
-    T val;
+    T *dst = O + G::at(G::row(yg, zg), k);
     if (wall) {
-      val = (((V.wneu >> f) & 1) ? T(1) : T(-1)) * own[cs_pos_xyz(x, yi, zi, NT, 2 * G::H)];
+      *dst = wall_reflect(*dst, (V.wneu >> f) & 1);
     } else {
       const int g[3] = {x, yg, zg};
-      val = refine_ghost<T, D>(phi, V.nbr, V.flags, V.parent, V.pofs, V.wneu, L, Lp, bid, g, a, own);
+      *dst = refine_ghost<T, D>(phi, V.nbr, V.flags, V.parent, V.pofs, V.wneu, L, Lp, bid, g, a, own);
     }
-    O[G::at(G::row(yg, zg), k)] = val;
   }
   for (int r = threadIdx.x; r < G::H / G::HN; r += blockDim.x) {
     const int y = r % NT, z = D == 3 ? r / NT : 0;
     const int side = ((y + z + 1 - c) & 1) ? 0 : 1;
     const bool wall = (fl & wall_bit(0, side)) != 0;
     if (!wall && s_nb[side] >= 0) continue;
-    const int xg = side ? NT : -1, xi = side ? NT - 1 : 0;
-    T val;
+    const int xg = side ? NT : -1;
+    T *dst = O + G::at(G::row(y, z), side ? G::HN : -1);
     if (wall) {
-      val = (((V.wneu >> side) & 1) ? T(1) : T(-1)) * own[cs_pos_xyz(xi, y, z, NT, 2 * G::H)];
+      *dst = wall_reflect(*dst, (V.wneu >> side) & 1);
     } else {
       const int g[3] = {xg, y, z};
-      val = refine_ghost<T, D>(phi, V.nbr, V.flags, V.parent, V.pofs, V.wneu, L, Lp, bid, g, 0, own);
+      *dst = refine_ghost<T, D>(phi, V.nbr, V.flags, V.parent, V.pofs, V.wneu, L, Lp, bid, g, 0, own);
     }
-    O[G::at(G::row(y, z), side ? G::HN : -1)] = val;
   }
 }
 
@@ -193,12 +216,16 @@ __device__ __forceinline__ void smooth_cs_block(const GmgView<T> &V, const LvArg
       for (int i = threadIdx.x; i < 2 * G::H; i += blockDim.x) sfl[i] = src[i];
     }
   }
+  // the block's own halves are in flight while the neighbour table is read
+#pragma unroll
+  for (int s = 0; s < SG; s++)
+    if (slot[s] >= 0)
+      cs_stage_interior<T, D, NT>(V, L, bid, color, slot[s] * V.rs_phi, slot[s] * V.rs_f, O + s * G::OS, B + s * G::H);
   __syncthreads();
   const int fl = s_fl;
 #pragma unroll
   for (int s = 0; s < SG; s++)
-    if (slot[s] >= 0) cs_stage<T, D, NT>(V, L, bid, color, s_nb, fl, slot[s] * V.rs_phi, slot[s] * V.rs_f, O + s * G::OS,
-                                         B + s * G::H);
+    if (slot[s] >= 0) cs_stage_faces<T, D, NT>(V, L, bid, color, s_nb, fl, slot[s] * V.rs_phi, O + s * G::OS);
   cp_async_wait_all();
   __syncthreads();
   bool special = false;

@@ -33,11 +33,10 @@ void set_error(const std::string &msg) { g_last_error = msg; }
     }                                                                                        \
   } while (0)
 
-__global__ void __launch_bounds__(1024) k_reduce_partials(const double *partials, int nb, const int *tree_blocks,
-                                                          const int *tree_boff, int ntree, double *out,
-                                                          const GridBar *bar) {
+__global__ void __launch_bounds__(kResThreads) k_reduce_partials(const double *partials, int nb, const int *tree_blocks,
+                                                                 const int *tree_boff, int ntree, double *out,
+                                                                 const GridBar *bar) {
   pdl_start();
-  __shared__ double s[3][1024];
   // unit blockIdx.x = (slot r, tree i): the blocks of tree i in slot r
   const int r = blockIdx.x / ntree, tr = blockIdx.x % ntree;
   partials += (size_t)r * nb * 3;
@@ -50,24 +49,8 @@ __global__ void __launch_bounds__(1024) k_reduce_partials(const double *partials
     b = fmax(b, partials[i * 3 + 1]);
     c += partials[i * 3 + 2];
   }
-  s[0][threadIdx.x] = a;
-  s[1][threadIdx.x] = b;
-  s[2][threadIdx.x] = c;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      s[0][threadIdx.x] += s[0][threadIdx.x + w];
-      s[1][threadIdx.x] = fmax(s[1][threadIdx.x], s[1][threadIdx.x + w]);
-      s[2][threadIdx.x] += s[2][threadIdx.x + w];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    out[0] = s[0][0];
-    out[1] = s[1][0];
-    out[2] = s[2][0];
-    out[3] = bar ? (double)bar->err : 0.0;  // a timed-out barrier of the coarse cycle
-  }
+  block_reduce3(a, b, c, out);  // fixed order: warp shuffles, then the warps in order
+  if (threadIdx.x == 0) out[3] = bar ? (double)bar->err : 0.0;  // a timed-out barrier of the coarse cycle
 }
 
 // Leaf-cell kernels over the slots r0 .. r0 + nr - 1: a CTA takes leaf
@@ -120,7 +103,22 @@ __global__ void k_leaf_accumulate(const int *__restrict__ leaf_ids, const long l
     const int tr = ntree > 1 ? tree_of[id] : 0;
     for (int r = 0; r < nr; r++) {
       if (!active[r * ntree + tr]) continue;
-      for (int c = threadIdx.x; c < ncell; c += blockDim.x) phi[r * rs + base + c] += (double)e[r * rs + base + c];
+      const long long o = r * rs + base;
+      if (((o | ncell) & 3) == 0) {  // four cells a thread: one float4 of e, two double2 of phi
+        for (int c = 4 * threadIdx.x; c < ncell; c += 4 * blockDim.x) {
+          const float4 d = __ldcs(reinterpret_cast<const float4 *>(e + o + c));
+          double2 *p = reinterpret_cast<double2 *>(phi + o + c);
+          double2 u = p[0], w = p[1];
+          u.x += f32_to_f64(d.x);
+          u.y += f32_to_f64(d.y);
+          w.x += f32_to_f64(d.z);
+          w.y += f32_to_f64(d.w);
+          p[0] = u;
+          p[1] = w;
+        }
+      } else {
+        for (int c = threadIdx.x; c < ncell; c += blockDim.x) phi[o + c] += f32_to_f64(e[o + c]);
+      }
     }
   }
 }
@@ -130,6 +128,20 @@ __global__ void k_leaf_accumulate(const int *__restrict__ leaf_ids, const long l
 // the events around each kernel measure the kernel, not the host.
 __global__ void k_delay(int us) {
   for (int i = 0; i < us; i++) __nanosleep(1000);
+}
+
+// Counts where the integer-operation conversions differ bit for bit from
+// the hardware's: bad[0] double -> float (round to nearest even), bad[1]
+// float -> double.
+__global__ void k_selftest_conv(const double *__restrict__ x, const float *__restrict__ f, long long n,
+                                unsigned long long *bad) {
+  unsigned long long b0 = 0, b1 = 0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    b0 += __float_as_uint(f64_to_f32_rn(x[k])) != __float_as_uint(__double2float_rn(x[k]));
+    b1 += __double_as_longlong(f32_to_f64(f[k])) != __double_as_longlong((double)f[k]);
+  }
+  if (b0) atomicAdd(bad, b0);
+  if (b1) atomicAdd(bad + 1, b1);
 }
 
 __global__ void k_to_float(const double *__restrict__ a, float *__restrict__ b, long long n) {
@@ -796,7 +808,7 @@ int residual_impl(gmg_tree *t, cudaStream_t s, float *rout) {
   for (int l = t->lmin; l <= t->lmax; l++) {
     LvArgs L = lv(t, l), Lp = l > t->lmin ? lv(t, l - 1) : L;
     if (!t->level_has_leaves[l - t->lmin]) continue;
-    const size_t sm = tile_bytes<double>(t, l);
+    const size_t sm = resnorm_smem_bytes<double>(D, L.n);
     with_nt<D>(L.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
       launch(t, s, 6, 0, l, [&] {
@@ -806,7 +818,7 @@ int residual_impl(gmg_tree *t, cudaStream_t s, float *rout) {
     });
   }
   launch(t, s, 7, 0, t->lmax, [&] {
-    klaunch(t, t->units(), 1024, 0, s, k_reduce_partials, (const double *)t->d_partials, (int)t->blocks.size(), (const int *)t->d_tree_blocks,
+    klaunch(t, t->units(), kResThreads, 0, s, k_reduce_partials, (const double *)t->d_partials, (int)t->blocks.size(), (const int *)t->d_tree_blocks,
                                                   t->d_tree_boff, t->ntree, t->d_red, t->d_bar);
   });
   CUDA_TRY(cudaGetLastError());
@@ -1824,6 +1836,20 @@ int gmg_get_level_sweeps(const gmg_tree *t, int level, int *n_down, int *n_up) {
   if (!t || level < t->lmin || level > t->lmax) return set_error("level out of range"), GMG_ERR_INVALID_ARG;
   if (n_down) *n_down = t->n_down_at(level);
   if (n_up) *n_up = t->n_up_at(level);
+  return GMG_OK;
+}
+
+int gmg_selftest_conversions(const double *x, const float *f, long long n, unsigned long long *mismatches,
+                             void *stream) {
+  if (n < 0 || (n > 0 && (!x || !f)) || !mismatches) return set_error("bad arguments"), GMG_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  CUDA_TRY(cudaMemsetAsync(mismatches, 0, 2 * sizeof(unsigned long long), s));
+  if (n > 0) {
+    const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+    k_selftest_conv<<<(unsigned)blocks, 256, 0, s>>>(x, f, n, mismatches);
+    CUDA_TRY(cudaGetLastError());
+  }
+  CUDA_TRY(cudaStreamSynchronize(s));
   return GMG_OK;
 }
 

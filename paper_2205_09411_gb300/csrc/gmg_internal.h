@@ -300,13 +300,9 @@ inline int cta_threads(const gmg_tree *t, int l) {
   return t->lev(l).ncell <= 512 ? 64 : 256;
 }
 
-// Threads per CTA of the FP64 residual-norm kernel: 16^3 blocks and larger
-// take 512, so that twice the warps keep the FP64 pipe busy (the residual
-// is bound by FP64 arithmetic).
-inline int resnorm_threads(const gmg_tree *t, int l) {
-  if (t->cta_threads) return t->cta_threads;
-  return t->lev(l).ncell >= 4096 ? 512 : cta_threads(t, l);
-}
+// Threads per CTA of the FP64 residual-norm kernel: as the level kernels
+// (at most 256, so that four CTAs of 16^3 blocks fit an SM).
+inline int resnorm_threads(const gmg_tree *t, int l) { return cta_threads(t, l); }
 
 void set_error(const std::string &msg);
 int build_tree(gmg_tree *T, const gmg_domain *dom);

@@ -13,7 +13,7 @@ namespace gmg {
 
 constexpr int kThreads = 256;      // threads per CTA of the per-level kernels (at most; see cta_threads)
 constexpr int kCoopThreads = 512;  // threads per CTA of the cooperative coarse cycle
-constexpr int kResThreads = 512;   // threads per CTA of the residual-norm kernel (at most)
+constexpr int kResThreads = 256;   // threads per CTA of the residual-norm kernel (at most)
 
 // cells of a block of side n (compile-time when n is)
 #define NCELL (D == 3 ? n * n * n : n * n)
@@ -28,6 +28,59 @@ constexpr int kResThreads = 512;   // threads per CTA of the residual-norm kerne
 __device__ __forceinline__ void pdl_start() {
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
 }
+
+// Conversions between double and float with integer operations.  A
+// hardware conversion of a double runs on the FP64 pipe, which the FP64
+// residual keeps busy (it is that kernel's bound on this GPU); the integer
+// pipes are idle there.  Both give the IEEE 754 results bit for bit.
+//
+// double -> float rounded to nearest, ties to even (IEEE 754
+// roundTiesToEven): for a result in float's normal range, the float keeps
+// the sign, the exponent rebased from bias 1023 to bias 127 and the top 23
+// of the 52 fraction bits; the 29 bits dropped round it up when they exceed
+// half a unit in the last place, or equal it with the kept fraction odd (a
+// carry out of the fraction raises the exponent, to infinity past the
+// largest float).  Zeros keep their sign; results that are subnormal,
+// infinite or NaN take the hardware conversion.
+__device__ __forceinline__ float f64_to_f32_rn(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const unsigned int hi = (unsigned int)(u >> 32), lo = (unsigned int)u;
+  const unsigned int e = (hi >> 20) & 0x7ffu, sign = hi & 0x80000000u;
+  if (e - 897u > 253u) {  // float exponent e - 896 outside [1, 254]
+    if ((hi & 0x7fffffffu) == 0u && lo == 0u) return __uint_as_float(sign);
+    return __double2float_rn(v);
+  }
+  const unsigned int frac = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned int rest = lo & 0x1fffffffu;
+  const unsigned int up = (rest > 0x10000000u || (rest == 0x10000000u && (frac & 1u))) ? 1u : 0u;
+  return __uint_as_float(sign | ((((e - 896u) << 23) | frac) + up));
+}
+
+// float -> double (exact): the exponent rebased from bias 127 to bias 1023,
+// the 23 fraction bits placed at the top of the 52.  Zeros keep their
+// sign; subnormal, infinite and NaN inputs take the hardware conversion.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned int b = __float_as_uint(f);
+  const unsigned int e = (b >> 23) & 0xffu, sign = b & 0x80000000u;
+  if (e - 1u > 253u) {  // not a normal float
+    if ((b & 0x7fffffffu) == 0u) return __hiloint2double((int)sign, 0);
+    return (double)f;
+  }
+  return __hiloint2double((int)(sign | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3)), (int)(b << 29));
+}
+
+// The wall reflection of v (reading W): v itself for a Neumann wall, -v
+// for a Dirichlet wall, by flipping the sign bit on the integer pipes (a
+// double multiply by -1 would queue on the FP64 pipe); exact either way.
+__device__ __forceinline__ float wall_reflect(float v, bool neumann) {
+  return neumann ? v : __int_as_float(__float_as_int(v) ^ (int)0x80000000u);
+}
+__device__ __forceinline__ double wall_reflect(double v, bool neumann) {
+  return neumann ? v : __hiloint2double(__double2hiint(v) ^ (int)0x80000000u, __double2loint(v));
+}
+
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(double v) { return f64_to_f32_rn(v); }
 
 // Position of cell j of a run of whole blocks of level L (the coarsest
 // level's unknowns of one root: blocks one after the other, natural cell
@@ -224,6 +277,15 @@ __host__ __device__ inline size_t level_smem_bytes(int D, int n) {
   return sizeof(T) * (size_t)(tile + nc) + (size_t)((nc + 15) / 16 * 16);
 }
 
+// Shared memory of the residual-norm kernel: the tile and the per-cell
+// flags of a cut block (b is read from global memory, once per cell).
+template <typename T>
+__host__ __device__ inline size_t resnorm_smem_bytes(int D, int n) {
+  const int tile = D == 3 ? TileGeo<T, 3>(n).size : TileGeo<T, 2>(n).size;
+  const int nc = D == 3 ? n * n * n : n * n;
+  return sizeof(T) * (size_t)tile + (size_t)((nc + 15) / 16 * 16);
+}
+
 // The flags of a cut block follow its dense b in shared memory.
 template <typename T>
 __device__ __forceinline__ unsigned char *level_flags(T *sbv, int ncell) {
@@ -363,7 +425,7 @@ __device__ __forceinline__ void load_tile(const GmgView<T> &V, const LvArgs &L, 
     T val;
     if (wall) {
       const int mx = a == 0 ? mn : u, my = a == 1 ? mn : (a == 0 ? u : v), mz = a == 2 ? mn : v;
-      val = (((V.wneu >> f) & 1) ? T(1) : T(-1)) * tile[G.idx(mx, my, mz)];
+      val = wall_reflect(tile[G.idx(mx, my, mz)], (V.wneu >> f) & 1);
     } else {
       const int g[3] = {gx, gy, gz};
       val = refine_ghost<T, D>(V.phi, V.nbr, V.flags, V.parent, V.pofs, V.wneu, L, Lp, bid, g, a, own);
@@ -882,7 +944,7 @@ __device__ __forceinline__ void block_reduce3(double s2, double mx, double b2, d
 // the residual itself is written as float (right-hand side of the FP32
 // correction V-cycle in the mixed path).
 template <typename T, int D, int NT>
-__global__ void __launch_bounds__(kResThreads, 2) k_resnorm(GmgView<T> V0, LvArgs L, LvArgs Lp, double *partials,
+__global__ void __launch_bounds__(kResThreads, 4) k_resnorm(GmgView<T> V0, LvArgs L, LvArgs Lp, double *partials,
                                                       float *rout, int nbt) {
   pdl_start();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -898,15 +960,17 @@ __global__ void __launch_bounds__(kResThreads, 2) k_resnorm(GmgView<T> V0, LvArg
   if (rout) rout += slot * V0.rs_f;
   const int n = NT ? NT : L.n;
   const TileGeo<T, D> G(n);
+  // the tile and a cut block's flags only: up to four CTAs of 16^3 FP64
+  // blocks per SM, so that one CTA's staging overlaps another's arithmetic
   T *tile = reinterpret_cast<T *>(smem_raw);
-  T *sbv = tile + G.size;
-  unsigned char *sfl = level_flags(sbv, NCELL);
+  unsigned char *sfl = reinterpret_cast<unsigned char *>(tile + G.size);
   const long long base = L.off + (long long)(bid - L.first) * NCELL;
+  const T *bg = V.b + base;  // the block's b, colour-split (read once per cell)
   const long long sb = V.st_base[bid];
   const int4 cl = V.cut_list[bid];
   const int m = cl.y + cl.z;
   CutCell<T, D> q;
-  load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv, sfl, sb, [&] {
+  load_tile<T, D, NT>(V, L, Lp, bid, tile, nullptr, sfl, sb, [&] {
     if ((int)threadIdx.x < m) q.fetch(V, cl.x + threadIdx.x);
   });
   const T inv_h2 = T(L.ih2);
@@ -917,7 +981,7 @@ __global__ void __launch_bounds__(kResThreads, 2) k_resnorm(GmgView<T> V0, LvArg
     if (rout) rout[base + cs_pos(c, n, NCELL, D)] = r;
     s2f = fmaf(r, r, s2f);
     mxf = fmaxf(mxf, fabsf(r));
-    const float bf = (float)bb;
+    const float bf = to_f32(bb);
     b2f = fmaf(bf, bf, b2f);
   };
   {  // listed cells first (stored stencils)
@@ -925,8 +989,8 @@ __global__ void __launch_bounds__(kResThreads, 2) k_resnorm(GmgView<T> V0, LvArg
       int x, y, z;
       cell_xyz<D>(u.c, n, &x, &y, &z);
       const int t = G.idx(x, y, z);
-      const T bb = sbv[cs_pos_xyz(x, y, z, n, NCELL)];
-      acc(u.c, (float)(bb - (u.a[0] * tile[t] + offdiag_of<T, D>(u.a, tile, t, G.sy, G.sz))), bb);
+      const T bb = __ldg(bg + cs_pos_xyz(x, y, z, n, NCELL));
+      acc(u.c, to_f32(bb - (u.a[0] * tile[t] + offdiag_of<T, D>(u.a, tile, t, G.sy, G.sz))), bb);
     };
     const int i = threadIdx.x, bd = blockDim.x;
     if (i < m) res(q);
@@ -940,16 +1004,16 @@ __global__ void __launch_bounds__(kResThreads, 2) k_resnorm(GmgView<T> V0, LvArg
     if (sb >= 0 && sfl[c]) continue;
     int x, y, z;
     cell_xyz<D>(c, n, &x, &y, &z);
-    const T bb = sbv[cs_pos_xyz(x, y, z, n, NCELL)];
-    acc(c, (float)resid_cell<T, D>(nullptr, -1, tile, G.idx(x, y, z), G.sy, G.sz, NCELL, c, inv_h2, bb), bb);
+    const T bb = __ldg(bg + cs_pos_xyz(x, y, z, n, NCELL));
+    acc(c, to_f32(resid_cell<T, D>(nullptr, -1, tile, G.idx(x, y, z), G.sy, G.sz, NCELL, c, inv_h2, bb)), bb);
   }
   block_reduce3((double)s2f, (double)mxf, (double)b2f, partials);
 }
 
 // Deterministic final reduction of the per-block partials (fixed order),
 // one CTA per unit (slot, tree).
-__global__ void __launch_bounds__(1024) k_reduce_partials(const double *partials, int nb, const int *tree_blocks,
-                                                          const int *tree_boff, int ntree, double *out,
-                                                          const GridBar *bar);
+__global__ void __launch_bounds__(kResThreads) k_reduce_partials(const double *partials, int nb, const int *tree_blocks,
+                                                                 const int *tree_boff, int ntree, double *out,
+                                                                 const GridBar *bar);
 
 }  // namespace gmg

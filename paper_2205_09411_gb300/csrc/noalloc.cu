@@ -25,29 +25,18 @@ __device__ __align__(256) double g_noalloc_scratch[3 * kNoAllocMaxBlocks + 2];
 // Fixed-order reduction of the partials held in the scratch array (slot 0
 // of a tree with several right-hand-side slots); writes
 // ||r||_2 / ||b||_2 (or ||r||_2 when b = 0) and max |r| to out[0], out[1].
-__global__ void __launch_bounds__(1024) k_reduce_noalloc(int nb, double *out) {
-  __shared__ double s[3][1024];
+__global__ void __launch_bounds__(gmg::kResThreads) k_reduce_noalloc(int nb, double *out) {
+  __shared__ double s[3];
   double a = 0.0, b = 0.0, c = 0.0;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
     a += g_noalloc_scratch[(size_t)i * 3];
     b = fmax(b, g_noalloc_scratch[(size_t)i * 3 + 1]);
     c += g_noalloc_scratch[(size_t)i * 3 + 2];
   }
-  s[0][threadIdx.x] = a;
-  s[1][threadIdx.x] = b;
-  s[2][threadIdx.x] = c;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      s[0][threadIdx.x] += s[0][threadIdx.x + w];
-      s[1][threadIdx.x] = fmax(s[1][threadIdx.x], s[1][threadIdx.x + w]);
-      s[2][threadIdx.x] += s[2][threadIdx.x + w];
-    }
-    __syncthreads();
-  }
+  gmg::block_reduce3(a, b, c, s);
   if (threadIdx.x == 0) {
-    out[0] = s[2][0] > 0.0 ? sqrt(s[0][0] / s[2][0]) : sqrt(s[0][0]);
-    out[1] = s[1][0];
+    out[0] = s[2] > 0.0 ? sqrt(s[0] / s[2]) : sqrt(s[0]);
+    out[1] = s[1];
   }
 }
 
@@ -140,7 +129,7 @@ void launch_resnorm(gmg_tree *t, int l, double *partials, const int *active, cud
     const gmg::LevelInfo &Pi = t->lev(l - 1);
     Lp = gmg::LvArgs{Pi.first, Pi.count, Pi.n, Pi.ncell, Pi.off, Pi.h, Pi.off, 0, 0, Pi.h * Pi.h, 1.0 / (Pi.h * Pi.h)};
   }
-  const size_t sm = gmg::level_smem_bytes<double>(D, Li.n);
+  const size_t sm = gmg::resnorm_smem_bytes<double>(D, Li.n);
   gmg::k_resnorm<double, D, NT><<<L.count, gmg::resnorm_threads(t, l), sm, s>>>(V, L, Lp, partials, nullptr,
                                                                   (int)t->blocks.size());
 }
@@ -185,7 +174,7 @@ extern "C" int gmg_residual_noalloc(gmg_tree *t, double *out, void *stream) {
     else
       launch_resnorm_any<2>(t, l, scratch, st.active, s);
   }
-  k_reduce_noalloc<<<1, 1024, 0, s>>>((int)nb, out);
+  k_reduce_noalloc<<<1, gmg::kResThreads, 0, s>>>((int)nb, out);
   e = cudaGetLastError();
   if (e != cudaSuccess) return gmg::set_error(std::string("kernel launch: ") + cudaGetErrorString(e)), GMG_ERR_CUDA;
   return GMG_OK;
