@@ -245,7 +245,7 @@ def algorithmic_bytes(kind, prec, level, t, leaf_level, nrhs=1, cluster=False):
         nb0, n0, _ = t.level_info(t.lmin)
         return tot + nb0 * (n0 ** D) ** 2 * 8  # coarsest-level inverses, once
     nb, n, _ = t.level_info(level)
-    cells = nb * n ** 3 * nrhs
+    cells = nb * n ** D * nrhs
     # the cut lists: each listed cell (stencil differs from the regular one)
     # brings its 7 coefficients and its 4-byte index, read once for all slots
     listed = int(t.cut_counts(level).sum())
@@ -263,6 +263,22 @@ def algorithmic_bytes(kind, prec, level, t, leaf_level, nrhs=1, cluster=False):
     if kind == "accumulate":  # read e32, read/write phi64 on the leaf cells of all levels
         return t.n_leaf_cells * nrhs * 20
     return 0
+
+
+# FP64 arithmetic of this GPU: 152 SMs x 2070 MHz x 2 FP64 FMAs (4 flops) a
+# clock per SM = 1.259 TFLOP/s, the nominal 1.25 TFLOP/s (ncu: the FP64 pipe
+# takes 16 cycles per warp instruction per SM, i.e. 2 thread operations a
+# clock).
+FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
+
+
+def residual_flops(t, level, nrhs):
+    """Algorithmic FP64 flops of one residual launch: per cell the sum of
+    the 2D neighbours (2D - 1 adds), phi_sum - 2D phi (one FMA) and b - h^-2
+    (...) (one FMA), an FMA counted as 2 flops: 9 in 3D, 7 in 2D."""
+    nb, n, _ = t.level_info(level)
+    D = t.dim
+    return nb * n ** D * nrhs * ((2 * D - 1) + 4)
 
 
 def source_hash():
@@ -397,6 +413,15 @@ def roofline_of(prof, t, nrhs, peak, peak_kind):
             "per_launch_us": per_launch_ms * 1e3, "algorithmic_bytes": alg,
             "share_of_kernel_time": by_kind[(dom_kind, dom_prec)] / prof_total,
             "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind}
+    if dom_kind == "resid_norm" and dom_prec == "fp64":
+        # bound by the FP64 pipe, not by HBM: flops against the FP64 peak
+        fl = residual_flops(t, lev, nrhs)
+        tf = fl / (per_launch_ms * 1e-3) / 1e12
+        roof.update({"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": tf / FP64_PEAK_TFLOPS, "algorithmic_flops": fl,
+                     "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak},
+                     "peak_source": "derived: 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM (the nominal 1.25 TFLOP/s); "
+                                    "5 adds and 2 FMAs per cell can fill at most 9/14 of it"})
     return roof, by_kind
 
 

@@ -73,3 +73,21 @@ def test_roofline_of_picks_the_dominant_kernel():
     assert roof["achieved"] == pytest.approx(alg / per_launch_s / 1e9)
     assert roof["frac"] == pytest.approx(roof["achieved"] / 6784.2)
     assert roof["share_of_kernel_time"] == pytest.approx(0.080 / 0.140)
+
+
+def test_fp64_residual_roofline_is_against_the_fp64_pipe():
+    """When the FP64 residual dominates, its roofline counts its algorithmic
+    FP64 flops (9 a cell in 3D: 5 adds, 2 FMAs) against the FP64 peak of
+    152 SMs x 2070 MHz x 4 flops a clock, and keeps the HBM figures beside."""
+    t = FakeTree()
+    prof = [("smooth", "fp32", 2, 8, 0.020), ("resid_norm", "fp64", 2, 2, 0.100)]
+    roof, _ = bench.roofline_of(prof, t, 3, 6784.2, "measured")
+    assert roof["kernel"] == "resid_norm_fp64_level2" and roof["bound"] == "alu" and roof["unit"] == "TFLOP/s"
+    per_launch_s = 0.100 / 2 * 1e-3
+    flops = 3 * 64 * 4096 * 9
+    assert roof["algorithmic_flops"] == flops
+    assert roof["achieved"] == pytest.approx(flops / per_launch_s / 1e12)
+    assert roof["peak"] == pytest.approx(152 * 2.07e9 * 4 / 1e12)
+    assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"])
+    alg = bench.algorithmic_bytes("resid_norm", "fp64", 2, t, 2, nrhs=3)
+    assert roof["hbm"]["achieved"] == pytest.approx(alg / per_launch_s / 1e9)
