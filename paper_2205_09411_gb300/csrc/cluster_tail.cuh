@@ -291,11 +291,16 @@ __device__ __forceinline__ void oct_smooth(const Oct<T, D> &Q, int color, int wn
 
 // Residual of F restricted into C: phi_C <- mean phi_F, b_C <- mean r_F
 // (the children of a coarse cell of this part lie in this part).  F's ghost
-// ring must be current.  When C is a full level and F is split, the coarse
-// cells go to the part's place in C, in this CTA's copy and in every other
-// CTA's (P CTAs, rank: this CTA), so that each CTA holds all of C.
+// ring must be current.  FP32: one thread per fine cell, the 2^D children
+// of a coarse cell on 2^D consecutive lanes (child d = dx + 2 dy + 4 dz),
+// the group's first lane summing them in the order of d, as the block
+// kernels do (FP64: one thread per coarse cell, the same order).  When C is a full level and F is split, the coarse cells go to the
+// part's place in C, in this CTA's copy and in every other CTA's (P CTAs,
+// rank: this CTA; the group's lanes share the remote stores), so that each
+// CTA holds all of C.
 template <typename T, int D>
 __device__ __forceinline__ void oct_resid_restrict(const Oct<T, D> &F, const Oct<T, D> &C, int rank, int P) {
+  constexpr int G = 1 << D;
   const int m0 = F.m[0], m1 = F.m[1];
   const int R = m0 + 2, sz = R * (m1 + 2);
   const int h0 = m0 / 2, h1 = m1 / 2, h2 = D == 3 ? F.m[2] / 2 : 1;
@@ -304,35 +309,82 @@ __device__ __forceinline__ void oct_resid_restrict(const Oct<T, D> &F, const Oct
   const bool bcast = C.full && !F.full;
   const int co[3] = {bcast ? F.o[0] / 2 : 0, bcast ? F.o[1] / 2 : 0, bcast ? F.o[2] / 2 : 0};
   const bool p2 = F.lg[0] >= 1;
-  for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+  if constexpr (sizeof(T) == 8) {
+    // FP64: one thread per coarse cell.  A warp's FP64 instruction costs the
+    // pipe the same however few of its lanes are on, so summing on one lane
+    // of eight would multiply the adds' cost by eight.
+    for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+      const int r = p2 ? j >> (F.lg[0] - 1) : j / h0;
+      const int qx = j - r * h0;
+      const int qy = p2 ? r & (h1 - 1) : r % h1;
+      const int qz = D == 3 ? (p2 ? r >> (F.lg[1] - 1) : r / h1) : 0;
+      T sp = T(0), sr = T(0);
+#pragma unroll
+      for (int d = 0; d < G; d++) {
+        const int x = 2 * qx + (d & 1), y = 2 * qy + ((d >> 1) & 1), z = 2 * qz + (D == 3 ? d >> 2 : 0);
+        const int c = x + m0 * (y + m1 * z);
+        const int t = oct_ti(F, x, y, z);
+        sp = sp + F.tile[t];
+        int e;
+        const bool cut = oct_cut(F, c, &e);
+        sr = sr + resid_cell<T, D>(F.cf, cut ? 0 : -1, F.tile, t, R, sz, F.mm, e, inv_h2, F.b[c]);
+      }
+      const int X = co[0] + qx, Y = co[1] + qy, Z = co[2] + qz;
+      const int ti = oct_ti(C, X, Y, Z), ci = X + C.m[0] * (Y + C.m[1] * Z);
+      C.tile[ti] = sp * w;
+      C.b[ci] = sr * w;
+      if (bcast)
+        for (int k = 1; k < P; k++) {
+          const int rk = rank ^ k;
+          peer(C.tile, rk)[ti] = sp * w;
+          peer(C.b, rk)[ci] = sr * w;
+        }
+    }
+    return;
+  }
+  const int lane = threadIdx.x & 31, d = lane & (G - 1), lead = lane & ~(G - 1);
+  const int dx = d & 1, dy = (d >> 1) & 1, dz = D == 3 ? d >> 2 : 0;
+  for (int base = 0; base < nc * G; base += blockDim.x) {  // the same trip count in every thread
+    const int i = base + (int)threadIdx.x;
+    const bool on = i < nc * G;
+    const int j = on ? i >> D : 0;
     const int r = p2 ? j >> (F.lg[0] - 1) : j / h0;
     const int qx = j - r * h0;
     const int qy = p2 ? r & (h1 - 1) : r % h1;
     const int qz = D == 3 ? (p2 ? r >> (F.lg[1] - 1) : r / h1) : 0;
+    T vp = T(0), vr = T(0);
+    if (on) {
+      const int x = 2 * qx + dx, y = 2 * qy + dy, z = 2 * qz + dz;
+      const int c = x + m0 * (y + m1 * z);
+      const int t = oct_ti(F, x, y, z);
+      vp = F.tile[t];
+      int e;
+      const bool cut = oct_cut(F, c, &e);
+      vr = resid_cell<T, D>(F.cf, cut ? 0 : -1, F.tile, t, R, sz, F.mm, e, inv_h2, F.b[c]);
+    }
+    // the group's first lane sums, then hands the means back to the group
     T sp = T(0), sr = T(0);
 #pragma unroll
-    for (int dz = 0; dz < (D == 3 ? 2 : 1); dz++)
-#pragma unroll
-      for (int dy = 0; dy < 2; dy++)
-#pragma unroll
-        for (int dx = 0; dx < 2; dx++) {
-          const int x = 2 * qx + dx, y = 2 * qy + dy, z = 2 * qz + dz;
-          const int c = x + m0 * (y + m1 * z);
-          const int t = oct_ti(F, x, y, z);
-          sp = sp + F.tile[t];
-          int e;
-          const bool cut = oct_cut(F, c, &e);
-          sr = sr + resid_cell<T, D>(F.cf, cut ? 0 : -1, F.tile, t, R, sz, F.mm, e, inv_h2, F.b[c]);
-        }
+    for (int k = 0; k < G; k++) {
+      const T tp = __shfl_sync(0xffffffffu, vp, lead + k), tr = __shfl_sync(0xffffffffu, vr, lead + k);
+      if (d == 0) {
+        sp = sp + tp;
+        sr = sr + tr;
+      }
+    }
+    const T cpv = __shfl_sync(0xffffffffu, sp * w, lead), crv = __shfl_sync(0xffffffffu, sr * w, lead);
+    if (!on) continue;
     const int X = co[0] + qx, Y = co[1] + qy, Z = co[2] + qz;
     const int ti = oct_ti(C, X, Y, Z), ci = X + C.m[0] * (Y + C.m[1] * Z);
-    C.tile[ti] = sp * w;
-    C.b[ci] = sr * w;
+    if (d == 0) {
+      C.tile[ti] = cpv;
+      C.b[ci] = crv;
+    }
     if (bcast)
-      for (int k = 1; k < P; k++) {
+      for (int k = 1 + d; k < P; k += G) {
         const int rk = rank ^ k;
-        peer(C.tile, rk)[ti] = sp * w;
-        peer(C.b, rk)[ci] = sr * w;
+        peer(C.tile, rk)[ti] = cpv;
+        peer(C.b, rk)[ci] = crv;
       }
   }
 }
@@ -495,14 +547,6 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_cycle_cluster(GmgView<T>
     oct_xyz(Qlo, c, &x, &y, &z);
     return (Qlo.o[0] + x) + Qlo.N * ((Qlo.o[1] + y) + (D == 3 ? Qlo.N * (Qlo.o[2] + z) : 0));
   };
-  if (A.stage_rows) {
-    double *rows = reinterpret_cast<double *>(smem_raw + A.off_rows);
-    for (int i = threadIdx.x; i < nlo * A.ncr; i += blockDim.x) {
-      const int c = i / A.ncr, j = i - c * A.ncr;
-      cp_async_elem(rows + i, cinv + (size_t)row_of(c) * A.ncr + j);
-    }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-  }
   // cut lists: per cell of the part its entry, and the blocks' coefficients
   for (int i = 0; i < ntl; i++) {
     const Oct<T, D> &q = Qs[i];
@@ -511,26 +555,59 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_cycle_cluster(GmgView<T>
     for (int c = threadIdx.x; c < nc; c += blockDim.x) q.eidx[c] = 0;
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < s_ecum[ntl]; k += blockDim.x) {  // every entry of every level
+  const int ne = s_ecum[ntl];  // entries of every level
+  auto entry = [&](int k, int *lvl, int *e) {
     int i = 0;
     while (k >= s_ecum[i + 1]) i++;
+    *lvl = i;
+    *e = k - s_ecum[i];
+  };
+  // the coefficients: copies all in flight together
+  for (int k = threadIdx.x; k < ne; k += blockDim.x) {
+    int i, e;
+    entry(k, &i, &e);
     const Oct<T, D> &q = Qs[i];
-    const int e = k - s_ecum[i], ge = s_e0[i] + e;
-    const int c = V.cut_cell[ge];
-    T cf[2 * D + 1];
+    const int ge = s_e0[i] + e;
 #pragma unroll
-    for (int kk = 0; kk < 2 * D + 1; kk++) cf[kk] = V.cut_coef[kk * V.n_cut + ge];
+    for (int kk = 0; kk < 2 * D + 1; kk++) cp_async_elem(q.cf + kk * q.mm + e, V.cut_coef + (size_t)kk * V.n_cut + ge);
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  if (A.stage_rows) {
+    double *rows = reinterpret_cast<double *>(smem_raw + A.off_rows);
+    for (int i = threadIdx.x; i < nlo * A.ncr; i += blockDim.x) {
+      const int c = i / A.ncr, j = i - c * A.ncr;
+      cp_async_elem(rows + i, cinv + (size_t)row_of(c) * A.ncr + j);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
+  // the entries' cells, kEntryBatch a thread at a time (their reads overlap)
+  constexpr int kEntryBatch = 4;
+  for (int k0 = threadIdx.x; k0 < ne; k0 += kEntryBatch * blockDim.x) {
+    int cells[kEntryBatch];
 #pragma unroll
-    for (int kk = 0; kk < 2 * D + 1; kk++) q.cf[kk * q.mm + e] = cf[kk];
-    // the entry's cell in cube coordinates (the block's origin plus its
-    // place in the block); is it in this part?
-    int X, Y, Z;
-    cell_xyz_rt<D>(c, q.nblk, &X, &Y, &Z);
-    const int x = X + (q.o[0] / q.nblk) * q.nblk - q.o[0];
-    const int y = Y + (q.o[1] / q.nblk) * q.nblk - q.o[1];
-    const int z = D == 3 ? Z + (q.o[2] / q.nblk) * q.nblk - q.o[2] : 0;
-    if (x >= 0 && x < q.m[0] && y >= 0 && y < q.m[1] && z >= 0 && z < q.m[2])
-      q.eidx[x + q.m[0] * (y + q.m[1] * z)] = (unsigned short)(e + 1);
+    for (int u = 0; u < kEntryBatch; u++) {
+      const int k = k0 + u * (int)blockDim.x;
+      int i = 0, e = 0;
+      if (k < ne) entry(k, &i, &e);
+      cells[u] = k < ne ? V.cut_cell[s_e0[i] + e] : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < kEntryBatch; u++) {
+      const int k = k0 + u * (int)blockDim.x;
+      if (k >= ne) continue;
+      int i, e;
+      entry(k, &i, &e);
+      const Oct<T, D> &q = Qs[i];
+      // the entry's cell in cube coordinates (the block's origin plus its
+      // place in the block); is it in this part?
+      int X, Y, Z;
+      cell_xyz_rt<D>(cells[u], q.nblk, &X, &Y, &Z);
+      const int x = X + (q.o[0] / q.nblk) * q.nblk - q.o[0];
+      const int y = Y + (q.o[1] / q.nblk) * q.nblk - q.o[1];
+      const int z = D == 3 ? Z + (q.o[2] / q.nblk) * q.nblk - q.o[2] : 0;
+      if (x >= 0 && x < q.m[0] && y >= 0 && y < q.m[1] && z >= 0 && z < q.m[2])
+        q.eidx[x + q.m[0] * (y + q.m[1] * z)] = (unsigned short)(e + 1);
+    }
   }
   if (A.stage_rows)
     asm volatile("cp.async.wait_group 1;\n" ::: "memory");
