@@ -232,6 +232,10 @@ def algorithmic_bytes(kind, prec, level, t, leaf_level, nrhs=1, cluster=False):
     the bottom (cluster=True) the cooperative kernel runs twice per cycle
     (down and up leg) and each launch counts half of its levels' bytes."""
     S = 8 if prec == "fp64" else 4
+    # BF16 storage (GMG_MIXED_BF16's finest level): phi 2 bytes, b and the
+    # coarser level's fields 4 bytes
+    Sp = 2 if prec == "bf16" else S
+    Sc = 4 if prec == "bf16" else S
     D = t.dim
     if kind in ("coarse_solve", "coarse_cluster"):
         top = cluster_top(t) if cluster else t.lmin - 1
@@ -250,17 +254,22 @@ def algorithmic_bytes(kind, prec, level, t, leaf_level, nrhs=1, cluster=False):
     # brings its 7 coefficients and its 4-byte index, read once for all slots
     listed = int(t.cut_counts(level).sum())
     entry = 7 * S + 4
+    if prec == "bf16":
+        entry = 7 * 4 + 4
     if kind == "smooth":  # read the other colour's phi, read b and write phi of one colour; one colour's list
-        return cells * 1.5 * S + listed * entry / 2
+        return cells * (Sp + 0.5 * Sc) + listed * entry / 2
     if kind == "resid_restrict":  # read phi, b; write parent phi, b
-        return cells * (2 * S + 2 * S / 8) + listed * entry
+        return cells * (Sp + Sc + 2 * Sc / 8) + listed * entry
     if kind == "prolong":  # read/write phi, read parent phi, old
-        return cells * (2 * S + 2 * S / 8)
+        return cells * (2 * Sp + 2 * Sc / 8)
     if kind == "fas_rhs":  # read phi, b; write b, old
         return cells * 4 * S + listed * entry
     if kind == "resid_norm":  # read phi64, b64 (+ write r32 in the mixed path)
         return cells * (16 + 4) + listed * (7 * 8 + 4)
     if kind == "accumulate":  # read e32, read/write phi64 on the leaf cells of all levels
+        if prec == "bf16":  # the finest level's e as BF16 (all its blocks are leaves)
+            nbl, nl, _ = t.level_info(t.lmax)
+            return nrhs * (t.n_leaf_cells * 20 - nbl * nl ** D * 2)
         return t.n_leaf_cells * nrhs * 20
     return 0
 
@@ -425,6 +434,22 @@ def roofline_of(prof, t, nrhs, peak, peak_kind):
     return roof, by_kind
 
 
+def finest_roofline(prof, t, nrhs, peak, peak_kind):
+    """HBM roofline of the finest level's half-sweep in a profiled pass (its
+    BF16 variant when the pass ran GMG_MIXED_BF16 on that level, else the
+    FP32 one): algorithmic bytes per launch / CUDA-event time per launch."""
+    rows = [r for r in prof if r[0] == "smooth" and r[2] == t.lmax and r[1] in ("bf16", "fp32")]
+    if not rows:
+        return None
+    row = max(rows, key=lambda r: (r[1] == "bf16", r[4]))
+    per_launch_ms = row[4] / row[3]
+    alg = algorithmic_bytes("smooth", row[1], t.lmax, t, t.lmax, nrhs)
+    achieved = alg / (per_launch_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "smooth_%s_level%d" % (row[1], t.lmax), "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "per_launch_us": per_launch_ms * 1e3,
+            "algorithmic_bytes": alg, "peak_source": peak_kind}
+
+
 def run_needle(G, args, world, flush, stream):
     """Batched needle workload: the adaptive 7-level needle tree (8^3
     blocks, 30,195,712 leaf cells) with 32 Gaussian-charge right-hand sides
@@ -474,7 +499,7 @@ def run_needle(G, args, world, flush, stream):
         return e0.elapsed_time(e1), st, t.last_launch_count() + 1, prof
 
     res = {}
-    for name, prec in (("mixed", G.MIXED), ("fp64", G.FP64)):
+    for name, prec in (("mixed", G.MIXED), ("mixed_bf16", G.MIXED_BF16), ("fp64", G.FP64)):
         one(prec)  # warm-up (graph capture)
         barrier(world)
         times, cyc, worst, launches = [], 0, 0.0, 0
@@ -486,19 +511,25 @@ def run_needle(G, args, world, flush, stream):
             launches += nl
         total = allreduce_max(sum(times), world)
         ts = sorted(times)
-        vc = cyc * (sched.inner_cycles if prec == G.MIXED else 1)  # V-cycles (FP32 ones in the mixed path)
+        vc = cyc * (sched.inner_cycles if prec != G.FP64 else 1)  # V-cycles (FP32 ones in the mixed path)
         res[name] = {"p50_ms": float(np.percentile(ts, 50)), "p99_ms": float(np.percentile(ts, 99)),
                      "solves_per_s": world * R * len(ts) / (total * 1e-3),
                      "munks": world * n * vc / (total * 1e-3) / 1e6,
                      "steps_per_solve": cyc / (R * len(ts)), "v_cycles_per_solve": vc / (R * len(ts)),
                      "worst_final_rel_residual": worst, "gpu_launches_per_batch": launches / len(ts)}
     _, _, _, prof = one(G.MIXED, profile=True)
+    _, _, _, prof_bf = one(G.MIXED_BF16, profile=True)
     peak, peak_kind = peaks()
     roof, by_kind = roofline_of(prof, t, R, peak, peak_kind)
+    roof_bf, _ = roofline_of(prof_bf, t, R, peak, peak_kind)
+    res["mixed_bf16"]["roofline"] = roof_bf
+    res["mixed_bf16"]["finest_level_kernels_us_per_launch"] = {
+        "%s_%s_l%d" % (k, p_, lv): round(ms * 1e3 / cnt, 2) for k, p_, lv, cnt, ms in prof_bf if p_ == "bf16"}
+    res["mixed_bf16"]["finest_level_roofline"] = finest_roofline(prof_bf, t, R, peak, peak_kind)
     out = {"workload": "needle3d_adaptive_7levels_8^3blocks_%drhs_gaussian_mixed_to_1e-8" % R, "unknowns": n,
            "rhs": R, "blocks": t.n_blocks, "levels": [t.lmin, t.lmax], "setup_s": setup_s,
            "latency_is": "one batched solve of all %d right-hand sides from phi = 0" % R,
-           "mixed": res["mixed"], "fp64": res["fp64"], "roofline": roof,
+           "mixed": res["mixed"], "mixed_bf16": res["mixed_bf16"], "fp64": res["fp64"], "roofline": roof,
            "autotuned": {"fine_sweeps": list(sched.fine_sweeps), "coarse_sweeps": list(sched.coarse_sweeps),
                          "inner_cycles": sched.inner_cycles, "slots_per_cta": sched.slots_per_cta,
                          "trials": len(sched.trials), "tuning_s": tune_s},
@@ -586,7 +617,7 @@ def run_forest(G, args, world, flush, stream):
     sizes = [q["n"] for q in qs]
     del trees
     res = {}
-    for name, prec in (("mixed", G.MIXED), ("fp64", G.FP64)):
+    for name, prec in (("mixed", G.MIXED), ("mixed_bf16", G.MIXED_BF16), ("fp64", G.FP64)):
         F.set_rhs(g)
         F.solve(prec, args.tol, 80)  # warm-up (graph capture)
         barrier(world)
@@ -602,7 +633,7 @@ def run_forest(G, args, world, flush, stream):
             times.append(e0.elapsed_time(e1))
             for i, u in enumerate(st["units"]):
                 off, cnt = F.tree_leaves(i)
-                munk_cyc += cnt * u["cycles"] * (best.inner_cycles if prec == G.MIXED else 1)
+                munk_cyc += cnt * u["cycles"] * (best.inner_cycles if prec != G.FP64 else 1)
             worst = max(worst, st["rel_l2"])
         total = allreduce_max(sum(times), world)
         ts = sorted(times)
@@ -610,14 +641,19 @@ def run_forest(G, args, world, flush, stream):
                      "solves_per_s": world * 64 * len(ts) / (total * 1e-3),
                      "munks": world * munk_cyc / (total * 1e-3) / 1e6,
                      "worst_final_rel_residual": worst}
-    F.profile(True)
-    F.profile_read()
-    F.set_rhs(g)
-    F.solve(G.MIXED, args.tol, 80)
-    prof = F.profile_read()
-    F.profile(False)
+    profs = {}
+    for prec in (G.MIXED, G.MIXED_BF16):
+        F.profile(True)
+        F.profile_read()
+        F.set_rhs(g)
+        F.solve(prec, args.tol, 80)
+        profs[prec] = F.profile_read()
+        F.profile(False)
+    prof = profs[G.MIXED]
     peak, peak_kind = peaks()
     roof, by_kind = roofline_of(prof, F, 1, peak, peak_kind)
+    res["mixed_bf16"]["finest_level_roofline"] = finest_roofline(profs[G.MIXED_BF16], F, 1, peak, peak_kind)
+    res["mixed_bf16"]["finest_level_roofline_fp32_state"] = finest_roofline(prof, F, 1, peak, peak_kind)
     out = {"workload": "forest_64_uniform_trees_32^3-256^3_ellipsoids_mixed_to_1e-8", "unknowns": n,
            "trees": 64, "tree_sizes": {str(k): sizes.count(k) for k in sorted(set(sizes))},
            "latency_is": "one solve of all 64 problems (each to its own 1e-8) from phi = 0",
@@ -627,7 +663,8 @@ def run_forest(G, args, world, flush, stream):
                          "inner_cycles": best.inner_cycles,
                          "tuning_s": tune_s, "trials": len(best.trials),
                          "sample": "8 problems of the same distribution (seed index 4), tiles 8 and 16"},
-           "setup_s": setup_s, "setup_parts": setup_parts, "mixed": res["mixed"], "fp64": res["fp64"], "roofline": roof,
+           "setup_s": setup_s, "setup_parts": setup_parts, "mixed": res["mixed"], "mixed_bf16": res["mixed_bf16"],
+           "fp64": res["fp64"], "roofline": roof,
            "kernel_ms_by_kind": {"%s_%s" % k: v for k, v in sorted(by_kind.items(), key=lambda kv: -kv[1])}}
     F.close()
     del g
@@ -886,6 +923,10 @@ def run_ours(args):
     clk = clocks.stop()
     fp64 = timed(G.FP64)
     e2e = timed(G.MIXED, e2e=True)
+    for _ in range(args.warmup):
+        solve(G.MIXED_BF16)
+    bf16 = timed(G.MIXED_BF16)
+    bf16["prof"] = timed(G.MIXED_BF16, profile=True)["prof"]
     # kernel durations: the same steps again with CUDA events around every
     # kernel (each phase is queued behind a short delay kernel, so the events
     # time the kernels and not the host)
@@ -913,6 +954,11 @@ def run_ours(args):
                    "setup_s": t_setup},
         "mixed": lat(mixed) | {"munks": munks(mixed), "final_rel_residual": mixed["rel"]},
         "fp64": lat(fp64) | {"munks": munks(fp64), "final_rel_residual": fp64["rel"]},
+        "mixed_bf16": lat(bf16) | {"munks": munks(bf16), "final_rel_residual": bf16["rel"],
+                                   "finest_level_roofline": finest_roofline(bf16["prof"], t, 1, peak, peak_kind),
+                                   "finest_level_kernels_us_per_launch": {
+                                       "%s_%s_l%d" % (k, p_, lv): round(ms * 1e3 / cnt, 2)
+                                       for k, p_, lv, cnt, ms in bf16["prof"] if p_ == "bf16"}},
         "e2e": {"value": munks(e2e), "unit": UNIT, "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
         "gpu_launches": mixed["launches"],
         "roofline": roofline,

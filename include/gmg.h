@@ -82,6 +82,21 @@ extern "C" {
 #define GMG_FP64 0  /* FAS V-cycles in FP64                                            */
 #define GMG_MIXED 1 /* FP64 defect correction around FP32 V-cycles; the fine residual,
                        the solution update and the coarsest-level solve stay in FP64  */
+#define GMG_MIXED_BF16 2 /* GMG_MIXED with the FP32 correction's state (e) on the finest
+                       level stored as BF16: 2 bytes a cell instead of 4 in the sweeps,
+                       restriction, prolongation and accumulation of that level; the
+                       arithmetic stays FP32, b stays FP32, and every result written
+                       to the level is rounded to BF16 (nearest, ties to even).  The
+                       BF16 values live in that level's part of the second FP32 buffer
+                       of the workspace (no extra memory).  A tree whose finest level
+                       runs inside the coarse cooperative or cluster kernels, or whose
+                       block side has no compiled kernel (3D: 4, 8, 16; 2D: 8, 16,
+                       32), runs GMG_MIXED instead.  The BF16 rounding limits what one
+                       correction can reduce (a few 1e-3 relative), so a step can
+                       reduce the residual less than a GMG_MIXED step; the solve still
+                       ends at the requested FP64 residual, checked in FP64.  No
+                       counterpart in the paper (Sec. 2.2 gives the smoother and
+                       transfers in one precision). */
 
 /* where a caller's array lives.  A GMG_HOST array in page-locked memory
  * mapped into the device's address space (cudaHostAlloc, cudaHostRegister,
@@ -376,7 +391,8 @@ long long gmg_last_launch_count(const gmg_tree *tree);
 /* Kernel timing: while enabled, every kernel the tree enqueues is bracketed
  * by CUDA events on its stream.  gmg_profile_read synchronises, aggregates
  * the recorded launches per (kernel kind, precision, level) into the caller's
- * arrays (up to `cap` entries: kind, prec 0 = FP64 / 1 = FP32, level,
+ * arrays (up to `cap` entries: kind, prec 0 = FP64 / 1 = FP32 / 2 = FP32
+ * arithmetic on BF16 storage (GMG_MIXED_BF16's finest level), level,
  * launches, total milliseconds), clears the record and returns the number of
  * entries (or a negative error).  Kinds: 0 smooth, 1 residual+restrict,
  * 2 FAS right-hand side, 3 coarse solve, 4 prolongation, 5 restriction of

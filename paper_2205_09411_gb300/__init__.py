@@ -17,10 +17,10 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Tree", "Forest", "load", "build", "GmgError", "FP64", "MIXED", "LIB_PATH"]
+__all__ = ["Tree", "Forest", "load", "build", "GmgError", "FP64", "MIXED", "MIXED_BF16", "LIB_PATH"]
 
 LIB_PATH = _build.LIB
-FP64, MIXED = 0, 1
+FP64, MIXED, MIXED_BF16 = 0, 1, 2
 HOST, DEVICE = 0, 1
 WALL_DIRICHLET, WALL_NEUMANN = 0, 1
 LSF_KINDS = {"none": 0, "sphere": 1, "capsule": 2, "ellipsoid": 3, "callback": 4, "shape": 5, "grid": 6}
@@ -602,7 +602,8 @@ class Tree:
                                       ms.ctypes.data_as(C.POINTER(C.c_double)))
         if cnt < 0:
             _check(cnt)
-        return [(self.KERNEL_KINDS[k[i]], "fp64" if p[i] == 0 else "fp32", int(lv[i]), int(n[i]), float(ms[i]))
+        names = {0: "fp64", 1: "fp32", 2: "bf16"}
+        return [(self.KERNEL_KINDS[k[i]], names[int(p[i])], int(lv[i]), int(n[i]), float(ms[i]))
                 for i in range(cnt)]
 
 

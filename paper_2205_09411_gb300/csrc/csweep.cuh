@@ -41,9 +41,99 @@ struct CsGeo {
   }
 };
 
-template <typename T, int D, int NT>
+// BF: the other colour's tile holds BF16 values (the finest level of
+// GMG_MIXED_BF16); b stays T.
+template <typename T, int D, int NT, bool BF = false>
 inline size_t cs_smem_bytes(int sg) {
-  return CsGeo<T, D, NT>::smem_bytes(sg);
+  if (!BF) return CsGeo<T, D, NT>::smem_bytes(sg);
+  using G = CsGeo<bf16s, D, NT>;
+  static_assert((sizeof(bf16s) * G::OS) % 16 == 0, "b must start on a 16-byte boundary");
+  return sizeof(bf16s) * (size_t)sg * G::OS + sizeof(T) * (size_t)sg * G::H + (size_t)((2 * G::H + 15) / 16 * 16);
+}
+
+// BF16 values a piece of a colour run is copied in: 8 (16 bytes), 4 or 2
+// (a run of a row holds NT / 2 cells, an even number on the BF16 levels)
+template <int HN>
+struct BfPiece {
+  static_assert(HN % 2 == 0, "BF16 levels have even runs");
+  static constexpr int value = HN % 8 == 0 ? 8 : (HN % 4 == 0 ? 4 : 2);
+};
+
+// cs_stage_interior for BF16 phi: slot base rs_h in hphi (level-local
+// offsets); b as T.
+template <typename T, int D, int NT>
+__device__ __forceinline__ void cs_stage_interior_bf(const GmgView<T> &V, const LvArgs &L, int bid, int c,
+                                                     long long rs_h, long long rs_f, bf16s *O, T *B) {
+  using G = CsGeo<bf16s, D, NT>;
+  constexpr int PW = BfPiece<G::HN>::value;
+  constexpr int VB = 16 / sizeof(T);
+  const long long pbase = rs_h + L.poff + (long long)(bid - L.first) * (2 * G::H);
+  const long long base = rs_f + L.off + (long long)(bid - L.first) * (2 * G::H);
+  const bf16s *oth = V.hphi + pbase + (1 - c) * G::H;
+  const T *bown = V.b + base + c * G::H;
+  for (int i = threadIdx.x; i < G::H / PW; i += blockDim.x) {
+    const int j = i * PW, r = j / G::HN, k = j - r * G::HN;
+    cp_async_bytes<2 * PW>(O + G::at(G::row(r % NT, D == 3 ? r / NT : 0), k), oth + j);
+  }
+  if (G::H % VB == 0) {
+    for (int i = threadIdx.x; i < G::H / VB; i += blockDim.x) cp_async16(B + i * VB, bown + i * VB);
+  } else {
+    for (int j = threadIdx.x; j < G::H; j += blockDim.x) cp_async_elem(B + j, bown + j);
+  }
+}
+
+// cs_stage_faces for BF16 phi.  The y and z face runs come in pieces as in
+// cs_stage_interior_bf.  An x ghost from a same-level neighbour comes as an
+// aligned 4-byte pair: the neighbour's cells 0 and 1 of the run to k = HN,
+// HN + 1 (ghost x = NT), or its cells HN - 2 and HN - 1 to k = -2, -1
+// (ghost x = -1); k = HN + 1 and -2 are row padding, never read.  At a wall
+// the own cell is staged by a plain load (a pair there would overwrite the
+// block's own first or last cell).
+template <typename T, int D, int NT>
+__device__ __forceinline__ void cs_stage_faces_bf(const GmgView<T> &V, const LvArgs &L, int bid, int c,
+                                                  const int *s_nb, int fl, long long rs_h, bf16s *O) {
+  using G = CsGeo<bf16s, D, NT>;
+  constexpr int PW = BfPiece<G::HN>::value;
+  const long long pown = rs_h + L.poff + (long long)(bid - L.first) * (2 * G::H) + c * G::H;  // own colour
+  constexpr int FR = D == 3 ? NT : 1;
+  constexpr int PR = G::HN / PW;
+  for (int i = threadIdx.x; i < (2 * D - 2) * FR * PR; i += blockDim.x) {
+    const int f = 2 + i / (FR * PR), rem = i - (f - 2) * FR * PR;
+    const int u = rem / PR, k = (rem - u * PR) * PW;
+    const int a = f >> 1, side = f & 1;
+    const int id = s_nb[f];
+    const bool wall = (fl & wall_bit(a, side)) != 0;
+    if (!wall && id < 0) continue;
+    const int yg = a == 1 ? (side ? NT : -1) : u, zg = a == 2 ? (side ? NT : -1) : u;
+    const bf16s *src;
+    if (wall) {
+      const int yi = a == 1 ? (side ? NT - 1 : 0) : u, zi = a == 2 ? (side ? NT - 1 : 0) : u;
+      src = V.hphi + pown + G::HN * (yi + (D == 3 ? NT * zi : 0));
+    } else {
+      const int ys = a == 1 ? (side ? 0 : NT - 1) : u, zs = a == 2 ? (side ? 0 : NT - 1) : u;
+      src = V.hphi + rs_h + L.poff + (long long)(id - L.first) * (2 * G::H) + (1 - c) * G::H +
+            G::HN * (ys + (D == 3 ? NT * zs : 0));
+    }
+    cp_async_bytes<2 * PW>(O + G::at(G::row(yg, D == 3 ? zg : 0), k), src + k);
+  }
+  for (int r = threadIdx.x; r < G::H / G::HN; r += blockDim.x) {
+    const int y = r % NT, z = D == 3 ? r / NT : 0;
+    const int qo = (y + z + 1 - c) & 1;
+    const int side = qo ? 0 : 1;
+    const int id = s_nb[side];
+    const bool wall = (fl & wall_bit(0, side)) != 0;
+    if (!wall && id < 0) continue;
+    if (wall) {
+      O[G::at(G::row(y, z), side ? G::HN : -1)] = V.hphi[pown + G::HN * (y + NT * z) + (side ? G::HN - 1 : 0)];
+    } else {
+      const long long rowb =
+          rs_h + L.poff + (long long)(id - L.first) * (2 * G::H) + (1 - c) * G::H + G::HN * (y + NT * z);
+      if (side)
+        cp_async_bytes<4>(O + G::at(G::row(y, z), G::HN), V.hphi + rowb);
+      else
+        cp_async_bytes<4>(O + G::at(G::row(y, z), -2), V.hphi + rowb + G::HN - 2);
+    }
+  }
 }
 
 // Stages slot s's other-colour half and own-colour b for a half-sweep of
@@ -141,13 +231,12 @@ __device__ __forceinline__ void cs_stage_faces(const GmgView<T> &V, const LvArgs
 // staged copies have landed): a wall ghost is the sign times the own cell
 // beside it (staged in the ghost's place by cs_stage_faces), a refinement
 // ghost follows reading G (refine_ghost, on the slot's own block).
-template <typename T, int D, int NT>
+// S is the tile's type: T, or bf16s for a BF16 level (phi: the slot's T
+// fields, for the coarse level; own: the block's own run, of type S).
+template <typename T, int D, int NT, typename S = T>
 __device__ __forceinline__ void cs_special_ghosts(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid,
-                                                  int c, const int *s_nb, int fl, long long rs_phi, T *O) {
-  using G = CsGeo<T, D, NT>;
-  const long long pbase = rs_phi + L.poff + (long long)(bid - L.first) * (2 * G::H);
-  const T *phi = V.phi + rs_phi;
-  const T *own = V.phi + pbase;
+                                                  int c, const int *s_nb, int fl, const T *phi, const S *own, S *O) {
+  using G = CsGeo<S, D, NT>;
   constexpr int FR = D == 3 ? NT : 1;
   // y and z faces: ghost (x, -1 or NT, z) / (x, y, -1 or NT) with x = 2k + qg
   for (int i = threadIdx.x; i < (2 * D - 2) * FR * G::HN; i += blockDim.x) {
@@ -159,12 +248,12 @@ __device__ __forceinline__ void cs_special_ghosts(const GmgView<T> &V, const LvA
     const int yg = a == 1 ? (side ? NT : -1) : u, zg = a == 2 ? (side ? NT : -1) : (D == 3 ? u : 0);
     const int qg = (yg + zg + 1 - c) & 1;  // the ghost row's other-colour parity
     const int x = 2 * k + qg;
-    T *dst = O + G::at(G::row(yg, zg), k);
+    S *dst = O + G::at(G::row(yg, zg), k);
     if (wall) {
       *dst = wall_reflect(*dst, (V.wneu >> f) & 1);
     } else {
       const int g[3] = {x, yg, zg};
-      *dst = refine_ghost<T, D>(phi, V.nbr, V.flags, V.parent, V.pofs, V.wneu, L, Lp, bid, g, a, own);
+      *dst = st_val<S>(refine_ghost<T, D>(phi, V.nbr, V.flags, V.parent, V.pofs, V.wneu, L, Lp, bid, g, a, own));
     }
   }
   for (int r = threadIdx.x; r < G::H / G::HN; r += blockDim.x) {
@@ -173,12 +262,12 @@ __device__ __forceinline__ void cs_special_ghosts(const GmgView<T> &V, const LvA
     const bool wall = (fl & wall_bit(0, side)) != 0;
     if (!wall && s_nb[side] >= 0) continue;
     const int xg = side ? NT : -1;
-    T *dst = O + G::at(G::row(y, z), side ? G::HN : -1);
+    S *dst = O + G::at(G::row(y, z), side ? G::HN : -1);
     if (wall) {
       *dst = wall_reflect(*dst, (V.wneu >> side) & 1);
     } else {
       const int g[3] = {xg, y, z};
-      *dst = refine_ghost<T, D>(phi, V.nbr, V.flags, V.parent, V.pofs, V.wneu, L, Lp, bid, g, 0, own);
+      *dst = st_val<S>(refine_ghost<T, D>(phi, V.nbr, V.flags, V.parent, V.pofs, V.wneu, L, Lp, bid, g, 0, own));
     }
   }
 }
@@ -186,14 +275,27 @@ __device__ __forceinline__ void cs_special_ghosts(const GmgView<T> &V, const LvA
 // One half-sweep of colour `color` on block bid for the slots slot[0 ..
 // SG - 1] (-1: skipped); shared memory as CsGeo::smem_bytes(SG).  Used by
 // the per-level kernel below and by the cooperative coarse cycle.
-template <typename T, int D, int NT, int SG>
+// BF: the level's phi is stored as BF16 (the finest level of
+// GMG_MIXED_BF16): tiles of BF16 values, arithmetic in T, each result
+// rounded to BF16 when written.
+template <typename T, int D, int NT, int SG, bool BF = false>
 __device__ __forceinline__ void smooth_cs_block(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid,
                                                 const int *slot, int color, unsigned char *smem_raw) {
-  using G = CsGeo<T, D, NT>;
+  using S = typename std::conditional<BF, bf16s, T>::type;
+  using G = CsGeo<S, D, NT>;
   __shared__ int s_nb[6];
   __shared__ int s_fl;
-  T *O = reinterpret_cast<T *>(smem_raw);
-  T *B = O + SG * G::OS;
+  S *O = reinterpret_cast<S *>(smem_raw);
+  T *B = reinterpret_cast<T *>(O + SG * G::OS);
+  S *Pf;  // the level's phi (slot 0)
+  long long rsP;
+  if constexpr (BF) {
+    Pf = V.hphi;
+    rsP = V.rs_h;
+  } else {
+    Pf = V.phi;
+    rsP = V.rs_phi;
+  }
   unsigned char *sfl = reinterpret_cast<unsigned char *>(B + SG * G::H);
   const long long sb = V.st_base[bid];
   // this colour's cut list: entry e0 + i goes to thread i (fetched while the
@@ -219,13 +321,24 @@ __device__ __forceinline__ void smooth_cs_block(const GmgView<T> &V, const LvArg
   // the block's own halves are in flight while the neighbour table is read
 #pragma unroll
   for (int s = 0; s < SG; s++)
-    if (slot[s] >= 0)
-      cs_stage_interior<T, D, NT>(V, L, bid, color, slot[s] * V.rs_phi, slot[s] * V.rs_f, O + s * G::OS, B + s * G::H);
+    if (slot[s] >= 0) {
+      if constexpr (BF)
+        cs_stage_interior_bf<T, D, NT>(V, L, bid, color, slot[s] * V.rs_h, slot[s] * V.rs_f, O + s * G::OS,
+                                       B + s * G::H);
+      else
+        cs_stage_interior<T, D, NT>(V, L, bid, color, slot[s] * V.rs_phi, slot[s] * V.rs_f, O + s * G::OS,
+                                    B + s * G::H);
+    }
   __syncthreads();
   const int fl = s_fl;
 #pragma unroll
   for (int s = 0; s < SG; s++)
-    if (slot[s] >= 0) cs_stage_faces<T, D, NT>(V, L, bid, color, s_nb, fl, slot[s] * V.rs_phi, O + s * G::OS);
+    if (slot[s] >= 0) {
+      if constexpr (BF)
+        cs_stage_faces_bf<T, D, NT>(V, L, bid, color, s_nb, fl, slot[s] * V.rs_h, O + s * G::OS);
+      else
+        cs_stage_faces<T, D, NT>(V, L, bid, color, s_nb, fl, slot[s] * V.rs_phi, O + s * G::OS);
+    }
   cp_async_wait_all();
   __syncthreads();
   bool special = false;
@@ -234,7 +347,10 @@ __device__ __forceinline__ void smooth_cs_block(const GmgView<T> &V, const LvArg
   if (special) {
 #pragma unroll
     for (int s = 0; s < SG; s++)
-      if (slot[s] >= 0) cs_special_ghosts<T, D, NT>(V, L, Lp, bid, color, s_nb, fl, slot[s] * V.rs_phi, O + s * G::OS);
+      if (slot[s] >= 0)
+        cs_special_ghosts<T, D, NT, S>(V, L, Lp, bid, color, s_nb, fl, V.phi + slot[s] * V.rs_phi,
+                                       Pf + slot[s] * rsP + L.poff + (long long)(bid - L.first) * (2 * G::H),
+                                       O + s * G::OS);
     __syncthreads();
   }
   const T h2 = T(L.h2), inv2d = T(1.0 / (2 * D));
@@ -260,10 +376,10 @@ __device__ __forceinline__ void smooth_cs_block(const GmgView<T> &V, const LvArg
 #pragma unroll
     for (int s = 0; s < SG; s++) {
       if (slot[s] < 0) continue;
-      const T *o = O + s * G::OS;
-      T sum = (o[t[0]] + o[t[1]]) + (o[t[2]] + o[t[3]]);
-      if (D == 3) sum += o[t[4]] + o[t[5]];
-      V.phi[slot[s] * V.rs_phi + pown + j] = (sum - h2 * B[s * G::H + j]) * inv2d;
+      const S *o = O + s * G::OS;
+      T sum = (ld_val(o[t[0]]) + ld_val(o[t[1]])) + (ld_val(o[t[2]]) + ld_val(o[t[3]]));
+      if (D == 3) sum += ld_val(o[t[4]]) + ld_val(o[t[5]]);
+      Pf[slot[s] * rsP + pown + j] = st_val<S>((sum - h2 * B[s * G::H + j]) * inv2d);
     }
   }
   auto upd = [&](const CutCell<T, D> &u) {
@@ -273,10 +389,11 @@ __device__ __forceinline__ void smooth_cs_block(const GmgView<T> &V, const LvArg
 #pragma unroll
     for (int s = 0; s < SG; s++) {
       if (slot[s] < 0) continue;
-      const T *o = O + s * G::OS;
-      T sum = u.a[1] * o[t[0]] + u.a[2] * o[t[1]] + u.a[3] * o[t[2]] + u.a[4] * o[t[3]];
-      if (D == 3) sum += u.a[5] * o[t[4]] + u.a[6] * o[t[5]];
-      V.phi[slot[s] * V.rs_phi + pown + j] = (B[s * G::H + j] - sum) / u.a[0];
+      const S *o = O + s * G::OS;
+      T sum = u.a[1] * ld_val(o[t[0]]) + u.a[2] * ld_val(o[t[1]]) + u.a[3] * ld_val(o[t[2]]) +
+              u.a[4] * ld_val(o[t[3]]);
+      if (D == 3) sum += u.a[5] * ld_val(o[t[4]]) + u.a[6] * ld_val(o[t[5]]);
+      Pf[slot[s] * rsP + pown + j] = st_val<S>((B[s * G::H + j] - sum) / u.a[0]);
     }
   };
   if ((int)threadIdx.x < m) upd(cq);
@@ -290,7 +407,7 @@ __device__ __forceinline__ void smooth_cs_block(const GmgView<T> &V, const LvArg
 // The half-sweep kernel: one CTA per (block, group of SG slots); the grid
 // holds count x ceil(nrhs / SG) CTAs, slot groups fastest.  Frozen units
 // are skipped per slot.
-template <typename T, int D, int NT, int SG>
+template <typename T, int D, int NT, int SG, bool BF = false>
 __global__ void __launch_bounds__(kThreads) k_smooth_cs(GmgView<T> V, LvArgs L, LvArgs Lp, int color) {
   pdl_start();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -306,7 +423,7 @@ __global__ void __launch_bounds__(kThreads) k_smooth_cs(GmgView<T> V, LvArgs L, 
     any = any || slot[s] >= 0;
   }
   if (!any) return;
-  smooth_cs_block<T, D, NT, SG>(V, L, Lp, bid, slot, color, smem_raw);
+  smooth_cs_block<T, D, NT, SG, BF>(V, L, Lp, bid, slot, color, smem_raw);
 }
 
 }  // namespace gmg

@@ -92,10 +92,14 @@ __global__ void k_leaf_copy(const int *__restrict__ leaf_ids, const long long *_
 
 // phi64 += e32 on leaf cells of the active units (mixed path: solution
 // accumulation in FP64)
+// With eh (GMG_MIXED_BF16), e of the blocks from h_first on (the finest
+// level) is read from its BF16 run: slot r at r * rs_h, level-local offset
+// cbase - h_off.
 __global__ void k_leaf_accumulate(const int *__restrict__ leaf_ids, const long long *__restrict__ cbase,
                                   double *__restrict__ phi, const float *__restrict__ e, int nlb, int ncell,
                                   long long rs, int nr, const int *__restrict__ active, const int *__restrict__ tree_of,
-                                  int ntree) {
+                                  int ntree, const unsigned short *__restrict__ eh, int h_first, long long h_off,
+                                  long long rs_h) {
   pdl_start();
   for (int lb = blockIdx.x; lb < nlb; lb += gridDim.x) {
     const int id = leaf_ids[lb];
@@ -103,6 +107,26 @@ __global__ void k_leaf_accumulate(const int *__restrict__ leaf_ids, const long l
     const int tr = ntree > 1 ? tree_of[id] : 0;
     for (int r = 0; r < nr; r++) {
       if (!active[r * ntree + tr]) continue;
+      if (eh && id >= h_first) {
+        const long long o = r * rs + base;
+        const unsigned short *eb = eh + r * rs_h + (base - h_off);
+        if ((ncell & 3) == 0) {  // four cells a thread: one 8-byte load of e, two double2 of phi
+          for (int c = 4 * threadIdx.x; c < ncell; c += 4 * blockDim.x) {
+            const uint2 d = __ldcs(reinterpret_cast<const uint2 *>(eb + c));
+            double2 *p = reinterpret_cast<double2 *>(phi + o + c);
+            double2 u = p[0], w = p[1];
+            u.x += f32_to_f64(ld_val((bf16s)(d.x & 0xffffu)));
+            u.y += f32_to_f64(ld_val((bf16s)(d.x >> 16)));
+            w.x += f32_to_f64(ld_val((bf16s)(d.y & 0xffffu)));
+            w.y += f32_to_f64(ld_val((bf16s)(d.y >> 16)));
+            p[0] = u;
+            p[1] = w;
+          }
+        } else {
+          for (int c = threadIdx.x; c < ncell; c += blockDim.x) phi[o + c] += f32_to_f64(ld_val((bf16s)eb[c]));
+        }
+        continue;
+      }
       const long long o = r * rs + base;
       if (((o | ncell) & 3) == 0) {  // four cells a thread: one float4 of e, two double2 of phi
         for (int c = 4 * threadIdx.x; c < ncell; c += 4 * blockDim.x) {
@@ -229,6 +253,27 @@ LvArgs lv(const gmg_tree *T, int l) {
   return a;
 }
 
+// GMG_MIXED_BF16: the finest level's phi of the FP32 correction is kept as
+// BF16 in that level's part of the second FP32 phi buffer (which only the
+// fused sweeps use, and not on this level): slot r's BF16 run starts at
+// float offset r * total_cells + (level offset) of that buffer, so it lies
+// inside the level's own part of the slot.  No extra memory.
+unsigned short *bf16_phi(gmg_tree *t) {
+  return reinterpret_cast<unsigned short *>(t->f_phi + (size_t)t->nrhs * t->total_cells + t->lev(t->lmax).off);
+}
+
+// Whether the finest level can hold BF16 state: it runs in the per-level
+// kernels (above the cooperative / cluster levels), its block side has
+// compiled kernels, and its runs start on 16-byte boundaries.  Otherwise
+// GMG_MIXED_BF16 runs as GMG_MIXED.
+bool bf16_eligible(const gmg_tree *t) {
+  const int ls = t->use_coop ? t->coop_split : t->lmin;
+  if (t->lmax <= ls || t->lmax <= t->lmin) return false;
+  const int n = t->lev(t->lmax).n;
+  const bool nt = t->D == 3 ? (n == 4 || n == 8 || n == 16) : (n == 8 || n == 16 || n == 32);
+  return nt && t->total_cells % 4 == 0 && t->lev(t->lmax).off % 4 == 0;
+}
+
 template <typename T>
 GmgView<T> view(gmg_tree *t);
 
@@ -260,6 +305,8 @@ GmgView<double> view<double>(gmg_tree *t) {
   v.ntree = t->ntree;
   v.tree_of = t->d_tree_of;
   v.active = t->d_active;
+  v.hphi = nullptr;
+  v.rs_h = 0;
   return v;
 }
 
@@ -291,6 +338,8 @@ GmgView<float> view<float>(gmg_tree *t) {
   v.ntree = t->ntree;
   v.tree_of = t->d_tree_of;
   v.active = t->d_active;
+  v.hphi = t->bf16_top ? bf16_phi(t) : nullptr;
+  v.rs_h = 2 * t->total_cells;
   return v;
 }
 
@@ -347,6 +396,21 @@ void set_smem_limits() {
   for (int n : {4, 8, 16, 32, 2}) with_nt<D>(n, [&](auto nt) { set_smem_limits_nt<T, D, decltype(nt)::value>(); });
 }
 
+// the BF16 variants of the finest level's kernels (FP32 arithmetic)
+template <int D, int NT>
+void bf16_attrs() {
+  if constexpr (NT != 0) {
+    kernel_attrs(k_smooth_cs<float, D, NT, 1, true>, true);
+    kernel_attrs(k_smooth_cs<float, D, NT, 2, true>, true);
+    kernel_attrs(k_smooth_cs<float, D, NT, 4, true>, true);
+    kernel_attrs(k_resid_restrict<float, D, NT, true>, true);
+    kernel_attrs(k_prolong<float, D, NT, 64, true>, true);
+    kernel_attrs(k_prolong<float, D, NT, 128, true>, true);
+    kernel_attrs(k_prolong<float, D, NT, 256, true>, true);
+    kernel_attrs(k_restrict_phi<float, D, NT, true>, false);
+  }
+}
+
 template <int D, int NT>
 void fused_attrs() {
   if constexpr (NT != 0) {
@@ -361,6 +425,10 @@ void set_all_smem_limits() {
   for (int n : {8, 16, 32}) {
     with_nt<2>(n, [&](auto nt) { fused_attrs<2, decltype(nt)::value>(); });
     with_nt<3>(n, [&](auto nt) { fused_attrs<3, decltype(nt)::value>(); });
+  }
+  for (int n : {4, 8, 16, 32}) {
+    with_nt<2>(n, [&](auto nt) { bf16_attrs<2, decltype(nt)::value>(); });
+    with_nt<3>(n, [&](auto nt) { bf16_attrs<3, decltype(nt)::value>(); });
   }
   set_smem_limits<double, 2>();
   set_smem_limits<double, 3>();
@@ -385,11 +453,26 @@ void set_all_smem_limits() {
 // per (block, slot), or per (block, group of slots_per_cta slots) when the
 // tree has several slots and the group's tiles fit in shared memory; blocks
 // of a side without a compiled kernel take the tile-based smooth_block.
+// bf: the level's phi is BF16 (GMG_MIXED_BF16's finest level; FP32 only).
 template <typename T, int D, int NT>
 void launch_smooth(const gmg_tree *t, const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int c, int threads,
-                   size_t sm, cudaStream_t s) {
+                   size_t sm, cudaStream_t s, bool bf = false) {
   if constexpr (NT != 0) {
     int sg = t->nrhs > 1 ? t->slots_per_cta : 1;
+    if constexpr (std::is_same<T, float>::value) {
+      if (bf) {
+        while (sg > 1 && cs_smem_bytes<T, D, NT, true>(sg) > 200 * 1024) sg /= 2;
+        const int grid = L.count * ((t->nrhs + sg - 1) / sg);
+        const size_t sms = cs_smem_bytes<T, D, NT, true>(sg);
+        if (sg == 4)
+          klaunch(t, grid, threads, sms, s, k_smooth_cs<T, D, NT, 4, true>, V, L, Lp, c);
+        else if (sg == 2)
+          klaunch(t, grid, threads, sms, s, k_smooth_cs<T, D, NT, 2, true>, V, L, Lp, c);
+        else
+          klaunch(t, grid, threads, sms, s, k_smooth_cs<T, D, NT, 1, true>, V, L, Lp, c);
+        return;
+      }
+    }
     while (sg > 1 && cs_smem_bytes<T, D, NT>(sg) > 200 * 1024) sg /= 2;
     const int grid = L.count * ((t->nrhs + sg - 1) / sg);
     const size_t sms = cs_smem_bytes<T, D, NT>(sg);
@@ -407,13 +490,42 @@ void launch_smooth(const gmg_tree *t, const GmgView<T> &V, const LvArgs &L, cons
 // k_prolong with the CTA size of the level's block kernels
 template <typename T, int D, int NT>
 void launch_prolong(const gmg_tree *t, int threads, int grid, size_t sm, cudaStream_t s, const GmgView<T> &V,
-                    const LvArgs &L, const LvArgs &Lp) {
+                    const LvArgs &L, const LvArgs &Lp, bool bf = false) {
+  if constexpr (std::is_same<T, float>::value && NT != 0) {
+    if (bf) {
+      if (threads == 64)
+        klaunch(t, grid, 64, sm, s, k_prolong<T, D, NT, 64, true>, V, L, Lp);
+      else if (threads == 128)
+        klaunch(t, grid, 128, sm, s, k_prolong<T, D, NT, 128, true>, V, L, Lp);
+      else
+        klaunch(t, grid, 256, sm, s, k_prolong<T, D, NT, 256, true>, V, L, Lp);
+      return;
+    }
+  }
   if (threads == 64)
     klaunch(t, grid, 64, sm, s, k_prolong<T, D, NT, 64>, V, L, Lp);
   else if (threads == 128)
     klaunch(t, grid, 128, sm, s, k_prolong<T, D, NT, 128>, V, L, Lp);
   else
     klaunch(t, grid, 256, sm, s, k_prolong<T, D, NT, 256>, V, L, Lp);
+}
+
+template <typename T, int D, int NT>
+void launch_resid_restrict(const gmg_tree *t, int grid, int threads, size_t sm, cudaStream_t s, const GmgView<T> &V,
+                           const LvArgs &L, const LvArgs &Lp, bool bf = false) {
+  if constexpr (std::is_same<T, float>::value && NT != 0) {
+    if (bf) {
+      klaunch(t, grid, threads, sm, s, k_resid_restrict<T, D, NT, true>, V, L, Lp);
+      return;
+    }
+  }
+  klaunch(t, grid, threads, sm, s, k_resid_restrict<T, D, NT>, V, L, Lp);
+}
+
+// Whether level l's FP32 phi is BF16 in the step being enqueued.
+template <typename T>
+bool bf16_level(const gmg_tree *t, int l) {
+  return std::is_same<T, float>::value && t->bf16_top && l == t->lmax;
 }
 
 template <typename T>
@@ -637,6 +749,7 @@ int coop_cycle(gmg_tree *t, cudaStream_t s, int ls) {
 template <typename T>
 bool fused_level(const gmg_tree *t, int l) {
   if (!std::is_same<T, float>::value || !t->use_fused) return false;
+  if (bf16_level<T>(t, l)) return false;
   const int n = t->lev(l).n;
   const bool n_ok = t->D == 3 ? (n == 8 || n == 16) : (n == 8 || n == 16 || n == 32);
   const int nd = t->n_down_at(l), nu = t->n_up_at(l);
@@ -678,6 +791,9 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s, bool end_restrict, int top) {
   const int R = t->nrhs;
   for (int l = top; l > ls; l--) {
     LvArgs L = lv(t, l), Lp = lv(t, l - 1);
+    const bool bf = bf16_level<T>(t, l);
+    const int Pl = bf ? 2 : P;
+    if (bf) L.poff = 0;  // the BF16 run is level-local
     const size_t sm = tile_bytes<T>(t, l);
     const int nt_l = cta_threads(t, l), nt_p = cta_threads(t, l - 1);
     const bool fused = fused_level<T>(t, l);
@@ -690,8 +806,9 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s, bool end_restrict, int top) {
       if (!fused)
         for (int k = 0; k < L.nd; k++)
           for (int c = 0; c < 2; c++)
-            launch(t, s, 0, P, l, [&] { launch_smooth<T, D, NT>(t, V, L, Lp, c, nt_l, sm, s); });
-      launch(t, s, 1, P, l, [&] { klaunch(t, L.count * R, nt_l, sm, s, k_resid_restrict<T, D, NT>, V, L, Lp); });
+            launch(t, s, 0, Pl, l, [&] { launch_smooth<T, D, NT>(t, V, L, Lp, c, nt_l, sm, s, bf); });
+      launch(t, s, 1, Pl, l,
+             [&] { launch_resid_restrict<T, D, NT>(t, L.count * R, nt_l, sm, s, V, L, Lp, bf); });
     });
     LvArgs Lpp = l - 2 >= t->lmin ? lv(t, l - 2) : Lp;
     const size_t smp = tile_bytes<T>(t, l - 1);
@@ -713,6 +830,9 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s, bool end_restrict, int top) {
   }
   for (int l = ls + 1; l <= top; l++) {
     LvArgs L = lv(t, l), Lp = lv(t, l - 1);
+    const bool bf = bf16_level<T>(t, l);
+    const int Pl = bf ? 2 : P;
+    if (bf) L.poff = 0;
     const int hm = L.n / 2 + 2;
     const size_t psm = sizeof(T) * (size_t)(D == 3 ? hm * hm * hm : hm * hm);
     const size_t sm = tile_bytes<T>(t, l);
@@ -721,21 +841,31 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s, bool end_restrict, int top) {
     if (fused) L.poff = L.off + other;  // the down leg left phi in the second buffer
     with_nt<D>(L.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
-      launch(t, s, 4, P, l, [&] { launch_prolong<T, D, NT>(t, cta_threads(t, l), L.count * R, psm, s, V, L, Lp); });
+      launch(t, s, 4, Pl, l,
+             [&] { launch_prolong<T, D, NT>(t, cta_threads(t, l), L.count * R, psm, s, V, L, Lp, bf); });
       if (!fused)
         for (int k = 0; k < L.nu; k++)
           for (int c = 0; c < 2; c++)
-            launch(t, s, 0, P, l, [&] { launch_smooth<T, D, NT>(t, V, L, Lp, c, nt_l, sm, s); });
+            launch(t, s, 0, Pl, l, [&] { launch_smooth<T, D, NT>(t, V, L, Lp, c, nt_l, sm, s, bf); });
     });
     if (fused) launch_fused<T, D>(t, s, l, L.nu, L.off + other, L.off);  // back to the first buffer
   }
   if (t->adaptive && end_restrict) {
     for (int l = top; l >= 2 && l > t->lmin; l--) {
       LvArgs L = lv(t, l), Lp = lv(t, l - 1);
+      const bool bf = bf16_level<T>(t, l);
+      if (bf) L.poff = 0;
       with_nt<D>(L.n, [&](auto nt) {
         constexpr int NT = decltype(nt)::value;
-        launch(t, s, 5, P, l,
-               [&] { klaunch(t, L.count * R, cta_threads(t, l), 0, s, k_restrict_phi<T, D, NT>, V, L, Lp); });
+        launch(t, s, 5, bf ? 2 : P, l, [&] {
+          if constexpr (std::is_same<T, float>::value && NT != 0) {
+            if (bf) {
+              klaunch(t, L.count * R, cta_threads(t, l), 0, s, k_restrict_phi<T, D, NT, true>, V, L, Lp);
+              return;
+            }
+          }
+          klaunch(t, L.count * R, cta_threads(t, l), 0, s, k_restrict_phi<T, D, NT>, V, L, Lp);
+        });
       });
     }
   }
@@ -758,13 +888,17 @@ int fmg_impl(gmg_tree *t, cudaStream_t s) {
   const int P = prec_of<T>();
   const int R = t->nrhs;
   for (int l = t->lmax; l > t->lmin; l--) {
-    const LvArgs L = lv(t, l), Lp = lv(t, l - 1);
+    LvArgs L = lv(t, l);
+    const LvArgs Lp = lv(t, l - 1);
+    const bool bf = bf16_level<T>(t, l);
+    if (bf) L.poff = 0;
     const LvArgs Lpp = l - 2 >= t->lmin ? lv(t, l - 2) : Lp;
     const size_t sm = tile_bytes<T>(t, l), smp = tile_bytes<T>(t, l - 1);
     const int nt_l = cta_threads(t, l), nt_p = cta_threads(t, l - 1);
     with_nt<D>(L.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
-      launch(t, s, 1, P, l, [&] { klaunch(t, L.count * R, nt_l, sm, s, k_resid_restrict<T, D, NT>, V, L, Lp); });
+      launch(t, s, 1, bf ? 2 : P, l,
+             [&] { launch_resid_restrict<T, D, NT>(t, L.count * R, nt_l, sm, s, V, L, Lp, bf); });
     });
     with_nt<D>(Lp.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
@@ -780,12 +914,16 @@ int fmg_impl(gmg_tree *t, cudaStream_t s) {
     });
   }
   for (int l = t->lmin + 1; l <= t->lmax; l++) {
-    const LvArgs L = lv(t, l), Lp = lv(t, l - 1);
+    LvArgs L = lv(t, l);
+    const LvArgs Lp = lv(t, l - 1);
+    const bool bf = bf16_level<T>(t, l);
+    if (bf) L.poff = 0;
     const int hm = L.n / 2 + 2;
     const size_t psm = sizeof(T) * (size_t)(D == 3 ? hm * hm * hm : hm * hm);
     with_nt<D>(L.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
-      launch(t, s, 4, P, l, [&] { launch_prolong<T, D, NT>(t, cta_threads(t, l), L.count * R, psm, s, V, L, Lp); });
+      launch(t, s, 4, bf ? 2 : P, l,
+             [&] { launch_prolong<T, D, NT>(t, cta_threads(t, l), L.count * R, psm, s, V, L, Lp, bf); });
     });
     const int rc = vcycle_impl<T, D>(t, s, true, l);
     if (rc) return rc;
@@ -854,17 +992,40 @@ int restrict_all_phi64_any(gmg_tree *t, cudaStream_t s) {
 // V-cycles on A e = r, phi += e in FP64 (and covered cells restricted).  The
 // FP32 cycles skip their closing restriction into covered cells: only the
 // leaf values of e are used, and the next step starts again from e = 0.
-int mixed_step(gmg_tree *t, cudaStream_t s) {
-  // e = 0 in the first FP32 phi buffer of every slot (frozen slots too: harmless)
-  CUDA_TRY(cudaMemsetAsync(t->f_phi, 0, (size_t)t->nrhs * t->total_cells * sizeof(float), s));
+//
+// bf16 (GMG_MIXED_BF16): the finest level's e is kept as BF16 when the tree
+// allows it (bf16_eligible); its FP32 part of the first buffer is then not
+// cleared, as nothing reads it.
+int mixed_step(gmg_tree *t, cudaStream_t s, bool bf16 = false) {
+  const bool bf = bf16 && bf16_eligible(t);
+  const size_t pitch = (size_t)t->total_cells * sizeof(float);
+  if (bf) {
+    // e = 0: the levels below the finest (their cells come first in each
+    // slot) as FP32, the finest level's BF16 runs
+    const long long off = t->lev(t->lmax).off;
+    const long long cells = (long long)t->lev(t->lmax).count * t->lev(t->lmax).ncell;
+    if (off > 0) CUDA_TRY(cudaMemset2DAsync(t->f_phi, pitch, 0, (size_t)off * sizeof(float), t->nrhs, s));
+    CUDA_TRY(cudaMemset2DAsync(bf16_phi(t), pitch, 0, (size_t)cells * sizeof(unsigned short), t->nrhs, s));
+  } else {
+    // e = 0 in the first FP32 phi buffer of every slot (frozen slots too: harmless)
+    CUDA_TRY(cudaMemsetAsync(t->f_phi, 0, (size_t)t->nrhs * t->total_cells * sizeof(float), s));
+  }
+  t->bf16_top = bf;
   for (int k = 0; k < t->inner_cycles; k++) {
     const int rc = t->fmg_steps ? fmg_any<float>(t, s) : vcycle_any<float>(t, s, k + 1 < t->inner_cycles);
-    if (rc) return rc;
+    if (rc) {
+      t->bf16_top = false;
+      return rc;
+    }
   }
-  launch(t, s, 8, 0, t->lmax, [&] {
+  const unsigned short *eh = bf ? bf16_phi(t) : nullptr;
+  const int h_first = t->lev(t->lmax).first;
+  const long long h_off = t->lev(t->lmax).off;
+  t->bf16_top = false;
+  launch(t, s, 8, bf ? 2 : 0, t->lmax, [&] {
     klaunch(t, leaf_grid(t), 256, 0, s, k_leaf_accumulate, (const int *)t->d_leaf, (const long long *)t->d_cbase, t->d_phi, (const float *)t->f_phi, n_leaf_blocks(t),
                                                    t->leaf_ncell(), t->total_cells, t->nrhs, t->d_active, t->d_tree_of,
-                                                   t->ntree);
+                                                   t->ntree, eh, h_first, h_off, 2 * t->total_cells);
   });
   CUDA_TRY(cudaGetLastError());
   if (t->adaptive) return restrict_all_phi64_any(t, s);
@@ -1666,12 +1827,14 @@ int gmg_residual(gmg_tree *t, double *rel_l2, double *linf, void *stream) {
 
 int gmg_iterate_begin(gmg_tree *t, int precision, const int *active, int residual_only, void *stream) {
   if (!t || !active) return set_error("null argument"), GMG_ERR_INVALID_ARG;
-  if (precision != GMG_FP64 && precision != GMG_MIXED) return set_error("bad precision"), GMG_ERR_INVALID_ARG;
+  if (precision != GMG_FP64 && precision != GMG_MIXED && precision != GMG_MIXED_BF16)
+    return set_error("bad precision"), GMG_ERR_INVALID_ARG;
   if (!t->bound) return set_error("tree not bound"), GMG_ERR_STATE;
   if (t->step_pending) return set_error("gmg_iterate_end has not collected the previous step"), GMG_ERR_STATE;
   cudaStream_t s = as_stream(stream);
   t->launches = 0;
-  const bool mixed = precision == GMG_MIXED;
+  const bool mixed = precision != GMG_FP64, bf16 = precision == GMG_MIXED_BF16;
+  const int cycle_graph = bf16 ? gmg_tree::kGraphCycleBf16 : mixed ? gmg_tree::kGraphCycleMixed : gmg_tree::kGraphCycle64;
   float *rout = mixed ? t->f_b : nullptr;
   int rc = upload_mask(t, active, s);
   if (rc) return rc;
@@ -1679,8 +1842,8 @@ int gmg_iterate_begin(gmg_tree *t, int precision, const int *active, int residua
     rc = run_graph(t, mixed ? gmg_tree::kGraphResidMixed : gmg_tree::kGraphResid64, s,
                    [&](cudaStream_t cs) { return residual_any(t, cs, rout); });
   else
-    rc = run_graph(t, mixed ? gmg_tree::kGraphCycleMixed : gmg_tree::kGraphCycle64, s, [&](cudaStream_t cs) {
-      int r = mixed ? mixed_step(t, cs) : (t->fmg_steps ? fmg_any<double>(t, cs) : vcycle_any<double>(t, cs));
+    rc = run_graph(t, cycle_graph, s, [&](cudaStream_t cs) {
+      int r = mixed ? mixed_step(t, cs, bf16) : (t->fmg_steps ? fmg_any<double>(t, cs) : vcycle_any<double>(t, cs));
       return r ? r : residual_any(t, cs, rout);
     });
   if (rc) return rc;
@@ -1707,7 +1870,8 @@ int gmg_iterate(gmg_tree *t, int precision, const int *active, int residual_only
 
 int gmg_solve(gmg_tree *t, int precision, double rel_tol, int max_cycles, gmg_stats *stats, void *stream) {
   if (!t || max_cycles < 0 || !(rel_tol > 0.0)) return set_error("bad arguments"), GMG_ERR_INVALID_ARG;
-  if (precision != GMG_FP64 && precision != GMG_MIXED) return set_error("bad precision"), GMG_ERR_INVALID_ARG;
+  if (precision != GMG_FP64 && precision != GMG_MIXED && precision != GMG_MIXED_BF16)
+    return set_error("bad precision"), GMG_ERR_INVALID_ARG;
   if (!t->bound) return set_error("tree not bound"), GMG_ERR_STATE;
   cudaStream_t s = as_stream(stream);
   t->launches = 0;
@@ -1715,7 +1879,8 @@ int gmg_solve(gmg_tree *t, int precision, double rel_tol, int max_cycles, gmg_st
   std::vector<int> act(R, 1), cyc(R, 0);
   std::vector<double> rel(R, 0.0), prev(R, INFINITY);
   int cycles = 0, rc = GMG_OK;
-  const bool mixed = precision == GMG_MIXED;
+  const bool mixed = precision != GMG_FP64, bf16 = precision == GMG_MIXED_BF16;
+  const int cycle_graph = bf16 ? gmg_tree::kGraphCycleBf16 : mixed ? gmg_tree::kGraphCycleMixed : gmg_tree::kGraphCycle64;
   float *rout = mixed ? t->f_b : nullptr;
   // first residual; then each iteration = one cycle + the residual after it,
   // on the slots that have not reached the tolerance yet
@@ -1749,8 +1914,8 @@ int gmg_solve(gmg_tree *t, int precision, double rel_tol, int max_cycles, gmg_st
       rc = upload_mask(t, act.data(), s);
       if (rc) return rc;
     }
-    rc = run_graph(t, mixed ? gmg_tree::kGraphCycleMixed : gmg_tree::kGraphCycle64, s, [&](cudaStream_t cs) {
-      int r = mixed ? mixed_step(t, cs) : (t->fmg_steps ? fmg_any<double>(t, cs) : vcycle_any<double>(t, cs));
+    rc = run_graph(t, cycle_graph, s, [&](cudaStream_t cs) {
+      int r = mixed ? mixed_step(t, cs, bf16) : (t->fmg_steps ? fmg_any<double>(t, cs) : vcycle_any<double>(t, cs));
       return r ? r : residual_any(t, cs, rout);
     });
     if (rc) return rc;

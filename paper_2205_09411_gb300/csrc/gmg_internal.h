@@ -84,6 +84,11 @@ struct GmgView {
   int ntree;
   const int *tree_of;    // [nb] tree of each block (forests; unused when ntree == 1)
   const int *active;     // [nrhs * ntree] 0 = unit frozen (converged or empty): its CTAs return at once
+  // GMG_MIXED_BF16: phi of the finest level as BF16 bits (top 16 bits of
+  // the float), level-local offsets (the level's LvArgs::poff is 0 for it),
+  // slot r at r * rs_h; null otherwise
+  unsigned short *hphi;
+  long long rs_h;
 };
 
 // Layout of a block inside a level field (phi, b, old; every level, both
@@ -124,6 +129,7 @@ __host__ __device__ __forceinline__ GmgView<T> slot_view(const GmgView<T> &V, in
   W.phi = V.phi + r * V.rs_phi;
   W.b = V.b + r * V.rs_f;
   W.old = V.old + r * V.rs_f;
+  W.hphi = V.hphi ? V.hphi + r * V.rs_h : nullptr;
   return W;
 }
 
@@ -250,13 +256,23 @@ struct gmg_tree {
     cudaGraphExec_t exec = nullptr;
     long long kernels = 0;
   };
-  enum { kGraphResid64 = 0, kGraphResidMixed, kGraphCycle64, kGraphCycleMixed, kGraphVcycle64, kGraphFmg64, kGraphSlots };
+  enum {
+    kGraphResid64 = 0,
+    kGraphResidMixed,
+    kGraphCycle64,
+    kGraphCycleMixed,
+    kGraphVcycle64,
+    kGraphFmg64,
+    kGraphCycleBf16,
+    kGraphSlots
+  };
   GraphSlot graphs[kGraphSlots];
   bool use_graphs = true;
   bool use_coop = true;       // coarse levels in one cooperative launch
   bool use_fused = false;     // temporally blocked FP32 sweeps on uniform levels
   int cta_threads = 0;        // threads per CTA of the block kernels (0: by block size)
   int inner_cycles = 1;       // FP32 V-cycles per defect-correction step of the mixed path
+  bool bf16_top = false;      // while a GMG_MIXED_BF16 step is enqueued: the finest level's FP32 state is BF16
   int slots_per_cta = 1;      // right-hand-side slots of a block per CTA in the half-sweeps (1, 2, 4)
   bool fmg_steps = false;     // solve steps are FMG cycles instead of V-cycles
   bool use_pdl = true;        // per-level kernels with programmatic dependent launch

@@ -5,6 +5,7 @@
 // V-cycle (double for the FP64 path, float inside the mixed path).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "gmg_internal.h"
@@ -81,6 +82,28 @@ __device__ __forceinline__ double wall_reflect(double v, bool neumann) {
 
 __device__ __forceinline__ float to_f32(float v) { return v; }
 __device__ __forceinline__ float to_f32(double v) { return f64_to_f32_rn(v); }
+
+// BF16 storage of the FP32 correction's state on the finest level
+// (GMG_MIXED_BF16): a value is kept as the top 16 bits of its float (sign,
+// 8 exponent bits, 7 fraction bits), held as unsigned short.  Widening is
+// exact (the low 16 bits become zero); narrowing rounds to nearest, ties to
+// even (__float2bfloat16_rn).  ld_val / st_val are the identity for float
+// and double, so kernels written with them compile to the same code for
+// those types.
+using bf16s = unsigned short;
+__device__ __forceinline__ float ld_val(float v) { return v; }
+__device__ __forceinline__ double ld_val(double v) { return v; }
+__device__ __forceinline__ float ld_val(bf16s u) { return __uint_as_float((unsigned)u << 16); }
+template <typename S>
+__device__ __forceinline__ S st_val(float v) { return v; }
+template <typename S>
+__device__ __forceinline__ S st_val(double v) { return v; }
+template <>
+__device__ __forceinline__ bf16s st_val<bf16s>(float v) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+// the wall reflection of a BF16 value: its sign bit flipped (Dirichlet)
+__device__ __forceinline__ bf16s wall_reflect(bf16s v, bool neumann) { return neumann ? v : (bf16s)(v ^ 0x8000u); }
 
 // Position of cell j of a run of whole blocks of level L (the coarsest
 // level's unknowns of one root: blocks one after the other, natural cell
@@ -178,14 +201,16 @@ __device__ __forceinline__ bool resolve_s(const int *s_nb, int bid, const LvArgs
 // `own` holds the block's own cells (phi, or old for a covered block in the
 // FAS kernel).  The tables come as plain arguments (not the view), so that
 // callers can keep a per-slot view in registers.
-template <typename T, int D>
+// `own` may be stored as BF16 (S = bf16s, the finest level of
+// GMG_MIXED_BF16); the coarse level's phi is always of type T.
+template <typename T, int D, typename S = T>
 __device__ __noinline__ T refine_ghost(const T *phi, const int *nbr, const int *flags, const int *parent,
                                        const int *pofs_t, int wneu, const LvArgs &L, const LvArgs &Lp, int bid,
-                                       const int *p, int a, const T *own) {
+                                       const int *p, int a, const S *own) {
   const int n = L.n;
   int q[3] = {p[0], p[1], p[2]};
   q[a] = p[a] < 0 ? 0 : n - 1;
-  const T f = own[cs_pos_xyz(q[0], q[1], D == 3 ? q[2] : 0, n, L.ncell)];
+  const T f = ld_val(own[cs_pos_xyz(q[0], q[1], D == 3 ? q[2] : 0, n, L.ncell)]);
   const long long dp = Lp.poff - Lp.off;  // phi of the coarse level may live in the second buffer
   const int P = parent[bid], po = pofs_t[bid];
   const int pofs[3] = {po & 1023, (po >> 10) & 1023, (po >> 20) & 1023};
@@ -235,6 +260,18 @@ template <typename T>
 __device__ __forceinline__ void cp_async_elem(T *smem, const T *gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   if (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+// cp.async of NB = 4, 8 or 16 bytes (both addresses NB-aligned)
+template <int NB>
+__device__ __forceinline__ void cp_async_bytes(void *smem, const void *gmem) {
+  static_assert(NB == 4 || NB == 8 || NB == 16, "cp.async copies 4, 8 or 16 bytes");
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if (NB == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+  else if (NB == 8)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
@@ -414,6 +451,119 @@ __device__ __forceinline__ void load_tile(const GmgView<T> &V, const LvArgs &L, 
   for (int f = 0; f < 2 * D; f++)
     if ((fl & wall_bit(f >> 1, f & 1)) || s_nb[f] < 0) sf |= (unsigned)f << (4 * nsf++);
   if (nsf == 0) return;  // every ghost came from a same-level neighbour
+  for (int i = threadIdx.x; i < nsf * nf; i += blockDim.x) {
+    const int k = i / nf, j = i - k * nf;
+    const int f = (int)((sf >> (4 * k)) & 15u);
+    const int a = f >> 1, side = f & 1;
+    const bool wall = (fl & wall_bit(a, side)) != 0;
+    const int u = j % n, v = D == 3 ? j / n : 0;
+    const int gn = side ? n : -1, mn = side ? n - 1 : 0;
+    const int gx = a == 0 ? gn : u, gy = a == 1 ? gn : (a == 0 ? u : v), gz = a == 2 ? gn : v;
+    T val;
+    if (wall) {
+      const int mx = a == 0 ? mn : u, my = a == 1 ? mn : (a == 0 ? u : v), mz = a == 2 ? mn : v;
+      val = wall_reflect(tile[G.idx(mx, my, mz)], (V.wneu >> f) & 1);
+    } else {
+      const int g[3] = {gx, gy, gz};
+      val = refine_ghost<T, D>(V.phi, V.nbr, V.flags, V.parent, V.pofs, V.wneu, L, Lp, bid, g, a, own);
+    }
+    tile[G.idx(gx, gy, gz)] = val;
+  }
+  __syncthreads();
+}
+
+// PW BF16 values in one load (16, 8, 4 or 2 bytes)
+template <int PW>
+struct BfVec;
+template <>
+struct BfVec<8> {
+  using type = uint4;
+};
+template <>
+struct BfVec<4> {
+  using type = uint2;
+};
+template <>
+struct BfVec<2> {
+  using type = unsigned int;
+};
+template <>
+struct BfVec<1> {
+  using type = unsigned short;
+};
+
+// load_tile for a level whose phi is stored as BF16 (the finest level of
+// GMG_MIXED_BF16; compiled block sides only): the same tile of T values,
+// widened on the way in.  The block's run is read in pieces of PW cells of
+// one colour of one row (16 bytes when a row's colour half allows), b as
+// 16-byte cp.async in the run's order, the face ghosts by plain loads, then
+// wall and refinement-boundary ghosts as in load_tile.  Ends with a barrier.
+template <typename T, int D, int NT, typename Mid = NoMid>
+__device__ __forceinline__ void load_tile_h(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, T *tile,
+                                            T *sbv, unsigned char *sflag, long long sb, Mid mid = Mid()) {
+  static_assert(NT != 0, "BF16 levels have a compiled block side");
+  __shared__ int s_nb[6];
+  __shared__ int s_fl;
+  constexpr int n = NT, HN = NT / 2;
+  constexpr int ncell = D == 3 ? n * n * n : n * n;
+  constexpr int PW = HN % 8 == 0 ? 8 : (HN % 4 == 0 ? 4 : (HN % 2 == 0 ? 2 : 1));
+  const TileGeo<T, D> G(n);
+  if (threadIdx.x < 2 * D) {
+    const int a = threadIdx.x >> 1, side = threadIdx.x & 1;
+    const int o[3] = {a == 0 ? 2 * side - 1 : 0, a == 1 ? 2 * side - 1 : 0, a == 2 ? 2 * side - 1 : 0};
+    s_nb[threadIdx.x] = V.nbr[(size_t)bid * kNbr + nbr_slot(o[0], o[1], o[2])];
+  }
+  if (threadIdx.x == 0) s_fl = V.flags[bid];
+  const long long base = L.off + (long long)(bid - L.first) * ncell;    // b
+  const long long pbase = L.poff + (long long)(bid - L.first) * ncell;  // phi, level-local
+  const bf16s *own = V.hphi + pbase;
+  constexpr int VEC = 16 / sizeof(T);
+  if (ncell % VEC == 0) {
+    for (int i = threadIdx.x; i < ncell / VEC; i += blockDim.x) cp_async16(sbv + i * VEC, V.b + base + i * VEC);
+  } else {
+    for (int q = threadIdx.x; q < ncell; q += blockDim.x) cp_async_elem(sbv + q, V.b + base + q);
+  }
+  using PV = typename BfVec<PW>::type;
+  for (int i = threadIdx.x; i < ncell / PW; i += blockDim.x) {
+    const PV v = __ldcg(reinterpret_cast<const PV *>(own) + i);
+    int x, y, z;
+    cs_xyz(i * PW, n, ncell, D, &x, &y, &z);
+    const bf16s *e = reinterpret_cast<const bf16s *>(&v);
+#pragma unroll
+    for (int q = 0; q < PW; q++) tile[G.idx(x + 2 * q, y, z)] = ld_val(e[q]);
+  }
+  if (sflag && sb >= 0) {  // which cells of a cut block have a non-regular stencil
+    const unsigned char *src = V.spec + sb / (2 * D + 1);
+    if (ncell % 16 == 0 && ((size_t)src & 15) == 0) {
+      for (int i = threadIdx.x; i < ncell / 16; i += blockDim.x) cp_async16(sflag + 16 * i, src + 16 * i);
+    } else {
+      for (int c = threadIdx.x; c < ncell; c += blockDim.x) sflag[c] = src[c];
+    }
+  }
+  __syncthreads();
+  mid();
+  const int fl = s_fl;
+  constexpr int nf = D == 3 ? n * n : n;
+  for (int i = threadIdx.x; i < 2 * D * nf; i += blockDim.x) {
+    const int f = i / nf, j = i - f * nf;
+    const int a = f >> 1, side = f & 1;
+    const int id = s_nb[f];
+    if ((fl & wall_bit(a, side)) || id < 0) continue;
+    const int u = j % n, v = D == 3 ? j / n : 0;
+    const int gn = side ? n : -1, sn = side ? 0 : n - 1;
+    const int gx = a == 0 ? gn : u, gy = a == 1 ? gn : (a == 0 ? u : v), gz = a == 2 ? gn : v;
+    const int qx = a == 0 ? sn : u, qy = a == 1 ? sn : (a == 0 ? u : v), qz = a == 2 ? sn : v;
+    tile[G.idx(gx, gy, gz)] =
+        ld_val(V.hphi[L.poff + (long long)(id - L.first) * ncell + cs_pos_xyz(qx, qy, qz, n, ncell)]);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  unsigned sf = 0;
+  int nsf = 0;
+#pragma unroll
+  for (int f = 0; f < 2 * D; f++)
+    if ((fl & wall_bit(f >> 1, f & 1)) || s_nb[f] < 0) sf |= (unsigned)f << (4 * nsf++);
+  if (nsf == 0) return;
   for (int i = threadIdx.x; i < nsf * nf; i += blockDim.x) {
     const int k = i / nf, j = i - k * nf;
     const int f = (int)((sf >> (4 * k)) & 15u);
@@ -631,7 +781,8 @@ __device__ __forceinline__ void cut_residuals(const GmgView<T> &V, const TileGeo
 // FAS kernel sets it): other CTAs of this launch may still read the parent
 // level's phi for their refinement-boundary ghosts, and must see the values
 // from before the restriction, as the sequential order has it.
-template <typename T, int D, int NT>
+// H: the level's phi is stored as BF16 (load_tile_h).
+template <typename T, int D, int NT, bool H = false>
 __device__ void resid_restrict_block(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, unsigned char *smem_raw) {
   const int n = NT ? NT : L.n, hn = n / 2;
   const TileGeo<T, D> G(n);
@@ -643,9 +794,13 @@ __device__ void resid_restrict_block(const GmgView<T> &V, const LvArgs &L, const
   const int4 cl = V.cut_list[bid];
   const int m = cl.y + cl.z;
   CutCell<T, D> q;
-  load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv, sfl, sb, [&] {
+  auto prefetch = [&] {
     if ((int)threadIdx.x < m) q.fetch(V, cl.x + threadIdx.x);
-  });
+  };
+  if constexpr (H)
+    load_tile_h<T, D, NT>(V, L, Lp, bid, tile, sbv, sfl, sb, prefetch);
+  else
+    load_tile<T, D, NT>(V, L, Lp, bid, tile, sbv, sfl, sb, prefetch);
   cut_residuals<T, D>(V, G, n, tile, sbv, cl, q);
   const T inv_h2 = T(L.ih2);
   const int pofs[3] = {po & 1023, (po >> 10) & 1023, (po >> 20) & 1023};
@@ -676,14 +831,14 @@ __device__ void resid_restrict_block(const GmgView<T> &V, const LvArgs &L, const
   }
 }
 
-template <typename T, int D, int NT>
+template <typename T, int D, int NT, bool H = false>
 __global__ void __launch_bounds__(kThreads) k_resid_restrict(GmgView<T> V, LvArgs L, LvArgs Lp) {
   pdl_start();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int bid;
   GmgView<T> W;
   if (!slot_item(V, L, &bid, &W)) return;
-  resid_restrict_block<T, D, NT>(W, L, Lp, bid, smem_raw);
+  resid_restrict_block<T, D, NT, H>(W, L, Lp, bid, smem_raw);
 }
 
 // FAS coarse right-hand side on covered cells: b <- A phi + (restricted r);
@@ -780,7 +935,9 @@ __global__ void __launch_bounds__(kThreads) k_coarse(GmgView<T> V, LvArgs Lc, co
 // (Sec. 2.2, 3.4): weights 3/4 and 1/4 per dimension from the parent cell
 // and its neighbours toward the fine cell (reading P).  The block's own
 // cells are held in registers, sized for CTAs of at least PT threads.
-template <typename T, int D, int NT, int PT = kThreads>
+// H: the fine level's phi is stored as BF16 (read, corrected in T, rounded
+// back).
+template <typename T, int D, int NT, int PT = kThreads, bool H = false>
 __device__ void prolong_block(const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int bid, unsigned char *smem_raw) {
   __shared__ int s_nb[kNbr];
   T *tile = reinterpret_cast<T *>(smem_raw);
@@ -793,6 +950,8 @@ __device__ void prolong_block(const GmgView<T> &V, const LvArgs &L, const LvArgs
   using VT = typename Vec16<T>::type;
   const long long base = L.poff + (long long)(bid - L.first) * NCELL;
   VT *__restrict__ fine = reinterpret_cast<VT *>(V.phi + base);
+  uint2 *__restrict__ fineh = H ? reinterpret_cast<uint2 *>(V.hphi + base) : nullptr;  // 4 BF16 a vector
+  static_assert(!H || VEC == 4, "BF16 levels are FP32 levels");
   // vectors in pairs: vector i of the red half and vector i of the black
   // half hold the two colours of the same 2 VEC consecutive cells of a row
   // (when a row's colour half is whole vectors)
@@ -805,8 +964,16 @@ __device__ void prolong_block(const GmgView<T> &V, const LvArgs &L, const LvArgs
     for (int k = 0; k < IV; k++) {
       const int i = threadIdx.x + k * blockDim.x;
       if (i < HV) {
-        rv[k] = fine[i];
-        rw[k] = fine[HV + i];
+        if constexpr (H) {
+          const uint2 a = fineh[i], b = fineh[HV + i];
+          rv[k] = make_float4(ld_val((bf16s)(a.x & 0xffffu)), ld_val((bf16s)(a.x >> 16)),
+                              ld_val((bf16s)(a.y & 0xffffu)), ld_val((bf16s)(a.y >> 16)));
+          rw[k] = make_float4(ld_val((bf16s)(b.x & 0xffffu)), ld_val((bf16s)(b.x >> 16)),
+                              ld_val((bf16s)(b.y & 0xffffu)), ld_val((bf16s)(b.y >> 16)));
+        } else {
+          rv[k] = fine[i];
+          rw[k] = fine[HV + i];
+        }
       }
     }
   }
@@ -862,31 +1029,43 @@ __device__ void prolong_block(const GmgView<T> &V, const LvArgs &L, const LvArgs
             e1[q] += b;
           }
         }
-        fine[i] = rv[k];
-        fine[HV + i] = rw[k];
+        if constexpr (H) {
+          auto pack = [](float lo, float hi) {
+            return (unsigned)st_val<bf16s>(lo) | ((unsigned)st_val<bf16s>(hi) << 16);
+          };
+          fineh[i] = make_uint2(pack(rv[k].x, rv[k].y), pack(rv[k].z, rv[k].w));
+          fineh[HV + i] = make_uint2(pack(rw[k].x, rw[k].y), pack(rw[k].z, rw[k].w));
+        } else {
+          fine[i] = rv[k];
+          fine[HV + i] = rw[k];
+        }
       }
     }
   } else {
     for (int q = threadIdx.x; q < NCELL; q += blockDim.x) {
       int x, y, z;
       cs_xyz(q, n, NCELL, D, &x, &y, &z);
-      V.phi[base + q] += interp(x, y, z);
+      if constexpr (H)
+        V.hphi[base + q] = st_val<bf16s>(ld_val(V.hphi[base + q]) + interp(x, y, z));
+      else
+        V.phi[base + q] += interp(x, y, z);
     }
   }
 }
 
-template <typename T, int D, int NT, int PT>
+template <typename T, int D, int NT, int PT, bool H = false>
 __global__ void __launch_bounds__(PT) k_prolong(GmgView<T> V, LvArgs L, LvArgs Lp) {
   pdl_start();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int bid;
   GmgView<T> W;
   if (!slot_item(V, L, &bid, &W)) return;
-  prolong_block<T, D, NT, PT>(W, L, Lp, bid, smem_raw);
+  prolong_block<T, D, NT, PT, H>(W, L, Lp, bid, smem_raw);
 }
 
 // phi of covered cells <- mean of the children (composite consistency).
-template <typename T, int D, int NT>
+// H: the fine level's phi is stored as BF16.
+template <typename T, int D, int NT, bool H = false>
 __global__ void __launch_bounds__(kThreads) k_restrict_phi(GmgView<T> V0, LvArgs L, LvArgs Lp) {
   pdl_start();
   int bid;
@@ -905,7 +1084,13 @@ __global__ void __launch_bounds__(kThreads) k_restrict_phi(GmgView<T> V0, LvArgs
     T sp = T(0);
     for (int dz = 0; dz < (D == 3 ? 2 : 1); dz++)
       for (int dy = 0; dy < 2; dy++)
-        for (int dx = 0; dx < 2; dx++) sp = sp + V.phi[base + cs_pos_xyz(2 * qx + dx, 2 * qy + dy, 2 * qz + dz, n, NCELL)];
+        for (int dx = 0; dx < 2; dx++) {
+          const long long f = base + cs_pos_xyz(2 * qx + dx, 2 * qy + dy, 2 * qz + dz, n, NCELL);
+          if constexpr (H)
+            sp = sp + ld_val(V.hphi[f]);
+          else
+            sp = sp + V.phi[f];
+        }
     V.phi[pbase + cs_pos_xyz(pofs[0] + qx, pofs[1] + qy, D == 3 ? pofs[2] + qz : 0, pn, Lp.ncell)] = sp * w;
   }
 }
