@@ -59,6 +59,25 @@ struct BfPiece {
   static constexpr int value = HN % 8 == 0 ? 8 : (HN % 4 == 0 ? 4 : 2);
 };
 
+// Two adjacent tile entries (the first at an even index) as floats, and a
+// paired store of two results (rounded to BF16 for a BF16 level).
+__device__ __forceinline__ void ld_pair(const float *p, float *v) {
+  const float2 w = *reinterpret_cast<const float2 *>(p);
+  v[0] = w.x;
+  v[1] = w.y;
+}
+__device__ __forceinline__ void ld_pair(const bf16s *p, float *v) {
+  const unsigned w = *reinterpret_cast<const unsigned *>(p);
+  v[0] = __uint_as_float(w << 16);
+  v[1] = __uint_as_float(w & 0xffff0000u);
+}
+__device__ __forceinline__ void st_pair(float *p, float v0, float v1) {
+  *reinterpret_cast<float2 *>(p) = make_float2(v0, v1);
+}
+__device__ __forceinline__ void st_pair(bf16s *p, float v0, float v1) {
+  *reinterpret_cast<unsigned *>(p) = (unsigned)st_val<bf16s>(v0) | ((unsigned)st_val<bf16s>(v1) << 16);
+}
+
 // cs_stage_interior for BF16 phi: slot base rs_h in hphi (level-local
 // offsets); b as T.
 template <typename T, int D, int NT>
@@ -369,17 +388,67 @@ __device__ __forceinline__ void smooth_cs_block(const GmgView<T> &V, const LvArg
     t[5] = D == 3 ? G::at(G::row(y, z + 1), k) : 0;
     return 2 * k + q + NT * (y + NT * z);  // natural index of the cell
   };
-  for (int j = threadIdx.x; j < G::H; j += blockDim.x) {
-    int t[6];
-    const int cn = nbrs(j, t);
-    if (sb >= 0 && sfl[cn]) continue;  // a listed cell
+  if constexpr (std::is_same<T, float>::value) {
+    // FP32 arithmetic: two cells of a row at a time, k and k + 1 (k even).
+    // Their x neighbours are three consecutive tile entries, their y and z
+    // neighbours and their b adjacent pairs (one 8-byte, or for BF16 one
+    // 4-byte, shared load each), their results one paired store.  Each
+    // cell's sum is the single-cell loop's, term for term and in the same
+    // order.
+    static_assert(G::RO % 2 == 0 && G::X0 % 2 == 0 && G::HN % 2 == 0, "pairs start on even tile entries");
+    for (int jp = threadIdx.x; jp < G::H / 2; jp += blockDim.x) {
+      const int j = 2 * jp;
+      const int r = j / G::HN, k = j - r * G::HN;
+      const int y = r % NT, z = D == 3 ? r / NT : 0;
+      const int q = (y + z + color) & 1;
+      const int cn = 2 * k + q + NT * (y + NT * z);  // natural index of the first cell
+      const bool l0 = sb >= 0 && sfl[cn], l1 = sb >= 0 && sfl[cn + 2];  // listed cells
+      if (l0 && l1) continue;
+      const int xa = G::at(G::row(y, z), k - 1 + q);
+      const int ym = G::at(G::row(y - 1, z), k), yp = G::at(G::row(y + 1, z), k);
+      const int zm = D == 3 ? G::at(G::row(y, z - 1), k) : 0, zp = D == 3 ? G::at(G::row(y, z + 1), k) : 0;
 #pragma unroll
-    for (int s = 0; s < SG; s++) {
-      if (slot[s] < 0) continue;
-      const S *o = O + s * G::OS;
-      T sum = (ld_val(o[t[0]]) + ld_val(o[t[1]])) + (ld_val(o[t[2]]) + ld_val(o[t[3]]));
-      if (D == 3) sum += ld_val(o[t[4]]) + ld_val(o[t[5]]);
-      Pf[slot[s] * rsP + pown + j] = st_val<S>((sum - h2 * B[s * G::H + j]) * inv2d);
+      for (int s = 0; s < SG; s++) {
+        if (slot[s] < 0) continue;
+        const S *o = O + s * G::OS;
+        const float x0 = ld_val(o[xa]), x1 = ld_val(o[xa + 1]), x2 = ld_val(o[xa + 2]);
+        float a[2], b[2], c[2] = {0.f, 0.f}, d[2] = {0.f, 0.f};
+        ld_pair(o + ym, a);
+        ld_pair(o + yp, b);
+        if (D == 3) {
+          ld_pair(o + zm, c);
+          ld_pair(o + zp, d);
+        }
+        float s0 = (x0 + x1) + (a[0] + b[0]);
+        float s1 = (x1 + x2) + (a[1] + b[1]);
+        if (D == 3) {
+          s0 += c[0] + d[0];
+          s1 += c[1] + d[1];
+        }
+        const float2 bb = *reinterpret_cast<const float2 *>(B + s * G::H + j);
+        const float v0 = (s0 - h2 * bb.x) * inv2d, v1 = (s1 - h2 * bb.y) * inv2d;
+        S *dst = Pf + slot[s] * rsP + pown + j;
+        if (!l0 && !l1 && ((size_t)dst & (2 * sizeof(S) - 1)) == 0) {
+          st_pair(dst, v0, v1);
+        } else {
+          if (!l0) dst[0] = st_val<S>(v0);
+          if (!l1) dst[1] = st_val<S>(v1);
+        }
+      }
+    }
+  } else {
+    for (int j = threadIdx.x; j < G::H; j += blockDim.x) {
+      int t[6];
+      const int cn = nbrs(j, t);
+      if (sb >= 0 && sfl[cn]) continue;  // a listed cell
+#pragma unroll
+      for (int s = 0; s < SG; s++) {
+        if (slot[s] < 0) continue;
+        const S *o = O + s * G::OS;
+        T sum = (ld_val(o[t[0]]) + ld_val(o[t[1]])) + (ld_val(o[t[2]]) + ld_val(o[t[3]]));
+        if (D == 3) sum += ld_val(o[t[4]]) + ld_val(o[t[5]]);
+        Pf[slot[s] * rsP + pown + j] = st_val<S>((sum - h2 * B[s * G::H + j]) * inv2d);
+      }
     }
   }
   auto upd = [&](const CutCell<T, D> &u) {
@@ -406,9 +475,12 @@ __device__ __forceinline__ void smooth_cs_block(const GmgView<T> &V, const LvArg
 
 // The half-sweep kernel: one CTA per (block, group of SG slots); the grid
 // holds count x ceil(nrhs / SG) CTAs, slot groups fastest.  Frozen units
-// are skipped per slot.
+// are skipped per slot.  FP32 16^3 blocks ask for five CTAs of 256 threads
+// per SM (at most 51 registers a thread; the paired loop would otherwise
+// take 58 and leave four).
 template <typename T, int D, int NT, int SG, bool BF = false>
-__global__ void __launch_bounds__(kThreads) k_smooth_cs(GmgView<T> V, LvArgs L, LvArgs Lp, int color) {
+__global__ void __launch_bounds__(kThreads, (NT == 16 && sizeof(T) == 4) ? 5 : 0)
+    k_smooth_cs(GmgView<T> V, LvArgs L, LvArgs Lp, int color) {
   pdl_start();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ngrp = (V.nrhs + SG - 1) / SG;
