@@ -18,7 +18,7 @@ namespace gmg {
 
 struct GridBar {
   unsigned int count;  // arrivals during the current launch
-  unsigned int unused;
+  unsigned int fold;   // CTAs of the residual kernel done (ResFold; 0 between launches)
   int err;             // first error recorded by a wait that ran out
   int pad;
 };

@@ -940,9 +940,31 @@ int fmg_any(gmg_tree *t, cudaStream_t s) {
 // Composite residual of the FP64 state over the leaf blocks: per-block
 // partials, deterministic final reduction into d_red and a copy to the
 // pinned host mirror; with `rout` also the float residual (mixed path).
+//
+// When one level holds all the leaves and its CTAs have kResThreads
+// threads, the residual launch's last CTA also does the final reduction
+// (ResFold), bit for bit as k_reduce_partials, and the step has one launch
+// fewer; at most 64 units, so that one CTA's reduction stays short.
 template <int D>
 int residual_impl(gmg_tree *t, cudaStream_t s, float *rout) {
   GmgView<double> V = view<double>(t);
+  int leaf_levels = 0, only = -1;
+  for (int l = t->lmin; l <= t->lmax; l++)
+    if (t->level_has_leaves[l - t->lmin]) {
+      leaf_levels++;
+      only = l;
+    }
+  ResFold F{};
+  if (leaf_levels == 1 && resnorm_threads(t, only) == kResThreads && t->units() <= 64) {
+    F.counter = &t->d_bar->fold;
+    F.out = t->d_red;
+    F.tree_blocks = t->d_tree_blocks;
+    F.tree_boff = t->d_tree_boff;
+    F.err = &t->d_bar->err;
+    F.ntree = t->ntree;
+    F.units = t->units();
+    F.on = 1;
+  }
   for (int l = t->lmin; l <= t->lmax; l++) {
     LvArgs L = lv(t, l), Lp = l > t->lmin ? lv(t, l - 1) : L;
     if (!t->level_has_leaves[l - t->lmin]) continue;
@@ -951,14 +973,15 @@ int residual_impl(gmg_tree *t, cudaStream_t s, float *rout) {
       constexpr int NT = decltype(nt)::value;
       launch(t, s, 6, 0, l, [&] {
         klaunch(t, L.count * t->nrhs, resnorm_threads(t, l), sm, s, k_resnorm<double, D, NT>, V, L, Lp, t->d_partials, rout,
-                                                                       (int)t->blocks.size());
+                                                                       (int)t->blocks.size(), F);
       });
     });
   }
-  launch(t, s, 7, 0, t->lmax, [&] {
-    klaunch(t, t->units(), kResThreads, 0, s, k_reduce_partials, (const double *)t->d_partials, (int)t->blocks.size(), (const int *)t->d_tree_blocks,
-                                                  t->d_tree_boff, t->ntree, t->d_red, t->d_bar);
-  });
+  if (!F.on)
+    launch(t, s, 7, 0, t->lmax, [&] {
+      klaunch(t, t->units(), kResThreads, 0, s, k_reduce_partials, (const double *)t->d_partials, (int)t->blocks.size(), (const int *)t->d_tree_blocks,
+                                                    t->d_tree_boff, t->ntree, t->d_red, t->d_bar);
+    });
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemcpyAsync(t->h_red, t->d_red, 4 * sizeof(double) * t->units(), cudaMemcpyDeviceToHost, s));
   return GMG_OK;

@@ -1125,21 +1125,61 @@ __device__ __forceinline__ void block_reduce3(double s2, double mx, double b2, d
   }
 }
 
+// The final norm reduction folded into the residual launch (when it is the
+// step's only residual launch, with kResThreads threads a CTA): each CTA
+// counts itself in after writing its partials, and the last one reduces
+// every unit's partials exactly as k_reduce_partials does (same threads,
+// same order: the same bits), then re-arms the counter.
+struct ResFold {
+  unsigned int *counter;  // 0 between launches
+  double *out;            // [units][4]: sum r^2, max |r|, sum b^2, barrier error
+  const int *tree_blocks, *tree_boff;
+  const int *err;         // the coarse cycle's barrier error word
+  int ntree, units, on;
+};
+
+__device__ __forceinline__ void fold_norms(const ResFold &F, const double *partials0, int nbt) {
+  __shared__ bool s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();  // this CTA's partials before its arrival
+    s_last = atomicAdd(F.counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int u = 0; u < F.units; u++) {
+    const int r = u / F.ntree, tr = u % F.ntree;
+    const double *p = partials0 + (size_t)r * nbt * 3;
+    const int b0 = F.tree_boff[tr], b1 = F.tree_boff[tr + 1];
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int k = b0 + threadIdx.x; k < b1; k += blockDim.x) {
+      const size_t i = (size_t)F.tree_blocks[k];
+      a += __ldcg(p + i * 3);
+      b = fmax(b, __ldcg(p + i * 3 + 1));
+      c += __ldcg(p + i * 3 + 2);
+    }
+    block_reduce3(a, b, c, F.out + (size_t)u * 4);
+    if (threadIdx.x == 0) F.out[(size_t)u * 4 + 3] = F.err ? (double)*F.err : 0.0;
+    __syncthreads();  // block_reduce3's shared words serve the next unit
+  }
+  if (threadIdx.x == 0) *F.counter = 0u;
+}
+
 // Residual norms over the leaf blocks of a level (reading R); with `rout`
 // the residual itself is written as float (right-hand side of the FP32
-// correction V-cycle in the mixed path).
+// correction V-cycle in the mixed path).  With F.on, the final reduction
+// follows in the last CTA (fold_norms).
 template <typename T, int D, int NT>
-__global__ void __launch_bounds__(kResThreads, 4) k_resnorm(GmgView<T> V0, LvArgs L, LvArgs Lp, double *partials,
-                                                      float *rout, int nbt) {
-  pdl_start();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void resnorm_block(const GmgView<T> &V0, const LvArgs &L, const LvArgs &Lp,
+                                              double *partials, float *rout, int nbt, unsigned char *smem_raw) {
   int bid;
   GmgView<T> V;
   const int slot = (int)(blockIdx.x % (unsigned)V0.nrhs);
   if (!slot_item(V0, L, &bid, &V)) return;  // a frozen slot keeps its last partials
   partials += ((size_t)slot * nbt + bid) * 3;
   if (V.flags[bid] & kHasChildren) {
-    if (threadIdx.x < 3) partials[threadIdx.x] = 0.0;
+    if (threadIdx.x == 0) partials[0] = partials[1] = partials[2] = 0.0;  // one writer, as block_reduce3
     return;
   }
   if (rout) rout += slot * V0.rs_f;
@@ -1193,6 +1233,15 @@ __global__ void __launch_bounds__(kResThreads, 4) k_resnorm(GmgView<T> V0, LvArg
     acc(c, to_f32(resid_cell<T, D>(nullptr, -1, tile, G.idx(x, y, z), G.sy, G.sz, NCELL, c, inv_h2, bb)), bb);
   }
   block_reduce3((double)s2f, (double)mxf, (double)b2f, partials);
+}
+
+template <typename T, int D, int NT>
+__global__ void __launch_bounds__(kResThreads, 4) k_resnorm(GmgView<T> V0, LvArgs L, LvArgs Lp, double *partials,
+                                                      float *rout, int nbt, ResFold F) {
+  pdl_start();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  resnorm_block<T, D, NT>(V0, L, Lp, partials, rout, nbt, smem_raw);
+  if (F.on) fold_norms(F, partials, nbt);
 }
 
 // Deterministic final reduction of the per-block partials (fixed order),

@@ -119,6 +119,8 @@ void launch_resnorm(gmg_tree *t, int l, double *partials, const int *active, cud
   for (int w = 0; w < 6; w++) V.wneu |= (t->wall_type[w] == GMG_WALL_NEUMANN ? 1 : 0) << w;
   V.nrhs = 1;  // slot 0 only, all trees of a forest as one unit
   V.rs_phi = V.rs_f = t->total_cells;
+  V.hphi = nullptr;
+  V.rs_h = 0;
   V.ntree = 1;
   V.tree_of = t->d_tree_of;
   V.active = active;
@@ -130,8 +132,9 @@ void launch_resnorm(gmg_tree *t, int l, double *partials, const int *active, cud
     Lp = gmg::LvArgs{Pi.first, Pi.count, Pi.n, Pi.ncell, Pi.off, Pi.h, Pi.off, 0, 0, Pi.h * Pi.h, 1.0 / (Pi.h * Pi.h)};
   }
   const size_t sm = gmg::resnorm_smem_bytes<double>(D, Li.n);
+  gmg::ResFold off{};  // partials only; the final reduction is its own launch here
   gmg::k_resnorm<double, D, NT><<<L.count, gmg::resnorm_threads(t, l), sm, s>>>(V, L, Lp, partials, nullptr,
-                                                                  (int)t->blocks.size());
+                                                                  (int)t->blocks.size(), off);
 }
 
 // the block sides the library's own residual launch specialises

@@ -41,6 +41,14 @@ def test_library_exports_every_declared_function(G):
     assert not missing, missing
 
 
+def test_precision_constants_match_the_header(G):
+    """The binding's precision codes are the header's GMG_FP64, GMG_MIXED and
+    GMG_MIXED_BF16."""
+    txt = open(os.path.join(ROOT, "include", "gmg.h")).read()
+    defs = dict((k, int(v)) for k, v in re.findall(r"^#define (GMG_(?:FP64|MIXED|MIXED_BF16)) (\d+)", txt, flags=re.M))
+    assert defs == {"GMG_FP64": G.FP64, "GMG_MIXED": G.MIXED, "GMG_MIXED_BF16": G.MIXED_BF16}
+
+
 def test_library_fails_loudly_without_binary(G, tmp_path, monkeypatch):
     import paper_2205_09411_gb300 as mod
     monkeypatch.setattr(mod, "_lib", None)
