@@ -315,7 +315,8 @@ int gmg_residual(gmg_tree *tree, double *rel_l2, double *linf, void *stream);
  * Errors: INVALID_ARG, STATE (tree not bound), CUDA. */
 int gmg_residual_noalloc(gmg_tree *tree, double *out, void *stream);
 /* Solves every unit (slot, tree) to ||b - A phi||_2 <= rel_tol ||b||_2 from
- * its current phi with GMG_FP64 V-cycles or GMG_MIXED defect correction.  A
+ * its current phi with GMG_FP64 V-cycles or GMG_MIXED / GMG_MIXED_BF16 defect
+ * correction.  A
  * unit that reaches the tolerance is frozen: later cycles skip its blocks,
  * so its result does not depend on the other units.  stats: NULL or an
  * array of nrhs * n_trees entries.  Synchronises once per cycle (the
@@ -336,8 +337,9 @@ int gmg_solve_history(gmg_tree *tree, int precision, double rel_tol, int max_cyc
 /* One step of the solve loop on the units with active[u] != 0 (host array
  * of nrhs * n_trees ints; the other units are left untouched): residual_only != 0 runs
  * the composite residual only (the first step of a new right-hand side; in
- * GMG_MIXED it also prepares the FP32 defect), else one V-cycle (FP64) or
- * one defect-correction step (GMG_MIXED) followed by the residual.  Writes
+ * GMG_MIXED and GMG_MIXED_BF16 it also prepares the FP32 defect), else one
+ * V-cycle (FP64) or one defect-correction step (GMG_MIXED, GMG_MIXED_BF16)
+ * followed by the residual.  Writes
  * every unit's relative L2 and max residual into rel_l2 / linf (host arrays
  * of nrhs * n_trees doubles, or NULL; a unit not stepped keeps its last
  * values).

@@ -159,3 +159,27 @@ def test_bf16_full_size_sphere_configuration():
     o.set_solution(phi)
     l2, _, bn = o.residual()
     assert l2 / bn <= 1.05e-8
+
+
+@pytest.mark.parametrize("name,option,value", [("c2_64", "fmg_steps", 1), ("adaptive3d", "inner_cycles", 2),
+                                               ("needle4", "inner_cycles", 2), ("c2_64", "fused_sweeps", 1)])
+def test_bf16_with_schedule_options(name, option, value):
+    """BF16 state under the other schedule options: FMG steps (the finest
+    level's BF16 kernels inside each FMG cycle), two FP32 cycles per step on
+    adaptive trees (the covered cells' phi restricted from the BF16 level
+    between them) and fused sweeps on the FP32 levels below: 1e-8 by the
+    oracle's own residual, with the BF16 kernels on the finest level only."""
+    import paper_2205_09411_gb300 as G
+    p = parity_cases()[name]
+    t = gpu_problem(p)
+    t.set_option("coarse_coop", 0)
+    t.set_option(option, value)
+    lv, _ = _bf16_levels(t, G.MIXED_BF16)
+    assert lv == [t.lmax], lv
+    t.set_rhs(np.asarray(p["rhs"](t.leaf_centers()), dtype=np.float64))
+    st = t.solve(G.MIXED_BF16, 1e-8, 80)
+    assert st["rel_l2"] <= 1e-8
+    o = oracle_problem(p)
+    o.set_solution(t.solution())
+    l2, _, bn = o.residual()
+    assert l2 / bn <= 1.05e-8
