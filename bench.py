@@ -266,6 +266,12 @@ def algorithmic_bytes(kind, prec, level, t, leaf_level, nrhs=1, cluster=False):
         return cells * 4 * S + listed * entry
     if kind == "resid_norm":  # read phi64, b64 (+ write r32 in the mixed path)
         return cells * (16 + 4) + listed * (7 * 8 + 4)
+    if kind in ("level_leg_down", "level_leg_up"):  # one cooperative launch: a leg's sweeps and transfer
+        nsw = t.level_sweeps(level)[0 if kind == "level_leg_down" else 1]
+        sweeps = 2 * nsw * (cells * (Sp + 0.5 * Sc) + listed * entry / 2)
+        if kind == "level_leg_down":
+            return sweeps + cells * (Sp + Sc + 2 * Sc / 8) + listed * entry
+        return sweeps + cells * (2 * Sp + 2 * Sc / 8)
     if kind == "accumulate":  # read e32, read/write phi64 on the leaf cells of all levels
         if prec == "bf16":  # the finest level's e as BF16 (all its blocks are leaves)
             nbl, nl, _ = t.level_info(t.lmax)

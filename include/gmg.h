@@ -400,7 +400,8 @@ long long gmg_last_launch_count(const gmg_tree *tree);
  * 2 FAS right-hand side, 3 coarse solve, 4 prolongation, 5 restriction of
  * phi, 6 residual norm, 7 norm reduction, 8 mixed-path accumulation,
  * 9 right-hand side / copies, 10 bottom of the cycle on a thread-block
- * cluster (GMG_OPT_CLUSTER_TAIL). */
+ * cluster (GMG_OPT_CLUSTER_TAIL), 11 down leg and 12 up leg of a level in one
+ * cooperative launch (GMG_OPT_LEVEL_LEGS). */
 int gmg_profile_enable(gmg_tree *tree, int enable);
 int gmg_profile_read(gmg_tree *tree, int cap, int *kind, int *prec, int *level, long long *launches, double *ms);
 
@@ -450,6 +451,12 @@ int gmg_profile_read(gmg_tree *tree, int cap, int *kind, int *prec, int *level, 
                                     N/2 cells a side), 16 (parts of N/2 x N/2 x N/4; non-portable
                                     cluster size, split levels' sides multiples of 8), or 0: 16
                                     when the tree and the device allow it, else 8; same arithmetic */
+#define GMG_OPT_LEVEL_LEGS 14    /* [0] a level whose (block, slot) CTAs fit on the GPU at once (256
+                                    threads, four per SM: the 512 blocks of a 128^3 tree in 16^3
+                                    blocks) runs its down leg (sweeps, residual and restriction) and
+                                    its up leg (prolongation, sweeps) as one cooperative launch each,
+                                    with a grid barrier between the phases; same results bit for bit
+                                    (half the launches, the same solve time on the 128^3 sphere) */
 int gmg_set_option(gmg_tree *tree, int option, long long value);
 
 /* Sweep schedule: N_down / N_up red-black sweeps on one level (default: the

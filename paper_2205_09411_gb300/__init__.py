@@ -565,7 +565,7 @@ class Tree:
 
     OPTIONS = {"graphs": 1, "coarse_coop": 2, "spin_limit": 3, "fused_sweeps": 4, "cta_threads": 5,
                "coop_max_blocks": 6, "inner_cycles": 7, "slots_per_cta": 8, "fmg_steps": 9, "pdl": 10,
-               "cluster_tail": 11, "device_setup": 12, "cluster_parts": 13}
+               "cluster_tail": 11, "device_setup": 12, "cluster_parts": 13, "level_legs": 14}
 
     def set_level_sweeps(self, level, n_down, n_up):
         """N_down / N_up red-black sweeps on one level (a tuning schedule)."""
@@ -586,7 +586,8 @@ class Tree:
         return int(load().gmg_last_launch_count(self.h))
 
     KERNEL_KINDS = ("smooth", "resid_restrict", "fas_rhs", "coarse_solve", "prolong", "restrict_phi",
-                    "resid_norm", "norm_reduce", "accumulate", "rhs_copy", "coarse_cluster")
+                    "resid_norm", "norm_reduce", "accumulate", "rhs_copy", "coarse_cluster", "level_leg_down",
+                    "level_leg_up")
 
     def profile(self, enable=True):
         _check(load().gmg_profile_enable(self.h, 1 if enable else 0))

@@ -608,6 +608,41 @@ __global__ void __launch_bounds__(kCoopThreads) k_cycle_coop(GmgView<T> V, const
 #undef GMG_LV
 }
 
+// One leg of a level in one cooperative launch: a CTA per (block, slot),
+// all resident at once, with a grid barrier between the phases that the
+// per-level kernels would run as separate launches.  mode 0, the down leg:
+// N_down red/black sweeps, then the residual and its restriction with phi
+// (resid_restrict_block).  mode 1, the up leg: the prolongation of the
+// coarse correction, then N_up red/black sweeps.  Every phase runs the
+// per-level kernels' block functions on the same inputs, so the results are
+// theirs bit for bit; a frozen unit's CTAs skip the work and still take
+// part in each barrier.  A barrier that runs out records GMG_ERR_TIMEOUT and
+// ends the launch.
+template <typename T, int D, int NT>
+__global__ void __launch_bounds__(kThreads, 4) k_level_leg(GmgView<T> V0, LvArgs L, LvArgs Lp, int mode, GridBar *bar,
+                                                           long long spin_limit) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int r = (int)(blockIdx.x % (unsigned)V0.nrhs);
+  const int bid = L.first + (int)(blockIdx.x / (unsigned)V0.nrhs);
+  const bool on = V0.active[unit_of(V0, r, bid)] != 0;
+  const GmgView<T> W = slot_view(V0, r);
+  const int slot0[1] = {0};
+  const unsigned int G = gridDim.x;
+  unsigned int epoch = 0;
+  if (mode == 1) {
+    if (on) prolong_block<T, D, NT>(W, L, Lp, bid, smem_raw);
+    if (!grid_sync(bar, G, spin_limit, &epoch)) return;
+  }
+  const int ns = mode == 0 ? L.nd : L.nu;
+  for (int k = 0; k < ns; k++)
+    for (int c = 0; c < 2; c++) {
+      if (on) smooth_cs_block<T, D, NT, 1>(W, L, Lp, bid, slot0, c, smem_raw);
+      // the up leg's last half-sweep needs no barrier: the launch ends
+      if (!(mode == 1 && k == ns - 1 && c == 1) && !grid_sync(bar, G, spin_limit, &epoch)) return;
+    }
+  if (mode == 0 && on) resid_restrict_block<T, D, NT>(W, L, Lp, bid, smem_raw);
+}
+
 // A cooperative kernel whose barrier waits for one CTA more than it has:
 // the wait must run out and record GMG_ERR_TIMEOUT (failure-detection test).
 __global__ void k_barrier_selftest(GridBar *bar, long long spin_limit) {

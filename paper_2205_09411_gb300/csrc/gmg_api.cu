@@ -389,6 +389,7 @@ void set_smem_limits_nt() {
   kernel_attrs(k_prolong<T, D, NT, 256>, true);
   kernel_attrs(k_resnorm<T, D, NT>, true);
   kernel_attrs(k_restrict_phi<T, D, NT>, false);
+  if constexpr (NT != 0) kernel_attrs(k_level_leg<T, D, NT>, true);
 }
 
 template <typename T, int D>
@@ -531,6 +532,51 @@ bool bf16_level(const gmg_tree *t, int l) {
 template <typename T>
 size_t tile_bytes(const gmg_tree *t, int l) {
   return level_smem_bytes<T>(t->D, t->lev(l).n);
+}
+
+// A level's down leg (mode 0) or up leg (mode 1) in one cooperative launch
+// (k_level_leg) when the level has a compiled block side, 256-thread CTAs,
+// and all its (block, slot) CTAs fit on the GPU at once; *smem gets the
+// launch's shared memory.
+template <typename T, int D, int NT>
+bool level_leg_ok(const gmg_tree *t, int l, size_t *smem) {
+  if constexpr (NT == 0) {
+    return false;
+  } else {
+    if (!t->use_level_legs || t->lev(l).n != NT || cta_threads(t, l) != kThreads) return false;
+    const int hm = NT / 2 + 2;
+    const size_t psm = sizeof(T) * (size_t)(D == 3 ? hm * hm * hm : hm * hm);
+    const size_t sm = std::max(std::max(cs_smem_bytes<T, D, NT>(1), tile_bytes<T>(t, l)), psm);
+    int per_sm = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level_leg<T, D, NT>, kThreads, sm) != cudaSuccess)
+      return false;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    *smem = sm;
+    return per_sm > 0 && (long long)t->lev(l).count * t->nrhs <= (long long)per_sm * sms;
+  }
+}
+
+template <typename T, int D, int NT>
+void launch_level_leg(gmg_tree *t, cudaStream_t s, const GmgView<T> &V, const LvArgs &L, const LvArgs &Lp, int l,
+                      int mode, size_t sm) {
+  if constexpr (NT != 0) {
+    cudaMemsetAsync(&t->d_bar->count, 0, sizeof(unsigned int), s);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(L.count * t->nrhs));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    GridBar *bar = t->d_bar;
+    const long long spin = t->spin_limit;
+    launch(t, s, 11 + mode, prec_of<T>(), l,
+           [&] { cudaLaunchKernelEx(&cfg, k_level_leg<T, D, NT>, V, L, Lp, mode, bar, spin); });
+  }
 }
 
 // The cooperative launch of the coarse part of a V-cycle (coarse_cycle.cuh)
@@ -803,6 +849,11 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s, bool end_restrict, int top) {
     }
     with_nt<D>(L.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
+      size_t lsm = 0;
+      if (!fused && !bf && L.nd > 0 && level_leg_ok<T, D, NT>(t, l, &lsm)) {
+        launch_level_leg<T, D, NT>(t, s, V, L, Lp, l, 0, lsm);
+        return;
+      }
       if (!fused)
         for (int k = 0; k < L.nd; k++)
           for (int c = 0; c < 2; c++)
@@ -841,6 +892,11 @@ int vcycle_impl(gmg_tree *t, cudaStream_t s, bool end_restrict, int top) {
     if (fused) L.poff = L.off + other;  // the down leg left phi in the second buffer
     with_nt<D>(L.n, [&](auto nt) {
       constexpr int NT = decltype(nt)::value;
+      size_t lsm = 0;
+      if (!fused && !bf && L.nu > 0 && level_leg_ok<T, D, NT>(t, l, &lsm)) {
+        launch_level_leg<T, D, NT>(t, s, V, L, Lp, l, 1, lsm);
+        return;
+      }
       launch(t, s, 4, Pl, l,
              [&] { launch_prolong<T, D, NT>(t, cta_threads(t, l), L.count * R, psm, s, V, L, Lp, bf); });
       if (!fused)
@@ -1976,6 +2032,7 @@ int gmg_set_option(gmg_tree *t, int option, long long value) {
       if (value != 0 && value != 8 && value != 16) return set_error("cluster parts must be 0 (auto), 8 or 16"), GMG_ERR_INVALID_ARG;
       t->cluster_parts = (int)value;
       break;
+    case GMG_OPT_LEVEL_LEGS: t->use_level_legs = value != 0; break;
     case GMG_OPT_PDL:
       t->use_pdl = value != 0;
       drop_graphs(t);

@@ -276,6 +276,7 @@ struct gmg_tree {
   int slots_per_cta = 1;      // right-hand-side slots of a block per CTA in the half-sweeps (1, 2, 4)
   bool fmg_steps = false;     // solve steps are FMG cycles instead of V-cycles
   bool use_pdl = true;        // per-level kernels with programmatic dependent launch
+  bool use_level_legs = false; // a level whose CTAs fit at once runs each leg as one cooperative launch
   bool setup_on_device = true;  // boundary detection of built-in level sets on the device when one is present
   bool setup_device = false;    // the last set-up ran its boundary detection on the device
   int cluster_mode = 1;       // bottom of the cycle on a thread-block cluster: 0 off, 1 when all units fit at once, 2 whenever eligible
