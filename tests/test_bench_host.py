@@ -43,6 +43,34 @@ def test_algorithmic_bytes_per_kind():
     assert bench.algorithmic_bytes("accumulate", "fp64", 2, t, 2, nrhs=2) == t.n_leaf_cells * 2 * 20
 
 
+def test_bf16_state_bytes():
+    """BF16 finest-level state: phi 2 bytes, b and the coarser level's fields
+    4 bytes, FP32 cut-list coefficients."""
+    t = FakeTree()
+    cells = 64 * 4096
+    listed = 640
+    entry = 7 * 4 + 4
+    assert bench.algorithmic_bytes("smooth", "bf16", 2, t, 2) == cells * (2 + 0.5 * 4) + listed * entry / 2
+    assert bench.algorithmic_bytes("resid_restrict", "bf16", 2, t, 2) == cells * (2 + 4 + 1) + listed * entry
+    assert bench.algorithmic_bytes("prolong", "bf16", 2, t, 2) == cells * (2 * 2 + 1)
+    # phi64 += e: 20 bytes a leaf cell, 18 on the finest level (all leaves there)
+    assert bench.algorithmic_bytes("accumulate", "bf16", 2, t, 2) == t.n_leaf_cells * 20 - cells * 2
+
+
+def test_level_leg_bytes_are_the_phases_bytes():
+    """A leg in one launch moves what its per-phase launches move: N sweeps of
+    two half-sweeps, plus the residual and restriction (down) or the
+    prolongation (up)."""
+    class Swept(FakeTree):
+        def level_sweeps(self, l):
+            return (2, 3)
+    t = Swept()
+    ab = bench.algorithmic_bytes
+    half = ab("smooth", "fp32", 2, t, 2)
+    assert ab("level_leg_down", "fp32", 2, t, 2) == 4 * half + ab("resid_restrict", "fp32", 2, t, 2)
+    assert ab("level_leg_up", "fp32", 2, t, 2) == 6 * half + ab("prolong", "fp32", 2, t, 2)
+
+
 def test_coarse_cycle_bytes_follow_the_level_visit_model():
     """The coarse kernels count 3S + 3S/8 (down leg) + 3S + 2S/8 (up leg)
     bytes a cell on each level they cover, plus the coarsest-level inverse
